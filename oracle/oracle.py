@@ -1,0 +1,223 @@
+"""ORACLE - TEST INFRASTRUCTURE ONLY.
+
+ctypes front end of ``music_oracle.c``, the plain FP64 CPU restatement of the
+paper's implicit step (Sec. 2).  Only the tests, ``__graft_entry__.smoke`` and
+the benchmark's CPU baseline may import this module.  It never imports the
+CUDA package and the CUDA package never imports it; both take their inputs
+from ``paper_1610_10053_gb300.inputs`` only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "liboracle.so")
+SRC = [os.path.join(HERE, "music_oracle.c"), os.path.join(HERE, "residual_body.h")]
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+
+class OrGrid(ctypes.Structure):
+    _fields_ = [
+        ("nd", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+        ("x0", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("wall_scalar", ctypes.c_int * 3),
+        ("gamma", ctypes.c_double), ("g", ctypes.c_double * 3),
+        ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
+        ("newton_max", ctypes.c_int), ("newton_tol", ctypes.c_double), ("precond", ctypes.c_int),
+        ("sweeps", ctypes.c_int), ("max_halvings", ctypes.c_int),
+    ]
+
+
+class OrStepStats(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+        ("halvings", ctypes.c_int), ("gmres_failures", ctypes.c_int), ("fnorm0", ctypes.c_double),
+        ("fnorm", ctypes.c_double), ("max_drho", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
+    os.makedirs(BUILD, exist_ok=True)
+    if not force and os.path.exists(LIB):
+        if os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in SRC):
+            return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=gnu11",
+           "-o", tmp, SRC[0], "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        G = ctypes.POINTER(OrGrid)
+        L.or_spatial_operator.argtypes = [G, _dbl_p, _dbl_p]
+        L.or_spatial_operator_dir.argtypes = [G, _dbl_p, _dbl_p, _dbl_p]
+        L.or_cn_residual.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_double, _dbl_p]
+        L.or_step_constant.argtypes = [G, _dbl_p, ctypes.c_double, _dbl_p]
+        L.or_fd_eps.argtypes = [ctypes.c_long, ctypes.c_double, _dbl_p]
+        L.or_fd_eps.restype = ctypes.c_double
+        L.or_norm2.argtypes = [ctypes.c_long, _dbl_p]
+        L.or_norm2.restype = ctypes.c_double
+        L.or_jv.argtypes = [G, _dbl_p, _dbl_p, _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p]
+        L.or_precond.argtypes = [G, _dbl_p, ctypes.c_double, _dbl_p, _dbl_p]
+        L.or_gmres_dense.argtypes = [ctypes.c_long, _dbl_p, _dbl_p, _dbl_p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+        L.or_newton_step.argtypes = [G, _dbl_p, ctypes.c_double, ctypes.POINTER(OrStepStats)]
+        L.or_cfl_rate.argtypes = [G, _dbl_p]
+        L.or_cfl_rate.restype = ctypes.c_double
+        L.or_run.argtypes = [G, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                             ctypes.POINTER(OrStepStats)]
+        L.or_diagnostics.argtypes = [G, _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dbl_p)
+
+
+def _vec(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def grid(prob) -> OrGrid:
+    g = OrGrid()
+    g.nd = prob.nd
+    for d in range(3):
+        g.n[d] = int(prob.n[d])
+        g.dx[d] = float(prob.length[d] / prob.n[d])
+        g.x0[d] = float(prob.x0[d])
+        g.bc[d] = int(prob.bc[d])
+        g.wall_scalar[d] = int(prob.wall_scalar[d])
+        g.g[d] = float(prob.g[d])
+    g.gamma = float(prob.gamma)
+    g.restart = int(prob.restart)
+    g.max_restarts = int(prob.max_restarts)
+    g.gmres_rtol = float(prob.gmres_rtol)
+    g.newton_max = int(prob.newton_max)
+    g.newton_tol = float(prob.newton_tol)
+    g.precond = int(prob.precond)
+    g.sweeps = int(prob.sweeps)
+    g.max_halvings = int(prob.max_halvings)
+    return g
+
+
+def spatial_operator(prob, U) -> np.ndarray:
+    """R(U), Eqs. 1-3."""
+    U = _vec(U)
+    R = np.empty_like(U)
+    g = grid(prob)
+    lib().or_spatial_operator(ctypes.byref(g), _p(U), _p(R))
+    return R
+
+
+def spatial_operator_dir(prob, U, V) -> np.ndarray:
+    """Exact (dR/dU) V by complex-step differentiation."""
+    U, V = _vec(U), _vec(V)
+    dR = np.empty_like(U)
+    g = grid(prob)
+    lib().or_spatial_operator_dir(ctypes.byref(g), _p(U), _p(V), _p(dR))
+    return dR
+
+
+def cn_residual(prob, U, Un, dt) -> np.ndarray:
+    """F(U) = U - U^n - dt/2 (R(U) + R(U^n)) (Crank-Nicolson)."""
+    U, Un = _vec(U), _vec(Un)
+    F = np.empty_like(U)
+    g = grid(prob)
+    lib().or_cn_residual(ctypes.byref(g), _p(U), _p(Un), float(dt), _p(F))
+    return F
+
+
+def fd_eps(U, v) -> float:
+    U, v = _vec(U), _vec(v)
+    un = lib().or_norm2(U.size, _p(U))
+    return lib().or_fd_eps(U.size, un, _p(v))
+
+
+def jv(prob, U, v, dt, eps: float = 0.0) -> np.ndarray:
+    """Jacobian-free J v (Knoll & Keyes 2004); eps <= 0 selects the default."""
+    U, v = _vec(U), _vec(v)
+    RU = spatial_operator(prob, U)
+    out = np.empty_like(U)
+    g = grid(prob)
+    lib().or_jv(ctypes.byref(g), _p(U), _p(RU), _p(v), float(dt), float(eps), _p(out))
+    return out
+
+
+def precond(prob, U, dt, r) -> np.ndarray:
+    """z = M^-1 r, the physics-based preconditioner with coefficients at U."""
+    U, r = _vec(U), _vec(r)
+    z = np.empty_like(U)
+    g = grid(prob)
+    lib().or_precond(ctypes.byref(g), _p(U), float(dt), _p(r), _p(z))
+    return z
+
+
+def gmres_dense(A, b, m=30, max_restarts=10, rtol=1e-10):
+    """The oracle's GMRES on a dense matrix with no preconditioner."""
+    A = _vec(A)
+    b = _vec(b)
+    x = np.empty_like(b)
+    its = ctypes.c_int(0)
+    rc = lib().or_gmres_dense(b.size, _p(A), _p(b), _p(x), int(m), int(max_restarts), float(rtol),
+                              ctypes.byref(its))
+    return x, rc, its.value
+
+
+def newton_step(prob, U, dt):
+    """One implicit step of size dt.  Returns (U_new, stats, rc)."""
+    U = _vec(U).copy()
+    st = OrStepStats()
+    g = grid(prob)
+    rc = lib().or_newton_step(ctypes.byref(g), _p(U), float(dt), ctypes.byref(st))
+    return U, st.as_dict(), rc
+
+
+def cfl_dt(prob, U, cfl) -> float:
+    U = _vec(U)
+    g = grid(prob)
+    return float(cfl) / lib().or_cfl_rate(ctypes.byref(g), _p(U))
+
+
+def run(prob, U=None, nsteps=None, cfl=None, dt_max=None):
+    """Advance nsteps CFL-limited implicit steps.  Returns (U, [stats])."""
+    U = _vec(prob.U if U is None else U).copy()
+    nsteps = prob.nsteps if nsteps is None else nsteps
+    cfl = prob.cfl if cfl is None else cfl
+    dt_max = prob.dt_max if dt_max is None else dt_max
+    st = (OrStepStats * max(nsteps, 1))()
+    g = grid(prob)
+    done = lib().or_run(ctypes.byref(g), _p(U), int(nsteps), float(cfl), float(dt_max), st)
+    if done != nsteps:
+        raise RuntimeError("oracle: Newton failed at step %d" % done)
+    return U, [st[i].as_dict() for i in range(nsteps)]
+
+
+DIAG_NAMES = ("mixing_height", "max_mach", "kh_mode_amplitude", "vertical_kinetic_energy",
+              "mean_kinetic_energy", "max_speed")
+
+
+def diagnostics(prob, U) -> dict:
+    U = _vec(U)
+    out = np.zeros(6)
+    g = grid(prob)
+    lib().or_diagnostics(ctypes.byref(g), _p(U), float(prob.rho_L), float(prob.rho_H), _p(out))
+    return dict(zip(DIAG_NAMES, out.tolist()))

@@ -1,0 +1,278 @@
+/*
+ * Spatial operator R(U) of the oracle, written once and instantiated twice by
+ * music_oracle.c: with T = double (the oracle proper) and with T = double
+ * complex (complex-step differentiation for the exact Jacobian pins).  Every
+ * branch is taken on the real part, so the complex instantiation is the exact
+ * derivative of the branch-frozen real operator.
+ *
+ * TEST INFRASTRUCTURE ONLY.  See music_oracle.c for the conventions.
+ *
+ * What it computes (Sec. 2 of the paper, Eqs. 1-3, staggered grid with
+ * upstream linear reconstruction and the van Leer limiter):
+ *   R_rho = -div(rho u)
+ *   R_E   = -div(rho e u) - p div(u)            (E = rho e, internal energy)
+ *   R_m   = -div(rho u (x) u) - grad p + rho g  (m_d on d-faces)
+ * Thermal diffusion (the div(chi grad T) term) is not part of this operator.
+ *
+ * Required macros: T, RE(x) (real part), FN(name) (name mangling).
+ */
+
+/* van Leer limited slope from the two one-sided differences a, b. */
+static T FN(vanleer)(T a, T b)
+{
+    if (RE(a) * RE(b) > 0.0)
+        return (2.0 * a) * b / (a + b);
+    return 0.0;
+}
+
+/*
+ * R(U).  U and R hold nv planes of N = nx*ny*nz values (rho, E, m_x, m_y
+ * [, m_z]), x fastest.  m_d[c] sits on the lower d-face of cell c.  On a wall
+ * direction w the stored lower wall face (c_w == 0) carries no flux and gets
+ * R = 0; the upper wall face is implicit.
+ */
+static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
+{
+    const int nd = g->nd;
+    const long N = or_ncells(g);
+    or_ext X;
+    or_ext_init(&X, g);
+    const long M = X.total;
+
+    T *rho = (T *)calloc(M, sizeof(T));
+    T *e = (T *)calloc(M, sizeof(T));
+    T *p = (T *)calloc(M, sizeof(T));
+    T *uf[3], *srho[3], *se[3], *Frho[3], *FE[3], *Phi[3];
+    T *su[3][3], *Psi[3][3];
+    for (int d = 0; d < 3; d++) {
+        uf[d] = srho[d] = se[d] = Frho[d] = FE[d] = Phi[d] = NULL;
+        for (int q = 0; q < 3; q++) su[d][q] = Psi[d][q] = NULL;
+    }
+    for (int d = 0; d < nd; d++) {
+        uf[d] = (T *)calloc(M, sizeof(T));
+        srho[d] = (T *)calloc(M, sizeof(T));
+        se[d] = (T *)calloc(M, sizeof(T));
+        Frho[d] = (T *)calloc(M, sizeof(T));
+        FE[d] = (T *)calloc(M, sizeof(T));
+        Phi[d] = (T *)calloc(M, sizeof(T));
+        for (int q = 0; q < nd; q++) {
+            su[d][q] = (T *)calloc(M, sizeof(T));
+            Psi[d][q] = (T *)calloc(M, sizeof(T));
+        }
+    }
+    T *Erho = (T *)calloc(M, sizeof(T)); /* E on the extended grid */
+
+    const double gm1 = g->gamma - 1.0;
+
+    /* --- a1: interior values, then ghost layers direction by direction --- */
+    for (long c = 0; c < N; c++) {
+        long x = or_ext_of_cell(&X, g, c);
+        rho[x] = U[c];
+        Erho[x] = U[N + c];
+    }
+    for (int d = 0; d < nd; d++) {
+        for (long x = 0; x < M; x++) {
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            int a = ix[d];
+            if (a >= 0 && a < g->n[d]) continue; /* not a ghost along d */
+            /* skip points that are ghosts along a later direction: they are
+               filled when that direction is processed */
+            int later = 0;
+            for (int q = d + 1; q < nd; q++)
+                if (ix[q] < 0 || ix[q] >= g->n[q]) later = 1;
+            if (later) continue;
+            int src[3] = {ix[0], ix[1], ix[2]};
+            if (g->bc[d] == OR_BC_PERIODIC) {
+                src[d] = ((a % g->n[d]) + g->n[d]) % g->n[d];
+                long s = or_ext_index(&X, src);
+                rho[x] = rho[s];
+                Erho[x] = Erho[s];
+            } else if (g->wall_scalar[d] == OR_WALL_MIRROR) {
+                src[d] = (a < 0) ? (-1 - a) : (2 * g->n[d] - 1 - a);
+                long s = or_ext_index(&X, src);
+                rho[x] = rho[s];
+                Erho[x] = Erho[s];
+            } else {
+                /* hydrostatic ghost: T extrapolated linearly, rho from the
+                   discrete balance (p_b - p_g) = +-dx g (rho_b + rho_g)/2
+                   across the wall face, p = rho T.  Only the first ghost
+                   layer enters any flux; deeper layers copy it. */
+                const int lower = (a < 0);
+                const int b0 = lower ? 0 : g->n[d] - 1;
+                const int b1 = lower ? 1 : g->n[d] - 2;
+                int i0[3] = {ix[0], ix[1], ix[2]}, i1[3] = {ix[0], ix[1], ix[2]};
+                i0[d] = b0;
+                i1[d] = b1;
+                long s0 = or_ext_index(&X, i0), s1 = or_ext_index(&X, i1);
+                T T0 = gm1 * Erho[s0] / rho[s0];
+                T T1 = gm1 * Erho[s1] / rho[s1];
+                T Tg = 2.0 * T0 - T1;
+                double hs = 0.5 * g->dx[d] * g->g[d];
+                T rg = lower ? rho[s0] * (T0 - hs) / (Tg + hs)
+                             : rho[s0] * (T0 + hs) / (Tg - hs);
+                rho[x] = rg;
+                Erho[x] = rg * Tg / gm1;
+            }
+        }
+    }
+    for (long x = 0; x < M; x++) {
+        e[x] = Erho[x] / rho[x];
+        p[x] = gm1 * Erho[x];
+    }
+
+    /* --- face velocities: interior faces from m / (mean of the two cells) --- */
+    for (int d = 0; d < nd; d++) {
+        for (long c = 0; c < N; c++) {
+            long x = or_ext_of_cell(&X, g, c);
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            if (g->bc[d] == OR_BC_WALL && ix[d] == 0) {
+                uf[d][x] = 0.0;
+                continue;
+            }
+            long xl = x - X.stride[d];
+            T rbar = 0.5 * (rho[xl] + rho[x]);
+            uf[d][x] = U[(2 + d) * N + c] / rbar;
+        }
+    }
+    /* ghost face velocities, direction by direction */
+    for (int w = 0; w < nd; w++) {
+        for (long x = 0; x < M; x++) {
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            int a = ix[w];
+            if (a >= 0 && a < g->n[w]) continue;
+            int later = 0;
+            for (int q = w + 1; q < nd; q++)
+                if (ix[q] < 0 || ix[q] >= g->n[q]) later = 1;
+            if (later) continue;
+            for (int d = 0; d < nd; d++) {
+                int src[3] = {ix[0], ix[1], ix[2]};
+                if (g->bc[w] == OR_BC_PERIODIC) {
+                    src[w] = ((a % g->n[w]) + g->n[w]) % g->n[w];
+                    uf[d][x] = uf[d][or_ext_index(&X, src)];
+                } else if (d == w) {
+                    /* normal velocity on w-faces: zero on the wall faces,
+                       odd reflection beyond them */
+                    const int n = g->n[w];
+                    if (a == n) {
+                        uf[d][x] = 0.0;
+                    } else {
+                        src[w] = (a < 0) ? -a : 2 * n - a;
+                        uf[d][x] = -uf[d][or_ext_index(&X, src)];
+                    }
+                } else {
+                    /* tangential velocity: stress-free, even reflection */
+                    src[w] = (a < 0) ? (-1 - a) : (2 * g->n[w] - 1 - a);
+                    uf[d][x] = uf[d][or_ext_index(&X, src)];
+                }
+            }
+        }
+    }
+
+    /* --- limited slopes --- */
+    for (int d = 0; d < nd; d++) {
+        const long s = X.stride[d];
+        for (long x = 0; x < M; x++) {
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            if (!or_ext_has(&X, ix, d, -1) || !or_ext_has(&X, ix, d, +1)) continue;
+            srho[d][x] = FN(vanleer)(rho[x] - rho[x - s], rho[x + s] - rho[x]);
+            se[d][x] = FN(vanleer)(e[x] - e[x - s], e[x + s] - e[x]);
+            for (int q = 0; q < nd; q++) /* slope of u_q along d, on q-faces */
+                su[q][d][x] = FN(vanleer)(uf[q][x] - uf[q][x - s], uf[q][x + s] - uf[q][x]);
+        }
+    }
+
+    /* --- mass and internal-energy fluxes on d-faces (upwind reconstruction) --- */
+    for (int d = 0; d < nd; d++) {
+        const long s = X.stride[d];
+        for (long x = 0; x < M; x++) {
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            if (!or_ext_has(&X, ix, d, -2) || !or_ext_has(&X, ix, d, +1)) continue;
+            T u = uf[d][x];
+            T rs, es;
+            if (RE(u) >= 0.0) {
+                rs = rho[x - s] + 0.5 * srho[d][x - s];
+                es = e[x - s] + 0.5 * se[d][x - s];
+            } else {
+                rs = rho[x] - 0.5 * srho[d][x];
+                es = e[x] - 0.5 * se[d][x];
+            }
+            Frho[d][x] = u * rs;
+            FE[d][x] = Frho[d][x] * es;
+        }
+    }
+
+    /* --- momentum fluxes --- */
+    for (int d = 0; d < nd; d++) {
+        const long s = X.stride[d];
+        /* flux of m_d along d at cell centres */
+        for (long x = 0; x < M; x++) {
+            int ix[3];
+            or_ext_coords(&X, x, ix);
+            if (!or_ext_has(&X, ix, d, -2) || !or_ext_has(&X, ix, d, +2)) continue;
+            T fm = 0.5 * (Frho[d][x] + Frho[d][x + s]);
+            T us = (RE(fm) >= 0.0) ? uf[d][x] + 0.5 * su[d][d][x]
+                                   : uf[d][x + s] - 0.5 * su[d][d][x + s];
+            Phi[d][x] = fm * us;
+        }
+        /* flux of m_d along q (q != d) on the (d,q) edges at the lower
+           d- and q-faces of cell x */
+        for (int q = 0; q < nd; q++) {
+            if (q == d) continue;
+            const long t = X.stride[q];
+            for (long x = 0; x < M; x++) {
+                int ix[3];
+                or_ext_coords(&X, x, ix);
+                if (!or_ext_has(&X, ix, d, -1) || !or_ext_has(&X, ix, q, -2) ||
+                    !or_ext_has(&X, ix, q, +1))
+                    continue;
+                T fm = 0.5 * (Frho[q][x - s] + Frho[q][x]);
+                T us = (RE(fm) >= 0.0) ? uf[d][x - t] + 0.5 * su[d][q][x - t]
+                                       : uf[d][x] - 0.5 * su[d][q][x];
+                Psi[d][q][x] = fm * us;
+            }
+        }
+    }
+
+    /* --- residual assembly on the interior --- */
+    for (long c = 0; c < N; c++) {
+        long x = or_ext_of_cell(&X, g, c);
+        int ix[3];
+        or_ext_coords(&X, x, ix);
+        T accr = 0.0, acce = 0.0, divu = 0.0;
+        for (int d = 0; d < nd; d++) {
+            const long s = X.stride[d];
+            accr += (Frho[d][x + s] - Frho[d][x]) / g->dx[d];
+            acce += (FE[d][x + s] - FE[d][x]) / g->dx[d];
+            divu += (uf[d][x + s] - uf[d][x]) / g->dx[d];
+        }
+        R[c] = -accr;
+        R[N + c] = -acce - p[x] * divu;
+        for (int d = 0; d < nd; d++) {
+            if (g->bc[d] == OR_BC_WALL && ix[d] == 0) {
+                R[(2 + d) * N + c] = 0.0;
+                continue;
+            }
+            const long s = X.stride[d];
+            T acc = 0.0;
+            for (int q = 0; q < nd; q++) {
+                if (q == d)
+                    acc += (Phi[d][x] - Phi[d][x - s]) / g->dx[d];
+                else
+                    acc += (Psi[d][q][x + X.stride[q]] - Psi[d][q][x]) / g->dx[q];
+            }
+            T rbar = 0.5 * (rho[x - s] + rho[x]);
+            R[(2 + d) * N + c] = (-acc - (p[x] - p[x - s]) / g->dx[d]) + rbar * g->g[d];
+        }
+    }
+
+    free(rho); free(e); free(p); free(Erho);
+    for (int d = 0; d < nd; d++) {
+        free(uf[d]); free(srho[d]); free(se[d]); free(Frho[d]); free(FE[d]); free(Phi[d]);
+        for (int q = 0; q < nd; q++) { free(su[d][q]); free(Psi[d][q]); }
+    }
+}
