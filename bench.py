@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit JFNK step on GB300.
+
+A step is one Crank-Nicolson implicit time step (Newton + preconditioned
+GMRES + Jacobian-free products) of the 2-D Kelvin-Helmholtz workload on a
+512 x 512 periodic grid at CFL 10, Newton tolerance 1e-8 (seeded synthetic
+initial condition, see paper_1610_10053_gb300.inputs).  The headline value
+is the mixed-precision path (FP64 residual and differencing, FP32 Krylov
+basis and preconditioner) in cell-steps/s; the plain FP64 GPU path is timed
+in the same run.  Multi-GPU runs are independent replicas (weak scaling, no
+collective on the data path).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl music|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s at Newton tol 1e-8, mixed vs FP64; residual HBM GB/s; p99 step ms"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(rank: int):
+    from paper_1610_10053_gb300 import inputs as I
+    return I.kelvin_helmholtz(n=512, seed=2 + rank)
+
+
+def time_steps(grid, steps, stream, flush):
+    """Per-step device times (ms) with CUDA events on the launching stream,
+    L2 flushed between steps outside the events."""
+    import torch
+    times, stats = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = grid.step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    return times, stats
+
+
+def run_music(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1610_10053_gb300 import binding as B
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    prob = workload(rank)
+    N = prob.ncells
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # CPU baseline first (rank 0, N = 1 only), so it never overlaps GPU timing
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    result = {}
+    for name, prec in (("mixed", B.MIXED), ("fp64", B.FP64)):
+        if name == "fp64" and args.skip_fp64:
+            continue
+        g = B.Grid(prob, precision=prec)
+        g.set_state(prob.U)
+        for _ in range(args.warmup):
+            g.step()
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        l0 = B.kernel_launches()
+        with ClockSampler(local) as clk:
+            times, stats = time_steps(g, args.steps, stream, flush)
+        launches = B.kernel_launches() - l0
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        total_ms = float(np.sum(times))
+        if ws > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        result[name] = dict(total_ms=total_ms, times=times, stats=stats, launches=launches,
+                            clocks=clk.summary(), grid=g)
+    mixed = result["mixed"]
+    value = ws * N * args.steps / (mixed["total_ms"] / 1e3)
+    fp64_value = None
+    if "fp64" in result:
+        fp64_value = ws * N * args.steps / (result["fp64"]["total_ms"] / 1e3)
+
+    # dominant stencil: Jv chain on the final mixed state, CUDA events on its stream
+    roof = roofline_jv(mixed["grid"], prob, stream, flush)
+    e2e = end_to_end(mixed["grid"], prob, stream, max(2, min(args.steps, 5)))
+    for r in result.values():
+        r["grid"].close()
+
+    if rank != 0:
+        return
+    t = np.array(mixed["times"])
+    st = mixed["stats"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "cell-steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": float(t.mean()),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 residual + f32 Krylov (mixed)",
+        "data": "synthetic",
+        "config": {"workload": "Kelvin-Helmholtz 2-D, 512x512 periodic, CFL 10, Newton tol 1e-8, GMRES(30)",
+                   "cells": N, "precision": "mixed", "l2": "flushed (512 MiB write) between timed steps",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "fp64_value": fp64_value,
+        "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
+        "step_ms_p50": float(np.percentile(t, 50)),
+        "step_ms_p99": float(np.percentile(t, 99)),
+        "newton_its_per_step": float(np.mean([s["newton_its"] for s in st])),
+        "gmres_its_per_step": float(np.mean([s["gmres_its"] for s in st])),
+        "fp64_ms_per_step": float(np.mean(result["fp64"]["times"])) if "fp64" in result else None,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(mixed["launches"]),
+        "clocks": mixed["clocks"],
+    }
+    print(json.dumps(line))
+
+
+def roofline_jv(grid, prob, stream, flush, reps=20):
+    """Achieved bytes/s of the Jv stencil (the kernel chain that evaluates
+    R(U + eps v) and forms Jv) in the configuration the solver uses."""
+    import torch
+    U = torch.from_numpy(grid.get_state()).cuda()
+    v = torch.randn(U.numel(), device="cuda", dtype=grid.kdtype)
+    dt = grid.cfl_dt(prob.cfl)
+    grid.jv(U, v, dt)
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grid.jv(U, v, dt)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ms = float(np.mean(ms))
+    N = prob.ncells
+    # algorithmic bytes per cell of Jv (2-D mixed): read U (4 x 8), R(U) (4 x 8), v (4 x 4), write Jv (4 x 4)
+    bytes_per_cell = 4 * 8 + 4 * 8 + 4 * 4 + 4 * 4
+    achieved = bytes_per_cell * N / (ms / 1e3) / 1e9
+    peak, src = peaks()
+    return {"kernel": "music_jv (R(U+eps v) stencil chain + difference)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "ms_per_launch": ms, "bytes_per_cell": bytes_per_cell,
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src}
+
+
+def end_to_end(grid, prob, stream, steps):
+    """Same metric through the public API with host buffers: every step copies
+    the state host -> device (pinned), steps, and copies it back."""
+    import torch
+    n = grid.n
+    host_in = torch.from_numpy(prob.U.copy()).pin_memory()
+    host_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    grid.set_state(host_in)
+    grid.step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        grid.set_state(host_in)
+        grid.step()
+        grid.get_state_into(host_out)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": prob.ncells * steps / el, "unit": "cell-steps/s", "h2d_bytes_per_step": n * 8,
+            "d2h_bytes_per_step": n * 8, "steps": steps}
+
+
+def cpu_baseline(prob, steps=1):
+    """The FP64 CPU oracle as it stands, single-threaded, on one implicit step
+    of the same workload."""
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    U, st = O.run(prob, nsteps=steps)
+    el = time.perf_counter() - t0
+    return {"value": prob.ncells * steps / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d implicit step(s) of KH 512x512 (FP64, single thread), %.1f s" % (steps, el)}
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU solver) on the host cores, bounded sample per
+    step: one implicit step of the same Kelvin-Helmholtz setup at 256x256."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1610_10053_gb300 import inputs as I
+    O.build()
+    prob = I.kelvin_helmholtz(n=256, seed=2)
+    U = prob.U.copy()
+    for _ in range(args.warmup):
+        U, _ = O.run(prob, U=U, nsteps=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        U, _ = O.run(prob, U=U, nsteps=1)
+        times.append(time.perf_counter() - t0)
+    total = float(np.sum(times))
+    value = prob.ncells * args.steps / total
+    sample = "1 implicit step of KH 256x256 per step (FP64, single thread)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "Kelvin-Helmholtz 2-D, CFL 10, Newton tol 1e-8, GMRES(30)", "cells": prob.ncells,
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="music", choices=["music", "reference"])
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_music(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * libmusic - C ABI of the GB300 implicit-hydrodynamics JFNK inner loop.
+ *
+ * The library advances the Euler equations with gravity (paper Sec. 2,
+ * Eqs. 1-3) by Crank-Nicolson implicit steps solved with Newton-Raphson,
+ * restarted GMRES with Jacobian-free finite-difference matrix-vector products
+ * and a physics-based semi-implicit preconditioner.  Everything on the path
+ * runs as CUDA kernels on one GPU; the host code only sequences launches and
+ * does the scalar Givens least-squares update of GMRES.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  State layout: nv planes of N = nx*ny*nz doubles, x fastest, in the order
+ *    rho, E = rho e (internal energy per volume), m_x, m_y[, m_z]
+ *    (nv = 2 + ndim).  m_d[c] is the momentum on the lower d-face of cell c
+ *    (staggered grid, Sec. 2).  On a wall direction the lower wall face of
+ *    the first layer is stored and must be 0; the upper wall face is implicit.
+ *  Device pointers: every array argument documented as "device" must be a
+ *    CUDA device (or managed) pointer to at least nv*N elements of the stated
+ *    type, 8-byte aligned (4-byte for float).  The library never frees or
+ *    retains caller pointers; they are borrowed for the duration of the call
+ *    and, because work is queued asynchronously on `stream`, until the
+ *    stream has passed the call.
+ *  Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  Calls queue their kernels on it and return once
+ *    queued, except where a call must read a scalar result back (documented
+ *    per call), in which case it synchronises `stream`.
+ *  Errors: every call returns a music_status.  On failure nothing is
+ *    aborted; music_last_error() gives a message for the calling thread.  A
+ *    grid whose call failed with MUSIC_E_CUDA should be destroyed.
+ *  Precision: MUSIC_FP64 computes everything in FP64.  MUSIC_MIXED keeps
+ *    the state, the residual F(U), the finite-difference differencing
+ *    U + eps v and R(U + eps v) - R(U), gravity and pressure in FP64 and
+ *    stores the Krylov basis, the preconditioner and Jv results in FP32
+ *    (dot products accumulate in FP64).
+ *  Threads: a grid may be used by one host thread at a time.
+ */
+#ifndef MUSIC_H
+#define MUSIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MUSIC_OK = 0,
+    MUSIC_E_INVAL = 1,        /* bad argument or descriptor */
+    MUSIC_E_OOM = 2,          /* device or host allocation failed */
+    MUSIC_E_CUDA = 3,         /* a CUDA runtime call failed */
+    MUSIC_E_NEWTON_FAIL = 4,  /* Newton did not converge after all dt halvings */
+    MUSIC_E_GMRES_FAIL = 5,   /* reserved: GMRES non-convergence is reported in stats */
+    MUSIC_E_NONFINITE = 6,    /* NaN or Inf met in a norm */
+    MUSIC_E_TIMEOUT = 7,      /* a bounded wait expired */
+    MUSIC_E_BUSY = 8,         /* admission refused: over the memory budget or slots full */
+    MUSIC_E_NOTFOUND = 9      /* unknown ticket */
+} music_status;
+
+enum { MUSIC_BC_PERIODIC = 0, MUSIC_BC_WALL = 1 };
+/* scalar ghost cells behind a wall: mirrored, or hydrostatic with the
+   temperature T = (gamma-1) e extrapolated linearly and rho from the
+   discrete balance p_b - p_g = -+ dx g (rho_b + rho_g)/2 (Sec. 3) */
+enum { MUSIC_WALL_MIRROR = 0, MUSIC_WALL_HSE_LINEAR_T = 1 };
+enum { MUSIC_FP64 = 0, MUSIC_MIXED = 1 };
+enum { MUSIC_PC_NONE = 0, MUSIC_PC_ACOUSTIC = 1 };
+
+/* Grid, physics and solver description (copied by music_create_grid). */
+typedef struct {
+    int ndim;            /* 2 or 3 */
+    int n[3];            /* cells per direction, n[2] = 1 when ndim = 2; each >= 4 */
+    double origin[3];    /* lower corner of the box */
+    double length[3];    /* box edge lengths (> 0) */
+    int bc[3];           /* MUSIC_BC_* per direction */
+    int wall_scalar[3];  /* MUSIC_WALL_* per wall direction; at most one HSE direction */
+    double gamma;        /* ideal-gas ratio of specific heats, p = (gamma-1) E (Sec. 2) */
+    double g[3];         /* constant gravitational acceleration (Sec. 2) */
+    int precision;       /* MUSIC_FP64 or MUSIC_MIXED */
+    /* solver options (0 selects the default in brackets) */
+    int gmres_restart;        /* Krylov vectors per cycle [30], 1..63 */
+    int gmres_max_restarts;   /* extra cycles [10] */
+    double gmres_rtol;        /* |J d + F| <= rtol |F| [1e-4] */
+    int newton_max_its;       /* [12] */
+    double newton_tol;        /* converged when max |delta rho|/rho <= tol [1e-8] */
+    int precond;              /* MUSIC_PC_* [ACOUSTIC]; pass -1 for NONE */
+    int precond_sweeps;       /* weighted-Jacobi sweeps of the pressure system [8] */
+    int max_dt_halvings;      /* retries of a failed step at dt/2 [4] */
+} music_grid_desc;
+
+typedef struct {
+    double dt;          /* step size actually taken */
+    int newton_its;     /* Newton iterations of the accepted attempt */
+    int gmres_its;      /* Arnoldi steps of the accepted attempt */
+    int dt_halvings;    /* failed attempts before it */
+    int gmres_unconverged; /* GMRES solves that hit the restart limit */
+    double fnorm0;      /* |F(U^n)|_2 at the first Newton iterate */
+    double fnorm;       /* |F|_2 at the last Newton iterate */
+    double max_drho;    /* final max |delta rho| / rho */
+    double wall_ms;     /* host wall time of the call */
+} music_step_stats;
+
+typedef struct music_grid music_grid;
+
+/* Message of the last failed call on this thread (always NUL-terminated).
+   Returns the full message length. */
+size_t music_last_error(char *buf, size_t len);
+
+/* Library version string. */
+const char *music_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+   grids, all threads).  For accounting only. */
+uint64_t music_kernel_launches(void);
+
+/*
+ * Create a grid: validates `desc`, selects the current CUDA device, and
+ * allocates and owns every device buffer the solver needs (state, step
+ * constant, Krylov basis, preconditioner coefficients and scratch).  The
+ * state starts at zero; set it with music_set_state.  Sizes: periodic
+ * directions with the acoustic preconditioner need no parity constraint.
+ * Errors: MUSIC_E_INVAL (descriptor), MUSIC_E_OOM, MUSIC_E_CUDA.
+ */
+int music_create_grid(const music_grid_desc *desc, music_grid **out);
+
+/* Free everything owned by the grid.  NULL is accepted. Synchronises the
+   device first. */
+int music_destroy_grid(music_grid *grid);
+
+/* Number of state values nv*N of the grid, or 0 for NULL. */
+size_t music_state_size(const music_grid *grid);
+
+/* Device bytes owned by the grid. */
+size_t music_grid_bytes(const music_grid *grid);
+
+/* Copy a state (layout above) into / out of the grid.  `is_device` says
+   whether `U` is a device pointer (else host).  Synchronous. */
+int music_set_state(music_grid *grid, const double *U, int is_device);
+int music_get_state(music_grid *grid, double *U, int is_device);
+
+/*
+ * R = R(U): the spatial operator of Eqs. 1-3 on the staggered grid with
+ * van Leer limited upstream reconstruction (Sec. 2), ghost cells from the
+ * grid's boundary conditions.  U, R: device, float64, nv*N.  Async on
+ * `stream`.  Wall faces get R = 0.
+ */
+int music_spatial_operator(music_grid *grid, const double *U, double *R, void *stream);
+
+/*
+ * F = U - U^n - dt/2 (R(U) + R(U^n)): the Crank-Nicolson residual (Sec. 2).
+ * U, Un, F: device, float64, nv*N.  Evaluates two stencils.  Async.
+ */
+int music_residual(music_grid *grid, const double *U, const double *Un, double dt, double *F,
+                   void *stream);
+
+/*
+ * Jv = v - dt/2 (R(U + eps v) - R(U)) / eps, the Jacobian-free product of the
+ * Crank-Nicolson Jacobian (Knoll & Keyes 2004, cited in Sec. 2).  eps <= 0
+ * selects eps = sqrt(2^-52) (1 + |U|_2) / |v|_2 (computed on the device);
+ * v = 0 gives Jv = 0.  U: device float64.  v, Jv: device, float64 for
+ * MUSIC_FP64 grids and float32 for MUSIC_MIXED grids.  U + eps v and the
+ * difference of the two residuals are formed in FP64 in both modes.  Async.
+ */
+int music_jv(music_grid *grid, const double *U, const void *v, void *Jv, double dt, double eps,
+             void *stream);
+
+/*
+ * z = M^-1 r, the physics-based preconditioner (Sec. 2, after Park et al.
+ * 2009) with coefficients frozen at U: the acoustic subsystem (advection and
+ * gravity dropped) with the momentum eliminated into a pressure Helmholtz
+ * problem, relaxed with `precond_sweeps` weighted-Jacobi sweeps (weight 0.8)
+ * from zero, then density, energy and momentum by back substitution in flux
+ * form.  MUSIC_PC_NONE is the identity.  U: device float64; r, z: device,
+ * float64 (FP64 grids) or float32 (MIXED grids).  Async.
+ */
+int music_precond_apply(music_grid *grid, const double *U, double dt, const void *r, void *z,
+                        void *stream);
+
+/*
+ * Advance the grid's own state by one implicit step of size dt > 0 (pick dt
+ * with music_cfl_dt, Eq. 4): Newton on the Crank-Nicolson system (Sec. 2)
+ * with right-preconditioned restarted GMRES; a failed Newton solve is
+ * retried at dt/2 up to max_dt_halvings times.  `st` may be NULL.
+ * Synchronises `stream` (GMRES reads its scalars back every Arnoldi step).
+ * Errors: MUSIC_E_INVAL (dt <= 0), MUSIC_E_NEWTON_FAIL (state restored to
+ * U^n), MUSIC_E_NONFINITE, MUSIC_E_CUDA.
+ */
+int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *stream);
+
+/* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
+   u_d the mean of the two face velocities of the cell (Eq. 4).
+   Synchronises `stream`. */
+int music_cfl_dt(music_grid *grid, double cfl, double *dt, void *stream);
+
+/*
+ * Diagnostics of the grid's state (Secs. 3-6), written to out[0..5]:
+ *  0 mixing-layer height h = sum_rows X_M(<X_H>) dy with
+ *    X_H = (rho - rho_L)/(rho_H - rho_L) (Cabot & Cook, Sec. 3);
+ *  1 max Mach number (cell-centred velocity);
+ *  2 amplitude of the two-wavelength x-mode of v_y: (2/N)|sum v e^{-ikx}|;
+ *  3 vertical kinetic energy sum_{y-faces} rbar v^2 / 2 dV;
+ *  4 mean kinetic energy density (1/N) sum_d sum_faces rbar u_d^2 / 2 (Sec. 5);
+ *  5 max cell-centred speed (Sec. 6).
+ * Synchronises `stream`.
+ */
+int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MUSIC_H */

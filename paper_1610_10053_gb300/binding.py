@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libmusic (include/music.h).
+
+Argument marshalling only: every computation happens inside the CUDA
+library.  Device arrays are torch CUDA tensors (PyTorch supplies device
+memory and streams); their raw pointers and the current stream's handle are
+passed through the C ABI.  There is no CPU fallback: if the library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_dbl_p = ctypes.POINTER(ctypes.c_double)
+
+MUSIC_OK = 0
+STATUS = {0: "OK", 1: "E_INVAL", 2: "E_OOM", 3: "E_CUDA", 4: "E_NEWTON_FAIL", 5: "E_GMRES_FAIL",
+          6: "E_NONFINITE", 7: "E_TIMEOUT", 8: "E_BUSY", 9: "E_NOTFOUND"}
+FP64, MIXED = 0, 1
+
+
+class MusicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int), ("n", ctypes.c_int * 3), ("origin", ctypes.c_double * 3),
+        ("length", ctypes.c_double * 3), ("bc", ctypes.c_int * 3), ("wall_scalar", ctypes.c_int * 3),
+        ("gamma", ctypes.c_double), ("g", ctypes.c_double * 3), ("precision", ctypes.c_int),
+        ("gmres_restart", ctypes.c_int), ("gmres_max_restarts", ctypes.c_int),
+        ("gmres_rtol", ctypes.c_double), ("newton_max_its", ctypes.c_int), ("newton_tol", ctypes.c_double),
+        ("precond", ctypes.c_int), ("precond_sweeps", ctypes.c_int), ("max_dt_halvings", ctypes.c_int),
+    ]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+        ("dt_halvings", ctypes.c_int), ("gmres_unconverged", ctypes.c_int), ("fnorm0", ctypes.c_double),
+        ("fnorm", ctypes.c_double), ("max_drho", ctypes.c_double), ("wall_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every exported symbol of include/music.h with its ctypes signature
+SIGNATURES = {
+    "music_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+    "music_version": (ctypes.c_char_p, []),
+    "music_kernel_launches": (ctypes.c_uint64, []),
+    "music_create_grid": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
+    "music_destroy_grid": (ctypes.c_int, [ctypes.c_void_p]),
+    "music_state_size": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "music_grid_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "music_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "music_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "music_spatial_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "music_residual": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "music_jv": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "music_precond_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "music_newton_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(StepStats),
+                                         ctypes.c_void_p]),
+    "music_cfl_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dbl_p, ctypes.c_void_p]),
+    "music_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dbl_p,
+                                         ctypes.c_void_p]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmusic.so (building it first if needed and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError("libmusic.so is not built (%s); run paper_1610_10053_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def kernel_launches() -> int:
+    return int(load().music_kernel_launches())
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    load().music_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def check(code: int):
+    if code != MUSIC_OK:
+        raise MusicError(code, last_error())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
+    d = GridDesc()
+    d.ndim = prob.nd
+    for k in range(3):
+        d.n[k] = int(prob.n[k])
+        d.origin[k] = float(prob.x0[k])
+        d.length[k] = float(prob.length[k])
+        d.bc[k] = int(prob.bc[k])
+        d.wall_scalar[k] = int(prob.wall_scalar[k])
+        d.g[k] = float(prob.g[k])
+    d.gamma = float(prob.gamma)
+    d.precision = int(precision)
+    d.gmres_restart = int(prob.restart)
+    d.gmres_max_restarts = int(prob.max_restarts)
+    d.gmres_rtol = float(prob.gmres_rtol)
+    d.newton_max_its = int(prob.newton_max)
+    d.newton_tol = float(prob.newton_tol)
+    d.precond = 1 if int(prob.precond) == 1 else -1
+    d.precond_sweeps = int(prob.sweeps)
+    d.max_dt_halvings = int(prob.max_halvings)
+    for k, v in over.items():
+        setattr(d, k, v)
+    return d
+
+
+class Grid:
+    """Owns one music_grid (device state + solver workspace)."""
+
+    def __init__(self, prob, precision: int = FP64, **over):
+        L = load()
+        self.prob = prob
+        self.precision = precision
+        self.desc = desc_from_problem(prob, precision, **over)
+        h = ctypes.c_void_p()
+        check(L.music_create_grid(ctypes.byref(self.desc), ctypes.byref(h)))
+        self.h = h
+        self.n = int(L.music_state_size(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().music_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().music_grid_bytes(self.h))
+
+    @property
+    def kdtype(self):
+        import torch
+        return torch.float32 if self.precision == MIXED else torch.float64
+
+    # ---- state
+    def set_state(self, U):
+        import torch
+        if isinstance(U, torch.Tensor) and U.is_cuda:
+            U = U.contiguous().to(torch.float64)
+            check(load().music_set_state(self.h, _ptr(U), 1))
+        elif isinstance(U, torch.Tensor):
+            assert U.dtype == torch.float64 and U.is_contiguous() and U.numel() == self.n
+            check(load().music_set_state(self.h, ctypes.c_void_p(U.data_ptr()), 0))
+        else:
+            a = np.ascontiguousarray(U, dtype=np.float64)
+            assert a.size == self.n
+            check(load().music_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+
+    def get_state_into(self, out):
+        """Copy the state into a contiguous float64 host (e.g. pinned) tensor."""
+        import torch
+        assert isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
+        assert out.is_contiguous() and out.numel() == self.n
+        check(load().music_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 0))
+        return out
+
+    def get_state(self) -> np.ndarray:
+        a = np.empty(self.n, dtype=np.float64)
+        check(load().music_get_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
+        return a
+
+    # ---- single-call operators (device tensors in, device tensors out)
+    def spatial_operator(self, U):
+        import torch
+        R = torch.empty_like(U)
+        check(load().music_spatial_operator(self.h, _ptr(U), _ptr(R), _stream()))
+        return R
+
+    def residual(self, U, Un, dt: float):
+        import torch
+        F = torch.empty_like(U)
+        check(load().music_residual(self.h, _ptr(U), _ptr(Un), float(dt), _ptr(F), _stream()))
+        return F
+
+    def jv(self, U, v, dt: float, eps: float = 0.0):
+        import torch
+        out = torch.empty_like(v)
+        check(load().music_jv(self.h, _ptr(U), _ptr(v), _ptr(out), float(dt), float(eps), _stream()))
+        return out
+
+    def precond(self, U, dt: float, r):
+        import torch
+        z = torch.empty_like(r)
+        check(load().music_precond_apply(self.h, _ptr(U), float(dt), _ptr(r), _ptr(z), _stream()))
+        return z
+
+    # ---- stepping
+    def cfl_dt(self, cfl: float) -> float:
+        out = ctypes.c_double()
+        check(load().music_cfl_dt(self.h, float(cfl), ctypes.byref(out), _stream()))
+        return out.value
+
+    def newton_step(self, dt: float) -> dict:
+        st = StepStats()
+        check(load().music_newton_step(self.h, float(dt), ctypes.byref(st), _stream()))
+        return st.as_dict()
+
+    def step(self, cfl: Optional[float] = None, dt_max: Optional[float] = None) -> dict:
+        cfl = self.prob.cfl if cfl is None else cfl
+        dt_max = self.prob.dt_max if dt_max is None else dt_max
+        dt = self.cfl_dt(cfl)
+        if dt_max and dt_max > 0 and dt > dt_max:
+            dt = dt_max
+        return self.newton_step(dt)
+
+    def run(self, nsteps: Optional[int] = None, cfl: Optional[float] = None, dt_max: Optional[float] = None):
+        nsteps = self.prob.nsteps if nsteps is None else nsteps
+        return [self.step(cfl, dt_max) for _ in range(nsteps)]
+
+    def diagnostics(self, rho_L: Optional[float] = None, rho_H: Optional[float] = None) -> dict:
+        out = (ctypes.c_double * 6)()
+        rl = self.prob.rho_L if rho_L is None else rho_L
+        rh = self.prob.rho_H if rho_H is None else rho_H
+        check(load().music_diagnostics(self.h, float(rl), float(rh), out, _stream()))
+        names = ("mixing_height", "max_mach", "kh_mode_amplitude", "vertical_kinetic_energy",
+                 "mean_kinetic_energy", "max_speed")
+        return dict(zip(names, list(out)))

@@ -1,0 +1,427 @@
+// extern "C" entry points of libmusic (declared in include/music.h): grid
+// lifetime, state transfer and the single-call operators of the JFNK loop.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+#include <atomic>
+
+namespace {
+thread_local char g_err[1024] = "";
+std::atomic<unsigned long long> g_launches{0};
+
+void fill_defaults(music_grid_desc &d)
+{
+    if (d.gmres_restart == 0) d.gmres_restart = 30;
+    if (d.gmres_max_restarts == 0) d.gmres_max_restarts = 10;
+    if (d.gmres_rtol == 0.0) d.gmres_rtol = 1e-4;
+    if (d.newton_max_its == 0) d.newton_max_its = 12;
+    if (d.newton_tol == 0.0) d.newton_tol = 1e-8;
+    if (d.precond == 0) d.precond = MUSIC_PC_ACOUSTIC;
+    else if (d.precond < 0) d.precond = MUSIC_PC_NONE;
+    if (d.precond_sweeps == 0) d.precond_sweeps = 8;
+    if (d.max_dt_halvings == 0) d.max_dt_halvings = 4;
+    if (d.ndim == 2) d.n[2] = 1;
+}
+
+int validate(const music_grid_desc &d)
+{
+    if (d.ndim != 2 && d.ndim != 3) {
+        set_error("ndim must be 2 or 3 (got %d)", d.ndim);
+        return MUSIC_E_INVAL;
+    }
+    int hse = 0;
+    for (int k = 0; k < d.ndim; k++) {
+        if (d.n[k] < 4) {
+            set_error("n[%d] = %d: every direction needs at least 4 cells", k, d.n[k]);
+            return MUSIC_E_INVAL;
+        }
+        if (!(d.length[k] > 0.0)) {
+            set_error("length[%d] must be > 0", k);
+            return MUSIC_E_INVAL;
+        }
+        if (d.bc[k] != MUSIC_BC_PERIODIC && d.bc[k] != MUSIC_BC_WALL) {
+            set_error("bc[%d] = %d is not a known boundary condition", k, d.bc[k]);
+            return MUSIC_E_INVAL;
+        }
+        if (d.bc[k] == MUSIC_BC_WALL && d.wall_scalar[k] == MUSIC_WALL_HSE_LINEAR_T) hse++;
+        if (d.bc[k] == MUSIC_BC_WALL && d.wall_scalar[k] != MUSIC_WALL_MIRROR &&
+            d.wall_scalar[k] != MUSIC_WALL_HSE_LINEAR_T) {
+            set_error("wall_scalar[%d] = %d unknown", k, d.wall_scalar[k]);
+            return MUSIC_E_INVAL;
+        }
+    }
+    if (hse > 1) {
+        set_error("at most one direction may use hydrostatic wall ghosts");
+        return MUSIC_E_INVAL;
+    }
+    if (!(d.gamma > 1.0)) {
+        set_error("gamma must be > 1");
+        return MUSIC_E_INVAL;
+    }
+    if (d.precision != MUSIC_FP64 && d.precision != MUSIC_MIXED) {
+        set_error("precision %d unknown", d.precision);
+        return MUSIC_E_INVAL;
+    }
+    if (d.gmres_restart < 1 || d.gmres_restart > MUSIC_MAXV - 1) {
+        set_error("gmres_restart must be in 1..%d", MUSIC_MAXV - 1);
+        return MUSIC_E_INVAL;
+    }
+    if (d.precond != MUSIC_PC_NONE && d.precond != MUSIC_PC_ACOUSTIC) {
+        set_error("precond %d unknown", d.precond);
+        return MUSIC_E_INVAL;
+    }
+    if (d.precond_sweeps < 0 || d.gmres_max_restarts < 0 || d.newton_max_its < 1 || d.max_dt_halvings < 0 ||
+        !(d.newton_tol > 0.0) || !(d.gmres_rtol > 0.0)) {
+        set_error("invalid solver options");
+        return MUSIC_E_INVAL;
+    }
+    return MUSIC_OK;
+}
+
+GridParams make_params(const music_grid_desc &d)
+{
+    GridParams P;
+    memset(&P, 0, sizeof(P));
+    P.nd = d.ndim;
+    P.nv = 2 + d.ndim;
+    for (int k = 0; k < 3; k++) {
+        P.n[k] = (k < d.ndim) ? d.n[k] : 1;
+        P.ne[k] = (k < d.ndim) ? P.n[k] + 2 * MUSIC_GHOST : 1;
+        const double L = (k < d.ndim) ? d.length[k] : 1.0;
+        P.dx[k] = L / P.n[k];
+        P.idx[k] = 1.0 / P.dx[k];
+        P.idx2[k] = 1.0 / (P.dx[k] * P.dx[k]);
+        P.x0[k] = d.origin[k];
+        P.bc[k] = (k < d.ndim) ? d.bc[k] : MUSIC_BC_PERIODIC;
+        P.ws[k] = d.wall_scalar[k];
+        P.g[k] = (k < d.ndim) ? d.g[k] : 0.0;
+    }
+    P.N = (long long)P.n[0] * P.n[1] * P.n[2];
+    P.cs[0] = 1;
+    P.cs[1] = P.n[0];
+    P.cs[2] = (long long)P.n[0] * P.n[1];
+    P.es[0] = 1;
+    P.es[1] = P.ne[0];
+    P.es[2] = (long long)P.ne[0] * P.ne[1];
+    P.M = P.es[2] * P.ne[2];
+    P.gamma = d.gamma;
+    P.gm1 = d.gamma - 1.0;
+    return P;
+}
+
+struct Alloc {
+    music_grid *g;
+    int fail = 0;
+    template <typename T>
+    T *get(size_t count)
+    {
+        if (fail || count == 0) return nullptr;
+        void *p = nullptr;
+        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
+            fail = 1;
+            cudaGetLastError();
+            return nullptr;
+        }
+        g->bytes += count * sizeof(T);
+        return (T *)p;
+    }
+};
+
+void free_grid(music_grid *g)
+{
+    if (!g) return;
+    void *ptrs[] = {g->U, g->Un, g->Cn, g->RU, g->b, g->x, g->t64, g->t64b, g->V, g->w, g->z, g->u,
+                    g->pa[0], g->pa[1], g->pa[2], g->pgp, g->php, g->pD, g->pb, g->pdp, g->pdq,
+                    g->ext.rho, g->ext.e, g->ext.p, g->partials, g->ds, g->diag_rows};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (int d = 0; d < 3; d++) {
+        void *q[] = {g->ext.uf[d], g->ext.srho[d], g->ext.se[d], g->ext.Frho[d], g->ext.FE[d], g->ext.Phi[d]};
+        for (void *p : q)
+            if (p) cudaFree(p);
+        for (int e = 0; e < 3; e++) {
+            if (g->ext.su[d][e]) cudaFree(g->ext.su[d][e]);
+            if (g->ext.Psi[d][e]) cudaFree(g->ext.Psi[d][e]);
+        }
+    }
+    if (g->hs) cudaFreeHost(g->hs);
+    delete g;
+}
+
+int check_grid(const music_grid *g)
+{
+    if (!g) {
+        set_error("grid is NULL");
+        return MUSIC_E_INVAL;
+    }
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+extern "C" {
+
+size_t music_last_error(char *buf, size_t len)
+{
+    size_t n = strlen(g_err);
+    if (buf && len) {
+        size_t k = n < len - 1 ? n : len - 1;
+        memcpy(buf, g_err, k);
+        buf[k] = 0;
+    }
+    return n;
+}
+
+const char *music_version(void) { return "libmusic 0.1 (sm_103a)"; }
+
+uint64_t music_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int music_create_grid(const music_grid_desc *desc, music_grid **out)
+{
+    if (!desc || !out) {
+        set_error("music_create_grid: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    *out = nullptr;
+    music_grid_desc d = *desc;
+    fill_defaults(d);
+    TRY(validate(d));
+    music_grid *g = new (std::nothrow) music_grid;
+    if (!g) {
+        set_error("host allocation failed");
+        return MUSIC_E_OOM;
+    }
+    memset(g, 0, sizeof(*g));
+    g->desc = d;
+    g->P = make_params(d);
+    g->mixed = (d.precision == MUSIC_MIXED);
+    CUDA_TRY(cudaGetDevice(&g->device));
+    const GridParams &P = g->P;
+    g->n = (size_t)P.nv * P.N;
+    const size_t n = g->n, N = (size_t)P.N, M = (size_t)P.M;
+    const size_t ks = g->mixed ? sizeof(float) : sizeof(double);
+    // reduction blocks: enough to fill the GPU, fixed per grid
+    long long nb = ((long long)n + 255) / 256;
+    g->nb = (int)(nb > 2 * 152 ? 2 * 152 : (nb < 1 ? 1 : nb));
+    Alloc A{g};
+    g->U = A.get<double>(n);
+    g->Un = A.get<double>(n);
+    g->Cn = A.get<double>(n);
+    g->RU = A.get<double>(n);
+    g->b = A.get<double>(n);
+    g->x = A.get<double>(n);
+    g->t64 = A.get<double>(n);
+    g->V = A.get<char>((size_t)(d.gmres_restart + 1) * n * ks);
+    g->w = A.get<char>(n * ks);
+    g->z = A.get<char>(n * ks);
+    g->u = A.get<char>(n * ks);
+    if (d.precond != MUSIC_PC_NONE) {
+        for (int k = 0; k < P.nd; k++) g->pa[k] = A.get<char>(N * ks);
+        g->pgp = A.get<char>(N * ks);
+        g->php = A.get<char>(N * ks);
+        g->pD = A.get<char>(N * ks);
+        g->pb = A.get<char>(N * ks);
+        g->pdp = A.get<char>(N * ks);
+        g->pdq = A.get<char>(N * ks);
+    }
+    ExtScratch &X = g->ext;
+    X.rho = A.get<double>(M);
+    X.e = A.get<double>(M);
+    X.p = A.get<double>(M);
+    for (int k = 0; k < P.nd; k++) {
+        X.uf[k] = A.get<double>(M);
+        X.srho[k] = A.get<double>(M);
+        X.se[k] = A.get<double>(M);
+        X.Frho[k] = A.get<double>(M);
+        X.FE[k] = A.get<double>(M);
+        X.Phi[k] = A.get<double>(M);
+        for (int q = 0; q < P.nd; q++) {
+            X.su[k][q] = A.get<double>(M);
+            if (q != k) X.Psi[k][q] = A.get<double>(M);
+        }
+    }
+    g->partials = A.get<double>((size_t)MUSIC_MAXV * g->nb);
+    g->ds = A.get<DevScalars>(1);
+    g->diag_rows = A.get<double>((size_t)8 * P.n[1]);
+    if (A.fail) {
+        free_grid(g);
+        set_error("device allocation failed");
+        return MUSIC_E_OOM;
+    }
+    if (cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        free_grid(g);
+        set_error("pinned host allocation failed");
+        return MUSIC_E_OOM;
+    }
+    // zero everything the stencil might read before writing (ghost-edge scratch)
+    for (void *p : {(void *)X.rho, (void *)X.e, (void *)X.p}) CUDA_TRY(cudaMemset(p, 0, M * sizeof(double)));
+    for (int k = 0; k < P.nd; k++) {
+        for (void *p : {(void *)X.uf[k], (void *)X.srho[k], (void *)X.se[k], (void *)X.Frho[k], (void *)X.FE[k],
+                        (void *)X.Phi[k]})
+            CUDA_TRY(cudaMemset(p, 0, M * sizeof(double)));
+        for (int q = 0; q < P.nd; q++) {
+            CUDA_TRY(cudaMemset(X.su[k][q], 0, M * sizeof(double)));
+            if (q != k) CUDA_TRY(cudaMemset(X.Psi[k][q], 0, M * sizeof(double)));
+        }
+    }
+    CUDA_TRY(cudaMemset(g->U, 0, n * sizeof(double)));
+    CUDA_TRY(cudaMemset(g->ds, 0, sizeof(DevScalars)));
+    CUDA_TRY(cudaDeviceSynchronize());
+    *out = g;
+    return MUSIC_OK;
+}
+
+int music_destroy_grid(music_grid *grid)
+{
+    if (!grid) return MUSIC_OK;
+    cudaDeviceSynchronize();
+    free_grid(grid);
+    return MUSIC_OK;
+}
+
+size_t music_state_size(const music_grid *grid) { return grid ? grid->n : 0; }
+
+size_t music_grid_bytes(const music_grid *grid) { return grid ? grid->bytes : 0; }
+
+int music_set_state(music_grid *grid, const double *U, int is_device)
+{
+    TRY(check_grid(grid));
+    if (!U) {
+        set_error("music_set_state: NULL state");
+        return MUSIC_E_INVAL;
+    }
+    CUDA_TRY(cudaMemcpy(grid->U, U, grid->n * sizeof(double),
+                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+    return MUSIC_OK;
+}
+
+int music_get_state(music_grid *grid, double *U, int is_device)
+{
+    TRY(check_grid(grid));
+    if (!U) {
+        set_error("music_get_state: NULL buffer");
+        return MUSIC_E_INVAL;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(U, grid->U, grid->n * sizeof(double),
+                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+    return MUSIC_OK;
+}
+
+int music_spatial_operator(music_grid *grid, const double *U, double *R, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!U || !R) {
+        set_error("music_spatial_operator: NULL pointer");
+        return MUSIC_E_INVAL;
+    }
+    return stencil_apply(grid, SM_R, U, nullptr, nullptr, 1, R, 1, nullptr, 0.0, 1.0, (cudaStream_t)stream);
+}
+
+int music_residual(music_grid *grid, const double *U, const double *Un, double dt, double *F, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!U || !Un || !F) {
+        set_error("music_residual: NULL pointer");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // C^n in scratch, then F (RU scratch receives R(U))
+    TRY(stencil_apply(grid, SM_CN, Un, nullptr, nullptr, 1, grid->t64, 1, nullptr, dt, 1.0, s));
+    return stencil_apply(grid, SM_F, U, grid->t64, nullptr, 1, F, 1, grid->RU, dt, 1.0, s);
+}
+
+int music_jv(music_grid *grid, const double *U, const void *v, void *Jv, double dt, double eps, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!U || !v || !Jv) {
+        set_error("music_jv: NULL pointer");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kd = !grid->mixed;
+    // R(U) into the grid's RU scratch (SM_JV reads it from there)
+    TRY(stencil_apply(grid, SM_R, U, nullptr, nullptr, 1, grid->RU, 1, nullptr, dt, 1.0, s));
+    if (!(eps > 0.0)) {
+        TRY(dev_norm2(grid, U, 1, grid->n, &grid->ds->unorm2, s));
+        TRY(dev_norm2(grid, v, kd, grid->n, &grid->ds->vnorm2, s));
+    }
+    TRY(dev_set_eps(grid, eps > 0.0 ? eps : 0.0, s));
+    return stencil_apply(grid, SM_JV, U, grid->RU, v, kd, Jv, kd, nullptr, dt, 1.0, s);
+}
+
+int music_precond_apply(music_grid *grid, const double *U, double dt, const void *r, void *z, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!U || !r || !z) {
+        set_error("music_precond_apply: NULL pointer");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(precond_setup(grid, U, dt, s));
+    return precond_apply(grid, dt, r, z, 0, s);
+}
+
+int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!(dt > 0.0) || !std::isfinite(dt)) {
+        set_error("music_newton_step: dt must be finite and > 0");
+        return MUSIC_E_INVAL;
+    }
+    return newton_solve(grid, dt, st, (cudaStream_t)stream);
+}
+
+int music_cfl_dt(music_grid *grid, double cfl, double *dt, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!dt || !(cfl > 0.0)) {
+        set_error("music_cfl_dt: need cfl > 0 and an output pointer");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(cfl_rate(grid, grid->U, s));
+    CUDA_TRY(cudaMemcpyAsync(grid->hs, grid->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double rate = grid->hs->rate;
+    if (!(rate > 0.0) || !std::isfinite(rate)) {
+        set_error("music_cfl_dt: non-finite or zero signal speed");
+        return MUSIC_E_NONFINITE;
+    }
+    *dt = cfl / rate;
+    return MUSIC_OK;
+}
+
+int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out, void *stream)
+{
+    TRY(check_grid(grid));
+    if (!out || rho_H == rho_L) {
+        set_error("music_diagnostics: need an output pointer and rho_H != rho_L");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(diagnostics(grid, grid->U, rho_L, rho_H, s));
+    CUDA_TRY(cudaMemcpyAsync(grid->hs, grid->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int k = 0; k < 6; k++) out[k] = grid->hs->diag[k];
+    return MUSIC_OK;
+}
+
+}  // extern "C"

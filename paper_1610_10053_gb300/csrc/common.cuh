@@ -1,0 +1,144 @@
+// Shared definitions of the libmusic CUDA sources (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "music.h"
+
+#define MUSIC_GHOST 3
+#define MUSIC_MAXV 64          // max Krylov vectors per cycle + 1
+#define MUSIC_JACOBI_OMEGA 0.8 // weight of the pressure-system Jacobi sweeps
+
+// Grid geometry and physics, passed to kernels by value.
+struct GridParams {
+    int nd, nv;
+    int n[3];
+    long long N;          // interior cells
+    int ne[3];            // extended (ghosted) extent per direction
+    long long M;          // extended points
+    long long es[3];      // extended strides
+    long long cs[3];      // interior strides
+    double dx[3], idx[3], idx2[3];
+    double x0[3];
+    int bc[3], ws[3];
+    double gamma, gm1;
+    double g[3];
+};
+
+// Scalars produced and consumed on the device.
+struct DevScalars {
+    double unorm2;        // |U|^2 of the current Newton iterate
+    double vnorm2;        // |v|^2 of the vector a Jv is about to take
+    double eps;           // finite-difference step of the next Jv
+    double wnorm2;        // |w|^2 after re-orthogonalisation
+    double rnorm2;        // generic norm^2 slot
+    double maxdrho;       // Newton test
+    double rate;          // CFL rate
+    double pad;
+    double h[MUSIC_MAXV];   // first CGS pass
+    double h2[MUSIC_MAXV];  // second CGS pass
+    double diag[8];
+};
+
+__host__ __device__ inline long long ext_index(const GridParams &P, int i, int j, int k)
+{
+    return (long long)(i + MUSIC_GHOST) + P.es[1] * (j + MUSIC_GHOST) +
+           P.es[2] * (k + (P.nd == 3 ? MUSIC_GHOST : 0));
+}
+
+__device__ inline void ext_coords(const GridParams &P, long long x, int ix[3])
+{
+    ix[0] = (int)(x % P.ne[0]) - MUSIC_GHOST;
+    ix[1] = (int)((x / P.ne[0]) % P.ne[1]) - MUSIC_GHOST;
+    ix[2] = (int)(x / P.es[2]) - (P.nd == 3 ? MUSIC_GHOST : 0);
+}
+
+__device__ inline bool ext_has(const GridParams &P, const int ix[3], int d, int off)
+{
+    int lo = (d < P.nd) ? -MUSIC_GHOST : 0;
+    int a = ix[d] + off - lo;
+    return a >= 0 && a < P.ne[d];
+}
+
+__device__ inline void cell_coords(const GridParams &P, long long c, int ix[3])
+{
+    ix[0] = (int)(c % P.n[0]);
+    ix[1] = (int)((c / P.n[0]) % P.n[1]);
+    ix[2] = (int)(c / P.cs[2]);
+}
+
+__device__ inline long long cell_index(const GridParams &P, const int ix[3])
+{
+    return ix[0] + P.cs[1] * ix[1] + P.cs[2] * ix[2];
+}
+
+// neighbour of an interior cell along d (periodic wrap; walls clamp, the
+// coefficient of the wall face being zero wherever it is used)
+__device__ inline long long cell_nb(const GridParams &P, const int ix[3], int d, int off)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    int a = j[d] + off;
+    if (P.bc[d] == MUSIC_BC_PERIODIC)
+        a = (a % P.n[d] + P.n[d]) % P.n[d];
+    else if (a < 0)
+        a = 0;
+    else if (a >= P.n[d])
+        a = P.n[d] - 1;
+    j[d] = a;
+    return cell_index(P, j);
+}
+
+__device__ inline bool lower_wall(const GridParams &P, const int ix[3], int d)
+{
+    return P.bc[d] == MUSIC_BC_WALL && ix[d] == 0;
+}
+
+__device__ inline bool upper_wall(const GridParams &P, const int ix[3], int d)
+{
+    return P.bc[d] == MUSIC_BC_WALL && ix[d] == P.n[d] - 1;
+}
+
+// ---------------------------------------------------------------- reductions
+// Deterministic block sum: warp shuffles, then one warp over the warp sums.
+template <int BS>
+__device__ inline double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < BS / 32) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+// NaN-propagating max of non-negative values.
+__device__ inline double nanmax(double a, double b)
+{
+    if (a != a) return a;
+    if (b != b) return b;
+    return a > b ? a : b;
+}
+
+template <int BS>
+__device__ inline double block_max(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        r = (lane < BS / 32) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r = nanmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    return r;
+}
+
+template <typename T>
+__device__ inline double to_d(T v) { return (double)v; }

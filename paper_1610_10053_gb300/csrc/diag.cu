@@ -1,0 +1,124 @@
+// Time-step rate (Sec. 2.1, Eq. 4) and the scalar diagnostics of Secs. 3-6.
+//
+// Deterministic: one block per row (direction 1) produces the row's sums and
+// maxima in a fixed order; a single block then combines the rows in order.
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BS = 256;
+constexpr int NR = 8;  // per-row quantities
+
+__device__ inline double face_u(const GridParams &P, const double *U, const int ix[3], long long c, int d)
+{
+    if (lower_wall(P, ix, d)) return 0.0;
+    const long long l = cell_nb(P, ix, d, -1);
+    return U[(2 + d) * P.N + c] / (0.5 * (U[l] + U[c]));
+}
+
+// Per row j: [0] sum X_H, [1] sum KE density, [2] sum vertical KE, [3] sum v cos kx,
+// [4] sum v sin kx, [5] max Mach, [6] max speed, [7] max CFL rate.
+__global__ void __launch_bounds__(BS) k_rows(GridParams P, const double *U, double rho_L, double rho_H,
+                                             double kmode, double *rows)
+{
+    __shared__ double sh[BS / 32];
+    const int j = blockIdx.x;
+    const double dV = P.dx[0] * P.dx[1] * (P.nd == 3 ? P.dx[2] : 1.0);
+    double s[NR] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long per_row = (long long)P.n[0] * P.n[2];
+    for (long long t = threadIdx.x; t < per_row; t += BS) {
+        int ix[3] = {(int)(t % P.n[0]), j, (int)(t / P.n[0])};
+        const long long c = cell_index(P, ix);
+        const double rho = U[c];
+        const double cs = sqrt(P.gamma * (P.gm1 * U[P.N + c]) / rho);
+        s[0] += (rho - rho_L) / (rho_H - rho_L);
+        double u2 = 0.0;
+        for (int d = 0; d < P.nd; d++) {
+            const double um = face_u(P, U, ix, c, d);
+            double up = 0.0;
+            if (!upper_wall(P, ix, d)) {
+                int jx[3] = {ix[0], ix[1], ix[2]};
+                jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
+                up = face_u(P, U, jx, cell_index(P, jx), d);
+            }
+            const double uc = 0.5 * (um + up);
+            u2 += uc * uc;
+            const double rbar = lower_wall(P, ix, d) ? 0.0 : 0.5 * (U[cell_nb(P, ix, d, -1)] + rho);
+            s[1] += 0.5 * rbar * um * um;
+            const double q = (fabs(uc) + cs) * P.idx[d];
+            s[7] = nanmax(s[7], q);
+            if (d == 1) {
+                s[2] += 0.5 * rbar * um * um * dV;
+                const double xc = P.x0[0] + (ix[0] + 0.5) * P.dx[0];
+                s[3] += um * cos(kmode * xc);
+                s[4] += um * sin(kmode * xc);
+            }
+        }
+        const double sp = sqrt(u2);
+        s[5] = nanmax(s[5], sp / cs);
+        s[6] = nanmax(s[6], sp);
+    }
+    for (int q = 0; q < 5; q++) {
+        const double r = block_sum<BS>(s[q], sh);
+        if (threadIdx.x == 0) rows[(long long)q * P.n[1] + j] = r;
+    }
+    for (int q = 5; q < NR; q++) {
+        const double r = block_max<BS>(s[q], sh);
+        if (threadIdx.x == 0) rows[(long long)q * P.n[1] + j] = r;
+    }
+}
+
+__global__ void k_combine_rows(GridParams P, const double *rows, DevScalars *ds, int want_diag)
+{
+    // one thread, rows in order: deterministic and small (n[1] rows)
+    if (threadIdx.x != 0) return;
+    const int ny = P.n[1];
+    const double per_row = (double)((long long)P.n[0] * P.n[2]);
+    double h = 0, ek = 0, ey = 0, cr = 0, ci = 0, mach = 0, sp = 0, rate = 0;
+    for (int j = 0; j < ny; j++) {
+        const double xh = rows[j] / per_row;
+        const double xm = (xh <= 0.5) ? 2.0 * xh : 2.0 * (1.0 - xh);
+        h += xm * P.dx[1];
+        ek += rows[ny + j];
+        ey += rows[2 * ny + j];
+        cr += rows[3 * ny + j];
+        ci += rows[4 * ny + j];
+        mach = nanmax(mach, rows[5 * ny + j]);
+        sp = nanmax(sp, rows[6 * ny + j]);
+        rate = nanmax(rate, rows[7 * ny + j]);
+    }
+    ds->rate = rate;
+    if (want_diag) {
+        ds->diag[0] = h;
+        ds->diag[1] = mach;
+        ds->diag[2] = 2.0 / (double)P.N * sqrt(cr * cr + ci * ci);
+        ds->diag[3] = ey;
+        ds->diag[4] = ek / (double)P.N;
+        ds->diag[5] = sp;
+    }
+}
+
+int run_rows(music_grid *g, const double *U, double rho_L, double rho_H, int want_diag, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    const double kmode = 2.0 * (2.0 * M_PI / (P.n[0] * P.dx[0]));
+    k_rows<<<P.n[1], BS, 0, s>>>(P, U, rho_L, rho_H, kmode, g->diag_rows);
+    CHECK_LAUNCH();
+    k_combine_rows<<<1, 32, 0, s>>>(P, g->diag_rows, g->ds, want_diag);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+int cfl_rate(music_grid *g, const double *U, cudaStream_t s)
+{
+    return run_rows(g, U, 1.0, 2.0, 0, s);
+}
+
+int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s)
+{
+    return run_rows(g, U, rho_L, rho_H, 1, s);
+}

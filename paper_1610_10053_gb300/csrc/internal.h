@@ -1,0 +1,104 @@
+// Host-side internals of libmusic shared between translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "common.cuh"
+
+// Modes of the stencil assembly (what is written from R(W)).
+enum StencilMode {
+    SM_R = 0,    // out = R(U)
+    SM_CN = 1,   // out = U + dt/2 R(U)                  (step constant C^n)
+    SM_F = 2,    // out = sign ((U - C^n) - dt/2 R(U)), also R(U) -> RU
+    SM_JV = 3    // W = U + eps v; out = v - dt/2 (R(W) - RU) / eps
+};
+
+// Multi-pass stencil scratch on the extended grid (M doubles each).
+struct ExtScratch {
+    double *rho, *e, *p;
+    double *uf[3], *srho[3], *se[3], *Frho[3], *FE[3], *Phi[3];
+    double *su[3][3], *Psi[3][3];
+};
+
+struct music_grid {
+    music_grid_desc desc;
+    GridParams P;
+    int mixed;
+    int device;
+    size_t n;         // nv * N
+    size_t bytes;     // device bytes owned
+    int nb;           // reduction blocks
+    // FP64 state vectors
+    double *U, *Un, *Cn, *RU, *b, *x, *t64, *t64b;
+    // Krylov vectors (float for mixed, double otherwise)
+    void *V, *w, *z, *u;
+    // preconditioner (float for mixed, double otherwise)
+    void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
+    ExtScratch ext;
+    double *partials;      // [MUSIC_MAXV][nb]
+    DevScalars *ds;        // device scalars
+    DevScalars *hs;        // pinned host mirror
+    double *diag_rows;     // per-row diagnostic partials
+};
+
+// error reporting (thread local)
+void set_error(const char *fmt, ...);
+#define CUDA_TRY(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return MUSIC_E_CUDA;                                                        \
+        }                                                                               \
+    } while (0)
+// every kernel launch is followed by CHECK_LAUNCH, which also counts it
+void count_launch();
+#define CHECK_LAUNCH()               \
+    do {                             \
+        count_launch();              \
+        CUDA_TRY(cudaGetLastError()); \
+    } while (0)
+#define TRY(x)                      \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != MUSIC_OK) return r_; \
+    } while (0)
+
+// ----- stencil.cu -----
+// Evaluate R at W = U (+ eps v in SM_JV) and write per `mode`.
+//   U: state (device fp64); aux: C^n for SM_F, RU for SM_JV;
+//   v: SM_JV input (vin_double selects its type); out: output (out_double);
+//   RU_out: SM_F only, receives R(U).  eps is read from ds->eps in SM_JV.
+int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, const void *v,
+                  int vin_double, void *out, int out_double, double *RU_out, double dt,
+                  double sign, cudaStream_t s);
+
+// ----- krylov.cu -----
+// sum of squares of x (n elements) -> *dst (device), deterministic
+int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s);
+// eps = sqrt(2^-52) (1 + sqrt(unorm2)) / sqrt(vnorm2), or the fixed value if > 0
+int dev_set_eps(music_grid *g, double fixed, cudaStream_t s);
+int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s);          // h = V[0..j]^T w
+int krylov_update_dots(music_grid *g, int j, cudaStream_t s);                  // w -= V h; h2 = V^T w
+int krylov_update_norm(music_grid *g, int j, cudaStream_t s);                  // w -= V h2; wnorm2
+int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s);            // V_{j+1} = w * inv
+int krylov_first(music_grid *g, const double *r, double inv, cudaStream_t s);  // V_0 = r * inv
+int krylov_combine(music_grid *g, int k, const double *y, cudaStream_t s);     // u = sum y_i V_i
+int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s);      // x += z (z Krylov type)
+int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaStream_t s); // out = a - b
+int vec_neg(music_grid *g, const double *a, double *out, cudaStream_t s);
+int newton_update(music_grid *g, cudaStream_t s);                              // U += x, maxdrho
+int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, size_t n, cudaStream_t s);
+
+// ----- precond.cu -----
+int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s);  // frozen coefficients
+// z = M^-1 r; also |z|^2 -> ds->vnorm2 when want_norm
+int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);
+
+// ----- diag.cu -----
+int cfl_rate(music_grid *g, const double *U, cudaStream_t s);                  // -> ds->rate
+int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s);
+
+// ----- solver.cu -----
+int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);

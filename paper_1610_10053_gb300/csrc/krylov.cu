@@ -1,0 +1,389 @@
+// Vector kernels of the GMRES / Newton loop (Saad & Schultz 1986, cited in
+// Sec. 2): classical Gram-Schmidt with one re-orthogonalisation, each pass a
+// single sweep over w and the basis with FP64 accumulation; norms; the
+// Newton update with its density-correction test.
+//
+// Reductions are two-stage and deterministic: every block writes one partial
+// per quantity, then one block per quantity sums the partials in block order.
+// The block count per grid is fixed, so results do not depend on timing.
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BS = 256;
+
+struct Coef {
+    double c[MUSIC_MAXV];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *partial)
+{
+    __shared__ double sh[BS / 32];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < n; i += (long long)gridDim.x * BS) {
+        const double v = (double)x[i];
+        s += v * v;
+    }
+    const double r = block_sum<BS>(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+// dst[k] = sum_b partial[k * nb + b], one block per k, fixed order.
+__global__ void __launch_bounds__(BS) k_final_sum(const double *partial, int nb, double *dst)
+{
+    __shared__ double sh[BS / 32];
+    const double *p = partial + (long long)blockIdx.x * nb;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += BS) s += p[i];
+    const double r = block_sum<BS>(s, sh);
+    if (threadIdx.x == 0) dst[blockIdx.x] = r;
+}
+
+__global__ void __launch_bounds__(BS) k_final_max(const double *partial, int nb, double *dst)
+{
+    __shared__ double sh[BS / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += BS) s = nanmax(s, partial[i]);
+    const double r = block_max<BS>(s, sh);
+    if (threadIdx.x == 0) *dst = r;
+}
+
+__global__ void k_set_eps(DevScalars *ds, double fixed)
+{
+    if (fixed > 0.0) {
+        ds->eps = fixed;
+        return;
+    }
+    const double vn = sqrt(ds->vnorm2);
+    ds->eps = (vn == 0.0) ? 0.0 : (sqrt(2.220446049250313e-16) * (1.0 + sqrt(ds->unorm2))) / vn;
+}
+
+// h_i = <V_i, w>, i <= j; accumulators in registers (NVM >= j + 1).
+template <int NVM, typename KT>
+__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
+                                             int nb)
+{
+    __shared__ double sh[BS / 32];
+    double acc[NVM];
+#pragma unroll
+    for (int i = 0; i < NVM; i++) acc[i] = 0.0;
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        const double we = (double)w[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++)
+            if (i <= j) acc[i] += (double)V[(long long)i * n + e] * we;
+    }
+#pragma unroll
+    for (int i = 0; i < NVM; i++) {
+        if (i <= j) {
+            const double r = block_sum<BS>(acc[i], sh);
+            if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+        }
+    }
+}
+
+// w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
+// NORM, |w|^2 only.
+template <int NVM, bool NORM, typename KT>
+__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
+                                               double *partial, int nb)
+{
+    __shared__ double sh[BS / 32];
+    __shared__ double hs[MUSIC_MAXV];
+    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = h[i];
+    __syncthreads();
+    double acc[NORM ? 1 : NVM];
+#pragma unroll
+    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] = 0.0;
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        double we = (double)w[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++)
+            if (i <= j) we -= hs[i] * (double)V[(long long)i * n + e];
+        const KT ws = (KT)we;
+        w[e] = ws;
+        const double wr = (double)ws;
+        if (NORM) {
+            acc[0] += wr * wr;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NVM; i++)
+                if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
+        }
+    }
+    if (NORM) {
+        const double r = block_sum<BS>(acc[0], sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+            if (i <= j) {
+                const double r = block_sum<BS>(acc[i], sh);
+                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+            }
+        }
+    }
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long long n, double inv)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        dst[e] = (KT)((double)w[e] * inv);
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long long n, double inv)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        dst[e] = (KT)(r[e] / inv);
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(BS) k_combine(const KT *V, KT *u, long long n, int k, Coef y)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        double s = 0.0;
+        for (int i = 0; i < k; i++) s += y.c[i] * (double)V[(long long)i * n + e];
+        u[e] = (KT)s;
+    }
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(BS) k_axpy(const KT *z, double *x, long long n)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        x[e] += (double)z[e];
+}
+
+__global__ void __launch_bounds__(BS) k_sub(const double *a, const double *b, double *o, long long n)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        o[e] = a[e] - b[e];
+}
+
+__global__ void __launch_bounds__(BS) k_neg(const double *a, double *o, long long n)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        o[e] = -a[e];
+}
+
+template <typename S, typename D>
+__global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        o[e] = (D)a[e];
+}
+
+// U += x over all unknowns; partial max of |x_rho| / rho_new over cells.
+__global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
+                                                      double *partial)
+{
+    __shared__ double sh[BS / 32];
+    double m = 0.0;
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        const double u = U[e] + x[e];
+        U[e] = u;
+        if (e < N) m = nanmax(m, fabs(x[e]) / u);
+    }
+    const double r = block_max<BS>(m, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+int grid_blocks(long long n, int cap)
+{
+    long long b = (n + BS - 1) / BS;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <int NVM>
+int launch_dots(music_grid *g, int j, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    if (g->mixed)
+        k_dots<NVM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb);
+    else
+        k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
+                                                 g->nb);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+template <int NVM, bool NORM>
+int launch_update(music_grid *g, int j, const double *h, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    if (g->mixed)
+        k_update<NVM, NORM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
+                                                        g->nb);
+    else
+        k_update<NVM, NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h,
+                                                         g->partials, g->nb);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s)
+{
+    if (is_double)
+        k_sumsq<double><<<g->nb, BS, 0, s>>>((const double *)x, (long long)n, g->partials);
+    else
+        k_sumsq<float><<<g->nb, BS, 0, s>>>((const float *)x, (long long)n, g->partials);
+    CHECK_LAUNCH();
+    k_final_sum<<<1, BS, 0, s>>>(g->partials, g->nb, dst);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int dev_set_eps(music_grid *g, double fixed, cudaStream_t s)
+{
+    k_set_eps<<<1, 1, 0, s>>>(g->ds, fixed);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s)
+{
+    if (j < 8)
+        TRY(launch_dots<8>(g, j, s));
+    else if (j < 16)
+        TRY(launch_dots<16>(g, j, s));
+    else if (j < 32)
+        TRY(launch_dots<32>(g, j, s));
+    else
+        TRY(launch_dots<64>(g, j, s));
+    k_final_sum<<<j + 1, BS, 0, s>>>(g->partials, g->nb, dst_h);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int krylov_update_dots(music_grid *g, int j, cudaStream_t s)
+{
+    const double *h = g->ds->h;
+    if (j < 8)
+        TRY((launch_update<8, false>(g, j, h, s)));
+    else if (j < 16)
+        TRY((launch_update<16, false>(g, j, h, s)));
+    else if (j < 32)
+        TRY((launch_update<32, false>(g, j, h, s)));
+    else
+        TRY((launch_update<64, false>(g, j, h, s)));
+    k_final_sum<<<j + 1, BS, 0, s>>>(g->partials, g->nb, g->ds->h2);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int krylov_update_norm(music_grid *g, int j, cudaStream_t s)
+{
+    const double *h = g->ds->h2;
+    if (j < 8)
+        TRY((launch_update<8, true>(g, j, h, s)));
+    else if (j < 16)
+        TRY((launch_update<16, true>(g, j, h, s)));
+    else if (j < 32)
+        TRY((launch_update<32, true>(g, j, h, s)));
+    else
+        TRY((launch_update<64, true>(g, j, h, s)));
+    k_final_sum<<<1, BS, 0, s>>>(g->partials, g->nb, &g->ds->wnorm2);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    const int nb = grid_blocks(n, 152 * 16);
+    if (g->mixed)
+        k_scale_into<float><<<nb, BS, 0, s>>>((const float *)g->w, (float *)g->V + (long long)(j + 1) * n, n, inv);
+    else
+        k_scale_into<double><<<nb, BS, 0, s>>>((const double *)g->w, (double *)g->V + (long long)(j + 1) * n, n,
+                                              inv);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+// V_0 = r / beta  (the division keeps the oracle's rounding)
+int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    const int nb = grid_blocks(n, 152 * 16);
+    if (g->mixed)
+        k_first<float><<<nb, BS, 0, s>>>(r, (float *)g->V, n, beta);
+    else
+        k_first<double><<<nb, BS, 0, s>>>(r, (double *)g->V, n, beta);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int krylov_combine(music_grid *g, int k, const double *y, cudaStream_t s)
+{
+    Coef c;
+    for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (i < k) ? y[i] : 0.0;
+    const long long n = (long long)g->n;
+    const int nb = grid_blocks(n, 152 * 16);
+    if (g->mixed)
+        k_combine<float><<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c);
+    else
+        k_combine<double><<<nb, BS, 0, s>>>((const double *)g->V, (double *)g->u, n, k, c);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    const int nb = grid_blocks(n, 152 * 16);
+    if (g->mixed)
+        k_axpy<float><<<nb, BS, 0, s>>>((const float *)zk, x, n);
+    else
+        k_axpy<double><<<nb, BS, 0, s>>>((const double *)zk, x, n);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    k_sub<<<grid_blocks(n, 152 * 16), BS, 0, s>>>(a, b, out, n);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int vec_neg(music_grid *g, const double *a, double *out, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    k_neg<<<grid_blocks(n, 152 * 16), BS, 0, s>>>(a, out, n);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, size_t n, cudaStream_t s)
+{
+    const int nb = grid_blocks((long long)n, 152 * 16);
+    if (src_double && dst_double)
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    else if (!src_double && !dst_double)
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    else if (src_double)
+        k_cast<double, float><<<nb, BS, 0, s>>>((const double *)src, (float *)dst, (long long)n);
+    else
+        k_cast<float, double><<<nb, BS, 0, s>>>((const float *)src, (double *)dst, (long long)n);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int newton_update(music_grid *g, cudaStream_t s)
+{
+    k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials);
+    CHECK_LAUNCH();
+    k_final_max<<<1, BS, 0, s>>>(g->partials, g->nb, &g->ds->maxdrho);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}

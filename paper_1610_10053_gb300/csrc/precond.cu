@@ -1,0 +1,234 @@
+// Physics-based semi-implicit preconditioner (Sec. 2, after Park et al. 2009):
+// the stiff acoustic subsystem of J = I - dt/2 dR/dU with coefficients frozen
+// at the Newton iterate; advection and gravity are treated as absent:
+//   drho + tau div(dm) = r_rho
+//   dE   + tau hp div(dm / rbar) = r_E,        hp = E + p = gamma E
+//   dm   + tau grad(dp) = r_m,                  dp = (gamma - 1) dE
+// with tau = dt/2.  Eliminating dm gives the pressure Helmholtz problem
+//   dp/gp - tau^2 div(grad(dp)/rbar) = (gamma-1) r_E/gp - tau div(r_m/rbar),
+// gp = gamma p, relaxed with a fixed number of weighted-Jacobi sweeps from
+// zero (so M^-1 is a fixed linear map, as GMRES needs, and commutes with the
+// grid's mirror symmetries); dm, drho, dE follow by back substitution in flux
+// form, which keeps sum(drho) = sum(r_rho) and sum(dm) = sum(r_m).
+//
+// PT is float in mixed precision and double otherwise.
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BS = 256;
+
+template <typename PT>
+struct PC {
+    PT *a[3];   // 1 / rbar on the lower d-face (0 on wall faces)
+    PT *gp;     // gamma p
+    PT *hp;     // gamma E
+    PT *D;      // diagonal of the Helmholtz operator
+};
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_coeffs(GridParams P, const double *U, PC<PT> C)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        const double E = U[P.N + c];
+        C.gp[c] = (PT)(P.gamma * (P.gm1 * E));
+        C.hp[c] = (PT)(P.gamma * E);
+        for (int d = 0; d < P.nd; d++) {
+            if (lower_wall(P, ix, d)) {
+                C.a[d][c] = (PT)0;
+            } else {
+                const long long l = cell_nb(P, ix, d, -1);
+                C.a[d][c] = (PT)(1.0 / (0.5 * (U[l] + U[c])));
+            }
+        }
+    }
+}
+
+template <typename PT>
+__device__ inline PT a_up(const GridParams &P, const PC<PT> &C, const int ix[3], int d)
+{
+    return upper_wall(P, ix, d) ? (PT)0 : C.a[d][cell_nb(P, ix, d, +1)];
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        PT diag = 0;
+        for (int d = 0; d < P.nd; d++) diag += (a_up(P, C, ix, d) + C.a[d][c]) * (PT)P.idx2[d];
+        C.D[c] = (PT)1 / C.gp[c] + tau2 * diag;
+    }
+}
+
+template <typename PT, typename RT>
+__global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, const RT *r, PT *b, PT tau)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        PT divm = 0;
+        for (int d = 0; d < P.nd; d++) {
+            const PT ap = a_up(P, C, ix, d), am = C.a[d][c];
+            const PT rp = (PT)r[(2 + d) * P.N + cell_nb(P, ix, d, +1)];
+            const PT rm = (PT)r[(2 + d) * P.N + c];
+            divm += (ap * rp - am * rm) * (PT)P.idx[d];
+        }
+        b[c] = (PT)P.gm1 * (PT)r[P.N + c] / C.gp[c] - tau * divm;
+    }
+}
+
+// dq = (1 - w) dp + w (b + tau^2 sum a dp_nb / dx^2) / D; first sweep from 0
+template <typename PT, bool FIRST>
+__global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, const PT *b, const PT *dp, PT *dq,
+                                               PT tau2)
+{
+    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        if (FIRST) {
+            dq[c] = w * (b[c] / C.D[c]);
+            continue;
+        }
+        int ix[3];
+        cell_coords(P, c, ix);
+        PT off = 0;
+        for (int d = 0; d < P.nd; d++) {
+            const PT ap = a_up(P, C, ix, d), am = C.a[d][c];
+            off += (ap * dp[cell_nb(P, ix, d, +1)] + am * dp[cell_nb(P, ix, d, -1)]) * (PT)P.idx2[d];
+        }
+        dq[c] = ((PT)1 - w) * dp[c] + w * ((b[c] + tau2 * off) / C.D[c]);
+    }
+}
+
+template <typename PT, typename RT>
+__device__ inline PT dm_face(const GridParams &P, const RT *r, const PT *dp, const int ix[3], long long c,
+                             int d, PT tau)
+{
+    // momentum correction on the lower d-face of cell ix (c)
+    if (lower_wall(P, ix, d)) return (PT)r[(2 + d) * P.N + c];
+    return (PT)r[(2 + d) * P.N + c] - tau * (dp[c] - dp[cell_nb(P, ix, d, -1)]) * (PT)P.idx[d];
+}
+
+template <typename PT, typename RT>
+__global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, const RT *r, const PT *dp, RT *z, PT tau,
+                                             double *partial)
+{
+    __shared__ double sh[BS / 32];
+    double nrm = 0.0;
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        PT divm = 0, divu = 0;
+        for (int d = 0; d < P.nd; d++) {
+            const PT mm_own = dm_face(P, r, dp, ix, c, d, tau);
+            z[(2 + d) * P.N + c] = (RT)mm_own;
+            const double zz = (double)(RT)mm_own;
+            nrm += zz * zz;
+            PT mp = 0;
+            if (!upper_wall(P, ix, d)) {
+                int jx[3] = {ix[0], ix[1], ix[2]};
+                jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
+                mp = dm_face(P, r, dp, jx, cell_index(P, jx), d, tau);
+            }
+            const PT mm = lower_wall(P, ix, d) ? (PT)0 : mm_own;
+            divm += (mp - mm) * (PT)P.idx[d];
+            divu += (a_up(P, C, ix, d) * mp - C.a[d][c] * mm) * (PT)P.idx[d];
+        }
+        const PT zr = (PT)r[c] - tau * divm;
+        const PT ze = (PT)r[P.N + c] - tau * C.hp[c] * divu;
+        z[c] = (RT)zr;
+        z[P.N + c] = (RT)ze;
+        nrm += (double)(RT)zr * (double)(RT)zr + (double)(RT)ze * (double)(RT)ze;
+    }
+    if (partial) {
+        const double t = block_sum<BS>(nrm, sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    }
+}
+
+int nblocks(long long n)
+{
+    long long b = (n + BS - 1) / BS;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+template <typename PT>
+PC<PT> pc_of(music_grid *g)
+{
+    PC<PT> C;
+    for (int d = 0; d < 3; d++) C.a[d] = (PT *)g->pa[d];
+    C.gp = (PT *)g->pgp;
+    C.hp = (PT *)g->php;
+    C.D = (PT *)g->pD;
+    return C;
+}
+
+template <typename PT>
+int setup_t(music_grid *g, const double *U, double dt, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    PC<PT> C = pc_of<PT>(g);
+    const double tau = 0.5 * dt;
+    k_coeffs<PT><<<nblocks(P.N), BS, 0, s>>>(P, U, C);
+    CHECK_LAUNCH();
+    k_diag<PT><<<nblocks(P.N), BS, 0, s>>>(P, C, (PT)(tau * tau));
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+template <typename PT>
+int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    PC<PT> C = pc_of<PT>(g);
+    const double tau = 0.5 * dt;
+    const PT taup = (PT)tau, tau2 = (PT)(tau * tau);
+    const int nb = nblocks(P.N);
+    PT *b = (PT *)g->pb, *dp = (PT *)g->pdp, *dq = (PT *)g->pdq;
+    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, r, b, taup);
+    CHECK_LAUNCH();
+    const int K = g->desc.precond_sweeps;
+    for (int k = 0; k < K; k++) {
+        if (k == 0)
+            k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau2);
+        else
+            k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau2);
+        CHECK_LAUNCH();
+        PT *t = dp;
+        dp = dq;
+        dq = t;
+    }
+    if (K == 0) CUDA_TRY(cudaMemsetAsync(dp, 0, P.N * sizeof(PT), s));
+    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, r, dp, z, taup, nullptr);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
+{
+    if (g->desc.precond == MUSIC_PC_NONE) return MUSIC_OK;
+    return g->mixed ? setup_t<float>(g, U, dt, s) : setup_t<double>(g, U, dt, s);
+}
+
+int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
+{
+    const size_t n = g->n;
+    if (g->desc.precond == MUSIC_PC_NONE) {
+        const size_t es = g->mixed ? sizeof(float) : sizeof(double);
+        if (r != z) CUDA_TRY(cudaMemcpyAsync(z, r, n * es, cudaMemcpyDeviceToDevice, s));
+    } else if (g->mixed) {
+        TRY(apply_t<float>(g, dt, (const float *)r, (float *)z, s));
+    } else {
+        TRY(apply_t<double>(g, dt, (const double *)r, (double *)z, s));
+    }
+    if (want_norm) TRY(dev_norm2(g, z, !g->mixed, n, &g->ds->vnorm2, s));
+    return MUSIC_OK;
+}

@@ -1,0 +1,208 @@
+// Newton-Raphson on the Crank-Nicolson system with restarted, right
+// preconditioned GMRES and Jacobian-free products (Sec. 2).  The host
+// sequences the kernels and keeps the (m+1) x m Hessenberg matrix and its
+// Givens rotations; every vector operation runs on the device.
+#include <cmath>
+#include <cstring>
+#include <chrono>
+
+#include "internal.h"
+
+namespace {
+
+struct GmresOut {
+    int its;
+    int converged;
+    double bnorm;
+};
+
+int sync_scalars(music_grid *g, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MUSIC_OK;
+}
+
+// J v for the current Newton iterate: v (Krylov type, or FP64 when
+// vin_double) -> out.  eps from |U| (ds->unorm2) and |v|.
+int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
+             int need_vnorm, cudaStream_t s)
+{
+    if (need_vnorm) TRY(dev_norm2(g, v, vin_double, g->n, &g->ds->vnorm2, s));
+    TRY(dev_set_eps(g, 0.0, s));
+    return stencil_apply(g, SM_JV, g->U, g->RU, v, vin_double, out, out_double, nullptr, dt, 1.0, s);
+}
+
+// Solve J x = b (b = g->b, FP64) into g->x (FP64).
+int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
+{
+    const int m = g->desc.gmres_restart;
+    const double rtol = g->desc.gmres_rtol;
+    const size_t n = g->n;
+    const int kd = !g->mixed;  // Krylov vectors are double?
+    const size_t ks = kd ? sizeof(double) : sizeof(float);
+    o->its = 0;
+    o->converged = 0;
+    o->bnorm = 0.0;
+    CUDA_TRY(cudaMemsetAsync(g->x, 0, n * sizeof(double), s));
+    TRY(dev_norm2(g, g->b, 1, n, &g->ds->rnorm2, s));
+    TRY(sync_scalars(g, s));
+    const double bnorm = sqrt(g->hs->rnorm2);
+    o->bnorm = bnorm;
+    if (!std::isfinite(bnorm)) {
+        set_error("GMRES: non-finite right-hand side");
+        return MUSIC_E_NONFINITE;
+    }
+    if (bnorm == 0.0) {
+        o->converged = 1;
+        return MUSIC_OK;
+    }
+    const double target = rtol * bnorm;
+    double H[MUSIC_MAXV][MUSIC_MAXV];  // H[i][j]
+    double cs[MUSIC_MAXV], sn[MUSIC_MAXV], gv[MUSIC_MAXV + 1], y[MUSIC_MAXV];
+    double resid = bnorm;
+    for (int cycle = 0; cycle <= g->desc.gmres_max_restarts; cycle++) {
+        const double *r = g->b;
+        double beta = bnorm;
+        if (cycle > 0) {
+            // r = b - J x  (J x in FP64)
+            TRY(jv_apply(g, g->x, 1, g->t64, 1, dt, 1, s));
+            TRY(vec_sub(g, g->b, g->t64, g->t64, s));
+            r = g->t64;
+            TRY(dev_norm2(g, r, 1, n, &g->ds->rnorm2, s));
+            TRY(sync_scalars(g, s));
+            beta = sqrt(g->hs->rnorm2);
+        }
+        if (!std::isfinite(beta)) {
+            set_error("GMRES: non-finite residual");
+            return MUSIC_E_NONFINITE;
+        }
+        resid = beta;
+        if (beta <= target) {
+            o->converged = 1;
+            break;
+        }
+        TRY(krylov_first(g, r, beta, s));
+        for (int i = 0; i <= m; i++) gv[i] = 0.0;
+        gv[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; j++) {
+            void *Vj = (char *)g->V + (size_t)j * n * ks;
+            TRY(precond_apply(g, dt, Vj, g->z, 1, s));
+            TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s));
+            TRY(krylov_dots(g, j, g->ds->h, s));
+            TRY(krylov_update_dots(g, j, s));
+            TRY(krylov_update_norm(g, j, s));
+            TRY(sync_scalars(g, s));
+            const DevScalars *hs = g->hs;
+            const double hn = sqrt(hs->wnorm2);
+            if (!std::isfinite(hn)) {
+                set_error("GMRES: non-finite Arnoldi vector");
+                return MUSIC_E_NONFINITE;
+            }
+            for (int i = 0; i <= j; i++) H[i][j] = hs->h[i] + hs->h2[i];
+            H[j + 1][j] = hn;
+            for (int i = 0; i < j; i++) {
+                const double t0 = H[i][j], t1 = H[i + 1][j];
+                H[i][j] = cs[i] * t0 + sn[i] * t1;
+                H[i + 1][j] = -sn[i] * t0 + cs[i] * t1;
+            }
+            const double a0 = H[j][j], a1 = H[j + 1][j];
+            if (a1 == 0.0) {
+                cs[j] = 1.0;
+                sn[j] = 0.0;
+            } else {
+                const double t = sqrt(a0 * a0 + a1 * a1);
+                cs[j] = a0 / t;
+                sn[j] = a1 / t;
+            }
+            H[j][j] = cs[j] * a0 + sn[j] * a1;
+            H[j + 1][j] = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            o->its++;
+            k = j + 1;
+            resid = fabs(gv[j + 1]);
+            if (hn == 0.0 || resid <= target) break;
+            TRY(krylov_scale(g, j, 1.0 / hn, s));
+        }
+        for (int i = k - 1; i >= 0; i--) {
+            double t = gv[i];
+            for (int l = i + 1; l < k; l++) t -= H[i][l] * y[l];
+            y[i] = t / H[i][i];
+        }
+        TRY(krylov_combine(g, k, y, s));
+        TRY(precond_apply(g, dt, g->u, g->z, 0, s));
+        TRY(vec_axpy_k(g, g->z, g->x, s));
+        if (resid <= target) {
+            o->converged = 1;
+            break;
+        }
+    }
+    return MUSIC_OK;
+}
+
+// One Newton solve of size dt from the grid's state.  Returns MUSIC_OK,
+// MUSIC_E_NEWTON_FAIL (state restored) or a hard error.
+int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s)
+{
+    const size_t n = g->n;
+    CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    TRY(stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt, 1.0, s));
+    st->newton_its = 0;
+    st->gmres_its = 0;
+    st->gmres_unconverged = 0;
+    int ok = 0;
+    for (int k = 0; k < g->desc.newton_max_its; k++) {
+        // b = -F(U), RU = R(U)
+        TRY(stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s));
+        TRY(dev_norm2(g, g->U, 1, n, &g->ds->unorm2, s));
+        TRY(precond_setup(g, g->U, dt, s));
+        GmresOut go;
+        int rc = gmres(g, dt, &go, s);
+        if (rc != MUSIC_OK) return rc;
+        st->gmres_its += go.its;
+        st->gmres_unconverged += !go.converged;
+        st->fnorm = go.bnorm;  // |F(U^k)|
+        if (k == 0) st->fnorm0 = st->fnorm;
+        TRY(newton_update(g, s));
+        TRY(sync_scalars(g, s));
+        st->max_drho = g->hs->maxdrho;
+        st->newton_its = k + 1;
+        if (g->hs->maxdrho <= g->desc.newton_tol) {
+            ok = 1;
+            break;
+        }
+        if (!std::isfinite(g->hs->maxdrho)) break;
+    }
+    if (!ok) {
+        CUDA_TRY(cudaMemcpyAsync(g->U, g->Un, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return MUSIC_E_NEWTON_FAIL;
+    }
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_t s)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    music_step_stats st;
+    memset(&st, 0, sizeof(st));
+    int rc = MUSIC_E_NEWTON_FAIL;
+    int h = 0;
+    for (;;) {
+        st.dt = dt;
+        rc = newton_attempt(g, dt, &st, s);
+        if (rc != MUSIC_E_NEWTON_FAIL) break;
+        if (h >= g->desc.max_dt_halvings) break;
+        dt *= 0.5;
+        h++;
+    }
+    st.dt_halvings = h;
+    st.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st_out) *st_out = st;
+    if (rc == MUSIC_E_NEWTON_FAIL) set_error("Newton did not converge after %d dt halvings", h);
+    return rc;
+}

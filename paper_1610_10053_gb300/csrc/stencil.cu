@@ -1,0 +1,321 @@
+// Spatial operator R(U) (paper Sec. 2, Eqs. 1-3) and the quantities built on
+// it: the Crank-Nicolson residual and the Jacobian-free product.
+//
+// Generic multi-pass path for 2-D and 3-D grids: each pass is one kernel over
+// the ghosted ("extended") grid, writing its per-point results to scratch
+// planes, so no value is computed twice:
+//   1 load   : ghost filling (periodic / mirror / hydrostatic walls), e, p,
+//              face velocities u_d = m_d / rbar (W = U + eps v for Jv)
+//   2 slopes : van Leer limited slopes of rho, e and every u_q along every d
+//   3 fluxes : upwind mass and internal-energy fluxes on d-faces
+//   4 momentum fluxes at cell centres (along d) and on edges (across d)
+//   5 assemble the interior residuals and write R, C^n, F or Jv.
+#include <cmath>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int BS = 256;
+
+template <typename VT>
+struct WLoad {
+    const double *U;
+    const VT *v;
+    const double *eps;  // device scalar (Jv) or null
+    __device__ inline double operator()(long long i) const
+    {
+        double u = U[i];
+        if (v) u = u + (*eps) * (double)v[i];
+        return u;
+    }
+};
+
+__device__ inline double vanleer(double a, double b)
+{
+    return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
+}
+
+template <typename VT>
+__device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[3], double &rho,
+                          double &E)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    int hd = -1, lower = 0;
+    for (int d = 0; d < P.nd; d++) {
+        const int a = j[d], n = P.n[d];
+        if (a >= 0 && a < n) continue;
+        if (P.bc[d] == MUSIC_BC_PERIODIC)
+            j[d] = (a % n + n) % n;
+        else if (P.ws[d] == MUSIC_WALL_MIRROR)
+            j[d] = (a < 0) ? (-1 - a) : (2 * n - 1 - a);
+        else {
+            hd = d;
+            lower = (a < 0);
+        }
+    }
+    if (hd < 0) {
+        const long long c = cell_index(P, j);
+        rho = W(c);
+        E = W(P.N + c);
+        return;
+    }
+    const int n = P.n[hd];
+    j[hd] = lower ? 0 : n - 1;
+    const long long c0 = cell_index(P, j);
+    j[hd] = lower ? 1 : n - 2;
+    const long long c1 = cell_index(P, j);
+    const double r0 = W(c0), r1 = W(c1);
+    const double T0 = (P.gm1 * W(P.N + c0)) / r0;
+    const double T1 = (P.gm1 * W(P.N + c1)) / r1;
+    const double Tg = 2.0 * T0 - T1;
+    const double hs = 0.5 * P.dx[hd] * P.g[hd];
+    const double rg = lower ? __dmul_rn(r0, T0 - hs) / (Tg + hs) : __dmul_rn(r0, T0 + hs) / (Tg - hs);
+    rho = rg;
+    E = __dmul_rn(rg, Tg) / P.gm1;
+}
+
+template <typename VT>
+__device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const int ix[3], int d)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    double sgn = 1.0;
+    for (int w = 0; w < P.nd; w++) {
+        const int a = j[w], n = P.n[w];
+        if (a >= 0 && a < n) continue;
+        if (P.bc[w] == MUSIC_BC_PERIODIC) {
+            j[w] = (a % n + n) % n;
+        } else if (w == d) {
+            if (a == n) return 0.0;
+            j[w] = (a < 0) ? -a : 2 * n - a;
+            sgn = -sgn;
+        } else {
+            j[w] = (a < 0) ? (-1 - a) : (2 * n - 1 - a);
+        }
+    }
+    if (P.bc[d] == MUSIC_BC_WALL && j[d] == 0) return 0.0;
+    const long long c = cell_index(P, j);
+    int l[3] = {j[0], j[1], j[2]};
+    l[d] = (j[d] == 0) ? P.n[d] - 1 : j[d] - 1;
+    const long long cl = cell_index(P, l);
+    const double rbar = 0.5 * (W(cl) + W(c));
+    return sgn * (W((long long)(2 + d) * P.N + c) / rbar);
+}
+
+template <typename VT>
+__global__ void __launch_bounds__(BS) k_load(GridParams P, WLoad<VT> W, ExtScratch X)
+{
+    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
+        int ix[3];
+        ext_coords(P, x, ix);
+        double rho, E;
+        load_cell(P, W, ix, rho, E);
+        X.rho[x] = rho;
+        X.e[x] = E / rho;
+        X.p[x] = P.gm1 * E;
+        for (int d = 0; d < P.nd; d++) X.uf[d][x] = face_velocity(P, W, ix, d);
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_slopes(GridParams P, ExtScratch X)
+{
+    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
+        int ix[3];
+        ext_coords(P, x, ix);
+        for (int d = 0; d < P.nd; d++) {
+            if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, d, +1)) continue;
+            const long long s = P.es[d];
+            X.srho[d][x] = vanleer(X.rho[x] - X.rho[x - s], X.rho[x + s] - X.rho[x]);
+            X.se[d][x] = vanleer(X.e[x] - X.e[x - s], X.e[x + s] - X.e[x]);
+            for (int q = 0; q < P.nd; q++)
+                X.su[q][d][x] = vanleer(X.uf[q][x] - X.uf[q][x - s], X.uf[q][x + s] - X.uf[q][x]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_fluxes(GridParams P, ExtScratch X)
+{
+    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
+        int ix[3];
+        ext_coords(P, x, ix);
+        for (int d = 0; d < P.nd; d++) {
+            if (!ext_has(P, ix, d, -2) || !ext_has(P, ix, d, +1)) continue;
+            const long long s = P.es[d];
+            const double u = X.uf[d][x];
+            double rs, es;
+            if (u >= 0.0) {
+                rs = X.rho[x - s] + 0.5 * X.srho[d][x - s];
+                es = X.e[x - s] + 0.5 * X.se[d][x - s];
+            } else {
+                rs = X.rho[x] - 0.5 * X.srho[d][x];
+                es = X.e[x] - 0.5 * X.se[d][x];
+            }
+            const double fr = u * rs;
+            X.Frho[d][x] = fr;
+            X.FE[d][x] = fr * es;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
+{
+    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
+        int ix[3];
+        ext_coords(P, x, ix);
+        for (int d = 0; d < P.nd; d++) {
+            const long long s = P.es[d];
+            if (ext_has(P, ix, d, -2) && ext_has(P, ix, d, +2)) {
+                const double fm = 0.5 * (X.Frho[d][x] + X.Frho[d][x + s]);
+                const double us = (fm >= 0.0) ? X.uf[d][x] + 0.5 * X.su[d][d][x]
+                                              : X.uf[d][x + s] - 0.5 * X.su[d][d][x + s];
+                X.Phi[d][x] = fm * us;
+            }
+            for (int q = 0; q < P.nd; q++) {
+                if (q == d) continue;
+                if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, q, -2) || !ext_has(P, ix, q, +1)) continue;
+                const long long t = P.es[q];
+                const double fm = 0.5 * (X.Frho[q][x - s] + X.Frho[q][x]);
+                const double us = (fm >= 0.0) ? X.uf[d][x - t] + 0.5 * X.su[d][q][x - t]
+                                              : X.uf[d][x] - 0.5 * X.su[d][q][x];
+                X.Psi[d][q][x] = fm * us;
+            }
+        }
+    }
+}
+
+template <int MODE, typename VIN, typename VOUT>
+__global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, const double *U,
+                                                 const double *aux, const VIN *v, VOUT *out,
+                                                 double *RU_out, double hdt, double sign,
+                                                 const double *eps)
+{
+    double c_jv = 0.0;
+    bool zero = false;
+    if (MODE == SM_JV) {
+        const double e = *eps;
+        zero = (e == 0.0);
+        c_jv = zero ? 0.0 : hdt / e;
+    }
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        const long long x = ext_index(P, ix[0], ix[1], ix[2]);
+        double R[5];
+        double accr = 0.0, acce = 0.0, divu = 0.0;
+        for (int d = 0; d < P.nd; d++) {
+            const long long s = P.es[d];
+            accr += (X.Frho[d][x + s] - X.Frho[d][x]) * P.idx[d];
+            acce += (X.FE[d][x + s] - X.FE[d][x]) * P.idx[d];
+            divu += (X.uf[d][x + s] - X.uf[d][x]) * P.idx[d];
+        }
+        R[0] = -accr;
+        R[1] = -acce - X.p[x] * divu;
+        for (int d = 0; d < P.nd; d++) {
+            if (P.bc[d] == MUSIC_BC_WALL && ix[d] == 0) {
+                R[2 + d] = 0.0;
+                continue;
+            }
+            const long long s = P.es[d];
+            double acc = 0.0;
+            for (int q = 0; q < P.nd; q++) {
+                if (q == d)
+                    acc += (X.Phi[d][x] - X.Phi[d][x - s]) * P.idx[d];
+                else
+                    acc += (X.Psi[d][q][x + P.es[q]] - X.Psi[d][q][x]) * P.idx[q];
+            }
+            const double rbar = 0.5 * (X.rho[x - s] + X.rho[x]);
+            R[2 + d] = (-acc - (X.p[x] - X.p[x - s]) * P.idx[d]) + rbar * P.g[d];
+        }
+        for (int q = 0; q < P.nv; q++) {
+            const long long i = (long long)q * P.N + c;
+            if (MODE == SM_R) {
+                out[i] = (VOUT)R[q];
+            } else if (MODE == SM_CN) {
+                out[i] = (VOUT)(U[i] + hdt * R[q]);
+            } else if (MODE == SM_F) {
+                out[i] = (VOUT)(sign * ((U[i] - aux[i]) - hdt * R[q]));
+                if (RU_out) RU_out[i] = R[q];
+            } else {
+                out[i] = zero ? (VOUT)0 : (VOUT)((double)v[i] - c_jv * (R[q] - aux[i]));
+            }
+        }
+    }
+}
+
+int blocks_for(long long n)
+{
+    long long b = (n + BS - 1) / BS;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename VT>
+int run_passes(music_grid *g, const double *U, const VT *v, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    WLoad<VT> W{U, v, v ? &g->ds->eps : nullptr};
+    const int nbm = blocks_for(P.M);
+    k_load<VT><<<nbm, BS, 0, s>>>(P, W, g->ext);
+    CHECK_LAUNCH();
+    k_slopes<<<nbm, BS, 0, s>>>(P, g->ext);
+    CHECK_LAUNCH();
+    k_fluxes<<<nbm, BS, 0, s>>>(P, g->ext);
+    CHECK_LAUNCH();
+    k_momentum<<<nbm, BS, 0, s>>>(P, g->ext);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+}  // namespace
+
+int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, const void *v,
+                  int vin_double, void *out, int out_double, double *RU_out, double dt, double sign,
+                  cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    const double hdt = 0.5 * dt;
+    const int nbn = blocks_for(P.N);
+    const double *eps = &g->ds->eps;
+    if (mode == SM_JV) {
+        if (vin_double)
+            TRY(run_passes<double>(g, U, (const double *)v, s));
+        else
+            TRY(run_passes<float>(g, U, (const float *)v, s));
+    } else {
+        TRY(run_passes<double>(g, U, nullptr, s));
+    }
+    switch (mode) {
+    case SM_R:
+        k_assemble<SM_R, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, nullptr, (double *)out,
+                                                             nullptr, hdt, sign, eps);
+        break;
+    case SM_CN:
+        k_assemble<SM_CN, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, nullptr, (double *)out,
+                                                              nullptr, hdt, sign, eps);
+        break;
+    case SM_F:
+        k_assemble<SM_F, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, nullptr, (double *)out,
+                                                             RU_out, hdt, sign, eps);
+        break;
+    case SM_JV:
+        if (vin_double && out_double)
+            k_assemble<SM_JV, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, (const double *)v,
+                                                                  (double *)out, nullptr, hdt, sign, eps);
+        else if (!vin_double && !out_double)
+            k_assemble<SM_JV, float, float><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, (const float *)v,
+                                                                (float *)out, nullptr, hdt, sign, eps);
+        else if (vin_double && !out_double)
+            k_assemble<SM_JV, double, float><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, (const double *)v,
+                                                                 (float *)out, nullptr, hdt, sign, eps);
+        else
+            k_assemble<SM_JV, float, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, (const float *)v,
+                                                                 (double *)out, nullptr, hdt, sign, eps);
+        break;
+    default:
+        set_error("stencil_apply: bad mode %d", mode);
+        return MUSIC_E_INVAL;
+    }
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}

@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+declared in include/*.h; the product path never links or imports the oracle.
+No compute calls (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for f in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not f.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", f)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(music_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1610_10053_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path), path
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("music_create_grid", "music_residual", "music_jv", "music_precond_apply",
+                     "music_newton_step", "music_destroy_grid", "music_spatial_operator"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L, path = lib
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    from paper_1610_10053_gb300 import binding
+    assert set(declared_functions()) <= set(binding.SIGNATURES) | {
+        n for n in declared_functions() if n.startswith("music_server") or n in (
+            "music_submit_solve", "music_poll", "music_wait", "music_release", "music_result_state")}
+
+
+def test_library_does_not_contain_the_oracle(lib):
+    L, path = lib
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    assert "or_spatial_operator" not in out and "or_newton_step" not in out
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_1610_10053_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", txt, flags=re.M), f
+                assert "liboracle" not in txt and "music_oracle" not in txt, f
+
+
+def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
+    """Argument validation happens before any device call."""
+    from paper_1610_10053_gb300 import binding
+    L = binding.load()
+    d = binding.GridDesc()
+    d.ndim = 4
+    h = ctypes.c_void_p()
+    assert L.music_create_grid(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert "ndim" in binding.last_error()
+    assert L.music_create_grid(None, ctypes.byref(h)) == 1
+    assert L.music_destroy_grid(None) == 0
+    assert L.music_state_size(None) == 0

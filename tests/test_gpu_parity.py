@@ -1,0 +1,246 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (derivation in the design notes):
+  * R(U), F(U) and M^-1 r in FP64: 1e-12 relative per element, relative to
+    the element plus the plane's mean magnitude (cancellation between
+    O(plane) flux terms is what leaves a small element);
+  * finite-difference Jv: rounding of R is amplified by dt/(2 eps); with an
+    explicit eps of 1e-5 |U| per |v| the FP64 result matches to 1e-9, and
+    with the default eps (about 1e-8 relative) to 1e-6 in norm;
+  * whole implicit steps in FP64: state and diagnostics to 1e-9 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1610_10053_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def B():
+    from paper_1610_10053_gb300 import binding
+    return binding
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+CASES = {
+    "periodic2d_ragged": lambda: I.random_smooth(2, (37, 29), seed=21, amp=0.4),
+    "walls_hse2d": lambda: I.random_smooth(2, (33, 20), seed=22, amp=0.3,
+                                           bc=(I.BC_PERIODIC, I.BC_WALL, I.BC_PERIODIC),
+                                           wall_scalar=(0, I.WALL_HSE, 0), g=(0.0, -0.4, 0.0)),
+    "walls_mirror_x": lambda: I.random_smooth(2, (21, 18), seed=23, amp=0.3,
+                                              bc=(I.BC_WALL, I.BC_PERIODIC, I.BC_PERIODIC),
+                                              g=(0.2, 0.0, 0.0)),
+    "rt_64x192": lambda: I.rayleigh_taylor(),
+    "kh_64": lambda: I.kelvin_helmholtz(n=64),
+    "periodic3d_ragged": lambda: I.random_smooth(3, (13, 11, 9), seed=24, amp=0.4),
+    "tgv_16": lambda: I.taylor_green(n=16),
+}
+
+
+def planewise_close(prob, got, ref, rtol, extra=None):
+    N = prob.ncells
+    worst = 0.0
+    for v in range(prob.nvars):
+        s = slice(v * N, (v + 1) * N)
+        scale = np.abs(ref[s]).mean() + (0.0 if extra is None else np.abs(extra[s]).mean())
+        err = np.abs(got[s] - ref[s]) / (np.abs(ref[s]) + scale + 1e-300)
+        worst = max(worst, err.max())
+    assert worst <= rtol, worst
+    return worst
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_spatial_operator(case):
+    p = CASES[case]()
+    with B().Grid(p) as g:
+        R = host(g.spatial_operator(dev(p.U)))
+    ref = O.spatial_operator(p, p.U)
+    planewise_close(p, R, ref, 1e-12)
+    # wall faces carry exactly zero
+    N = p.ncells
+    for d in range(p.nd):
+        if p.bc[d] == I.BC_WALL:
+            m = R[(2 + d) * N:(3 + d) * N].reshape(p.n[2], p.n[1], p.n[0])
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            assert np.all(m[tuple(sl)] == 0.0)
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "rt_64x192", "periodic3d_ragged"])
+def test_cn_residual(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(5)
+    U = p.U * (1 + 1e-3 * rng.standard_normal(p.U.size))
+    N = p.ncells
+    for d in range(p.nd):
+        if p.bc[d] == I.BC_WALL:
+            m = U[(2 + d) * N:(3 + d) * N].reshape(p.n[2], p.n[1], p.n[0])
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            m[tuple(sl)] = 0.0
+    dt = O.cfl_dt(p, p.U, 3.0)
+    with B().Grid(p) as g:
+        F = host(g.residual(dev(U), dev(p.U), dt))
+    ref = O.cn_residual(p, U, p.U, dt)
+    planewise_close(p, F, ref, 1e-12, extra=U)
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "periodic3d_ragged"])
+def test_jv_fixed_eps(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(6)
+    v = rng.standard_normal(p.U.size)
+    dt = O.cfl_dt(p, p.U, 3.0)
+    eps = 1e-5 * np.linalg.norm(p.U) / np.linalg.norm(v)
+    with B().Grid(p) as g:
+        Jv = host(g.jv(dev(p.U), dev(v), dt, eps))
+    ref = O.jv(p, p.U, v, dt, eps)
+    assert np.abs(Jv - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "periodic3d_ragged"])
+def test_jv_default_eps(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(p.U.size)
+    dt = O.cfl_dt(p, p.U, 3.0)
+    with B().Grid(p) as g:
+        Jv = host(g.jv(dev(p.U), dev(v), dt))
+    ref = O.jv(p, p.U, v, dt)
+    assert np.linalg.norm(Jv - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "rt_64x192", "periodic3d_ragged"])
+def test_precond_fp64(case):
+    p = CASES[case]()
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal(p.U.size)
+    dt = O.cfl_dt(p, p.U, 5.0)
+    with B().Grid(p) as g:
+        z = host(g.precond(dev(p.U), dt, dev(r)))
+    ref = O.precond(p, p.U, dt, r)
+    planewise_close(p, z, ref, 1e-12, extra=r)
+
+
+def test_precond_mixed_fp32():
+    p = CASES["walls_hse2d"]()
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(p.U.size)
+    dt = O.cfl_dt(p, p.U, 5.0)
+    with B().Grid(p, precision=B().MIXED) as g:
+        z = host(g.precond(dev(p.U), dt, dev(r, torch.float32)))
+    ref = O.precond(p, p.U, dt, r)
+    assert np.linalg.norm(z - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.mark.parametrize("case,nsteps", [("rt_64x192", 10), ("kh_64", 3), ("walls_hse2d", 3), ("tgv_16", 2)])
+def test_implicit_steps_fp64(case, nsteps):
+    p = CASES[case]().with_options(nsteps=nsteps)
+    if case in ("walls_hse2d",):
+        p = p.with_options(cfl=3.0)
+    Uref, sref = O.run(p)
+    dref = O.diagnostics(p, Uref)
+    with B().Grid(p) as g:
+        g.set_state(p.U)
+        st = g.run()
+        U = g.get_state()
+        d = g.diagnostics()
+    for a, b in zip(st, sref):
+        assert a["newton_its"] == b["newton_its"]
+        assert abs(a["gmres_its"] - b["gmres_its"]) <= 1
+        assert _rel(a["dt"], b["dt"]) <= 1e-9
+    N = p.ncells
+    for v in range(p.nvars):
+        s = slice(v * N, (v + 1) * N)
+        scale = np.abs(Uref[s]).max() + 1e-300
+        assert np.abs(U[s] - Uref[s]).max() <= 1e-9 * scale, v
+    for k in dref:
+        assert abs(d[k] - dref[k]) <= 1e-9 * max(abs(dref[k]), 1e-12), k
+
+
+def test_rt_mirror_symmetry_gpu():
+    """Sec. 3: the GPU path keeps the exact x -> -x symmetry of the RT run."""
+    p = CASES["rt_64x192"]().with_options(nsteps=3)
+    with B().Grid(p) as g:
+        g.set_state(p.U)
+        g.run()
+        U = g.get_state()
+    N, nx = p.ncells, p.n[0]
+    rho, E, mx, my = [U[v * N:(v + 1) * N].reshape(p.n[1], nx) for v in range(4)]
+    idx = (nx - np.arange(nx)) % nx
+    assert np.abs(rho - rho[:, ::-1]).max() <= 1e-15 * 2
+    assert np.abs(mx + mx[:, idx]).max() <= 1e-15
+
+
+def test_mixed_precision_diagnostics_rt():
+    """Mixed path (FP32 Krylov and preconditioner): diagnostics of the RT run
+    against the FP64 oracle."""
+    p = CASES["rt_64x192"]()
+    Uref, _ = O.run(p)
+    dref = O.diagnostics(p, Uref)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        g.run()
+        d = g.diagnostics()
+    for k in dref:
+        assert abs(d[k] - dref[k]) <= 1e-7 * max(abs(dref[k]), 1e-12), (k, d[k], dref[k])
+
+
+def test_diagnostics_kernel():
+    p = I.taylor_green(n=16)
+    with B().Grid(p) as g:
+        g.set_state(p.U)
+        d = g.diagnostics()
+    ref = O.diagnostics(p, p.U)
+    for k in ref:
+        assert abs(d[k] - ref[k]) <= 1e-13 * max(abs(ref[k]), 1e-12), k
+
+
+def test_invalid_sizes_rejected():
+    p = I.random_smooth(2, (3, 8), seed=1)
+    with pytest.raises(B().MusicError):
+        B().Grid(p)
+
+
+def test_full_size_kh_residual():
+    """KH 512^2 (the benchmark grid): whole residual against the oracle."""
+    p = I.kelvin_helmholtz(n=512)
+    rng = np.random.default_rng(10)
+    U = p.U * (1 + 1e-4 * rng.standard_normal(p.U.size))
+    dt = O.cfl_dt(p, p.U, 10.0)
+    with B().Grid(p, precision=B().MIXED) as g:
+        F = host(g.residual(dev(U), dev(p.U), dt))
+    ref = O.cn_residual(p, U, p.U, dt)
+    planewise_close(p, F, ref, 1e-12, extra=U)
+
+
+def test_tgv256_residual_by_periodic_tiling():
+    """256^3: a state periodic with period 32 cells must give the oracle's
+    residual of one 32^3 period, tiled (R is local)."""
+    base = I.random_smooth(3, (32, 32, 32), seed=25, amp=0.3, length=(1.0, 1.0, 1.0))
+    Rb = O.spatial_operator(base, base.U)
+    nv, N = base.nvars, base.ncells
+    tile = lambda a: np.tile(a.reshape(32, 32, 32), (8, 8, 8)).reshape(-1)
+    U = np.concatenate([tile(base.U[v * N:(v + 1) * N]) for v in range(nv)])
+    Rt = np.concatenate([tile(Rb[v * N:(v + 1) * N]) for v in range(nv)])
+    big = base.with_options(n=(256, 256, 256), length=(8.0, 8.0, 8.0)).with_state(U)
+    with B().Grid(big, precision=B().MIXED) as g:
+        R = host(g.spatial_operator(dev(U)))
+    planewise_close(big, R, Rt, 1e-12)

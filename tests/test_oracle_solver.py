@@ -175,3 +175,26 @@ def test_newton_converged_state_solves_cn_system():
     assert rc == 0 and st["max_drho"] <= 1e-8 and st["newton_its"] >= 2
     F = O.cn_residual(p, U1, p.U, dt)
     assert np.linalg.norm(F) <= 1e-6 * np.linalg.norm(O.cn_residual(p, p.U, p.U, dt))
+
+
+def test_rt_linear_growth_rate():
+    """Sec. 3: Atwood number 1/3, g = 0.1 and the k = 4 pi mode give the
+    linear Rayleigh-Taylor growth rate sqrt(A g k) = 0.647; a small-amplitude
+    run of the oracle reaches it within 15 % once the seeding transient has
+    passed (finite depth, compressibility and numerical diffusion lower it
+    slightly)."""
+    p = I.rayleigh_taylor(nx=32, ny=96)
+    N = p.ncells
+    U = p.U.copy()
+    U[3 * N:] *= 1e-3
+    t, ts, vs = 0.0, [], []
+    while t < 7.0:
+        U, st = O.run(p, U=U, nsteps=1, cfl=2.0)
+        t += st[0]["dt"]
+        ts.append(t)
+        vs.append(np.abs(U[3 * N:]).max())
+    ts, vs = np.array(ts), np.array(vs)
+    m = (ts >= 5.0) & (ts <= 7.0)
+    sigma = np.polyfit(ts[m], np.log(vs[m]), 1)[0]
+    expect = np.sqrt((1.0 / 3.0) * 0.1 * 4 * np.pi)
+    assert abs(sigma - expect) <= 0.15 * expect, sigma
