@@ -105,9 +105,21 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(rank: int):
+WORKLOADS = {
+    "kh512": ("Kelvin-Helmholtz 2-D, 512x512 periodic, CFL 10, Newton tol 1e-8, GMRES(30)",
+              lambda I, r: I.kelvin_helmholtz(n=512, seed=2 + r)),
+    "kh2048": ("Kelvin-Helmholtz 2-D, 2048x2048 periodic, CFL 10, Newton tol 1e-8, GMRES(30)",
+               lambda I, r: I.kelvin_helmholtz(n=2048, seed=2 + r)),
+    "rt64x192": ("Rayleigh-Taylor 2-D, 64x192, CFL 5, Newton tol 1e-8, GMRES(30)",
+                 lambda I, r: I.rayleigh_taylor()),
+    "tgv128": ("Taylor-Green vortex 3-D, 128^3 periodic, CFL 20, Newton tol 1e-8, GMRES(30)",
+               lambda I, r: I.taylor_green(n=128)),
+}
+
+
+def workload(name: str, rank: int):
     from paper_1610_10053_gb300 import inputs as I
-    return I.kelvin_helmholtz(n=512, seed=2 + rank)
+    return WORKLOADS[name][1](I, rank)
 
 
 def time_steps(grid, steps, stream, flush):
@@ -137,7 +149,7 @@ def run_music(args):
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl")
-    prob = workload(rank)
+    prob = workload(args.workload, rank)
     N = prob.ncells
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -202,7 +214,7 @@ def run_music(args):
         "vs_baseline": None,
         "dtype": "f64 residual + f32 Krylov (mixed)",
         "data": "synthetic",
-        "config": {"workload": "Kelvin-Helmholtz 2-D, 512x512 periodic, CFL 10, Newton tol 1e-8, GMRES(30)",
+        "config": {"workload": WORKLOADS[args.workload][0],
                    "cells": N, "precision": "mixed", "l2": "flushed (512 MiB write) between timed steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "fp64_value": fp64_value,
@@ -323,6 +335,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="music", choices=["music", "reference"])
+    ap.add_argument("--workload", default="kh512", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -211,6 +211,14 @@ int music_create_grid(const music_grid_desc *desc, music_grid **out)
     g->desc = d;
     g->P = make_params(d);
     g->mixed = (d.precision == MUSIC_MIXED);
+    {
+        // MUSIC_STENCIL=multipass selects the multi-pass stencil on 2-D grids
+        const char *sv = getenv("MUSIC_STENCIL");
+        g->stencil_variant = (sv && strcmp(sv, "multipass") == 0) ? STENCIL_MULTIPASS : STENCIL_AUTO;
+        // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep
+        const char *pv = getenv("MUSIC_PRECOND");
+        g->pc_variant = (pv && strcmp(pv, "multikernel") == 0) ? PC_MULTIKERNEL : PC_AUTO;
+    }
     CUDA_TRY(cudaGetDevice(&g->device));
     const GridParams &P = g->P;
     g->n = (size_t)P.nv * P.N;

@@ -21,8 +21,13 @@ struct ExtScratch {
     double *su[3][3], *Psi[3][3];
 };
 
+enum StencilVariant { STENCIL_AUTO = 0, STENCIL_FUSED = 1, STENCIL_MULTIPASS = 2 };
+enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
+
 struct music_grid {
     music_grid_desc desc;
+    int stencil_variant;  // STENCIL_*: fused shared-memory kernel (2-D) or multi-pass
+    int pc_variant;       // PC_*: fused 2-D preconditioner kernel or one kernel per sweep
     GridParams P;
     int mixed;
     int device;
@@ -77,6 +82,8 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
 // ----- krylov.cu -----
 // sum of squares of x (n elements) -> *dst (device), deterministic
 int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s);
+// *dst = sum of g->partials[0..count) in order (second stage of a reduction)
+int final_sum(music_grid *g, int count, double *dst, cudaStream_t s);
 // eps = sqrt(2^-52) (1 + sqrt(unorm2)) / sqrt(vnorm2), or the fixed value if > 0
 int dev_set_eps(music_grid *g, double fixed, cudaStream_t s);
 int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s);          // h = V[0..j]^T w

@@ -193,6 +193,133 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
 }
 
+
+// ---- mixed precision: FP32 basis, FP32 arithmetic inside a 4-element chunk
+// (float4 loads), FP64 accumulation across chunks and in the reductions.
+__device__ inline float dot4(const float4 a, const float4 b)
+{
+    float s = a.x * b.x;
+    s = fmaf(a.y, b.y, s);
+    s = fmaf(a.z, b.z, s);
+    return fmaf(a.w, b.w, s);
+}
+
+template <int NVM>
+__global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
+                                                 double *partial, int nb)
+{
+    __shared__ double sh[BS / 32];
+    double acc[NVM];
+#pragma unroll
+    for (int i = 0; i < NVM; i++) acc[i] = 0.0;
+    // float4 path only when every basis vector starts 16-byte aligned
+    const long long n4 = (n & 3) ? 0 : (n >> 2);
+    const long long stride = (long long)gridDim.x * BS;
+    const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    for (long long e = t0; e < n4; e += stride) {
+        const float4 we = reinterpret_cast<const float4 *>(w)[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++)
+            if (i <= j) acc[i] += (double)dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+    }
+    for (long long e = 4 * n4 + t0; e < n; e += stride) {
+        const float we = w[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++)
+            if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
+    }
+#pragma unroll
+    for (int i = 0; i < NVM; i++) {
+        if (i <= j) {
+            const double r = block_sum<BS>(acc[i], sh);
+            if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+        }
+    }
+}
+
+template <int NVM, bool NORM>
+__global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
+                                                   double *partial, int nb)
+{
+    __shared__ double sh[BS / 32];
+    __shared__ float hs[MUSIC_MAXV];
+    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (float)h[i];
+    __syncthreads();
+    double acc[NORM ? 1 : NVM];
+#pragma unroll
+    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] = 0.0;
+    // float4 path only when every basis vector starts 16-byte aligned
+    const long long n4 = (n & 3) ? 0 : (n >> 2);
+    const long long stride = (long long)gridDim.x * BS;
+    const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    for (long long e = t0; e < n4; e += stride) {
+        float4 we = reinterpret_cast<const float4 *>(w)[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++) {
+            if (i <= j) {
+                const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
+                const float c = -hs[i];
+                we.x = fmaf(c, v.x, we.x);
+                we.y = fmaf(c, v.y, we.y);
+                we.z = fmaf(c, v.z, we.z);
+                we.w = fmaf(c, v.w, we.w);
+            }
+        }
+        reinterpret_cast<float4 *>(w)[e] = we;
+        if (NORM) {
+            acc[0] += (double)dot4(we, we);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NVM; i++)
+                if (i <= j) acc[i] += (double)dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+        }
+    }
+    for (long long e = 4 * n4 + t0; e < n; e += stride) {
+        float we = w[e];
+#pragma unroll
+        for (int i = 0; i < NVM; i++)
+            if (i <= j) we = fmaf(-hs[i], V[(long long)i * n + e], we);
+        w[e] = we;
+        if (NORM) {
+            acc[0] += (double)(we * we);
+        } else {
+#pragma unroll
+            for (int i = 0; i < NVM; i++)
+                if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
+        }
+    }
+    if (NORM) {
+        const double r = block_sum<BS>(acc[0], sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+            if (i <= j) {
+                const double r = block_sum<BS>(acc[i], sh);
+                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, long long n, int k, Coef y)
+{
+    __shared__ float ys[MUSIC_MAXV];
+    for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)y.c[i];
+    __syncthreads();
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        float s = 0.0f;
+        for (int i = 0; i < k; i++) s = fmaf(ys[i], V[(long long)i * n + e], s);
+        u[e] = s;
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_scale_f32(const float *w, float *dst, long long n, float inv)
+{
+    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+        dst[e] = w[e] * inv;
+}
+
 int grid_blocks(long long n, int cap)
 {
     long long b = (n + BS - 1) / BS;
@@ -206,7 +333,7 @@ int launch_dots(music_grid *g, int j, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     if (g->mixed)
-        k_dots<NVM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb);
+        k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb);
     else
         k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
                                                  g->nb);
@@ -219,8 +346,8 @@ int launch_update(music_grid *g, int j, const double *h, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     if (g->mixed)
-        k_update<NVM, NORM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
-                                                        g->nb);
+        k_update_f32<NVM, NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
+                                                      g->nb);
     else
         k_update<NVM, NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h,
                                                          g->partials, g->nb);
@@ -238,6 +365,13 @@ int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst
         k_sumsq<float><<<g->nb, BS, 0, s>>>((const float *)x, (long long)n, g->partials);
     CHECK_LAUNCH();
     k_final_sum<<<1, BS, 0, s>>>(g->partials, g->nb, dst);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int final_sum(music_grid *g, int count, double *dst, cudaStream_t s)
+{
+    k_final_sum<<<1, BS, 0, s>>>(g->partials, count, dst);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -301,7 +435,7 @@ int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
-        k_scale_into<float><<<nb, BS, 0, s>>>((const float *)g->w, (float *)g->V + (long long)(j + 1) * n, n, inv);
+        k_scale_f32<<<nb, BS, 0, s>>>((const float *)g->w, (float *)g->V + (long long)(j + 1) * n, n, (float)inv);
     else
         k_scale_into<double><<<nb, BS, 0, s>>>((const double *)g->w, (double *)g->V + (long long)(j + 1) * n, n,
                                               inv);
@@ -329,7 +463,7 @@ int krylov_combine(music_grid *g, int k, const double *y, cudaStream_t s)
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
-        k_combine<float><<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c);
+        k_combine_f32<<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c);
     else
         k_combine<double><<<nb, BS, 0, s>>>((const double *)g->V, (double *)g->u, n, k, c);
     CHECK_LAUNCH();

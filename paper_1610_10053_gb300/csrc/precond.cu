@@ -210,6 +210,160 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     return MUSIC_OK;
 }
 
+
+// ---------------------------------------------------------------- fused 2-D
+// The whole application z = M^-1 r in one kernel on 2-D grids: a CTA owns a
+// TX x TY tile and stages the frozen coefficients and r on the tile plus a
+// halo of H = K + 1 cells (K sweeps).  The right-hand side, the K Jacobi
+// sweeps (each valid on a region one cell narrower than the last) and the
+// back substitution all run in shared memory, so r is read and z written
+// once; the block's share of |z|^2 goes to `partial`.  Values equal the
+// sweep-by-sweep global iterates, since every tile point used lies at least
+// K cells inside the staged region.
+constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 12;
+
+template <typename PT>
+__device__ inline long long pc_map(const GridParams &P, int gx, int gy, bool &inside_x, bool &inside_y)
+{
+    // periodic directions wrap; wall directions clamp (their faces outside
+    // the domain get a zero coefficient, which decouples the clamped cells)
+    const int n0 = P.n[0], n1 = P.n[1];
+    int x = gx, y = gy;
+    inside_x = inside_y = true;
+    if (P.bc[0] == MUSIC_BC_PERIODIC)
+        x = (x % n0 + n0) % n0;
+    else {
+        inside_x = (gx > 0 && gx < n0);
+        x = min(max(x, 0), n0 - 1);
+    }
+    if (P.bc[1] == MUSIC_BC_PERIODIC)
+        y = (y % n1 + n1) % n1;
+    else {
+        inside_y = (gy > 0 && gy < n1);
+        y = min(max(y, 0), n1 - 1);
+    }
+    return x + (long long)n0 * y;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z,
+                                                               PT tau, PT tau2, int K, double *partial)
+{
+    constexpr int NT = PTX * PTY;
+    const int H = K + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
+    extern __shared__ unsigned char smraw[];
+    PT *ax = (PT *)smraw, *ay = ax + R, *D = ay + R, *b = D + R, *dA = b + R, *dB = dA + R;
+    __shared__ double red[NT / 32];
+    const int i0 = blockIdx.x * PTX - H, j0 = blockIdx.y * PTY - H;
+    const int tid = threadIdx.x;
+    const long long N = P.N;
+    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    const PT ix0 = (PT)P.idx[0], ix1 = (PT)P.idx[1];
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        bool inx, iny;
+        const long long c = pc_map<PT>(P, i0 + lx, j0 + ly, inx, iny);
+        ax[q] = inx ? C.a[0][c] : (PT)0;
+        ay[q] = iny ? C.a[1][c] : (PT)0;
+        D[q] = C.D[c];
+    }
+    __syncthreads();
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        if (lx >= RX - 1 || ly >= RY - 1) continue;
+        bool inx, iny;
+        const long long c = pc_map<PT>(P, i0 + lx, j0 + ly, inx, iny);
+        const long long cx = pc_map<PT>(P, i0 + lx + 1, j0 + ly, inx, iny);
+        const long long cy = pc_map<PT>(P, i0 + lx, j0 + ly + 1, inx, iny);
+        PT divm = (ax[q + 1] * r[2 * N + cx] - ax[q] * r[2 * N + c]) * ix0;
+        divm += (ay[q + RX] * r[3 * N + cy] - ay[q] * r[3 * N + c]) * ix1;
+        b[q] = (PT)P.gm1 * r[N + c] / C.gp[c] - tau * divm;
+    }
+    __syncthreads();
+    const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
+    PT *src = dA, *dst = dB;
+    for (int k = 0; k < K; k++) {
+        for (int q = tid; q < R; q += NT) {
+            const int lx = q % RX, ly = q / RX;
+            if (lx < k || ly < k || lx >= RX - 1 - k || ly >= RY - 1 - k) continue;
+            if (k == 0) {
+                dst[q] = w * (b[q] / D[q]);
+            } else {
+                PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
+                off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
+                dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) / D[q]);
+            }
+        }
+        __syncthreads();
+        PT *t = src;
+        src = dst;
+        dst = t;
+    }
+    // src holds dp; back substitution on the tile
+    const int tx = tid % PTX, ty = tid / PTX;
+    const int gx = blockIdx.x * PTX + tx, gy = blockIdx.y * PTY + ty;
+    double nrm = 0.0;
+    if (gx < P.n[0] && gy < P.n[1]) {
+        const int q = (ty + H) * RX + (tx + H);
+        const long long c = gx + (long long)P.n[0] * gy;
+        const bool wlx = (P.bc[0] == MUSIC_BC_WALL && gx == 0), wux = (P.bc[0] == MUSIC_BC_WALL && gx == P.n[0] - 1);
+        const bool wly = (P.bc[1] == MUSIC_BC_WALL && gy == 0), wuy = (P.bc[1] == MUSIC_BC_WALL && gy == P.n[1] - 1);
+        const long long cxp = (gx + 1 == P.n[0]) ? c - gx : c + 1;
+        const long long cyp = (gy + 1 == P.n[1]) ? gx : c + P.n[0];
+        const PT dp = (K > 0) ? src[q] : (PT)0;
+        const PT dpxm = (K > 0) ? src[q - 1] : (PT)0, dpxp = (K > 0) ? src[q + 1] : (PT)0;
+        const PT dpym = (K > 0) ? src[q - RX] : (PT)0, dpyp = (K > 0) ? src[q + RX] : (PT)0;
+        const PT mx_own = wlx ? r[2 * N + c] : r[2 * N + c] - tau * (dp - dpxm) * ix0;
+        const PT my_own = wly ? r[3 * N + c] : r[3 * N + c] - tau * (dp - dpym) * ix1;
+        const PT mxp = wux ? (PT)0 : r[2 * N + cxp] - tau * (dpxp - dp) * ix0;
+        const PT myp = wuy ? (PT)0 : r[3 * N + cyp] - tau * (dpyp - dp) * ix1;
+        const PT mxm = wlx ? (PT)0 : mx_own, mym = wly ? (PT)0 : my_own;
+        PT divm = (mxp - mxm) * ix0;
+        divm += (myp - mym) * ix1;
+        PT divu = (ax[q + 1] * mxp - ax[q] * mxm) * ix0;
+        divu += (ay[q + RX] * myp - ay[q] * mym) * ix1;
+        const PT zr = r[c] - tau * divm;
+        const PT ze = r[N + c] - tau * C.hp[c] * divu;
+        z[c] = zr;
+        z[N + c] = ze;
+        z[2 * N + c] = mx_own;
+        z[3 * N + c] = my_own;
+        nrm = (double)zr * zr + (double)ze * ze + (double)mx_own * mx_own + (double)my_own * my_own;
+    }
+    if (partial) {
+        const double t = block_sum<NT>(nrm, red);
+        if (tid == 0) partial[blockIdx.x + gridDim.x * blockIdx.y] = t;
+    }
+}
+
+template <typename PT>
+int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    const int K = g->desc.precond_sweeps, H = K + 1;
+    const size_t smem = (size_t)6 * (PTX + 2 * H) * (PTY + 2 * H) * sizeof(PT);
+    static bool attr = false;
+    if (!attr) {
+        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(6 * (PTX + 2 * (PC_FUSED_MAXK + 1)) * (PTY + 2 * (PC_FUSED_MAXK + 1)) *
+                                            sizeof(PT))));
+        attr = true;
+    }
+    const double tau = 0.5 * dt;
+    dim3 grid((P.n[0] + PTX - 1) / PTX, (P.n[1] + PTY - 1) / PTY);
+    const int nblk = grid.x * grid.y;
+    double *part = (want_norm && nblk <= MUSIC_MAXV * g->nb) ? g->partials : nullptr;
+    k_precond_fused2d<PT><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau), K, part);
+    CHECK_LAUNCH();
+    if (want_norm) {
+        if (part)
+            TRY(final_sum(g, nblk, &g->ds->vnorm2, s));
+        else
+            TRY(dev_norm2(g, z, sizeof(PT) == 8, g->n, &g->ds->vnorm2, s));
+    }
+    return MUSIC_OK;
+}
+
 }  // namespace
 
 int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
@@ -224,6 +378,10 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
     if (g->desc.precond == MUSIC_PC_NONE) {
         const size_t es = g->mixed ? sizeof(float) : sizeof(double);
         if (r != z) CUDA_TRY(cudaMemcpyAsync(z, r, n * es, cudaMemcpyDeviceToDevice, s));
+    } else if (g->P.nd == 2 && g->desc.precond_sweeps <= PC_FUSED_MAXK && g->pc_variant != PC_MULTIKERNEL) {
+        if (g->mixed)
+            return apply_fused2d<float>(g, dt, (const float *)r, (float *)z, want_norm, s);
+        return apply_fused2d<double>(g, dt, (const double *)r, (double *)z, want_norm, s);
     } else if (g->mixed) {
         TRY(apply_t<float>(g, dt, (const float *)r, (float *)z, s));
     } else {

@@ -21,12 +21,12 @@ constexpr int BS = 256;
 template <typename VT>
 struct WLoad {
     const double *U;
-    const VT *v;
-    const double *eps;  // device scalar (Jv) or null
+    const VT *v;        // Jv direction or null
+    double eps;         // finite-difference step (Jv only)
     __device__ inline double operator()(long long i) const
     {
         double u = U[i];
-        if (v) u = u + (*eps) * (double)v[i];
+        if (v) u = u + eps * (double)v[i];
         return u;
     }
 };
@@ -43,7 +43,10 @@ __device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[
     int j[3] = {ix[0], ix[1], ix[2]};
     int hd = -1, lower = 0;
     for (int d = 0; d < P.nd; d++) {
-        const int a = j[d], n = P.n[d];
+        const int n = P.n[d];
+        // tile halos of ragged edges may lie beyond the ghost layers; their
+        // values are never used, so clamp wall directions into the ghost range
+        const int a = (P.bc[d] == MUSIC_BC_WALL) ? min(max(j[d], -MUSIC_GHOST), n - 1 + MUSIC_GHOST) : j[d];
         if (a >= 0 && a < n) continue;
         if (P.bc[d] == MUSIC_BC_PERIODIC)
             j[d] = (a % n + n) % n;
@@ -81,7 +84,9 @@ __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const i
     int j[3] = {ix[0], ix[1], ix[2]};
     double sgn = 1.0;
     for (int w = 0; w < P.nd; w++) {
-        const int a = j[w], n = P.n[w];
+        const int n = P.n[w];
+        const int a = (P.bc[w] == MUSIC_BC_WALL) ? min(max(j[w], -MUSIC_GHOST), n - 1 + MUSIC_GHOST) : j[w];
+        j[w] = a;
         if (a >= 0 && a < n) continue;
         if (P.bc[w] == MUSIC_BC_PERIODIC) {
             j[w] = (a % n + n) % n;
@@ -103,8 +108,10 @@ __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const i
 }
 
 template <typename VT>
-__global__ void __launch_bounds__(BS) k_load(GridParams P, WLoad<VT> W, ExtScratch X)
+__global__ void __launch_bounds__(BS) k_load(GridParams P, const double *U, const VT *v, const double *eps,
+                                             ExtScratch X)
 {
+    const WLoad<VT> W{U, v, v ? *eps : 0.0};
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -242,6 +249,223 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
     }
 }
 
+
+// ---------------------------------------------------------------- fused 2-D
+// One kernel per evaluation of R on 2-D grids.  A CTA owns a TX x TY tile of
+// cells and stages the tile plus a halo of 3 cells below / 2 above in shared
+// memory (RX x RY points, x fastest).  Each phase computes one family of
+// intermediate values once per point of the region it is needed on:
+//   1 ghost-mapped rho, e, p and face velocities u, v (global loads, L1/L2)
+//   2 van Leer slopes of rho, e, u, v along x and y
+//   3 upwind mass and energy fluxes on x- and y-faces
+//   4 momentum fluxes: centres (Phi) and corners (Psi)
+//   5 the residuals of the tile's cells, written per mode (coalesced in x).
+template <int TX, int TY>
+struct Tile2D {
+    static constexpr int RX = TX + 5, RY = TY + 5, R = RX * RY, NARR = 17;
+    static constexpr size_t SMEM = (size_t)NARR * R * sizeof(double);
+};
+
+template <int MODE, typename VIN, typename VOUT, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
+                                                    const VIN *v, VOUT *out, double *RU_out, double hdt,
+                                                    double sign, const double *eps)
+{
+    using TL = Tile2D<TX, TY>;
+    constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
+    extern __shared__ double sm[];
+    double *rho = sm, *ee = sm + R, *pp = sm + 2 * R, *uu = sm + 3 * R, *vv = sm + 4 * R;
+    double *srx = sm + 5 * R, *sry = sm + 6 * R, *sex = sm + 7 * R, *sey = sm + 8 * R;
+    double *sux = sm + 9 * R, *suy = sm + 10 * R, *svx = sm + 11 * R, *svy = sm + 12 * R;
+    double *Frx = sm + 13 * R, *Fry = sm + 14 * R, *FEx = sm + 15 * R, *FEy = sm + 16 * R;
+    // scalar slopes are dead after phase 3: their planes hold the momentum fluxes
+    double *Phx = srx, *Phy = sry, *Psxy = sex, *Psyx = sey;
+    const int i0 = blockIdx.x * TX - 3, j0 = blockIdx.y * TY - 3;
+    const int tid = threadIdx.x;
+    const double epsv = (MODE == SM_JV) ? *eps : 0.0;
+    const WLoad<VIN> W{U, (MODE == SM_JV) ? v : nullptr, epsv};
+
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        double r, E;
+        load_cell(P, W, ix, r, E);
+        rho[q] = r;
+        ee[q] = E / r;
+        pp[q] = P.gm1 * E;
+        uu[q] = face_velocity(P, W, ix, 0);
+        vv[q] = face_velocity(P, W, ix, 1);
+    }
+    __syncthreads();
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        if (lx >= 1 && lx < RX - 1) {
+            srx[q] = vanleer(rho[q] - rho[q - 1], rho[q + 1] - rho[q]);
+            sex[q] = vanleer(ee[q] - ee[q - 1], ee[q + 1] - ee[q]);
+            sux[q] = vanleer(uu[q] - uu[q - 1], uu[q + 1] - uu[q]);
+            svx[q] = vanleer(vv[q] - vv[q - 1], vv[q + 1] - vv[q]);
+        }
+        if (ly >= 1 && ly < RY - 1) {
+            sry[q] = vanleer(rho[q] - rho[q - RX], rho[q + RX] - rho[q]);
+            sey[q] = vanleer(ee[q] - ee[q - RX], ee[q + RX] - ee[q]);
+            suy[q] = vanleer(uu[q] - uu[q - RX], uu[q + RX] - uu[q]);
+            svy[q] = vanleer(vv[q] - vv[q - RX], vv[q + RX] - vv[q]);
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        if (lx >= 2 && lx < RX - 1) {
+            const double u = uu[q];
+            double rs, es;
+            if (u >= 0.0) {
+                rs = rho[q - 1] + 0.5 * srx[q - 1];
+                es = ee[q - 1] + 0.5 * sex[q - 1];
+            } else {
+                rs = rho[q] - 0.5 * srx[q];
+                es = ee[q] - 0.5 * sex[q];
+            }
+            const double fr = u * rs;
+            Frx[q] = fr;
+            FEx[q] = fr * es;
+        }
+        if (ly >= 2 && ly < RY - 1) {
+            const double u = vv[q];
+            double rs, es;
+            if (u >= 0.0) {
+                rs = rho[q - RX] + 0.5 * sry[q - RX];
+                es = ee[q - RX] + 0.5 * sey[q - RX];
+            } else {
+                rs = rho[q] - 0.5 * sry[q];
+                es = ee[q] - 0.5 * sey[q];
+            }
+            const double fr = u * rs;
+            Fry[q] = fr;
+            FEy[q] = fr * es;
+        }
+    }
+    __syncthreads();
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        if (lx >= 2 && lx < RX - 2) {
+            const double fm = 0.5 * (Frx[q] + Frx[q + 1]);
+            const double us = (fm >= 0.0) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
+            Phx[q] = fm * us;
+        }
+        if (ly >= 2 && ly < RY - 2) {
+            const double fm = 0.5 * (Fry[q] + Fry[q + RX]);
+            const double us = (fm >= 0.0) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
+            Phy[q] = fm * us;
+        }
+        if (lx >= 1 && ly >= 2 && ly < RY - 1) {
+            const double fm = 0.5 * (Fry[q - 1] + Fry[q]);
+            const double us = (fm >= 0.0) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
+            Psxy[q] = fm * us;
+        }
+        if (ly >= 1 && lx >= 2 && lx < RX - 1) {
+            const double fm = 0.5 * (Frx[q - RX] + Frx[q]);
+            const double us = (fm >= 0.0) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
+            Psyx[q] = fm * us;
+        }
+    }
+    __syncthreads();
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx = blockIdx.x * TX + tx, gy = blockIdx.y * TY + ty;
+    if (gx >= P.n[0] || gy >= P.n[1]) return;
+    const int q = (ty + 3) * RX + (tx + 3);
+    const double ix0 = P.idx[0], ix1 = P.idx[1];
+    double Rv[4];
+    {
+        double accr = (Frx[q + 1] - Frx[q]) * ix0;
+        accr += (Fry[q + RX] - Fry[q]) * ix1;
+        double acce = (FEx[q + 1] - FEx[q]) * ix0;
+        acce += (FEy[q + RX] - FEy[q]) * ix1;
+        double divu = (uu[q + 1] - uu[q]) * ix0;
+        divu += (vv[q + RX] - vv[q]) * ix1;
+        Rv[0] = -accr;
+        Rv[1] = -acce - pp[q] * divu;
+    }
+    if (P.bc[0] == MUSIC_BC_WALL && gx == 0) {
+        Rv[2] = 0.0;
+    } else {
+        double acc = (Phx[q] - Phx[q - 1]) * ix0;
+        acc += (Psxy[q + RX] - Psxy[q]) * ix1;
+        const double rbar = 0.5 * (rho[q - 1] + rho[q]);
+        Rv[2] = (-acc - (pp[q] - pp[q - 1]) * ix0) + rbar * P.g[0];
+    }
+    if (P.bc[1] == MUSIC_BC_WALL && gy == 0) {
+        Rv[3] = 0.0;
+    } else {
+        double acc = (Psyx[q + 1] - Psyx[q]) * ix0;
+        acc += (Phy[q] - Phy[q - RX]) * ix1;
+        const double rbar = 0.5 * (rho[q - RX] + rho[q]);
+        Rv[3] = (-acc - (pp[q] - pp[q - RX]) * ix1) + rbar * P.g[1];
+    }
+    const long long c = gx + (long long)P.n[0] * gy;
+    const double c_jv = (MODE == SM_JV && epsv != 0.0) ? hdt / epsv : 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const long long i = (long long)k * P.N + c;
+        if (MODE == SM_R) {
+            out[i] = (VOUT)Rv[k];
+        } else if (MODE == SM_CN) {
+            out[i] = (VOUT)(U[i] + hdt * Rv[k]);
+        } else if (MODE == SM_F) {
+            out[i] = (VOUT)(sign * ((U[i] - aux[i]) - hdt * Rv[k]));
+            if (RU_out) RU_out[i] = Rv[k];
+        } else {
+            out[i] = (epsv == 0.0) ? (VOUT)0 : (VOUT)((double)v[i] - c_jv * (Rv[k] - aux[i]));
+        }
+    }
+}
+
+constexpr int FTX = 32, FTY = 8;
+
+template <int MODE, typename VIN, typename VOUT>
+int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN *v, VOUT *out, double *RU_out,
+                   double hdt, double sign, cudaStream_t s)
+{
+    using TL = Tile2D<FTX, FTY>;
+    static bool attr = false;
+    auto kern = k_fused2d<MODE, VIN, VOUT, FTX, FTY>;
+    if (!attr) {
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM));
+        attr = true;
+    }
+    const GridParams &P = g->P;
+    dim3 grid((P.n[0] + FTX - 1) / FTX, (P.n[1] + FTY - 1) / FTY);
+    kern<<<grid, FTX * FTY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int fused2d_apply(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
+                  void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s)
+{
+    switch (mode) {
+    case SM_R:
+        return launch_fused2d<SM_R, double, double>(g, U, aux, nullptr, (double *)out, nullptr, hdt, sign, s);
+    case SM_CN:
+        return launch_fused2d<SM_CN, double, double>(g, U, aux, nullptr, (double *)out, nullptr, hdt, sign, s);
+    case SM_F:
+        return launch_fused2d<SM_F, double, double>(g, U, aux, nullptr, (double *)out, RU_out, hdt, sign, s);
+    case SM_JV:
+        if (vin_double && out_double)
+            return launch_fused2d<SM_JV, double, double>(g, U, aux, (const double *)v, (double *)out, nullptr, hdt,
+                                                         sign, s);
+        if (!vin_double && !out_double)
+            return launch_fused2d<SM_JV, float, float>(g, U, aux, (const float *)v, (float *)out, nullptr, hdt, sign,
+                                                       s);
+        if (vin_double)
+            return launch_fused2d<SM_JV, double, float>(g, U, aux, (const double *)v, (float *)out, nullptr, hdt,
+                                                        sign, s);
+        return launch_fused2d<SM_JV, float, double>(g, U, aux, (const float *)v, (double *)out, nullptr, hdt, sign,
+                                                    s);
+    }
+    set_error("stencil: bad mode %d", mode);
+    return MUSIC_E_INVAL;
+}
+
 int blocks_for(long long n)
 {
     long long b = (n + BS - 1) / BS;
@@ -254,9 +478,8 @@ template <typename VT>
 int run_passes(music_grid *g, const double *U, const VT *v, cudaStream_t s)
 {
     const GridParams &P = g->P;
-    WLoad<VT> W{U, v, v ? &g->ds->eps : nullptr};
     const int nbm = blocks_for(P.M);
-    k_load<VT><<<nbm, BS, 0, s>>>(P, W, g->ext);
+    k_load<VT><<<nbm, BS, 0, s>>>(P, U, v, &g->ds->eps, g->ext);
     CHECK_LAUNCH();
     k_slopes<<<nbm, BS, 0, s>>>(P, g->ext);
     CHECK_LAUNCH();
@@ -275,6 +498,8 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
 {
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
+    if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS)
+        return fused2d_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
     const int nbn = blocks_for(P.N);
     const double *eps = &g->ds->eps;
     if (mode == SM_JV) {

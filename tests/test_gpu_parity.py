@@ -50,13 +50,35 @@ CASES = {
 }
 
 
-def planewise_close(prob, got, ref, rtol, extra=None):
+def term_scales(prob, U):
+    """Per-plane magnitude T_v of the largest terms that R sums (flux
+    differences over dx, pressure gradient, gravity).  Rounding of a sum of
+    such terms is bounded by a few ulp of T_v, whatever R itself is."""
+    N, nd = prob.ncells, prob.nd
+    rho = U[:N]
+    E = U[N:2 * N]
+    gm1 = prob.gamma - 1.0
+    p = gm1 * E
+    e = E / rho
+    m = np.abs(U[2 * N:]).max() if nd else 0.0
+    u = m / rho.min()
+    h = min(prob.dx[d] for d in range(nd))
+    T_rho = m / h
+    T_E = (m * np.abs(e).max() + p.max() * u) / h
+    T_m = (m * u + p.max()) / h + rho.max() * max(abs(x) for x in prob.g)
+    return [T_rho, T_E] + [T_m] * nd
+
+
+def planewise_close(prob, got, ref, rtol, extra=None, U=None):
+    """|got - ref| <= rtol |ref| + 1e-2 rtol T_v per element (T_v from
+    term_scales; `extra` adds a plane of O(1) magnitudes such as U in F)."""
     N = prob.ncells
+    T = term_scales(prob, prob.U if U is None else U)
     worst = 0.0
     for v in range(prob.nvars):
         s = slice(v * N, (v + 1) * N)
-        scale = np.abs(ref[s]).mean() + (0.0 if extra is None else np.abs(extra[s]).mean())
-        err = np.abs(got[s] - ref[s]) / (np.abs(ref[s]) + scale + 1e-300)
+        floor = 1e-2 * T[v] + (0.0 if extra is None else np.abs(extra[s]).max())
+        err = np.abs(got[s] - ref[s]) / (np.abs(ref[s]) + floor + 1e-300)
         worst = max(worst, err.max())
     assert worst <= rtol, worst
     return worst
@@ -95,7 +117,7 @@ def test_cn_residual(case):
     with B().Grid(p) as g:
         F = host(g.residual(dev(U), dev(p.U), dt))
     ref = O.cn_residual(p, U, p.U, dt)
-    planewise_close(p, F, ref, 1e-12, extra=U)
+    planewise_close(p, F, ref, 1e-12, extra=U, U=U)
 
 
 @pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "periodic3d_ragged"])
@@ -150,6 +172,16 @@ def _rel(a, b):
     return abs(a - b) / max(abs(b), 1e-300)
 
 
+# magnitudes below which a diagnostic is rounding noise (cancellation)
+DIAG_FLOOR = {"mixing_height": 1e-6, "max_mach": 1e-6, "kh_mode_amplitude": 1e-8,
+              "vertical_kinetic_energy": 1e-10, "mean_kinetic_energy": 1e-10, "max_speed": 1e-8}
+
+
+def diag_close(d, dref, rtol):
+    for k in dref:
+        assert abs(d[k] - dref[k]) <= rtol * max(abs(dref[k]), DIAG_FLOOR[k]), (k, d[k], dref[k])
+
+
 @pytest.mark.parametrize("case,nsteps", [("rt_64x192", 10), ("kh_64", 3), ("walls_hse2d", 3), ("tgv_16", 2)])
 def test_implicit_steps_fp64(case, nsteps):
     p = CASES[case]().with_options(nsteps=nsteps)
@@ -164,15 +196,15 @@ def test_implicit_steps_fp64(case, nsteps):
         d = g.diagnostics()
     for a, b in zip(st, sref):
         assert a["newton_its"] == b["newton_its"]
-        assert abs(a["gmres_its"] - b["gmres_its"]) <= 1
+        # a linear-tolerance test on the edge may flip by rounding
+        assert abs(a["gmres_its"] - b["gmres_its"]) <= max(1, 0.05 * b["gmres_its"])
         assert _rel(a["dt"], b["dt"]) <= 1e-9
     N = p.ncells
     for v in range(p.nvars):
         s = slice(v * N, (v + 1) * N)
         scale = np.abs(Uref[s]).max() + 1e-300
         assert np.abs(U[s] - Uref[s]).max() <= 1e-9 * scale, v
-    for k in dref:
-        assert abs(d[k] - dref[k]) <= 1e-9 * max(abs(dref[k]), 1e-12), k
+    diag_close(d, dref, 1e-9)
 
 
 def test_rt_mirror_symmetry_gpu():
@@ -199,8 +231,7 @@ def test_mixed_precision_diagnostics_rt():
         g.set_state(p.U)
         g.run()
         d = g.diagnostics()
-    for k in dref:
-        assert abs(d[k] - dref[k]) <= 1e-7 * max(abs(dref[k]), 1e-12), (k, d[k], dref[k])
+    diag_close(d, dref, 1e-7)
 
 
 def test_diagnostics_kernel():
@@ -209,8 +240,7 @@ def test_diagnostics_kernel():
         g.set_state(p.U)
         d = g.diagnostics()
     ref = O.diagnostics(p, p.U)
-    for k in ref:
-        assert abs(d[k] - ref[k]) <= 1e-13 * max(abs(ref[k]), 1e-12), k
+    diag_close(d, ref, 1e-13)
 
 
 def test_invalid_sizes_rejected():
@@ -228,7 +258,7 @@ def test_full_size_kh_residual():
     with B().Grid(p, precision=B().MIXED) as g:
         F = host(g.residual(dev(U), dev(p.U), dt))
     ref = O.cn_residual(p, U, p.U, dt)
-    planewise_close(p, F, ref, 1e-12, extra=U)
+    planewise_close(p, F, ref, 1e-12, extra=U, U=U)
 
 
 def test_tgv256_residual_by_periodic_tiling():
@@ -244,3 +274,48 @@ def test_tgv256_residual_by_periodic_tiling():
     with B().Grid(big, precision=B().MIXED) as g:
         R = host(g.spatial_operator(dev(U)))
     planewise_close(big, R, Rt, 1e-12)
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "walls_mirror_x", "rt_64x192"])
+def test_spatial_operator_multipass_variant(case, monkeypatch):
+    """The generic multi-pass stencil (used for 3-D) on 2-D grids."""
+    monkeypatch.setenv("MUSIC_STENCIL", "multipass")
+    p = CASES[case]()
+    with B().Grid(p) as g:
+        R = host(g.spatial_operator(dev(p.U)))
+    planewise_close(p, R, O.spatial_operator(p, p.U), 1e-12)
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "walls_mirror_x"])
+@pytest.mark.parametrize("variant", ["fused", "multikernel"])
+def test_precond_variants(case, variant, monkeypatch):
+    """Fused tile-resident preconditioner and one-kernel-per-sweep version."""
+    if variant == "multikernel":
+        monkeypatch.setenv("MUSIC_PRECOND", "multikernel")
+    p = CASES[case]()
+    rng = np.random.default_rng(11)
+    r = rng.standard_normal(p.U.size)
+    N = p.ncells
+    for d in range(p.nd):
+        if p.bc[d] == I.BC_WALL:
+            m = r[(2 + d) * N:(3 + d) * N].reshape(p.n[2], p.n[1], p.n[0])
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            m[tuple(sl)] = 0.0
+    dt = O.cfl_dt(p, p.U, 8.0)
+    with B().Grid(p) as g:
+        z = host(g.precond(dev(p.U), dt, dev(r)))
+    planewise_close(p, z, O.precond(p, p.U, dt, r), 1e-12, extra=r)
+
+
+def test_precond_sweep_counts():
+    """0, 1 and 12 sweeps (the fused kernel's halo limit) and 13 (fallback)."""
+    p = CASES["walls_hse2d"]()
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal(p.U.size)
+    dt = O.cfl_dt(p, p.U, 8.0)
+    for K in (1, 12, 13):
+        q = p.with_options(sweeps=K)
+        with B().Grid(q) as g:
+            z = host(g.precond(dev(q.U), dt, dev(r)))
+        planewise_close(q, z, O.precond(q, q.U, dt, r), 1e-12, extra=r)
