@@ -80,11 +80,11 @@ typedef struct {
     /* solver options (0 selects the default in brackets) */
     int gmres_restart;        /* Krylov vectors per cycle [30], 1..63 */
     int gmres_max_restarts;   /* extra cycles [10] */
-    double gmres_rtol;        /* |J d + F| <= rtol |F| [1e-4] */
+    double gmres_rtol;        /* |J d + F| <= rtol |F| [1e-2] */
     int newton_max_its;       /* [12] */
     double newton_tol;        /* converged when max |delta rho|/rho <= tol [1e-8] */
     int precond;              /* MUSIC_PC_* [ACOUSTIC]; pass -1 for NONE */
-    int precond_sweeps;       /* weighted-Jacobi sweeps of the pressure system [8] */
+    int precond_sweeps;       /* weighted-Jacobi sweeps of the pressure system [16] */
     int max_dt_halvings;      /* retries of a failed step at dt/2 [4] */
 } music_grid_desc;
 

@@ -38,7 +38,10 @@ struct DevScalars {
     double h[MUSIC_MAXV];   // first CGS pass
     double h2[MUSIC_MAXV];  // second CGS pass
     double diag[8];
+    unsigned int counters[8];  // last-block-done counters, 0 between launches
 };
+
+enum { CNT_DOTS = 0, CNT_UPDATE, CNT_NORMW, CNT_SUMSQ, CNT_NEWTON, CNT_PRECOND };
 
 __host__ __device__ inline long long ext_index(const GridParams &P, int i, int j, int k)
 {
@@ -142,3 +145,51 @@ __device__ inline double block_max(double v, double *sh)
 
 template <typename T>
 __device__ inline double to_d(T v) { return (double)v; }
+
+// True in the one block of the grid that finishes last.  Every block calls it
+// after writing its partials; the fence makes them visible to the last block,
+// which then reads them through L2 (__ldcg).  The counter is reset for the
+// next launch.  No block ever waits on another.
+__device__ inline bool last_block_done(unsigned int *counter)
+{
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+        last = (atomicAdd(counter, 1u) == nb - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) *counter = 0;
+    return last;
+}
+
+// In the last block: dst[i] = sum_b partial[i * stride + b], b < nb, i < count,
+// each in a fixed order (thread t takes b = t, t + BS, ..., then the tree).
+template <int BS>
+__device__ inline void finish_sums(const double *partial, int nb, long long stride, int count, double *dst,
+                                   double *sh)
+{
+    for (int i = 0; i < count; i++) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nb; b += BS) s += __ldcg(partial + i * stride + b);
+        const double r = block_sum<BS>(s, sh);
+        if (threadIdx.x == 0) dst[i] = r;
+    }
+}
+
+template <int BS>
+__device__ inline void finish_max(const double *partial, int nb, double *dst, double *sh)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += BS) s = nanmax(s, __ldcg(partial + b));
+    const double r = block_max<BS>(s, sh);
+    if (threadIdx.x == 0) *dst = r;
+}
+
+// eps = sqrt(2^-52) (1 + |U|) / |v| for the next Jacobian-free product
+__device__ inline double fd_eps(double unorm2, double vnorm2)
+{
+    const double vn = sqrt(vnorm2);
+    return (vn == 0.0) ? 0.0 : (sqrt(2.220446049250313e-16) * (1.0 + sqrt(unorm2))) / vn;
+}

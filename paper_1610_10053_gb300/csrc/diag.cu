@@ -70,33 +70,34 @@ __global__ void __launch_bounds__(BS) k_rows(GridParams P, const double *U, doub
     }
 }
 
-__global__ void k_combine_rows(GridParams P, const double *rows, DevScalars *ds, int want_diag)
+__global__ void __launch_bounds__(BS) k_combine_rows(GridParams P, const double *rows, DevScalars *ds,
+                                                      int want_diag)
 {
-    // one thread, rows in order: deterministic and small (n[1] rows)
-    if (threadIdx.x != 0) return;
+    // one block; thread t takes rows t, t + BS, ... and the block tree
+    // combines them: a fixed order for a given grid
+    __shared__ double sh[BS / 32];
     const int ny = P.n[1];
     const double per_row = (double)((long long)P.n[0] * P.n[2]);
-    double h = 0, ek = 0, ey = 0, cr = 0, ci = 0, mach = 0, sp = 0, rate = 0;
-    for (int j = 0; j < ny; j++) {
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < ny; j += BS) {
         const double xh = rows[j] / per_row;
         const double xm = (xh <= 0.5) ? 2.0 * xh : 2.0 * (1.0 - xh);
-        h += xm * P.dx[1];
-        ek += rows[ny + j];
-        ey += rows[2 * ny + j];
-        cr += rows[3 * ny + j];
-        ci += rows[4 * ny + j];
-        mach = nanmax(mach, rows[5 * ny + j]);
-        sp = nanmax(sp, rows[6 * ny + j]);
-        rate = nanmax(rate, rows[7 * ny + j]);
+        a[0] += xm * P.dx[1];
+        for (int q = 1; q < 5; q++) a[q] += rows[(long long)q * ny + j];
+        for (int q = 5; q < 8; q++) a[q] = nanmax(a[q], rows[(long long)q * ny + j]);
     }
-    ds->rate = rate;
+    double r[8];
+    for (int q = 0; q < 5; q++) r[q] = block_sum<BS>(a[q], sh);
+    for (int q = 5; q < 8; q++) r[q] = block_max<BS>(a[q], sh);
+    if (threadIdx.x != 0) return;
+    ds->rate = r[7];
     if (want_diag) {
-        ds->diag[0] = h;
-        ds->diag[1] = mach;
-        ds->diag[2] = 2.0 / (double)P.N * sqrt(cr * cr + ci * ci);
-        ds->diag[3] = ey;
-        ds->diag[4] = ek / (double)P.N;
-        ds->diag[5] = sp;
+        ds->diag[0] = r[0];
+        ds->diag[1] = r[5];
+        ds->diag[2] = 2.0 / (double)P.N * sqrt(r[3] * r[3] + r[4] * r[4]);
+        ds->diag[3] = r[2];
+        ds->diag[4] = r[1] / (double)P.N;
+        ds->diag[5] = r[6];
     }
 }
 
@@ -106,7 +107,7 @@ int run_rows(music_grid *g, const double *U, double rho_L, double rho_H, int wan
     const double kmode = 2.0 * (2.0 * M_PI / (P.n[0] * P.dx[0]));
     k_rows<<<P.n[1], BS, 0, s>>>(P, U, rho_L, rho_H, kmode, g->diag_rows);
     CHECK_LAUNCH();
-    k_combine_rows<<<1, 32, 0, s>>>(P, g->diag_rows, g->ds, want_diag);
+    k_combine_rows<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds, want_diag);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

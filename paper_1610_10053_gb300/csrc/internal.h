@@ -100,7 +100,8 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
 
 // ----- precond.cu -----
 int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s);  // frozen coefficients
-// z = M^-1 r; also |z|^2 -> ds->vnorm2 when want_norm
+// z = M^-1 r; with want_norm also |z|^2 -> ds->vnorm2 and the Jv step
+// eps(|U|, |z|) -> ds->eps
 int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);
 
 // ----- diag.cu -----

@@ -19,7 +19,8 @@ struct Coef {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *partial)
+__global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *partial, double *dst,
+                                              unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double s = 0.0;
@@ -29,6 +30,7 @@ __global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *p
     }
     const double r = block_sum<BS>(s, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    if (last_block_done(counter)) finish_sums<BS>(partial, gridDim.x, 0, 1, dst, sh);
 }
 
 // dst[k] = sum_b partial[k * nb + b], one block per k, fixed order.
@@ -57,14 +59,13 @@ __global__ void k_set_eps(DevScalars *ds, double fixed)
         ds->eps = fixed;
         return;
     }
-    const double vn = sqrt(ds->vnorm2);
-    ds->eps = (vn == 0.0) ? 0.0 : (sqrt(2.220446049250313e-16) * (1.0 + sqrt(ds->unorm2))) / vn;
+    ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
 }
 
 // h_i = <V_i, w>, i <= j; accumulators in registers (NVM >= j + 1).
 template <int NVM, typename KT>
 __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
-                                             int nb)
+                                             int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double acc[NVM];
@@ -83,13 +84,14 @@ __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long
             if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
         }
     }
+    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
 }
 
 // w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
 // NORM, |w|^2 only.
 template <int NVM, bool NORM, typename KT>
 __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                               double *partial, int nb)
+                                               double *partial, int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     __shared__ double hs[MUSIC_MAXV];
@@ -126,6 +128,7 @@ __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, 
             }
         }
     }
+    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
 }
 
 template <typename KT>
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
 
 // U += x over all unknowns; partial max of |x_rho| / rho_new over cells.
 __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
-                                                      double *partial)
+                                                      double *partial, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double m = 0.0;
@@ -191,6 +194,7 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
     }
     const double r = block_max<BS>(m, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    if (last_block_done(counter)) finish_max<BS>(partial, gridDim.x, dst, sh);
 }
 
 
@@ -206,7 +210,7 @@ __device__ inline float dot4(const float4 a, const float4 b)
 
 template <int NVM>
 __global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
-                                                 double *partial, int nb)
+                                                 double *partial, int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double acc[NVM];
@@ -235,11 +239,12 @@ __global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w,
             if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
         }
     }
+    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
 }
 
 template <int NVM, bool NORM>
 __global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
-                                                   double *partial, int nb)
+                                                   double *partial, int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     __shared__ float hs[MUSIC_MAXV];
@@ -300,6 +305,7 @@ __global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, lon
             }
         }
     }
+    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
 }
 
 __global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, long long n, int k, Coef y)
@@ -332,11 +338,13 @@ template <int NVM>
 int launch_dots(music_grid *g, int j, cudaStream_t s)
 {
     const long long n = (long long)g->n;
+    unsigned int *cnt = &g->ds->counters[CNT_DOTS];
     if (g->mixed)
-        k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb);
+        k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
+                                             g->ds->h, cnt);
     else
         k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
-                                                 g->nb);
+                                                 g->nb, g->ds->h, cnt);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -345,12 +353,14 @@ template <int NVM, bool NORM>
 int launch_update(music_grid *g, int j, const double *h, cudaStream_t s)
 {
     const long long n = (long long)g->n;
+    double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
+    unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
     if (g->mixed)
         k_update_f32<NVM, NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
-                                                      g->nb);
+                                                      g->nb, dst, cnt);
     else
         k_update<NVM, NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h,
-                                                         g->partials, g->nb);
+                                                         g->partials, g->nb, dst, cnt);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -359,12 +369,11 @@ int launch_update(music_grid *g, int j, const double *h, cudaStream_t s)
 
 int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s)
 {
+    unsigned int *cnt = &g->ds->counters[CNT_SUMSQ];
     if (is_double)
-        k_sumsq<double><<<g->nb, BS, 0, s>>>((const double *)x, (long long)n, g->partials);
+        k_sumsq<double><<<g->nb, BS, 0, s>>>((const double *)x, (long long)n, g->partials, dst, cnt);
     else
-        k_sumsq<float><<<g->nb, BS, 0, s>>>((const float *)x, (long long)n, g->partials);
-    CHECK_LAUNCH();
-    k_final_sum<<<1, BS, 0, s>>>(g->partials, g->nb, dst);
+        k_sumsq<float><<<g->nb, BS, 0, s>>>((const float *)x, (long long)n, g->partials, dst, cnt);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -393,8 +402,6 @@ int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s)
         TRY(launch_dots<32>(g, j, s));
     else
         TRY(launch_dots<64>(g, j, s));
-    k_final_sum<<<j + 1, BS, 0, s>>>(g->partials, g->nb, dst_h);
-    CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
@@ -409,8 +416,6 @@ int krylov_update_dots(music_grid *g, int j, cudaStream_t s)
         TRY((launch_update<32, false>(g, j, h, s)));
     else
         TRY((launch_update<64, false>(g, j, h, s)));
-    k_final_sum<<<j + 1, BS, 0, s>>>(g->partials, g->nb, g->ds->h2);
-    CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
@@ -425,8 +430,6 @@ int krylov_update_norm(music_grid *g, int j, cudaStream_t s)
         TRY((launch_update<32, true>(g, j, h, s)));
     else
         TRY((launch_update<64, true>(g, j, h, s)));
-    k_final_sum<<<1, BS, 0, s>>>(g->partials, g->nb, &g->ds->wnorm2);
-    CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
@@ -515,9 +518,8 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
 
 int newton_update(music_grid *g, cudaStream_t s)
 {
-    k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials);
-    CHECK_LAUNCH();
-    k_final_max<<<1, BS, 0, s>>>(g->partials, g->nb, &g->ds->maxdrho);
+    k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials, &g->ds->maxdrho,
+                                          &g->ds->counters[CNT_NEWTON]);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

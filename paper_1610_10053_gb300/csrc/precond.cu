@@ -220,7 +220,7 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
 // once; the block's share of |z|^2 goes to `partial`.  Values equal the
 // sweep-by-sweep global iterates, since every tile point used lies at least
 // K cells inside the staged region.
-constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 12;
+constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;
 
 template <typename PT>
 __device__ inline long long pc_map(const GridParams &P, int gx, int gy, bool &inside_x, bool &inside_y)
@@ -247,7 +247,8 @@ __device__ inline long long pc_map(const GridParams &P, int gx, int gy, bool &in
 
 template <typename PT>
 __global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z,
-                                                               PT tau, PT tau2, int K, double *partial)
+                                                               PT tau, PT tau2, int K, double *partial,
+                                                               DevScalars *ds)
 {
     constexpr int NT = PTX * PTY;
     const int H = K + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
@@ -331,8 +332,14 @@ __global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<P
         nrm = (double)zr * zr + (double)ze * ze + (double)mx_own * mx_own + (double)my_own * my_own;
     }
     if (partial) {
+        // |z|^2 and, in the last block, the finite-difference step of the Jv
+        // that follows: eps = sqrt(2^-52) (1 + |U|) / |z|
         const double t = block_sum<NT>(nrm, red);
         if (tid == 0) partial[blockIdx.x + gridDim.x * blockIdx.y] = t;
+        if (last_block_done(&ds->counters[CNT_PRECOND])) {
+            finish_sums<NT>(partial, gridDim.x * gridDim.y, 0, 1, &ds->vnorm2, red);
+            if (tid == 0) ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
+        }
     }
 }
 
@@ -353,13 +360,12 @@ int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, c
     dim3 grid((P.n[0] + PTX - 1) / PTX, (P.n[1] + PTY - 1) / PTY);
     const int nblk = grid.x * grid.y;
     double *part = (want_norm && nblk <= MUSIC_MAXV * g->nb) ? g->partials : nullptr;
-    k_precond_fused2d<PT><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau), K, part);
+    k_precond_fused2d<PT><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau), K, part,
+                                                        g->ds);
     CHECK_LAUNCH();
-    if (want_norm) {
-        if (part)
-            TRY(final_sum(g, nblk, &g->ds->vnorm2, s));
-        else
-            TRY(dev_norm2(g, z, sizeof(PT) == 8, g->n, &g->ds->vnorm2, s));
+    if (want_norm && !part) {
+        TRY(dev_norm2(g, z, sizeof(PT) == 8, g->n, &g->ds->vnorm2, s));
+        TRY(dev_set_eps(g, 0.0, s));
     }
     return MUSIC_OK;
 }
@@ -387,6 +393,9 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
     } else {
         TRY(apply_t<double>(g, dt, (const double *)r, (double *)z, s));
     }
-    if (want_norm) TRY(dev_norm2(g, z, !g->mixed, n, &g->ds->vnorm2, s));
+    if (want_norm) {
+        TRY(dev_norm2(g, z, !g->mixed, n, &g->ds->vnorm2, s));
+        TRY(dev_set_eps(g, 0.0, s));
+    }
     return MUSIC_OK;
 }

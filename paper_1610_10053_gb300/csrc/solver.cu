@@ -28,8 +28,11 @@ int sync_scalars(music_grid *g, cudaStream_t s)
 int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
              int need_vnorm, cudaStream_t s)
 {
-    if (need_vnorm) TRY(dev_norm2(g, v, vin_double, g->n, &g->ds->vnorm2, s));
-    TRY(dev_set_eps(g, 0.0, s));
+    // eps comes with |v|: computed here, or already by the preconditioner
+    if (need_vnorm) {
+        TRY(dev_norm2(g, v, vin_double, g->n, &g->ds->vnorm2, s));
+        TRY(dev_set_eps(g, 0.0, s));
+    }
     return stencil_apply(g, SM_JV, g->U, g->RU, v, vin_double, out, out_double, nullptr, dt, 1.0, s);
 }
 

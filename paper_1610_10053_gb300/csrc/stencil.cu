@@ -252,9 +252,11 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
 
 // ---------------------------------------------------------------- fused 2-D
 // One kernel per evaluation of R on 2-D grids.  A CTA owns a TX x TY tile of
-// cells and stages the tile plus a halo of 3 cells below / 2 above in shared
-// memory (RX x RY points, x fastest).  Each phase computes one family of
-// intermediate values once per point of the region it is needed on:
+// cells [X0, X1) x [Y0, Y1) (local coordinates) and stages the tile plus a
+// halo of 3 cells below / 2 above in shared memory (RX x RY points, x
+// fastest).  Each intermediate is computed once, and only on the exact
+// sub-rectangle that the tile's residuals reach (the stencil is a cross, not
+// a square), which keeps FP64 divisions near the minimum of 11 per cell:
 //   1 ghost-mapped rho, e, p and face velocities u, v (global loads, L1/L2)
 //   2 van Leer slopes of rho, e, u, v along x and y
 //   3 upwind mass and energy fluxes on x- and y-faces
@@ -263,8 +265,15 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
 template <int TX, int TY>
 struct Tile2D {
     static constexpr int RX = TX + 5, RY = TY + 5, R = RX * RY, NARR = 17;
+    static constexpr int X0 = 3, X1 = 3 + TX, Y0 = 3, Y1 = 3 + TY;
     static constexpr size_t SMEM = (size_t)NARR * R * sizeof(double);
 };
+
+// loop of the CTA's threads over the local rectangle [x0,x1) x [y0,y1)
+#define TILE_RECT(x0, x1, y0, y1)                                                   \
+    for (int k_ = tid, w_ = (x1) - (x0), n_ = ((x1) - (x0)) * ((y1) - (y0)); k_ < n_; \
+         k_ += NT)                                                                  \
+        for (int lx = (x0) + k_ % w_, ly = (y0) + k_ / w_, q = ly * RX + lx, once_ = 1; once_; once_ = 0)
 
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
@@ -273,6 +282,7 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *
 {
     using TL = Tile2D<TX, TY>;
     constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
+    constexpr int X0 = TL::X0, X1 = TL::X1, Y0 = TL::Y0, Y1 = TL::Y1;
     extern __shared__ double sm[];
     double *rho = sm, *ee = sm + R, *pp = sm + 2 * R, *uu = sm + 3 * R, *vv = sm + 4 * R;
     double *srx = sm + 5 * R, *sry = sm + 6 * R, *sex = sm + 7 * R, *sey = sm + 8 * R;
@@ -285,94 +295,114 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
     const WLoad<VIN> W{U, (MODE == SM_JV) ? v : nullptr, epsv};
 
-    for (int q = tid; q < R; q += NT) {
-        const int lx = q % RX, ly = q / RX;
+    // ---- phase 1: cell scalars on the cross-shaped region, face velocities
+    auto rho_at = [&](int lx, int ly, int q) {
         const int ix[3] = {i0 + lx, j0 + ly, 0};
         double r, E;
         load_cell(P, W, ix, r, E);
         rho[q] = r;
+    };
+    auto e_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        double r, E;
+        load_cell(P, W, ix, r, E);
         ee[q] = E / r;
         pp[q] = P.gm1 * E;
+    };
+    auto u_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
         uu[q] = face_velocity(P, W, ix, 0);
+    };
+    auto v_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
         vv[q] = face_velocity(P, W, ix, 1);
+    };
+    TILE_RECT(0, RX, Y0 - 1, Y1) rho_at(lx, ly, q);
+    TILE_RECT(X0 - 1, X1, 0, Y0 - 1) rho_at(lx, ly, q);
+    TILE_RECT(X0 - 1, X1, Y1, RY) rho_at(lx, ly, q);
+    TILE_RECT(1, RX, Y0, Y1) e_at(lx, ly, q);
+    TILE_RECT(X0, X1, 1, Y0) e_at(lx, ly, q);
+    TILE_RECT(X0, X1, Y1, RY) e_at(lx, ly, q);
+    TILE_RECT(1, RX, Y0, Y1) u_at(lx, ly, q);
+    TILE_RECT(X0, X1, 1, Y0) u_at(lx, ly, q);
+    TILE_RECT(X0, X1, Y1, RY) u_at(lx, ly, q);
+    if (tid == 0) u_at(X0 - 1, Y0 - 1, (Y0 - 1) * RX + X0 - 1);
+    if (tid == 1) u_at(X1, Y0 - 1, (Y0 - 1) * RX + X1);
+    TILE_RECT(X0, X1, 1, RY) v_at(lx, ly, q);
+    TILE_RECT(1, X0, Y0, Y1) v_at(lx, ly, q);
+    TILE_RECT(X1, RX, Y0, Y1) v_at(lx, ly, q);
+    if (tid == 2) v_at(X0 - 1, Y0 - 1, (Y0 - 1) * RX + X0 - 1);
+    if (tid == 3) v_at(X0 - 1, Y1, Y1 * RX + X0 - 1);
+    __syncthreads();
+
+    // ---- phase 2: limited slopes, each on the rectangle its fluxes need
+    TILE_RECT(X0 - 2, X1 + 1, Y0 - 1, Y1) srx[q] = vanleer(rho[q] - rho[q - 1], rho[q + 1] - rho[q]);
+    TILE_RECT(X0 - 1, X1 + 1, Y0, Y1) sex[q] = vanleer(ee[q] - ee[q - 1], ee[q + 1] - ee[q]);
+    TILE_RECT(X0 - 1, X1, Y0 - 2, Y1 + 1) sry[q] = vanleer(rho[q] - rho[q - RX], rho[q + RX] - rho[q]);
+    TILE_RECT(X0, X1, Y0 - 1, Y1 + 1) sey[q] = vanleer(ee[q] - ee[q - RX], ee[q + RX] - ee[q]);
+    TILE_RECT(X0 - 1, X1 + 1, Y0, Y1) {
+        sux[q] = vanleer(uu[q] - uu[q - 1], uu[q + 1] - uu[q]);
+        svx[q] = vanleer(vv[q] - vv[q - 1], vv[q + 1] - vv[q]);
+    }
+    TILE_RECT(X0, X1, Y0 - 1, Y1 + 1) {
+        suy[q] = vanleer(uu[q] - uu[q - RX], uu[q + RX] - uu[q]);
+        svy[q] = vanleer(vv[q] - vv[q - RX], vv[q + RX] - vv[q]);
     }
     __syncthreads();
-    for (int q = tid; q < R; q += NT) {
-        const int lx = q % RX, ly = q / RX;
-        if (lx >= 1 && lx < RX - 1) {
-            srx[q] = vanleer(rho[q] - rho[q - 1], rho[q + 1] - rho[q]);
-            sex[q] = vanleer(ee[q] - ee[q - 1], ee[q + 1] - ee[q]);
-            sux[q] = vanleer(uu[q] - uu[q - 1], uu[q + 1] - uu[q]);
-            svx[q] = vanleer(vv[q] - vv[q - 1], vv[q + 1] - vv[q]);
-        }
-        if (ly >= 1 && ly < RY - 1) {
-            sry[q] = vanleer(rho[q] - rho[q - RX], rho[q + RX] - rho[q]);
-            sey[q] = vanleer(ee[q] - ee[q - RX], ee[q + RX] - ee[q]);
-            suy[q] = vanleer(uu[q] - uu[q - RX], uu[q + RX] - uu[q]);
-            svy[q] = vanleer(vv[q] - vv[q - RX], vv[q + RX] - vv[q]);
-        }
-    }
-    __syncthreads();
-    for (int q = tid; q < R; q += NT) {
-        const int lx = q % RX, ly = q / RX;
-        if (lx >= 2 && lx < RX - 1) {
-            const double u = uu[q];
-            double rs, es;
-            if (u >= 0.0) {
-                rs = rho[q - 1] + 0.5 * srx[q - 1];
-                es = ee[q - 1] + 0.5 * sex[q - 1];
-            } else {
-                rs = rho[q] - 0.5 * srx[q];
-                es = ee[q] - 0.5 * sex[q];
-            }
-            const double fr = u * rs;
-            Frx[q] = fr;
+
+    // ---- phase 3: upwind mass and energy fluxes
+    TILE_RECT(X0 - 1, X1 + 1, Y0 - 1, Y1) {
+        const double u = uu[q];
+        const bool up = (u >= 0.0);
+        const double rs = up ? rho[q - 1] + 0.5 * srx[q - 1] : rho[q] - 0.5 * srx[q];
+        const double fr = u * rs;
+        Frx[q] = fr;
+        if (lx >= X0 && ly >= Y0) {
+            const double es = up ? ee[q - 1] + 0.5 * sex[q - 1] : ee[q] - 0.5 * sex[q];
             FEx[q] = fr * es;
         }
-        if (ly >= 2 && ly < RY - 1) {
-            const double u = vv[q];
-            double rs, es;
-            if (u >= 0.0) {
-                rs = rho[q - RX] + 0.5 * sry[q - RX];
-                es = ee[q - RX] + 0.5 * sey[q - RX];
-            } else {
-                rs = rho[q] - 0.5 * sry[q];
-                es = ee[q] - 0.5 * sey[q];
-            }
-            const double fr = u * rs;
-            Fry[q] = fr;
+    }
+    TILE_RECT(X0 - 1, X1, Y0 - 1, Y1 + 1) {
+        const double u = vv[q];
+        const bool up = (u >= 0.0);
+        const double rs = up ? rho[q - RX] + 0.5 * sry[q - RX] : rho[q] - 0.5 * sry[q];
+        const double fr = u * rs;
+        Fry[q] = fr;
+        if (lx >= X0 && ly >= Y0) {
+            const double es = up ? ee[q - RX] + 0.5 * sey[q - RX] : ee[q] - 0.5 * sey[q];
             FEy[q] = fr * es;
         }
     }
     __syncthreads();
-    for (int q = tid; q < R; q += NT) {
-        const int lx = q % RX, ly = q / RX;
-        if (lx >= 2 && lx < RX - 2) {
-            const double fm = 0.5 * (Frx[q] + Frx[q + 1]);
-            const double us = (fm >= 0.0) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
-            Phx[q] = fm * us;
-        }
-        if (ly >= 2 && ly < RY - 2) {
-            const double fm = 0.5 * (Fry[q] + Fry[q + RX]);
-            const double us = (fm >= 0.0) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
-            Phy[q] = fm * us;
-        }
-        if (lx >= 1 && ly >= 2 && ly < RY - 1) {
-            const double fm = 0.5 * (Fry[q - 1] + Fry[q]);
-            const double us = (fm >= 0.0) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
-            Psxy[q] = fm * us;
-        }
-        if (ly >= 1 && lx >= 2 && lx < RX - 1) {
-            const double fm = 0.5 * (Frx[q - RX] + Frx[q]);
-            const double us = (fm >= 0.0) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
-            Psyx[q] = fm * us;
-        }
+
+    // ---- phase 4: momentum fluxes
+    TILE_RECT(X0 - 1, X1, Y0, Y1) {
+        const double fm = 0.5 * (Frx[q] + Frx[q + 1]);
+        const double us = (fm >= 0.0) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
+        Phx[q] = fm * us;
+    }
+    TILE_RECT(X0, X1, Y0 - 1, Y1) {
+        const double fm = 0.5 * (Fry[q] + Fry[q + RX]);
+        const double us = (fm >= 0.0) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
+        Phy[q] = fm * us;
+    }
+    TILE_RECT(X0, X1, Y0, Y1 + 1) {
+        const double fm = 0.5 * (Fry[q - 1] + Fry[q]);
+        const double us = (fm >= 0.0) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
+        Psxy[q] = fm * us;
+    }
+    TILE_RECT(X0, X1 + 1, Y0, Y1) {
+        const double fm = 0.5 * (Frx[q - RX] + Frx[q]);
+        const double us = (fm >= 0.0) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
+        Psyx[q] = fm * us;
     }
     __syncthreads();
+
+    // ---- phase 5: residuals of the tile
     const int tx = tid % TX, ty = tid / TX;
     const int gx = blockIdx.x * TX + tx, gy = blockIdx.y * TY + ty;
     if (gx >= P.n[0] || gy >= P.n[1]) return;
-    const int q = (ty + 3) * RX + (tx + 3);
+    const int q = (ty + Y0) * RX + (tx + X0);
     const double ix0 = P.idx[0], ix1 = P.idx[1];
     double Rv[4];
     {
@@ -418,8 +448,9 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *
         }
     }
 }
+#undef TILE_RECT
 
-constexpr int FTX = 32, FTY = 8;
+constexpr int FTX = 32, FTY = 16;
 
 template <int MODE, typename VIN, typename VOUT>
 int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN *v, VOUT *out, double *RU_out,

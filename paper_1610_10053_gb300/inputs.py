@@ -64,11 +64,11 @@ class Problem:
     dt_max: float = 0.0
     restart: int = 30
     max_restarts: int = 10
-    gmres_rtol: float = 1e-4
+    gmres_rtol: float = 1e-2
     newton_max: int = 12
     newton_tol: float = 1e-8
     precond: int = PC_ACOUSTIC
-    sweeps: int = 8
+    sweeps: int = 16
     max_halvings: int = 4
     rho_L: float = 1.0   # light / heavy densities for the mixing height
     rho_H: float = 2.0
