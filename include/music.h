@@ -205,6 +205,17 @@ int music_cfl_dt(music_grid *grid, double cfl, double *dt, void *stream);
  */
 int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out, void *stream);
 
+/*
+ * Timing of the Jacobian-free stencil: while enabled, every launch of the
+ * stencil in its Jv mode (the dominant kernel of a step) is bracketed by CUDA
+ * events on the stream it is launched on; music_profile_read returns the
+ * number of such launches and their summed device time since the last
+ * enable (it waits for recorded launches to finish).  Enabling resets the
+ * counters.  Off by default; costs two event records per launch.
+ */
+int music_profile_enable(music_grid *grid, int on);
+int music_profile_read(music_grid *grid, uint64_t *launches, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ SIGNATURES = {
     "music_cfl_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dbl_p, ctypes.c_void_p]),
     "music_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dbl_p,
                                          ctypes.c_void_p]),
+    "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
 }
 
 _lib = None
@@ -267,6 +269,16 @@ class Grid:
     def run(self, nsteps: Optional[int] = None, cfl: Optional[float] = None, dt_max: Optional[float] = None):
         nsteps = self.prob.nsteps if nsteps is None else nsteps
         return [self.step(cfl, dt_max) for _ in range(nsteps)]
+
+    def profile(self, on: bool = True):
+        """Time every Jv-mode stencil launch with CUDA events (see music.h)."""
+        check(load().music_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        n = ctypes.c_uint64()
+        ms = ctypes.c_double()
+        check(load().music_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        return int(n.value), float(ms.value)
 
     def diagnostics(self, rho_L: Optional[float] = None, rho_H: Optional[float] = None) -> dict:
         out = (ctypes.c_double * 6)()

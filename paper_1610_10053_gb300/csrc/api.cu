@@ -151,6 +151,8 @@ void free_grid(music_grid *g)
         }
     }
     if (g->hs) cudaFreeHost(g->hs);
+    if (g->prof_events_made)
+        for (int i = 0; i < 2 * 256; i++) cudaEventDestroy(g->prof_ev[i]);
     delete g;
 }
 
@@ -429,6 +431,25 @@ int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out,
     CUDA_TRY(cudaMemcpyAsync(grid->hs, grid->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     for (int k = 0; k < 6; k++) out[k] = grid->hs->diag[k];
+    return MUSIC_OK;
+}
+
+int music_profile_enable(music_grid *grid, int on)
+{
+    TRY(check_grid(grid));
+    if (grid->prof_pending) TRY(prof_harvest(grid, 1));
+    grid->prof_on = on ? 1 : 0;
+    grid->prof_launches = 0;
+    grid->prof_ms = 0.0;
+    return MUSIC_OK;
+}
+
+int music_profile_read(music_grid *grid, uint64_t *launches, double *ms)
+{
+    TRY(check_grid(grid));
+    if (grid->prof_pending) TRY(prof_harvest(grid, 1));
+    if (launches) *launches = grid->prof_launches;
+    if (ms) *ms = grid->prof_ms;
     return MUSIC_OK;
 }
 

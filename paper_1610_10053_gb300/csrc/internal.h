@@ -45,7 +45,19 @@ struct music_grid {
     DevScalars *ds;        // device scalars
     DevScalars *hs;        // pinned host mirror
     double *diag_rows;     // per-row diagnostic partials
+    // optional timing of the Jacobian-free stencil launches (music_profile_*)
+    int prof_on;
+    int prof_pending;            // event pairs recorded, not yet harvested
+    cudaEvent_t prof_ev[2 * 256];
+    unsigned long long prof_launches;
+    double prof_ms;
+    int prof_events_made;
 };
+
+// record the start / end of a profiled launch; harvest completed pairs
+int prof_begin(music_grid *g, cudaStream_t s);
+int prof_end(music_grid *g, cudaStream_t s);
+int prof_harvest(music_grid *g, int wait);
 
 // error reporting (thread local)
 void set_error(const char *fmt, ...);

@@ -44,15 +44,6 @@ __global__ void __launch_bounds__(BS) k_final_sum(const double *partial, int nb,
     if (threadIdx.x == 0) dst[blockIdx.x] = r;
 }
 
-__global__ void __launch_bounds__(BS) k_final_max(const double *partial, int nb, double *dst)
-{
-    __shared__ double sh[BS / 32];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += BS) s = nanmax(s, partial[i]);
-    const double r = block_max<BS>(s, sh);
-    if (threadIdx.x == 0) *dst = r;
-}
-
 __global__ void k_set_eps(DevScalars *ds, double fixed)
 {
     if (fixed > 0.0) {

@@ -20,6 +20,7 @@ int sync_scalars(music_grid *g, cudaStream_t s)
 {
     CUDA_TRY(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    if (g->prof_pending) TRY(prof_harvest(g, 0));
     return MUSIC_OK;
 }
 
@@ -187,6 +188,40 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
 }
 
 }  // namespace
+
+// ---- timing of the Jacobian-free stencil (CUDA events on the launch stream)
+int prof_begin(music_grid *g, cudaStream_t s)
+{
+    if (!g->prof_events_made) {
+        for (int i = 0; i < 2 * 256; i++) CUDA_TRY(cudaEventCreate(&g->prof_ev[i]));
+        g->prof_events_made = 1;
+    }
+    if (g->prof_pending == 256) TRY(prof_harvest(g, 1));
+    CUDA_TRY(cudaEventRecord(g->prof_ev[2 * g->prof_pending], s));
+    return MUSIC_OK;
+}
+
+int prof_end(music_grid *g, cudaStream_t s)
+{
+    CUDA_TRY(cudaEventRecord(g->prof_ev[2 * g->prof_pending + 1], s));
+    g->prof_pending++;
+    return MUSIC_OK;
+}
+
+// Accumulate the recorded pairs; with wait = 0 only after they completed
+// (the caller has synchronised the stream), with wait = 1 it waits for them.
+int prof_harvest(music_grid *g, int wait)
+{
+    for (int i = 0; i < g->prof_pending; i++) {
+        if (wait) CUDA_TRY(cudaEventSynchronize(g->prof_ev[2 * i + 1]));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, g->prof_ev[2 * i], g->prof_ev[2 * i + 1]));
+        g->prof_ms += ms;
+        g->prof_launches++;
+    }
+    g->prof_pending = 0;
+    return MUSIC_OK;
+}
 
 int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_t s)
 {

@@ -529,8 +529,15 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
 {
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
-    if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS)
-        return fused2d_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS) {
+        const bool prof = g->prof_on && mode == SM_JV;
+        if (prof) TRY(prof_begin(g, s));
+        TRY(fused2d_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
+        if (prof) TRY(prof_end(g, s));
+        return MUSIC_OK;
+    }
+    const bool prof = g->prof_on && mode == SM_JV;
+    if (prof) TRY(prof_begin(g, s));
     const int nbn = blocks_for(P.N);
     const double *eps = &g->ds->eps;
     if (mode == SM_JV) {
@@ -573,5 +580,6 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
         return MUSIC_E_INVAL;
     }
     CHECK_LAUNCH();
+    if (prof) TRY(prof_end(g, s));
     return MUSIC_OK;
 }

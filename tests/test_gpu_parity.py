@@ -317,3 +317,15 @@ def test_precond_sweep_counts():
         with B().Grid(q) as g:
             z = host(g.precond(dev(q.U), dt, dev(r)))
         planewise_close(q, z, O.precond(q, q.U, dt, r), 1e-12, extra=r)
+
+
+def test_profile_counts_jv_launches():
+    p = CASES["kh_64"]().with_options(nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        g.profile(True)
+        st = g.run()
+        n, ms = g.profile_read()
+        g.profile(False)
+    # one Jv per Arnoldi step plus one per GMRES restart
+    assert n >= st[0]["gmres_its"] and ms > 0.0
