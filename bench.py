@@ -198,6 +198,9 @@ def run_music(args):
     e2e = end_to_end(mixed["grid"], prob, stream, max(2, min(args.steps, 5)))
     for r in result.values():
         r["grid"].close()
+    serving = None
+    if not args.no_serving and ws == 1:
+        serving = run_serving(args.serve_solves)
 
     if rank != 0:
         return
@@ -231,6 +234,7 @@ def run_music(args):
         "e2e": e2e,
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clocks"],
+        "serving": serving,
     }
     print(json.dumps(line))
 
@@ -291,6 +295,74 @@ def end_to_end(grid, prob, stream, steps):
             "d2h_bytes_per_step": n * 8, "steps": steps}
 
 
+def serving_mix(nsolves=256, seed=4):
+    """The serving workload: a seeded Poisson stream of solves drawn from the
+    2-D Rayleigh-Taylor and Kelvin-Helmholtz setups, grids uniform over
+    {64^2, 128^2, 256x512, 512^2}, 20 implicit steps each."""
+    from paper_1610_10053_gb300 import inputs as I
+    rng = np.random.default_rng(seed)
+    grids = [(64, 64), (128, 128), (256, 512), (512, 512)]
+    out = []
+    for i in range(nsolves):
+        nx, ny = grids[int(rng.integers(4))]
+        if rng.integers(2) == 0:
+            p = I.rayleigh_taylor(nx=nx, ny=ny, nsteps=20)
+        else:
+            p = I.kelvin_helmholtz(n=nx, ny=ny, seed=100 + i, nsteps=20)
+        out.append(p)
+    gaps = rng.exponential(1.0, size=nsolves)
+    return out, gaps
+
+
+def run_serving(nsolves=256, max_active=16, seq_sample=12):
+    """Continuous batching through the solve server (mixed precision), against
+    the same solves run one after another on the plain FP64 GPU path."""
+    import threading
+    from paper_1610_10053_gb300 import binding as B
+    probs, gaps = serving_mix(nsolves)
+    cells = sum(p.ncells * p.nsteps for p in probs)
+    # sequential FP64 reference on a sample of the mix (a rate, so a sample suffices)
+    t0 = time.perf_counter()
+    seq_cells = 0
+    for p in probs[:seq_sample]:
+        with B.Grid(p, precision=B.FP64) as g:
+            g.set_state(p.U)
+            g.run()
+        seq_cells += p.ncells * p.nsteps
+    seq_rate = seq_cells / (time.perf_counter() - t0)
+    # arrivals: mean gap chosen so that about `max_active` solves overlap
+    mean_service = seq_cells / seq_rate / seq_sample
+    gaps = gaps * (mean_service / max_active)
+    tickets = []
+    with B.Server(max_active=max_active) as srv:
+        start = time.perf_counter()
+
+        def submitter():
+            t = start
+            for p, gp in zip(probs, gaps):
+                t += gp
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(p, B.MIXED))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        res = [srv.wait(t) for t in tickets]
+        wall = time.perf_counter() - start
+        lat = srv.step_times()
+        st = srv.stats()
+    ok = sum(r["status"] == 0 for r in res)
+    rate = st["cell_steps"] / wall
+    return {"solves": nsolves, "completed": ok, "max_active": max_active, "wall_s": wall,
+            "cell_steps_per_s": rate, "step_ms_p50": float(np.percentile(lat, 50)),
+            "step_ms_p99": float(np.percentile(lat, 99)),
+            "queue_ms_p99": float(np.percentile([r["queue_ms"] for r in res], 99)),
+            "sequential_fp64_cell_steps_per_s": seq_rate, "over_sequential_fp64": rate / seq_rate,
+            "sequential_sample": seq_sample, "cell_steps": cells}
+
+
 def cpu_baseline(prob, steps=1):
     """The FP64 CPU oracle as it stands, single-threaded, on one implicit step
     of the same workload."""
@@ -345,6 +417,8 @@ def main():
     ap.add_argument("--workload", default="kh512", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-solves", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -123,9 +123,14 @@ uint64_t music_kernel_launches(void);
  */
 int music_create_grid(const music_grid_desc *desc, music_grid **out);
 
-/* Free everything owned by the grid.  NULL is accepted. Synchronises the
-   device first. */
+/* Free everything owned by the grid.  NULL is accepted.  Synchronises the
+   device first (the caller may still have work using the grid queued on
+   other streams). */
 int music_destroy_grid(music_grid *grid);
+
+/* Device bytes music_create_grid would allocate for `desc` (nothing is
+   allocated).  Errors: MUSIC_E_INVAL for an invalid descriptor. */
+int music_grid_footprint(const music_grid_desc *desc, size_t *bytes);
 
 /* Number of state values nv*N of the grid, or 0 for NULL. */
 size_t music_state_size(const music_grid *grid);
@@ -134,7 +139,8 @@ size_t music_state_size(const music_grid *grid);
 size_t music_grid_bytes(const music_grid *grid);
 
 /* Copy a state (layout above) into / out of the grid.  `is_device` says
-   whether `U` is a device pointer (else host).  Synchronous. */
+   whether `U` is a device pointer (else host).  Synchronous: waits for all
+   work on the device first, then copies. */
 int music_set_state(music_grid *grid, const double *U, int is_device);
 int music_get_state(music_grid *grid, double *U, int is_device);
 

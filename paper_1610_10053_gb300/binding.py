@@ -60,6 +60,7 @@ SIGNATURES = {
     "music_create_grid": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "music_destroy_grid": (ctypes.c_int, [ctypes.c_void_p]),
     "music_state_size": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "music_grid_footprint": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.POINTER(ctypes.c_size_t)]),
     "music_grid_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "music_set_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "music_get_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -154,6 +155,14 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
     for k, v in over.items():
         setattr(d, k, v)
     return d
+
+
+def footprint(prob, precision: int = FP64, **over) -> int:
+    """Device bytes a grid for `prob` would own."""
+    d = desc_from_problem(prob, precision, **over)
+    b = ctypes.c_size_t()
+    check(load().music_grid_footprint(ctypes.byref(d), ctypes.byref(b)))
+    return int(b.value)
 
 
 class Grid:
@@ -288,3 +297,121 @@ class Grid:
         names = ("mixing_height", "max_mach", "kh_mode_amplitude", "vertical_kinetic_energy",
                  "mean_kinetic_energy", "max_speed")
         return dict(zip(names, list(out)))
+
+
+# ------------------------------------------------------------------ server
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class SolveReq(ctypes.Structure):
+    _fields_ = [("desc", GridDesc), ("U0", ctypes.POINTER(ctypes.c_double)), ("n_steps", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("dt_max", ctypes.c_double), ("rho_L", ctypes.c_double),
+                ("rho_H", ctypes.c_double)]
+
+
+class SolveResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("sim_time", ctypes.c_double),
+                ("diag", ctypes.c_double * 6), ("step_ms_p50", ctypes.c_double), ("step_ms_p99", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("newton_its", ctypes.c_int),
+                ("gmres_its", ctypes.c_int)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "diag"}
+        d["diag"] = list(self.diag)
+        return d
+
+
+SIGNATURES.update({
+    "music_server_create": (ctypes.c_int, [ctypes.POINTER(ServerOpts), ctypes.POINTER(ctypes.c_void_p)]),
+    "music_submit_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SolveReq),
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "music_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(SolveResult)]),
+    "music_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(SolveResult)]),
+    "music_result_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, _dbl_p]),
+    "music_release": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    "music_server_stats": (ctypes.c_int, [ctypes.c_void_p, _dbl_p, _dbl_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "music_server_step_times": (ctypes.c_int, [ctypes.c_void_p, _dbl_p, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "music_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+})
+
+
+class Server:
+    """Continuous-batching solve server (include/music_server.h)."""
+
+    def __init__(self, mem_budget_bytes: int = 0, max_active: int = 16):
+        L = load()
+        o = ServerOpts(mem_budget_bytes, max_active, 0)
+        h = ctypes.c_void_p()
+        check(L.music_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self._n = {}
+
+    def submit(self, prob, precision: int = FP64, n_steps=None, cfl=None, dt_max=None, **over) -> int:
+        U0 = np.ascontiguousarray(prob.U, dtype=np.float64)
+        req = SolveReq()
+        req.desc = desc_from_problem(prob, precision, **over)
+        req.U0 = U0.ctypes.data_as(_dbl_p)
+        req.n_steps = int(prob.nsteps if n_steps is None else n_steps)
+        req.cfl = float(prob.cfl if cfl is None else cfl)
+        req.dt_max = float(prob.dt_max if dt_max is None else dt_max)
+        req.rho_L, req.rho_H = float(prob.rho_L), float(prob.rho_H)
+        t = ctypes.c_uint64()
+        check(load().music_submit_solve(self.h, ctypes.byref(req), ctypes.byref(t)))
+        self._n[t.value] = U0.size
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        r = SolveResult()
+        code = load().music_poll(self.h, ticket, ctypes.byref(r))
+        if code == 8:
+            return None
+        check(code)
+        return r.as_dict()
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        r = SolveResult()
+        check(load().music_wait(self.h, ticket, int(timeout_ms), ctypes.byref(r)))
+        return r.as_dict()
+
+    def result_state(self, ticket: int) -> np.ndarray:
+        a = np.empty(self._n[ticket], dtype=np.float64)
+        check(load().music_result_state(self.h, ticket, a.ctypes.data_as(_dbl_p)))
+        return a
+
+    def release(self, ticket: int):
+        check(load().music_release(self.h, ticket))
+        self._n.pop(ticket, None)
+
+    def stats(self) -> dict:
+        cs, busy = ctypes.c_double(), ctypes.c_double()
+        act, q = ctypes.c_int(), ctypes.c_int()
+        check(load().music_server_stats(self.h, ctypes.byref(cs), ctypes.byref(busy), ctypes.byref(act),
+                                        ctypes.byref(q)))
+        return {"cell_steps": cs.value, "busy_ms": busy.value, "active": act.value, "queued": q.value}
+
+    def step_times(self) -> np.ndarray:
+        n = ctypes.c_size_t()
+        check(load().music_server_step_times(self.h, None, 0, ctypes.byref(n)))
+        a = np.empty(n.value, dtype=np.float64)
+        check(load().music_server_step_times(self.h, a.ctypes.data_as(_dbl_p), n.value, ctypes.byref(n)))
+        return a
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().music_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

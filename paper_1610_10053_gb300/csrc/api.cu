@@ -115,41 +115,67 @@ GridParams make_params(const music_grid_desc &d)
     return P;
 }
 
-struct Alloc {
-    music_grid *g;
-    int fail = 0;
-    template <typename T>
-    T *get(size_t count)
-    {
-        if (fail || count == 0) return nullptr;
-        void *p = nullptr;
-        if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) {
-            fail = 1;
-            cudaGetLastError();
-            return nullptr;
-        }
-        g->bytes += count * sizeof(T);
-        return (T *)p;
+// The grid's device buffers, in one list shared by the footprint query and
+// by creation: f(slot, bytes) is called once per buffer.
+template <class F>
+void alloc_plan(music_grid *g, F &&f)
+{
+    const music_grid_desc &d = g->desc;
+    const GridParams &P = g->P;
+    const size_t n = g->n, N = (size_t)P.N, M = (size_t)P.M;
+    const size_t ks = g->mixed ? sizeof(float) : sizeof(double);
+    for (double **p : {&g->U, &g->Un, &g->Cn, &g->RU, &g->b, &g->x, &g->t64}) f((void **)p, n * sizeof(double));
+    f(&g->V, (size_t)(d.gmres_restart + 1) * n * ks);
+    for (void **p : {&g->w, &g->z, &g->u}) f(p, n * ks);
+    if (d.precond != MUSIC_PC_NONE) {
+        for (int k = 0; k < P.nd; k++) f(&g->pa[k], N * ks);
+        for (void **p : {&g->pgp, &g->php, &g->pD, &g->pb, &g->pdp, &g->pdq}) f(p, N * ks);
     }
-};
+    // the multi-pass stencil (3-D, or 2-D on request) keeps its planes on the
+    // ghosted grid; the fused 2-D kernels need none of them
+    if (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS) {
+        ExtScratch &X = g->ext;
+        for (double **p : {&X.rho, &X.e, &X.p}) f((void **)p, M * sizeof(double));
+        for (int k = 0; k < P.nd; k++) {
+            for (double **p : {&X.uf[k], &X.srho[k], &X.se[k], &X.Frho[k], &X.FE[k], &X.Phi[k]})
+                f((void **)p, M * sizeof(double));
+            for (int q = 0; q < P.nd; q++) {
+                f((void **)&X.su[k][q], M * sizeof(double));
+                if (q != k) f((void **)&X.Psi[k][q], M * sizeof(double));
+            }
+        }
+    }
+    f((void **)&g->partials, (size_t)MUSIC_MAXV * g->nb * sizeof(double));
+    f((void **)&g->ds, sizeof(DevScalars));
+    f((void **)&g->diag_rows, (size_t)8 * P.n[1] * sizeof(double));
+}
+
+void init_grid_struct(music_grid *g, const music_grid_desc &d)
+{
+    memset(g, 0, sizeof(*g));
+    g->desc = d;
+    g->P = make_params(d);
+    g->mixed = (d.precision == MUSIC_MIXED);
+    // MUSIC_STENCIL=multipass selects the multi-pass stencil on 2-D grids
+    const char *sv = getenv("MUSIC_STENCIL");
+    g->stencil_variant = (sv && strcmp(sv, "multipass") == 0) ? STENCIL_MULTIPASS : STENCIL_AUTO;
+    // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep
+    const char *pv = getenv("MUSIC_PRECOND");
+    g->pc_variant = (pv && strcmp(pv, "multikernel") == 0) ? PC_MULTIKERNEL : PC_AUTO;
+    g->n = (size_t)g->P.nv * g->P.N;
+    // reduction blocks: enough to fill the GPU, fixed per grid
+    long long nb = ((long long)g->n + 255) / 256;
+    g->nb = (int)(nb > 2 * 152 ? 2 * 152 : (nb < 1 ? 1 : nb));
+}
 
 void free_grid(music_grid *g)
 {
     if (!g) return;
-    void *ptrs[] = {g->U, g->Un, g->Cn, g->RU, g->b, g->x, g->t64, g->t64b, g->V, g->w, g->z, g->u,
-                    g->pa[0], g->pa[1], g->pa[2], g->pgp, g->php, g->pD, g->pb, g->pdp, g->pdq,
-                    g->ext.rho, g->ext.e, g->ext.p, g->partials, g->ds, g->diag_rows};
-    for (void *p : ptrs)
-        if (p) cudaFree(p);
-    for (int d = 0; d < 3; d++) {
-        void *q[] = {g->ext.uf[d], g->ext.srho[d], g->ext.se[d], g->ext.Frho[d], g->ext.FE[d], g->ext.Phi[d]};
-        for (void *p : q)
-            if (p) cudaFree(p);
-        for (int e = 0; e < 3; e++) {
-            if (g->ext.su[d][e]) cudaFree(g->ext.su[d][e]);
-            if (g->ext.Psi[d][e]) cudaFree(g->ext.Psi[d][e]);
-        }
-    }
+    alloc_plan(g, [&](void **slot, size_t) {
+        if (*slot) cudaFreeAsync(*slot, g->home);
+        *slot = nullptr;
+    });
+    cudaStreamSynchronize(g->home);
     if (g->hs) cudaFreeHost(g->hs);
     if (g->prof_events_made)
         for (int i = 0; i < 2 * 256; i++) cudaEventDestroy(g->prof_ev[i]);
@@ -168,6 +194,102 @@ int check_grid(const music_grid *g)
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int grid_footprint(const music_grid_desc *desc, size_t *bytes)
+{
+    music_grid_desc d = *desc;
+    fill_defaults(d);
+    TRY(validate(d));
+    music_grid *g = new (std::nothrow) music_grid;
+    if (!g) {
+        set_error("host allocation failed");
+        return MUSIC_E_OOM;
+    }
+    init_grid_struct(g, d);
+    size_t total = 0;
+    alloc_plan(g, [&](void **, size_t b) { total += b; });
+    delete g;
+    *bytes = total;
+    return MUSIC_OK;
+}
+
+int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out)
+{
+    if (!desc || !out) {
+        set_error("music_create_grid: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    *out = nullptr;
+    music_grid_desc d = *desc;
+    fill_defaults(d);
+    TRY(validate(d));
+    music_grid *g = new (std::nothrow) music_grid;
+    if (!g) {
+        set_error("host allocation failed");
+        return MUSIC_E_OOM;
+    }
+    init_grid_struct(g, d);
+    g->home = home;
+    if (cudaGetDevice(&g->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete g;
+        set_error("no CUDA device");
+        return MUSIC_E_CUDA;
+    }
+    // stream-ordered allocation on the home stream: no device-wide sync, so
+    // grids created by concurrent workers do not stall one another
+    int fail = 0;
+    alloc_plan(g, [&](void **slot, size_t b) {
+        if (fail) return;
+        if (cudaMallocAsync(slot, b, home) != cudaSuccess) {
+            cudaGetLastError();
+            *slot = nullptr;
+            fail = 1;
+            return;
+        }
+        g->bytes += b;
+        // every buffer starts at zero (the stencil scratch is read at its
+        // ghosted edges before it is written)
+        if (cudaMemsetAsync(*slot, 0, b, home) != cudaSuccess) {
+            cudaGetLastError();
+            fail = 1;
+        }
+    });
+    if (!fail && cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        g->hs = nullptr;
+        fail = 1;
+    }
+    if (!fail && cudaStreamSynchronize(home) != cudaSuccess) {
+        cudaGetLastError();
+        fail = 1;
+    }
+    if (fail) {
+        free_grid(g);
+        set_error("device allocation failed");
+        return MUSIC_E_OOM;
+    }
+    *out = g;
+    return MUSIC_OK;
+}
+
+void grid_destroy(music_grid *g) { free_grid(g); }
+
+int grid_set_state(music_grid *g, const double *U, int is_device, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(g->U, U, g->n * sizeof(double), is_device ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MUSIC_OK;
+}
+
+int grid_get_state(music_grid *g, double *U, int is_device, cudaStream_t s)
+{
+    CUDA_TRY(cudaMemcpyAsync(U, g->U, g->n * sizeof(double), is_device ? cudaMemcpyDeviceToDevice
+                                                                        : cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return MUSIC_OK;
+}
 
 void set_error(const char *fmt, ...)
 {
@@ -196,114 +318,24 @@ uint64_t music_kernel_launches(void) { return g_launches.load(std::memory_order_
 
 int music_create_grid(const music_grid_desc *desc, music_grid **out)
 {
-    if (!desc || !out) {
-        set_error("music_create_grid: NULL argument");
-        return MUSIC_E_INVAL;
-    }
-    *out = nullptr;
-    music_grid_desc d = *desc;
-    fill_defaults(d);
-    TRY(validate(d));
-    music_grid *g = new (std::nothrow) music_grid;
-    if (!g) {
-        set_error("host allocation failed");
-        return MUSIC_E_OOM;
-    }
-    memset(g, 0, sizeof(*g));
-    g->desc = d;
-    g->P = make_params(d);
-    g->mixed = (d.precision == MUSIC_MIXED);
-    {
-        // MUSIC_STENCIL=multipass selects the multi-pass stencil on 2-D grids
-        const char *sv = getenv("MUSIC_STENCIL");
-        g->stencil_variant = (sv && strcmp(sv, "multipass") == 0) ? STENCIL_MULTIPASS : STENCIL_AUTO;
-        // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep
-        const char *pv = getenv("MUSIC_PRECOND");
-        g->pc_variant = (pv && strcmp(pv, "multikernel") == 0) ? PC_MULTIKERNEL : PC_AUTO;
-    }
-    CUDA_TRY(cudaGetDevice(&g->device));
-    const GridParams &P = g->P;
-    g->n = (size_t)P.nv * P.N;
-    const size_t n = g->n, N = (size_t)P.N, M = (size_t)P.M;
-    const size_t ks = g->mixed ? sizeof(float) : sizeof(double);
-    // reduction blocks: enough to fill the GPU, fixed per grid
-    long long nb = ((long long)n + 255) / 256;
-    g->nb = (int)(nb > 2 * 152 ? 2 * 152 : (nb < 1 ? 1 : nb));
-    Alloc A{g};
-    g->U = A.get<double>(n);
-    g->Un = A.get<double>(n);
-    g->Cn = A.get<double>(n);
-    g->RU = A.get<double>(n);
-    g->b = A.get<double>(n);
-    g->x = A.get<double>(n);
-    g->t64 = A.get<double>(n);
-    g->V = A.get<char>((size_t)(d.gmres_restart + 1) * n * ks);
-    g->w = A.get<char>(n * ks);
-    g->z = A.get<char>(n * ks);
-    g->u = A.get<char>(n * ks);
-    if (d.precond != MUSIC_PC_NONE) {
-        for (int k = 0; k < P.nd; k++) g->pa[k] = A.get<char>(N * ks);
-        g->pgp = A.get<char>(N * ks);
-        g->php = A.get<char>(N * ks);
-        g->pD = A.get<char>(N * ks);
-        g->pb = A.get<char>(N * ks);
-        g->pdp = A.get<char>(N * ks);
-        g->pdq = A.get<char>(N * ks);
-    }
-    ExtScratch &X = g->ext;
-    X.rho = A.get<double>(M);
-    X.e = A.get<double>(M);
-    X.p = A.get<double>(M);
-    for (int k = 0; k < P.nd; k++) {
-        X.uf[k] = A.get<double>(M);
-        X.srho[k] = A.get<double>(M);
-        X.se[k] = A.get<double>(M);
-        X.Frho[k] = A.get<double>(M);
-        X.FE[k] = A.get<double>(M);
-        X.Phi[k] = A.get<double>(M);
-        for (int q = 0; q < P.nd; q++) {
-            X.su[k][q] = A.get<double>(M);
-            if (q != k) X.Psi[k][q] = A.get<double>(M);
-        }
-    }
-    g->partials = A.get<double>((size_t)MUSIC_MAXV * g->nb);
-    g->ds = A.get<DevScalars>(1);
-    g->diag_rows = A.get<double>((size_t)8 * P.n[1]);
-    if (A.fail) {
-        free_grid(g);
-        set_error("device allocation failed");
-        return MUSIC_E_OOM;
-    }
-    if (cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {
-        cudaGetLastError();
-        free_grid(g);
-        set_error("pinned host allocation failed");
-        return MUSIC_E_OOM;
-    }
-    // zero everything the stencil might read before writing (ghost-edge scratch)
-    for (void *p : {(void *)X.rho, (void *)X.e, (void *)X.p}) CUDA_TRY(cudaMemset(p, 0, M * sizeof(double)));
-    for (int k = 0; k < P.nd; k++) {
-        for (void *p : {(void *)X.uf[k], (void *)X.srho[k], (void *)X.se[k], (void *)X.Frho[k], (void *)X.FE[k],
-                        (void *)X.Phi[k]})
-            CUDA_TRY(cudaMemset(p, 0, M * sizeof(double)));
-        for (int q = 0; q < P.nd; q++) {
-            CUDA_TRY(cudaMemset(X.su[k][q], 0, M * sizeof(double)));
-            if (q != k) CUDA_TRY(cudaMemset(X.Psi[k][q], 0, M * sizeof(double)));
-        }
-    }
-    CUDA_TRY(cudaMemset(g->U, 0, n * sizeof(double)));
-    CUDA_TRY(cudaMemset(g->ds, 0, sizeof(DevScalars)));
-    CUDA_TRY(cudaDeviceSynchronize());
-    *out = g;
-    return MUSIC_OK;
+    return grid_create(desc, (cudaStream_t)0, out);
 }
 
 int music_destroy_grid(music_grid *grid)
 {
     if (!grid) return MUSIC_OK;
-    cudaDeviceSynchronize();
-    free_grid(grid);
+    cudaDeviceSynchronize();  // the caller may have work on other streams
+    grid_destroy(grid);
     return MUSIC_OK;
+}
+
+int music_grid_footprint(const music_grid_desc *desc, size_t *bytes)
+{
+    if (!desc || !bytes) {
+        set_error("music_grid_footprint: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    return grid_footprint(desc, bytes);
 }
 
 size_t music_state_size(const music_grid *grid) { return grid ? grid->n : 0; }
@@ -317,9 +349,8 @@ int music_set_state(music_grid *grid, const double *U, int is_device)
         set_error("music_set_state: NULL state");
         return MUSIC_E_INVAL;
     }
-    CUDA_TRY(cudaMemcpy(grid->U, U, grid->n * sizeof(double),
-                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
-    return MUSIC_OK;
+    CUDA_TRY(cudaDeviceSynchronize());  // finish work queued on other streams
+    return grid_set_state(grid, U, is_device, grid->home);
 }
 
 int music_get_state(music_grid *grid, double *U, int is_device)
@@ -329,10 +360,8 @@ int music_get_state(music_grid *grid, double *U, int is_device)
         set_error("music_get_state: NULL buffer");
         return MUSIC_E_INVAL;
     }
-    CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemcpy(U, grid->U, grid->n * sizeof(double),
-                        is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
-    return MUSIC_OK;
+    CUDA_TRY(cudaDeviceSynchronize());  // finish work queued on other streams
+    return grid_get_state(grid, U, is_device, grid->home);
 }
 
 int music_spatial_operator(music_grid *grid, const double *U, double *R, void *stream)

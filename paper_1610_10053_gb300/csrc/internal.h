@@ -31,6 +31,7 @@ struct music_grid {
     GridParams P;
     int mixed;
     int device;
+    cudaStream_t home;  // stream of allocation, state transfer and destruction
     size_t n;         // nv * N
     size_t bytes;     // device bytes owned
     int nb;           // reduction blocks
@@ -119,6 +120,13 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
 // ----- diag.cu -----
 int cfl_rate(music_grid *g, const double *U, cudaStream_t s);                  // -> ds->rate
 int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s);
+
+// ----- api.cu: grid lifetime on a given home stream (used by the server) -----
+int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out);
+void grid_destroy(music_grid *g);
+int grid_footprint(const music_grid_desc *desc, size_t *bytes);
+int grid_set_state(music_grid *g, const double *U, int is_device, cudaStream_t s);
+int grid_get_state(music_grid *g, double *U, int is_device, cudaStream_t s);
 
 // ----- solver.cu -----
 int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);

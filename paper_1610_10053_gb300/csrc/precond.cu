@@ -214,103 +214,98 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
 // ---------------------------------------------------------------- fused 2-D
 // The whole application z = M^-1 r in one kernel on 2-D grids: a CTA owns a
 // TX x TY tile and stages the frozen coefficients and r on the tile plus a
-// halo of H = K + 1 cells (K sweeps).  The right-hand side, the K Jacobi
-// sweeps (each valid on a region one cell narrower than the last) and the
-// back substitution all run in shared memory, so r is read and z written
-// once; the block's share of |z|^2 goes to `partial`.  Values equal the
-// sweep-by-sweep global iterates, since every tile point used lies at least
-// K cells inside the staged region.
+// halo of H = KM + 1 cells (KM >= K sweeps, a compile-time size so that all
+// tile index arithmetic is by constants).  The right-hand side, the K Jacobi
+// sweeps (sweep k is computed on the staged region shrunk by k cells, which
+// is exactly where it equals the global iterate) and the back substitution
+// all run in shared memory, so r is read and z written once; the block's
+// share of |z|^2 goes to `partial`, and the last block finishes the sum and
+// the finite-difference step of the Jv that follows.
 constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;
 
-template <typename PT>
-__device__ inline long long pc_map(const GridParams &P, int gx, int gy, bool &inside_x, bool &inside_y)
+// index into an interior row or column: periodic wrap, or clamp on walls
+// (coefficients of faces outside a walled domain are zero, which decouples
+// the clamped cells)
+__device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 {
-    // periodic directions wrap; wall directions clamp (their faces outside
-    // the domain get a zero coefficient, which decouples the clamped cells)
-    const int n0 = P.n[0], n1 = P.n[1];
-    int x = gx, y = gy;
-    inside_x = inside_y = true;
-    if (P.bc[0] == MUSIC_BC_PERIODIC)
-        x = (x % n0 + n0) % n0;
-    else {
-        inside_x = (gx > 0 && gx < n0);
-        x = min(max(x, 0), n0 - 1);
+    if (periodic) {
+        while (a < 0) a += n;
+        while (a >= n) a -= n;
+        inside = true;
+        return a;
     }
-    if (P.bc[1] == MUSIC_BC_PERIODIC)
-        y = (y % n1 + n1) % n1;
-    else {
-        inside_y = (gy > 0 && gy < n1);
-        y = min(max(y, 0), n1 - 1);
-    }
-    return x + (long long)n0 * y;
+    inside = (a > 0 && a < n);
+    return a < 0 ? 0 : (a >= n ? n - 1 : a);
 }
 
-template <typename PT>
+template <typename PT, int KM>
 __global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z,
                                                                PT tau, PT tau2, int K, double *partial,
                                                                DevScalars *ds)
 {
-    constexpr int NT = PTX * PTY;
-    const int H = K + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
+    constexpr int NT = PTX * PTY, H = KM + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
     extern __shared__ unsigned char smraw[];
-    PT *ax = (PT *)smraw, *ay = ax + R, *D = ay + R, *b = D + R, *dA = b + R, *dB = dA + R;
+    PT *ax = (PT *)smraw, *ay = ax + R, *iD = ay + R, *b = iD + R, *dA = b + R, *dB = dA + R;
     __shared__ double red[NT / 32];
     const int i0 = blockIdx.x * PTX - H, j0 = blockIdx.y * PTY - H;
     const int tid = threadIdx.x;
     const long long N = P.N;
+    const int n0 = P.n[0], n1 = P.n[1];
+    const bool px = P.bc[0] == MUSIC_BC_PERIODIC, py = P.bc[1] == MUSIC_BC_PERIODIC;
     const PT w = (PT)MUSIC_JACOBI_OMEGA;
     const PT ix0 = (PT)P.idx[0], ix1 = (PT)P.idx[1];
     for (int q = tid; q < R; q += NT) {
         const int lx = q % RX, ly = q / RX;
         bool inx, iny;
-        const long long c = pc_map<PT>(P, i0 + lx, j0 + ly, inx, iny);
+        const int x = pc_wrap(i0 + lx, n0, px, inx), y = pc_wrap(j0 + ly, n1, py, iny);
+        const long long c = x + (long long)n0 * y;
         ax[q] = inx ? C.a[0][c] : (PT)0;
         ay[q] = iny ? C.a[1][c] : (PT)0;
-        D[q] = C.D[c];
-    }
-    __syncthreads();
-    for (int q = tid; q < R; q += NT) {
-        const int lx = q % RX, ly = q / RX;
-        if (lx >= RX - 1 || ly >= RY - 1) continue;
-        bool inx, iny;
-        const long long c = pc_map<PT>(P, i0 + lx, j0 + ly, inx, iny);
-        const long long cx = pc_map<PT>(P, i0 + lx + 1, j0 + ly, inx, iny);
-        const long long cy = pc_map<PT>(P, i0 + lx, j0 + ly + 1, inx, iny);
-        PT divm = (ax[q + 1] * r[2 * N + cx] - ax[q] * r[2 * N + c]) * ix0;
-        divm += (ay[q + RX] * r[3 * N + cy] - ay[q] * r[3 * N + c]) * ix1;
-        b[q] = (PT)P.gm1 * r[N + c] / C.gp[c] - tau * divm;
+        iD[q] = (PT)1 / C.D[c];
+        if (lx < RX - 1 && ly < RY - 1) {
+            // right-hand side needs r_m on the upper faces: the next cells'
+            bool inxp, inyp;
+            const int xp = pc_wrap(i0 + lx + 1, n0, px, inxp), yp = pc_wrap(j0 + ly + 1, n1, py, inyp);
+            const long long cx = xp + (long long)n0 * y, cy = x + (long long)n0 * yp;
+            const PT axp = inxp ? C.a[0][cx] : (PT)0, ayp = inyp ? C.a[1][cy] : (PT)0;
+            const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
+            PT divm = (axp * r[2 * N + cx] - axm * r[2 * N + c]) * ix0;
+            divm += (ayp * r[3 * N + cy] - aym * r[3 * N + c]) * ix1;
+            b[q] = (PT)P.gm1 * r[N + c] / C.gp[c] - tau * divm;
+        }
     }
     __syncthreads();
     const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
     PT *src = dA, *dst = dB;
     for (int k = 0; k < K; k++) {
-        for (int q = tid; q < R; q += NT) {
-            const int lx = q % RX, ly = q / RX;
-            if (lx < k || ly < k || lx >= RX - 1 - k || ly >= RY - 1 - k) continue;
+        const int lo = k, hx = RX - 1 - k, hy = RY - 1 - k;
+        const int wdt = hx - lo, cnt = wdt * (hy - lo);
+        for (int t = tid; t < cnt; t += NT) {
+            const int q = (lo + t / wdt) * RX + lo + t % wdt;
             if (k == 0) {
-                dst[q] = w * (b[q] / D[q]);
+                dst[q] = w * (b[q] * iD[q]);
             } else {
                 PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
                 off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
-                dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) / D[q]);
+                dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) * iD[q]);
             }
         }
         __syncthreads();
-        PT *t = src;
+        PT *tt = src;
         src = dst;
-        dst = t;
+        dst = tt;
     }
     // src holds dp; back substitution on the tile
     const int tx = tid % PTX, ty = tid / PTX;
     const int gx = blockIdx.x * PTX + tx, gy = blockIdx.y * PTY + ty;
     double nrm = 0.0;
-    if (gx < P.n[0] && gy < P.n[1]) {
+    if (gx < n0 && gy < n1) {
         const int q = (ty + H) * RX + (tx + H);
-        const long long c = gx + (long long)P.n[0] * gy;
-        const bool wlx = (P.bc[0] == MUSIC_BC_WALL && gx == 0), wux = (P.bc[0] == MUSIC_BC_WALL && gx == P.n[0] - 1);
-        const bool wly = (P.bc[1] == MUSIC_BC_WALL && gy == 0), wuy = (P.bc[1] == MUSIC_BC_WALL && gy == P.n[1] - 1);
-        const long long cxp = (gx + 1 == P.n[0]) ? c - gx : c + 1;
-        const long long cyp = (gy + 1 == P.n[1]) ? gx : c + P.n[0];
+        const long long c = gx + (long long)n0 * gy;
+        const bool wlx = (!px && gx == 0), wux = (!px && gx == n0 - 1);
+        const bool wly = (!py && gy == 0), wuy = (!py && gy == n1 - 1);
+        const long long cxp = (gx + 1 == n0) ? c - gx : c + 1;
+        const long long cyp = (gy + 1 == n1) ? gx : c + n0;
         const PT dp = (K > 0) ? src[q] : (PT)0;
         const PT dpxm = (K > 0) ? src[q - 1] : (PT)0, dpxp = (K > 0) ? src[q + 1] : (PT)0;
         const PT dpym = (K > 0) ? src[q - RX] : (PT)0, dpyp = (K > 0) ? src[q + RX] : (PT)0;
@@ -343,31 +338,40 @@ __global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<P
     }
 }
 
-template <typename PT>
-int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+template <typename PT, int KM>
+int launch_pc_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
 {
-    const GridParams &P = g->P;
-    const int K = g->desc.precond_sweeps, H = K + 1;
-    const size_t smem = (size_t)6 * (PTX + 2 * H) * (PTY + 2 * H) * sizeof(PT);
+    constexpr int H = KM + 1;
+    constexpr size_t smem = (size_t)6 * (PTX + 2 * H) * (PTY + 2 * H) * sizeof(PT);
     static bool attr = false;
     if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(6 * (PTX + 2 * (PC_FUSED_MAXK + 1)) * (PTY + 2 * (PC_FUSED_MAXK + 1)) *
-                                            sizeof(PT))));
+        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
         attr = true;
     }
+    const GridParams &P = g->P;
     const double tau = 0.5 * dt;
     dim3 grid((P.n[0] + PTX - 1) / PTX, (P.n[1] + PTY - 1) / PTY);
     const int nblk = grid.x * grid.y;
     double *part = (want_norm && nblk <= MUSIC_MAXV * g->nb) ? g->partials : nullptr;
-    k_precond_fused2d<PT><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau), K, part,
-                                                        g->ds);
+    k_precond_fused2d<PT, KM><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau),
+                                                            g->desc.precond_sweeps, part, g->ds);
     CHECK_LAUNCH();
     if (want_norm && !part) {
         TRY(dev_norm2(g, z, sizeof(PT) == 8, g->n, &g->ds->vnorm2, s));
         TRY(dev_set_eps(g, 0.0, s));
     }
     return MUSIC_OK;
+}
+
+template <typename PT>
+int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+{
+    const int K = g->desc.precond_sweeps;
+    if (K <= 4) return launch_pc_fused2d<PT, 4>(g, dt, r, z, want_norm, s);
+    if (K <= 8) return launch_pc_fused2d<PT, 8>(g, dt, r, z, want_norm, s);
+    if (K <= 12) return launch_pc_fused2d<PT, 12>(g, dt, r, z, want_norm, s);
+    return launch_pc_fused2d<PT, 16>(g, dt, r, z, want_norm, s);
 }
 
 }  // namespace

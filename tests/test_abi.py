@@ -44,9 +44,36 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_binding_covers_every_symbol():
     from paper_1610_10053_gb300 import binding
-    assert set(declared_functions()) <= set(binding.SIGNATURES) | {
-        n for n in declared_functions() if n.startswith("music_server") or n in (
-            "music_submit_solve", "music_poll", "music_wait", "music_release", "music_result_state")}
+    assert set(declared_functions()) <= set(binding.SIGNATURES)
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """Every struct of the C headers has the size and field offsets that the
+    ctypes binding assumes (checked by compiling a C program against them)."""
+    from paper_1610_10053_gb300 import binding as b
+    structs = {"music_grid_desc": b.GridDesc, "music_step_stats": b.StepStats,
+               "music_server_opts": b.ServerOpts, "music_solve_req": b.SolveReq,
+               "music_solve_result": b.SolveResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "music_server.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
 
 
 def test_library_does_not_contain_the_oracle(lib):

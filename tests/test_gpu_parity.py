@@ -192,16 +192,22 @@ def test_implicit_steps_fp64(case, nsteps):
         st = g.run()
         U = g.get_state()
         d = g.diagnostics()
+    same_path = True
     for a, b in zip(st, sref):
         assert a["newton_its"] == b["newton_its"]
         # a linear-tolerance test on the edge may flip by rounding
         assert abs(a["gmres_its"] - b["gmres_its"]) <= max(1, 0.05 * b["gmres_its"])
+        same_path &= a["gmres_its"] == b["gmres_its"]
         assert _rel(a["dt"], b["dt"]) <= 1e-9
+    # Same Newton/GMRES path: only rounding separates the states.  Otherwise
+    # both are converged iterates of the same Crank-Nicolson root, each within
+    # about the Newton tolerance (max |delta rho|/rho <= 1e-8) of it.
+    tol = 1e-9 if same_path else p.newton_tol
     N = p.ncells
     for v in range(p.nvars):
         s = slice(v * N, (v + 1) * N)
         scale = np.abs(Uref[s]).max() + 1e-300
-        assert np.abs(U[s] - Uref[s]).max() <= 1e-9 * scale, v
+        assert np.abs(U[s] - Uref[s]).max() <= tol * scale, (v, same_path)
     diag_close(d, dref, 1e-9)
 
 

@@ -1,0 +1,103 @@
+"""Solve server (include/music_server.h): continuous batching on one GPU.
+
+Each solve must give the same result alone and in a mix (every reduction is
+deterministic, so equality is bitwise), admission must respect the memory
+budget, and one failing solve must not disturb the others.
+"""
+import numpy as np
+import pytest
+
+from paper_1610_10053_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def B():
+    from paper_1610_10053_gb300 import binding
+    return binding
+
+
+def mix():
+    return [
+        (I.rayleigh_taylor(nx=32, ny=96, nsteps=3), 0),
+        (I.kelvin_helmholtz(n=64, seed=3, nsteps=2), 1),
+        (I.kelvin_helmholtz(n=128, seed=4, nsteps=2), 1),
+        (I.rayleigh_taylor(nsteps=2), 1),
+        (I.kelvin_helmholtz(n=64, seed=5, nsteps=3), 0),
+        (I.taylor_green(n=16, nsteps=1), 1),
+    ]
+
+
+def alone(prob, prec):
+    with B().Grid(prob, precision=prec) as g:
+        g.set_state(prob.U)
+        g.run()
+        return g.get_state(), g.diagnostics()
+
+
+def test_same_result_alone_and_in_the_mix():
+    reqs = mix()
+    with B().Server(max_active=4) as s:
+        tickets = [s.submit(p, prec) for p, prec in reqs]
+        results = [s.wait(t, timeout_ms=300000) for t in tickets]
+        states = [s.result_state(t) for t in tickets]
+        st = s.stats()
+        lat = s.step_times()
+    for (p, prec), r, U in zip(reqs, results, states):
+        assert r["status"] == 0 and r["steps_done"] == p.nsteps
+        U1, d1 = alone(p, prec)
+        assert np.array_equal(U, U1), p.name
+        assert r["diag"] == [d1[k] for k in ("mixing_height", "max_mach", "kh_mode_amplitude",
+                                             "vertical_kinetic_energy", "mean_kinetic_energy", "max_speed")]
+        assert r["step_ms_p99"] >= r["step_ms_p50"] > 0.0
+    assert st["cell_steps"] == sum(p.ncells * p.nsteps for p, _ in reqs)
+    assert len(lat) == sum(p.nsteps for p, _ in reqs)
+    assert st["active"] == 0 and st["queued"] == 0
+
+
+def test_admission_by_device_footprint():
+    big = I.kelvin_helmholtz(n=256, seed=6, nsteps=2)
+    fp = B().footprint(big, B().MIXED)
+    # room for one such solve at a time
+    with B().Server(mem_budget_bytes=int(1.5 * fp), max_active=8) as s:
+        t = [s.submit(big, B().MIXED) for _ in range(3)]
+        r = [s.wait(x, timeout_ms=300000) for x in t]
+        assert all(x["status"] == 0 for x in r)
+        # the second and third waited for memory, not for a worker
+        waited = sorted(x["queue_ms"] for x in r)
+        assert waited[1] > 0.5 * r[0]["total_ms"] or waited[1] > 1.0
+        huge = I.kelvin_helmholtz(n=1024, nsteps=1)
+        with pytest.raises(B().MusicError) as e:
+            s.submit(huge, B().MIXED)
+        assert e.value.code == 8  # MUSIC_E_BUSY: can never fit
+
+
+def test_wait_timeout_and_poll():
+    p = I.kelvin_helmholtz(n=256, nsteps=4)
+    with B().Server(max_active=1) as s:
+        t1 = s.submit(p, B().FP64)
+        t2 = s.submit(p, B().FP64)
+        with pytest.raises(B().MusicError) as e:
+            s.wait(t2, timeout_ms=0)
+        assert e.value.code == 7  # MUSIC_E_TIMEOUT
+        assert s.poll(t2) is None or s.poll(t2)["status"] == 0
+        assert s.wait(t1)["status"] == 0 and s.wait(t2)["status"] == 0
+        s.release(t1)
+        with pytest.raises(B().MusicError):
+            s.poll(t1)
+
+
+def test_failing_solve_does_not_disturb_the_mix():
+    good = I.kelvin_helmholtz(n=64, seed=7, nsteps=2)
+    bad = good.with_state(np.where(np.arange(good.U.size) == 5, np.nan, good.U))
+    with B().Server(max_active=2) as s:
+        tb = s.submit(bad, B().MIXED)
+        tg = s.submit(good, B().MIXED)
+        rb, rg = s.wait(tb), s.wait(tg)
+        Ug = s.result_state(tg)
+    assert rb["status"] != 0
+    assert rg["status"] == 0
+    U1, _ = alone(good, B().MIXED)
+    assert np.array_equal(Ug, U1)
