@@ -208,6 +208,20 @@ def test_implicit_steps_fp64(case, nsteps):
         s = slice(v * N, (v + 1) * N)
         scale = np.abs(Uref[s]).max() + 1e-300
         assert np.abs(U[s] - Uref[s]).max() <= tol * scale, (v, same_path)
+    diag_close(d, dref, tol)
+
+
+def test_tgv_tight_newton_diagnostics_1e9():
+    """With the Newton tolerance well below 1e-9 the converged states no
+    longer depend on the iteration path, and the FP64 diagnostics match the
+    oracle to 1e-9 even where a GMRES count differs."""
+    p = CASES["tgv_16"]().with_options(nsteps=2, newton_tol=1e-11, newton_max=20)
+    Uref, _ = O.run(p)
+    dref = O.diagnostics(p, Uref)
+    with B().Grid(p) as g:
+        g.set_state(p.U)
+        g.run()
+        d = g.diagnostics()
     diag_close(d, dref, 1e-9)
 
 
