@@ -199,6 +199,27 @@ int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *s
 int music_cfl_dt(music_grid *grid, double cfl, double *dt, void *stream);
 
 /*
+ * Allocation-free CFL rate, for callers that cannot allocate device memory:
+ * code running inside another framework's memory pool or custom allocator
+ * (which forbids cudaMalloc behind its back), embedded drivers and real-time
+ * loops that must never block in the allocator, and code that may run while
+ * the device is nearly full.  The paper has no counterpart: it is a service
+ * variant of the reduction behind music_cfl_dt that needs no music_grid.
+ *
+ * Writes rate = max_cells,d ((|u_d| + c_s) / dx_d) of the state U (Eq. 4;
+ * dt = cfl / rate) into *rate.  U: device, float64, nv*N in the layout above;
+ * rate: device pointer to one double.  Async on `stream`; it allocates
+ * nothing: its scratch is a fixed device array inside the library, sized for
+ * grids of at most 16384 rows (n[1]), held by every GPU that loads the
+ * library until the process exits.  The first call on each device looks up
+ * that array's address; make it before any stream capture.  Calls whose work
+ * overlaps on the GPU (other streams, other threads) share the array and
+ * race; serialise them.  Errors: MUSIC_E_INVAL (bad descriptor or pointers,
+ * n[1] > 16384), MUSIC_E_CUDA.
+ */
+int music_cfl_rate_noalloc(const music_grid_desc *desc, const double *U, double *rate, void *stream);
+
+/*
  * Diagnostics of the grid's state (Secs. 3-6), written to out[0..5]:
  *  0 mixing-layer height h = sum_rows X_M(<X_H>) dy with
  *    X_H = (rho - rho_L)/(rho_H - rho_L) (Cabot & Cook, Sec. 3);

@@ -76,6 +76,8 @@ SIGNATURES = {
     "music_cfl_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _dbl_p, ctypes.c_void_p]),
     "music_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _dbl_p,
                                          ctypes.c_void_p]),
+    "music_cfl_rate_noalloc": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
 }
@@ -155,6 +157,13 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
     for k, v in over.items():
         setattr(d, k, v)
     return d
+
+
+def cfl_rate_noalloc(prob, U, rate, precision: int = FP64):
+    """max (|u|+c)/dx of the device state U into the one-element device tensor
+    `rate`, without any device allocation (music_cfl_rate_noalloc)."""
+    d = desc_from_problem(prob, precision)
+    check(load().music_cfl_rate_noalloc(ctypes.byref(d), _ptr(U), _ptr(rate), _stream()))
 
 
 def footprint(prob, precision: int = FP64, **over) -> int:

@@ -195,6 +195,14 @@ int check_grid(const music_grid *g)
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+void fill_grid_params(const music_grid_desc &d, GridParams *P) { *P = make_params(d); }
+
+int grid_validate(music_grid_desc *d)
+{
+    fill_defaults(*d);
+    return validate(*d);
+}
+
 int grid_footprint(const music_grid_desc *desc, size_t *bytes)
 {
     music_grid_desc d = *desc;

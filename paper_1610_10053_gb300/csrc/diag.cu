@@ -3,6 +3,7 @@
 // Deterministic: one block per row (direction 1) produces the row's sums and
 // maxima in a fixed order; a single block then combines the rows in order.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -122,4 +123,75 @@ int cfl_rate(music_grid *g, const double *U, cudaStream_t s)
 int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s)
 {
     return run_rows(g, U, rho_L, rho_H, 1, s);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the CFL-rate reduction (music_cfl_rate_noalloc).
+//
+// Its scratch -- the per-row partials of k_rows and the result slot written
+// by k_combine_rows -- lives in one file-scope device array of fixed size,
+// which every GPU that loads this library holds until the process exits.  In
+// host code `g_noalloc_scratch` names a host-side stand-in, not device
+// memory, so the kernels get the array's device address, looked up once per
+// device with cudaGetSymbolAddress on the first call made with that device
+// current.
+namespace {
+
+constexpr int NOALLOC_MAX_ROWS = 16384;  // grid rows (n[1]) the scratch holds
+struct NoallocScratch {
+    double rows[NR * NOALLOC_MAX_ROWS];  // 8 quantities per row
+    DevScalars ds;                       // k_combine_rows writes ds.rate here
+};
+static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+NoallocScratch *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+__global__ void k_copy_rate(const NoallocScratch *S, double *rate) { *rate = S->ds.rate; }
+
+}  // namespace
+
+extern "C" int music_cfl_rate_noalloc(const music_grid_desc *desc, const double *U, double *rate, void *stream)
+{
+    if (!desc || !U || !rate) {
+        set_error("music_cfl_rate_noalloc: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    music_grid_desc d = *desc;
+    TRY(grid_validate(&d));
+    if (d.n[1] > NOALLOC_MAX_ROWS) {
+        set_error("music_cfl_rate_noalloc: n[1] = %d rows exceeds the fixed scratch of %d rows", d.n[1],
+                  NOALLOC_MAX_ROWS);
+        return MUSIC_E_INVAL;
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("music_cfl_rate_noalloc: device %d beyond the %d supported", dev, NOALLOC_MAX_DEVICES);
+        return MUSIC_E_INVAL;
+    }
+    NoallocScratch *S = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = (NoallocScratch *)p;
+        }
+        S = g_noalloc_ptr[dev];
+    }
+    GridParams P;
+    fill_grid_params(d, &P);
+    cudaStream_t s = (cudaStream_t)stream;
+    const double kmode = 2.0 * (2.0 * M_PI / (P.n[0] * P.dx[0]));
+    // every row slot k_combine_rows reads is written by k_rows first, so
+    // nothing needs clearing between calls
+    k_rows<<<P.n[1], BS, 0, s>>>(P, U, 1.0, 2.0, kmode, S->rows);
+    CHECK_LAUNCH();
+    k_combine_rows<<<1, BS, 0, s>>>(P, S->rows, &S->ds, 0);
+    CHECK_LAUNCH();
+    k_copy_rate<<<1, 1, 0, s>>>(S, rate);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
 }

@@ -125,6 +125,10 @@ int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cuda
 int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out);
 void grid_destroy(music_grid *g);
 int grid_footprint(const music_grid_desc *desc, size_t *bytes);
+// geometry and physics of a descriptor whose defaults are filled in
+void fill_grid_params(const music_grid_desc &d, GridParams *P);
+// fill in defaults and validate, allocating nothing
+int grid_validate(music_grid_desc *d);
 int grid_set_state(music_grid *g, const double *U, int is_device, cudaStream_t s);
 int grid_get_state(music_grid *g, double *U, int is_device, cudaStream_t s);
 
