@@ -395,13 +395,14 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = float(np.sum(times))
     value = prob.ncells * args.steps / total
-    sample = "1 implicit step of KH 256x256 per step (FP64, single thread)"
+    sample = ("each step: one implicit step of the same Kelvin-Helmholtz setup on a 256x256 grid "
+              "(a quarter of the cells; FP64, single thread); cell-steps/s is a rate")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "Kelvin-Helmholtz 2-D, CFL 10, Newton tol 1e-8, GMRES(30)", "cells": prob.ncells,
+        "config": {"workload": WORKLOADS["kh512"][0], "cells": 512 * 512, "precision": "fp64 (oracle)",
                    "sample": sample},
         "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
