@@ -52,6 +52,8 @@
 #define OR_PC_ACOUSTIC 1
 #define OR_GHOST 3
 #define OR_JACOBI_OMEGA 0.8
+#define OR_GEOM_CARTESIAN 0
+#define OR_GEOM_SPHERICAL 1   /* 2-D axisymmetric: direction 0 = r, 1 = theta */
 
 typedef struct {
     int nd;              /* 2 or 3 */
@@ -71,6 +73,13 @@ typedef struct {
     int precond;         /* OR_PC_* */
     int sweeps;          /* weighted Jacobi sweeps of the pressure system */
     int max_halvings;    /* dt halvings after a failed Newton solve */
+    /* geometry and radiative diffusion (Sec. 2 Eqs. 2 and 4, Sec. 6) */
+    int geom;            /* OR_GEOM_* */
+    const double *gface; /* spherical: radial gravity on the n[0]+1 r-faces, else NULL */
+    int conduct;         /* add div(chi grad T), chi = chi0 T^6.5 / rho^2 */
+    double chi0;         /* 16 sigma / (3 kappa0) of the Kramers-law opacity */
+    int flux_wall[3];    /* wall faces carry the prescribed chi dT/dn = lum (/ r^2 if spherical) */
+    double lum;
 } or_grid;
 
 typedef struct {
@@ -138,24 +147,64 @@ static long or_ext_of_cell(const or_ext *X, const or_grid *g, long c)
     return or_ext_index(X, ix);
 }
 
+/* ---------------- spherical (r, theta) metric, 2 pi dropped throughout ---------------- */
+static double or_r(const or_grid *g, double i) { return g->x0[0] + i * g->dx[0]; }
+static double or_th(const or_grid *g, double j) { return g->x0[1] + j * g->dx[1]; }
+
+/* volume of cell (i, j) */
+static double or_sph_vol(const or_grid *g, int i, int j)
+{
+    double ra = or_r(g, i), rb = or_r(g, i + 1);
+    return (rb * rb * rb - ra * ra * ra) / 3.0 * (cos(or_th(g, j)) - cos(or_th(g, j + 1)));
+}
+
+/* area of the lower d-face of cell (i, j) */
+static double or_sph_area(const or_grid *g, int d, int i, int j)
+{
+    if (d == 0) {
+        double r = or_r(g, i);
+        return r * r * (cos(or_th(g, j)) - cos(or_th(g, j + 1)));
+    }
+    double ra = or_r(g, i), rb = or_r(g, i + 1);
+    return 0.5 * (rb * rb - ra * ra) * sin(or_th(g, j));
+}
+
+/* distance between the centres of the two cells that share the lower d-face
+   of cell (i, j): dr, or the arc r_c dtheta at the cell-centre radius */
+static double or_sph_h(const or_grid *g, int d, int i)
+{
+    return d == 0 ? g->dx[0] : or_r(g, i + 0.5) * g->dx[1];
+}
+
+/* radial gravity on r-face i (spherical), or the constant component */
+static double or_gface(const or_grid *g, int d, int i)
+{
+    if (g->geom == OR_GEOM_SPHERICAL && d == 0 && g->gface) return g->gface[i];
+    return g->g[d];
+}
+
 /* ---------------- R(U): real and complex-step instantiations ---------------- */
 #define FN2(a, b) a##b
 #define FN1(a, b) FN2(a, b)
 
 #define T double
 #define RE(x) (x)
+#define SQRT(x) sqrt(x)
 #define FN(name) FN1(name, _r)
 #include "residual_body.h"
 #undef T
 #undef RE
+#undef SQRT
 #undef FN
 
 #define T double complex
 #define RE(x) creal(x)
+#define SQRT(x) csqrt(x)
 #define FN(name) FN1(name, _c)
 #include "residual_body.h"
 #undef T
 #undef RE
+#undef SQRT
 #undef FN
 
 /* Eqs. 1-3: R(U) (spatial operator, no time discretisation). */
@@ -300,6 +349,137 @@ static void or_cell_coords(const or_grid *g, long c, int ix[3])
  * Jacobi, unlike red-black Gauss-Seidel on an even grid, commutes with the
  * mirror reflections of the grid, so M^-1 keeps the symmetry of Sec. 3.
  */
+/*
+ * General form of the same preconditioner for spherical grids and for grids
+ * with radiative diffusion.  With conduction, the energy row gains
+ * -tau div(chi grad dT), dT = dp / rho (coefficients frozen, the density
+ * change neglected), so the pressure problem becomes
+ *   dp/gp - tau^2 div(grad(dp)/rbar) - (tau (gamma-1)/gp) div(chi grad(dp/rho)) = b
+ * and the energy back substitution gains + tau div(chi grad(dp/rho)).  Every
+ * divergence is (1/V) sum(A F) over the cell faces; gradients divide by the
+ * distance between cell centres (dr, or r_c dtheta).
+ */
+static void or_precond_general(const or_grid *g, const double *U, double dt, const double *r, double *z)
+{
+    const int nd = g->nd;
+    const long N = or_ncells(g);
+    const double gam = g->gamma, gm1 = gam - 1.0;
+    const double tau = 0.5 * dt, tau2 = tau * tau;
+    const int sph = (g->geom == OR_GEOM_SPHERICAL);
+    double *gp = (double *)malloc(N * sizeof(double));
+    double *hp = (double *)malloc(N * sizeof(double));
+    double *rh = (double *)malloc(N * sizeof(double));
+    double *b = (double *)malloc(N * sizeof(double));
+    double *dp = (double *)calloc(N, sizeof(double));
+    double *dq = (double *)malloc(N * sizeof(double));
+    double *chi = (double *)calloc(N, sizeof(double));
+    for (long c = 0; c < N; c++) {
+        gp[c] = gam * (gm1 * U[N + c]);
+        hp[c] = gam * U[N + c];
+        rh[c] = U[c];
+        if (g->conduct) {
+            double t = gm1 * U[N + c] / U[c];
+            double t3 = t * t * t;
+            chi[c] = g->chi0 * (t3 * t3 * sqrt(t)) / (U[c] * U[c]);
+        }
+    }
+    /* per cell and direction: divergence weights W (A/V) of the lower / upper
+       face, gradient lengths h, 1/rbar and face chi (0 across walls) */
+#define IS_LW(d, ix) (g->bc[d] == OR_BC_WALL && (ix)[d] == 0)
+#define IS_UW(d, ix) (g->bc[d] == OR_BC_WALL && (ix)[d] == g->n[d] - 1)
+    double *Wm = (double *)malloc(N * 3 * sizeof(double)), *Wp = (double *)malloc(N * 3 * sizeof(double));
+    double *hm = (double *)malloc(N * 3 * sizeof(double)), *hpl = (double *)malloc(N * 3 * sizeof(double));
+    double *am = (double *)malloc(N * 3 * sizeof(double)), *ap = (double *)malloc(N * 3 * sizeof(double));
+    double *km = (double *)malloc(N * 3 * sizeof(double)), *kp = (double *)malloc(N * 3 * sizeof(double));
+    for (long c = 0; c < N; c++) {
+        int ix[3];
+        or_cell_coords(g, c, ix);
+        const double V = sph ? or_sph_vol(g, ix[0], ix[1]) : 0.0;
+        for (int d = 0; d < nd; d++) {
+            const long k = c * 3 + d;
+            if (sph) {
+                int up[3] = {ix[0], ix[1], ix[2]};
+                up[d] += 1;
+                Wm[k] = or_sph_area(g, d, ix[0], ix[1]) / V;
+                Wp[k] = or_sph_area(g, d, up[0], up[1]) / V;
+                hm[k] = hpl[k] = or_sph_h(g, d, ix[0]);
+            } else {
+                Wm[k] = Wp[k] = 1.0 / g->dx[d];
+                hm[k] = hpl[k] = g->dx[d];
+            }
+            long l = or_nb(g, ix, d, -1), u = or_nb(g, ix, d, +1);
+            am[k] = IS_LW(d, ix) ? 0.0 : 1.0 / (0.5 * (U[l] + U[c]));
+            ap[k] = IS_UW(d, ix) ? 0.0 : 1.0 / (0.5 * (U[c] + U[u]));
+            km[k] = IS_LW(d, ix) ? 0.0 : 0.5 * (chi[l] + chi[c]);
+            kp[k] = IS_UW(d, ix) ? 0.0 : 0.5 * (chi[c] + chi[u]);
+        }
+    }
+    double *D = (double *)malloc(N * sizeof(double));
+    for (long c = 0; c < N; c++) {
+        int ix[3];
+        or_cell_coords(g, c, ix);
+        double divm = 0.0, diag = 0.0, dth = 0.0;
+        for (int d = 0; d < nd; d++) {
+            const long k = c * 3 + d;
+            double rp = r[(2 + d) * N + or_nb(g, ix, d, +1)], rm = r[(2 + d) * N + c];
+            divm += Wp[k] * ap[k] * rp - Wm[k] * am[k] * rm;
+            diag += Wp[k] * ap[k] / hpl[k] + Wm[k] * am[k] / hm[k];
+            dth += Wp[k] * kp[k] / hpl[k] + Wm[k] * km[k] / hm[k];
+        }
+        b[c] = gm1 * r[N + c] / gp[c] - tau * divm;
+        D[c] = 1.0 / gp[c] + tau2 * diag + (tau * gm1 / gp[c]) * dth / rh[c];
+    }
+    const double omega = OR_JACOBI_OMEGA;
+    for (int sw = 0; sw < g->sweeps; sw++) {
+        for (long c = 0; c < N; c++) {
+            int ix[3];
+            or_cell_coords(g, c, ix);
+            double off = 0.0;
+            for (int d = 0; d < nd; d++) {
+                const long k = c * 3 + d;
+                long u = or_nb(g, ix, d, +1), l = or_nb(g, ix, d, -1);
+                off += tau2 * (Wp[k] * ap[k] / hpl[k] * dp[u] + Wm[k] * am[k] / hm[k] * dp[l]);
+                off += (tau * gm1 / gp[c]) * (Wp[k] * kp[k] / hpl[k] * dp[u] / rh[u] +
+                                              Wm[k] * km[k] / hm[k] * dp[l] / rh[l]);
+            }
+            dq[c] = (1.0 - omega) * dp[c] + omega * ((b[c] + off) / D[c]);
+        }
+        memcpy(dp, dq, N * sizeof(double));
+    }
+    /* back substitution */
+    for (int d = 0; d < nd; d++) {
+        for (long c = 0; c < N; c++) {
+            int ix[3];
+            or_cell_coords(g, c, ix);
+            if (IS_LW(d, ix))
+                z[(2 + d) * N + c] = r[(2 + d) * N + c];
+            else
+                z[(2 + d) * N + c] = r[(2 + d) * N + c] - tau * (dp[c] - dp[or_nb(g, ix, d, -1)]) / hm[c * 3 + d];
+        }
+    }
+    for (long c = 0; c < N; c++) {
+        int ix[3];
+        or_cell_coords(g, c, ix);
+        double divm = 0.0, divu = 0.0, dth = 0.0;
+        for (int d = 0; d < nd; d++) {
+            const long k = c * 3 + d;
+            long u = or_nb(g, ix, d, +1), l = or_nb(g, ix, d, -1);
+            double mp = IS_UW(d, ix) ? 0.0 : z[(2 + d) * N + u];
+            double mm = IS_LW(d, ix) ? 0.0 : z[(2 + d) * N + c];
+            divm += Wp[k] * mp - Wm[k] * mm;
+            divu += Wp[k] * ap[k] * mp - Wm[k] * am[k] * mm;
+            dth += Wp[k] * kp[k] * (dp[u] / rh[u] - dp[c] / rh[c]) / hpl[k] -
+                   Wm[k] * km[k] * (dp[c] / rh[c] - dp[l] / rh[l]) / hm[k];
+        }
+        z[c] = r[c] - tau * divm;
+        z[N + c] = (r[N + c] - tau * hp[c] * divu) + tau * dth;
+    }
+#undef IS_LW
+#undef IS_UW
+    free(gp); free(hp); free(rh); free(b); free(dp); free(dq); free(chi); free(D);
+    free(Wm); free(Wp); free(hm); free(hpl); free(am); free(ap); free(km); free(kp);
+}
+
 void or_precond(const or_grid *g, const double *U, double dt, const double *r, double *z)
 {
     const int nd = g->nd;
@@ -307,6 +487,10 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
     const long n = (long)or_nvars(g) * N;
     if (g->precond == OR_PC_NONE) {
         memcpy(z, r, n * sizeof(double));
+        return;
+    }
+    if (g->geom == OR_GEOM_SPHERICAL || g->conduct) {
+        or_precond_general(g, U, dt, r, z);
         return;
     }
     const double gam = g->gamma, gm1 = gam - 1.0;
@@ -658,7 +842,8 @@ double or_cfl_rate(const or_grid *g, const double *U)
                 long r = or_nb(g, ix, d, +1);
                 up = U[(2 + d) * N + r] / (0.5 * (rho + U[r]));
             }
-            double q = (fabs(0.5 * (um + up)) + cs) / g->dx[d];
+            double h = (g->geom == OR_GEOM_SPHERICAL) ? or_sph_h(g, d, ix[0]) : g->dx[d];
+            double q = (fabs(0.5 * (um + up)) + cs) / h;
             if (q > lam) lam = q;
         }
     }

@@ -30,6 +30,8 @@ class OrGrid(ctypes.Structure):
         ("restart", ctypes.c_int), ("max_restarts", ctypes.c_int), ("gmres_rtol", ctypes.c_double),
         ("newton_max", ctypes.c_int), ("newton_tol", ctypes.c_double), ("precond", ctypes.c_int),
         ("sweeps", ctypes.c_int), ("max_halvings", ctypes.c_int),
+        ("geom", ctypes.c_int), ("gface", ctypes.POINTER(ctypes.c_double)), ("conduct", ctypes.c_int),
+        ("chi0", ctypes.c_double), ("flux_wall", ctypes.c_int * 3), ("lum", ctypes.c_double),
     ]
 
 
@@ -116,6 +118,16 @@ def grid(prob) -> OrGrid:
     g.precond = int(prob.precond)
     g.sweeps = int(prob.sweeps)
     g.max_halvings = int(prob.max_halvings)
+    g.geom = int(prob.geometry)
+    if prob.gface is not None:
+        gf = np.ascontiguousarray(prob.gface, dtype=np.float64)
+        g._keep = gf  # keep the table alive as long as the struct
+        g.gface = gf.ctypes.data_as(_dbl_p)
+    g.conduct = int(prob.conduct)
+    g.chi0 = float(prob.chi0)
+    for d in range(3):
+        g.flux_wall[d] = int(prob.flux_wall[d])
+    g.lum = float(prob.lum)
     return g
 
 

@@ -10,11 +10,17 @@
  * What it computes (Sec. 2 of the paper, Eqs. 1-3, staggered grid with
  * upstream linear reconstruction and the van Leer limiter):
  *   R_rho = -div(rho u)
- *   R_E   = -div(rho e u) - p div(u)            (E = rho e, internal energy)
+ *   R_E   = -div(rho e u) - p div(u) + div(chi grad T)   (E = rho e)
  *   R_m   = -div(rho u (x) u) - grad p + rho g  (m_d on d-faces)
- * Thermal diffusion (the div(chi grad T) term) is not part of this operator.
+ * with T = (gamma - 1) e and the photon conductivity chi = 16 sigma T^3 /
+ * (3 kappa rho) of Sec. 2 for a Kramers opacity kappa = kappa0 rho T^-3.5,
+ * i.e. chi = chi0 T^6.5 / rho^2 (conduction only when g->conduct).
+ * Cartesian grids, or 2-D axisymmetric spherical (r, theta) grids where every
+ * divergence is (1/V) sum(A F) over the faces of the control volume and the
+ * momentum equations carry the geometric terms +rho u_theta^2 / r (radial)
+ * and -rho u_r u_theta / r (polar).
  *
- * Required macros: T, RE(x) (real part), FN(name) (name mangling).
+ * Required macros: T, RE(x) (real part), SQRT(x), FN(name) (name mangling).
  */
 
 /* van Leer limited slope from the two one-sided differences a, b. */
@@ -61,6 +67,13 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
         }
     }
     T *Erho = (T *)calloc(M, sizeof(T)); /* E on the extended grid */
+    T *Tt = NULL, *chi = NULL, *Gc[3] = {NULL, NULL, NULL};
+    if (g->conduct) {
+        Tt = (T *)calloc(M, sizeof(T));
+        chi = (T *)calloc(M, sizeof(T));
+        for (int d = 0; d < nd; d++) Gc[d] = (T *)calloc(M, sizeof(T));
+    }
+    const int sph = (g->geom == OR_GEOM_SPHERICAL);
 
     const double gm1 = g->gamma - 1.0;
 
@@ -108,7 +121,7 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
                 T T0 = gm1 * Erho[s0] / rho[s0];
                 T T1 = gm1 * Erho[s1] / rho[s1];
                 T Tg = 2.0 * T0 - T1;
-                double hs = 0.5 * g->dx[d] * g->g[d];
+                double hs = 0.5 * g->dx[d] * or_gface(g, d, lower ? 0 : g->n[d]);
                 T rg = lower ? rho[s0] * (T0 - hs) / (Tg + hs)
                              : rho[s0] * (T0 + hs) / (Tg - hs);
                 rho[x] = rg;
@@ -119,6 +132,38 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
     for (long x = 0; x < M; x++) {
         e[x] = Erho[x] / rho[x];
         p[x] = gm1 * Erho[x];
+    }
+    if (g->conduct) {
+        /* temperature and conductivity per cell; gradient flux chi dT/dn on
+           every d-face (arithmetic mean of the two cells' chi); wall faces
+           carry the prescribed flux or none */
+        for (long x = 0; x < M; x++) {
+            Tt[x] = gm1 * e[x];
+            T t3 = Tt[x] * Tt[x] * Tt[x];
+            chi[x] = g->chi0 * (t3 * t3 * SQRT(Tt[x])) / (rho[x] * rho[x]);
+        }
+        for (int d = 0; d < nd; d++) {
+            const long s = X.stride[d];
+            for (long x = 0; x < M; x++) {
+                int ix[3];
+                or_ext_coords(&X, x, ix);
+                if (!or_ext_has(&X, ix, d, -1)) continue;
+                if (g->bc[d] == OR_BC_WALL && (ix[d] == 0 || ix[d] == g->n[d])) {
+                    double G = 0.0;
+                    if (g->flux_wall[d]) {
+                        G = g->lum;
+                        if (sph && d == 0) {
+                            double rf = or_r(g, ix[0]);
+                            G = G / (rf * rf);
+                        }
+                    }
+                    Gc[d][x] = G;
+                    continue;
+                }
+                double h = sph ? or_sph_h(g, d, ix[0]) : g->dx[d];
+                Gc[d][x] = 0.5 * (chi[x - s] + chi[x]) * (Tt[x] - Tt[x - s]) / h;
+            }
+        }
     }
 
     /* --- face velocities: interior faces from m / (mean of the two cells) --- */
@@ -239,7 +284,7 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
     }
 
     /* --- residual assembly on the interior --- */
-    for (long c = 0; c < N; c++) {
+    for (long c = 0; c < N && !sph; c++) {
         long x = or_ext_of_cell(&X, g, c);
         int ix[3];
         or_ext_coords(&X, x, ix);
@@ -252,6 +297,14 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
         }
         R[c] = -accr;
         R[N + c] = -acce - p[x] * divu;
+        if (g->conduct) {
+            T cond = 0.0;
+            for (int d = 0; d < nd; d++) {
+                const long s = X.stride[d];
+                cond += (Gc[d][x + s] - Gc[d][x]) / g->dx[d];
+            }
+            R[N + c] = R[N + c] + cond;
+        }
         for (int d = 0; d < nd; d++) {
             if (g->bc[d] == OR_BC_WALL && ix[d] == 0) {
                 R[(2 + d) * N + c] = 0.0;
@@ -269,8 +322,61 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
             R[(2 + d) * N + c] = (-acc - (p[x] - p[x - s]) / g->dx[d]) + rbar * g->g[d];
         }
     }
+    /* spherical (r, theta): area-weighted divergences over each control volume */
+    for (long c = 0; c < N && sph; c++) {
+        long x = or_ext_of_cell(&X, g, c);
+        int ix[3];
+        or_ext_coords(&X, x, ix);
+        const int i = ix[0], j = ix[1];
+        const long s0 = X.stride[0], s1 = X.stride[1];
+        const double V = or_sph_vol(g, i, j);
+        const double Arm = or_sph_area(g, 0, i, j), Arp = or_sph_area(g, 0, i + 1, j);
+        const double Atm = or_sph_area(g, 1, i, j), Atp = or_sph_area(g, 1, i, j + 1);
+        T fr = (Arp * Frho[0][x + s0] - Arm * Frho[0][x]) + (Atp * Frho[1][x + s1] - Atm * Frho[1][x]);
+        T fe = (Arp * FE[0][x + s0] - Arm * FE[0][x]) + (Atp * FE[1][x + s1] - Atm * FE[1][x]);
+        T du = (Arp * uf[0][x + s0] - Arm * uf[0][x]) + (Atp * uf[1][x + s1] - Atm * uf[1][x]);
+        R[c] = -fr / V;
+        R[N + c] = -fe / V - p[x] * (du / V);
+        if (g->conduct) {
+            T cd = (Arp * Gc[0][x + s0] - Arm * Gc[0][x]) + (Atp * Gc[1][x + s1] - Atm * Gc[1][x]);
+            R[N + c] = R[N + c] + cd / V;
+        }
+        const double ctj = cos(or_th(g, j)), ctj1 = cos(or_th(g, j + 1));
+        /* radial momentum on r-face i: control volume r_{i-1/2}..r_{i+1/2} */
+        if (g->bc[0] == OR_BC_WALL && i == 0) {
+            R[2 * N + c] = 0.0;
+        } else {
+            const double rm = or_r(g, i - 0.5), rp = or_r(g, i + 0.5), rf = or_r(g, i);
+            const double Vr = (rp * rp * rp - rm * rm * rm) / 3.0 * (ctj - ctj1);
+            const double Acp = rp * rp * (ctj - ctj1), Acm = rm * rm * (ctj - ctj1);
+            const double Em = 0.5 * (rp * rp - rm * rm) * sin(or_th(g, j));
+            const double Ep = 0.5 * (rp * rp - rm * rm) * sin(or_th(g, j + 1));
+            T acc = (Acp * Phi[0][x] - Acm * Phi[0][x - s0]) + (Ep * Psi[0][1][x + s1] - Em * Psi[0][1][x]);
+            T rbar = 0.5 * (rho[x - s0] + rho[x]);
+            T ut = 0.25 * ((uf[1][x - s0] + uf[1][x]) + (uf[1][x - s0 + s1] + uf[1][x + s1]));
+            R[2 * N + c] = ((-acc / Vr - (p[x] - p[x - s0]) / g->dx[0]) + rbar * ut * ut / rf) +
+                           rbar * or_gface(g, 0, i);
+        }
+        /* polar momentum on theta-face j: control volume theta_{j-1/2}..theta_{j+1/2} */
+        if (g->bc[1] == OR_BC_WALL && j == 0) {
+            R[3 * N + c] = 0.0;
+        } else {
+            const double ra = or_r(g, i), rb = or_r(g, i + 1), rc = or_r(g, i + 0.5);
+            const double cm = cos(or_th(g, j - 0.5)), cp = cos(or_th(g, j + 0.5));
+            const double Vt = (rb * rb * rb - ra * ra * ra) / 3.0 * (cm - cp);
+            const double Bp = 0.5 * (rb * rb - ra * ra) * sin(or_th(g, j + 0.5));
+            const double Bm = 0.5 * (rb * rb - ra * ra) * sin(or_th(g, j - 0.5));
+            const double Fa = ra * ra * (cm - cp), Fb = rb * rb * (cm - cp);
+            T acc = (Fb * Psi[1][0][x + s0] - Fa * Psi[1][0][x]) + (Bp * Phi[1][x] - Bm * Phi[1][x - s1]);
+            T rbar = 0.5 * (rho[x - s1] + rho[x]);
+            T ur = 0.25 * ((uf[0][x - s1] + uf[0][x]) + (uf[0][x - s1 + s0] + uf[0][x + s0]));
+            R[3 * N + c] = ((-acc / Vt - (p[x] - p[x - s1]) / (rc * g->dx[1])) - rbar * ur * uf[1][x] / rc) +
+                           rbar * g->g[1];
+        }
+    }
 
-    free(rho); free(e); free(p); free(Erho);
+    free(rho); free(e); free(p); free(Erho); free(Tt); free(chi);
+    for (int d = 0; d < nd; d++) free(Gc[d]);
     for (int d = 0; d < nd; d++) {
         free(uf[d]); free(srho[d]); free(se[d]); free(Frho[d]); free(FE[d]); free(Phi[d]);
         for (int q = 0; q < nd; q++) { free(su[d][q]); free(Psi[d][q]); }

@@ -43,6 +43,8 @@ WALL_MIRROR = 0
 WALL_HSE = 1
 PC_NONE = 0
 PC_ACOUSTIC = 1
+GEOM_CARTESIAN = 0
+GEOM_SPHERICAL = 1
 
 
 @dataclasses.dataclass
@@ -72,6 +74,13 @@ class Problem:
     max_halvings: int = 4
     rho_L: float = 1.0   # light / heavy densities for the mixing height
     rho_H: float = 2.0
+    # geometry and radiative diffusion
+    geometry: int = GEOM_CARTESIAN      # GEOM_SPHERICAL: 2-D (r, theta), direction 0 = r
+    gface: Optional[np.ndarray] = None  # radial gravity on the n[0]+1 r-faces (spherical)
+    conduct: int = 0                    # div(chi grad T) with chi = chi0 T^6.5 / rho^2
+    chi0: float = 0.0
+    flux_wall: tuple = (0, 0, 0)        # walls with the prescribed flux chi dT/dn = lum (/ r^2)
+    lum: float = 0.0
 
     @property
     def ncells(self) -> int:
@@ -267,3 +276,124 @@ def config_problem(index: int, **kw) -> Problem:
     if index == 2:
         return taylor_green(**kw)
     raise ValueError(index)
+
+
+# ------------------------------------------------------------ spherical wedge
+def lane_emden(n: float = 3.0, h: float = 1e-4):
+    """Lane-Emden solution theta(xi) of index n by classical RK4 (series start
+    at small xi).  Returns (xi, theta, dtheta) arrays up to the first zero and
+    the zero xi_1 (interpolated)."""
+    def f(x, y):
+        return np.array([y[1], -y[0] ** n - 2.0 * y[1] / x]) if y[0] > 0 else np.array([y[1], -2.0 * y[1] / x])
+    x = 1e-6
+    y = np.array([1.0 - x * x / 6.0, -x / 3.0])
+    xs, ts, ds = [0.0], [1.0], [0.0]
+    while y[0] > 0:
+        k1 = f(x, y)
+        k2 = f(x + h / 2, y + h / 2 * k1)
+        k3 = f(x + h / 2, y + h / 2 * k2)
+        k4 = f(x + h, y + h * k3)
+        yn = y + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        if yn[0] <= 0:
+            frac = y[0] / (y[0] - yn[0])
+            xi1 = x + frac * h
+            xs.append(xi1)
+            ts.append(0.0)
+            ds.append(y[1] + frac * (yn[1] - y[1]))
+            return np.array(xs), np.array(ts), np.array(ds), xi1
+        x += h
+        y = yn
+        xs.append(x)
+        ts.append(y[0])
+        ds.append(y[1])
+
+
+def spherical_wedge(nr: int = 256, nth: int = 128, seed: int = 5, noise: float = 1e-6, cfl: float = 100.0,
+                    nsteps: int = 500, cfl_rad: float = 500.0, gamma: float = 5.0 / 3.0) -> Problem:
+    """2-D spherical-wedge radiative hydrostatic test (Sec. 6 setup, polytrope
+    background in code units).
+
+    A Lane-Emden n = 3 polytrope with central density and temperature 1
+    (p = rho T, G = 1, so K = 1 and the length unit alpha = 1/sqrt(pi))
+    gives the radial gravity g(r) = -M(r)/r^2 on the r-faces and seeds the
+    first cell.  Outward from there each cell is set so that the discrete
+    balance across the face between it and the previous cell holds exactly:
+    p_j - p_{j-1} = dr g_f (rho_j + rho_{j-1})/2 (hydrostatic) and
+    r_f^2 chi_f (T_j - T_{j-1})/dr = Lambda (constant luminosity), chi_f the
+    mean of the two cells' chi = chi0 T^6.5/rho^2, Lambda from the
+    polytrope's temperature gradient at the first face.  chi0 makes the
+    radiative CFL number max(D dt / dx^2), D = chi/(rho c_v), equal cfl_rad
+    at dt = cfl x the acoustic limit on the polytrope.  Domain r in
+    [0.1, 0.9] R, theta in [pi/4, 3 pi/4] (periodic); radial walls with
+    hydrostatic ghosts and the prescribed flux Lambda/r^2; relative density
+    noise of 1e-6 (Philox, seed 5); fluid at rest.
+    """
+    xs, ts, ds, xi1 = lane_emden(3.0)
+    alpha = 1.0 / math.sqrt(math.pi)
+    R = xi1 * alpha
+    r0, r1 = 0.1 * R, 0.9 * R
+    th0, th1 = math.pi / 4, 3 * math.pi / 4
+    dr, dth = (r1 - r0) / nr, (th1 - th0) / nth
+
+    def poly(r):
+        xi = r / alpha
+        t = np.interp(xi, xs, ts)
+        dt_ = np.interp(xi, xs, ds)
+        return t, dt_
+
+    rf = r0 + np.arange(nr + 1) * dr
+    tf, dtf = poly(rf)
+    xi_f = rf / alpha
+    mass = 4 * math.pi * alpha ** 3 * (-(xi_f ** 2) * dtf)
+    gface = -mass / rf ** 2
+    rc = r0 + (np.arange(nr) + 0.5) * dr
+    tc, _ = poly(rc)
+    rho_p, T_p = tc ** 3, tc
+    cv = 1.0 / (gamma - 1.0)
+    cs = np.sqrt(gamma * T_p)
+    h_min = np.minimum(dr, rc * dth)
+    dt_ac = cfl / np.max(cs / h_min)
+    D_over = T_p ** 6.5 / rho_p ** 2 / (rho_p * cv) / h_min ** 2
+    chi0 = cfl_rad / (dt_ac * np.max(D_over))
+
+    def chi(rho, T):
+        return chi0 * T ** 6.5 / rho ** 2
+
+    # Lambda from the polytrope's temperature gradient at the first interior face
+    t1, dt1 = poly(rf[1])
+    Lam = rf[1] ** 2 * chi(t1 ** 3, t1) * dt1 / alpha
+    rho = np.empty(nr)
+    T = np.empty(nr)
+    rho[0], T[0] = rho_p[0], T_p[0]
+    for j in range(1, nr):
+        gf, r_ = gface[j], rf[j]
+        x = np.array([rho_p[j] / rho_p[j - 1] * rho[j - 1], T[j - 1] + Lam * dr / (r_ ** 2 * chi(rho[j - 1], T[j - 1]))])
+        for _ in range(60):
+            ro, Tn = x
+            f1 = ro * Tn - rho[j - 1] * T[j - 1] - dr * gf * (ro + rho[j - 1]) / 2
+            cf = 0.5 * (chi(ro, Tn) + chi(rho[j - 1], T[j - 1]))
+            f2 = r_ ** 2 * cf * (Tn - T[j - 1]) / dr - Lam
+            dcr = 0.5 * chi(ro, Tn) * (-2.0 / ro)
+            dct = 0.5 * chi(ro, Tn) * (6.5 / Tn)
+            J = np.array([[Tn - dr * gf / 2, ro],
+                          [r_ ** 2 * dcr * (Tn - T[j - 1]) / dr, r_ ** 2 * (dct * (Tn - T[j - 1]) + cf) / dr]])
+            step = np.linalg.solve(J, -np.array([f1, f2]))
+            x = x + step
+            if np.all(np.abs(step) <= 1e-15 * np.abs(x)):
+                break
+        rho[j], T[j] = x
+    if np.any(rho <= 0) or np.any(T <= 0):
+        raise RuntimeError("radiative-equilibrium march left the physical range")
+    shape = (nr, nth, 1)
+    rho2 = np.repeat(rho[None, :], nth, axis=0)
+    T2 = np.repeat(T[None, :], nth, axis=0)
+    rng = np.random.Generator(np.random.Philox(seed))
+    rho2 = rho2 * (1.0 + noise * rng.uniform(-1.0, 1.0, size=rho2.shape))
+    # the noise perturbs density at fixed pressure (temperature compensates)
+    E = (rho[None, :] * T[None, :]).repeat(nth, axis=0) / (gamma - 1.0)
+    z = np.zeros_like(rho2)
+    U = _pack(2, rho2.reshape(1, nth, nr), E.reshape(1, nth, nr), [z.reshape(1, nth, nr), z.reshape(1, nth, nr)])
+    return Problem("spherical_wedge", 2, shape, (r0, th0, 0.0), (r1 - r0, th1 - th0, 1.0),
+                   (BC_WALL, BC_PERIODIC, BC_PERIODIC), (WALL_HSE, WALL_MIRROR, WALL_MIRROR), gamma,
+                   (0.0, 0.0, 0.0), U, cfl=cfl, nsteps=nsteps, geometry=GEOM_SPHERICAL, gface=gface,
+                   conduct=1, chi0=float(chi0), flux_wall=(1, 0, 0), lum=float(Lam))
