@@ -114,6 +114,9 @@ WORKLOADS = {
                  lambda I, r: I.rayleigh_taylor()),
     "tgv128": ("Taylor-Green vortex 3-D, 128^3 periodic, CFL 20, Newton tol 1e-8, GMRES(30)",
                lambda I, r: I.taylor_green(n=128)),
+    "wedge256": ("2-D spherical wedge 256 (r) x 128 (theta), radiative diffusion, polytrope n=3 background, "
+                 "dt = 100x acoustic CFL, Newton tol 1e-8, GMRES(30)",
+                 lambda I, r: I.spherical_wedge(seed=5 + r)),
 }
 
 
@@ -195,6 +198,7 @@ def run_music(args):
         fp64_value = ws * N * args.steps / (result["fp64"]["total_ms"] / 1e3)
 
     roof = roofline_jv(mixed, prob)
+    final_diag = mixed["grid"].diagnostics()
     e2e = end_to_end(mixed["grid"], prob, stream, max(2, min(args.steps, 5)))
     for r in result.values():
         r["grid"].close()
@@ -235,6 +239,8 @@ def run_music(args):
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clocks"],
         "serving": serving,
+        "final_diagnostics": final_diag,
+        "sim_time": float(sum(x["dt"] for x in mixed["stats"])),
     }
     print(json.dumps(line))
 

@@ -65,6 +65,7 @@ enum { MUSIC_BC_PERIODIC = 0, MUSIC_BC_WALL = 1 };
 enum { MUSIC_WALL_MIRROR = 0, MUSIC_WALL_HSE_LINEAR_T = 1 };
 enum { MUSIC_FP64 = 0, MUSIC_MIXED = 1 };
 enum { MUSIC_PC_NONE = 0, MUSIC_PC_ACOUSTIC = 1 };
+enum { MUSIC_GEOM_CARTESIAN = 0, MUSIC_GEOM_SPHERICAL = 1 };
 
 /* Grid, physics and solver description (copied by music_create_grid). */
 typedef struct {
@@ -86,6 +87,19 @@ typedef struct {
     int precond;              /* MUSIC_PC_* [ACOUSTIC]; pass -1 for NONE */
     int precond_sweeps;       /* weighted-Jacobi sweeps of the pressure system [16] */
     int max_dt_halvings;      /* retries of a failed step at dt/2 [4] */
+    /* geometry and radiative diffusion (Sec. 2 Eq. 2 and the photon
+       conductivity; Sec. 6) */
+    int geometry;             /* MUSIC_GEOM_*; SPHERICAL is 2-D axisymmetric with
+                                 direction 0 = r (walls), 1 = theta, origin and
+                                 length in (r, theta) */
+    const double *g_radial;   /* SPHERICAL: host array of the radial gravity on the
+                                 n[0]+1 r-faces (copied at creation); NULL: g[0] */
+    int conduct;              /* 1: add div(chi grad T), T = (gamma-1) e,
+                                 chi = chi0 T^6.5 / rho^2 (Kramers opacity) */
+    double chi0;
+    int flux_wall[3];         /* 1: this direction's wall faces carry the prescribed
+                                 chi dT/dn = lum (spherical r-walls: lum / r^2) */
+    double lum;
 } music_grid_desc;
 
 typedef struct {

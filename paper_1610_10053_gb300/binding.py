@@ -38,6 +38,8 @@ class GridDesc(ctypes.Structure):
         ("gmres_restart", ctypes.c_int), ("gmres_max_restarts", ctypes.c_int),
         ("gmres_rtol", ctypes.c_double), ("newton_max_its", ctypes.c_int), ("newton_tol", ctypes.c_double),
         ("precond", ctypes.c_int), ("precond_sweeps", ctypes.c_int), ("max_dt_halvings", ctypes.c_int),
+        ("geometry", ctypes.c_int), ("g_radial", ctypes.POINTER(ctypes.c_double)), ("conduct", ctypes.c_int),
+        ("chi0", ctypes.c_double), ("flux_wall", ctypes.c_int * 3), ("lum", ctypes.c_double),
     ]
 
 
@@ -154,6 +156,17 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
     d.precond = 1 if int(prob.precond) == 1 else -1
     d.precond_sweeps = int(prob.sweeps)
     d.max_dt_halvings = int(prob.max_halvings)
+    d.geometry = int(getattr(prob, "geometry", 0))
+    gf = getattr(prob, "gface", None)
+    if gf is not None:
+        gf = np.ascontiguousarray(gf, dtype=np.float64)
+        d._keep = gf  # the library copies the table at creation
+        d.g_radial = gf.ctypes.data_as(_dbl_p)
+    d.conduct = int(getattr(prob, "conduct", 0))
+    d.chi0 = float(getattr(prob, "chi0", 0.0))
+    for k in range(3):
+        d.flux_wall[k] = int(getattr(prob, "flux_wall", (0, 0, 0))[k])
+    d.lum = float(getattr(prob, "lum", 0.0))
     for k, v in over.items():
         setattr(d, k, v)
     return d

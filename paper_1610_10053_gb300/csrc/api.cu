@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -81,6 +82,21 @@ int validate(const music_grid_desc &d)
         set_error("invalid solver options");
         return MUSIC_E_INVAL;
     }
+    if (d.geometry != MUSIC_GEOM_CARTESIAN && d.geometry != MUSIC_GEOM_SPHERICAL) {
+        set_error("geometry %d unknown", d.geometry);
+        return MUSIC_E_INVAL;
+    }
+    if (d.geometry == MUSIC_GEOM_SPHERICAL) {
+        if (d.ndim != 2 || d.bc[0] != MUSIC_BC_WALL || !(d.origin[0] > 0.0) || !(d.origin[1] > 0.0) ||
+            !(d.origin[1] + d.length[1] < 3.14159265358979323846)) {
+            set_error("spherical grids are 2-D with walls in r, r > 0 and 0 < theta < pi");
+            return MUSIC_E_INVAL;
+        }
+    }
+    if (d.conduct && !(d.chi0 >= 0.0)) {
+        set_error("chi0 must be >= 0");
+        return MUSIC_E_INVAL;
+    }
     return MUSIC_OK;
 }
 
@@ -112,6 +128,12 @@ GridParams make_params(const music_grid_desc &d)
     P.M = P.es[2] * P.ne[2];
     P.gamma = d.gamma;
     P.gm1 = d.gamma - 1.0;
+    P.geom = d.geometry;
+    P.conduct = d.conduct ? 1 : 0;
+    P.chi0 = d.chi0;
+    P.lum = d.lum;
+    for (int k = 0; k < 3; k++) P.flux_wall[k] = (k < d.ndim && d.bc[k] == MUSIC_BC_WALL) ? d.flux_wall[k] : 0;
+    P.gface = nullptr;
     return P;
 }
 
@@ -130,11 +152,21 @@ void alloc_plan(music_grid *g, F &&f)
     if (d.precond != MUSIC_PC_NONE) {
         for (int k = 0; k < P.nd; k++) f(&g->pa[k], N * ks);
         for (void **p : {&g->pgp, &g->php, &g->pD, &g->pb, &g->pdp, &g->pdq}) f(p, N * ks);
+        if (general_grid(P)) {
+            f(&g->prh, N * ks);
+            for (int k = 0; k < P.nd; k++) f(&g->pkf[k], N * ks);
+        }
     }
-    // the multi-pass stencil (3-D, or 2-D on request) keeps its planes on the
-    // ghosted grid; the fused 2-D kernels need none of them
-    if (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS) {
+    if (P.geom == MUSIC_GEOM_SPHERICAL) f((void **)&g->gface, (size_t)(P.n[0] + 1) * sizeof(double));
+    // the multi-pass stencil (3-D, spherical, conducting, or 2-D on request)
+    // keeps its planes on the ghosted grid; the fused 2-D kernels need none
+    if (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS || general_grid(P)) {
         ExtScratch &X = g->ext;
+        if (P.conduct) {
+            f((void **)&X.Tt, M * sizeof(double));
+            f((void **)&X.chi, M * sizeof(double));
+            for (int k = 0; k < P.nd; k++) f((void **)&X.Gc[k], M * sizeof(double));
+        }
         for (double **p : {&X.rho, &X.e, &X.p}) f((void **)p, M * sizeof(double));
         for (int k = 0; k < P.nd; k++) {
             for (double **p : {&X.uf[k], &X.srho[k], &X.se[k], &X.Frho[k], &X.FE[k], &X.Phi[k]})
@@ -263,6 +295,20 @@ int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out
             fail = 1;
         }
     });
+    if (!fail && g->gface) {
+        // radial gravity on the r-faces: the table given, else the constant g[0]
+        std::vector<double> tab(g->P.n[0] + 1, d.g[0]);
+        if (d.g_radial)
+            for (int i = 0; i <= g->P.n[0]; i++) tab[i] = d.g_radial[i];
+        if (cudaMemcpyAsync(g->gface, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice, home) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(home) != cudaSuccess) {
+            cudaGetLastError();
+            fail = 1;
+        }
+        g->P.gface = g->gface;
+    }
+    g->desc.g_radial = nullptr;  // copied; the caller's array is not retained
     if (!fail && cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {
         cudaGetLastError();
         g->hs = nullptr;

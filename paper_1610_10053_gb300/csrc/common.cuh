@@ -23,7 +23,41 @@ struct GridParams {
     int bc[3], ws[3];
     double gamma, gm1;
     double g[3];
+    int geom;              // MUSIC_GEOM_*
+    int conduct;
+    double chi0, lum;
+    int flux_wall[3];
+    const double *gface;   // spherical: radial gravity on the n[0]+1 r-faces (device), or null
 };
+
+// ---- spherical (r, theta) metric, 2 pi dropped (2-D axisymmetric grids)
+__host__ __device__ inline double sph_r(const GridParams &P, double i) { return P.x0[0] + i * P.dx[0]; }
+__host__ __device__ inline double sph_th(const GridParams &P, double j) { return P.x0[1] + j * P.dx[1]; }
+__device__ inline double sph_vol(const GridParams &P, int i, int j)
+{
+    const double ra = sph_r(P, i), rb = sph_r(P, i + 1);
+    return (rb * rb * rb - ra * ra * ra) / 3.0 * (cos(sph_th(P, j)) - cos(sph_th(P, j + 1)));
+}
+// area of the lower d-face of cell (i, j)
+__device__ inline double sph_area(const GridParams &P, int d, int i, int j)
+{
+    if (d == 0) {
+        const double r = sph_r(P, i);
+        return r * r * (cos(sph_th(P, j)) - cos(sph_th(P, j + 1)));
+    }
+    const double ra = sph_r(P, i), rb = sph_r(P, i + 1);
+    return 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j));
+}
+// distance between the centres of the two cells sharing a d-face of column i
+__device__ inline double sph_h(const GridParams &P, int d, int i)
+{
+    return d == 0 ? P.dx[0] : sph_r(P, i + 0.5) * P.dx[1];
+}
+// gravity on d-face i (radial table for spherical r-faces)
+__device__ inline double face_g(const GridParams &P, int d, int i)
+{
+    return (P.geom == MUSIC_GEOM_SPHERICAL && d == 0 && P.gface) ? P.gface[i] : P.g[d];
+}
 
 // Scalars produced and consumed on the device.
 struct DevScalars {

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(BS) k_rows(GridParams P, const double *U, doub
             u2 += uc * uc;
             const double rbar = lower_wall(P, ix, d) ? 0.0 : 0.5 * (U[cell_nb(P, ix, d, -1)] + rho);
             s[1] += 0.5 * rbar * um * um;
-            const double q = (fabs(uc) + cs) * P.idx[d];
+            const double q = (P.geom == MUSIC_GEOM_SPHERICAL) ? (fabs(uc) + cs) / sph_h(P, d, ix[0])
+                                                              : (fabs(uc) + cs) * P.idx[d];
             s[7] = nanmax(s[7], q);
             if (d == 1) {
                 s[2] += 0.5 * rbar * um * um * dV;

@@ -19,10 +19,14 @@ struct ExtScratch {
     double *rho, *e, *p;
     double *uf[3], *srho[3], *se[3], *Frho[3], *FE[3], *Phi[3];
     double *su[3][3], *Psi[3][3];
+    double *Tt, *chi, *Gc[3];  // radiative diffusion: T, chi per cell, chi dT/dn per face
 };
 
 enum StencilVariant { STENCIL_AUTO = 0, STENCIL_FUSED = 1, STENCIL_MULTIPASS = 2 };
 enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
+
+// grids that need the general (geometry / conduction) code paths
+inline bool general_grid(const GridParams &P) { return P.geom == MUSIC_GEOM_SPHERICAL || P.conduct; }
 
 struct music_grid {
     music_grid_desc desc;
@@ -41,6 +45,8 @@ struct music_grid {
     void *V, *w, *z, *u;
     // preconditioner (float for mixed, double otherwise)
     void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
+    void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
+    double *gface;         // spherical: radial gravity on the r-faces
     ExtScratch ext;
     double *partials;      // [MUSIC_MAXV][nb]
     DevScalars *ds;        // device scalars

@@ -374,11 +374,256 @@ int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, c
     return launch_pc_fused2d<PT, 16>(g, dt, r, z, want_norm, s);
 }
 
+
+// ---------------------------------------------------------------- general form
+// Spherical grids and grids with radiative diffusion: every divergence is a
+// weighted sum W = A/V over the cell's faces (1/dx on Cartesian grids),
+// gradients divide by the distance h between cell centres, and the energy
+// row gains -tau div(chi grad dT) with dT = dp / rho (coefficients frozen,
+// the density change neglected).  Pressure problem:
+//   dp/gp - tau^2 div(grad(dp)/rbar) - (tau (gamma-1)/gp) div(chi grad(dp/rho)) = b.
+struct Geo {
+    double Wm, Wp, h;  // weights of the lower / upper d-face, centre distance
+};
+
+__device__ inline Geo geo(const GridParams &P, const int ix[3], int d)
+{
+    Geo o;
+    if (P.geom == MUSIC_GEOM_SPHERICAL) {
+        const double V = sph_vol(P, ix[0], ix[1]);
+        o.Wm = sph_area(P, d, ix[0], ix[1]) / V;
+        o.Wp = sph_area(P, d, ix[0] + (d == 0), ix[1] + (d == 1)) / V;
+        o.h = sph_h(P, d, ix[0]);
+    } else {
+        o.Wm = o.Wp = P.idx[d];
+        o.h = P.dx[d];
+    }
+    return o;
+}
+
+template <typename PT>
+struct PCG {
+    PT *a[3], *kf[3];  // 1/rbar and mean chi on the lower d-face (0 on walls)
+    PT *gp, *hp, *rh, *D;
+    PT *chi;           // cell chi (scratch during setup)
+};
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_gen_cell(GridParams P, const double *U, PCG<PT> C)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        const double rho = U[c], E = U[P.N + c];
+        C.gp[c] = (PT)(P.gamma * (P.gm1 * E));
+        C.hp[c] = (PT)(P.gamma * E);
+        C.rh[c] = (PT)rho;
+        double chi = 0.0;
+        if (P.conduct) {
+            const double t = P.gm1 * E / rho;
+            const double t3 = t * t * t;
+            chi = P.chi0 * (t3 * t3 * sqrt(t)) / (rho * rho);
+        }
+        C.chi[c] = (PT)chi;
+        for (int d = 0; d < P.nd; d++) {
+            if (lower_wall(P, ix, d)) {
+                C.a[d][c] = (PT)0;
+            } else {
+                const long long l = cell_nb(P, ix, d, -1);
+                C.a[d][c] = (PT)(1.0 / (0.5 * (U[l] + U[c])));
+            }
+        }
+    }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_gen_face(GridParams P, PCG<PT> C, double tau)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        for (int d = 0; d < P.nd; d++)
+            C.kf[d][c] = lower_wall(P, ix, d) ? (PT)0 : (PT)(0.5 * ((double)C.chi[cell_nb(P, ix, d, -1)] + (double)C.chi[c]));
+    }
+}
+
+template <typename PT>
+__device__ inline void up_coeffs(const GridParams &P, const PCG<PT> &C, const int ix[3], int d, long long &u,
+                                 double &ap, double &kp)
+{
+    u = cell_nb(P, ix, d, +1);
+    const bool uw = upper_wall(P, ix, d);
+    ap = uw ? 0.0 : (double)C.a[d][u];
+    kp = uw ? 0.0 : (double)C.kf[d][u];
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double tau)
+{
+    const double tau2 = tau * tau;
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        double diag = 0.0, dth = 0.0;
+        for (int d = 0; d < P.nd; d++) {
+            const Geo G = geo(P, ix, d);
+            long long u;
+            double ap, kp;
+            up_coeffs(P, C, ix, d, u, ap, kp);
+            diag += G.Wp * ap / G.h + G.Wm * (double)C.a[d][c] / G.h;
+            dth += G.Wp * kp / G.h + G.Wm * (double)C.kf[d][c] / G.h;
+        }
+        const double gp = C.gp[c];
+        C.D[c] = (PT)(1.0 / gp + tau2 * diag + (tau * P.gm1 / gp) * dth / (double)C.rh[c]);
+    }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_gen_rhs(GridParams P, PCG<PT> C, const PT *r, PT *b, double tau)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        double divm = 0.0;
+        for (int d = 0; d < P.nd; d++) {
+            const Geo G = geo(P, ix, d);
+            long long u;
+            double ap, kp;
+            up_coeffs(P, C, ix, d, u, ap, kp);
+            divm += G.Wp * ap * (double)r[(2 + d) * P.N + u] - G.Wm * (double)C.a[d][c] * (double)r[(2 + d) * P.N + c];
+        }
+        b[c] = (PT)(P.gm1 * (double)r[P.N + c] / (double)C.gp[c] - tau * divm);
+    }
+}
+
+template <typename PT, bool FIRST>
+__global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq,
+                                                   double tau)
+{
+    const double w = MUSIC_JACOBI_OMEGA, tau2 = tau * tau;
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        if (FIRST) {
+            dq[c] = (PT)(w * ((double)b[c] / (double)C.D[c]));
+            continue;
+        }
+        int ix[3];
+        cell_coords(P, c, ix);
+        const double th = tau * P.gm1 / (double)C.gp[c];
+        double off = 0.0;
+        for (int d = 0; d < P.nd; d++) {
+            const Geo G = geo(P, ix, d);
+            long long u;
+            double ap, kp;
+            up_coeffs(P, C, ix, d, u, ap, kp);
+            const long long l = cell_nb(P, ix, d, -1);
+            const double am = C.a[d][c], km = C.kf[d][c];
+            off += tau2 * (G.Wp * ap / G.h * (double)dp[u] + G.Wm * am / G.h * (double)dp[l]);
+            off += th * (G.Wp * kp / G.h * (double)dp[u] / (double)C.rh[u] +
+                         G.Wm * km / G.h * (double)dp[l] / (double)C.rh[l]);
+        }
+        dq[c] = (PT)((1.0 - w) * (double)dp[c] + w * (((double)b[c] + off) / (double)C.D[c]));
+    }
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_gen_back(GridParams P, PCG<PT> C, const PT *r, const PT *dp, PT *z,
+                                                 double tau)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        double divm = 0.0, divu = 0.0, dth = 0.0;
+        const double tc = (double)dp[c] / (double)C.rh[c];
+        for (int d = 0; d < P.nd; d++) {
+            const Geo G = geo(P, ix, d);
+            long long u;
+            double ap, kp;
+            up_coeffs(P, C, ix, d, u, ap, kp);
+            const long long l = cell_nb(P, ix, d, -1);
+            const bool lw = lower_wall(P, ix, d), uw = upper_wall(P, ix, d);
+            const double own = lw ? (double)r[(2 + d) * P.N + c]
+                                  : (double)r[(2 + d) * P.N + c] - tau * ((double)dp[c] - (double)dp[l]) / G.h;
+            z[(2 + d) * P.N + c] = (PT)own;
+            // the upper face's correction is the next cell's own one (same h)
+            int jx[3] = {ix[0], ix[1], ix[2]};
+            jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
+            const double hu = (P.geom == MUSIC_GEOM_SPHERICAL) ? sph_h(P, d, jx[0]) : P.dx[d];
+            const double mp = uw ? 0.0 : (double)r[(2 + d) * P.N + u] - tau * ((double)dp[u] - (double)dp[c]) / hu;
+            const double mm = lw ? 0.0 : own;
+            divm += G.Wp * mp - G.Wm * mm;
+            divu += G.Wp * ap * mp - G.Wm * (double)C.a[d][c] * mm;
+            dth += G.Wp * kp * ((double)dp[u] / (double)C.rh[u] - tc) / G.h -
+                   G.Wm * (double)C.kf[d][c] * (tc - (double)dp[l] / (double)C.rh[l]) / G.h;
+        }
+        z[c] = (PT)((double)r[c] - tau * divm);
+        z[P.N + c] = (PT)(((double)r[P.N + c] - tau * (double)C.hp[c] * divu) + tau * dth);
+    }
+}
+
+template <typename PT>
+PCG<PT> pcg_of(music_grid *g)
+{
+    PCG<PT> C;
+    for (int d = 0; d < 3; d++) {
+        C.a[d] = (PT *)g->pa[d];
+        C.kf[d] = (PT *)g->pkf[d];
+    }
+    C.gp = (PT *)g->pgp;
+    C.hp = (PT *)g->php;
+    C.rh = (PT *)g->prh;
+    C.D = (PT *)g->pD;
+    C.chi = (PT *)g->pb;  // the rhs buffer is free during setup
+    return C;
+}
+
+template <typename PT>
+int gen_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    PCG<PT> C = pcg_of<PT>(g);
+    const int nb = nblocks(P.N);
+    k_gen_cell<PT><<<nb, BS, 0, s>>>(P, U, C);
+    CHECK_LAUNCH();
+    k_gen_face<PT><<<nb, BS, 0, s>>>(P, C, 0.5 * dt);
+    CHECK_LAUNCH();
+    k_gen_diag<PT><<<nb, BS, 0, s>>>(P, C, 0.5 * dt);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+template <typename PT>
+int gen_apply(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    PCG<PT> C = pcg_of<PT>(g);
+    const double tau = 0.5 * dt;
+    const int nb = nblocks(P.N);
+    PT *b = (PT *)g->pb, *dp = (PT *)g->pdp, *dq = (PT *)g->pdq;
+    k_gen_rhs<PT><<<nb, BS, 0, s>>>(P, C, r, b, tau);
+    CHECK_LAUNCH();
+    const int K = g->desc.precond_sweeps;
+    for (int k = 0; k < K; k++) {
+        if (k == 0)
+            k_gen_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau);
+        else
+            k_gen_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau);
+        CHECK_LAUNCH();
+        PT *t = dp;
+        dp = dq;
+        dq = t;
+    }
+    if (K == 0) CUDA_TRY(cudaMemsetAsync(dp, 0, P.N * sizeof(PT), s));
+    k_gen_back<PT><<<nb, BS, 0, s>>>(P, C, r, dp, z, tau);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
 }  // namespace
 
 int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
 {
     if (g->desc.precond == MUSIC_PC_NONE) return MUSIC_OK;
+    if (general_grid(g->P)) return g->mixed ? gen_setup<float>(g, U, dt, s) : gen_setup<double>(g, U, dt, s);
     return g->mixed ? setup_t<float>(g, U, dt, s) : setup_t<double>(g, U, dt, s);
 }
 
@@ -388,6 +633,11 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
     if (g->desc.precond == MUSIC_PC_NONE) {
         const size_t es = g->mixed ? sizeof(float) : sizeof(double);
         if (r != z) CUDA_TRY(cudaMemcpyAsync(z, r, n * es, cudaMemcpyDeviceToDevice, s));
+    } else if (general_grid(g->P)) {
+        if (g->mixed)
+            TRY(gen_apply<float>(g, dt, (const float *)r, (float *)z, s));
+        else
+            TRY(gen_apply<double>(g, dt, (const double *)r, (double *)z, s));
     } else if (g->P.nd == 2 && g->desc.precond_sweeps <= PC_FUSED_MAXK && g->pc_variant != PC_MULTIKERNEL) {
         if (g->mixed)
             return apply_fused2d<float>(g, dt, (const float *)r, (float *)z, want_norm, s);

@@ -72,7 +72,7 @@ __device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[
     const double T0 = (P.gm1 * W(P.N + c0)) / r0;
     const double T1 = (P.gm1 * W(P.N + c1)) / r1;
     const double Tg = 2.0 * T0 - T1;
-    const double hs = 0.5 * P.dx[hd] * P.g[hd];
+    const double hs = 0.5 * P.dx[hd] * face_g(P, hd, lower ? 0 : n);
     const double rg = lower ? __dmul_rn(r0, T0 - hs) / (Tg + hs) : __dmul_rn(r0, T0 + hs) / (Tg - hs);
     rho = rg;
     E = __dmul_rn(rg, Tg) / P.gm1;
@@ -118,9 +118,46 @@ __global__ void __launch_bounds__(BS) k_load(GridParams P, const double *U, cons
         double rho, E;
         load_cell(P, W, ix, rho, E);
         X.rho[x] = rho;
-        X.e[x] = E / rho;
+        const double e = E / rho;
+        X.e[x] = e;
         X.p[x] = P.gm1 * E;
         for (int d = 0; d < P.nd; d++) X.uf[d][x] = face_velocity(P, W, ix, d);
+        if (P.conduct) {
+            // T = (gamma-1) e and the photon conductivity chi = chi0 T^6.5 / rho^2
+            const double T = P.gm1 * e;
+            const double t3 = T * T * T;
+            X.Tt[x] = T;
+            X.chi[x] = P.chi0 * (t3 * t3 * sqrt(T)) / (rho * rho);
+        }
+    }
+}
+
+// radiative diffusion: chi dT/dn on every d-face (mean of the two cells' chi);
+// wall faces carry the prescribed flux (lum, or lum / r^2 on spherical
+// r-walls) or none
+__global__ void __launch_bounds__(BS) k_cond(GridParams P, ExtScratch X)
+{
+    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
+        int ix[3];
+        ext_coords(P, x, ix);
+        for (int d = 0; d < P.nd; d++) {
+            if (!ext_has(P, ix, d, -1)) continue;
+            if (P.bc[d] == MUSIC_BC_WALL && (ix[d] == 0 || ix[d] == P.n[d])) {
+                double G = 0.0;
+                if (P.flux_wall[d]) {
+                    G = P.lum;
+                    if (P.geom == MUSIC_GEOM_SPHERICAL && d == 0) {
+                        const double rf = sph_r(P, ix[0]);
+                        G = G / (rf * rf);
+                    }
+                }
+                X.Gc[d][x] = G;
+                continue;
+            }
+            const long long s = P.es[d];
+            const double h = (P.geom == MUSIC_GEOM_SPHERICAL) ? sph_h(P, d, ix[0]) : P.dx[d];
+            X.Gc[d][x] = 0.5 * (X.chi[x - s] + X.chi[x]) * (X.Tt[x] - X.Tt[x - s]) / h;
+        }
     }
 }
 
@@ -190,6 +227,56 @@ __global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
     }
 }
 
+// Spherical (r, theta) assembly of one cell and its lower faces: every
+// divergence is (1/V) sum(A F) over the control volume, the momenta carry
+// the geometric terms +rho u_t^2 / r (radial) and -rho u_r u_t / r (polar),
+// pressure gradients divide by dr or r_c dtheta, gravity from the r-face table.
+__device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int ix[3], long long x, double *R)
+{
+    const int i = ix[0], j = ix[1];
+    const long long s0 = P.es[0], s1 = P.es[1];
+    const double V = sph_vol(P, i, j);
+    const double Arm = sph_area(P, 0, i, j), Arp = sph_area(P, 0, i + 1, j);
+    const double Atm = sph_area(P, 1, i, j), Atp = sph_area(P, 1, i, j + 1);
+    const double fr = (Arp * X.Frho[0][x + s0] - Arm * X.Frho[0][x]) + (Atp * X.Frho[1][x + s1] - Atm * X.Frho[1][x]);
+    const double fe = (Arp * X.FE[0][x + s0] - Arm * X.FE[0][x]) + (Atp * X.FE[1][x + s1] - Atm * X.FE[1][x]);
+    const double du = (Arp * X.uf[0][x + s0] - Arm * X.uf[0][x]) + (Atp * X.uf[1][x + s1] - Atm * X.uf[1][x]);
+    R[0] = -fr / V;
+    R[1] = -fe / V - X.p[x] * (du / V);
+    if (P.conduct) {
+        const double cd = (Arp * X.Gc[0][x + s0] - Arm * X.Gc[0][x]) + (Atp * X.Gc[1][x + s1] - Atm * X.Gc[1][x]);
+        R[1] = R[1] + cd / V;
+    }
+    const double ctj = cos(sph_th(P, j)), ctj1 = cos(sph_th(P, j + 1));
+    if (P.bc[0] == MUSIC_BC_WALL && i == 0) {
+        R[2] = 0.0;
+    } else {
+        const double rm = sph_r(P, i - 0.5), rp = sph_r(P, i + 0.5), rf = sph_r(P, i);
+        const double Vr = (rp * rp * rp - rm * rm * rm) / 3.0 * (ctj - ctj1);
+        const double Acp = rp * rp * (ctj - ctj1), Acm = rm * rm * (ctj - ctj1);
+        const double Em = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j));
+        const double Ep = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j + 1));
+        const double acc = (Acp * X.Phi[0][x] - Acm * X.Phi[0][x - s0]) + (Ep * X.Psi[0][1][x + s1] - Em * X.Psi[0][1][x]);
+        const double rbar = 0.5 * (X.rho[x - s0] + X.rho[x]);
+        const double ut = 0.25 * ((X.uf[1][x - s0] + X.uf[1][x]) + (X.uf[1][x - s0 + s1] + X.uf[1][x + s1]));
+        R[2] = ((-acc / Vr - (X.p[x] - X.p[x - s0]) / P.dx[0]) + rbar * ut * ut / rf) + rbar * face_g(P, 0, i);
+    }
+    if (P.bc[1] == MUSIC_BC_WALL && j == 0) {
+        R[3] = 0.0;
+    } else {
+        const double ra = sph_r(P, i), rb = sph_r(P, i + 1), rc = sph_r(P, i + 0.5);
+        const double cm = cos(sph_th(P, j - 0.5)), cp = cos(sph_th(P, j + 0.5));
+        const double Vt = (rb * rb * rb - ra * ra * ra) / 3.0 * (cm - cp);
+        const double Bp = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j + 0.5));
+        const double Bm = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j - 0.5));
+        const double Fa = ra * ra * (cm - cp), Fb = rb * rb * (cm - cp);
+        const double acc = (Fb * X.Psi[1][0][x + s0] - Fa * X.Psi[1][0][x]) + (Bp * X.Phi[1][x] - Bm * X.Phi[1][x - s1]);
+        const double rbar = 0.5 * (X.rho[x - s1] + X.rho[x]);
+        const double ur = 0.25 * ((X.uf[0][x - s1] + X.uf[0][x]) + (X.uf[0][x - s1 + s0] + X.uf[0][x + s0]));
+        R[3] = ((-acc / Vt - (X.p[x] - X.p[x - s1]) / (rc * P.dx[1])) - rbar * ur * X.uf[1][x] / rc) + rbar * P.g[1];
+    }
+}
+
 template <int MODE, typename VIN, typename VOUT>
 __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, const double *U,
                                                  const double *aux, const VIN *v, VOUT *out,
@@ -217,7 +304,13 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
         }
         R[0] = -accr;
         R[1] = -acce - X.p[x] * divu;
-        for (int d = 0; d < P.nd; d++) {
+        if (P.conduct) {
+            double cond = 0.0;
+            for (int d = 0; d < P.nd; d++) cond += (X.Gc[d][x + P.es[d]] - X.Gc[d][x]) * P.idx[d];
+            R[1] = R[1] + cond;
+        }
+        if (P.geom == MUSIC_GEOM_SPHERICAL) sph_assemble(P, X, ix, x, R);
+        for (int d = 0; d < P.nd && P.geom != MUSIC_GEOM_SPHERICAL; d++) {
             if (P.bc[d] == MUSIC_BC_WALL && ix[d] == 0) {
                 R[2 + d] = 0.0;
                 continue;
@@ -518,6 +611,10 @@ int run_passes(music_grid *g, const double *U, const VT *v, cudaStream_t s)
     CHECK_LAUNCH();
     k_momentum<<<nbm, BS, 0, s>>>(P, g->ext);
     CHECK_LAUNCH();
+    if (P.conduct) {
+        k_cond<<<nbm, BS, 0, s>>>(P, g->ext);
+        CHECK_LAUNCH();
+    }
     return MUSIC_OK;
 }
 
@@ -529,7 +626,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
 {
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
-    if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS) {
+    if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P)) {
         const bool prof = g->prof_on && mode == SM_JV;
         if (prof) TRY(prof_begin(g, s));
         TRY(fused2d_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
