@@ -204,7 +204,7 @@ def run_music(args):
         r["grid"].close()
     serving = None
     if not args.no_serving and ws == 1:
-        serving = run_serving(args.serve_solves)
+        serving = run_serving(args.serve_solves, lane_cells=args.serve_lane_cells)
 
     if rank != 0:
         return
@@ -320,7 +320,7 @@ def serving_mix(nsolves=256, seed=4):
     return out, gaps
 
 
-def run_serving(nsolves=256, max_active=16, seq_sample=12):
+def run_serving(nsolves=256, max_active=16, seq_sample=12, lane_cells=0):
     """Continuous batching through the solve server (mixed precision), against
     the same solves run one after another on the plain FP64 GPU path."""
     import threading
@@ -340,7 +340,7 @@ def run_serving(nsolves=256, max_active=16, seq_sample=12):
     mean_service = seq_cells / seq_rate / seq_sample
     gaps = gaps * (mean_service / max_active)
     tickets = []
-    with B.Server(max_active=max_active) as srv:
+    with B.Server(max_active=max_active, batch_max_cells=lane_cells) as srv:
         start = time.perf_counter()
 
         def submitter():
@@ -361,7 +361,10 @@ def run_serving(nsolves=256, max_active=16, seq_sample=12):
         st = srv.stats()
     ok = sum(r["status"] == 0 for r in res)
     rate = st["cell_steps"] / wall
+    lane = 16384 if lane_cells == 0 else lane_cells
     return {"solves": nsolves, "completed": ok, "max_active": max_active, "wall_s": wall,
+            "batch_lane_max_cells": lane,
+            "batch_lane_solves": sum(1 for p in probs if 0 <= lane and p.ncells <= lane),
             "cell_steps_per_s": rate, "step_ms_p50": float(np.percentile(lat, 50)),
             "step_ms_p99": float(np.percentile(lat, 99)),
             "queue_ms_p99": float(np.percentile([r["queue_ms"] for r in res], 99)),
@@ -425,6 +428,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-lane-cells", type=int, default=0,
+                    help="largest solve the server's batch lane takes (0: default 16384, -1: no lane)")
     ap.add_argument("--serve-solves", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:

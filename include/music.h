@@ -207,6 +207,23 @@ int music_precond_apply(music_grid *grid, const double *U, double dt, const void
  */
 int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *stream);
 
+/*
+ * Advance `count` grids (1..512) by one implicit step each in ONE kernel
+ * launch: every grid's step (CFL time step of Eq. 4 from its own state with
+ * cfl[i], capped by dt_max[i] > 0 (dt_max may be NULL); Newton on the
+ * Crank-Nicolson system; restarted
+ * right-preconditioned GMRES with Jacobian-free products; dt halvings on
+ * failure) runs in one CTA on the device with no host synchronisation, using
+ * the grid's own buffers.  Meant for many small grids, which cannot fill the
+ * GPU one at a time.  Every grid must be 2-D Cartesian without radiative
+ * diffusion, use at most 16 preconditioner sweeps, and all must share one
+ * precision.  stats[i] (may be NULL) receives grid i's outcome.  Synchronises
+ * `stream`.  Returns MUSIC_OK, or the first failing grid's status (its state
+ * is restored to the start of the step); MUSIC_E_INVAL for a bad batch.
+ */
+int music_batch_step(music_grid **grids, int count, const double *cfl, const double *dt_max,
+                     music_step_stats *stats, void *stream);
+
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).
    Synchronises `stream`. */

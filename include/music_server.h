@@ -4,12 +4,14 @@
  *
  * The paper runs one solve per job on CPU clusters; this service layer has
  * no counterpart there.  Requests are copied at submission and queued on the
- * host.  Worker threads admit them first-fit in arrival order whenever a
- * worker is free and the device footprint of the admitted solves (see
- * music_grid_footprint) stays within the memory budget; each worker owns a
- * CUDA stream, so the kernels of concurrent solves overlap on the device.  A
- * solve keeps its state and Krylov basis resident until it finishes, then
- * frees them and its worker admits the next request.  Every reduction in the
+ * host and admitted first-fit in arrival order while the device footprint of
+ * the admitted solves (see music_grid_footprint) stays within the memory
+ * budget.  Small solves go to the batch lane: one thread advances all of its
+ * resident solves together, one music_batch_step launch per round, and new
+ * solves join between rounds (continuous batching at step granularity).
+ * Larger solves go to per-stream workers, so their kernels overlap on the
+ * device.  A solve keeps its state and Krylov basis resident until it
+ * finishes, then frees them and the next request is admitted.  Every reduction in the
  * library is deterministic, so a solve gives the same result alone and in a
  * mix.  All calls are thread safe and never abort.
  */
@@ -26,7 +28,11 @@ typedef struct music_server music_server;
 
 typedef struct {
     size_t mem_budget_bytes;  /* device bytes the admitted solves may own (0: 60% of free memory) */
-    int max_active;           /* concurrently resident solves = worker threads = streams [16], <= 256 */
+    int max_active;           /* per-stream workers = concurrently resident large solves [16], <= 256 */
+    int batch_max_cells;      /* solves of at most this many cells (2-D Cartesian, no radiative
+                                 diffusion, <= 16 preconditioner sweeps) join the batch lane
+                                 [16384]; -1: no batch lane */
+    int batch_size;           /* solves per batched launch [152], <= 512 */
     int reserved;
 } music_server_opts;
 

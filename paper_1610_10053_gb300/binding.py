@@ -80,6 +80,8 @@ SIGNATURES = {
                                          ctypes.c_void_p]),
     "music_cfl_rate_noalloc": (ctypes.c_int, [ctypes.POINTER(GridDesc), ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_void_p]),
+    "music_batch_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _dbl_p, _dbl_p,
+                                        ctypes.POINTER(StepStats), ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
 }
@@ -177,6 +179,21 @@ def cfl_rate_noalloc(prob, U, rate, precision: int = FP64):
     `rate`, without any device allocation (music_cfl_rate_noalloc)."""
     d = desc_from_problem(prob, precision)
     check(load().music_cfl_rate_noalloc(ctypes.byref(d), _ptr(U), _ptr(rate), _stream()))
+
+
+def batch_step(grids, cfl=None, dt_max=None):
+    """One implicit step of every grid in one launch (music_batch_step), each
+    with its problem's cfl (or the given per-grid values).
+    Returns (status, [stats dict per grid])."""
+    n = len(grids)
+    arr = (ctypes.c_void_p * n)(*[g.h.value for g in grids])
+    cf = (ctypes.c_double * n)(*[float(g.prob.cfl if cfl is None else cfl[i]) for i, g in enumerate(grids)])
+    dm = (ctypes.c_double * n)(*[float(g.prob.dt_max if dt_max is None else dt_max[i]) for i, g in enumerate(grids)])
+    st = (StepStats * n)()
+    code = load().music_batch_step(arr, n, cf, dm, st, _stream())
+    if code == 1:
+        check(code)
+    return code, [st[i].as_dict() for i in range(n)]
 
 
 def footprint(prob, precision: int = FP64, **over) -> int:
@@ -323,7 +340,8 @@ class Grid:
 
 # ------------------------------------------------------------------ server
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int), ("reserved", ctypes.c_int)]
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
+                ("batch_max_cells", ctypes.c_int), ("batch_size", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class SolveReq(ctypes.Structure):
@@ -363,9 +381,10 @@ SIGNATURES.update({
 class Server:
     """Continuous-batching solve server (include/music_server.h)."""
 
-    def __init__(self, mem_budget_bytes: int = 0, max_active: int = 16):
+    def __init__(self, mem_budget_bytes: int = 0, max_active: int = 16, batch_max_cells: int = 0,
+                 batch_size: int = 0):
         L = load()
-        o = ServerOpts(mem_budget_bytes, max_active, 0)
+        o = ServerOpts(mem_budget_bytes, max_active, batch_max_cells, batch_size, 0)
         h = ctypes.c_void_p()
         check(L.music_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.h = h

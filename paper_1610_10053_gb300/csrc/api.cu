@@ -178,6 +178,8 @@ void alloc_plan(music_grid *g, F &&f)
         }
     }
     f((void **)&g->partials, (size_t)MUSIC_MAXV * g->nb * sizeof(double));
+    f((void **)&g->hg, (size_t)(MUSIC_MAXV * MUSIC_MAXV + 4 * MUSIC_MAXV) * sizeof(double));
+    f(&g->binst, 1024);  // batched-solver descriptor (sizeof checked in batched.cu)
     f((void **)&g->ds, sizeof(DevScalars));
     f((void **)&g->diag_rows, (size_t)8 * P.n[1] * sizeof(double));
 }

@@ -8,6 +8,7 @@
 #define MUSIC_GHOST 3
 #define MUSIC_MAXV 64          // max Krylov vectors per cycle + 1
 #define MUSIC_JACOBI_OMEGA 0.8 // weight of the pressure-system Jacobi sweeps
+#define MUSIC_BATCH_MAX 512    // grids per batched launch
 
 // Grid geometry and physics, passed to kernels by value.
 struct GridParams {
@@ -73,6 +74,9 @@ struct DevScalars {
     double h2[MUSIC_MAXV];  // second CGS pass
     double diag[8];
     unsigned int counters[8];  // last-block-done counters, 0 between launches
+    // outputs of a batched step (music_batch_step)
+    double step_dt, step_fnorm0, step_fnorm, step_maxdrho;
+    int step_status, step_newton, step_gmres, step_halvings, step_unconverged, step_pad;
 };
 
 enum { CNT_DOTS = 0, CNT_UPDATE, CNT_NORMW, CNT_SUMSQ, CNT_NEWTON, CNT_PRECOND };

@@ -47,6 +47,9 @@ struct music_grid {
     void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
     void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
     double *gface;         // spherical: radial gravity on the r-faces
+    double *hg;            // Hessenberg and Givens storage of the batched solver
+    void *binst;           // device copy of this grid's batched-solver descriptor
+    int binst_ready;
     ExtScratch ext;
     double *partials;      // [MUSIC_MAXV][nb]
     DevScalars *ds;        // device scalars
@@ -137,6 +140,10 @@ void fill_grid_params(const music_grid_desc &d, GridParams *P);
 int grid_validate(music_grid_desc *d);
 int grid_set_state(music_grid *g, const double *U, int is_device, cudaStream_t s);
 int grid_get_state(music_grid *g, double *U, int is_device, cudaStream_t s);
+
+// ----- batched.cu -----
+extern "C" int music_batch_step(music_grid **grids, int count, const double *cfl, const double *dt_max,
+                                music_step_stats *stats, void *stream);
 
 // ----- solver.cu -----
 int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);

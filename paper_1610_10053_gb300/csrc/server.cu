@@ -49,6 +49,7 @@ struct Job {
     double cfl = 1.0, dt_max = 0.0, rho_L = 1.0, rho_H = 2.0;
     size_t footprint = 0;
     bool done = false;
+    bool failed = false;
     music_solve_result res;
     std::vector<double> step_ms;
     clk::time_point t_submit, t_admit, t_done;
@@ -73,15 +74,30 @@ struct music_server {
     double busy_ms = 0.0;
     clk::time_point busy_since;
     std::vector<double> all_step_ms;
+    // batch lane
+    bool lane = false;
+    int lane_cells = 16384, lane_size = 152;
+    std::thread lane_thread;
+    cudaStream_t lane_stream = nullptr;
 };
 
 namespace {
 
-// Take the first pending job that fits; caller holds the lock.
-Job *admit_locked(music_server *S)
+bool lane_eligible(const music_server *S, const Job *j)
+{
+    const music_grid_desc &d = j->desc;
+    const long long cells = (long long)d.n[0] * d.n[1] * (d.ndim == 3 ? d.n[2] : 1);
+    return S->lane && d.ndim == 2 && d.geometry == MUSIC_GEOM_CARTESIAN && !d.conduct &&
+           d.precond_sweeps <= 16 && cells <= S->lane_cells;
+}
+
+// Take the first pending job that fits (the lane takes only its own kind,
+// the workers only the other); caller holds the lock.
+Job *admit_locked(music_server *S, bool for_lane = false)
 {
     for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
         Job *j = S->jobs[*it].get();
+        if (lane_eligible(S, j) != for_lane) continue;
         if (S->used + j->footprint <= S->budget) {
             S->pending.erase(it);
             S->used += j->footprint;
@@ -125,6 +141,125 @@ int run_job(Job *j, cudaStream_t s)
     return rc;
 }
 
+// Record a finished solve and free its budget; caller holds the lock.
+void finish_locked(music_server *S, Job *j, int rc)
+{
+    j->res.status = rc;
+    j->t_done = clk::now();
+    j->res.queue_ms = ms_between(j->t_submit, j->t_admit);
+    j->res.total_ms = ms_between(j->t_submit, j->t_done);
+    j->res.step_ms_p50 = percentile(j->step_ms, 50.0);
+    j->res.step_ms_p99 = percentile(j->step_ms, 99.0);
+    j->done = true;
+    const double cells = (double)j->desc.n[0] * j->desc.n[1] * (j->desc.ndim == 3 ? j->desc.n[2] : 1);
+    S->cell_steps += cells * j->res.steps_done;
+    S->all_step_ms.insert(S->all_step_ms.end(), j->step_ms.begin(), j->step_ms.end());
+    S->used -= j->footprint;
+    S->active--;
+    if (S->active == 0) S->busy_ms += ms_between(S->busy_since, clk::now());
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();  // memory freed: someone may fit now
+}
+
+// The batch lane: all resident small solves advance together, one batched
+// launch per round per precision; new solves join between rounds.
+void lane_main(music_server *S)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t s = S->lane_stream;
+    struct Slot {
+        Job *j;
+        music_grid *g;
+    };
+    std::vector<Slot> act;
+    for (;;) {
+        std::vector<Job *> fresh;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            for (;;) {
+                while ((int)(act.size() + fresh.size()) < S->lane_size) {
+                    Job *j = admit_locked(S, true);
+                    if (!j) break;
+                    fresh.push_back(j);
+                }
+                if (!act.empty() || !fresh.empty() || S->stop) break;
+                S->cv_work.wait(lk);
+            }
+            if (S->stop && act.empty() && fresh.empty()) return;
+        }
+        for (Job *j : fresh) {
+            music_grid *g = nullptr;
+            int rc = grid_create(&j->desc, s, &g);
+            if (rc == MUSIC_OK) rc = grid_set_state(g, j->U0.data(), 0, s);
+            if (rc != MUSIC_OK) {
+                if (g) grid_destroy(g);
+                std::lock_guard<std::mutex> lk(S->mu);
+                finish_locked(S, j, rc);
+                continue;
+            }
+            act.push_back({j, g});
+        }
+        // one round: a batched step per precision present
+        for (int mixed = 0; mixed < 2; mixed++) {
+            std::vector<music_grid *> gs;
+            std::vector<double> cf, dm;
+            std::vector<size_t> idx;
+            for (size_t k = 0; k < act.size(); k++)
+                if (act[k].g->mixed == mixed && act[k].j->res.steps_done < act[k].j->n_steps) {
+                    gs.push_back(act[k].g);
+                    cf.push_back(act[k].j->cfl);
+                    dm.push_back(act[k].j->dt_max);
+                    idx.push_back(k);
+                }
+            if (gs.empty()) continue;
+            const auto t0 = clk::now();
+            std::vector<music_step_stats> st(gs.size());
+            const int rc = music_batch_step(gs.data(), (int)gs.size(), cf.data(), dm.data(), st.data(), s);
+            const double ms = ms_between(t0, clk::now());
+            // a bad batch or a CUDA failure fails the whole group; otherwise each
+            // grid's own status (read back by the call) decides
+            const bool group_err = (rc == MUSIC_E_INVAL || rc == MUSIC_E_OOM || rc == MUSIC_E_CUDA);
+            for (size_t q = 0; q < gs.size(); q++) {
+                Job *j = act[idx[q]].j;
+                const int srcode = group_err ? rc : gs[q]->hs->step_status;
+                if (srcode != MUSIC_OK) {
+                    j->res.status = srcode;
+                    j->n_steps = j->res.steps_done;  // stop here; reported below
+                    j->failed = true;
+                    continue;
+                }
+                j->step_ms.push_back(ms);
+                j->res.sim_time += st[q].dt;
+                j->res.steps_done++;
+                j->res.newton_its += st[q].newton_its;
+                j->res.gmres_its += st[q].gmres_its;
+            }
+        }
+        // retire finished solves
+        for (size_t k = 0; k < act.size();) {
+            Job *j = act[k].j;
+            if (j->res.steps_done < j->n_steps) {
+                k++;
+                continue;
+            }
+            music_grid *g = act[k].g;
+            int rc = j->failed ? j->res.status : MUSIC_OK;
+            if (rc == MUSIC_OK) rc = music_diagnostics(g, j->rho_L, j->rho_H, j->res.diag, s);
+            if (rc == MUSIC_OK) {
+                j->Ufinal.resize(g->n);
+                rc = grid_get_state(g, j->Ufinal.data(), 0, s);
+            }
+            grid_destroy(g);
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                finish_locked(S, j, rc);
+            }
+            act[k] = act.back();
+            act.pop_back();
+        }
+    }
+}
+
 void worker_main(music_server *S, int w)
 {
     cudaSetDevice(S->device);
@@ -138,21 +273,7 @@ void worker_main(music_server *S, int w)
         }
         const int rc = run_job(j, s);
         std::lock_guard<std::mutex> lk(S->mu);
-        j->res.status = rc;
-        j->t_done = clk::now();
-        j->res.queue_ms = ms_between(j->t_submit, j->t_admit);
-        j->res.total_ms = ms_between(j->t_submit, j->t_done);
-        j->res.step_ms_p50 = percentile(j->step_ms, 50.0);
-        j->res.step_ms_p99 = percentile(j->step_ms, 99.0);
-        j->done = true;
-        const double cells = (double)j->desc.n[0] * j->desc.n[1] * (j->desc.ndim == 3 ? j->desc.n[2] : 1);
-        S->cell_steps += cells * j->res.steps_done;
-        S->all_step_ms.insert(S->all_step_ms.end(), j->step_ms.begin(), j->step_ms.end());
-        S->used -= j->footprint;
-        S->active--;
-        if (S->active == 0) S->busy_ms += ms_between(S->busy_since, clk::now());
-        S->cv_done.notify_all();
-        S->cv_work.notify_all();  // memory freed: someone may fit now
+        finish_locked(S, j, rc);
     }
 }
 
@@ -206,6 +327,19 @@ int music_server_create(const music_server_opts *opts, music_server **out)
         }
         S->streams.push_back(st);
     }
+    S->lane = (o.batch_max_cells >= 0);
+    S->lane_cells = o.batch_max_cells > 0 ? o.batch_max_cells : 16384;
+    S->lane_size = o.batch_size > 0 ? (o.batch_size > MUSIC_BATCH_MAX ? MUSIC_BATCH_MAX : o.batch_size) : 152;
+    if (S->lane) {
+        if (cudaStreamCreateWithFlags(&S->lane_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t x : S->streams) cudaStreamDestroy(x);
+            delete S;
+            set_error("cudaStreamCreate failed");
+            return MUSIC_E_CUDA;
+        }
+        S->lane_thread = std::thread(lane_main, S);
+    }
     for (int w = 0; w < o.max_active; w++) S->workers.emplace_back(worker_main, S, w);
     *out = S;
     return MUSIC_OK;
@@ -247,7 +381,7 @@ int music_submit_solve(music_server *S, const music_solve_req *req, uint64_t *ti
     S->jobs[t] = std::move(j);
     S->pending.push_back(t);
     *ticket = t;
-    S->cv_work.notify_one();
+    S->cv_work.notify_all();  // the lane and the workers take different kinds
     return MUSIC_OK;
 }
 
@@ -359,7 +493,9 @@ int music_server_destroy(music_server *S)
     }
     S->cv_work.notify_all();
     for (std::thread &t : S->workers) t.join();
+    if (S->lane_thread.joinable()) S->lane_thread.join();
     for (cudaStream_t st : S->streams) cudaStreamDestroy(st);
+    if (S->lane_stream) cudaStreamDestroy(S->lane_stream);
     delete S;
     return MUSIC_OK;
 }

@@ -1,0 +1,126 @@
+// Per-tile device code of the fused 2-D physics-based preconditioner (Sec. 2,
+// after Park et al.): used by the one-launch-per-application kernel and by
+// the persistent batched kernel.
+#pragma once
+#include "internal.h"
+
+namespace tile {
+
+constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;
+
+template <typename PT>
+struct PC {
+    PT *a[3];   // 1 / rbar on the lower d-face (0 on wall faces)
+    PT *gp;     // gamma p
+    PT *hp;     // gamma E
+    PT *D;      // diagonal of the Helmholtz operator
+};
+
+// index into an interior row or column: periodic wrap, or clamp on walls
+// (coefficients of faces outside a walled domain are zero, which decouples
+// the clamped cells)
+__device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
+{
+    if (periodic) {
+        while (a < 0) a += n;
+        while (a >= n) a -= n;
+        inside = true;
+        return a;
+    }
+    inside = (a > 0 && a < n);
+    return a < 0 ? 0 : (a >= n ? n - 1 : a);
+}
+
+// One tile (bx, by) of the fused preconditioner, run by a CTA of PTX*PTY
+// threads with 6 (PTX+2H)(PTY+2H) PT of shared memory at `smraw`; returns the
+// calling thread's share of |z|^2.
+template <typename PT, int KM>
+__device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT *r, PT *z, PT tau, PT tau2, int K,
+                                 int bx, int by, unsigned char *smraw)
+{
+    constexpr int NT = PTX * PTY, H = KM + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
+    PT *ax = (PT *)smraw, *ay = ax + R, *iD = ay + R, *b = iD + R, *dA = b + R, *dB = dA + R;
+    const int i0 = bx * PTX - H, j0 = by * PTY - H;
+    const int tid = threadIdx.x;
+    const long long N = P.N;
+    const int n0 = P.n[0], n1 = P.n[1];
+    const bool px = P.bc[0] == MUSIC_BC_PERIODIC, py = P.bc[1] == MUSIC_BC_PERIODIC;
+    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    const PT ix0 = (PT)P.idx[0], ix1 = (PT)P.idx[1];
+    for (int q = tid; q < R; q += NT) {
+        const int lx = q % RX, ly = q / RX;
+        bool inx, iny;
+        const int x = pc_wrap(i0 + lx, n0, px, inx), y = pc_wrap(j0 + ly, n1, py, iny);
+        const long long c = x + (long long)n0 * y;
+        ax[q] = inx ? C.a[0][c] : (PT)0;
+        ay[q] = iny ? C.a[1][c] : (PT)0;
+        iD[q] = (PT)1 / C.D[c];
+        if (lx < RX - 1 && ly < RY - 1) {
+            // right-hand side needs r_m on the upper faces: the next cells'
+            bool inxp, inyp;
+            const int xp = pc_wrap(i0 + lx + 1, n0, px, inxp), yp = pc_wrap(j0 + ly + 1, n1, py, inyp);
+            const long long cx = xp + (long long)n0 * y, cy = x + (long long)n0 * yp;
+            const PT axp = inxp ? C.a[0][cx] : (PT)0, ayp = inyp ? C.a[1][cy] : (PT)0;
+            const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
+            PT divm = (axp * r[2 * N + cx] - axm * r[2 * N + c]) * ix0;
+            divm += (ayp * r[3 * N + cy] - aym * r[3 * N + c]) * ix1;
+            b[q] = (PT)P.gm1 * r[N + c] / C.gp[c] - tau * divm;
+        }
+    }
+    __syncthreads();
+    const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
+    PT *src = dA, *dst = dB;
+    for (int k = 0; k < K; k++) {
+        const int lo = k, hx = RX - 1 - k, hy = RY - 1 - k;
+        const int wdt = hx - lo, cnt = wdt * (hy - lo);
+        for (int t = tid; t < cnt; t += NT) {
+            const int q = (lo + t / wdt) * RX + lo + t % wdt;
+            if (k == 0) {
+                dst[q] = w * (b[q] * iD[q]);
+            } else {
+                PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
+                off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
+                dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) * iD[q]);
+            }
+        }
+        __syncthreads();
+        PT *tt = src;
+        src = dst;
+        dst = tt;
+    }
+    // src holds dp; back substitution on the tile
+    const int tx = tid % PTX, ty = tid / PTX;
+    const int gx = bx * PTX + tx, gy = by * PTY + ty;
+    double nrm = 0.0;
+    if (gx < n0 && gy < n1) {
+        const int q = (ty + H) * RX + (tx + H);
+        const long long c = gx + (long long)n0 * gy;
+        const bool wlx = (!px && gx == 0), wux = (!px && gx == n0 - 1);
+        const bool wly = (!py && gy == 0), wuy = (!py && gy == n1 - 1);
+        const long long cxp = (gx + 1 == n0) ? c - gx : c + 1;
+        const long long cyp = (gy + 1 == n1) ? gx : c + n0;
+        const PT dp = (K > 0) ? src[q] : (PT)0;
+        const PT dpxm = (K > 0) ? src[q - 1] : (PT)0, dpxp = (K > 0) ? src[q + 1] : (PT)0;
+        const PT dpym = (K > 0) ? src[q - RX] : (PT)0, dpyp = (K > 0) ? src[q + RX] : (PT)0;
+        const PT mx_own = wlx ? r[2 * N + c] : r[2 * N + c] - tau * (dp - dpxm) * ix0;
+        const PT my_own = wly ? r[3 * N + c] : r[3 * N + c] - tau * (dp - dpym) * ix1;
+        const PT mxp = wux ? (PT)0 : r[2 * N + cxp] - tau * (dpxp - dp) * ix0;
+        const PT myp = wuy ? (PT)0 : r[3 * N + cyp] - tau * (dpyp - dp) * ix1;
+        const PT mxm = wlx ? (PT)0 : mx_own, mym = wly ? (PT)0 : my_own;
+        PT divm = (mxp - mxm) * ix0;
+        divm += (myp - mym) * ix1;
+        PT divu = (ax[q + 1] * mxp - ax[q] * mxm) * ix0;
+        divu += (ay[q + RX] * myp - ay[q] * mym) * ix1;
+        const PT zr = r[c] - tau * divm;
+        const PT ze = r[N + c] - tau * C.hp[c] * divu;
+        z[c] = zr;
+        z[N + c] = ze;
+        z[2 * N + c] = mx_own;
+        z[3 * N + c] = my_own;
+        nrm = (double)zr * zr + (double)ze * ze + (double)mx_own * mx_own + (double)my_own * my_own;
+    }
+    __syncthreads();  // the tile's shared memory may be reused by the caller
+    return nrm;
+}
+
+}  // namespace tile

@@ -1,0 +1,297 @@
+// Per-tile device code of the fused 2-D stencil (Sec. 2, Eqs. 1-3): used by
+// the one-launch-per-evaluation kernel and by the persistent batched kernel.
+#pragma once
+#include "internal.h"
+
+namespace tile {
+
+template <typename VT>
+struct WLoad {
+    const double *U;
+    const VT *v;        // Jv direction or null
+    double eps;         // finite-difference step (Jv only)
+    __device__ inline double operator()(long long i) const
+    {
+        double u = U[i];
+        if (v) u = u + eps * (double)v[i];
+        return u;
+    }
+};
+
+__device__ inline double vanleer(double a, double b)
+{
+    return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
+}
+
+template <typename VT>
+__device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[3], double &rho,
+                          double &E)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    int hd = -1, lower = 0;
+    for (int d = 0; d < P.nd; d++) {
+        const int n = P.n[d];
+        // tile halos of ragged edges may lie beyond the ghost layers; their
+        // values are never used, so clamp wall directions into the ghost range
+        const int a = (P.bc[d] == MUSIC_BC_WALL) ? min(max(j[d], -MUSIC_GHOST), n - 1 + MUSIC_GHOST) : j[d];
+        if (a >= 0 && a < n) continue;
+        if (P.bc[d] == MUSIC_BC_PERIODIC)
+            j[d] = (a % n + n) % n;
+        else if (P.ws[d] == MUSIC_WALL_MIRROR)
+            j[d] = (a < 0) ? (-1 - a) : (2 * n - 1 - a);
+        else {
+            hd = d;
+            lower = (a < 0);
+        }
+    }
+    if (hd < 0) {
+        const long long c = cell_index(P, j);
+        rho = W(c);
+        E = W(P.N + c);
+        return;
+    }
+    const int n = P.n[hd];
+    j[hd] = lower ? 0 : n - 1;
+    const long long c0 = cell_index(P, j);
+    j[hd] = lower ? 1 : n - 2;
+    const long long c1 = cell_index(P, j);
+    const double r0 = W(c0), r1 = W(c1);
+    const double T0 = (P.gm1 * W(P.N + c0)) / r0;
+    const double T1 = (P.gm1 * W(P.N + c1)) / r1;
+    const double Tg = 2.0 * T0 - T1;
+    const double hs = 0.5 * P.dx[hd] * face_g(P, hd, lower ? 0 : n);
+    const double rg = lower ? __dmul_rn(r0, T0 - hs) / (Tg + hs) : __dmul_rn(r0, T0 + hs) / (Tg - hs);
+    rho = rg;
+    E = __dmul_rn(rg, Tg) / P.gm1;
+}
+
+template <typename VT>
+__device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const int ix[3], int d)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    double sgn = 1.0;
+    for (int w = 0; w < P.nd; w++) {
+        const int n = P.n[w];
+        const int a = (P.bc[w] == MUSIC_BC_WALL) ? min(max(j[w], -MUSIC_GHOST), n - 1 + MUSIC_GHOST) : j[w];
+        j[w] = a;
+        if (a >= 0 && a < n) continue;
+        if (P.bc[w] == MUSIC_BC_PERIODIC) {
+            j[w] = (a % n + n) % n;
+        } else if (w == d) {
+            if (a == n) return 0.0;
+            j[w] = (a < 0) ? -a : 2 * n - a;
+            sgn = -sgn;
+        } else {
+            j[w] = (a < 0) ? (-1 - a) : (2 * n - 1 - a);
+        }
+    }
+    if (P.bc[d] == MUSIC_BC_WALL && j[d] == 0) return 0.0;
+    const long long c = cell_index(P, j);
+    int l[3] = {j[0], j[1], j[2]};
+    l[d] = (j[d] == 0) ? P.n[d] - 1 : j[d] - 1;
+    const long long cl = cell_index(P, l);
+    const double rbar = 0.5 * (W(cl) + W(c));
+    return sgn * (W((long long)(2 + d) * P.N + c) / rbar);
+}
+
+// ---------------------------------------------------------------- fused 2-D
+// One kernel per evaluation of R on 2-D grids.  A CTA owns a TX x TY tile of
+// cells [X0, X1) x [Y0, Y1) (local coordinates) and stages the tile plus a
+// halo of 3 cells below / 2 above in shared memory (RX x RY points, x
+// fastest).  Each intermediate is computed once, and only on the exact
+// sub-rectangle that the tile's residuals reach (the stencil is a cross, not
+// a square), which keeps FP64 divisions near the minimum of 11 per cell:
+//   1 ghost-mapped rho, e, p and face velocities u, v (global loads, L1/L2)
+//   2 van Leer slopes of rho, e, u, v along x and y
+//   3 upwind mass and energy fluxes on x- and y-faces
+//   4 momentum fluxes: centres (Phi) and corners (Psi)
+//   5 the residuals of the tile's cells, written per mode (coalesced in x).
+template <int TX, int TY>
+struct Tile2D {
+    static constexpr int RX = TX + 5, RY = TY + 5, R = RX * RY, NARR = 17;
+    static constexpr int X0 = 3, X1 = 3 + TX, Y0 = 3, Y1 = 3 + TY;
+    static constexpr size_t SMEM = (size_t)NARR * R * sizeof(double);
+};
+
+// loop of the CTA's threads over the local rectangle [x0,x1) x [y0,y1)
+#define TILE_RECT(x0, x1, y0, y1)                                                   \
+    for (int k_ = tid, w_ = (x1) - (x0), n_ = ((x1) - (x0)) * ((y1) - (y0)); k_ < n_; \
+         k_ += NT)                                                                  \
+        for (int lx = (x0) + k_ % w_, ly = (y0) + k_ / w_, q = ly * RX + lx, once_ = 1; once_; once_ = 0)
+
+// One tile (bx, by) of the fused stencil, run by a CTA of TX*TY threads with
+// Tile2D<TX, TY>::SMEM bytes of shared memory at `sm`.  epsv is the finite-
+// difference step (SM_JV).  Callable from any kernel that owns such a CTA.
+template <int MODE, typename VIN, typename VOUT, int TX, int TY>
+__device__ void fused2d_tile(const GridParams &P, const double *U, const double *aux, const VIN *v, VOUT *out,
+                             double *RU_out, double hdt, double sign, double epsv, int bx, int by, double *sm)
+{
+    using TL = Tile2D<TX, TY>;
+    constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
+    constexpr int X0 = TL::X0, X1 = TL::X1, Y0 = TL::Y0, Y1 = TL::Y1;
+    double *rho = sm, *ee = sm + R, *pp = sm + 2 * R, *uu = sm + 3 * R, *vv = sm + 4 * R;
+    double *srx = sm + 5 * R, *sry = sm + 6 * R, *sex = sm + 7 * R, *sey = sm + 8 * R;
+    double *sux = sm + 9 * R, *suy = sm + 10 * R, *svx = sm + 11 * R, *svy = sm + 12 * R;
+    double *Frx = sm + 13 * R, *Fry = sm + 14 * R, *FEx = sm + 15 * R, *FEy = sm + 16 * R;
+    // scalar slopes are dead after phase 3: their planes hold the momentum fluxes
+    double *Phx = srx, *Phy = sry, *Psxy = sex, *Psyx = sey;
+    const int i0 = bx * TX - 3, j0 = by * TY - 3;
+    const int tid = threadIdx.x;
+    const WLoad<VIN> W{U, (MODE == SM_JV) ? v : nullptr, epsv};
+
+    // ---- phase 1: cell scalars on the cross-shaped region, face velocities
+    auto rho_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        double r, E;
+        load_cell(P, W, ix, r, E);
+        rho[q] = r;
+    };
+    auto e_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        double r, E;
+        load_cell(P, W, ix, r, E);
+        ee[q] = E / r;
+        pp[q] = P.gm1 * E;
+    };
+    auto u_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        uu[q] = face_velocity(P, W, ix, 0);
+    };
+    auto v_at = [&](int lx, int ly, int q) {
+        const int ix[3] = {i0 + lx, j0 + ly, 0};
+        vv[q] = face_velocity(P, W, ix, 1);
+    };
+    TILE_RECT(0, RX, Y0 - 1, Y1) rho_at(lx, ly, q);
+    TILE_RECT(X0 - 1, X1, 0, Y0 - 1) rho_at(lx, ly, q);
+    TILE_RECT(X0 - 1, X1, Y1, RY) rho_at(lx, ly, q);
+    TILE_RECT(1, RX, Y0, Y1) e_at(lx, ly, q);
+    TILE_RECT(X0, X1, 1, Y0) e_at(lx, ly, q);
+    TILE_RECT(X0, X1, Y1, RY) e_at(lx, ly, q);
+    TILE_RECT(1, RX, Y0, Y1) u_at(lx, ly, q);
+    TILE_RECT(X0, X1, 1, Y0) u_at(lx, ly, q);
+    TILE_RECT(X0, X1, Y1, RY) u_at(lx, ly, q);
+    if (tid == 0) u_at(X0 - 1, Y0 - 1, (Y0 - 1) * RX + X0 - 1);
+    if (tid == 1) u_at(X1, Y0 - 1, (Y0 - 1) * RX + X1);
+    TILE_RECT(X0, X1, 1, RY) v_at(lx, ly, q);
+    TILE_RECT(1, X0, Y0, Y1) v_at(lx, ly, q);
+    TILE_RECT(X1, RX, Y0, Y1) v_at(lx, ly, q);
+    if (tid == 2) v_at(X0 - 1, Y0 - 1, (Y0 - 1) * RX + X0 - 1);
+    if (tid == 3) v_at(X0 - 1, Y1, Y1 * RX + X0 - 1);
+    __syncthreads();
+
+    // ---- phase 2: limited slopes, each on the rectangle its fluxes need
+    TILE_RECT(X0 - 2, X1 + 1, Y0 - 1, Y1) srx[q] = vanleer(rho[q] - rho[q - 1], rho[q + 1] - rho[q]);
+    TILE_RECT(X0 - 1, X1 + 1, Y0, Y1) sex[q] = vanleer(ee[q] - ee[q - 1], ee[q + 1] - ee[q]);
+    TILE_RECT(X0 - 1, X1, Y0 - 2, Y1 + 1) sry[q] = vanleer(rho[q] - rho[q - RX], rho[q + RX] - rho[q]);
+    TILE_RECT(X0, X1, Y0 - 1, Y1 + 1) sey[q] = vanleer(ee[q] - ee[q - RX], ee[q + RX] - ee[q]);
+    TILE_RECT(X0 - 1, X1 + 1, Y0, Y1) {
+        sux[q] = vanleer(uu[q] - uu[q - 1], uu[q + 1] - uu[q]);
+        svx[q] = vanleer(vv[q] - vv[q - 1], vv[q + 1] - vv[q]);
+    }
+    TILE_RECT(X0, X1, Y0 - 1, Y1 + 1) {
+        suy[q] = vanleer(uu[q] - uu[q - RX], uu[q + RX] - uu[q]);
+        svy[q] = vanleer(vv[q] - vv[q - RX], vv[q + RX] - vv[q]);
+    }
+    __syncthreads();
+
+    // ---- phase 3: upwind mass and energy fluxes
+    TILE_RECT(X0 - 1, X1 + 1, Y0 - 1, Y1) {
+        const double u = uu[q];
+        const bool up = (u >= 0.0);
+        const double rs = up ? rho[q - 1] + 0.5 * srx[q - 1] : rho[q] - 0.5 * srx[q];
+        const double fr = u * rs;
+        Frx[q] = fr;
+        if (lx >= X0 && ly >= Y0) {
+            const double es = up ? ee[q - 1] + 0.5 * sex[q - 1] : ee[q] - 0.5 * sex[q];
+            FEx[q] = fr * es;
+        }
+    }
+    TILE_RECT(X0 - 1, X1, Y0 - 1, Y1 + 1) {
+        const double u = vv[q];
+        const bool up = (u >= 0.0);
+        const double rs = up ? rho[q - RX] + 0.5 * sry[q - RX] : rho[q] - 0.5 * sry[q];
+        const double fr = u * rs;
+        Fry[q] = fr;
+        if (lx >= X0 && ly >= Y0) {
+            const double es = up ? ee[q - RX] + 0.5 * sey[q - RX] : ee[q] - 0.5 * sey[q];
+            FEy[q] = fr * es;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 4: momentum fluxes
+    TILE_RECT(X0 - 1, X1, Y0, Y1) {
+        const double fm = 0.5 * (Frx[q] + Frx[q + 1]);
+        const double us = (fm >= 0.0) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
+        Phx[q] = fm * us;
+    }
+    TILE_RECT(X0, X1, Y0 - 1, Y1) {
+        const double fm = 0.5 * (Fry[q] + Fry[q + RX]);
+        const double us = (fm >= 0.0) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
+        Phy[q] = fm * us;
+    }
+    TILE_RECT(X0, X1, Y0, Y1 + 1) {
+        const double fm = 0.5 * (Fry[q - 1] + Fry[q]);
+        const double us = (fm >= 0.0) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
+        Psxy[q] = fm * us;
+    }
+    TILE_RECT(X0, X1 + 1, Y0, Y1) {
+        const double fm = 0.5 * (Frx[q - RX] + Frx[q]);
+        const double us = (fm >= 0.0) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
+        Psyx[q] = fm * us;
+    }
+    __syncthreads();
+
+    // ---- phase 5: residuals of the tile
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx = bx * TX + tx, gy = by * TY + ty;
+    if (gx >= P.n[0] || gy >= P.n[1]) return;
+    const int q = (ty + Y0) * RX + (tx + X0);
+    const double ix0 = P.idx[0], ix1 = P.idx[1];
+    double Rv[4];
+    {
+        double accr = (Frx[q + 1] - Frx[q]) * ix0;
+        accr += (Fry[q + RX] - Fry[q]) * ix1;
+        double acce = (FEx[q + 1] - FEx[q]) * ix0;
+        acce += (FEy[q + RX] - FEy[q]) * ix1;
+        double divu = (uu[q + 1] - uu[q]) * ix0;
+        divu += (vv[q + RX] - vv[q]) * ix1;
+        Rv[0] = -accr;
+        Rv[1] = -acce - pp[q] * divu;
+    }
+    if (P.bc[0] == MUSIC_BC_WALL && gx == 0) {
+        Rv[2] = 0.0;
+    } else {
+        double acc = (Phx[q] - Phx[q - 1]) * ix0;
+        acc += (Psxy[q + RX] - Psxy[q]) * ix1;
+        const double rbar = 0.5 * (rho[q - 1] + rho[q]);
+        Rv[2] = (-acc - (pp[q] - pp[q - 1]) * ix0) + rbar * P.g[0];
+    }
+    if (P.bc[1] == MUSIC_BC_WALL && gy == 0) {
+        Rv[3] = 0.0;
+    } else {
+        double acc = (Psyx[q + 1] - Psyx[q]) * ix0;
+        acc += (Phy[q] - Phy[q - RX]) * ix1;
+        const double rbar = 0.5 * (rho[q - RX] + rho[q]);
+        Rv[3] = (-acc - (pp[q] - pp[q - RX]) * ix1) + rbar * P.g[1];
+    }
+    const long long c = gx + (long long)P.n[0] * gy;
+    const double c_jv = (MODE == SM_JV && epsv != 0.0) ? hdt / epsv : 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const long long i = (long long)k * P.N + c;
+        if (MODE == SM_R) {
+            out[i] = (VOUT)Rv[k];
+        } else if (MODE == SM_CN) {
+            out[i] = (VOUT)(U[i] + hdt * Rv[k]);
+        } else if (MODE == SM_F) {
+            out[i] = (VOUT)(sign * ((U[i] - aux[i]) - hdt * Rv[k]));
+            if (RU_out) RU_out[i] = Rv[k];
+        } else {
+            out[i] = (epsv == 0.0) ? (VOUT)0 : (VOUT)((double)v[i] - c_jv * (Rv[k] - aux[i]));
+        }
+    }
+}
+#undef TILE_RECT
+
+}  // namespace tile

@@ -1,0 +1,78 @@
+"""Persistent batched step (music_batch_step): many grids, one launch."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1610_10053_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_parity import B, diag_close  # noqa: E402
+
+
+def problems():
+    return [I.rayleigh_taylor(nx=32, ny=96, nsteps=3), I.kelvin_helmholtz(n=64, seed=3, nsteps=3),
+            I.kelvin_helmholtz(n=40, ny=72, seed=4, nsteps=3), I.rayleigh_taylor(nx=20, ny=60, nsteps=3)]
+
+
+def run_batched(probs, prec, nsteps):
+    grids = [B().Grid(p, precision=prec) for p in probs]
+    for g, p in zip(grids, probs):
+        g.set_state(p.U)
+    stats = []
+    for _ in range(nsteps):
+        code, st = B().batch_step(grids)
+        assert code == 0, B().last_error()
+        stats.append(st)
+    out = [(g.get_state(), g.diagnostics()) for g in grids]
+    for g in grids:
+        g.close()
+    return out, stats
+
+
+def test_batched_fp64_matches_oracle():
+    probs = problems()
+    out, stats = run_batched(probs, B().FP64, 3)
+    for k, p in enumerate(probs):
+        Uref, sref = O.run(p)
+        dref = O.diagnostics(p, Uref)
+        same = all(stats[s][k]["gmres_its"] == sref[s]["gmres_its"] for s in range(3))
+        for s in range(3):
+            assert stats[s][k]["newton_its"] == sref[s]["newton_its"]
+        tol = 1e-9 if same else p.newton_tol
+        U, d = out[k]
+        N = p.ncells
+        for v in range(p.nvars):
+            sl = slice(v * N, (v + 1) * N)
+            assert np.abs(U[sl] - Uref[sl]).max() <= tol * (np.abs(Uref[sl]).max() + 1e-300), (k, v, same)
+        diag_close(d, dref, tol)
+
+
+def test_batched_mixed_matches_oracle_diagnostics():
+    probs = problems()
+    out, _ = run_batched(probs, B().MIXED, 3)
+    for k, p in enumerate(probs):
+        Uref, _ = O.run(p)
+        diag_close(out[k][1], O.diagnostics(p, Uref), 1e-6)
+
+
+def test_batch_member_is_independent_of_the_batch():
+    """A grid's step in a batch of one and in a batch of many is bitwise the
+    same: every CTA works on its own grid only."""
+    probs = problems()
+    alone, _ = run_batched([probs[1]], B().MIXED, 2)
+    mixed, _ = run_batched(probs, B().MIXED, 2)
+    assert np.array_equal(alone[0][0], mixed[1][0])
+
+
+def test_batch_rejects_unsupported_grids():
+    p3 = I.taylor_green(n=8)
+    with B().Grid(p3) as g3, B().Grid(problems()[0]) as g2:
+        with pytest.raises(B().MusicError):
+            B().batch_step([g2, g3])
+    pc = I.random_smooth(2, (16, 16), seed=1).with_options(conduct=1, chi0=0.01)
+    with B().Grid(pc) as gc:
+        with pytest.raises(B().MusicError):
+            B().batch_step([gc], cfl=[1.0])

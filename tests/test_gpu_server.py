@@ -2,7 +2,9 @@
 
 Each solve must give the same result alone and in a mix (every reduction is
 deterministic, so equality is bitwise), admission must respect the memory
-budget, and one failing solve must not disturb the others.
+budget, and one failing solve must not disturb the others.  A solve the batch
+lane takes is compared with the same solve stepped alone as a batch of one
+(music_batch_step); every other solve with the per-grid path (music_newton_step).
 """
 import numpy as np
 import pytest
@@ -30,16 +32,30 @@ def mix():
     ]
 
 
-def alone(prob, prec):
+LANE_CELLS = 16384  # the server's default batch_max_cells
+
+
+def lane_route(prob, lane_cells=LANE_CELLS):
+    return (lane_cells >= 0 and prob.nd == 2 and prob.geometry == I.GEOM_CARTESIAN and not prob.conduct
+            and prob.sweeps <= 16 and prob.ncells <= lane_cells)
+
+
+def alone(prob, prec, lane_cells=LANE_CELLS):
     with B().Grid(prob, precision=prec) as g:
         g.set_state(prob.U)
-        g.run()
+        if lane_route(prob, lane_cells):
+            for _ in range(prob.nsteps):
+                code, _st = B().batch_step([g])
+                assert code == 0
+        else:
+            g.run()
         return g.get_state(), g.diagnostics()
 
 
-def test_same_result_alone_and_in_the_mix():
+@pytest.mark.parametrize("lane_cells", [LANE_CELLS, -1], ids=["batch-lane", "workers-only"])
+def test_same_result_alone_and_in_the_mix(lane_cells):
     reqs = mix()
-    with B().Server(max_active=4) as s:
+    with B().Server(max_active=4, batch_max_cells=lane_cells) as s:
         tickets = [s.submit(p, prec) for p, prec in reqs]
         results = [s.wait(t, timeout_ms=300000) for t in tickets]
         states = [s.result_state(t) for t in tickets]
@@ -47,7 +63,7 @@ def test_same_result_alone_and_in_the_mix():
         lat = s.step_times()
     for (p, prec), r, U in zip(reqs, results, states):
         assert r["status"] == 0 and r["steps_done"] == p.nsteps
-        U1, d1 = alone(p, prec)
+        U1, d1 = alone(p, prec, lane_cells)
         assert np.array_equal(U, U1), p.name
         assert r["diag"] == [d1[k] for k in ("mixing_height", "max_mach", "kh_mode_amplitude",
                                              "vertical_kinetic_energy", "mean_kinetic_energy", "max_speed")]
@@ -101,3 +117,26 @@ def test_failing_solve_does_not_disturb_the_mix():
     assert rg["status"] == 0
     U1, _ = alone(good, B().MIXED)
     assert np.array_equal(Ug, U1)
+
+
+def test_continuous_batching_in_the_lane():
+    """More small solves than lane slots, of mixed lengths and precisions: they
+    join and leave the batch at step boundaries and each matches its batch of one."""
+    reqs = []
+    for k in range(20):
+        if k % 3 == 0:
+            p = I.rayleigh_taylor(nx=16, ny=48, nsteps=1 + k % 4)
+        else:
+            p = I.kelvin_helmholtz(n=32 + 16 * (k % 3), seed=20 + k, nsteps=1 + k % 5)
+        reqs.append((p, k % 2))
+    with B().Server(max_active=2, batch_size=6) as s:
+        tickets = [s.submit(p, prec) for p, prec in reqs]
+        results = [s.wait(t, timeout_ms=300000) for t in tickets]
+        states = [s.result_state(t) for t in tickets]
+        st = s.stats()
+    for (p, prec), r, U in zip(reqs, results, states):
+        assert lane_route(p)
+        assert r["status"] == 0 and r["steps_done"] == p.nsteps
+        U1, _ = alone(p, prec)
+        assert np.array_equal(U, U1), p.name
+    assert st["cell_steps"] == sum(p.ncells * p.nsteps for p, _ in reqs)
