@@ -134,6 +134,7 @@ GridParams make_params(const music_grid_desc &d)
     P.lum = d.lum;
     for (int k = 0; k < 3; k++) P.flux_wall[k] = (k < d.ndim && d.bc[k] == MUSIC_BC_WALL) ? d.flux_wall[k] : 0;
     P.gface = nullptr;
+    P.dt_dev = nullptr;
     return P;
 }
 
@@ -148,7 +149,7 @@ void alloc_plan(music_grid *g, F &&f)
     const size_t ks = g->mixed ? sizeof(float) : sizeof(double);
     for (double **p : {&g->U, &g->Un, &g->Cn, &g->RU, &g->b, &g->x, &g->t64}) f((void **)p, n * sizeof(double));
     f(&g->V, (size_t)(d.gmres_restart + 1) * n * ks);
-    for (void **p : {&g->w, &g->z, &g->u}) f(p, n * ks);
+    for (void **p : {&g->w, &g->z, &g->u, &g->q}) f(p, n * ks);
     if (d.precond != MUSIC_PC_NONE) {
         for (int k = 0; k < P.nd; k++) f(&g->pa[k], N * ks);
         for (void **p : {&g->pgp, &g->php, &g->pD, &g->pb, &g->pdp, &g->pdq}) f(p, N * ks);
@@ -181,6 +182,7 @@ void alloc_plan(music_grid *g, F &&f)
     f((void **)&g->hg, (size_t)(MUSIC_MAXV * MUSIC_MAXV + 4 * MUSIC_MAXV) * sizeof(double));
     f(&g->binst, 1024);  // batched-solver descriptor (sizeof checked in batched.cu)
     f((void **)&g->ds, sizeof(DevScalars));
+    f((void **)&g->ctl, sizeof(SolveCtl));
     f((void **)&g->diag_rows, (size_t)8 * P.n[1] * sizeof(double));
 }
 
@@ -196,6 +198,9 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep
     const char *pv = getenv("MUSIC_PRECOND");
     g->pc_variant = (pv && strcmp(pv, "multikernel") == 0) ? PC_MULTIKERNEL : PC_AUTO;
+    // MUSIC_SOLVER=host sequences Newton and GMRES from the host
+    const char *so = getenv("MUSIC_SOLVER");
+    g->solver_variant = (so && strcmp(so, "host") == 0) ? SOLVER_HOST : SOLVER_GRAPH;
     g->n = (size_t)g->P.nv * g->P.N;
     // reduction blocks: enough to fill the GPU, fixed per grid
     long long nb = ((long long)g->n + 255) / 256;
@@ -205,6 +210,7 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
 void free_grid(music_grid *g)
 {
     if (!g) return;
+    graph_release(g);
     alloc_plan(g, [&](void **slot, size_t) {
         if (*slot) cudaFreeAsync(*slot, g->home);
         *slot = nullptr;
@@ -227,7 +233,15 @@ int check_grid(const music_grid *g)
 
 }  // namespace
 
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local long long t_launches = 0;
+
+void count_launch()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    t_launches++;
+}
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long capture_launches() { return t_launches; }
 
 void fill_grid_params(const music_grid_desc &d, GridParams *P) { *P = make_params(d); }
 

@@ -29,7 +29,24 @@ struct GridParams {
     double chi0, lum;
     int flux_wall[3];
     const double *gface;   // spherical: radial gravity on the n[0]+1 r-faces (device), or null
+    const double *dt_dev;  // launches recorded into a solver graph read dt here (device), else null
 };
+
+// dt/2 of a launch: the value passed, or the device copy for launches that
+// were recorded into a solver graph (same arithmetic either way)
+__device__ __forceinline__ double call_hdt(const GridParams &P, double hdt)
+{
+    return P.dt_dev ? 0.5 * *P.dt_dev : hdt;
+}
+template <typename PT>
+__device__ __forceinline__ void call_tau(const GridParams &P, PT &tau, PT &tau2)
+{
+    if (P.dt_dev) {
+        const double t = 0.5 * *P.dt_dev;
+        tau = (PT)t;
+        tau2 = (PT)(t * t);
+    }
+}
 
 // ---- spherical (r, theta) metric, 2 pi dropped (2-D axisymmetric grids)
 __host__ __device__ inline double sph_r(const GridParams &P, double i) { return P.x0[0] + i * P.dx[0]; }
@@ -80,6 +97,29 @@ struct DevScalars {
 };
 
 enum { CNT_DOTS = 0, CNT_UPDATE, CNT_NORMW, CNT_SUMSQ, CNT_NEWTON, CNT_PRECOND };
+
+// Control state of one Newton attempt driven from the device (solver graph):
+// loop counters, statistics and status first (the host reads these back),
+// then the Hessenberg matrix with its Givens rotations.
+struct SolveCtl {
+    double dt;                         // step size of the attempt
+    double bnorm, target, beta, resid; // |b|, eta |b|, cycle start residual, current residual
+    double inv;                        // 1 / h_{j+1,j} of the pending basis scaling
+    double fnorm0, fnorm, maxdrho;
+    int j;            // Arnoldi index of the next iteration
+    int k;            // basis vectors in the current cycle's correction
+    int scale_idx;    // basis vector the pending scaling writes
+    int scale;        // 1: V[scale_idx] = w * inv pending
+    int cycle, converged, its;
+    int newton_it, newton_its, gmres_its, unconverged;
+    int cycles, restarts, solves;  // bodies run: cycles, restart residuals, corrections
+    int status;       // MUSIC_OK, MUSIC_E_NONFINITE, or MUSIC_E_TIMEOUT (loop cap reached)
+    int stop;         // 1: leave every loop (hard error)
+    int ok;           // 1: Newton converged
+    int guard;        // loop bodies run, against a hard cap
+    double cs[MUSIC_MAXV], sn[MUSIC_MAXV], gv[MUSIC_MAXV + 1], y[MUSIC_MAXV];
+    double H[MUSIC_MAXV * MUSIC_MAXV]; // H[i * MUSIC_MAXV + j]
+};
 
 __host__ __device__ inline long long ext_index(const GridParams &P, int i, int j, int k)
 {

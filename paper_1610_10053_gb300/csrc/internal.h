@@ -23,6 +23,7 @@ struct ExtScratch {
 };
 
 enum StencilVariant { STENCIL_AUTO = 0, STENCIL_FUSED = 1, STENCIL_MULTIPASS = 2 };
+enum SolverVariant { SOLVER_GRAPH = 0, SOLVER_HOST = 1 };
 enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
 
 // grids that need the general (geometry / conduction) code paths
@@ -32,6 +33,7 @@ struct music_grid {
     music_grid_desc desc;
     int stencil_variant;  // STENCIL_*: fused shared-memory kernel (2-D) or multi-pass
     int pc_variant;       // PC_*: fused 2-D preconditioner kernel or one kernel per sweep
+    int solver_variant;   // SOLVER_*: device-driven graph or host-sequenced Newton/GMRES
     GridParams P;
     int mixed;
     int device;
@@ -43,6 +45,7 @@ struct music_grid {
     double *U, *Un, *Cn, *RU, *b, *x, *t64, *t64b;
     // Krylov vectors (float for mixed, double otherwise)
     void *V, *w, *z, *u;
+    void *q;              // copy of the current Arnoldi vector (solver graph)
     // preconditioner (float for mixed, double otherwise)
     void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
     void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
@@ -54,6 +57,10 @@ struct music_grid {
     double *partials;      // [MUSIC_MAXV][nb]
     DevScalars *ds;        // device scalars
     DevScalars *hs;        // pinned host mirror
+    SolveCtl *ctl;         // device control of a graph-driven Newton attempt
+    SolveCtl *hctl;        // pinned host mirror of its leading scalars
+    cudaGraphExec_t gexec; // the recorded Newton attempt (null until first use)
+    long long glaunch[6];  // kernels per recorded section: top, Newton, cycle, restart, correction, Arnoldi
     double *diag_rows;     // per-row diagnostic partials
     // optional timing of the Jacobian-free stencil launches (music_profile_*)
     int prof_on;
@@ -108,16 +115,18 @@ int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst
 int final_sum(music_grid *g, int count, double *dst, cudaStream_t s);
 // eps = sqrt(2^-52) (1 + sqrt(unorm2)) / sqrt(vnorm2), or the fixed value if > 0
 int dev_set_eps(music_grid *g, double fixed, cudaStream_t s);
-int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s);          // h = V[0..j]^T w
-int krylov_update_dots(music_grid *g, int j, cudaStream_t s);                  // w -= V h; h2 = V^T w
-int krylov_update_norm(music_grid *g, int j, cudaStream_t s);                  // w -= V h2; wnorm2
+// the three CGS passes; jdev (device, or null) overrides j, which then bounds it
+int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s);        // h = V[0..j]^T w
+int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h; h2 = V^T w
+int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h2; wnorm2
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s);            // V_{j+1} = w * inv
 int krylov_first(music_grid *g, const double *r, double inv, cudaStream_t s);  // V_0 = r * inv
-int krylov_combine(music_grid *g, int k, const double *y, cudaStream_t s);     // u = sum y_i V_i
+// u = sum_{i<k} y_i V_i; kdev / ydev (device, or null) override k / y
+int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s);
 int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s);      // x += z (z Krylov type)
 int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaStream_t s); // out = a - b
 int vec_neg(music_grid *g, const double *a, double *out, cudaStream_t s);
-int newton_update(music_grid *g, cudaStream_t s);                              // U += x, maxdrho
+int newton_update(music_grid *g, const int *skip, cudaStream_t s);             // U += x, maxdrho (unless *skip)
 int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, size_t n, cudaStream_t s);
 
 // ----- precond.cu -----
@@ -147,3 +156,17 @@ extern "C" int music_batch_step(music_grid **grids, int count, const double *cfl
 
 // ----- solver.cu -----
 int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);
+// J v for the current Newton iterate (eps from |U| and, with need_vnorm, |v|)
+int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
+             int need_vnorm, cudaStream_t s);
+
+// ----- graph.cu -----
+// One Newton attempt (Sec. 2) as a recorded CUDA graph whose Newton, restart
+// and Arnoldi loops are conditional nodes driven by device-side control.
+// Same arguments and results as the host-sequenced attempt.
+int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);
+void graph_release(music_grid *g);
+
+// ----- api.cu -----
+void count_launches(long long k);   // add kernels run by a graph launch
+long long capture_launches();       // kernels launched by this thread so far

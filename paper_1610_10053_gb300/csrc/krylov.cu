@@ -55,8 +55,8 @@ __global__ void k_set_eps(DevScalars *ds, double fixed)
 
 // h_i = <V_i, w>, i <= j; accumulators in registers (NVM >= j + 1).
 template <int NVM, typename KT>
-__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
-                                             int nb, double *dst, unsigned int *counter)
+__device__ __forceinline__ void k_dots_body(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
+                                            double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double acc[NVM];
@@ -78,11 +78,31 @@ __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long
     if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
 }
 
+template <int NVM, typename KT>
+__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
+                                  double *dst, unsigned int *counter, const int *jdev)
+{
+    if (!jdev) {
+        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter);
+        return;
+    }
+    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
+    j = *jdev;
+    if (j < 8)
+        k_dots_body<8, KT>(V, w, n, j, partial, nb, dst, counter);
+    else if (NVM > 8 && j < 16)
+        k_dots_body<(NVM > 8 ? 16 : 8), KT>(V, w, n, j, partial, nb, dst, counter);
+    else if (NVM > 16 && j < 32)
+        k_dots_body<(NVM > 16 ? 32 : 8), KT>(V, w, n, j, partial, nb, dst, counter);
+    else
+        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter);
+}
+
 // w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
 // NORM, |w|^2 only.
 template <int NVM, bool NORM, typename KT>
-__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                               double *partial, int nb, double *dst, unsigned int *counter)
+__device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, int j, const double *h,
+                                              double *partial, int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     __shared__ double hs[MUSIC_MAXV];
@@ -122,6 +142,26 @@ __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, 
     if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
 }
 
+template <int NVM, bool NORM, typename KT>
+__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
+{
+    if (!jdev) {
+        k_update_body<NVM, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
+        return;
+    }
+    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
+    j = *jdev;
+    if (j < 8)
+        k_update_body<8, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
+    else if (NVM > 8 && j < 16)
+        k_update_body<(NVM > 8 ? 16 : 8), NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
+    else if (NVM > 16 && j < 32)
+        k_update_body<(NVM > 16 ? 32 : 8), NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
+    else
+        k_update_body<NVM, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
+}
+
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long long n, double inv)
 {
@@ -137,11 +177,16 @@ __global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long lon
 }
 
 template <typename KT>
-__global__ void __launch_bounds__(BS) k_combine(const KT *V, KT *u, long long n, int k, Coef y)
+__global__ void __launch_bounds__(BS) k_combine(const KT *V, KT *u, long long n, int k, Coef y, const int *kdev,
+                                                const double *ydev)
 {
+    __shared__ double ys[MUSIC_MAXV];
+    if (kdev) k = *kdev;
+    for (int i = threadIdx.x; i < k; i += BS) ys[i] = ydev ? ydev[i] : y.c[i];
+    __syncthreads();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         double s = 0.0;
-        for (int i = 0; i < k; i++) s += y.c[i] * (double)V[(long long)i * n + e];
+        for (int i = 0; i < k; i++) s += ys[i] * (double)V[(long long)i * n + e];
         u[e] = (KT)s;
     }
 }
@@ -174,8 +219,10 @@ __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
 
 // U += x over all unknowns; partial max of |x_rho| / rho_new over cells.
 __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
-                                                      double *partial, double *dst, unsigned int *counter)
+                                                      double *partial, double *dst, unsigned int *counter,
+                                                      const int *skip)
 {
+    if (skip && *skip) return;  // a hard error ended the linear solve: U stays as it is
     __shared__ double sh[BS / 32];
     double m = 0.0;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
@@ -200,8 +247,8 @@ __device__ inline float dot4(const float4 a, const float4 b)
 }
 
 template <int NVM>
-__global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
-                                                 double *partial, int nb, double *dst, unsigned int *counter)
+__device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, long long n, int j, double *partial,
+                                                int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     double acc[NVM];
@@ -233,9 +280,29 @@ __global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w,
     if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
 }
 
+template <int NVM>
+__global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
+{
+    if (!jdev) {
+        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter);
+        return;
+    }
+    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
+    j = *jdev;
+    if (j < 8)
+        k_dots_f32_body<8>(V, w, n, j, partial, nb, dst, counter);
+    else if (NVM > 8 && j < 16)
+        k_dots_f32_body<(NVM > 8 ? 16 : 8)>(V, w, n, j, partial, nb, dst, counter);
+    else if (NVM > 16 && j < 32)
+        k_dots_f32_body<(NVM > 16 ? 32 : 8)>(V, w, n, j, partial, nb, dst, counter);
+    else
+        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter);
+}
+
 template <int NVM, bool NORM>
-__global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
-                                                   double *partial, int nb, double *dst, unsigned int *counter)
+__device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long long n, int j, const double *h,
+                                                  double *partial, int nb, double *dst, unsigned int *counter)
 {
     __shared__ double sh[BS / 32];
     __shared__ float hs[MUSIC_MAXV];
@@ -299,10 +366,32 @@ __global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, lon
     if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
 }
 
-__global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, long long n, int k, Coef y)
+template <int NVM, bool NORM>
+__global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
+{
+    if (!jdev) {
+        k_update_f32_body<NVM, NORM>(V, w, n, j, h, partial, nb, dst, counter);
+        return;
+    }
+    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
+    j = *jdev;
+    if (j < 8)
+        k_update_f32_body<8, NORM>(V, w, n, j, h, partial, nb, dst, counter);
+    else if (NVM > 8 && j < 16)
+        k_update_f32_body<(NVM > 8 ? 16 : 8), NORM>(V, w, n, j, h, partial, nb, dst, counter);
+    else if (NVM > 16 && j < 32)
+        k_update_f32_body<(NVM > 16 ? 32 : 8), NORM>(V, w, n, j, h, partial, nb, dst, counter);
+    else
+        k_update_f32_body<NVM, NORM>(V, w, n, j, h, partial, nb, dst, counter);
+}
+
+__global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, long long n, int k, Coef y,
+                                                    const int *kdev, const double *ydev)
 {
     __shared__ float ys[MUSIC_MAXV];
-    for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)y.c[i];
+    if (kdev) k = *kdev;
+    for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)(ydev ? ydev[i] : y.c[i]);
     __syncthreads();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         float s = 0.0f;
@@ -326,32 +415,32 @@ int grid_blocks(long long n, int cap)
 }
 
 template <int NVM>
-int launch_dots(music_grid *g, int j, cudaStream_t s)
+int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     unsigned int *cnt = &g->ds->counters[CNT_DOTS];
     if (g->mixed)
         k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
-                                             g->ds->h, cnt);
+                                             g->ds->h, cnt, jdev);
     else
         k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
-                                                 g->nb, g->ds->h, cnt);
+                                                 g->nb, g->ds->h, cnt, jdev);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
 template <int NVM, bool NORM>
-int launch_update(music_grid *g, int j, const double *h, cudaStream_t s)
+int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
     unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
     if (g->mixed)
         k_update_f32<NVM, NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
-                                                      g->nb, dst, cnt);
+                                                      g->nb, dst, cnt, jdev);
     else
         k_update<NVM, NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h,
-                                                         g->partials, g->nb, dst, cnt);
+                                                         g->partials, g->nb, dst, cnt, jdev);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -383,45 +472,34 @@ int dev_set_eps(music_grid *g, double fixed, cudaStream_t s)
     return MUSIC_OK;
 }
 
-int krylov_dots(music_grid *g, int j, double *dst_h, cudaStream_t s)
+// NVM (basis vectors a thread accumulates) covers j; with jdev the index is
+// read on the device and j is its upper bound.
+int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
-    if (j < 8)
-        TRY(launch_dots<8>(g, j, s));
-    else if (j < 16)
-        TRY(launch_dots<16>(g, j, s));
-    else if (j < 32)
-        TRY(launch_dots<32>(g, j, s));
-    else
-        TRY(launch_dots<64>(g, j, s));
-    return MUSIC_OK;
+    if (j < 8) return launch_dots<8>(g, j, jdev, s);
+    if (j < 16) return launch_dots<16>(g, j, jdev, s);
+    if (j < 32) return launch_dots<32>(g, j, jdev, s);
+    return launch_dots<64>(g, j, jdev, s);
 }
 
-int krylov_update_dots(music_grid *g, int j, cudaStream_t s)
+template <bool NORM>
+int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
-    const double *h = g->ds->h;
-    if (j < 8)
-        TRY((launch_update<8, false>(g, j, h, s)));
-    else if (j < 16)
-        TRY((launch_update<16, false>(g, j, h, s)));
-    else if (j < 32)
-        TRY((launch_update<32, false>(g, j, h, s)));
-    else
-        TRY((launch_update<64, false>(g, j, h, s)));
-    return MUSIC_OK;
+    const double *h = NORM ? g->ds->h2 : g->ds->h;
+    if (j < 8) return launch_update<8, NORM>(g, j, jdev, h, s);
+    if (j < 16) return launch_update<16, NORM>(g, j, jdev, h, s);
+    if (j < 32) return launch_update<32, NORM>(g, j, jdev, h, s);
+    return launch_update<64, NORM>(g, j, jdev, h, s);
 }
 
-int krylov_update_norm(music_grid *g, int j, cudaStream_t s)
+int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
-    const double *h = g->ds->h2;
-    if (j < 8)
-        TRY((launch_update<8, true>(g, j, h, s)));
-    else if (j < 16)
-        TRY((launch_update<16, true>(g, j, h, s)));
-    else if (j < 32)
-        TRY((launch_update<32, true>(g, j, h, s)));
-    else
-        TRY((launch_update<64, true>(g, j, h, s)));
-    return MUSIC_OK;
+    return update_any<false>(g, j, jdev, s);
+}
+
+int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s)
+{
+    return update_any<true>(g, j, jdev, s);
 }
 
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
@@ -450,16 +528,16 @@ int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
     return MUSIC_OK;
 }
 
-int krylov_combine(music_grid *g, int k, const double *y, cudaStream_t s)
+int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s)
 {
     Coef c;
-    for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (i < k) ? y[i] : 0.0;
+    for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (y && i < k) ? y[i] : 0.0;
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
-        k_combine_f32<<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c);
+        k_combine_f32<<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c, kdev, ydev);
     else
-        k_combine<double><<<nb, BS, 0, s>>>((const double *)g->V, (double *)g->u, n, k, c);
+        k_combine<double><<<nb, BS, 0, s>>>((const double *)g->V, (double *)g->u, n, k, c, kdev, ydev);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -507,10 +585,10 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
     return MUSIC_OK;
 }
 
-int newton_update(music_grid *g, cudaStream_t s)
+int newton_update(music_grid *g, const int *skip, cudaStream_t s)
 {
     k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials, &g->ds->maxdrho,
-                                          &g->ds->counters[CNT_NEWTON]);
+                                          &g->ds->counters[CNT_NEWTON], skip);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

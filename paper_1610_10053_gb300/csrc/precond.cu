@@ -52,6 +52,8 @@ __device__ inline PT a_up(const GridParams &P, const PC<PT> &C, const int ix[3],
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
 {
+    PT tau_unused = 0;
+    call_tau(P, tau_unused, tau2);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -64,6 +66,8 @@ __global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
 template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, const RT *r, PT *b, PT tau)
 {
+    PT tau2_unused = 0;
+    call_tau(P, tau, tau2_unused);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -83,6 +87,8 @@ template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, const PT *b, const PT *dp, PT *dq,
                                                PT tau2)
 {
+    PT tau_unused = 0;
+    call_tau(P, tau_unused, tau2);
     const PT w = (PT)MUSIC_JACOBI_OMEGA;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
@@ -113,6 +119,8 @@ template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, const RT *r, const PT *dp, RT *z, PT tau,
                                              double *partial)
 {
+    PT tau2_unused = 0;
+    call_tau(P, tau, tau2_unused);
     __shared__ double sh[BS / 32];
     double nrm = 0.0;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
@@ -222,6 +230,7 @@ __global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<P
                                                                PT tau, PT tau2, int K, double *partial,
                                                                DevScalars *ds)
 {
+    call_tau(P, tau, tau2);
     constexpr int NT = PTX * PTY;
     extern __shared__ unsigned char smraw[];
     __shared__ double red[NT / 32];
@@ -339,6 +348,7 @@ __global__ void __launch_bounds__(BS) k_gen_cell(GridParams P, const double *U, 
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_face(GridParams P, PCG<PT> C, double tau)
 {
+    tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -360,6 +370,7 @@ __device__ inline void up_coeffs(const GridParams &P, const PCG<PT> &C, const in
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double tau)
 {
+    tau = call_hdt(P, tau);
     const double tau2 = tau * tau;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
@@ -381,6 +392,7 @@ __global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_rhs(GridParams P, PCG<PT> C, const PT *r, PT *b, double tau)
 {
+    tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -400,6 +412,7 @@ template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq,
                                                    double tau)
 {
+    tau = call_hdt(P, tau);
     const double w = MUSIC_JACOBI_OMEGA, tau2 = tau * tau;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
@@ -429,6 +442,7 @@ template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_back(GridParams P, PCG<PT> C, const PT *r, const PT *dp, PT *z,
                                                  double tau)
 {
+    tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);

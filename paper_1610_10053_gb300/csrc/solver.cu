@@ -1,7 +1,9 @@
 // Newton-Raphson on the Crank-Nicolson system with restarted, right
-// preconditioned GMRES and Jacobian-free products (Sec. 2).  The host
-// sequences the kernels and keeps the (m+1) x m Hessenberg matrix and its
-// Givens rotations; every vector operation runs on the device.
+// preconditioned GMRES and Jacobian-free products (Sec. 2).  Two drivers run
+// the same kernels: the recorded graph of graph.cu (default), whose loops
+// and Givens rotations run on the device, and the host-sequenced attempt
+// below, which keeps the (m+1) x m Hessenberg matrix on the host and is used
+// while the Jacobian-free stencil is being timed (music_profile_enable).
 #include <cmath>
 #include <cstring>
 #include <chrono>
@@ -22,19 +24,6 @@ int sync_scalars(music_grid *g, cudaStream_t s)
     CUDA_TRY(cudaStreamSynchronize(s));
     if (g->prof_pending) TRY(prof_harvest(g, 0));
     return MUSIC_OK;
-}
-
-// J v for the current Newton iterate: v (Krylov type, or FP64 when
-// vin_double) -> out.  eps from |U| (ds->unorm2) and |v|.
-int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
-             int need_vnorm, cudaStream_t s)
-{
-    // eps comes with |v|: computed here, or already by the preconditioner
-    if (need_vnorm) {
-        TRY(dev_norm2(g, v, vin_double, g->n, &g->ds->vnorm2, s));
-        TRY(dev_set_eps(g, 0.0, s));
-    }
-    return stencil_apply(g, SM_JV, g->U, g->RU, v, vin_double, out, out_double, nullptr, dt, 1.0, s);
 }
 
 // Solve J x = b (b = g->b, FP64) into g->x (FP64).
@@ -94,9 +83,9 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
             void *Vj = (char *)g->V + (size_t)j * n * ks;
             TRY(precond_apply(g, dt, Vj, g->z, 1, s));
             TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s));
-            TRY(krylov_dots(g, j, g->ds->h, s));
-            TRY(krylov_update_dots(g, j, s));
-            TRY(krylov_update_norm(g, j, s));
+            TRY(krylov_dots(g, j, nullptr, s));
+            TRY(krylov_update_dots(g, j, nullptr, s));
+            TRY(krylov_update_norm(g, j, nullptr, s));
             TRY(sync_scalars(g, s));
             const DevScalars *hs = g->hs;
             const double hn = sqrt(hs->wnorm2);
@@ -135,7 +124,7 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
             for (int l = i + 1; l < k; l++) t -= H[i][l] * y[l];
             y[i] = t / H[i][i];
         }
-        TRY(krylov_combine(g, k, y, s));
+        TRY(krylov_combine(g, k, y, nullptr, nullptr, s));
         TRY(precond_apply(g, dt, g->u, g->z, 0, s));
         TRY(vec_axpy_k(g, g->z, g->x, s));
         if (resid <= target) {
@@ -169,7 +158,7 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
         st->gmres_unconverged += !go.converged;
         st->fnorm = go.bnorm;  // |F(U^k)|
         if (k == 0) st->fnorm0 = st->fnorm;
-        TRY(newton_update(g, s));
+        TRY(newton_update(g, nullptr, s));
         TRY(sync_scalars(g, s));
         st->max_drho = g->hs->maxdrho;
         st->newton_its = k + 1;
@@ -188,6 +177,19 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
 }
 
 }  // namespace
+
+// J v for the current Newton iterate: v (Krylov type, or FP64 when
+// vin_double) -> out.  eps from |U| (ds->unorm2) and |v|.
+int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
+             int need_vnorm, cudaStream_t s)
+{
+    // eps comes with |v|: computed here, or already by the preconditioner
+    if (need_vnorm) {
+        TRY(dev_norm2(g, v, vin_double, g->n, &g->ds->vnorm2, s));
+        TRY(dev_set_eps(g, 0.0, s));
+    }
+    return stencil_apply(g, SM_JV, g->U, g->RU, v, vin_double, out, out_double, nullptr, dt, 1.0, s);
+}
 
 // ---- timing of the Jacobian-free stencil (CUDA events on the launch stream)
 int prof_begin(music_grid *g, cudaStream_t s)
@@ -232,7 +234,10 @@ int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_
     int h = 0;
     for (;;) {
         st.dt = dt;
-        rc = newton_attempt(g, dt, &st, s);
+        if (g->solver_variant == SOLVER_GRAPH && !g->prof_on)
+            rc = graph_newton_attempt(g, dt, &st, s);
+        else
+            rc = newton_attempt(g, dt, &st, s);
         if (rc != MUSIC_E_NEWTON_FAIL) break;
         if (h >= g->desc.max_dt_halvings) break;
         dt *= 0.5;

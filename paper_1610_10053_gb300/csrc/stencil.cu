@@ -196,6 +196,7 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
                                                  double *RU_out, double hdt, double sign,
                                                  const double *eps)
 {
+    hdt = call_hdt(P, hdt);
     double c_jv = 0.0;
     bool zero = false;
     if (MODE == SM_JV) {
@@ -265,7 +266,8 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *
 {
     extern __shared__ double sm[];
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
-    fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, hdt, sign, epsv, blockIdx.x, blockIdx.y, sm);
+    fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
+                                          blockIdx.y, sm);
 }
 
 
