@@ -224,6 +224,46 @@ int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *s
 int music_batch_step(music_grid **grids, int count, const double *cfl, const double *dt_max,
                      music_step_stats *stats, void *stream);
 
+/*
+ * Tile shapes of the fused 2-D kernels (the residual / Jacobian-free product
+ * stencil of Sec. 2 and the physics-based preconditioner), picked by timing.
+ * The paper has no counterpart: its code ran on CPUs.  Every candidate shape
+ * gives bitwise identical results, so tuning changes speed only.
+ */
+typedef struct {
+    int tunable;              /* 0: the grid has no fused 2-D kernels (3-D, spherical, radiative
+                                 diffusion, or the multi-pass stencil); nothing was timed */
+    int from_cache;           /* 1: the shapes came from an earlier tuning of the same
+                                 configuration in this process; nothing was timed */
+    int stencil_tile[2];      /* chosen (TX, TY) of the stencil */
+    int precond_tile[2];      /* chosen (TX, TY) of the preconditioner */
+    int n_stencil, n_precond; /* candidates timed (0 when not timed) */
+    int stencil_cand[8][2];   /* candidate shapes ... */
+    int precond_cand[8][2];
+    double stencil_us[8];     /* ... and their median launch times in microseconds
+                                 (stencil: Jacobian-free product mode) */
+    double precond_us[8];
+} music_tune_report;
+
+#define MUSIC_TUNE_FORCE 1u   /* time the candidates even when the configuration is cached */
+
+/*
+ * Time every candidate tile shape of the grid's fused 2-D kernels on its
+ * current state at step size dt (> 0), keep the fastest for this grid, and
+ * remember them for the configuration (extent, boundaries, precision,
+ * preconditioner and sweeps): grids created later with the same
+ * configuration start with these shapes.  Overwrites the grid's solver
+ * scratch buffers (the state is unchanged).  Synchronises `stream`.
+ * Errors: MUSIC_E_INVAL, MUSIC_E_CUDA.
+ */
+int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_report *report, void *stream);
+
+/* Set the fused kernels' tile shapes to given candidates ((TX, TY) pairs;
+   NULL keeps that kernel's shape).  MUSIC_E_INVAL for a shape that is not a
+   candidate.  music_get_tiles reads the current shapes. */
+int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile);
+int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile);
+
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).
    Synchronises `stream`. */

@@ -55,6 +55,21 @@ class StepStats(ctypes.Structure):
 
 
 # every exported symbol of include/music.h with its ctypes signature
+class TuneReport(ctypes.Structure):
+    _fields_ = [("tunable", ctypes.c_int), ("from_cache", ctypes.c_int), ("stencil_tile", ctypes.c_int * 2),
+                ("precond_tile", ctypes.c_int * 2), ("n_stencil", ctypes.c_int), ("n_precond", ctypes.c_int),
+                ("stencil_cand", (ctypes.c_int * 2) * 8), ("precond_cand", (ctypes.c_int * 2) * 8),
+                ("stencil_us", ctypes.c_double * 8), ("precond_us", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        return {"tunable": self.tunable, "from_cache": self.from_cache,
+                "stencil_tile": tuple(self.stencil_tile), "precond_tile": tuple(self.precond_tile),
+                "stencil_us": {tuple(self.stencil_cand[i]): self.stencil_us[i] for i in range(self.n_stencil)},
+                "precond_us": {tuple(self.precond_cand[i]): self.precond_us[i] for i in range(self.n_precond)}}
+
+
+MUSIC_TUNE_FORCE = 1
+
 SIGNATURES = {
     "music_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "music_version": (ctypes.c_char_p, []),
@@ -83,6 +98,10 @@ SIGNATURES = {
     "music_batch_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _dbl_p, _dbl_p,
                                         ctypes.POINTER(StepStats), ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "music_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint, ctypes.POINTER(TuneReport),
+                                      ctypes.c_void_p]),
+    "music_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "music_get_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
 }
 
@@ -313,6 +332,28 @@ class Grid:
         if dt_max and dt_max > 0 and dt > dt_max:
             dt = dt_max
         return self.newton_step(dt)
+
+    def autotune(self, dt: Optional[float] = None, force: bool = False) -> dict:
+        """Pick the fused kernels' tile shapes by timing (music_autotune); dt
+        defaults to the CFL step of the problem."""
+        if dt is None:
+            dt = self.cfl_dt(self.prob.cfl)
+            if self.prob.dt_max and 0 < self.prob.dt_max < dt:
+                dt = self.prob.dt_max
+        rep = TuneReport()
+        check(load().music_autotune(self.h, float(dt), MUSIC_TUNE_FORCE if force else 0, ctypes.byref(rep),
+                                    _stream()))
+        return rep.as_dict()
+
+    def set_tiles(self, stencil=None, precond=None):
+        st = (ctypes.c_int * 2)(*stencil) if stencil is not None else None
+        pt = (ctypes.c_int * 2)(*precond) if precond is not None else None
+        check(load().music_set_tiles(self.h, st, pt))
+
+    def tiles(self):
+        st, pt = (ctypes.c_int * 2)(), (ctypes.c_int * 2)()
+        check(load().music_get_tiles(self.h, st, pt))
+        return tuple(st), tuple(pt)
 
     def run(self, nsteps: Optional[int] = None, cfl: Optional[float] = None, dt_max: Optional[float] = None):
         nsteps = self.prob.nsteps if nsteps is None else nsteps

@@ -9,6 +9,8 @@
 #include <vector>
 
 #include "internal.h"
+#include "tile_precond.cuh"
+#include "tiles.h"
 
 #include <atomic>
 
@@ -178,7 +180,11 @@ void alloc_plan(music_grid *g, F &&f)
             }
         }
     }
-    f((void **)&g->partials, (size_t)MUSIC_MAXV * g->nb * sizeof(double));
+    // reduction partials: the Krylov kernels' and the preconditioner's
+    // tile-independent |z|^2 blocks (2-D)
+    size_t np = (size_t)MUSIC_MAXV * g->nb;
+    if (P.nd == 2 && (size_t)tile::norm_partial_count(P) > np) np = (size_t)tile::norm_partial_count(P);
+    f((void **)&g->partials, np * sizeof(double));
     f((void **)&g->hg, (size_t)(MUSIC_MAXV * MUSIC_MAXV + 4 * MUSIC_MAXV) * sizeof(double));
     f(&g->binst, 1024);  // batched-solver descriptor (sizeof checked in batched.cu)
     f((void **)&g->ds, sizeof(DevScalars));
@@ -201,6 +207,9 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     // MUSIC_SOLVER=host sequences Newton and GMRES from the host
     const char *so = getenv("MUSIC_SOLVER");
     g->solver_variant = (so && strcmp(so, "host") == 0) ? SOLVER_HOST : SOLVER_GRAPH;
+    g->stile = STENCIL_TILE_DEFAULT;
+    g->ptile = PRECOND_TILE_DEFAULT;
+    tune_lookup(g);  // shapes an earlier tuning picked for this configuration
     g->n = (size_t)g->P.nv * g->P.N;
     // reduction blocks: enough to fill the GPU, fixed per grid
     long long nb = ((long long)g->n + 255) / 256;

@@ -34,6 +34,7 @@ struct music_grid {
     int stencil_variant;  // STENCIL_*: fused shared-memory kernel (2-D) or multi-pass
     int pc_variant;       // PC_*: fused 2-D preconditioner kernel or one kernel per sweep
     int solver_variant;   // SOLVER_*: device-driven graph or host-sequenced Newton/GMRES
+    int stile, ptile;     // tile shapes of the fused 2-D stencil / preconditioner (indices, tiles.h)
     GridParams P;
     int mixed;
     int device;
@@ -166,6 +167,10 @@ int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_do
 // Same arguments and results as the host-sequenced attempt.
 int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);
 void graph_release(music_grid *g);
+
+// ----- tune.cu -----
+// set the grid's tile shapes from an earlier tuning of its configuration
+void tune_lookup(music_grid *g);
 
 // ----- api.cu -----
 void count_launches(long long k);   // add kernels run by a graph launch

@@ -16,6 +16,7 @@
 
 #include "internal.h"
 #include "tile_precond.cuh"
+#include "tiles.h"
 
 namespace {
 
@@ -215,75 +216,6 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
 
 
 // ---------------------------------------------------------------- fused 2-D
-// The whole application z = M^-1 r in one kernel on 2-D grids: a CTA owns a
-// TX x TY tile and stages the frozen coefficients and r on the tile plus a
-// halo of H = KM + 1 cells (KM >= K sweeps, a compile-time size so that all
-// tile index arithmetic is by constants).  The right-hand side, the K Jacobi
-// sweeps (sweep k is computed on the staged region shrunk by k cells, which
-// is exactly where it equals the global iterate) and the back substitution
-// all run in shared memory, so r is read and z written once; the block's
-// share of |z|^2 goes to `partial`, and the last block finishes the sum and
-// the finite-difference step of the Jv that follows.
-
-template <typename PT, int KM>
-__global__ void __launch_bounds__(PTX *PTY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z,
-                                                               PT tau, PT tau2, int K, double *partial,
-                                                               DevScalars *ds)
-{
-    call_tau(P, tau, tau2);
-    constexpr int NT = PTX * PTY;
-    extern __shared__ unsigned char smraw[];
-    __shared__ double red[NT / 32];
-    const double nrm = precond2d_tile<PT, KM>(P, C, r, z, tau, tau2, K, blockIdx.x, blockIdx.y, smraw);
-    if (partial) {
-        // |z|^2 and, in the last block, the finite-difference step of the Jv
-        // that follows: eps = sqrt(2^-52) (1 + |U|) / |z|
-        const double t = block_sum<NT>(nrm, red);
-        if (threadIdx.x == 0) partial[blockIdx.x + gridDim.x * blockIdx.y] = t;
-        if (last_block_done(&ds->counters[CNT_PRECOND])) {
-            finish_sums<NT>(partial, gridDim.x * gridDim.y, 0, 1, &ds->vnorm2, red);
-            if (threadIdx.x == 0) ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
-        }
-    }
-}
-
-template <typename PT, int KM>
-int launch_pc_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
-{
-    constexpr int H = KM + 1;
-    constexpr size_t smem = (size_t)6 * (PTX + 2 * H) * (PTY + 2 * H) * sizeof(PT);
-    static bool attr = false;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        attr = true;
-    }
-    const GridParams &P = g->P;
-    const double tau = 0.5 * dt;
-    dim3 grid((P.n[0] + PTX - 1) / PTX, (P.n[1] + PTY - 1) / PTY);
-    const int nblk = grid.x * grid.y;
-    double *part = (want_norm && nblk <= MUSIC_MAXV * g->nb) ? g->partials : nullptr;
-    k_precond_fused2d<PT, KM><<<grid, PTX * PTY, smem, s>>>(P, pc_of<PT>(g), r, z, (PT)tau, (PT)(tau * tau),
-                                                            g->desc.precond_sweeps, part, g->ds);
-    CHECK_LAUNCH();
-    if (want_norm && !part) {
-        TRY(dev_norm2(g, z, sizeof(PT) == 8, g->n, &g->ds->vnorm2, s));
-        TRY(dev_set_eps(g, 0.0, s));
-    }
-    return MUSIC_OK;
-}
-
-template <typename PT>
-int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
-{
-    const int K = g->desc.precond_sweeps;
-    if (K <= 4) return launch_pc_fused2d<PT, 4>(g, dt, r, z, want_norm, s);
-    if (K <= 8) return launch_pc_fused2d<PT, 8>(g, dt, r, z, want_norm, s);
-    if (K <= 12) return launch_pc_fused2d<PT, 12>(g, dt, r, z, want_norm, s);
-    return launch_pc_fused2d<PT, 16>(g, dt, r, z, want_norm, s);
-}
-
-
 // ---------------------------------------------------------------- general form
 // Spherical grids and grids with radiative diffusion: every divergence is a
 // weighted sum W = A/V over the cell's faces (1/dx on Cartesian grids),
@@ -553,9 +485,7 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
         else
             TRY(gen_apply<double>(g, dt, (const double *)r, (double *)z, s));
     } else if (g->P.nd == 2 && g->desc.precond_sweeps <= PC_FUSED_MAXK && g->pc_variant != PC_MULTIKERNEL) {
-        if (g->mixed)
-            return apply_fused2d<float>(g, dt, (const float *)r, (float *)z, want_norm, s);
-        return apply_fused2d<double>(g, dt, (const double *)r, (double *)z, want_norm, s);
+        return precond2d_dispatch(g, dt, r, z, want_norm, s);
     } else if (g->mixed) {
         TRY(apply_t<float>(g, dt, (const float *)r, (float *)z, s));
     } else {
@@ -566,4 +496,20 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
         TRY(dev_set_eps(g, 0.0, s));
     }
     return MUSIC_OK;
+}
+
+int precond2d_dispatch(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
+{
+    switch (g->ptile) {
+    case 0:
+        return precond2d_apply_t<16, 8>(g, dt, r, z, want_norm, s);
+    case 1:
+        return precond2d_apply_t<16, 16>(g, dt, r, z, want_norm, s);
+    case 2:
+        return precond2d_apply_t<32, 8>(g, dt, r, z, want_norm, s);
+    case 3:
+        return precond2d_apply_t<32, 16>(g, dt, r, z, want_norm, s);
+    }
+    set_error("preconditioner: bad tile index %d", g->ptile);
+    return MUSIC_E_INVAL;
 }

@@ -13,6 +13,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "tiles.h"
 #include "tile_stencil.cuh"
 
 namespace {
@@ -257,67 +258,6 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
 }
 
 
-// ---------------------------------------------------------------- fused 2-D
-// (per-tile body in tile_stencil.cuh)
-template <int MODE, typename VIN, typename VOUT, int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
-                                                    const VIN *v, VOUT *out, double *RU_out, double hdt,
-                                                    double sign, const double *eps)
-{
-    extern __shared__ double sm[];
-    const double epsv = (MODE == SM_JV) ? *eps : 0.0;
-    fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
-                                          blockIdx.y, sm);
-}
-
-
-constexpr int FTX = 32, FTY = 16;
-
-template <int MODE, typename VIN, typename VOUT>
-int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN *v, VOUT *out, double *RU_out,
-                   double hdt, double sign, cudaStream_t s)
-{
-    using TL = Tile2D<FTX, FTY>;
-    static bool attr = false;
-    auto kern = k_fused2d<MODE, VIN, VOUT, FTX, FTY>;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM));
-        attr = true;
-    }
-    const GridParams &P = g->P;
-    dim3 grid((P.n[0] + FTX - 1) / FTX, (P.n[1] + FTY - 1) / FTY);
-    kern<<<grid, FTX * FTY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps);
-    CHECK_LAUNCH();
-    return MUSIC_OK;
-}
-
-int fused2d_apply(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
-                  void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s)
-{
-    switch (mode) {
-    case SM_R:
-        return launch_fused2d<SM_R, double, double>(g, U, aux, nullptr, (double *)out, nullptr, hdt, sign, s);
-    case SM_CN:
-        return launch_fused2d<SM_CN, double, double>(g, U, aux, nullptr, (double *)out, nullptr, hdt, sign, s);
-    case SM_F:
-        return launch_fused2d<SM_F, double, double>(g, U, aux, nullptr, (double *)out, RU_out, hdt, sign, s);
-    case SM_JV:
-        if (vin_double && out_double)
-            return launch_fused2d<SM_JV, double, double>(g, U, aux, (const double *)v, (double *)out, nullptr, hdt,
-                                                         sign, s);
-        if (!vin_double && !out_double)
-            return launch_fused2d<SM_JV, float, float>(g, U, aux, (const float *)v, (float *)out, nullptr, hdt, sign,
-                                                       s);
-        if (vin_double)
-            return launch_fused2d<SM_JV, double, float>(g, U, aux, (const double *)v, (float *)out, nullptr, hdt,
-                                                        sign, s);
-        return launch_fused2d<SM_JV, float, double>(g, U, aux, (const float *)v, (double *)out, nullptr, hdt, sign,
-                                                    s);
-    }
-    set_error("stencil: bad mode %d", mode);
-    return MUSIC_E_INVAL;
-}
-
 int blocks_for(long long n)
 {
     long long b = (n + BS - 1) / BS;
@@ -357,7 +297,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P)) {
         const bool prof = g->prof_on && mode == SM_JV;
         if (prof) TRY(prof_begin(g, s));
-        TRY(fused2d_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
+        TRY(fused2d_dispatch(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
         if (prof) TRY(prof_end(g, s));
         return MUSIC_OK;
     }
@@ -407,4 +347,23 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     CHECK_LAUNCH();
     if (prof) TRY(prof_end(g, s));
     return MUSIC_OK;
+}
+
+int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
+                     void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s)
+{
+    switch (g->stile) {
+    case 0:
+        return fused2d_apply_t<16, 8>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    case 1:
+        return fused2d_apply_t<16, 16>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    case 2:
+        return fused2d_apply_t<32, 8>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    case 3:
+        return fused2d_apply_t<32, 16>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    case 4:
+        return fused2d_apply_t<32, 32>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
+    }
+    set_error("stencil: bad tile index %d", g->stile);
+    return MUSIC_E_INVAL;
 }

@@ -6,7 +6,8 @@
 
 namespace tile {
 
-constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;
+constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;  // tile of the persistent batched kernel
+constexpr int NRX = 16, NRY = 8;  // blocks of cells of the tile-independent |z|^2 reduction
 
 template <typename PT>
 struct PC {
@@ -31,16 +32,16 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
     return a < 0 ? 0 : (a >= n ? n - 1 : a);
 }
 
-// One tile (bx, by) of the fused preconditioner, run by a CTA of PTX*PTY
-// threads with 6 (PTX+2H)(PTY+2H) PT of shared memory at `smraw`; returns the
-// calling thread's share of |z|^2.
-template <typename PT, int KM>
+// One TX x TY tile (bx, by) of the fused preconditioner, run by a CTA of
+// TX*TY threads with 6 (TX+2H)(TY+2H) PT of shared memory at `smraw`; returns
+// the calling thread's cell's |z|^2 (thread t owns cell (t % TX, t / TX)).
+template <typename PT, int KM, int TX = PTX, int TY = PTY>
 __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT *r, PT *z, PT tau, PT tau2, int K,
                                  int bx, int by, unsigned char *smraw)
 {
-    constexpr int NT = PTX * PTY, H = KM + 1, RX = PTX + 2 * H, RY = PTY + 2 * H, R = RX * RY;
+    constexpr int NT = TX * TY, H = KM + 1, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
     PT *ax = (PT *)smraw, *ay = ax + R, *iD = ay + R, *b = iD + R, *dA = b + R, *dB = dA + R;
-    const int i0 = bx * PTX - H, j0 = by * PTY - H;
+    const int i0 = bx * TX - H, j0 = by * TY - H;
     const int tid = threadIdx.x;
     const long long N = P.N;
     const int n0 = P.n[0], n1 = P.n[1];
@@ -89,8 +90,8 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         dst = tt;
     }
     // src holds dp; back substitution on the tile
-    const int tx = tid % PTX, ty = tid / PTX;
-    const int gx = bx * PTX + tx, gy = by * PTY + ty;
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx = bx * TX + tx, gy = by * TY + ty;
     double nrm = 0.0;
     if (gx < n0 && gy < n1) {
         const int q = (ty + H) * RX + (tx + H);
@@ -121,6 +122,54 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     }
     __syncthreads();  // the tile's shared memory may be reused by the caller
     return nrm;
+}
+
+// |z|^2 partials on a fixed decomposition of the grid into NRX x NRY blocks
+// of cells, each summed in a fixed order (lane l takes cells l, l+32, ... of
+// the block, then a warp tree), so the total does not depend on the tile
+// shape of the kernel that produced z.  `v` is the thread's cell value as
+// returned by precond2d_tile; `buf` holds TX*TY doubles of shared memory.
+template <int TX, int TY>
+__device__ void norm_partials(const GridParams &P, double v, int bx, int by, double *partial, double *buf)
+{
+    static_assert(TX % NRX == 0 && TY % NRY == 0, "tile must be a multiple of the reduction block");
+    constexpr int SX = TX / NRX, SY = TY / NRY, NS = SX * SY, NW = TX * TY / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    buf[tid] = v;
+    __syncthreads();
+    const int nsx = (P.n[0] + NRX - 1) / NRX, nsy = (P.n[1] + NRY - 1) / NRY;
+    for (int q = warp; q < NS; q += NW) {
+        const int sx = q % SX, sy = q / SX;
+        double a = 0.0;
+        for (int c = lane; c < NRX * NRY; c += 32) a += buf[(sy * NRY + c / NRX) * TX + sx * NRX + c % NRX];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        const int gx = bx * SX + sx, gy = by * SY + sy;
+        if (lane == 0 && gx < nsx && gy < nsy) partial[(long long)gy * nsx + gx] = a;
+    }
+}
+
+// number of partials norm_partials writes for the grid
+__host__ __device__ inline long long norm_partial_count(const GridParams &P)
+{
+    return (long long)((P.n[0] + NRX - 1) / NRX) * ((P.n[1] + NRY - 1) / NRY);
+}
+
+// In one CTA of at least 128 threads: *dst = sum of partial[0, count) in a
+// fixed order (128 strided runs, then a fixed halving tree in `buf`).
+__device__ inline void sum_partials_fixed(const double *partial, long long count, double *dst, double *buf)
+{
+    const int tid = threadIdx.x;
+    if (tid < 128) {
+        double a = 0.0;
+        for (long long b = tid; b < count; b += 128) a += __ldcg(partial + b);
+        buf[tid] = a;
+    }
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (tid < w) buf[tid] += buf[tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) *dst = buf[0];
 }
 
 }  // namespace tile

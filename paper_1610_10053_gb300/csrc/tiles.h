@@ -1,0 +1,34 @@
+// Tile shapes of the fused 2-D kernels (residual / Jacobian-free product
+// stencil and physics-based preconditioner) and their per-shape entry
+// points.  Every shape computes the same arithmetic per cell, and the
+// preconditioner's |z|^2 is reduced on a tile-independent decomposition, so
+// all shapes give bitwise identical results; the autotuner (tune.cu) picks
+// the fastest by timing.  Each shape is instantiated in its own translation
+// unit (tiles_<TX>x<TY>.cu) so the library builds in parallel.
+#pragma once
+#include "internal.h"
+
+struct TileShape {
+    int x, y;
+};
+
+constexpr int N_STENCIL_TILES = 5, N_PRECOND_TILES = 4;
+constexpr TileShape STENCIL_TILES[N_STENCIL_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}, {32, 32}};
+constexpr TileShape PRECOND_TILES[N_PRECOND_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}};
+constexpr int STENCIL_TILE_DEFAULT = 3, PRECOND_TILE_DEFAULT = 3;  // 32 x 16 both
+
+// fused 2-D stencil of one tile shape (same contract as stencil_apply's
+// fused branch; hdt = dt / 2)
+template <int TX, int TY>
+int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
+                    void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s);
+
+// fused 2-D preconditioner of one tile shape: z = M^-1 r (Krylov type of the
+// grid), with want_norm also |z|^2 -> ds->vnorm2 and the Jv step -> ds->eps
+template <int TX, int TY>
+int precond2d_apply_t(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);
+
+// the grid's shapes, by index into the tables above
+int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
+                     void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s);
+int precond2d_dispatch(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);

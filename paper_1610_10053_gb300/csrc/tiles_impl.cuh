@@ -1,0 +1,141 @@
+// Definitions behind tiles.h; included once per tile shape by tiles_*.cu,
+// which instantiate fused2d_apply_t / precond2d_apply_t for that shape.
+#pragma once
+#include "tile_precond.cuh"
+#include "tile_stencil.cuh"
+#include "tiles.h"
+
+namespace {
+
+using namespace tile;
+
+template <int MODE, typename VIN, typename VOUT, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
+                                                    const VIN *v, VOUT *out, double *RU_out, double hdt,
+                                                    double sign, const double *eps)
+{
+    extern __shared__ double sm[];
+    const double epsv = (MODE == SM_JV) ? *eps : 0.0;
+    fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
+                                          blockIdx.y, sm);
+}
+
+template <int MODE, typename VIN, typename VOUT, int TX, int TY>
+int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN *v, VOUT *out, double *RU_out,
+                   double hdt, double sign, cudaStream_t s)
+{
+    using TL = Tile2D<TX, TY>;
+    static bool attr = false;
+    auto kern = k_fused2d<MODE, VIN, VOUT, TX, TY>;
+    if (!attr) {
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM));
+        attr = true;
+    }
+    const GridParams &P = g->P;
+    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
+    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+// The whole application z = M^-1 r in one kernel: a CTA owns a TX x TY tile
+// and stages the frozen coefficients and r on the tile plus a halo of
+// H = KM + 1 cells (KM >= K sweeps, a compile-time size so that all tile
+// index arithmetic is by constants).  The right-hand side, the K Jacobi
+// sweeps (sweep k is computed on the staged region shrunk by k cells, which
+// is exactly where it equals the global iterate) and the back substitution
+// all run in shared memory, so r is read and z written once; |z|^2 is reduced
+// on the tile-independent decomposition, and the last block finishes it and
+// the finite-difference step of the Jv that follows.
+template <typename PT, int KM, int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z, PT tau,
+                                                             PT tau2, int K, double *partial, DevScalars *ds)
+{
+    call_tau(P, tau, tau2);
+    extern __shared__ unsigned char smraw[];
+    __shared__ double buf[TX * TY];
+    const double nrm = precond2d_tile<PT, KM, TX, TY>(P, C, r, z, tau, tau2, K, blockIdx.x, blockIdx.y, smraw);
+    if (partial) {
+        norm_partials<TX, TY>(P, nrm, blockIdx.x, blockIdx.y, partial, buf);
+        if (last_block_done(&ds->counters[CNT_PRECOND])) {
+            sum_partials_fixed(partial, norm_partial_count(P), &ds->vnorm2, buf);
+            if (threadIdx.x == 0) ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
+        }
+    }
+}
+
+template <typename PT, int KM, int TX, int TY>
+int launch_pc_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+{
+    constexpr int H = KM + 1;
+    constexpr size_t smem = (size_t)6 * (TX + 2 * H) * (TY + 2 * H) * sizeof(PT);
+    static bool attr = false;
+    if (!attr) {
+        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT, KM, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr = true;
+    }
+    const GridParams &P = g->P;
+    const double tau = 0.5 * dt;
+    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
+    PC<PT> C;
+    for (int d = 0; d < 3; d++) C.a[d] = (PT *)g->pa[d];
+    C.gp = (PT *)g->pgp;
+    C.hp = (PT *)g->php;
+    C.D = (PT *)g->pD;
+    k_precond_fused2d<PT, KM, TX, TY><<<grid, TX * TY, smem, s>>>(P, C, r, z, (PT)tau, (PT)(tau * tau),
+                                                                  g->desc.precond_sweeps,
+                                                                  want_norm ? g->partials : nullptr, g->ds);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+template <typename PT, int TX, int TY>
+int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+{
+    const int K = g->desc.precond_sweeps;
+    if (K <= 4) return launch_pc_fused2d<PT, 4, TX, TY>(g, dt, r, z, want_norm, s);
+    if (K <= 8) return launch_pc_fused2d<PT, 8, TX, TY>(g, dt, r, z, want_norm, s);
+    if (K <= 12) return launch_pc_fused2d<PT, 12, TX, TY>(g, dt, r, z, want_norm, s);
+    return launch_pc_fused2d<PT, 16, TX, TY>(g, dt, r, z, want_norm, s);
+}
+
+}  // namespace
+
+template <int TX, int TY>
+int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
+                    void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s)
+{
+    switch (mode) {
+    case SM_R:
+        return launch_fused2d<SM_R, double, double, TX, TY>(g, U, aux, nullptr, (double *)out, nullptr, hdt, sign,
+                                                            s);
+    case SM_CN:
+        return launch_fused2d<SM_CN, double, double, TX, TY>(g, U, aux, nullptr, (double *)out, nullptr, hdt,
+                                                             sign, s);
+    case SM_F:
+        return launch_fused2d<SM_F, double, double, TX, TY>(g, U, aux, nullptr, (double *)out, RU_out, hdt, sign,
+                                                            s);
+    case SM_JV:
+        if (vin_double && out_double)
+            return launch_fused2d<SM_JV, double, double, TX, TY>(g, U, aux, (const double *)v, (double *)out,
+                                                                 nullptr, hdt, sign, s);
+        if (!vin_double && !out_double)
+            return launch_fused2d<SM_JV, float, float, TX, TY>(g, U, aux, (const float *)v, (float *)out, nullptr,
+                                                               hdt, sign, s);
+        if (vin_double)
+            return launch_fused2d<SM_JV, double, float, TX, TY>(g, U, aux, (const double *)v, (float *)out,
+                                                                nullptr, hdt, sign, s);
+        return launch_fused2d<SM_JV, float, double, TX, TY>(g, U, aux, (const float *)v, (double *)out, nullptr,
+                                                            hdt, sign, s);
+    }
+    set_error("stencil: bad mode %d", mode);
+    return MUSIC_E_INVAL;
+}
+
+template <int TX, int TY>
+int precond2d_apply_t(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
+{
+    if (g->mixed) return apply_fused2d<float, TX, TY>(g, dt, (const float *)r, (float *)z, want_norm, s);
+    return apply_fused2d<double, TX, TY>(g, dt, (const double *)r, (double *)z, want_norm, s);
+}

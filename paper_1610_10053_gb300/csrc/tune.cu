@@ -1,0 +1,217 @@
+// Autotuner of the fused 2-D kernels' tile shapes.  The paper's code ran on
+// CPUs; this has no counterpart there.  Every candidate shape computes the
+// same result bitwise (tiles.h), so the choice is by speed alone: each is
+// timed with CUDA events on the grid's own state, the median of a few
+// launches taken, and the fastest kept for the grid and for every later grid
+// of the same configuration (extent, boundaries, precision, sweeps) in this
+// process.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "internal.h"
+#include "tiles.h"
+
+namespace {
+
+using Key = std::tuple<int, int, int, int, int, int, int>;
+
+std::mutex g_tune_mu;
+std::map<Key, std::pair<int, int>> g_tune_cache;  // -> (stencil, preconditioner) tile indices
+
+bool fused_grid(const music_grid *g)
+{
+    return g->P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(g->P);
+}
+
+bool fused_precond(const music_grid *g)
+{
+    return fused_grid(g) && g->desc.precond != MUSIC_PC_NONE && g->desc.precond_sweeps <= 16 &&
+           g->pc_variant != PC_MULTIKERNEL;
+}
+
+Key key_of(const music_grid *g)
+{
+    return Key(g->P.n[0], g->P.n[1], g->P.bc[0], g->P.bc[1], g->mixed, g->desc.precond_sweeps, g->desc.precond);
+}
+
+constexpr int WARM = 2, REPS = 5;
+
+// median launch time in microseconds of `launch` on stream s
+template <typename F>
+int time_median(cudaStream_t s, cudaEvent_t *ev, F &&launch, double *us)
+{
+    for (int i = 0; i < WARM; i++) TRY(launch());
+    float t[REPS];
+    for (int i = 0; i < REPS; i++) {
+        CUDA_TRY(cudaEventRecord(ev[2 * i], s));
+        TRY(launch());
+        CUDA_TRY(cudaEventRecord(ev[2 * i + 1], s));
+    }
+    CUDA_TRY(cudaEventSynchronize(ev[2 * REPS - 1]));
+    for (int i = 0; i < REPS; i++) CUDA_TRY(cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]));
+    std::sort(t, t + REPS);
+    *us = 1e3 * (double)t[REPS / 2];
+    return MUSIC_OK;
+}
+
+struct Events {
+    cudaEvent_t ev[2 * REPS] = {};
+    ~Events()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    int make()
+    {
+        for (cudaEvent_t &e : ev) CUDA_TRY(cudaEventCreate(&e));
+        return MUSIC_OK;
+    }
+};
+
+int tune(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
+{
+    Events E;
+    TRY(E.make());
+    const int kd = !g->mixed;
+    // R(U) for the products, coefficients at U, |U| for eps, and a Krylov-type
+    // right-hand side (R(U) cast) for the preconditioner
+    TRY(stencil_apply(g, SM_R, g->U, nullptr, nullptr, 1, g->RU, 1, nullptr, dt, 1.0, s));
+    TRY(dev_norm2(g, g->U, 1, g->n, &g->ds->unorm2, s));
+    TRY(vec_cast_copy(g->RU, 1, g->w, kd, g->n, s));
+    int best_p = g->ptile;
+    if (fused_precond(g)) {
+        TRY(precond_setup(g, g->U, dt, s));
+        double best = 1e300;
+        for (int p = 0; p < N_PRECOND_TILES; p++) {
+            g->ptile = p;
+            double us = 0.0;
+            TRY(time_median(s, E.ev, [&] { return precond_apply(g, dt, g->w, g->z, 1, s); }, &us));
+            rep->precond_cand[p][0] = PRECOND_TILES[p].x;
+            rep->precond_cand[p][1] = PRECOND_TILES[p].y;
+            rep->precond_us[p] = us;
+            if (us < best) {
+                best = us;
+                best_p = p;
+            }
+        }
+        rep->n_precond = N_PRECOND_TILES;
+        g->ptile = best_p;
+    } else {
+        TRY(vec_cast_copy(g->RU, 1, g->z, kd, g->n, s));
+    }
+    // the input of the timed products: z (M^-1 R(U), or R(U)) with its eps
+    TRY(dev_norm2(g, g->z, kd, g->n, &g->ds->vnorm2, s));
+    TRY(dev_set_eps(g, 0.0, s));
+    double best = 1e300;
+    int best_s = g->stile;
+    for (int t = 0; t < N_STENCIL_TILES; t++) {
+        g->stile = t;
+        double us = 0.0;
+        TRY(time_median(s, E.ev, [&] {
+            return stencil_apply(g, SM_JV, g->U, g->RU, g->z, kd, g->u, kd, nullptr, dt, 1.0, s);
+        }, &us));
+        rep->stencil_cand[t][0] = STENCIL_TILES[t].x;
+        rep->stencil_cand[t][1] = STENCIL_TILES[t].y;
+        rep->stencil_us[t] = us;
+        if (us < best) {
+            best = us;
+            best_s = t;
+        }
+    }
+    rep->n_stencil = N_STENCIL_TILES;
+    g->stile = best_s;
+    return MUSIC_OK;
+}
+
+int tile_index(const TileShape *tab, int n, const int *xy)
+{
+    for (int i = 0; i < n; i++)
+        if (tab[i].x == xy[0] && tab[i].y == xy[1]) return i;
+    return -1;
+}
+
+}  // namespace
+
+void tune_lookup(music_grid *g)
+{
+    if (!fused_grid(g)) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key_of(g));
+    if (it == g_tune_cache.end()) return;
+    g->stile = it->second.first;
+    g->ptile = it->second.second;
+}
+
+extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tune_report *rep, void *stream)
+{
+    if (!g || !rep || !(dt > 0.0)) {
+        set_error("music_autotune: need a grid, a report and dt > 0");
+        return MUSIC_E_INVAL;
+    }
+    memset(rep, 0, sizeof(*rep));
+    if (!fused_grid(g)) return MUSIC_OK;  // nothing to tune
+    rep->tunable = 1;
+    const int s0 = g->stile, p0 = g->ptile;
+    bool cached = false;
+    if (!(flags & MUSIC_TUNE_FORCE)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key_of(g));
+        if (it != g_tune_cache.end()) {
+            g->stile = it->second.first;
+            g->ptile = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached) {
+        const int rc = tune(g, dt, rep, (cudaStream_t)stream);
+        if (rc != MUSIC_OK) {
+            g->stile = s0;
+            g->ptile = p0;
+            return rc;
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key_of(g)] = std::make_pair(g->stile, g->ptile);
+    }
+    rep->from_cache = cached ? 1 : 0;
+    rep->stencil_tile[0] = STENCIL_TILES[g->stile].x;
+    rep->stencil_tile[1] = STENCIL_TILES[g->stile].y;
+    rep->precond_tile[0] = PRECOND_TILES[g->ptile].x;
+    rep->precond_tile[1] = PRECOND_TILES[g->ptile].y;
+    if (g->stile != s0 || g->ptile != p0) graph_release(g);  // the recorded attempt used the old shapes
+    return MUSIC_OK;
+}
+
+extern "C" int music_set_tiles(music_grid *g, const int *stencil_tile, const int *precond_tile)
+{
+    if (!g) {
+        set_error("music_set_tiles: grid is NULL");
+        return MUSIC_E_INVAL;
+    }
+    int st = g->stile, pt = g->ptile;
+    if (stencil_tile) st = tile_index(STENCIL_TILES, N_STENCIL_TILES, stencil_tile);
+    if (precond_tile) pt = tile_index(PRECOND_TILES, N_PRECOND_TILES, precond_tile);
+    if (st < 0 || pt < 0) {
+        set_error("music_set_tiles: not a candidate tile shape");
+        return MUSIC_E_INVAL;
+    }
+    if (st != g->stile || pt != g->ptile) graph_release(g);
+    g->stile = st;
+    g->ptile = pt;
+    return MUSIC_OK;
+}
+
+extern "C" int music_get_tiles(const music_grid *g, int *stencil_tile, int *precond_tile)
+{
+    if (!g || !stencil_tile || !precond_tile) {
+        set_error("music_get_tiles: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    stencil_tile[0] = STENCIL_TILES[g->stile].x;
+    stencil_tile[1] = STENCIL_TILES[g->stile].y;
+    precond_tile[0] = PRECOND_TILES[g->ptile].x;
+    precond_tile[1] = PRECOND_TILES[g->ptile].y;
+    return MUSIC_OK;
+}

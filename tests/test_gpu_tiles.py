@@ -1,0 +1,130 @@
+"""Tile shapes of the fused 2-D kernels and the autotuner that picks them.
+
+Every shape must give bitwise identical results: the stencil's arithmetic is
+per cell, and the preconditioner reduces |z|^2 on a fixed 16 x 8 block
+decomposition of the grid whatever its tile, so the Jacobian-free step eps,
+and with it every later iterate, cannot depend on the shape.  The tests use
+ragged grids (extents that no tile divides) with periodic and wall
+boundaries.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from paper_1610_10053_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+STENCIL = [(16, 8), (16, 16), (32, 8), (32, 16), (32, 32)]
+PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16)]
+
+
+def B():
+    from paper_1610_10053_gb300 import binding
+    return binding
+
+
+def problems():
+    return {
+        "kh_ragged": I.kelvin_helmholtz(n=45, ny=37, seed=11, nsteps=2),
+        "rt_ragged_walls": I.rayleigh_taylor(nx=21, ny=70, nsteps=2),
+    }
+
+
+@pytest.mark.parametrize("name", ["kh_ragged", "rt_ragged_walls"])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_operators_identical_for_every_tile(name, prec):
+    p = problems()[name]
+    rng = np.random.default_rng(5)
+    kt = torch.float32 if prec == "MIXED" else torch.float64
+    U = torch.from_numpy(p.U).cuda()
+    Un = U * 0.999
+    v = torch.from_numpy(rng.standard_normal(p.U.size)).cuda().to(kt)
+    dt = 2e-3
+    ref = None
+    for st in STENCIL:
+        with B().Grid(p, precision=getattr(B(), prec)) as g:
+            g.set_tiles(stencil=st)
+            assert g.tiles()[0] == st
+            out = [g.spatial_operator(U), g.residual(U, Un, dt), g.jv(U, v, dt)]
+            torch.cuda.synchronize()
+            out = [t.cpu().numpy() for t in out]
+        if ref is None:
+            ref = out
+        for a, b in zip(out, ref):
+            assert np.array_equal(a, b), (name, prec, st)
+    ref = None
+    for pt in PRECOND:
+        with B().Grid(p, precision=getattr(B(), prec)) as g:
+            g.set_tiles(precond=pt)
+            z = g.precond(U, dt, v)
+            torch.cuda.synchronize()
+            z = z.cpu().numpy()
+        if ref is None:
+            ref = z
+        assert np.array_equal(z, ref), (name, prec, pt)
+
+
+@pytest.mark.parametrize("name,prec", [("kh_ragged", "MIXED"), ("rt_ragged_walls", "FP64")])
+def test_steps_identical_for_every_tile_pair(name, prec):
+    """Whole implicit steps: eps comes from the preconditioner's |z|, so this
+    also checks that the fused reduction does not depend on the tile."""
+    p = problems()[name]
+    ref = None
+    for st, pt in itertools.product(STENCIL, PRECOND):
+        with B().Grid(p, precision=getattr(B(), prec)) as g:
+            g.set_tiles(stencil=st, precond=pt)
+            g.set_state(p.U)
+            stats = g.run()
+            U = g.get_state()
+        key = (U, [(s["newton_its"], s["gmres_its"], s["fnorm"]) for s in stats])
+        if ref is None:
+            ref = key
+        assert np.array_equal(key[0], ref[0]), (name, st, pt)
+        assert key[1] == ref[1], (name, st, pt)
+
+
+def test_autotune_picks_a_candidate_and_caches_it():
+    p = I.kelvin_helmholtz(n=96, ny=80, seed=12, nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        U0 = g.get_state()
+        rep = g.autotune(force=True)
+        assert rep["tunable"] == 1 and rep["from_cache"] == 0
+        assert set(rep["stencil_us"]) == set(STENCIL) and set(rep["precond_us"]) == set(PRECOND)
+        assert all(t > 0.0 for t in rep["stencil_us"].values())
+        assert all(t > 0.0 for t in rep["precond_us"].values())
+        assert rep["stencil_tile"] == min(rep["stencil_us"], key=rep["stencil_us"].get)
+        assert rep["precond_tile"] == min(rep["precond_us"], key=rep["precond_us"].get)
+        assert g.tiles() == (rep["stencil_tile"], rep["precond_tile"])
+        assert np.array_equal(g.get_state(), U0)  # tuning leaves the state alone
+        g.step()
+    # a new grid of the same configuration starts with the tuned shapes
+    with B().Grid(p, precision=B().MIXED) as g2:
+        assert g2.tiles() == (rep["stencil_tile"], rep["precond_tile"])
+        g2.set_state(p.U)
+        rep2 = g2.autotune()
+        assert rep2["from_cache"] == 1 and rep2["stencil_tile"] == rep["stencil_tile"]
+    # another precision is another configuration
+    with B().Grid(p, precision=B().FP64) as g3:
+        assert g3.tiles() == ((32, 16), (32, 16))
+
+
+def test_autotune_has_nothing_to_do_on_general_grids():
+    p = I.taylor_green(n=12, nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        assert g.autotune()["tunable"] == 0
+
+
+def test_set_tiles_rejects_other_shapes():
+    p = I.kelvin_helmholtz(n=32, nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        with pytest.raises(B().MusicError) as e:
+            g.set_tiles(stencil=(24, 8))
+        assert e.value.code == 1
+        with pytest.raises(B().MusicError):
+            g.set_tiles(precond=(32, 32))
