@@ -226,9 +226,11 @@ int music_batch_step(music_grid **grids, int count, const double *cfl, const dou
 
 /*
  * Tile shapes of the fused 2-D kernels (the residual / Jacobian-free product
- * stencil of Sec. 2 and the physics-based preconditioner), picked by timing.
- * The paper has no counterpart: its code ran on CPUs.  Every candidate shape
- * gives bitwise identical results, so tuning changes speed only.
+ * stencil of Sec. 2 and the physics-based preconditioner) and the halo depth
+ * of the preconditioner (its K sweeps in 1, 2 or 4 launches, halo K/stages +
+ * 1), picked by timing.  The paper has no counterpart: its code ran on CPUs.
+ * Every candidate gives bitwise identical results, so tuning changes speed
+ * only.
  */
 typedef struct {
     int tunable;              /* 0: the grid has no fused 2-D kernels (3-D, spherical, radiative
@@ -237,12 +239,13 @@ typedef struct {
                                  configuration in this process; nothing was timed */
     int stencil_tile[2];      /* chosen (TX, TY) of the stencil */
     int precond_tile[2];      /* chosen (TX, TY) of the preconditioner */
+    int precond_stages;       /* chosen number of launches of its sweeps */
     int n_stencil, n_precond; /* candidates timed (0 when not timed) */
-    int stencil_cand[8][2];   /* candidate shapes ... */
-    int precond_cand[8][2];
-    double stencil_us[8];     /* ... and their median launch times in microseconds
-                                 (stencil: Jacobian-free product mode) */
-    double precond_us[8];
+    int stencil_cand[8][2];   /* candidate (TX, TY) ... */
+    int precond_cand[16][3];  /* candidate (TX, TY, stages) ... */
+    double stencil_us[8];     /* ... and their median times in microseconds (stencil:
+                                 one Jacobian-free product; preconditioner: all its launches) */
+    double precond_us[16];
 } music_tune_report;
 
 #define MUSIC_TUNE_FORCE 1u   /* time the candidates even when the configuration is cached */
@@ -259,10 +262,12 @@ typedef struct {
 int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_report *report, void *stream);
 
 /* Set the fused kernels' tile shapes to given candidates ((TX, TY) pairs;
-   NULL keeps that kernel's shape).  MUSIC_E_INVAL for a shape that is not a
-   candidate.  music_get_tiles reads the current shapes. */
-int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile);
-int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile);
+   NULL keeps that kernel's shape) and the preconditioner's stage count (1, 2
+   or 4; <= 0 keeps it).  MUSIC_E_INVAL for a shape that is not a candidate
+   or a split that leaves more than 8 sweeps per stage.  music_get_tiles
+   reads the current choice. */
+int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile, int precond_stages);
+int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile, int *precond_stages);
 
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).

@@ -57,13 +57,16 @@ class StepStats(ctypes.Structure):
 # every exported symbol of include/music.h with its ctypes signature
 class TuneReport(ctypes.Structure):
     _fields_ = [("tunable", ctypes.c_int), ("from_cache", ctypes.c_int), ("stencil_tile", ctypes.c_int * 2),
-                ("precond_tile", ctypes.c_int * 2), ("n_stencil", ctypes.c_int), ("n_precond", ctypes.c_int),
-                ("stencil_cand", (ctypes.c_int * 2) * 8), ("precond_cand", (ctypes.c_int * 2) * 8),
-                ("stencil_us", ctypes.c_double * 8), ("precond_us", ctypes.c_double * 8)]
+                ("precond_tile", ctypes.c_int * 2), ("precond_stages", ctypes.c_int), ("n_stencil", ctypes.c_int),
+                ("n_precond", ctypes.c_int), ("stencil_cand", (ctypes.c_int * 2) * 8),
+                ("precond_cand", (ctypes.c_int * 3) * 16), ("stencil_us", ctypes.c_double * 8),
+                ("precond_us", ctypes.c_double * 16)]
 
     def as_dict(self):
+        """stencil_us keys: (TX, TY); precond_us keys: (TX, TY, stages)."""
         return {"tunable": self.tunable, "from_cache": self.from_cache,
                 "stencil_tile": tuple(self.stencil_tile), "precond_tile": tuple(self.precond_tile),
+                "precond_stages": self.precond_stages,
                 "stencil_us": {tuple(self.stencil_cand[i]): self.stencil_us[i] for i in range(self.n_stencil)},
                 "precond_us": {tuple(self.precond_cand[i]): self.precond_us[i] for i in range(self.n_precond)}}
 
@@ -100,8 +103,10 @@ SIGNATURES = {
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "music_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint, ctypes.POINTER(TuneReport),
                                       ctypes.c_void_p]),
-    "music_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
-    "music_get_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "music_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_int]),
+    "music_get_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
 }
 
@@ -345,15 +350,16 @@ class Grid:
                                     _stream()))
         return rep.as_dict()
 
-    def set_tiles(self, stencil=None, precond=None):
+    def set_tiles(self, stencil=None, precond=None, stages: int = 0):
         st = (ctypes.c_int * 2)(*stencil) if stencil is not None else None
         pt = (ctypes.c_int * 2)(*precond) if precond is not None else None
-        check(load().music_set_tiles(self.h, st, pt))
+        check(load().music_set_tiles(self.h, st, pt, int(stages)))
 
     def tiles(self):
-        st, pt = (ctypes.c_int * 2)(), (ctypes.c_int * 2)()
-        check(load().music_get_tiles(self.h, st, pt))
-        return tuple(st), tuple(pt)
+        """((stencil TX, TY), (preconditioner TX, TY), preconditioner stages)"""
+        st, pt, q = (ctypes.c_int * 2)(), (ctypes.c_int * 2)(), ctypes.c_int()
+        check(load().music_get_tiles(self.h, st, pt, ctypes.byref(q)))
+        return tuple(st), tuple(pt), q.value
 
     def run(self, nsteps: Optional[int] = None, cfl: Optional[float] = None, dt_max: Optional[float] = None):
         nsteps = self.prob.nsteps if nsteps is None else nsteps

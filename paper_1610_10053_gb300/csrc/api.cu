@@ -209,6 +209,7 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     g->solver_variant = (so && strcmp(so, "host") == 0) ? SOLVER_HOST : SOLVER_GRAPH;
     g->stile = STENCIL_TILE_DEFAULT;
     g->ptile = PRECOND_TILE_DEFAULT;
+    g->psplit = default_split(d.precond_sweeps);
     tune_lookup(g);  // shapes an earlier tuning picked for this configuration
     g->n = (size_t)g->P.nv * g->P.N;
     // reduction blocks: enough to fill the GPU, fixed per grid

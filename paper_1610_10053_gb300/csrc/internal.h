@@ -35,6 +35,7 @@ struct music_grid {
     int pc_variant;       // PC_*: fused 2-D preconditioner kernel or one kernel per sweep
     int solver_variant;   // SOLVER_*: device-driven graph or host-sequenced Newton/GMRES
     int stile, ptile;     // tile shapes of the fused 2-D stencil / preconditioner (indices, tiles.h)
+    int psplit;           // launches the fused preconditioner's sweeps are split over (1, 2 or 4)
     GridParams P;
     int mixed;
     int device;

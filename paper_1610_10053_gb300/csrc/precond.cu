@@ -484,7 +484,7 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
             TRY(gen_apply<float>(g, dt, (const float *)r, (float *)z, s));
         else
             TRY(gen_apply<double>(g, dt, (const double *)r, (double *)z, s));
-    } else if (g->P.nd == 2 && g->desc.precond_sweeps <= PC_FUSED_MAXK && g->pc_variant != PC_MULTIKERNEL) {
+    } else if (g->P.nd == 2 && g->desc.precond_sweeps <= PC_STAGED_MAXK && g->pc_variant != PC_MULTIKERNEL) {
         return precond2d_dispatch(g, dt, r, z, want_norm, s);
     } else if (g->mixed) {
         TRY(apply_t<float>(g, dt, (const float *)r, (float *)z, s));

@@ -6,7 +6,10 @@
 
 namespace tile {
 
-constexpr int PTX = 32, PTY = 16, PC_FUSED_MAXK = 16;  // tile of the persistent batched kernel
+constexpr int PTX = 32, PTY = 16;  // tile of the persistent batched kernel
+constexpr int PC_FUSED_MAXK = 16;  // sweeps of a one-launch application
+constexpr int PC_STAGE_MAXK = 8;   // sweeps of one stage of a split application
+constexpr int PC_STAGED_MAXK = 32; // sweeps of a split application (4 stages)
 constexpr int NRX = 16, NRY = 8;  // blocks of cells of the tile-independent |z|^2 reduction
 
 template <typename PT>
@@ -35,9 +38,18 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 // One TX x TY tile (bx, by) of the fused preconditioner, run by a CTA of
 // TX*TY threads with 6 (TX+2H)(TY+2H) PT of shared memory at `smraw`; returns
 // the calling thread's cell's |z|^2 (thread t owns cell (t % TX, t / TX)).
-template <typename PT, int KM, int TX = PTX, int TY = PTY>
+//
+// The K Jacobi sweeps may be split over several launches (stages) with a
+// shallower halo each: a FIRST stage builds the right-hand side from r and
+// starts from dp = 0; a later stage reads the right-hand side (bg) and dp
+// (dpin) of the whole staged region from global memory.  A stage that is not
+// the LAST writes its tile's dp to dpout; the LAST one back-substitutes into
+// z.  Every sweep computes the same values whatever the split, so the result
+// does not depend on it.  K <= KM sweeps per stage.
+template <typename PT, int KM, int TX = PTX, int TY = PTY, bool FIRST = true, bool LAST = true>
 __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT *r, PT *z, PT tau, PT tau2, int K,
-                                 int bx, int by, unsigned char *smraw)
+                                 int bx, int by, unsigned char *smraw, PT *bg = nullptr, const PT *dpin = nullptr,
+                                 PT *dpout = nullptr)
 {
     constexpr int NT = TX * TY, H = KM + 1, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
     PT *ax = (PT *)smraw, *ay = ax + R, *iD = ay + R, *b = iD + R, *dA = b + R, *dB = dA + R;
@@ -56,7 +68,10 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         ax[q] = inx ? C.a[0][c] : (PT)0;
         ay[q] = iny ? C.a[1][c] : (PT)0;
         iD[q] = (PT)1 / C.D[c];
-        if (lx < RX - 1 && ly < RY - 1) {
+        if (!FIRST) {
+            b[q] = bg[c];
+            dA[q] = dpin[c];
+        } else if (lx < RX - 1 && ly < RY - 1) {
             // right-hand side needs r_m on the upper faces: the next cells'
             bool inxp, inyp;
             const int xp = pc_wrap(i0 + lx + 1, n0, px, inxp), yp = pc_wrap(j0 + ly + 1, n1, py, inyp);
@@ -69,14 +84,19 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         }
     }
     __syncthreads();
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx = bx * TX + tx, gy = by * TY + ty;
+    if (FIRST && !LAST && gx < n0 && gy < n1) bg[gx + (long long)n0 * gy] = b[(ty + H) * RX + tx + H];
     const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
     PT *src = dA, *dst = dB;
     for (int k = 0; k < K; k++) {
-        const int lo = k, hx = RX - 1 - k, hy = RY - 1 - k;
+        // the first stage's sweep k is valid on [k, R - 1 - k) (its right-hand
+        // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1)
+        const int lo = FIRST ? k : k + 1, hx = RX - 1 - k, hy = RY - 1 - k;
         const int wdt = hx - lo, cnt = wdt * (hy - lo);
         for (int t = tid; t < cnt; t += NT) {
             const int q = (lo + t / wdt) * RX + lo + t % wdt;
-            if (k == 0) {
+            if (FIRST && k == 0) {
                 dst[q] = w * (b[q] * iD[q]);
             } else {
                 PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
@@ -89,9 +109,13 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         src = dst;
         dst = tt;
     }
-    // src holds dp; back substitution on the tile
-    const int tx = tid % TX, ty = tid / TX;
-    const int gx = bx * TX + tx, gy = by * TY + ty;
+    // src holds dp
+    if (!LAST) {
+        if (gx < n0 && gy < n1) dpout[gx + (long long)n0 * gy] = src[(ty + H) * RX + tx + H];
+        __syncthreads();
+        return 0.0;
+    }
+    // back substitution on the tile
     double nrm = 0.0;
     if (gx < n0 && gy < n1) {
         const int q = (ty + H) * RX + (tx + H);

@@ -16,6 +16,18 @@ constexpr int N_STENCIL_TILES = 5, N_PRECOND_TILES = 4;
 constexpr TileShape STENCIL_TILES[N_STENCIL_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}, {32, 32}};
 constexpr TileShape PRECOND_TILES[N_PRECOND_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}};
 constexpr int STENCIL_TILE_DEFAULT = 3, PRECOND_TILE_DEFAULT = 3;  // 32 x 16 both
+// the preconditioner's K sweeps run in 1, 2 or 4 launches (halo depth K + 1,
+// K/2 + 1 or K/4 + 1): one launch takes up to 16 sweeps, a split up to 8 per
+// stage (so 17..32 sweeps need 4 stages)
+constexpr int N_PRECOND_SPLITS = 3;
+constexpr int PRECOND_SPLITS[N_PRECOND_SPLITS] = {1, 2, 4};
+inline bool split_ok(int sweeps, int stages)
+{
+    if (stages == 1) return sweeps <= 16;
+    return sweeps >= stages && (sweeps + stages - 1) / stages <= 8;
+}
+// the split a grid starts with: one launch when the sweeps allow it
+inline int default_split(int sweeps) { return sweeps <= 16 ? 1 : 4; }
 
 // fused 2-D stencil of one tile shape (same contract as stencil_apply's
 // fused branch; hdt = dt / 2)

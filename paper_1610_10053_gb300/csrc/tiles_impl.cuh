@@ -38,24 +38,30 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
     return MUSIC_OK;
 }
 
-// The whole application z = M^-1 r in one kernel: a CTA owns a TX x TY tile
-// and stages the frozen coefficients and r on the tile plus a halo of
-// H = KM + 1 cells (KM >= K sweeps, a compile-time size so that all tile
-// index arithmetic is by constants).  The right-hand side, the K Jacobi
-// sweeps (sweep k is computed on the staged region shrunk by k cells, which
-// is exactly where it equals the global iterate) and the back substitution
-// all run in shared memory, so r is read and z written once; |z|^2 is reduced
-// on the tile-independent decomposition, and the last block finishes it and
-// the finite-difference step of the Jv that follows.
-template <typename PT, int KM, int TX, int TY>
+// The application z = M^-1 r in one kernel, or in a few (stages) with a
+// shallower halo each: a CTA owns a TX x TY tile and stages the frozen
+// coefficients and r (or, after the first stage, the right-hand side and dp)
+// on the tile plus a halo of H = KM + 1 cells (KM >= the stage's sweeps, a
+// compile-time size so that all tile index arithmetic is by constants).  The
+// right-hand side, the stage's Jacobi sweeps (sweep k is computed on the
+// staged region shrunk by k cells, which is exactly where it equals the
+// global iterate) and, in the last stage, the back substitution all run in
+// shared memory.  One stage reads r and writes z once; more stages trade a
+// global write and read of the right-hand side and dp per stage for less
+// redundant halo work.  |z|^2 is reduced on the tile-independent
+// decomposition, and the last block finishes it and the finite-difference
+// step of the Jv that follows.
+template <typename PT, int KM, int TX, int TY, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z, PT tau,
-                                                             PT tau2, int K, double *partial, DevScalars *ds)
+                                                             PT tau2, int K, double *partial, DevScalars *ds,
+                                                             PT *bg, const PT *dpin, PT *dpout)
 {
     call_tau(P, tau, tau2);
     extern __shared__ unsigned char smraw[];
     __shared__ double buf[TX * TY];
-    const double nrm = precond2d_tile<PT, KM, TX, TY>(P, C, r, z, tau, tau2, K, blockIdx.x, blockIdx.y, smraw);
-    if (partial) {
+    const double nrm = precond2d_tile<PT, KM, TX, TY, FIRST, LAST>(P, C, r, z, tau, tau2, K, blockIdx.x,
+                                                                   blockIdx.y, smraw, bg, dpin, dpout);
+    if (LAST && partial) {
         norm_partials<TX, TY>(P, nrm, blockIdx.x, blockIdx.y, partial, buf);
         if (last_block_done(&ds->counters[CNT_PRECOND])) {
             sum_partials_fixed(partial, norm_partial_count(P), &ds->vnorm2, buf);
@@ -64,15 +70,16 @@ __global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT>
     }
 }
 
-template <typename PT, int KM, int TX, int TY>
-int launch_pc_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+template <typename PT, int KM, int TX, int TY, bool FIRST, bool LAST>
+int launch_pc_stage(music_grid *g, double dt, const PT *r, PT *z, int K, int want_norm, PT *dpin, PT *dpout,
+                    cudaStream_t s)
 {
     constexpr int H = KM + 1;
     constexpr size_t smem = (size_t)6 * (TX + 2 * H) * (TY + 2 * H) * sizeof(PT);
+    auto kern = k_precond_fused2d<PT, KM, TX, TY, FIRST, LAST>;
     static bool attr = false;
     if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(k_precond_fused2d<PT, KM, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr = true;
     }
     const GridParams &P = g->P;
@@ -83,21 +90,55 @@ int launch_pc_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_nor
     C.gp = (PT *)g->pgp;
     C.hp = (PT *)g->php;
     C.D = (PT *)g->pD;
-    k_precond_fused2d<PT, KM, TX, TY><<<grid, TX * TY, smem, s>>>(P, C, r, z, (PT)tau, (PT)(tau * tau),
-                                                                  g->desc.precond_sweeps,
-                                                                  want_norm ? g->partials : nullptr, g->ds);
+    kern<<<grid, TX * TY, smem, s>>>(P, C, r, z, (PT)tau, (PT)(tau * tau), K, want_norm ? g->partials : nullptr,
+                                     g->ds, (PT *)g->pb, dpin, dpout);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
+// the K sweeps in `stages` launches of ceil(K / stages) sweeps (the last may
+// have fewer); one stage takes KM = the smallest of 4, 8, 12, 16 covering K,
+// split stages 4 or 8
 template <typename PT, int TX, int TY>
-int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, cudaStream_t s)
+int apply_fused2d(music_grid *g, double dt, const PT *r, PT *z, int want_norm, int stages, cudaStream_t s)
 {
     const int K = g->desc.precond_sweeps;
-    if (K <= 4) return launch_pc_fused2d<PT, 4, TX, TY>(g, dt, r, z, want_norm, s);
-    if (K <= 8) return launch_pc_fused2d<PT, 8, TX, TY>(g, dt, r, z, want_norm, s);
-    if (K <= 12) return launch_pc_fused2d<PT, 12, TX, TY>(g, dt, r, z, want_norm, s);
-    return launch_pc_fused2d<PT, 16, TX, TY>(g, dt, r, z, want_norm, s);
+    if ((stages <= 1 || K < 2) && K <= 16) {
+        if (K <= 4) return launch_pc_stage<PT, 4, TX, TY, true, true>(g, dt, r, z, K, want_norm, 0, 0, s);
+        if (K <= 8) return launch_pc_stage<PT, 8, TX, TY, true, true>(g, dt, r, z, K, want_norm, 0, 0, s);
+        if (K <= 12) return launch_pc_stage<PT, 12, TX, TY, true, true>(g, dt, r, z, K, want_norm, 0, 0, s);
+        return launch_pc_stage<PT, 16, TX, TY, true, true>(g, dt, r, z, K, want_norm, 0, 0, s);
+    }
+    const int d = (K + stages - 1) / stages;
+    if (d > 8) {
+        set_error("preconditioner: %d stages of %d sweeps exceed the staged halo", stages, d);
+        return MUSIC_E_INVAL;
+    }
+    PT *buf[2] = {(PT *)g->pdp, (PT *)g->pdq};
+    int done = 0, st = 0;
+    while (done < K) {
+        const int k = (K - done < d) ? K - done : d;
+        const bool first = (done == 0), last = (done + k == K);
+        PT *in = buf[(st + 1) & 1], *out = buf[st & 1];
+        if (d <= 4) {
+            if (first)
+                TRY((launch_pc_stage<PT, 4, TX, TY, true, false>(g, dt, r, z, k, 0, nullptr, out, s)));
+            else if (last)
+                TRY((launch_pc_stage<PT, 4, TX, TY, false, true>(g, dt, r, z, k, want_norm, in, nullptr, s)));
+            else
+                TRY((launch_pc_stage<PT, 4, TX, TY, false, false>(g, dt, r, z, k, 0, in, out, s)));
+        } else {
+            if (first)
+                TRY((launch_pc_stage<PT, 8, TX, TY, true, false>(g, dt, r, z, k, 0, nullptr, out, s)));
+            else if (last)
+                TRY((launch_pc_stage<PT, 8, TX, TY, false, true>(g, dt, r, z, k, want_norm, in, nullptr, s)));
+            else
+                TRY((launch_pc_stage<PT, 8, TX, TY, false, false>(g, dt, r, z, k, 0, in, out, s)));
+        }
+        done += k;
+        st++;
+    }
+    return MUSIC_OK;
 }
 
 }  // namespace
@@ -136,6 +177,7 @@ int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux,
 template <int TX, int TY>
 int precond2d_apply_t(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
-    if (g->mixed) return apply_fused2d<float, TX, TY>(g, dt, (const float *)r, (float *)z, want_norm, s);
-    return apply_fused2d<double, TX, TY>(g, dt, (const double *)r, (double *)z, want_norm, s);
+    if (g->mixed)
+        return apply_fused2d<float, TX, TY>(g, dt, (const float *)r, (float *)z, want_norm, g->psplit, s);
+    return apply_fused2d<double, TX, TY>(g, dt, (const double *)r, (double *)z, want_norm, g->psplit, s);
 }

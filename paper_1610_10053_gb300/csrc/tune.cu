@@ -1,6 +1,7 @@
-// Autotuner of the fused 2-D kernels' tile shapes.  The paper's code ran on
-// CPUs; this has no counterpart there.  Every candidate shape computes the
-// same result bitwise (tiles.h), so the choice is by speed alone: each is
+// Autotuner of the fused 2-D kernels' tile shapes and of the halo depth of
+// the fused preconditioner (its sweeps in 1, 2 or 4 launches).  The paper's
+// code ran on CPUs; this has no counterpart there.  Every candidate computes
+// the same result bitwise (tiles.h), so the choice is by speed alone: each is
 // timed with CUDA events on the grid's own state, the median of a few
 // launches taken, and the fastest kept for the grid and for every later grid
 // of the same configuration (extent, boundaries, precision, sweeps) in this
@@ -12,6 +13,7 @@
 #include <tuple>
 
 #include "internal.h"
+#include "tile_precond.cuh"
 #include "tiles.h"
 
 namespace {
@@ -19,7 +21,10 @@ namespace {
 using Key = std::tuple<int, int, int, int, int, int, int>;
 
 std::mutex g_tune_mu;
-std::map<Key, std::pair<int, int>> g_tune_cache;  // -> (stencil, preconditioner) tile indices
+struct Choice {
+    int stile, ptile, psplit;
+};
+std::map<Key, Choice> g_tune_cache;  // -> stencil tile, preconditioner tile and stages
 
 bool fused_grid(const music_grid *g)
 {
@@ -28,7 +33,7 @@ bool fused_grid(const music_grid *g)
 
 bool fused_precond(const music_grid *g)
 {
-    return fused_grid(g) && g->desc.precond != MUSIC_PC_NONE && g->desc.precond_sweeps <= 16 &&
+    return fused_grid(g) && g->desc.precond != MUSIC_PC_NONE && g->desc.precond_sweeps <= tile::PC_STAGED_MAXK &&
            g->pc_variant != PC_MULTIKERNEL;
 }
 
@@ -81,24 +86,33 @@ int tune(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
     TRY(stencil_apply(g, SM_R, g->U, nullptr, nullptr, 1, g->RU, 1, nullptr, dt, 1.0, s));
     TRY(dev_norm2(g, g->U, 1, g->n, &g->ds->unorm2, s));
     TRY(vec_cast_copy(g->RU, 1, g->w, kd, g->n, s));
-    int best_p = g->ptile;
+    int best_p = g->ptile, best_q = g->psplit;
     if (fused_precond(g)) {
         TRY(precond_setup(g, g->U, dt, s));
         double best = 1e300;
+        int nc = 0;
         for (int p = 0; p < N_PRECOND_TILES; p++) {
-            g->ptile = p;
-            double us = 0.0;
-            TRY(time_median(s, E.ev, [&] { return precond_apply(g, dt, g->w, g->z, 1, s); }, &us));
-            rep->precond_cand[p][0] = PRECOND_TILES[p].x;
-            rep->precond_cand[p][1] = PRECOND_TILES[p].y;
-            rep->precond_us[p] = us;
-            if (us < best) {
-                best = us;
-                best_p = p;
+            for (int q = 0; q < N_PRECOND_SPLITS; q++) {
+                if (!split_ok(g->desc.precond_sweeps, PRECOND_SPLITS[q])) continue;
+                g->ptile = p;
+                g->psplit = PRECOND_SPLITS[q];
+                double us = 0.0;
+                TRY(time_median(s, E.ev, [&] { return precond_apply(g, dt, g->w, g->z, 1, s); }, &us));
+                rep->precond_cand[nc][0] = PRECOND_TILES[p].x;
+                rep->precond_cand[nc][1] = PRECOND_TILES[p].y;
+                rep->precond_cand[nc][2] = PRECOND_SPLITS[q];
+                rep->precond_us[nc] = us;
+                nc++;
+                if (us < best) {
+                    best = us;
+                    best_p = p;
+                    best_q = PRECOND_SPLITS[q];
+                }
             }
         }
-        rep->n_precond = N_PRECOND_TILES;
+        rep->n_precond = nc;
         g->ptile = best_p;
+        g->psplit = best_q;
     } else {
         TRY(vec_cast_copy(g->RU, 1, g->z, kd, g->n, s));
     }
@@ -141,8 +155,9 @@ void tune_lookup(music_grid *g)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key_of(g));
     if (it == g_tune_cache.end()) return;
-    g->stile = it->second.first;
-    g->ptile = it->second.second;
+    g->stile = it->second.stile;
+    g->ptile = it->second.ptile;
+    g->psplit = it->second.psplit;
 }
 
 extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tune_report *rep, void *stream)
@@ -154,14 +169,15 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
     memset(rep, 0, sizeof(*rep));
     if (!fused_grid(g)) return MUSIC_OK;  // nothing to tune
     rep->tunable = 1;
-    const int s0 = g->stile, p0 = g->ptile;
+    const int s0 = g->stile, p0 = g->ptile, q0 = g->psplit;
     bool cached = false;
     if (!(flags & MUSIC_TUNE_FORCE)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key_of(g));
         if (it != g_tune_cache.end()) {
-            g->stile = it->second.first;
-            g->ptile = it->second.second;
+            g->stile = it->second.stile;
+            g->ptile = it->second.ptile;
+            g->psplit = it->second.psplit;
             cached = true;
         }
     }
@@ -170,45 +186,52 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
         if (rc != MUSIC_OK) {
             g->stile = s0;
             g->ptile = p0;
+            g->psplit = q0;
             return rc;
         }
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key_of(g)] = std::make_pair(g->stile, g->ptile);
+        g_tune_cache[key_of(g)] = Choice{g->stile, g->ptile, g->psplit};
     }
     rep->from_cache = cached ? 1 : 0;
     rep->stencil_tile[0] = STENCIL_TILES[g->stile].x;
     rep->stencil_tile[1] = STENCIL_TILES[g->stile].y;
     rep->precond_tile[0] = PRECOND_TILES[g->ptile].x;
     rep->precond_tile[1] = PRECOND_TILES[g->ptile].y;
-    if (g->stile != s0 || g->ptile != p0) graph_release(g);  // the recorded attempt used the old shapes
+    rep->precond_stages = g->psplit;
+    if (g->stile != s0 || g->ptile != p0 || g->psplit != q0) graph_release(g);  // recorded with the old ones
     return MUSIC_OK;
 }
 
-extern "C" int music_set_tiles(music_grid *g, const int *stencil_tile, const int *precond_tile)
+extern "C" int music_set_tiles(music_grid *g, const int *stencil_tile, const int *precond_tile, int precond_stages)
 {
     if (!g) {
         set_error("music_set_tiles: grid is NULL");
         return MUSIC_E_INVAL;
     }
-    int st = g->stile, pt = g->ptile;
+    int st = g->stile, pt = g->ptile, q = g->psplit;
     if (stencil_tile) st = tile_index(STENCIL_TILES, N_STENCIL_TILES, stencil_tile);
     if (precond_tile) pt = tile_index(PRECOND_TILES, N_PRECOND_TILES, precond_tile);
-    if (st < 0 || pt < 0) {
-        set_error("music_set_tiles: not a candidate tile shape");
+    if (precond_stages > 0) q = precond_stages;
+    bool q_ok = false;
+    for (int i = 0; i < N_PRECOND_SPLITS; i++) q_ok |= (PRECOND_SPLITS[i] == q);
+    if (st < 0 || pt < 0 || !q_ok || !split_ok(g->desc.precond_sweeps, q)) {
+        set_error("music_set_tiles: not a candidate tile shape or stage count");
         return MUSIC_E_INVAL;
     }
-    if (st != g->stile || pt != g->ptile) graph_release(g);
+    if (st != g->stile || pt != g->ptile || q != g->psplit) graph_release(g);
     g->stile = st;
     g->ptile = pt;
+    g->psplit = q;
     return MUSIC_OK;
 }
 
-extern "C" int music_get_tiles(const music_grid *g, int *stencil_tile, int *precond_tile)
+extern "C" int music_get_tiles(const music_grid *g, int *stencil_tile, int *precond_tile, int *precond_stages)
 {
-    if (!g || !stencil_tile || !precond_tile) {
+    if (!g || !stencil_tile || !precond_tile || !precond_stages) {
         set_error("music_get_tiles: NULL argument");
         return MUSIC_E_INVAL;
     }
+    *precond_stages = g->psplit;
     stencil_tile[0] = STENCIL_TILES[g->stile].x;
     stencil_tile[1] = STENCIL_TILES[g->stile].y;
     precond_tile[0] = PRECOND_TILES[g->ptile].x;

@@ -327,12 +327,13 @@ def test_precond_variants(case, variant, monkeypatch):
 
 
 def test_precond_sweep_counts():
-    """1 and 16 sweeps (the fused kernel's halo limit) and 17 (fallback)."""
+    """1 and 16 sweeps (the one-launch kernel's halo limit), 17 and 32 (four
+    staged launches) and 33 (one kernel per sweep)."""
     p = CASES["walls_hse2d"]()
     rng = np.random.default_rng(12)
     r = rng.standard_normal(p.U.size)
     dt = O.cfl_dt(p, p.U, 8.0)
-    for K in (1, 16, 17):
+    for K in (1, 16, 17, 32, 33):
         q = p.with_options(sweeps=K)
         with B().Grid(q) as g:
             z = host(g.precond(dev(q.U), dt, dev(r)))

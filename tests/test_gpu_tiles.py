@@ -1,10 +1,13 @@
-"""Tile shapes of the fused 2-D kernels and the autotuner that picks them.
+"""Tile shapes of the fused 2-D kernels, the halo depth of the fused
+preconditioner (its sweeps in 1, 2 or 4 launches), and the autotuner that
+picks them.
 
-Every shape must give bitwise identical results: the stencil's arithmetic is
-per cell, and the preconditioner reduces |z|^2 on a fixed 16 x 8 block
-decomposition of the grid whatever its tile, so the Jacobian-free step eps,
-and with it every later iterate, cannot depend on the shape.  The tests use
-ragged grids (extents that no tile divides) with periodic and wall
+Every candidate must give bitwise identical results: the stencil's
+arithmetic is per cell, every Jacobi sweep computes the same values however
+the sweeps are split, and the preconditioner reduces |z|^2 on a fixed 16 x 8
+block decomposition of the grid whatever its tile, so the Jacobian-free step
+eps, and with it every later iterate, cannot depend on the choice.  The tests
+use ragged grids (extents that no tile divides) with periodic and wall
 boundaries.
 """
 import itertools
@@ -20,6 +23,7 @@ torch = pytest.importorskip("torch")
 
 STENCIL = [(16, 8), (16, 16), (32, 8), (32, 16), (32, 32)]
 PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16)]
+STAGES = [1, 2, 4]
 
 
 def B():
@@ -57,15 +61,16 @@ def test_operators_identical_for_every_tile(name, prec):
         for a, b in zip(out, ref):
             assert np.array_equal(a, b), (name, prec, st)
     ref = None
-    for pt in PRECOND:
+    for pt, q in itertools.product(PRECOND, STAGES):
         with B().Grid(p, precision=getattr(B(), prec)) as g:
-            g.set_tiles(precond=pt)
+            g.set_tiles(precond=pt, stages=q)
+            assert g.tiles()[1:] == (pt, q)
             z = g.precond(U, dt, v)
             torch.cuda.synchronize()
             z = z.cpu().numpy()
         if ref is None:
             ref = z
-        assert np.array_equal(z, ref), (name, prec, pt)
+        assert np.array_equal(z, ref), (name, prec, pt, q)
 
 
 @pytest.mark.parametrize("name,prec", [("kh_ragged", "MIXED"), ("rt_ragged_walls", "FP64")])
@@ -74,17 +79,18 @@ def test_steps_identical_for_every_tile_pair(name, prec):
     also checks that the fused reduction does not depend on the tile."""
     p = problems()[name]
     ref = None
-    for st, pt in itertools.product(STENCIL, PRECOND):
+    for st, pt, q in [(s, t, 1) for s, t in itertools.product(STENCIL, PRECOND)] + [
+            ((16, 8), (16, 8), 2), ((32, 16), (32, 8), 4), ((16, 16), (32, 16), 2)]:
         with B().Grid(p, precision=getattr(B(), prec)) as g:
-            g.set_tiles(stencil=st, precond=pt)
+            g.set_tiles(stencil=st, precond=pt, stages=q)
             g.set_state(p.U)
             stats = g.run()
             U = g.get_state()
         key = (U, [(s["newton_its"], s["gmres_its"], s["fnorm"]) for s in stats])
         if ref is None:
             ref = key
-        assert np.array_equal(key[0], ref[0]), (name, st, pt)
-        assert key[1] == ref[1], (name, st, pt)
+        assert np.array_equal(key[0], ref[0]), (name, st, pt, q)
+        assert key[1] == ref[1], (name, st, pt, q)
 
 
 def test_autotune_picks_a_candidate_and_caches_it():
@@ -94,23 +100,25 @@ def test_autotune_picks_a_candidate_and_caches_it():
         U0 = g.get_state()
         rep = g.autotune(force=True)
         assert rep["tunable"] == 1 and rep["from_cache"] == 0
-        assert set(rep["stencil_us"]) == set(STENCIL) and set(rep["precond_us"]) == set(PRECOND)
+        assert set(rep["stencil_us"]) == set(STENCIL)
+        assert set(rep["precond_us"]) == {pt + (q,) for pt, q in itertools.product(PRECOND, STAGES)}
         assert all(t > 0.0 for t in rep["stencil_us"].values())
         assert all(t > 0.0 for t in rep["precond_us"].values())
         assert rep["stencil_tile"] == min(rep["stencil_us"], key=rep["stencil_us"].get)
-        assert rep["precond_tile"] == min(rep["precond_us"], key=rep["precond_us"].get)
-        assert g.tiles() == (rep["stencil_tile"], rep["precond_tile"])
+        best = min(rep["precond_us"], key=rep["precond_us"].get)
+        assert rep["precond_tile"] + (rep["precond_stages"],) == best
+        assert g.tiles() == (rep["stencil_tile"], rep["precond_tile"], rep["precond_stages"])
         assert np.array_equal(g.get_state(), U0)  # tuning leaves the state alone
         g.step()
     # a new grid of the same configuration starts with the tuned shapes
     with B().Grid(p, precision=B().MIXED) as g2:
-        assert g2.tiles() == (rep["stencil_tile"], rep["precond_tile"])
+        assert g2.tiles() == (rep["stencil_tile"], rep["precond_tile"], rep["precond_stages"])
         g2.set_state(p.U)
         rep2 = g2.autotune()
         assert rep2["from_cache"] == 1 and rep2["stencil_tile"] == rep["stencil_tile"]
     # another precision is another configuration
     with B().Grid(p, precision=B().FP64) as g3:
-        assert g3.tiles() == ((32, 16), (32, 16))
+        assert g3.tiles() == ((32, 16), (32, 16), 1)
 
 
 def test_autotune_has_nothing_to_do_on_general_grids():
@@ -128,3 +136,18 @@ def test_set_tiles_rejects_other_shapes():
         assert e.value.code == 1
         with pytest.raises(B().MusicError):
             g.set_tiles(precond=(32, 32))
+        with pytest.raises(B().MusicError):
+            g.set_tiles(stages=3)
+
+
+def test_stage_split_must_fit_the_staged_halo():
+    """A split must give every stage at least one sweep and at most eight."""
+    p = I.kelvin_helmholtz(n=32, nsteps=1).with_options(sweeps=3)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_tiles(stages=2)
+        with pytest.raises(B().MusicError):
+            g.set_tiles(stages=4)  # more stages than sweeps
+    with B().Grid(p.with_options(sweeps=20), precision=B().MIXED) as g:
+        with pytest.raises(B().MusicError):
+            g.set_tiles(stages=2)  # 10 sweeps per stage
+        g.set_tiles(stages=4)
