@@ -28,12 +28,18 @@ typedef struct music_server music_server;
 
 typedef struct {
     size_t mem_budget_bytes;  /* device bytes the admitted solves may own (0: 60% of free memory) */
-    int max_active;           /* per-stream workers = concurrently resident large solves [16], <= 256 */
-    int batch_max_cells;      /* solves of at most this many cells (2-D Cartesian, no radiative
-                                 diffusion, <= 16 preconditioner sweeps) join the batch lane
-                                 [16384]; -1: no batch lane */
+    int max_active;           /* per-stream workers = concurrently resident solves off the batch
+                                 lane [16], <= 256 */
+    int batch_max_cells;      /* > 0: solves of at most this many cells (2-D Cartesian, no radiative
+                                 diffusion, <= 16 preconditioner sweeps) join the batch lane;
+                                 <= 0: no batch lane [0] */
     int batch_size;           /* solves per batched launch [152], <= 512 */
-    int reserved;
+    int autotune;             /* 1: a worker tunes the tile shapes of each new grid configuration
+                                 (music_autotune) before its first step; later solves of that
+                                 configuration reuse them [0] */
+    int graph;                /* 1: workers run each Newton attempt as the recorded solver graph;
+                                 0: host-sequenced kernels, which overlap better across many
+                                 concurrent solves on this hardware [0] */
 } music_server_opts;
 
 typedef struct {

@@ -388,7 +388,8 @@ class Grid:
 # ------------------------------------------------------------------ server
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int),
-                ("batch_max_cells", ctypes.c_int), ("batch_size", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("batch_max_cells", ctypes.c_int), ("batch_size", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("graph", ctypes.c_int)]
 
 
 class SolveReq(ctypes.Structure):
@@ -429,9 +430,10 @@ class Server:
     """Continuous-batching solve server (include/music_server.h)."""
 
     def __init__(self, mem_budget_bytes: int = 0, max_active: int = 16, batch_max_cells: int = 0,
-                 batch_size: int = 0):
+                 batch_size: int = 0, autotune: bool = False, graph: bool = False):
         L = load()
-        o = ServerOpts(mem_budget_bytes, max_active, batch_max_cells, batch_size, 0)
+        o = ServerOpts(mem_budget_bytes, max_active, batch_max_cells, batch_size, 1 if autotune else 0,
+                       1 if graph else 0)
         h = ctypes.c_void_p()
         check(L.music_server_create(ctypes.byref(o), ctypes.byref(h)))
         self.h = h

@@ -50,6 +50,8 @@ struct Job {
     size_t footprint = 0;
     bool done = false;
     bool failed = false;
+    int autotune = 0;
+    int graph = 0;
     music_solve_result res;
     std::vector<double> step_ms;
     clk::time_point t_submit, t_admit, t_done;
@@ -114,7 +116,16 @@ int run_job(Job *j, cudaStream_t s)
 {
     music_grid *g = nullptr;
     TRY(grid_create(&j->desc, s, &g));
+    g->solver_variant = j->graph ? SOLVER_GRAPH : SOLVER_HOST;
     int rc = grid_set_state(g, j->U0.data(), 0, s);
+    if (rc == MUSIC_OK && j->autotune && j->n_steps > 0) {
+        // tile shapes for this configuration (timed once per process, then cached)
+        double dt = 0.0;
+        rc = music_cfl_dt(g, j->cfl, &dt, s);
+        if (rc == MUSIC_OK && j->dt_max > 0.0 && dt > j->dt_max) dt = j->dt_max;
+        music_tune_report rep;
+        if (rc == MUSIC_OK) rc = music_autotune(g, dt, 0, &rep, s);
+    }
     double t = 0.0;
     for (int k = 0; rc == MUSIC_OK && k < j->n_steps; k++) {
         const auto t0 = clk::now();
@@ -327,8 +338,8 @@ int music_server_create(const music_server_opts *opts, music_server **out)
         }
         S->streams.push_back(st);
     }
-    S->lane = (o.batch_max_cells >= 0);
-    S->lane_cells = o.batch_max_cells > 0 ? o.batch_max_cells : 16384;
+    S->lane = (o.batch_max_cells > 0);
+    S->lane_cells = o.batch_max_cells;
     S->lane_size = o.batch_size > 0 ? (o.batch_size > MUSIC_BATCH_MAX ? MUSIC_BATCH_MAX : o.batch_size) : 152;
     if (S->lane) {
         if (cudaStreamCreateWithFlags(&S->lane_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -372,6 +383,8 @@ int music_submit_solve(music_server *S, const music_solve_req *req, uint64_t *ti
     j->rho_L = req->rho_L;
     j->rho_H = (req->rho_H == req->rho_L) ? req->rho_L + 1.0 : req->rho_H;
     j->footprint = fp;
+    j->autotune = S->opts.autotune;
+    j->graph = S->opts.graph;
     memset(&j->res, 0, sizeof(j->res));
     j->res.status = MUSIC_E_BUSY;
     j->t_submit = clk::now();

@@ -32,11 +32,11 @@ def mix():
     ]
 
 
-LANE_CELLS = 16384  # the server's default batch_max_cells
+LANE_CELLS = 16384  # batch_max_cells of the lane tests
 
 
 def lane_route(prob, lane_cells=LANE_CELLS):
-    return (lane_cells >= 0 and prob.nd == 2 and prob.geometry == I.GEOM_CARTESIAN and not prob.conduct
+    return (lane_cells > 0 and prob.nd == 2 and prob.geometry == I.GEOM_CARTESIAN and not prob.conduct
             and prob.sweeps <= 16 and prob.ncells <= lane_cells)
 
 
@@ -52,7 +52,7 @@ def alone(prob, prec, lane_cells=LANE_CELLS):
         return g.get_state(), g.diagnostics()
 
 
-@pytest.mark.parametrize("lane_cells", [LANE_CELLS, -1], ids=["batch-lane", "workers-only"])
+@pytest.mark.parametrize("lane_cells", [LANE_CELLS, 0], ids=["batch-lane", "workers-only"])
 def test_same_result_alone_and_in_the_mix(lane_cells):
     reqs = mix()
     with B().Server(max_active=4, batch_max_cells=lane_cells) as s:
@@ -115,7 +115,7 @@ def test_failing_solve_does_not_disturb_the_mix():
         Ug = s.result_state(tg)
     assert rb["status"] != 0
     assert rg["status"] == 0
-    U1, _ = alone(good, B().MIXED)
+    U1, _ = alone(good, B().MIXED, lane_cells=0)  # this server has no batch lane
     assert np.array_equal(Ug, U1)
 
 
@@ -129,7 +129,7 @@ def test_continuous_batching_in_the_lane():
         else:
             p = I.kelvin_helmholtz(n=32 + 16 * (k % 3), seed=20 + k, nsteps=1 + k % 5)
         reqs.append((p, k % 2))
-    with B().Server(max_active=2, batch_size=6) as s:
+    with B().Server(max_active=2, batch_max_cells=LANE_CELLS, batch_size=6) as s:
         tickets = [s.submit(p, prec) for p, prec in reqs]
         results = [s.wait(t, timeout_ms=300000) for t in tickets]
         states = [s.result_state(t) for t in tickets]
@@ -140,3 +140,34 @@ def test_continuous_batching_in_the_lane():
         U1, _ = alone(p, prec)
         assert np.array_equal(U, U1), p.name
     assert st["cell_steps"] == sum(p.ncells * p.nsteps for p, _ in reqs)
+
+
+def test_autotuning_server_gives_the_same_results():
+    """With autotune each new configuration is tuned before its first step;
+    every tile shape computes the same result, so the solves match the
+    untuned ones bitwise."""
+    reqs = [(I.kelvin_helmholtz(n=96, seed=31, nsteps=2), 1), (I.rayleigh_taylor(nx=24, ny=72, nsteps=2), 0),
+            (I.kelvin_helmholtz(n=96, seed=32, nsteps=2), 1)]
+    out = {}
+    for tune in (False, True):
+        with B().Server(max_active=2, autotune=tune) as s:
+            t = [s.submit(p, prec) for p, prec in reqs]
+            r = [s.wait(x, timeout_ms=300000) for x in t]
+            out[tune] = [s.result_state(x) for x in t]
+            assert all(x["status"] == 0 for x in r)
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
+
+
+def test_graph_workers_give_the_same_results():
+    """Workers stepping with the recorded solver graph and with host-sequenced
+    kernels compute identical solves."""
+    reqs = [(I.kelvin_helmholtz(n=64, seed=41, nsteps=2), 1), (I.rayleigh_taylor(nx=16, ny=48, nsteps=2), 0)]
+    out = {}
+    for graph in (False, True):
+        with B().Server(max_active=2, graph=graph) as s:
+            t = [s.submit(p, prec) for p, prec in reqs]
+            assert all(s.wait(x, timeout_ms=300000)["status"] == 0 for x in t)
+            out[graph] = [s.result_state(x) for x in t]
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
