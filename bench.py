@@ -263,6 +263,11 @@ JV_FLOPS_PER_CELL_2D = 151
 # Algorithmic bytes of one cell in mixed precision: U (4 x 8), R(U) (4 x 8),
 # v (4 x 4) read, Jv (4 x 4) written.
 JV_BYTES_PER_CELL_2D = 96
+# DRAM bytes per cell of one Jv-mode launch (dram__bytes_read.sum +
+# dram__bytes_write.sum over the cells of the launch) from an ncu capture of
+# the same kernel source on KH 2048^2 (state larger than L2, 32x16 tile),
+# scaled to the bench's launch by its cell count
+JV_TRAFFIC_B_PER_CELL_2D = 93.3
 # FP64 peak derived from the part's unit counts and clock: 152 SMs x 2 FP64
 # FMA per clock x 2 flops x 2.07 GHz (nominal GB300 FP64 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -279,17 +284,24 @@ def roofline_jv(mixed, prob):
         return None
     per = ms / n
     N = prob.ncells
-    flops = JV_FLOPS_PER_CELL_2D * N if prob.nd == 2 else None
+    # the per-cell figures are those of the fused 2-D kernel; 3-D, spherical
+    # and conducting grids run the multi-pass stencil
+    fused = prob.nd == 2 and prob.geometry == 0 and not prob.conduct
+    flops = JV_FLOPS_PER_CELL_2D * N if fused else None
     achieved = flops / (per / 1e3) / 1e12 if flops else None
     hbm, src = peaks()
-    return {"kernel": "k_fused2d (Jacobian-free product mode)", "bound": "alu",
+    return {"kernel": "k_fused2d (Jacobian-free product mode)" if fused else
+            "multi-pass stencil k_load..k_assemble (Jacobian-free product mode)", "bound": "alu",
             "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None, "traffic": None,
-            "launches": n, "ms_per_launch": per, "flops_per_cell": JV_FLOPS_PER_CELL_2D,
+            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+            "traffic": JV_TRAFFIC_B_PER_CELL_2D * N if fused else None,
+            "traffic_note": "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells",
+            "launches": n, "ms_per_launch": per, "flops_per_cell": JV_FLOPS_PER_CELL_2D if fused else None,
             "timing": "CUDA events around each launch, same-length pass after the timed region",
             "peak_note": "FP64 derived from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
-            "hbm_view": {"achieved_gbs": JV_BYTES_PER_CELL_2D * N / (per / 1e3) / 1e9, "peak_gbs": hbm,
-                         "peak_source": src, "bytes_per_cell": JV_BYTES_PER_CELL_2D}}
+            "hbm_view": {"achieved_gbs": JV_BYTES_PER_CELL_2D * N / (per / 1e3) / 1e9 if fused else None,
+                         "peak_gbs": hbm, "peak_source": src,
+                         "bytes_per_cell": JV_BYTES_PER_CELL_2D if fused else None}}
 
 
 def end_to_end(grid, prob, stream, steps):
