@@ -106,7 +106,8 @@ __device__ double precond_all(const BInst<KT> &I, double dt, const KT *r, KT *z,
     const int ntx = (P.n[0] + PTX - 1) / PTX, nty = (P.n[1] + PTY - 1) / PTY;
     const double tau = 0.5 * dt;
     for (int t = 0; t < ntx * nty; t++)
-        nrm += precond2d_tile<KT, KM>(P, I.pc, r, z, (KT)tau, (KT)(tau * tau), I.sweeps, t % ntx, t / ntx, sm);
+        nrm += precond2d_tile<KT, KM, PTX, PTY, true, true, 0>(P, I.pc, r, z, (KT)tau, (KT)(tau * tau), I.sweeps,
+                                                                t % ntx, t / ntx, sm);
     return nrm;
 }
 

@@ -13,6 +13,7 @@
 namespace {
 
 constexpr int BS = 256;
+constexpr int RUN = 4;  // float4 chunks summed in FP32 before an FP64 add (16 elements)
 
 struct Coef {
     double c[MUSIC_MAXV];
@@ -75,7 +76,7 @@ __device__ __forceinline__ void k_dots_body(const KT *V, const KT *w, long long 
             if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
         }
     }
-    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
+    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
 template <int NVM, typename KT>
@@ -139,7 +140,12 @@ __device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, i
             }
         }
     }
-    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
+    if (last_block_done(counter)) {
+        if (NORM)
+            finish_sums<BS>(partial, nb, nb, 1, dst, sh);
+        else
+            finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+    }
 }
 
 template <int NVM, bool NORM, typename KT>
@@ -258,12 +264,28 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
     const long long n4 = (n & 3) ? 0 : (n >> 2);
     const long long stride = (long long)gridDim.x * BS;
     const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    // FP32 runs of RUN float4 chunks (16 elements), then FP64: FP64 adds and
+    // conversions run at 1/74 of the FP32 rate on this part
+    float run[NVM];
+#pragma unroll
+    for (int i = 0; i < NVM; i++) run[i] = 0.0f;
+    int k = 0;
     for (long long e = t0; e < n4; e += stride) {
         const float4 we = reinterpret_cast<const float4 *>(w)[e];
 #pragma unroll
         for (int i = 0; i < NVM; i++)
-            if (i <= j) acc[i] += (double)dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+            if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+        if (++k == RUN) {
+#pragma unroll
+            for (int i = 0; i < NVM; i++) {
+                acc[i] += (double)run[i];
+                run[i] = 0.0f;
+            }
+            k = 0;
+        }
     }
+#pragma unroll
+    for (int i = 0; i < NVM; i++) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
         const float we = w[e];
 #pragma unroll
@@ -277,7 +299,7 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
             if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
         }
     }
-    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, j + 1, dst, sh);
+    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
 template <int NVM>
@@ -309,8 +331,13 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
     for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (float)h[i];
     __syncthreads();
     double acc[NORM ? 1 : NVM];
+    float run[NORM ? 1 : NVM];
 #pragma unroll
-    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] = 0.0;
+    for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+        acc[i] = 0.0;
+        run[i] = 0.0f;
+    }
+    int k = 0;
     // float4 path only when every basis vector starts 16-byte aligned
     const long long n4 = (n & 3) ? 0 : (n >> 2);
     const long long stride = (long long)gridDim.x * BS;
@@ -330,13 +357,23 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
         }
         reinterpret_cast<float4 *>(w)[e] = we;
         if (NORM) {
-            acc[0] += (double)dot4(we, we);
+            run[0] += dot4(we, we);
         } else {
 #pragma unroll
             for (int i = 0; i < NVM; i++)
-                if (i <= j) acc[i] += (double)dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+                if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+        }
+        if (++k == RUN) {
+#pragma unroll
+            for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+                acc[i] += (double)run[i];
+                run[i] = 0.0f;
+            }
+            k = 0;
         }
     }
+#pragma unroll
+    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
         float we = w[e];
 #pragma unroll
@@ -363,7 +400,12 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
             }
         }
     }
-    if (last_block_done(counter)) finish_sums<BS>(partial, nb, nb, NORM ? 1 : j + 1, dst, sh);
+    if (last_block_done(counter)) {
+        if (NORM)
+            finish_sums<BS>(partial, nb, nb, 1, dst, sh);
+        else
+            finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+    }
 }
 
 template <int NVM, bool NORM>

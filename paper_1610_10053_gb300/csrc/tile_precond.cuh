@@ -45,8 +45,13 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 // (dpin) of the whole staged region from global memory.  A stage that is not
 // the LAST writes its tile's dp to dpout; the LAST one back-substitutes into
 // z.  Every sweep computes the same values whatever the split, so the result
-// does not depend on it.  K <= KM sweeps per stage.
-template <typename PT, int KM, int TX = PTX, int TY = PTY, bool FIRST = true, bool LAST = true>
+// does not depend on it.  K <= KM sweeps per stage.  MAXCPT bounds the
+// staged cells per thread kept in registers across the sweeps (0: sweep from
+// shared memory only).  Measured on KH grids, registers pay for FP32 (512^2:
+// 61 -> 55 us per application) and cost for FP64 (226 -> 244 us), hence the
+// default.
+template <typename PT, int KM, int TX = PTX, int TY = PTY, bool FIRST = true, bool LAST = true,
+          int MAXCPT = (sizeof(PT) == 4 ? 8 : 0)>
 __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT *r, PT *z, PT tau, PT tau2, int K,
                                  int bx, int by, unsigned char *smraw, PT *bg = nullptr, const PT *dpin = nullptr,
                                  PT *dpout = nullptr)
@@ -89,25 +94,71 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     if (FIRST && !LAST && gx < n0 && gy < n1) bg[gx + (long long)n0 * gy] = b[(ty + H) * RX + tx + H];
     const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
     PT *src = dA, *dst = dB;
-    for (int k = 0; k < K; k++) {
-        // the first stage's sweep k is valid on [k, R - 1 - k) (its right-hand
-        // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1)
-        const int lo = FIRST ? k : k + 1, hx = RX - 1 - k, hy = RY - 1 - k;
-        const int wdt = hx - lo, cnt = wdt * (hy - lo);
-        for (int t = tid; t < cnt; t += NT) {
-            const int q = (lo + t / wdt) * RX + lo + t % wdt;
-            if (FIRST && k == 0) {
-                dst[q] = w * (b[q] * iD[q]);
-            } else {
-                PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
-                off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
-                dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) * iD[q]);
-            }
+    // the first stage's sweep k is valid on [k, R - 1 - k) (its right-hand
+    // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1)
+    constexpr int CPT = (R + NT - 1) / NT;  // staged cells per thread
+    if constexpr (CPT <= MAXCPT) {
+        // each thread keeps its cells' coefficients and current dp in
+        // registers across the sweeps, so a sweep reads only the four
+        // neighbours from shared memory (same arithmetic as below)
+        PT cax[CPT], cxp[CPT], cay[CPT], cyp[CPT], cb[CPT], ci[CPT], cur[CPT];
+#pragma unroll
+        for (int s = 0; s < CPT; s++) {
+            const int q = tid + s * NT;
+            const bool in = q < R;
+            const int lx = q % RX, ly = q / RX;
+            const bool nx = in && lx < RX - 1, ny = in && ly < RY - 1;
+            cax[s] = in ? ax[q] : (PT)0;
+            cxp[s] = nx ? ax[q + 1] : (PT)0;
+            cay[s] = in ? ay[q] : (PT)0;
+            cyp[s] = ny ? ay[q + RX] : (PT)0;
+            cb[s] = in ? b[q] : (PT)0;
+            ci[s] = in ? iD[q] : (PT)0;
+            cur[s] = (!FIRST && in) ? src[q] : (PT)0;
         }
-        __syncthreads();
-        PT *tt = src;
-        src = dst;
-        dst = tt;
+        for (int k = 0; k < K; k++) {
+            const int lo = FIRST ? k : k + 1, hx = RX - 1 - k, hy = RY - 1 - k;
+#pragma unroll
+            for (int s = 0; s < CPT; s++) {
+                const int q = tid + s * NT;
+                const int lx = q % RX, ly = q / RX;
+                if (q < R && lx >= lo && lx < hx && ly >= lo && ly < hy) {
+                    PT v;
+                    if (FIRST && k == 0) {
+                        v = w * (cb[s] * ci[s]);
+                    } else {
+                        PT off = (cxp[s] * src[q + 1] + cax[s] * src[q - 1]) * i20;
+                        off += (cyp[s] * src[q + RX] + cay[s] * src[q - RX]) * i21;
+                        v = ((PT)1 - w) * cur[s] + w * ((cb[s] + tau2 * off) * ci[s]);
+                    }
+                    cur[s] = v;
+                    dst[q] = v;
+                }
+            }
+            __syncthreads();
+            PT *tt = src;
+            src = dst;
+            dst = tt;
+        }
+    } else {
+        for (int k = 0; k < K; k++) {
+            const int lo = FIRST ? k : k + 1, hx = RX - 1 - k, hy = RY - 1 - k;
+            const int wdt = hx - lo, cnt = wdt * (hy - lo);
+            for (int t = tid; t < cnt; t += NT) {
+                const int q = (lo + t / wdt) * RX + lo + t % wdt;
+                if (FIRST && k == 0) {
+                    dst[q] = w * (b[q] * iD[q]);
+                } else {
+                    PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
+                    off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
+                    dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) * iD[q]);
+                }
+            }
+            __syncthreads();
+            PT *tt = src;
+            src = dst;
+            dst = tt;
+        }
     }
     // src holds dp
     if (!LAST) {
