@@ -952,3 +952,237 @@ void or_diagnostics(const or_grid *g, const double *U, double rho_L, double rho_
     out[5] = speed;
     for (int d = 0; d < nd; d++) free(uf[d]);
 }
+
+/* ---------------- passive scalars (Sec. 2.2) ---------------- */
+/*
+ * ns passive scalars carried as partial densities q_i = c_i rho (ns planes
+ * of N values).  Their equation d(c_i rho)/dt = -div(c_i rho u) is solved by
+ * its own unpreconditioned Jacobian-free Newton-Krylov iteration, inside the
+ * fluid's Newton loop: iteration k solves the scalar Crank-Nicolson system
+ * linearised at q^k with the fluid frozen at the same iterate U^k that the
+ * fluid residual of iteration k uses, with the fluid's GMRES settings.  The
+ * loop stops on the fluid density test alone (the paper's default), or, with
+ * `enforce`, also on max |delta q_i| / rho <= newton_tol.  After a step the
+ * concentrations are renormalised to sum to one: c_i <- c_i / sum_j c_j.
+ * Cartesian grids only.
+ */
+
+/* mass fluxes of U on the extended grid (nd arrays of the extended size) */
+static double **or_mass_fluxes(const or_grid *g, const double *U)
+{
+    or_ext X;
+    or_ext_init(&X, g);
+    const long n = (long)or_nvars(g) * or_ncells(g);
+    double **Fr = (double **)calloc(3, sizeof(double *));
+    for (int d = 0; d < g->nd; d++) Fr[d] = (double *)calloc(X.total, sizeof(double));
+    double *R = (double *)malloc(n * sizeof(double));
+    spatial_operator_f_r(g, U, R, Fr);
+    free(R);
+    return Fr;
+}
+
+static void or_free_fluxes(const or_grid *g, double **Fr)
+{
+    for (int d = 0; d < g->nd; d++) free(Fr[d]);
+    free(Fr);
+}
+
+/* S = scalar operator of q with the fluid frozen at U */
+void or_scalar_operator(const or_grid *g, const double *U, const double *q, int ns, double *S)
+{
+    double **Fr = or_mass_fluxes(g, U);
+    scalar_operator_r(g, U, Fr, q, ns, S);
+    or_free_fluxes(g, Fr);
+}
+
+/* exact dS/dq v by complex-step differentiation (h = 1e-30) */
+void or_scalar_operator_dir(const or_grid *g, const double *U, const double *q, const double *v, int ns,
+                            double *dS)
+{
+    const long nq = (long)ns * or_ncells(g);
+    double **Fr = or_mass_fluxes(g, U);
+    double complex *qc = (double complex *)malloc(nq * sizeof(double complex));
+    double complex *Sc = (double complex *)malloc(nq * sizeof(double complex));
+    const double h = 1e-30;
+    for (long i = 0; i < nq; i++) qc[i] = q[i] + I * h * v[i];
+    scalar_operator_c(g, U, Fr, qc, ns, Sc);
+    for (long i = 0; i < nq; i++) dS[i] = cimag(Sc[i]) / h;
+    free(qc);
+    free(Sc);
+    or_free_fluxes(g, Fr);
+}
+
+typedef struct {
+    const or_grid *g;
+    const double *rho;
+    double *const *Fr;
+    const double *q;
+    const double *Sq;
+    double qnorm;
+    double dt;
+    int ns;
+} or_scal_ctx;
+
+/* v - dt/2 (S(q + eps v) - S(q)) / eps */
+static void or_scal_jv(void *ctx, const double *v, double *out)
+{
+    or_scal_ctx *c = (or_scal_ctx *)ctx;
+    const long nq = (long)c->ns * or_ncells(c->g);
+    const double eps = or_fd_eps(nq, c->qnorm, v);
+    if (eps == 0.0) {
+        for (long i = 0; i < nq; i++) out[i] = 0.0;
+        return;
+    }
+    double *W = (double *)malloc(nq * sizeof(double));
+    double *SW = (double *)malloc(nq * sizeof(double));
+    for (long i = 0; i < nq; i++) W[i] = c->q[i] + eps * v[i];
+    scalar_operator_r(c->g, c->rho, c->Fr, W, c->ns, SW);
+    const double a = 0.5 * c->dt / eps;
+    for (long i = 0; i < nq; i++) out[i] = v[i] - a * (SW[i] - c->Sq[i]);
+    free(W);
+    free(SW);
+}
+
+/* the scalar solve is unpreconditioned: M = I */
+static void or_scal_identity(void *ctx, const double *in, double *out)
+{
+    or_scal_ctx *c = (or_scal_ctx *)ctx;
+    memcpy(out, in, (long)c->ns * or_ncells(c->g) * sizeof(double));
+}
+
+/* c_i <- c_i / sum_j c_j with the cell density rho */
+static void or_scalar_renormalise(const or_grid *g, const double *rho, double *q, int ns)
+{
+    const long N = or_ncells(g);
+    for (long k = 0; k < N; k++) {
+        double s = 0.0;
+        for (int i = 0; i < ns; i++) s += q[(long)i * N + k] / rho[k];
+        if (!(s > 0.0)) continue;
+        for (int i = 0; i < ns; i++) q[(long)i * N + k] = (q[(long)i * N + k] / rho[k] / s) * rho[k];
+    }
+}
+
+/* One implicit step of the fluid and the scalars; returns 0 or 1 (Newton
+ * failed: U and q restored).  scal_gmres receives the scalar GMRES steps. */
+int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, int enforce, or_step_stats *st,
+                     int *scal_gmres)
+{
+    const long N = or_ncells(g);
+    const long n = (long)or_nvars(g) * N;
+    const long nq = (long)ns * N;
+    double *Un = (double *)malloc(n * sizeof(double));
+    double *qn = (double *)malloc(nq * sizeof(double));
+    double *Cn = (double *)malloc(n * sizeof(double));
+    double *F = (double *)malloc(n * sizeof(double));
+    double *RU = (double *)malloc(n * sizeof(double));
+    double *x = (double *)malloc(n * sizeof(double));
+    double *Cs = (double *)malloc(nq * sizeof(double));
+    double *Sq = (double *)malloc(nq * sizeof(double));
+    double *bs = (double *)malloc(nq * sizeof(double));
+    double *dq = (double *)malloc(nq * sizeof(double));
+    memcpy(Un, U, n * sizeof(double));
+    memcpy(qn, q, nq * sizeof(double));
+    or_step_constant(g, Un, dt, Cn);
+    {
+        double **Fr = or_mass_fluxes(g, Un);
+        scalar_operator_r(g, Un, Fr, qn, ns, Sq);
+        for (long i = 0; i < nq; i++) Cs[i] = qn[i] + 0.5 * dt * Sq[i];
+        or_free_fluxes(g, Fr);
+    }
+    st->dt = dt;
+    st->newton_its = 0;
+    st->gmres_its = 0;
+    st->gmres_failures = 0;
+    *scal_gmres = 0;
+    int ok = 0;
+    for (int k = 0; k < g->newton_max; k++) {
+        /* scalars, with the fluid frozen at U^k */
+        double **Fr = or_mass_fluxes(g, U);
+        scalar_operator_r(g, U, Fr, q, ns, Sq);
+        for (long i = 0; i < nq; i++) bs[i] = -((q[i] - Cs[i]) - 0.5 * dt * Sq[i]);
+        or_scal_ctx sc = {g, U, Fr, q, Sq, or_norm(nq, q), dt, ns};
+        or_gmres_stats sgs;
+        or_gmres(nq, or_scal_jv, or_scal_identity, &sc, bs, dq, g->restart, g->max_restarts, g->gmres_rtol,
+                 &sgs);
+        *scal_gmres += sgs.its;
+        double mq = 0.0;
+        for (long i = 0; i < nq; i++) {
+            q[i] += dq[i];
+            double t = fabs(dq[i]) / U[i % N];
+            if (!(t <= mq)) mq = t;
+        }
+        or_free_fluxes(g, Fr);
+        /* the fluid, as in or_newton_step */
+        or_cn_residual_cached(g, U, Cn, dt, F, RU);
+        st->fnorm = or_norm(n, F);
+        if (k == 0) st->fnorm0 = st->fnorm;
+        for (long i = 0; i < n; i++) F[i] = -F[i];
+        or_newton_ctx ctx = {g, U, RU, or_norm(n, U), dt};
+        or_gmres_stats gs;
+        int rc = or_gmres(n, or_ctx_jv, or_ctx_precond, &ctx, F, x, g->restart, g->max_restarts, g->gmres_rtol,
+                          &gs);
+        st->gmres_its += gs.its;
+        st->gmres_failures += rc;
+        double mx = 0.0;
+        for (long i = 0; i < n; i++) U[i] += x[i];
+        for (long c = 0; c < N; c++) {
+            double t = fabs(x[c]) / U[c];
+            if (!(t <= mx)) mx = t;
+        }
+        st->max_drho = mx;
+        st->newton_its = k + 1;
+        if (mx <= g->newton_tol && (!enforce || mq <= g->newton_tol)) {
+            ok = 1;
+            break;
+        }
+    }
+    if (ok) {
+        or_scalar_renormalise(g, U, q, ns);
+    } else {
+        memcpy(U, Un, n * sizeof(double));
+        memcpy(q, qn, nq * sizeof(double));
+    }
+    free(Un); free(qn); free(Cn); free(F); free(RU); free(x); free(Cs); free(Sq); free(bs); free(dq);
+    return ok ? 0 : 1;
+}
+
+int or_run_s(const or_grid *g, double *U, double *q, int ns, int nsteps, double cfl, double dt_max, int enforce,
+             or_step_stats *st, int *scal_gmres)
+{
+    for (int s = 0; s < nsteps; s++) {
+        double dt = cfl / or_cfl_rate(g, U);
+        if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
+        int h = 0;
+        for (;;) {
+            int rc = or_newton_step_s(g, U, q, ns, dt, enforce, &st[s], &scal_gmres[s]);
+            if (rc == 0) break;
+            if (h >= g->max_halvings) return s;
+            dt = 0.5 * dt;
+            h++;
+        }
+        st[s].halvings = h;
+    }
+    return nsteps;
+}
+
+/* mixing width from the first two scalars: h = sum_rows 2 min(<c_1>, <c_2>) dy,
+   <.> the mean over a row of cells normal to direction 1 */
+double or_scalar_mixing_width(const or_grid *g, const double *U, const double *q)
+{
+    const long N = or_ncells(g);
+    const int nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    double h = 0.0;
+    for (int j = 0; j < ny; j++) {
+        double a1 = 0.0, a2 = 0.0;
+        for (int k = 0; k < nz; k++)
+            for (int i = 0; i < nx; i++) {
+                const long c = i + (long)nx * (j + (long)ny * k);
+                a1 += q[c] / U[c];
+                a2 += q[N + c] / U[c];
+            }
+        a1 /= (double)nx * nz;
+        a2 /= (double)nx * nz;
+        h += 2.0 * (a1 < a2 ? a1 : a2) * g->dx[1];
+    }
+    return h;
+}

@@ -87,6 +87,14 @@ def lib():
         L.or_run.argtypes = [G, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                              ctypes.POINTER(OrStepStats)]
         L.or_diagnostics.argtypes = [G, _dbl_p, ctypes.c_double, ctypes.c_double, _dbl_p]
+        L.or_scalar_operator.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_int, _dbl_p]
+        L.or_scalar_operator_dir.argtypes = [G, _dbl_p, _dbl_p, _dbl_p, ctypes.c_int, _dbl_p]
+        L.or_newton_step_s.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(OrStepStats), ctypes.POINTER(ctypes.c_int)]
+        L.or_run_s.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_int, ctypes.POINTER(OrStepStats), ctypes.POINTER(ctypes.c_int)]
+        L.or_scalar_mixing_width.argtypes = [G, _dbl_p, _dbl_p]
+        L.or_scalar_mixing_width.restype = ctypes.c_double
     return _lib
 
 
@@ -233,3 +241,63 @@ def diagnostics(prob, U) -> dict:
     g = grid(prob)
     lib().or_diagnostics(ctypes.byref(g), _p(U), float(prob.rho_L), float(prob.rho_H), _p(out))
     return dict(zip(DIAG_NAMES, out.tolist()))
+
+
+# ---------------- passive scalars (Sec. 2.2) ----------------
+def scalar_operator(prob, U, q) -> np.ndarray:
+    """S_i = -div(c_i rho u) of the partial densities q with the fluid frozen at U."""
+    U, q = _vec(U), _vec(q)
+    ns = q.size // prob.ncells
+    S = np.empty_like(q)
+    g = grid(prob)
+    lib().or_scalar_operator(ctypes.byref(g), _p(U), _p(q), ns, _p(S))
+    return S
+
+
+def scalar_operator_dir(prob, U, q, v) -> np.ndarray:
+    """Exact (dS/dq) v by complex-step differentiation."""
+    U, q, v = _vec(U), _vec(q), _vec(v)
+    ns = q.size // prob.ncells
+    dS = np.empty_like(q)
+    g = grid(prob)
+    lib().or_scalar_operator_dir(ctypes.byref(g), _p(U), _p(q), _p(v), ns, _p(dS))
+    return dS
+
+
+def newton_step_s(prob, U, q, dt, enforce=None):
+    """One implicit step of the fluid and its scalars.  Returns (U, q, stats, scalar GMRES steps, rc)."""
+    U, q = _vec(U).copy(), _vec(q).copy()
+    ns = q.size // prob.ncells
+    st = OrStepStats()
+    its = ctypes.c_int(0)
+    enforce = prob.scalar_enforce if enforce is None else enforce
+    g = grid(prob)
+    rc = lib().or_newton_step_s(ctypes.byref(g), _p(U), _p(q), ns, float(dt), int(enforce), ctypes.byref(st),
+                                ctypes.byref(its))
+    return U, q, st.as_dict(), its.value, rc
+
+
+def run_s(prob, U=None, q=None, nsteps=None, cfl=None, dt_max=None, enforce=None):
+    """nsteps CFL-limited steps of the fluid and its scalars.  Returns (U, q, [stats], [scalar GMRES steps])."""
+    U = _vec(prob.U if U is None else U).copy()
+    q = _vec(prob.q if q is None else q).copy()
+    ns = q.size // prob.ncells
+    nsteps = prob.nsteps if nsteps is None else nsteps
+    cfl = prob.cfl if cfl is None else cfl
+    dt_max = prob.dt_max if dt_max is None else dt_max
+    enforce = prob.scalar_enforce if enforce is None else enforce
+    st = (OrStepStats * max(nsteps, 1))()
+    its = (ctypes.c_int * max(nsteps, 1))()
+    g = grid(prob)
+    done = lib().or_run_s(ctypes.byref(g), _p(U), _p(q), ns, int(nsteps), float(cfl), float(dt_max), int(enforce),
+                          st, its)
+    if done != nsteps:
+        raise RuntimeError("oracle: Newton failed at step %d" % done)
+    return U, q, [st[i].as_dict() for i in range(nsteps)], [its[i] for i in range(nsteps)]
+
+
+def scalar_mixing_width(prob, U, q) -> float:
+    """h = sum_rows 2 min(<c_1>, <c_2>) dy (Sec. 3, passive-scalar form)."""
+    U, q = _vec(U), _vec(q)
+    g = grid(prob)
+    return float(lib().or_scalar_mixing_width(ctypes.byref(g), _p(U), _p(q)))

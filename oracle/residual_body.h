@@ -35,9 +35,11 @@ static T FN(vanleer)(T a, T b)
  * R(U).  U and R hold nv planes of N = nx*ny*nz values (rho, E, m_x, m_y
  * [, m_z]), x fastest.  m_d[c] sits on the lower d-face of cell c.  On a wall
  * direction w the stored lower wall face (c_w == 0) carries no flux and gets
- * R = 0; the upper wall face is implicit.
+ * R = 0; the upper wall face is implicit.  Fout, when not NULL, receives the
+ * mass fluxes u rho* on the d-faces (one extended-grid array per direction,
+ * the flux of the lower d-face of each point) for the passive scalars.
  */
-static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
+static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
 {
     const int nd = g->nd;
     const long N = or_ncells(g);
@@ -375,10 +377,89 @@ static void FN(spatial_operator)(const or_grid *g, const T *U, T *R)
         }
     }
 
+    if (Fout)
+        for (int d = 0; d < nd; d++) memcpy(Fout[d], Frho[d], M * sizeof(T));
     free(rho); free(e); free(p); free(Erho); free(Tt); free(chi);
     for (int d = 0; d < nd; d++) free(Gc[d]);
     for (int d = 0; d < nd; d++) {
         free(uf[d]); free(srho[d]); free(se[d]); free(Frho[d]); free(FE[d]); free(Phi[d]);
         for (int q = 0; q < nd; q++) { free(su[d][q]); free(Psi[d][q]); }
     }
+}
+
+static void FN(spatial_operator)(const or_grid *g, const T *U, T *R) { FN(spatial_operator_f)(g, U, R, NULL); }
+
+/*
+ * Passive scalars (Sec. 2.2): S_i(q) = -div(c_i rho u) for the partial
+ * densities q_i = c_i rho of ns scalars (ns planes of N values), with the
+ * fluid frozen: rho (N cell densities) and the mass fluxes Fr[d] (extended
+ * grid, lower d-face of each point) of the fluid state.  The scalar flux on
+ * a face is the mass flux times c_i reconstructed upwind with the van Leer
+ * limiter, the form of the internal-energy flux, so a uniform c_i is carried
+ * exactly like the density.  Ghost values of c_i: periodic wrap, mirror at
+ * walls (wall faces carry no mass flux).  Cartesian grids.
+ */
+static void FN(scalar_operator)(const or_grid *g, const double *rho, double *const *Fr, const T *q, int ns, T *S)
+{
+    const int nd = g->nd;
+    const long N = or_ncells(g);
+    or_ext X;
+    or_ext_init(&X, g);
+    const long M = X.total;
+    T *c = (T *)calloc(M, sizeof(T));
+    T *sc = (T *)calloc(M, sizeof(T));
+    T *Fs[3] = {NULL, NULL, NULL};
+    for (int d = 0; d < nd; d++) Fs[d] = (T *)calloc(M, sizeof(T));
+    for (int i = 0; i < ns; i++) {
+        for (long k = 0; k < N; k++) c[or_ext_of_cell(&X, g, k)] = q[(long)i * N + k] / rho[k];
+        for (int d = 0; d < nd; d++) {
+            for (long x = 0; x < M; x++) {
+                int ix[3];
+                or_ext_coords(&X, x, ix);
+                int a = ix[d];
+                if (a >= 0 && a < g->n[d]) continue;
+                int later = 0;
+                for (int w = d + 1; w < nd; w++)
+                    if (ix[w] < 0 || ix[w] >= g->n[w]) later = 1;
+                if (later) continue;
+                int src[3] = {ix[0], ix[1], ix[2]};
+                if (g->bc[d] == OR_BC_PERIODIC)
+                    src[d] = ((a % g->n[d]) + g->n[d]) % g->n[d];
+                else
+                    src[d] = (a < 0) ? (-1 - a) : (2 * g->n[d] - 1 - a);
+                c[x] = c[or_ext_index(&X, src)];
+            }
+        }
+        for (int d = 0; d < nd; d++) {
+            const long s = X.stride[d];
+            for (long x = 0; x < M; x++) {
+                int ix[3];
+                or_ext_coords(&X, x, ix);
+                sc[x] = 0.0;
+                if (!or_ext_has(&X, ix, d, -1) || !or_ext_has(&X, ix, d, +1)) continue;
+                sc[x] = FN(vanleer)(c[x] - c[x - s], c[x + s] - c[x]);
+            }
+            for (long x = 0; x < M; x++) {
+                int ix[3];
+                or_ext_coords(&X, x, ix);
+                Fs[d][x] = 0.0;
+                if (!or_ext_has(&X, ix, d, -2) || !or_ext_has(&X, ix, d, +1)) continue;
+                const double f = Fr[d][x];
+                const T cs = (f >= 0.0) ? c[x - s] + 0.5 * sc[x - s] : c[x] - 0.5 * sc[x];
+                Fs[d][x] = f * cs;
+            }
+        }
+        for (long k = 0; k < N; k++) {
+            const long x = or_ext_of_cell(&X, g, k);
+            T acc = 0.0;
+            for (int d = 0; d < nd; d++) {
+                const long s = X.stride[d];
+                acc += (Fs[d][x + s] - Fs[d][x]) / g->dx[d];
+            }
+            S[(long)i * N + k] = -acc;
+        }
+    }
+    free(c);
+    free(sc);
+    for (int d = 0; d < nd; d++) free(Fs[d]);
 }

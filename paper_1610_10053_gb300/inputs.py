@@ -81,6 +81,13 @@ class Problem:
     chi0: float = 0.0
     flux_wall: tuple = (0, 0, 0)        # walls with the prescribed flux chi dT/dn = lum (/ r^2)
     lum: float = 0.0
+    # passive scalars (Sec. 2.2): partial densities q_i = c_i rho, ns planes of N
+    q: Optional[np.ndarray] = None
+    scalar_enforce: int = 0             # 1: the Newton test also checks the scalar corrections
+
+    @property
+    def nscalars(self) -> int:
+        return 0 if self.q is None else int(self.q.size // self.ncells)
 
     @property
     def ncells(self) -> int:
@@ -123,8 +130,10 @@ def _pack(nd, rho, E, moms):
 
 
 def rayleigh_taylor(nx: int = 64, ny: int = 192, perturbation: str = "benchmark",
-                    cfl: float = 5.0, nsteps: int = 10) -> Problem:
-    """Single-mode Rayleigh-Taylor instability (Sec. 3)."""
+                    cfl: float = 5.0, nsteps: int = 10, scalars: bool = False) -> Problem:
+    """Single-mode Rayleigh-Taylor instability (Sec. 3); with `scalars`, the
+    two marker scalars of Sec. 3: (c_1, c_2) = (1, 0) where the cell centre
+    has y <= 0 and (0, 1) above, as partial densities c_i rho."""
     gamma, gmag, P0 = 1.4, 0.1, 2.5
     n = (nx, ny, 1)
     x0, length = (-0.25, -0.75, 0.0), (0.5, 1.5, 1.0)
@@ -150,9 +159,13 @@ def rayleigh_taylor(nx: int = 64, ny: int = 192, perturbation: str = "benchmark"
     my = dens(Yf) * vy
     my[:, 0, :] = 0.0  # lower wall face
     U = _pack(2, rho, E, [mx, my])
+    q = None
+    if scalars:
+        c1 = np.where(Yc <= 0.0, 1.0, 0.0)
+        q = np.concatenate([(c1 * rho).ravel(), ((1.0 - c1) * rho).ravel()])
     return Problem("rayleigh_taylor", 2, n, x0, length, (BC_PERIODIC, BC_WALL, BC_PERIODIC),
                    (WALL_MIRROR, WALL_HSE, WALL_MIRROR), gamma, (0.0, -gmag, 0.0), U,
-                   cfl=cfl, nsteps=nsteps, rho_L=1.0, rho_H=2.0)
+                   cfl=cfl, nsteps=nsteps, rho_L=1.0, rho_H=2.0, q=q)
 
 
 def kelvin_helmholtz(n: int = 512, seed: int = 2, noise: float = 1e-4, cfl: float = 10.0,
