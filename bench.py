@@ -112,6 +112,9 @@ WORKLOADS = {
                lambda I, r: I.kelvin_helmholtz(n=2048, seed=2 + r)),
     "rt64x192": ("Rayleigh-Taylor 2-D, 64x192, CFL 5, Newton tol 1e-8, GMRES(30)",
                  lambda I, r: I.rayleigh_taylor()),
+    "rt64x192_scalars": ("Rayleigh-Taylor 2-D, 64x192, two passive scalars (unpreconditioned scalar JFNK), "
+                         "CFL 5, Newton tol 1e-8, GMRES(30)",
+                         lambda I, r: I.rayleigh_taylor(scalars=True)),
     "tgv128": ("Taylor-Green vortex 3-D, 128^3 periodic, CFL 20, Newton tol 1e-8, GMRES(30)",
                lambda I, r: I.taylor_green(n=128)),
     "wedge256": ("2-D spherical wedge 256 (r) x 128 (theta), radiative diffusion, polytrope n=3 background, "
@@ -168,6 +171,8 @@ def run_music(args):
             continue
         g = B.Grid(prob, precision=prec)
         g.set_state(prob.U)
+        if prob.q is not None:
+            g.set_scalars(prob.q)
         tune = g.autotune()  # tile shapes and preconditioner stages (untimed)
         for _ in range(args.warmup):
             g.step()
@@ -207,6 +212,8 @@ def run_music(args):
 
     roof = roofline_jv(mixed, prob)
     final_diag = mixed["grid"].diagnostics()
+    if prob.q is not None:
+        final_diag["scalar_mixing_width"] = mixed["grid"].scalar_mixing_width()
     e2e = end_to_end(mixed["grid"], prob, stream, max(2, min(args.steps, 5)))
     for r in result.values():
         r["grid"].close()
@@ -242,6 +249,8 @@ def run_music(args):
         "step_ms_p99": float(np.percentile(t, 99)),
         "newton_its_per_step": float(np.mean([s["newton_its"] for s in st])),
         "gmres_its_per_step": float(np.mean([s["gmres_its"] for s in st])),
+        "scalar_gmres_its_per_step": float(np.mean([s["scalar_gmres_its"] for s in st])) if prob.q is not None
+        else None,
         "fp64_ms_per_step": float(np.mean(result["fp64"]["times"])) if "fp64" in result else None,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -100,6 +100,10 @@ typedef struct {
     int flux_wall[3];         /* 1: this direction's wall faces carry the prescribed
                                  chi dT/dn = lum (spherical r-walls: lum / r^2) */
     double lum;
+    /* passive scalars (Sec. 2.2), Cartesian grids */
+    int nscalars;             /* scalars carried as partial densities c_i rho, 0..8 [0] */
+    int scalar_enforce;       /* 1: the Newton test also requires max |delta(c_i rho)| / rho
+                                 <= newton_tol; 0: the density test alone (Sec. 2.2) [0] */
 } music_grid_desc;
 
 typedef struct {
@@ -112,6 +116,8 @@ typedef struct {
     double fnorm;       /* |F|_2 at the last Newton iterate */
     double max_drho;    /* final max |delta rho| / rho */
     double wall_ms;     /* host wall time of the call */
+    int scalar_gmres_its;  /* Arnoldi steps of the passive-scalar solves */
+    int pad;
 } music_step_stats;
 
 typedef struct music_grid music_grid;
@@ -268,6 +274,31 @@ int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_repor
    reads the current choice. */
 int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile, int precond_stages);
 int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile, int *precond_stages);
+
+/*
+ * Passive scalars (Sec. 2.2).  A grid created with nscalars > 0 carries
+ * their partial densities q_i = c_i rho (nscalars planes of N values, the
+ * layout of the state's planes) next to the fluid state; they start at
+ * zero.  music_newton_step then also advances them: every Newton iteration
+ * solves the scalars' Crank-Nicolson system d q_i/dt = -div(c_i rho u) by an
+ * unpreconditioned Jacobian-free Newton-Krylov step with the fluid frozen at
+ * that iteration's fluid iterate (face mass flux times c_i reconstructed
+ * upwind with the van Leer limiter); the loop stops on the fluid's density
+ * test (and on the scalar corrections with scalar_enforce); after the step
+ * the concentrations are renormalised to sum to one.  The fluid is advanced
+ * exactly as without scalars.  Pointers as for music_set_state.
+ */
+int music_set_scalars(music_grid *grid, const double *q, int is_device, void *stream);
+int music_get_scalars(music_grid *grid, double *q, int is_device, void *stream);
+
+/* S_i = -div(c_i rho u) of device partial densities q (nscalars planes)
+   with the fluid frozen at the device state U; S device, same layout. */
+int music_scalar_operator(music_grid *grid, const double *U, const double *q, double *S, void *stream);
+
+/* Mixing width of Sec. 3 from the grid's first two scalars and state:
+   h = sum over rows of 2 min(<c_1>, <c_2>) dy, <.> the mean of a row of
+   cells normal to direction 1.  Synchronises `stream`. */
+int music_scalar_mixing_width(music_grid *grid, double *h, void *stream);
 
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).

@@ -44,7 +44,9 @@ typedef struct {
 
 typedef struct {
     music_grid_desc desc;     /* problem and solver options (copied) */
-    const double *U0;         /* host initial state, nv*N doubles (copied at submission) */
+    const double *U0;         /* host initial state, nv*N doubles followed by the nscalars
+                                 planes of partial densities when desc.nscalars > 0 (copied at
+                                 submission) */
     int n_steps;              /* implicit steps to take (>= 0) */
     double cfl;               /* each step: dt = cfl-limited (Eq. 4), > 0 */
     double dt_max;            /* optional cap on dt (<= 0: none) */
@@ -81,7 +83,8 @@ int music_poll(music_server *s, uint64_t ticket, music_solve_result *res);
    is still pending then. */
 int music_wait(music_server *s, uint64_t ticket, int timeout_ms, music_solve_result *res);
 
-/* Copy the final state of a finished solve into host memory (nv*N doubles). */
+/* Copy the final state of a finished solve into host memory (nv*N doubles,
+   then the scalar planes when the solve carries passive scalars). */
 int music_result_state(music_server *s, uint64_t ticket, double *U);
 
 /* Forget a finished solve (MUSIC_E_BUSY if it has not finished). */

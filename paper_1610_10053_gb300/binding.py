@@ -40,6 +40,7 @@ class GridDesc(ctypes.Structure):
         ("precond", ctypes.c_int), ("precond_sweeps", ctypes.c_int), ("max_dt_halvings", ctypes.c_int),
         ("geometry", ctypes.c_int), ("g_radial", ctypes.POINTER(ctypes.c_double)), ("conduct", ctypes.c_int),
         ("chi0", ctypes.c_double), ("flux_wall", ctypes.c_int * 3), ("lum", ctypes.c_double),
+        ("nscalars", ctypes.c_int), ("scalar_enforce", ctypes.c_int),
     ]
 
 
@@ -48,10 +49,11 @@ class StepStats(ctypes.Structure):
         ("dt", ctypes.c_double), ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
         ("dt_halvings", ctypes.c_int), ("gmres_unconverged", ctypes.c_int), ("fnorm0", ctypes.c_double),
         ("fnorm", ctypes.c_double), ("max_drho", ctypes.c_double), ("wall_ms", ctypes.c_double),
+        ("scalar_gmres_its", ctypes.c_int), ("pad", ctypes.c_int),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
 # every exported symbol of include/music.h with its ctypes signature
@@ -101,6 +103,11 @@ SIGNATURES = {
     "music_batch_step": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, _dbl_p, _dbl_p,
                                         ctypes.POINTER(StepStats), ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "music_set_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "music_get_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "music_scalar_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_void_p]),
+    "music_scalar_mixing_width": (ctypes.c_int, [ctypes.c_void_p, _dbl_p, ctypes.c_void_p]),
     "music_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint, ctypes.POINTER(TuneReport),
                                       ctypes.c_void_p]),
     "music_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -193,6 +200,8 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
     for k in range(3):
         d.flux_wall[k] = int(getattr(prob, "flux_wall", (0, 0, 0))[k])
     d.lum = float(getattr(prob, "lum", 0.0))
+    d.nscalars = int(getattr(prob, "nscalars", 0))
+    d.scalar_enforce = int(getattr(prob, "scalar_enforce", 0))
     for k, v in over.items():
         setattr(d, k, v)
     return d
@@ -293,6 +302,27 @@ class Grid:
         a = np.empty(self.n, dtype=np.float64)
         check(load().music_get_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
         return a
+
+    # ---- passive scalars (partial densities, nscalars planes)
+    def set_scalars(self, q):
+        a = np.ascontiguousarray(q, dtype=np.float64)
+        check(load().music_set_scalars(self.h, a.ctypes.data_as(ctypes.c_void_p), 0, _stream()))
+
+    def get_scalars(self) -> np.ndarray:
+        a = np.empty(self.desc.nscalars * self.prob.ncells, dtype=np.float64)
+        check(load().music_get_scalars(self.h, a.ctypes.data_as(ctypes.c_void_p), 0, _stream()))
+        return a
+
+    def scalar_operator(self, U, q):
+        import torch
+        S = torch.empty_like(q)
+        check(load().music_scalar_operator(self.h, _ptr(U), _ptr(q), _ptr(S), _stream()))
+        return S
+
+    def scalar_mixing_width(self) -> float:
+        h = ctypes.c_double()
+        check(load().music_scalar_mixing_width(self.h, ctypes.byref(h), _stream()))
+        return h.value
 
     # ---- single-call operators (device tensors in, device tensors out)
     def spatial_operator(self, U):
@@ -440,7 +470,10 @@ class Server:
         self._n = {}
 
     def submit(self, prob, precision: int = FP64, n_steps=None, cfl=None, dt_max=None, **over) -> int:
-        U0 = np.ascontiguousarray(prob.U, dtype=np.float64)
+        """The initial state is the fluid's planes, then the scalars' when the
+        problem carries passive scalars (so is result_state)."""
+        U0 = np.ascontiguousarray(prob.U if prob.q is None else np.concatenate([prob.U, prob.q]),
+                                  dtype=np.float64)
         req = SolveReq()
         req.desc = desc_from_problem(prob, precision, **over)
         req.U0 = U0.ctypes.data_as(_dbl_p)

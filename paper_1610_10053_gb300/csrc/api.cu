@@ -99,6 +99,10 @@ int validate(const music_grid_desc &d)
         set_error("chi0 must be >= 0");
         return MUSIC_E_INVAL;
     }
+    if (d.nscalars < 0 || d.nscalars > 8 || (d.nscalars > 0 && d.geometry != MUSIC_GEOM_CARTESIAN)) {
+        set_error("nscalars must be 0..8, on Cartesian grids");
+        return MUSIC_E_INVAL;
+    }
     return MUSIC_OK;
 }
 
@@ -190,6 +194,15 @@ void alloc_plan(music_grid *g, F &&f)
     f((void **)&g->ds, sizeof(DevScalars));
     f((void **)&g->ctl, sizeof(SolveCtl));
     f((void **)&g->diag_rows, (size_t)8 * P.n[1] * sizeof(double));
+    if (g->ns > 0) {
+        const size_t nq = (size_t)g->ns * N;
+        KSpace &S = g->sc;
+        for (double **p : {&S.U, &S.RU, &S.b, &S.x, &S.t64, &g->sq_n, &g->sq_c}) f((void **)p, nq * sizeof(double));
+        f(&S.V, (size_t)(d.gmres_restart + 1) * nq * ks);
+        for (void **p : {&S.w, &S.z, &S.u}) f(p, nq * ks);
+        f((void **)&g->sfr, (size_t)P.nd * N * sizeof(double));
+        f((void **)&S.ds, sizeof(DevScalars));
+    }
 }
 
 void init_grid_struct(music_grid *g, const music_grid_desc &d)
@@ -212,6 +225,10 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     g->psplit = default_split(d.precond_sweeps);
     tune_lookup(g);  // shapes an earlier tuning picked for this configuration
     g->n = (size_t)g->P.nv * g->P.N;
+    g->ns = d.nscalars;
+    g->sc.n = (size_t)g->ns * g->P.N;
+    // scalar grids run the host-sequenced Newton loop
+    if (g->ns > 0) g->solver_variant = SOLVER_HOST;
     // reduction blocks: enough to fill the GPU, fixed per grid
     long long nb = ((long long)g->n + 255) / 256;
     g->nb = (int)(nb > 2 * 152 ? 2 * 152 : (nb < 1 ? 1 : nb));
@@ -227,6 +244,7 @@ void free_grid(music_grid *g)
     });
     cudaStreamSynchronize(g->home);
     if (g->hs) cudaFreeHost(g->hs);
+    if (g->sc.hs) cudaFreeHost(g->sc.hs);
     if (g->prof_events_made)
         for (int i = 0; i < 2 * 256; i++) cudaEventDestroy(g->prof_ev[i]);
     delete g;
@@ -338,6 +356,11 @@ int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out
     if (!fail && cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {
         cudaGetLastError();
         g->hs = nullptr;
+        fail = 1;
+    }
+    if (!fail && g->ns > 0 && cudaMallocHost(&g->sc.hs, sizeof(DevScalars)) != cudaSuccess) {
+        cudaGetLastError();
+        g->sc.hs = nullptr;
         fail = 1;
     }
     if (!fail && cudaStreamSynchronize(home) != cudaSuccess) {

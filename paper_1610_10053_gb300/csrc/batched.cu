@@ -478,7 +478,7 @@ extern "C" int music_batch_step(music_grid **grids, int count, const double *cfl
             set_error("music_batch_step: grid %d is NULL", i);
             return MUSIC_E_INVAL;
         }
-        if (g->P.nd != 2 || general_grid(g->P) || g->desc.precond_sweeps > PC_FUSED_MAXK ||
+        if (g->P.nd != 2 || general_grid(g->P) || g->desc.precond_sweeps > PC_FUSED_MAXK || g->ns > 0 ||
             g->mixed != grids[0]->mixed) {
             set_error("music_batch_step: grid %d is not a batchable 2-D Cartesian grid of the batch's precision "
                       "(at most %d preconditioner sweeps)", i, PC_FUSED_MAXK);

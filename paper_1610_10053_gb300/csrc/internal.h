@@ -29,6 +29,16 @@ enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
 // grids that need the general (geometry / conduction) code paths
 inline bool general_grid(const GridParams &P) { return P.geom == MUSIC_GEOM_SPHERICAL || P.conduct; }
 
+// The vectors one GMRES solve works on.  A grid with passive scalars keeps
+// a second set for the scalars' solve and swaps it in (swap_space) while that
+// solve runs, so the GMRES driver and the Krylov kernels serve both.
+struct KSpace {
+    double *U, *RU, *b, *x, *t64;  // iterate, its operator, right-hand side, correction, scratch (FP64)
+    void *V, *w, *z, *u;           // Krylov basis and work vectors (Krylov type)
+    size_t n;                      // unknowns
+    DevScalars *ds, *hs;           // device scalars and their pinned host mirror
+};
+
 struct music_grid {
     music_grid_desc desc;
     int stencil_variant;  // STENCIL_*: fused shared-memory kernel (2-D) or multi-pass
@@ -64,6 +74,14 @@ struct music_grid {
     cudaGraphExec_t gexec; // the recorded Newton attempt (null until first use)
     long long glaunch[6];  // kernels per recorded section: top, Newton, cycle, restart, correction, Arnoldi
     double *diag_rows;     // per-row diagnostic partials
+    // passive scalars (Sec. 2.2)
+    int ns;                // scalars (planes of N partial densities in sc.U)
+    KSpace sc;             // the scalars' solve (swapped with the fluid's while it runs)
+    int in_scalar;         // 1 while sc is swapped in
+    double *sq_n, *sq_c;   // scalars at the start of the attempt, their step constant
+    double *sfr;           // face mass fluxes (nd planes of N, lower faces) of the frozen fluid
+    const double *srho;    // density of the frozen fluid (device, N values)
+    double *fr_capture;    // when set, the stencil's non-Jv modes write their face mass fluxes here
     // optional timing of the Jacobian-free stencil launches (music_profile_*)
     int prof_on;
     int prof_pending;            // event pairs recorded, not yet harvested
@@ -155,6 +173,20 @@ int grid_get_state(music_grid *g, double *U, int is_device, cudaStream_t s);
 // ----- batched.cu -----
 extern "C" int music_batch_step(music_grid **grids, int count, const double *cfl, const double *dt_max,
                                 music_step_stats *stats, void *stream);
+
+// ----- scalars.cu -----
+// the scalar operator in stencil_apply's modes, with the fluid frozen at
+// g->srho / g->sfr (used while the scalar space is swapped in)
+int scalar_apply(music_grid *g, int mode, const double *q, const double *aux, const void *v, int vin_double,
+                 void *out, int out_double, double *RS_out, double dt, double sign, cudaStream_t s);
+// q += x; max |x| / rho -> ds->maxdrho (scalar space swapped in)
+int scalar_update(music_grid *g, cudaStream_t s);
+// c_i <- c_i / sum_j c_j with the fluid density rho (device)
+int scalar_renormalise(music_grid *g, const double *rho, cudaStream_t s);
+// copy the multi-pass stencil's face mass fluxes to g->fr_capture
+int capture_ext_fluxes(music_grid *g, cudaStream_t s);
+// swap the fluid and scalar solve spaces
+void swap_space(music_grid *g);
 
 // ----- solver.cu -----
 int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);

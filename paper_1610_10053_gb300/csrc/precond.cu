@@ -476,7 +476,7 @@ int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
 int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
     const size_t n = g->n;
-    if (g->desc.precond == MUSIC_PC_NONE) {
+    if (g->desc.precond == MUSIC_PC_NONE || g->in_scalar) {  // the scalars' solve is unpreconditioned
         const size_t es = g->mixed ? sizeof(float) : sizeof(double);
         if (r != z) CUDA_TRY(cudaMemcpyAsync(z, r, n * es, cudaMemcpyDeviceToDevice, s));
     } else if (general_grid(g->P)) {

@@ -89,7 +89,7 @@ bool lane_eligible(const music_server *S, const Job *j)
 {
     const music_grid_desc &d = j->desc;
     const long long cells = (long long)d.n[0] * d.n[1] * (d.ndim == 3 ? d.n[2] : 1);
-    return S->lane && d.ndim == 2 && d.geometry == MUSIC_GEOM_CARTESIAN && !d.conduct &&
+    return S->lane && d.ndim == 2 && d.geometry == MUSIC_GEOM_CARTESIAN && !d.conduct && d.nscalars == 0 &&
            d.precond_sweeps <= 16 && cells <= S->lane_cells;
 }
 
@@ -112,12 +112,28 @@ Job *admit_locked(music_server *S, bool for_lane = false)
     return nullptr;
 }
 
+// the job's initial state (fluid, then scalar planes) into the grid, and back
+int set_job_state(music_grid *g, Job *j, cudaStream_t s)
+{
+    TRY(grid_set_state(g, j->U0.data(), 0, s));
+    if (g->ns > 0) TRY(music_set_scalars(g, j->U0.data() + g->n, 0, s));
+    return MUSIC_OK;
+}
+
+int get_job_state(music_grid *g, Job *j, cudaStream_t s)
+{
+    j->Ufinal.resize(g->n + g->sc.n);
+    TRY(grid_get_state(g, j->Ufinal.data(), 0, s));
+    if (g->ns > 0) TRY(music_get_scalars(g, j->Ufinal.data() + g->n, 0, s));
+    return MUSIC_OK;
+}
+
 int run_job(Job *j, cudaStream_t s)
 {
     music_grid *g = nullptr;
     TRY(grid_create(&j->desc, s, &g));
     g->solver_variant = j->graph ? SOLVER_GRAPH : SOLVER_HOST;
-    int rc = grid_set_state(g, j->U0.data(), 0, s);
+    int rc = set_job_state(g, j, s);
     if (rc == MUSIC_OK && j->autotune && j->n_steps > 0) {
         // tile shapes for this configuration (timed once per process, then cached)
         double dt = 0.0;
@@ -145,8 +161,7 @@ int run_job(Job *j, cudaStream_t s)
     j->res.sim_time = t;
     if (rc == MUSIC_OK) rc = music_diagnostics(g, j->rho_L, j->rho_H, j->res.diag, s);
     if (rc == MUSIC_OK) {
-        j->Ufinal.resize(g->n);
-        rc = grid_get_state(g, j->Ufinal.data(), 0, s);
+        rc = get_job_state(g, j, s);
     }
     grid_destroy(g);
     return rc;
@@ -376,7 +391,7 @@ int music_submit_solve(music_server *S, const music_solve_req *req, uint64_t *ti
     }
     j->desc = req->desc;
     const size_t ncell = (size_t)req->desc.n[0] * req->desc.n[1] * (req->desc.ndim == 3 ? req->desc.n[2] : 1);
-    j->U0.assign(req->U0, req->U0 + (2 + req->desc.ndim) * ncell);
+    j->U0.assign(req->U0, req->U0 + (2 + req->desc.ndim + (size_t)req->desc.nscalars) * ncell);
     j->n_steps = req->n_steps;
     j->cfl = req->cfl;
     j->dt_max = req->dt_max;

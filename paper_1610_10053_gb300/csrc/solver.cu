@@ -135,20 +135,69 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
     return MUSIC_OK;
 }
 
+// The stencil call `call`, with its face mass fluxes captured for the
+// passive scalars when the grid has any.
+template <typename F>
+int with_fluxes(music_grid *g, F &&call)
+{
+    if (g->ns > 0) g->fr_capture = g->sfr;
+    const int rc = call();
+    g->fr_capture = nullptr;
+    return rc;
+}
+
+// Swaps the scalar solve space in for its lifetime.
+struct ScalarSpace {
+    music_grid *g;
+    explicit ScalarSpace(music_grid *g_) : g(g_) { swap_space(g); }
+    ~ScalarSpace() { swap_space(g); }
+};
+
+// One Newton iteration of the passive scalars (Sec. 2.2) with the fluid
+// frozen at its current iterate, whose face mass fluxes are in g->sfr:
+// b = -((q - C_s) - dt/2 S(q)), unpreconditioned GMRES, q += x.  *maxdq
+// receives max |delta q| / rho.
+int scalar_iteration(music_grid *g, double dt, music_step_stats *st, double *maxdq, cudaStream_t s)
+{
+    g->srho = g->U;  // the fluid iterate's density plane
+    ScalarSpace sp(g);
+    TRY(stencil_apply(g, SM_F, g->U, g->sq_c, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s));
+    TRY(dev_norm2(g, g->U, 1, g->n, &g->ds->unorm2, s));
+    GmresOut go;
+    TRY(gmres(g, dt, &go, s));
+    st->scalar_gmres_its += go.its;
+    TRY(scalar_update(g, s));
+    TRY(sync_scalars(g, s));
+    *maxdq = g->hs->maxdrho;
+    return MUSIC_OK;
+}
+
 // One Newton solve of size dt from the grid's state.  Returns MUSIC_OK,
 // MUSIC_E_NEWTON_FAIL (state restored) or a hard error.
 int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s)
 {
     const size_t n = g->n;
+    const size_t nq = g->sc.n;
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    TRY(stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt, 1.0, s));
+    TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt,
+                                                  1.0, s); }));
+    if (g->ns > 0) {
+        // scalar step constant C_s = q^n + dt/2 S(q^n) with the fluid at U^n
+        CUDA_TRY(cudaMemcpyAsync(g->sq_n, g->sc.U, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        g->srho = g->Un;
+        TRY(scalar_apply(g, SM_CN, g->sq_n, nullptr, nullptr, 1, g->sq_c, 1, nullptr, dt, 1.0, s));
+    }
     st->newton_its = 0;
     st->gmres_its = 0;
     st->gmres_unconverged = 0;
+    st->scalar_gmres_its = 0;
     int ok = 0;
     for (int k = 0; k < g->desc.newton_max_its; k++) {
-        // b = -F(U), RU = R(U)
-        TRY(stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s));
+        // b = -F(U), RU = R(U) (and the face mass fluxes of U for the scalars)
+        TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt,
+                                                      -1.0, s); }));
+        double maxdq = 0.0;
+        if (g->ns > 0) TRY(scalar_iteration(g, dt, st, &maxdq, s));
         TRY(dev_norm2(g, g->U, 1, n, &g->ds->unorm2, s));
         TRY(precond_setup(g, g->U, dt, s));
         GmresOut go;
@@ -162,7 +211,7 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
         TRY(sync_scalars(g, s));
         st->max_drho = g->hs->maxdrho;
         st->newton_its = k + 1;
-        if (g->hs->maxdrho <= g->desc.newton_tol) {
+        if (g->hs->maxdrho <= g->desc.newton_tol && (!g->desc.scalar_enforce || maxdq <= g->desc.newton_tol)) {
             ok = 1;
             break;
         }
@@ -170,9 +219,12 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     }
     if (!ok) {
         CUDA_TRY(cudaMemcpyAsync(g->U, g->Un, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if (g->ns > 0)
+            CUDA_TRY(cudaMemcpyAsync(g->sc.U, g->sq_n, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         return MUSIC_E_NEWTON_FAIL;
     }
+    if (g->ns > 0) TRY(scalar_renormalise(g, g->U, s));
     return MUSIC_OK;
 }
 
@@ -234,7 +286,7 @@ int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_
     int h = 0;
     for (;;) {
         st.dt = dt;
-        if (g->solver_variant == SOLVER_GRAPH && !g->prof_on)
+        if (g->solver_variant == SOLVER_GRAPH && !g->prof_on && g->ns == 0)
             rc = graph_newton_attempt(g, dt, &st, s);
         else
             rc = newton_attempt(g, dt, &st, s);

@@ -292,6 +292,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
                   int vin_double, void *out, int out_double, double *RU_out, double dt, double sign,
                   cudaStream_t s)
 {
+    if (g->in_scalar) return scalar_apply(g, mode, U, aux, v, vin_double, out, out_double, RU_out, dt, sign, s);
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
     if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P)) {
@@ -312,6 +313,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
             TRY(run_passes<float>(g, U, (const float *)v, s));
     } else {
         TRY(run_passes<double>(g, U, nullptr, s));
+        if (g->fr_capture) TRY(capture_ext_fluxes(g, s));  // face mass fluxes for passive scalars
     }
     switch (mode) {
     case SM_R:

@@ -121,10 +121,13 @@ struct Tile2D {
 
 // One tile (bx, by) of the fused stencil, run by a CTA of TX*TY threads with
 // Tile2D<TX, TY>::SMEM bytes of shared memory at `sm`.  epsv is the finite-
-// difference step (SM_JV).  Callable from any kernel that owns such a CTA.
+// difference step (SM_JV).  Fr_out (null: none) receives the mass fluxes of
+// the tile cells' lower x- and y-faces (2 planes of N) for passive scalars.
+// Callable from any kernel that owns such a CTA.
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __device__ void fused2d_tile(const GridParams &P, const double *U, const double *aux, const VIN *v, VOUT *out,
-                             double *RU_out, double hdt, double sign, double epsv, int bx, int by, double *sm)
+                             double *RU_out, double hdt, double sign, double epsv, int bx, int by, double *sm,
+                             double *Fr_out = nullptr)
 {
     using TL = Tile2D<TX, TY>;
     constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
@@ -276,6 +279,10 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
         Rv[3] = (-acc - (pp[q] - pp[q - RX]) * ix1) + rbar * P.g[1];
     }
     const long long c = gx + (long long)P.n[0] * gy;
+    if (MODE != SM_JV && Fr_out) {
+        Fr_out[c] = Frx[q];
+        Fr_out[P.N + c] = Fry[q];
+    }
     const double c_jv = (MODE == SM_JV && epsv != 0.0) ? hdt / epsv : 0.0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {

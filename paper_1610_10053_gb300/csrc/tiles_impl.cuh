@@ -12,12 +12,12 @@ using namespace tile;
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
                                                     const VIN *v, VOUT *out, double *RU_out, double hdt,
-                                                    double sign, const double *eps)
+                                                    double sign, const double *eps, double *Fr_out)
 {
     extern __shared__ double sm[];
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
     fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
-                                          blockIdx.y, sm);
+                                          blockIdx.y, sm, Fr_out);
 }
 
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
@@ -33,7 +33,8 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
     }
     const GridParams &P = g->P;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
-    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps);
+    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps,
+                                         MODE == SM_JV ? nullptr : g->fr_capture);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

@@ -1,0 +1,143 @@
+"""GPU passive scalars (Sec. 2.2) against the oracle.
+
+The scalar operator in FP64 to 1e-12 of its term scale; whole steps with
+scalars (Newton, the scalars' unpreconditioned GMRES, renormalisation) to
+1e-9 in FP64 and the mixing width to 1e-7 in mixed precision; passivity (the
+fluid bitwise unchanged by the scalars); the solve server carrying them.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1610_10053_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from test_gpu_parity import B  # noqa: E402
+
+
+def with_c(p, seed):
+    rng = np.random.default_rng(seed)
+    N = p.ncells
+    i = np.arange(N) % p.n[0]
+    j = (np.arange(N) // p.n[0]) % p.n[1]
+    k = np.arange(N) // (p.n[0] * p.n[1])
+    a = rng.uniform(0, 2 * np.pi, 3)
+    c = 0.5 + 0.3 * np.sin(2 * np.pi * i / p.n[0] + a[0]) * np.cos(2 * np.pi * j / p.n[1] + a[1]) * \
+        np.cos(2 * np.pi * k / p.n[2] + a[2])
+    rho = p.U[:N]
+    return p.with_options(q=np.concatenate([c * rho, (1.0 - c) * rho]))
+
+
+CASES = {
+    "periodic_2d": lambda: with_c(I.random_smooth(2, (20, 14), seed=71, amp=0.3), 1),
+    "walls_2d": lambda: with_c(I.random_smooth(2, (12, 18), seed=72, amp=0.3,
+                                               bc=(I.BC_PERIODIC, I.BC_WALL, I.BC_PERIODIC),
+                                               wall_scalar=(0, I.WALL_HSE, 0), g=(0.0, -0.4, 0.0)), 2),
+    "periodic_3d": lambda: with_c(I.random_smooth(3, (9, 8, 7), seed=73, amp=0.3), 3),
+    "rt_sharp": lambda: I.rayleigh_taylor(nx=16, ny=48, scalars=True),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_scalar_operator(case, prec):
+    p = CASES[case]()
+    with B().Grid(p, precision=getattr(B(), prec)) as g:
+        S = g.scalar_operator(torch.from_numpy(p.U).cuda(), torch.from_numpy(p.q).cuda())
+        torch.cuda.synchronize()
+        S = S.cpu().numpy()
+    ref = O.scalar_operator(p, p.U, p.q)
+    scale = max(np.abs(ref).max(), np.abs(O.spatial_operator(p, p.U)[:p.ncells]).max())
+    assert np.abs(S - ref).max() <= 1e-12 * scale
+
+
+def run_gpu(p, prec, nsteps=None):
+    with B().Grid(p, precision=prec) as g:
+        g.set_state(p.U)
+        if p.q is not None:
+            g.set_scalars(p.q)
+        st = g.run(nsteps)
+        U = g.get_state()
+        q = g.get_scalars() if p.q is not None else None
+        h = g.scalar_mixing_width() if p.q is not None else None
+    return U, q, st, h
+
+
+def test_steps_fp64_against_oracle():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=3, scalars=True)
+    U, q, st, h = run_gpu(p, B().FP64)
+    Ur, qr, str_, sg = O.run_s(p)
+    assert [s["newton_its"] for s in st] == [s["newton_its"] for s in str_]
+    assert np.abs(U - Ur).max() <= 1e-9 * np.abs(Ur).max()
+    assert np.abs(q - qr).max() <= 1e-9 * np.abs(qr).max()
+    hr = O.scalar_mixing_width(p, Ur, qr)
+    assert abs(h - hr) <= 1e-9 * (abs(hr) + 1e-3)
+    assert all(s["scalar_gmres_its"] >= s["newton_its"] for s in st)
+
+
+def test_steps_mixed_mixing_width_against_fp64_oracle():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=3, scalars=True)
+    U, q, st, h = run_gpu(p, B().MIXED)
+    Ur, qr, _, _ = O.run_s(p)
+    hr = O.scalar_mixing_width(p, Ur, qr)
+    assert abs(h - hr) <= 1e-7 * (abs(hr) + 1e-3)
+    assert np.abs(q - qr).max() <= 1e-6 * np.abs(qr).max()
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_scalars_are_passive_on_the_gpu(prec):
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=3, scalars=True)
+    U, q, st, h = run_gpu(p, getattr(B(), prec))
+    U0, _, st0, _ = run_gpu(p.with_options(q=None), getattr(B(), prec))
+    assert np.array_equal(U, U0)
+    assert [s["gmres_its"] for s in st] == [s["gmres_its"] for s in st0]
+
+
+def test_renormalised_and_bounded():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=3, scalars=True)
+    U, q, st, h = run_gpu(p, B().MIXED)
+    N = p.ncells
+    c = q.reshape(2, N) / U[:N]
+    assert np.abs(c.sum(axis=0) - 1.0).max() <= 4e-16
+    assert c.min() >= -1e-6 and c.max() <= 1.0 + 1e-6
+
+
+def test_enforced_scalar_convergence_matches_oracle():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=2, scalars=True).with_options(scalar_enforce=1)
+    U, q, st, h = run_gpu(p, B().FP64)
+    Ur, qr, str_, _ = O.run_s(p)
+    assert [s["newton_its"] for s in st] == [s["newton_its"] for s in str_]
+    assert np.abs(q - qr).max() <= 1e-9 * np.abs(qr).max()
+
+
+def test_3d_steps_with_scalars():
+    """At Newton tolerance 1e-8 the GPU and the oracle may take different
+    GMRES paths on this flow and agree only to that tolerance; at 1e-11 both
+    solutions are converged well below the comparison's 1e-9."""
+    p = with_c(I.taylor_green(n=12, nsteps=2), 4).with_options(newton_tol=1e-11)
+    U, q, st, h = run_gpu(p, B().FP64)
+    Ur, qr, str_, _ = O.run_s(p)
+    assert np.abs(q - qr).max() <= 1e-9 * np.abs(qr).max()
+
+
+def test_batch_step_rejects_scalar_grids():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=1, scalars=True)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        g.set_scalars(p.q)
+        with pytest.raises(B().MusicError):
+            B().batch_step([g])
+
+
+def test_server_carries_scalars():
+    p = I.rayleigh_taylor(nx=16, ny=48, nsteps=2, scalars=True)
+    U, q, st, h = run_gpu(p, B().MIXED)
+    with B().Server(max_active=2) as s:
+        t = s.submit(p, B().MIXED)
+        assert s.wait(t, timeout_ms=300000)["status"] == 0
+        out = s.result_state(t)
+    assert np.array_equal(out[:U.size], U)
+    assert np.array_equal(out[U.size:], q)
