@@ -953,6 +953,9 @@ void or_diagnostics(const or_grid *g, const double *U, double rho_L, double rho_
     for (int d = 0; d < nd; d++) free(uf[d]);
 }
 
+double or_select_dt(const or_grid *g, const double *U, double cfl_hydro, double cfl_adv, double cfl_rad,
+                    double dt_max, int *which);
+
 /* ---------------- passive scalars (Sec. 2.2) ---------------- */
 /*
  * ns passive scalars carried as partial densities q_i = c_i rho (ns planes
@@ -1146,12 +1149,12 @@ int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, 
     return ok ? 0 : 1;
 }
 
-int or_run_s(const or_grid *g, double *U, double *q, int ns, int nsteps, double cfl, double dt_max, int enforce,
-             or_step_stats *st, int *scal_gmres)
+int or_run_s(const or_grid *g, double *U, double *q, int ns, int nsteps, double cfl, double cfl_adv, double cfl_rad,
+             double dt_max, int enforce, or_step_stats *st, int *scal_gmres)
 {
     for (int s = 0; s < nsteps; s++) {
-        double dt = cfl / or_cfl_rate(g, U);
-        if (dt_max > 0.0 && dt > dt_max) dt = dt_max;
+        int which;
+        double dt = or_select_dt(g, U, cfl, cfl_adv, cfl_rad, dt_max, &which);
         int h = 0;
         for (;;) {
             int rc = or_newton_step_s(g, U, q, ns, dt, enforce, &st[s], &scal_gmres[s]);
@@ -1185,4 +1188,99 @@ double or_scalar_mixing_width(const or_grid *g, const double *U, const double *q
         h += 2.0 * (a1 < a2 ? a1 : a2) * g->dx[1];
     }
     return h;
+}
+
+/* ---------------- time-step limits (Sec. 2, choice of the time step) ---------------- */
+/*
+ * rates[0] = max (|u_d| + c_s) / h_d   (hydrodynamic CFL, Eq. 4);
+ * rates[1] = max |u_d| / h_d           (advective CFL);
+ * rates[2] = max D / h_d^2             (radiative CFL; 0 without conduction)
+ * over cells and directions, u_d the mean of the cell's two face velocities,
+ * h_d the distance between cell centres (dr, or r_c dtheta), and D = chi /
+ * (rho c_v) the radiative diffusivity, c_v = 1 / (gamma - 1) (p = rho T).
+ */
+void or_dt_rates(const or_grid *g, const double *U, double *rates)
+{
+    const long N = or_ncells(g);
+    double lh = 0.0, la = 0.0, lr = 0.0;
+    const double gm1 = g->gamma - 1.0;
+    for (long c = 0; c < N; c++) {
+        int ix[3];
+        or_cell_coords(g, c, ix);
+        double rho = U[c];
+        double cs = sqrt(g->gamma * (gm1 * U[N + c]) / rho);
+        double D = 0.0;
+        if (g->conduct) {
+            double T = gm1 * U[N + c] / rho;
+            double t3 = T * T * T;
+            double chi = g->chi0 * (t3 * t3 * sqrt(T)) / (rho * rho);
+            D = chi * gm1 / rho;
+        }
+        for (int d = 0; d < g->nd; d++) {
+            double um = 0.0, up = 0.0;
+            if (!or_wall_face(g, ix, d)) {
+                long l = or_nb(g, ix, d, -1);
+                um = U[(2 + d) * N + c] / (0.5 * (U[l] + rho));
+            }
+            if (!(g->bc[d] == OR_BC_WALL && ix[d] == g->n[d] - 1)) {
+                long r = or_nb(g, ix, d, +1);
+                up = U[(2 + d) * N + r] / (0.5 * (rho + U[r]));
+            }
+            double h = (g->geom == OR_GEOM_SPHERICAL) ? or_sph_h(g, d, ix[0]) : g->dx[d];
+            double a = fabs(0.5 * (um + up));
+            if ((a + cs) / h > lh) lh = (a + cs) / h;
+            if (a / h > la) la = a / h;
+            if (D / (h * h) > lr) lr = D / (h * h);
+        }
+    }
+    rates[0] = lh;
+    rates[1] = la;
+    rates[2] = lr;
+}
+
+/* The most restrictive of the limits given (each <= 0: not applied):
+ * dt = min(cfl_hydro / rates[0], cfl_adv / rates[1], cfl_rad / rates[2],
+ * dt_max).  *which = 0, 1, 2 or 3 names the limit that applied. */
+double or_select_dt(const or_grid *g, const double *U, double cfl_hydro, double cfl_adv, double cfl_rad,
+                    double dt_max, int *which)
+{
+    double r[3];
+    or_dt_rates(g, U, r);
+    const double lim[3] = {cfl_hydro, cfl_adv, cfl_rad};
+    double dt = INFINITY;
+    *which = -1;
+    for (int k = 0; k < 3; k++) {
+        if (!(lim[k] > 0.0) || !(r[k] > 0.0)) continue;
+        double t = lim[k] / r[k];
+        if (t < dt) {
+            dt = t;
+            *which = k;
+        }
+    }
+    if (dt_max > 0.0 && dt_max < dt) {
+        dt = dt_max;
+        *which = 3;
+    }
+    return dt;
+}
+
+/* nsteps steps with the time step chosen by or_select_dt (limits <= 0 not
+ * applied); returns the steps completed */
+int or_run_dt(const or_grid *g, double *U, int nsteps, double cfl_hydro, double cfl_adv, double cfl_rad,
+              double dt_max, or_step_stats *st)
+{
+    for (int s = 0; s < nsteps; s++) {
+        int which;
+        double dt = or_select_dt(g, U, cfl_hydro, cfl_adv, cfl_rad, dt_max, &which);
+        int h = 0;
+        for (;;) {
+            int rc = or_newton_step(g, U, dt, &st[s]);
+            if (rc == 0) break;
+            if (h >= g->max_halvings) return s;
+            dt = 0.5 * dt;
+            h++;
+        }
+        st[s].halvings = h;
+    }
+    return nsteps;
 }

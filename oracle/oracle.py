@@ -92,9 +92,16 @@ def lib():
         L.or_newton_step_s.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                        ctypes.POINTER(OrStepStats), ctypes.POINTER(ctypes.c_int)]
         L.or_run_s.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                               ctypes.c_int, ctypes.POINTER(OrStepStats), ctypes.POINTER(ctypes.c_int)]
+                               ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(OrStepStats),
+                               ctypes.POINTER(ctypes.c_int)]
+        L.or_run_dt.argtypes = [G, _dbl_p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.POINTER(OrStepStats)]
         L.or_scalar_mixing_width.argtypes = [G, _dbl_p, _dbl_p]
         L.or_scalar_mixing_width.restype = ctypes.c_double
+        L.or_dt_rates.argtypes = [G, _dbl_p, _dbl_p]
+        L.or_select_dt.argtypes = [G, _dbl_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_int)]
+        L.or_select_dt.restype = ctypes.c_double
     return _lib
 
 
@@ -225,7 +232,11 @@ def run(prob, U=None, nsteps=None, cfl=None, dt_max=None):
     dt_max = prob.dt_max if dt_max is None else dt_max
     st = (OrStepStats * max(nsteps, 1))()
     g = grid(prob)
-    done = lib().or_run(ctypes.byref(g), _p(U), int(nsteps), float(cfl), float(dt_max), st)
+    if prob.cfl_adv > 0.0 or prob.cfl_rad > 0.0:
+        done = lib().or_run_dt(ctypes.byref(g), _p(U), int(nsteps), float(cfl), float(prob.cfl_adv),
+                               float(prob.cfl_rad), float(dt_max), st)
+    else:
+        done = lib().or_run(ctypes.byref(g), _p(U), int(nsteps), float(cfl), float(dt_max), st)
     if done != nsteps:
         raise RuntimeError("oracle: Newton failed at step %d" % done)
     return U, [st[i].as_dict() for i in range(nsteps)]
@@ -289,8 +300,8 @@ def run_s(prob, U=None, q=None, nsteps=None, cfl=None, dt_max=None, enforce=None
     st = (OrStepStats * max(nsteps, 1))()
     its = (ctypes.c_int * max(nsteps, 1))()
     g = grid(prob)
-    done = lib().or_run_s(ctypes.byref(g), _p(U), _p(q), ns, int(nsteps), float(cfl), float(dt_max), int(enforce),
-                          st, its)
+    done = lib().or_run_s(ctypes.byref(g), _p(U), _p(q), ns, int(nsteps), float(cfl), float(prob.cfl_adv),
+                          float(prob.cfl_rad), float(dt_max), int(enforce), st, its)
     if done != nsteps:
         raise RuntimeError("oracle: Newton failed at step %d" % done)
     return U, q, [st[i].as_dict() for i in range(nsteps)], [its[i] for i in range(nsteps)]
@@ -301,3 +312,24 @@ def scalar_mixing_width(prob, U, q) -> float:
     U, q = _vec(U), _vec(q)
     g = grid(prob)
     return float(lib().or_scalar_mixing_width(ctypes.byref(g), _p(U), _p(q)))
+
+
+# ---------------- time-step limits ----------------
+def dt_rates(prob, U) -> tuple:
+    """(max (|u|+c_s)/h, max |u|/h, max D/h^2) over cells and directions."""
+    U = _vec(U)
+    r = np.zeros(3)
+    g = grid(prob)
+    lib().or_dt_rates(ctypes.byref(g), _p(U), _p(r))
+    return tuple(r.tolist())
+
+
+def select_dt(prob, U, cfl_hydro=0.0, cfl_adv=0.0, cfl_rad=0.0, dt_max=0.0):
+    """The most restrictive limit; returns (dt, which) with which = 0 hydro,
+    1 advective, 2 radiative, 3 dt_max."""
+    U = _vec(U)
+    w = ctypes.c_int(-1)
+    g = grid(prob)
+    dt = lib().or_select_dt(ctypes.byref(g), _p(U), float(cfl_hydro), float(cfl_adv), float(cfl_rad),
+                            float(dt_max), ctypes.byref(w))
+    return float(dt), w.value

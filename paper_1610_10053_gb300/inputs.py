@@ -61,9 +61,11 @@ class Problem:
     gamma: float
     g: tuple            # constant gravity vector
     U: np.ndarray       # initial state, shape (nv * N,)
-    cfl: float = 1.0
+    cfl: float = 1.0                   # CFL_hydro limit of the time step
     nsteps: int = 1
     dt_max: float = 0.0
+    cfl_adv: float = 0.0               # advective CFL limit (0: none)
+    cfl_rad: float = 0.0               # radiative CFL limit (0: none)
     restart: int = 30
     max_restarts: int = 10
     gmres_rtol: float = 1e-2
@@ -166,6 +168,15 @@ def rayleigh_taylor(nx: int = 64, ny: int = 192, perturbation: str = "benchmark"
     return Problem("rayleigh_taylor", 2, n, x0, length, (BC_PERIODIC, BC_WALL, BC_PERIODIC),
                    (WALL_MIRROR, WALL_HSE, WALL_MIRROR), gamma, (0.0, -gmag, 0.0), U,
                    cfl=cfl, nsteps=nsteps, rho_L=1.0, rho_H=2.0, q=q)
+
+
+def rt_paper(nx: int = 100, ny: int = 300, nsteps: int = 100, scalars: bool = True) -> Problem:
+    """The paper's own Rayleigh-Taylor runs (Sec. 3): the perturbation of its
+    Eq. for the initial vertical velocity, grids of aspect ratio one (100x300,
+    300x900), CFL_hydro fixed at 0.8, the unpreconditioned JFNK solver, and
+    the two marker scalars."""
+    p = rayleigh_taylor(nx=nx, ny=ny, perturbation="paper", cfl=0.8, nsteps=nsteps, scalars=scalars)
+    return dataclasses.replace(p, name="rt_paper", precond=PC_NONE)
 
 
 def kelvin_helmholtz(n: int = 512, seed: int = 2, noise: float = 1e-4, cfl: float = 10.0,
