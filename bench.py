@@ -115,6 +115,9 @@ WORKLOADS = {
     "rt64x192_scalars": ("Rayleigh-Taylor 2-D, 64x192, two passive scalars (unpreconditioned scalar JFNK), "
                          "CFL 5, Newton tol 1e-8, GMRES(30)",
                          lambda I, r: I.rayleigh_taylor(scalars=True)),
+    "rt_paper": ("Rayleigh-Taylor 2-D at the paper's settings: 100x300, CFL_hydro 0.8, unpreconditioned JFNK, "
+                 "two passive scalars, Newton tol 1e-8, GMRES(30)",
+                 lambda I, r: I.rt_paper()),
     "tgv128": ("Taylor-Green vortex 3-D, 128^3 periodic, CFL 20, Newton tol 1e-8, GMRES(30)",
                lambda I, r: I.taylor_green(n=128)),
     "wedge256": ("2-D spherical wedge 256 (r) x 128 (theta), radiative diffusion, polytrope n=3 background, "
@@ -217,6 +220,12 @@ def run_music(args):
     e2e = end_to_end(mixed["grid"], prob, stream, max(2, min(args.steps, 5)))
     for r in result.values():
         r["grid"].close()
+    series = None
+    if args.series > 0 and rank == 0:
+        series = run_series(prob, args.series, max(1, args.every))
+    dt_study = None
+    if args.dt_study > 0 and rank == 0:
+        dt_study = run_dt_study(args.dt_study, args.dt_study_t)
     serving = None
     if not args.no_serving and ws == 1:
         serving = run_serving(args.serve_solves, lane_cells=args.serve_lane_cells)
@@ -258,6 +267,8 @@ def run_music(args):
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clocks"],
         "serving": serving,
+        "series": series,
+        "dt_study": dt_study,
         "final_diagnostics": final_diag,
         "sim_time": float(sum(x["dt"] for x in mixed["stats"])),
     }
@@ -404,6 +415,64 @@ def run_serving(nsolves=256, max_active=16, seq_sample=12, lane_cells=0):
             "sequential_sample": seq_sample, "cell_steps": cells}
 
 
+def run_series(prob, nsteps, every):
+    """Mixing widths over a run (mixed precision, after the timed part): the
+    density-based width of Sec. 3 and, with scalars, the scalar-based one,
+    every `every` steps."""
+    from paper_1610_10053_gb300 import binding as B
+    out = {"t": [], "h_density": [], "h_scalar": [], "newton_its": [], "gmres_its": []}
+    t = 0.0
+    with B.Grid(prob, precision=B.MIXED) as g:
+        g.set_state(prob.U)
+        if prob.q is not None:
+            g.set_scalars(prob.q)
+        g.autotune()
+        t0 = time.perf_counter()
+        for k in range(nsteps):
+            st = g.step()
+            t += st["dt"]
+            if (k + 1) % every == 0 or k + 1 == nsteps:
+                out["t"].append(t)
+                out["h_density"].append(g.diagnostics()["mixing_height"])
+                out["h_scalar"].append(g.scalar_mixing_width() if prob.q is not None else None)
+                out["newton_its"].append(st["newton_its"])
+                out["gmres_its"].append(st["gmres_its"])
+        out["wall_s"] = time.perf_counter() - t0
+    out["steps"] = nsteps
+    return out
+
+
+def run_dt_study(n, t_end, cfls=(0.05, 10.0, 50.0)):
+    """Sec. 5's time-step study at a smaller size: the Taylor-Green vortex to
+    t_end with CFL_hydro fixed at the smallest value and capped at the larger
+    ones; the mean kinetic energy over time for each (mixed precision)."""
+    from paper_1610_10053_gb300 import binding as B
+    from paper_1610_10053_gb300 import inputs as I
+    out = {}
+    for cfl in cfls:
+        p = I.taylor_green(n=n).with_options(cfl=cfl)
+        rec = {"t": [0.0], "kinetic_energy": [], "steps": 0, "newton_its": 0, "gmres_its": 0}
+        with B.Grid(p, precision=B.MIXED) as g:
+            g.set_state(p.U)
+            rec["kinetic_energy"].append(g.diagnostics()["mean_kinetic_energy"])
+            t, nrec = 0.0, 1
+            t0 = time.perf_counter()
+            while t < t_end * (1 - 1e-12):
+                dt = min(g.cfl_dt(cfl), t_end - t)
+                st = g.newton_step(dt)
+                t += st["dt"]
+                rec["steps"] += 1
+                rec["newton_its"] += st["newton_its"]
+                rec["gmres_its"] += st["gmres_its"]
+                if t >= nrec * t_end / 8 * (1 - 1e-12):
+                    rec["t"].append(t)
+                    rec["kinetic_energy"].append(g.diagnostics()["mean_kinetic_energy"])
+                    nrec += 1
+            rec["wall_s"] = time.perf_counter() - t0
+        out["cfl_%g" % cfl] = rec
+    return {"grid": "%d^3" % n, "t_end": t_end, "runs": out}
+
+
 def cpu_baseline(prob, steps=1):
     """The FP64 CPU oracle as it stands, single-threaded, on one implicit step
     of the same workload."""
@@ -460,6 +529,12 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--series", type=int, default=0,
+                    help="after the timed steps, run this many more recording the mixing widths")
+    ap.add_argument("--every", type=int, default=100, help="record the series every this many steps")
+    ap.add_argument("--dt-study", type=int, default=0,
+                    help="also run the Taylor-Green time-step study on this many cells per edge")
+    ap.add_argument("--dt-study-t", type=float, default=2.0, help="end time of the time-step study")
     ap.add_argument("--serve-lane-cells", type=int, default=0,
                     help="largest solve the server's batch lane takes (<= 0: no batch lane)")
     ap.add_argument("--serve-solves", type=int, default=256)

@@ -300,6 +300,25 @@ int music_scalar_operator(music_grid *grid, const double *U, const double *q, do
    cells normal to direction 1.  Synchronises `stream`. */
 int music_scalar_mixing_width(music_grid *grid, double *h, void *stream);
 
+/*
+ * Time-step limits (Sec. 2, choice of the time step).  Each limit <= 0 is
+ * not applied; the step is the most restrictive of the others:
+ *   cfl_hydro / max (|u_d| + c_s) / h_d     (Eq. 4),
+ *   cfl_adv   / max |u_d| / h_d             (the paper caps it at 0.5),
+ *   cfl_rad   / max D / h_d^2               (radiative diffusion grids,
+ *                                            D = chi / (rho c_v)),
+ *   dt_max,
+ * maxima over cells and directions of the grid's state, u_d the mean of the
+ * cell's two face velocities, h_d the distance between cell centres (dr, or
+ * r_c dtheta on spherical grids).  *which (may be NULL) receives 0, 1, 2 or 3
+ * for the limit that applied.  Synchronises `stream`.  Errors: MUSIC_E_INVAL
+ * (no limit applies), MUSIC_E_NONFINITE.
+ */
+typedef struct {
+    double cfl_hydro, cfl_adv, cfl_rad, dt_max;
+} music_dt_limits;
+int music_select_dt(music_grid *grid, const music_dt_limits *limits, double *dt, int *which, void *stream);
+
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).
    Synchronises `stream`. */

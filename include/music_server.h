@@ -51,6 +51,8 @@ typedef struct {
     double cfl;               /* each step: dt = cfl-limited (Eq. 4), > 0 */
     double dt_max;            /* optional cap on dt (<= 0: none) */
     double rho_L, rho_H;      /* densities of the mixing-height diagnostic */
+    double cfl_adv, cfl_rad;  /* optional advective / radiative CFL limits (<= 0: none); the step
+                                 is the most restrictive limit (music_select_dt) */
 } music_solve_req;
 
 typedef struct {

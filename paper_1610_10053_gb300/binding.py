@@ -57,6 +57,11 @@ class StepStats(ctypes.Structure):
 
 
 # every exported symbol of include/music.h with its ctypes signature
+class DtLimits(ctypes.Structure):
+    _fields_ = [("cfl_hydro", ctypes.c_double), ("cfl_adv", ctypes.c_double), ("cfl_rad", ctypes.c_double),
+                ("dt_max", ctypes.c_double)]
+
+
 class TuneReport(ctypes.Structure):
     _fields_ = [("tunable", ctypes.c_int), ("from_cache", ctypes.c_int), ("stencil_tile", ctypes.c_int * 2),
                 ("precond_tile", ctypes.c_int * 2), ("precond_stages", ctypes.c_int), ("n_stencil", ctypes.c_int),
@@ -104,6 +109,8 @@ SIGNATURES = {
                                         ctypes.POINTER(StepStats), ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "music_set_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "music_select_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(DtLimits), _dbl_p,
+                                       ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "music_get_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     "music_scalar_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_void_p]),
@@ -360,12 +367,23 @@ class Grid:
         check(load().music_newton_step(self.h, float(dt), ctypes.byref(st), _stream()))
         return st.as_dict()
 
+    def select_dt(self, cfl_hydro: float = 0.0, cfl_adv: float = 0.0, cfl_rad: float = 0.0,
+                  dt_max: float = 0.0):
+        """(dt, which) of music_select_dt: the most restrictive limit."""
+        lim = DtLimits(float(cfl_hydro), float(cfl_adv), float(cfl_rad), float(dt_max))
+        dt, w = ctypes.c_double(), ctypes.c_int()
+        check(load().music_select_dt(self.h, ctypes.byref(lim), ctypes.byref(dt), ctypes.byref(w), _stream()))
+        return dt.value, w.value
+
     def step(self, cfl: Optional[float] = None, dt_max: Optional[float] = None) -> dict:
         cfl = self.prob.cfl if cfl is None else cfl
         dt_max = self.prob.dt_max if dt_max is None else dt_max
-        dt = self.cfl_dt(cfl)
-        if dt_max and dt_max > 0 and dt > dt_max:
-            dt = dt_max
+        if self.prob.cfl_adv > 0 or self.prob.cfl_rad > 0:
+            dt, _ = self.select_dt(cfl, self.prob.cfl_adv, self.prob.cfl_rad, dt_max or 0.0)
+        else:
+            dt = self.cfl_dt(cfl)
+            if dt_max and dt_max > 0 and dt > dt_max:
+                dt = dt_max
         return self.newton_step(dt)
 
     def autotune(self, dt: Optional[float] = None, force: bool = False) -> dict:
@@ -425,7 +443,7 @@ class ServerOpts(ctypes.Structure):
 class SolveReq(ctypes.Structure):
     _fields_ = [("desc", GridDesc), ("U0", ctypes.POINTER(ctypes.c_double)), ("n_steps", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("dt_max", ctypes.c_double), ("rho_L", ctypes.c_double),
-                ("rho_H", ctypes.c_double)]
+                ("rho_H", ctypes.c_double), ("cfl_adv", ctypes.c_double), ("cfl_rad", ctypes.c_double)]
 
 
 class SolveResult(ctypes.Structure):
@@ -481,6 +499,7 @@ class Server:
         req.cfl = float(prob.cfl if cfl is None else cfl)
         req.dt_max = float(prob.dt_max if dt_max is None else dt_max)
         req.rho_L, req.rho_H = float(prob.rho_L), float(prob.rho_H)
+        req.cfl_adv, req.cfl_rad = float(prob.cfl_adv), float(prob.cfl_rad)
         t = ctypes.c_uint64()
         check(load().music_submit_solve(self.h, ctypes.byref(req), ctypes.byref(t)))
         self._n[t.value] = U0.size

@@ -86,7 +86,8 @@ struct DevScalars {
     double rnorm2;        // generic norm^2 slot
     double maxdrho;       // Newton test
     double rate;          // CFL rate
-    double pad;
+    double rate_adv;      // advective rate max |u_d| / h_d
+    double rate_rad;      // radiative rate max D / h_d^2
     double h[MUSIC_MAXV];   // first CGS pass
     double h2[MUSIC_MAXV];  // second CGS pass
     double diag[8];

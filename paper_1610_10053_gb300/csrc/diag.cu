@@ -103,6 +103,69 @@ __global__ void __launch_bounds__(BS) k_combine_rows(GridParams P, const double 
     }
 }
 
+// Per row j: the maxima over its cells and directions of (|u_d| + c_s) / h_d,
+// |u_d| / h_d and D / h_d^2 (D = chi / (rho c_v), 0 without radiative
+// diffusion); the first has k_rows' expression, so both give the same rate.
+__global__ void __launch_bounds__(BS) k_rate_rows(GridParams P, const double *U, double *rows)
+{
+    __shared__ double sh[BS / 32];
+    const int j = blockIdx.x;
+    double s[3] = {0, 0, 0};
+    const long long per_row = (long long)P.n[0] * P.n[2];
+    for (long long t = threadIdx.x; t < per_row; t += BS) {
+        int ix[3] = {(int)(t % P.n[0]), j, (int)(t / P.n[0])};
+        const long long c = cell_index(P, ix);
+        const double rho = U[c];
+        const double cs = sqrt(P.gamma * (P.gm1 * U[P.N + c]) / rho);
+        double D = 0.0;
+        if (P.conduct) {
+            const double T = P.gm1 * U[P.N + c] / rho;
+            const double t3 = T * T * T;
+            const double chi = P.chi0 * (t3 * t3 * sqrt(T)) / (rho * rho);
+            D = chi * P.gm1 / rho;
+        }
+        for (int d = 0; d < P.nd; d++) {
+            const double um = face_u(P, U, ix, c, d);
+            double up = 0.0;
+            if (!upper_wall(P, ix, d)) {
+                int jx[3] = {ix[0], ix[1], ix[2]};
+                jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
+                up = face_u(P, U, jx, cell_index(P, jx), d);
+            }
+            const double a = fabs(0.5 * (um + up));
+            if (P.geom == MUSIC_GEOM_SPHERICAL) {
+                const double h = sph_h(P, d, ix[0]);
+                s[0] = nanmax(s[0], (a + cs) / h);
+                s[1] = nanmax(s[1], a / h);
+                s[2] = nanmax(s[2], D / (h * h));
+            } else {
+                s[0] = nanmax(s[0], (a + cs) * P.idx[d]);
+                s[1] = nanmax(s[1], a * P.idx[d]);
+                s[2] = nanmax(s[2], D * P.idx2[d]);
+            }
+        }
+    }
+    for (int q = 0; q < 3; q++) {
+        const double r = block_max<BS>(s[q], sh);
+        if (threadIdx.x == 0) rows[(long long)q * P.n[1] + j] = r;
+    }
+}
+
+__global__ void __launch_bounds__(BS) k_combine_rates(GridParams P, const double *rows, DevScalars *ds)
+{
+    __shared__ double sh[BS / 32];
+    double a[3] = {0, 0, 0};
+    for (int j = threadIdx.x; j < P.n[1]; j += BS)
+        for (int q = 0; q < 3; q++) a[q] = nanmax(a[q], rows[(long long)q * P.n[1] + j]);
+    double r[3];
+    for (int q = 0; q < 3; q++) r[q] = block_max<BS>(a[q], sh);
+    if (threadIdx.x == 0) {
+        ds->rate = r[0];
+        ds->rate_adv = r[1];
+        ds->rate_rad = r[2];
+    }
+}
+
 int run_rows(music_grid *g, const double *U, double rho_L, double rho_H, int want_diag, cudaStream_t s)
 {
     const GridParams &P = g->P;
@@ -124,6 +187,49 @@ int cfl_rate(music_grid *g, const double *U, cudaStream_t s)
 int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s)
 {
     return run_rows(g, U, rho_L, rho_H, 1, s);
+}
+
+extern "C" int music_select_dt(music_grid *g, const music_dt_limits *lim, double *dt, int *which, void *stream)
+{
+    if (!g || !lim || !dt) {
+        set_error("music_select_dt: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const GridParams &P = g->P;
+    k_rate_rows<<<P.n[1], BS, 0, s>>>(P, g->U, g->diag_rows);
+    CHECK_LAUNCH();
+    k_combine_rates<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds);
+    CHECK_LAUNCH();
+    CUDA_TRY(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double rates[3] = {g->hs->rate, g->hs->rate_adv, g->hs->rate_rad};
+    const double cfl[3] = {lim->cfl_hydro, lim->cfl_adv, lim->cfl_rad};
+    double best = INFINITY;
+    int w = -1;
+    for (int k = 0; k < 3; k++) {
+        if (!std::isfinite(rates[k])) {
+            set_error("music_select_dt: non-finite rate");
+            return MUSIC_E_NONFINITE;
+        }
+        if (!(cfl[k] > 0.0) || !(rates[k] > 0.0)) continue;
+        const double t = cfl[k] / rates[k];
+        if (t < best) {
+            best = t;
+            w = k;
+        }
+    }
+    if (lim->dt_max > 0.0 && lim->dt_max < best) {
+        best = lim->dt_max;
+        w = 3;
+    }
+    if (w < 0) {
+        set_error("music_select_dt: no limit applies (all <= 0, or the state is at rest)");
+        return MUSIC_E_INVAL;
+    }
+    *dt = best;
+    if (which) *which = w;
+    return MUSIC_OK;
 }
 
 // ---------------------------------------------------------------------------

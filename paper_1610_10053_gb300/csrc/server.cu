@@ -46,7 +46,7 @@ struct Job {
     music_grid_desc desc;
     std::vector<double> U0, Ufinal;
     int n_steps = 0;
-    double cfl = 1.0, dt_max = 0.0, rho_L = 1.0, rho_H = 2.0;
+    double cfl = 1.0, dt_max = 0.0, rho_L = 1.0, rho_H = 2.0, cfl_adv = 0.0, cfl_rad = 0.0;
     size_t footprint = 0;
     bool done = false;
     bool failed = false;
@@ -90,6 +90,7 @@ bool lane_eligible(const music_server *S, const Job *j)
     const music_grid_desc &d = j->desc;
     const long long cells = (long long)d.n[0] * d.n[1] * (d.ndim == 3 ? d.n[2] : 1);
     return S->lane && d.ndim == 2 && d.geometry == MUSIC_GEOM_CARTESIAN && !d.conduct && d.nscalars == 0 &&
+           !(j->cfl_adv > 0.0) && !(j->cfl_rad > 0.0) &&
            d.precond_sweeps <= 16 && cells <= S->lane_cells;
 }
 
@@ -146,9 +147,15 @@ int run_job(Job *j, cudaStream_t s)
     for (int k = 0; rc == MUSIC_OK && k < j->n_steps; k++) {
         const auto t0 = clk::now();
         double dt = 0.0;
-        rc = music_cfl_dt(g, j->cfl, &dt, s);
-        if (rc != MUSIC_OK) break;
-        if (j->dt_max > 0.0 && dt > j->dt_max) dt = j->dt_max;
+        if (j->cfl_adv > 0.0 || j->cfl_rad > 0.0) {
+            const music_dt_limits lim = {j->cfl, j->cfl_adv, j->cfl_rad, j->dt_max};
+            rc = music_select_dt(g, &lim, &dt, nullptr, s);
+            if (rc != MUSIC_OK) break;
+        } else {
+            rc = music_cfl_dt(g, j->cfl, &dt, s);
+            if (rc != MUSIC_OK) break;
+            if (j->dt_max > 0.0 && dt > j->dt_max) dt = j->dt_max;
+        }
         music_step_stats st;
         rc = newton_solve(g, dt, &st, s);
         if (rc != MUSIC_OK) break;
@@ -395,6 +402,8 @@ int music_submit_solve(music_server *S, const music_solve_req *req, uint64_t *ti
     j->n_steps = req->n_steps;
     j->cfl = req->cfl;
     j->dt_max = req->dt_max;
+    j->cfl_adv = req->cfl_adv;
+    j->cfl_rad = req->cfl_rad;
     j->rho_L = req->rho_L;
     j->rho_H = (req->rho_H == req->rho_L) ? req->rho_L + 1.0 : req->rho_H;
     j->footprint = fp;

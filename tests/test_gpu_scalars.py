@@ -141,3 +141,26 @@ def test_server_carries_scalars():
         out = s.result_state(t)
     assert np.array_equal(out[:U.size], U)
     assert np.array_equal(out[U.size:], q)
+
+
+def test_paper_rt_settings_against_oracle():
+    """The paper's RT settings (Sec. 3): unpreconditioned JFNK at CFL 0.8 with
+    its perturbation and the marker scalars; both mixing widths per step."""
+    p = I.rt_paper(nx=20, ny=60, nsteps=4)
+    with B().Grid(p, precision=B().FP64) as g:
+        g.set_state(p.U)
+        g.set_scalars(p.q)
+        hs = []
+        for _ in range(p.nsteps):
+            g.step()
+            hs.append((g.diagnostics()["mixing_height"], g.scalar_mixing_width()))
+        U, q = g.get_state(), g.get_scalars()
+    Ur, qr, st, sg = O.run_s(p)
+    assert np.abs(U - Ur).max() <= 1e-9 * np.abs(Ur).max()
+    assert np.abs(q - qr).max() <= 1e-9 * np.abs(qr).max()
+    dr = O.diagnostics(p, Ur)
+    assert abs(hs[-1][0] - dr["mixing_height"]) <= 1e-9 * (abs(dr["mixing_height"]) + 1e-3)
+    hsr = O.scalar_mixing_width(p, Ur, qr)
+    assert abs(hs[-1][1] - hsr) <= 1e-9 * (abs(hsr) + 1e-3)
+    # the scalar width starts from the sharp interface and grows
+    assert 0.0 <= hs[0][1] <= hs[-1][1]
