@@ -333,3 +333,39 @@ def select_dt(prob, U, cfl_hydro=0.0, cfl_adv=0.0, cfl_rad=0.0, dt_max=0.0):
     dt = lib().or_select_dt(ctypes.byref(g), _p(U), float(cfl_hydro), float(cfl_adv), float(cfl_rad),
                             float(dt_max), ctypes.byref(w))
     return float(dt), w.value
+
+
+# ---------------- grid convergence of the velocity field (Sec. 4) ----------------
+def face_vy(prob, U) -> np.ndarray:
+    """Vertical velocity on the lower y-faces of a 2-D grid, (ny, nx): m_y over
+    the mean density of the two cells sharing the face (the staggered
+    velocity of Sec. 2); a walled lower face carries zero."""
+    U = _vec(U)
+    nx, ny = prob.n[0], prob.n[1]
+    N = nx * ny
+    rho = U[:N].reshape(ny, nx)
+    my = U[3 * N:4 * N].reshape(ny, nx)
+    below = np.roll(rho, 1, axis=0)
+    v = my / (0.5 * (below + rho))
+    if prob.bc[1] == 1:  # wall: the lower boundary face
+        v[0, :] = 0.0
+    return v
+
+
+def coarsen_faces(v, r) -> np.ndarray:
+    """Face-average coarsening by r of y-face values (ny, nx): a coarse y-face
+    coincides with every r-th fine y-face row and is the mean of the r fine
+    faces that tile it."""
+    ny, nx = v.shape
+    rows = v[::r, :]
+    return rows.reshape(ny // r, nx // r, r).mean(axis=2)
+
+
+def velocity_error(prob_fine, U_fine, prob_coarse, U_coarse) -> float:
+    """Relative L1 error of the coarse vertical velocity against the coarsened
+    fine one: sum |v_low - coarse(v_high)| / sum |coarse(v_high)|."""
+    r = prob_fine.n[0] // prob_coarse.n[0]
+    assert prob_fine.n[0] == r * prob_coarse.n[0] and prob_fine.n[1] == r * prob_coarse.n[1]
+    vh = coarsen_faces(face_vy(prob_fine, U_fine), r)
+    vl = face_vy(prob_coarse, U_coarse)
+    return float(np.abs(vl - vh).sum() / np.abs(vh).sum())
