@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -226,6 +227,9 @@ def run_music(args):
     dt_study = None
     if args.dt_study > 0 and rank == 0:
         dt_study = run_dt_study(args.dt_study, args.dt_study_t)
+    convergence = None
+    if args.convergence > 0 and rank == 0:
+        convergence = run_convergence(args.convergence, args.conv_t)
     serving = None
     if not args.no_serving and ws == 1:
         serving = run_serving(args.serve_solves, lane_cells=args.serve_lane_cells)
@@ -269,6 +273,7 @@ def run_music(args):
         "serving": serving,
         "series": series,
         "dt_study": dt_study,
+        "convergence": convergence,
         "final_diagnostics": final_diag,
         "sim_time": float(sum(x["dt"] for x in mixed["stats"])),
     }
@@ -473,6 +478,44 @@ def run_dt_study(n, t_end, cfls=(0.05, 10.0, 50.0)):
     return {"grid": "%d^3" % n, "t_end": t_end, "runs": out}
 
 
+def run_convergence(n_max, t_end, n_min=64):
+    """Sec. 4's grid-convergence study: the KH setup (no noise: a per-cell
+    random seed differs between grids and cannot converge) run to t_end on
+    n^2 grids, n = n_min .. n_max by doubling, each compared with the finest
+    by the relative L1 error of the vertical velocity (mixed precision)."""
+    from paper_1610_10053_gb300 import binding as B
+    from paper_1610_10053_gb300 import inputs as I
+
+    def run_to(n):
+        p = I.kelvin_helmholtz(n=n, seed=2, noise=0.0)
+        g = B.Grid(p, precision=B.MIXED)
+        g.set_state(p.U)
+        g.autotune()
+        t, steps, t0 = 0.0, 0, time.perf_counter()
+        while t < t_end * (1 - 1e-12):
+            dt = min(g.cfl_dt(p.cfl), t_end - t)
+            t += g.newton_step(dt)["dt"]
+            steps += 1
+        return g, steps, time.perf_counter() - t0
+
+    ref, steps, wall = run_to(n_max)
+    out = {"t_end": t_end, "reference": "%d^2" % n_max, "reference_steps": steps, "reference_wall_s": wall,
+           "n": [], "error": [], "steps": [], "wall_s": []}
+    n = n_min
+    while n < n_max:
+        g, steps, wall = run_to(n)
+        out["n"].append(n)
+        out["error"].append(B.velocity_error(ref, g))
+        out["steps"].append(steps)
+        out["wall_s"].append(wall)
+        g.close()
+        n *= 2
+    ref.close()
+    e = out["error"]
+    out["order"] = [math.log2(e[k] / e[k + 1]) for k in range(len(e) - 1)]
+    return out
+
+
 def cpu_baseline(prob, steps=1):
     """The FP64 CPU oracle as it stands, single-threaded, on one implicit step
     of the same workload."""
@@ -535,6 +578,9 @@ def main():
     ap.add_argument("--dt-study", type=int, default=0,
                     help="also run the Taylor-Green time-step study on this many cells per edge")
     ap.add_argument("--dt-study-t", type=float, default=2.0, help="end time of the time-step study")
+    ap.add_argument("--convergence", type=int, default=0,
+                    help="also run the KH grid-convergence study up to this many cells per edge")
+    ap.add_argument("--conv-t", type=float, default=0.5, help="end time of the convergence study")
     ap.add_argument("--serve-lane-cells", type=int, default=0,
                     help="largest solve the server's batch lane takes (<= 0: no batch lane)")
     ap.add_argument("--serve-solves", type=int, default=256)

@@ -319,6 +319,16 @@ typedef struct {
 } music_dt_limits;
 int music_select_dt(music_grid *grid, const music_dt_limits *limits, double *dt, int *which, void *stream);
 
+/*
+ * Grid-convergence measure of Sec. 4 between two 2-D grids of the same box
+ * whose extents differ by an integer factor r (fine = r x coarse): the
+ * vertical velocity on the y-faces (m_y over the mean density of the two
+ * cells), the fine one coarsened by averaging the r fine faces that tile each
+ * coarse face, and *err = sum |v_coarse - v_fine coarsened| / sum |v_fine
+ * coarsened|.  Reads both grids' states; synchronises `stream`.
+ */
+int music_velocity_error(music_grid *fine, music_grid *coarse, double *err, void *stream);
+
 /* dt = cfl / max_cells,d ((|u_d| + c_s) / dx_d) of the grid's state, with
    u_d the mean of the two face velocities of the cell (Eq. 4).
    Synchronises `stream`. */

@@ -109,6 +109,7 @@ SIGNATURES = {
                                         ctypes.POINTER(StepStats), ctypes.c_void_p]),
     "music_profile_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "music_set_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    "music_velocity_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _dbl_p, ctypes.c_void_p]),
     "music_select_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(DtLimits), _dbl_p,
                                        ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]),
     "music_get_scalars": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
@@ -234,6 +235,14 @@ def batch_step(grids, cfl=None, dt_max=None):
     if code == 1:
         check(code)
     return code, [st[i].as_dict() for i in range(n)]
+
+
+def velocity_error(fine, coarse) -> float:
+    """Relative L1 error of the coarse grid's vertical velocity against the
+    fine grid's, coarsened by face averaging (music_velocity_error)."""
+    e = ctypes.c_double()
+    check(load().music_velocity_error(fine.h, coarse.h, ctypes.byref(e), _stream()))
+    return e.value
 
 
 def footprint(prob, precision: int = FP64, **over) -> int:

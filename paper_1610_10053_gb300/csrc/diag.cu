@@ -189,6 +189,64 @@ int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cuda
     return run_rows(g, U, rho_L, rho_H, 1, s);
 }
 
+// Convergence study of Sec. 4: one thread per coarse y-face compares the
+// coarse vertical velocity with the mean of the r fine faces tiling it; the
+// sums |v_c - mean| and |mean| go through a deterministic two-stage reduction.
+__device__ inline double yface_v(const GridParams &P, const double *U, int i, int j)
+{
+    if (P.bc[1] == MUSIC_BC_WALL && j == 0) return 0.0;
+    const long long c = i + (long long)P.n[0] * j;
+    const long long b = i + (long long)P.n[0] * (j == 0 ? P.n[1] - 1 : j - 1);
+    return U[3 * P.N + c] / (0.5 * (U[b] + U[c]));
+}
+
+__global__ void __launch_bounds__(BS) k_vy_error(GridParams Pf, const double *Uf, GridParams Pc, const double *Uc,
+                                                 int r, double *partial, double *dst, unsigned int *counter)
+{
+    __shared__ double sh[BS / 32];
+    double a = 0.0, b = 0.0;
+    for (long long f = blockIdx.x * (long long)BS + threadIdx.x; f < Pc.N; f += (long long)gridDim.x * BS) {
+        const int i = (int)(f % Pc.n[0]), j = (int)(f / Pc.n[0]);
+        double m = 0.0;
+        for (int k = 0; k < r; k++) m += yface_v(Pf, Uf, i * r + k, j * r);
+        m /= (double)r;
+        a += fabs(yface_v(Pc, Uc, i, j) - m);
+        b += fabs(m);
+    }
+    const double ra = block_sum<BS>(a, sh);
+    const double rb = block_sum<BS>(b, sh);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = ra;
+        partial[gridDim.x + blockIdx.x] = rb;
+    }
+    if (last_block_done(counter)) finish_sums<BS>(partial, gridDim.x, gridDim.x, 2, dst, sh);
+}
+
+extern "C" int music_velocity_error(music_grid *fine, music_grid *coarse, double *err, void *stream)
+{
+    if (!fine || !coarse || !err) {
+        set_error("music_velocity_error: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    const GridParams &Pf = fine->P, &Pc = coarse->P;
+    const int r = Pc.n[0] > 0 ? Pf.n[0] / Pc.n[0] : 0;
+    if (Pf.nd != 2 || Pc.nd != 2 || r < 1 || Pf.n[0] != r * Pc.n[0] || Pf.n[1] != r * Pc.n[1] ||
+        Pf.bc[1] != Pc.bc[1]) {
+        set_error("music_velocity_error: 2-D grids whose extents differ by one integer factor");
+        return MUSIC_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int nb = (int)((Pc.N + BS - 1) / BS);
+    if (nb > coarse->nb) nb = coarse->nb;
+    k_vy_error<<<nb, BS, 0, s>>>(Pf, fine->U, Pc, coarse->U, r, coarse->partials, &coarse->ds->diag[6],
+                                 &coarse->ds->counters[CNT_SUMSQ]);
+    CHECK_LAUNCH();
+    CUDA_TRY(cudaMemcpyAsync(coarse->hs, coarse->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *err = coarse->hs->diag[6] / coarse->hs->diag[7];
+    return MUSIC_OK;
+}
+
 extern "C" int music_select_dt(music_grid *g, const music_dt_limits *lim, double *dt, int *which, void *stream)
 {
     if (!g || !lim || !dt) {
