@@ -99,6 +99,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value: float, ws: int, device) -> float:
+    """The largest of the ranks' values (a replica job takes its slowest
+    rank's time)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws: int, cells: int, steps: int, total_ms: float) -> float:
+    """Whole-job cell-steps/s: the cell-steps of all ranks over the slowest
+    rank's time (replicas: every rank advances its own grid)."""
+    return ws * cells * steps / (total_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -199,20 +217,16 @@ def run_music(args):
         time_steps(g, args.steps, stream, flush)
         jv_launches, jv_ms = g.profile_read()
         g.profile(False)
-        total_ms = float(np.sum(times))
-        if ws > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(float(np.sum(times)), ws, "cuda")
         result[name] = dict(total_ms=total_ms, times=times, stats=stats, launches=launches,
                             clocks=clk.summary(), grid=g, jv_launches=jv_launches, jv_ms=jv_ms,
                             tiles={"stencil": list(tune["stencil_tile"]), "precond": list(tune["precond_tile"]),
                                    "precond_stages": tune["precond_stages"]} if tune["tunable"] else None)
     mixed = result["mixed"]
-    value = ws * N * args.steps / (mixed["total_ms"] / 1e3)
+    value = job_rate(ws, N, args.steps, mixed["total_ms"])
     fp64_value = None
     if "fp64" in result:
-        fp64_value = ws * N * args.steps / (result["fp64"]["total_ms"] / 1e3)
+        fp64_value = job_rate(ws, N, args.steps, result["fp64"]["total_ms"])
 
     roof = roofline_jv(mixed, prob)
     final_diag = mixed["grid"].diagnostics()
