@@ -81,7 +81,7 @@ typedef struct {
     /* solver options (0 selects the default in brackets) */
     int gmres_restart;        /* Krylov vectors per cycle [30], 1..63 */
     int gmres_max_restarts;   /* extra cycles [10] */
-    double gmres_rtol;        /* |J d + F| <= rtol |F| [1e-2] */
+    double gmres_rtol;        /* |J d + F| <= rtol |F| [1e-1] */
     int newton_max_its;       /* [12] */
     double newton_tol;        /* converged when max |delta rho|/rho <= tol [1e-8] */
     int precond;              /* MUSIC_PC_* [ACOUSTIC]; pass -1 for NONE */

@@ -22,7 +22,7 @@ void fill_defaults(music_grid_desc &d)
 {
     if (d.gmres_restart == 0) d.gmres_restart = 30;
     if (d.gmres_max_restarts == 0) d.gmres_max_restarts = 10;
-    if (d.gmres_rtol == 0.0) d.gmres_rtol = 1e-2;
+    if (d.gmres_rtol == 0.0) d.gmres_rtol = 1e-1;
     if (d.newton_max_its == 0) d.newton_max_its = 12;
     if (d.newton_tol == 0.0) d.newton_tol = 1e-8;
     if (d.precond == 0) d.precond = MUSIC_PC_ACOUSTIC;

@@ -68,7 +68,7 @@ class Problem:
     cfl_rad: float = 0.0               # radiative CFL limit (0: none)
     restart: int = 30
     max_restarts: int = 10
-    gmres_rtol: float = 1e-2
+    gmres_rtol: float = 1e-1
     newton_max: int = 12
     newton_tol: float = 1e-8
     precond: int = PC_ACOUSTIC

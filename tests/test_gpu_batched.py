@@ -41,13 +41,19 @@ def test_batched_fp64_matches_oracle():
         same = all(stats[s][k]["gmres_its"] == sref[s]["gmres_its"] for s in range(3))
         for s in range(3):
             assert stats[s][k]["newton_its"] == sref[s]["newton_its"]
-        tol = 1e-9 if same else p.newton_tol
         U, d = out[k]
+        if not same:
+            # a GMRES stopping test flipped by rounding: compare the two roots
+            # at Newton tolerance 1e-11, where they no longer depend on the path
+            p = p.with_options(newton_tol=1e-11, newton_max=20)
+            Uref, _ = O.run(p)
+            dref = O.diagnostics(p, Uref)
+            (U, d), = run_batched([p], B().FP64, 3)[0]
         N = p.ncells
         for v in range(p.nvars):
             sl = slice(v * N, (v + 1) * N)
-            assert np.abs(U[sl] - Uref[sl]).max() <= tol * (np.abs(Uref[sl]).max() + 1e-300), (k, v, same)
-        diag_close(d, dref, tol)
+            assert np.abs(U[sl] - Uref[sl]).max() <= 1e-9 * (np.abs(Uref[sl]).max() + 1e-300), (k, v, same)
+        diag_close(d, dref, 1e-9)
 
 
 def test_batched_mixed_matches_oracle_diagnostics():

@@ -200,15 +200,27 @@ def test_implicit_steps_fp64(case, nsteps):
         same_path &= a["gmres_its"] == b["gmres_its"]
         assert _rel(a["dt"], b["dt"]) <= 1e-9
     # Same Newton/GMRES path: only rounding separates the states.  Otherwise
-    # both are converged iterates of the same Crank-Nicolson root, each within
-    # about the Newton tolerance (max |delta rho|/rho <= 1e-8) of it.
-    tol = 1e-9 if same_path else p.newton_tol
+    # (a GMRES stopping test on the edge flipped by rounding) both are
+    # converged iterates of the same Crank-Nicolson root, but the density
+    # test (max |delta rho|/rho <= 1e-8) bounds the momentum planes only to
+    # about 1/Mach times that; both sides are then re-run at Newton tolerance
+    # 1e-11, where the root no longer depends on the path, and compared at
+    # the same 1e-9.
+    if not same_path:
+        p = p.with_options(newton_tol=1e-11, newton_max=20)
+        Uref, _ = O.run(p)
+        dref = O.diagnostics(p, Uref)
+        with B().Grid(p) as g:
+            g.set_state(p.U)
+            g.run()
+            U = g.get_state()
+            d = g.diagnostics()
     N = p.ncells
     for v in range(p.nvars):
         s = slice(v * N, (v + 1) * N)
         scale = np.abs(Uref[s]).max() + 1e-300
-        assert np.abs(U[s] - Uref[s]).max() <= tol * scale, (v, same_path)
-    diag_close(d, dref, tol)
+        assert np.abs(U[s] - Uref[s]).max() <= 1e-9 * scale, (v, same_path)
+    diag_close(d, dref, 1e-9)
 
 
 def test_tgv_tight_newton_diagnostics_1e9():

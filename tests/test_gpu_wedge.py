@@ -75,18 +75,29 @@ def test_wedge_background_stays_at_rest_gpu():
     assert np.abs(U[2 * N:]).max() <= 1e-15
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_wedge_steps_against_oracle(prec):
-    p0, _ = wedge(nr=20, nth=12, noise=1e-3)
-    p = p0.with_options(nsteps=2)
+def _wedge_run(p, pr):
     Uref, sref = O.run(p)
     dref = O.diagnostics(p, Uref)
-    pr = B().FP64 if prec == "fp64" else B().MIXED
     with B().Grid(p, precision=pr) as g:
         g.set_state(p.U)
         st = g.run()
         d = g.diagnostics()
-    for a, b in zip(st, sref):
-        assert a["newton_its"] == b["newton_its"] or prec == "mixed"
+    return d, dref, st, sref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_wedge_steps_against_oracle(prec):
+    """FP64 on the oracle's Newton/GMRES path matches to 1e-9.  Where a path
+    differs (always in mixed precision) both roots are compared at Newton
+    tolerance 1e-11: the density test at 1e-8 bounds this flow's small
+    velocities only to about 1/Mach times that."""
+    p0, _ = wedge(nr=20, nth=12, noise=1e-3)
+    p = p0.with_options(nsteps=2)
+    pr = B().FP64 if prec == "fp64" else B().MIXED
+    d, dref, st, sref = _wedge_run(p, pr)
+    same = prec == "fp64" and all(a["newton_its"] == b["newton_its"] and a["gmres_its"] == b["gmres_its"]
+                                  for a, b in zip(st, sref))
+    if not same:
+        d, dref, st, sref = _wedge_run(p.with_options(newton_tol=1e-11, newton_max=20), pr)
     diag_close({"max_speed": d["max_speed"]}, {"max_speed": dref["max_speed"]},
-               1e-8 if prec == "fp64" else 1e-6)
+               1e-9 if prec == "fp64" else 1e-7)
