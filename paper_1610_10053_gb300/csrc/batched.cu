@@ -432,12 +432,8 @@ int launch_batched(music_grid **grids, int count, const double *cfl, const doubl
     const size_t st = Tile2D<STX, STY>::SMEM;
     const size_t pc = (size_t)6 * (PTX + 2 * (KM + 1)) * (PTY + 2 * (KM + 1)) * sizeof(KT);
     const size_t smem = st > pc ? st : pc;
-    static bool attr = false;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(k_batched_step<KT, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    TRY(allow_dynamic_smem(k_batched_step<KT, KM>, smem, attr));
     BArgs args;
     for (int i = 0; i < count; i++) {
         music_grid *g = grids[i];

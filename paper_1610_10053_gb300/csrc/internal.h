@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <cstdint>
 #include <string>
 
 #include "common.cuh"
@@ -118,6 +120,21 @@ void count_launch();
         int r_ = (x);               \
         if (r_ != MUSIC_OK) return r_; \
     } while (0)
+
+// Allow a kernel `smem` bytes of dynamic shared memory on the current device,
+// once per device (the attribute is per device; `done` holds one bit per
+// device and may be shared by concurrent callers).
+template <typename K>
+int allow_dynamic_smem(K kern, size_t smem, std::atomic<uint64_t> &done)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return MUSIC_OK;
+    CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    done.fetch_or(bit, std::memory_order_release);
+    return MUSIC_OK;
+}
 
 // ----- stencil.cu -----
 // Evaluate R at W = U (+ eps v in SM_JV) and write per `mode`.

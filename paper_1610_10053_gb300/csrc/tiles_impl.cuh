@@ -25,12 +25,9 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
                    double hdt, double sign, cudaStream_t s)
 {
     using TL = Tile2D<TX, TY>;
-    static bool attr = false;
+    static std::atomic<uint64_t> attr{0};
     auto kern = k_fused2d<MODE, VIN, VOUT, TX, TY>;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::SMEM));
-        attr = true;
-    }
+    TRY(allow_dynamic_smem(kern, TL::SMEM, attr));
     const GridParams &P = g->P;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
     kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps,
@@ -78,11 +75,8 @@ int launch_pc_stage(music_grid *g, double dt, const PT *r, PT *z, int K, int wan
     constexpr int H = KM + 1;
     constexpr size_t smem = (size_t)6 * (TX + 2 * H) * (TY + 2 * H) * sizeof(PT);
     auto kern = k_precond_fused2d<PT, KM, TX, TY, FIRST, LAST>;
-    static bool attr = false;
-    if (!attr) {
-        CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    TRY(allow_dynamic_smem(kern, smem, attr));
     const GridParams &P = g->P;
     const double tau = 0.5 * dt;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
