@@ -184,8 +184,10 @@ int music_residual(music_grid *grid, const double *U, const double *Un, double d
  * Crank-Nicolson Jacobian (Knoll & Keyes 2004, cited in Sec. 2).  eps <= 0
  * selects eps = sqrt(2^-52) (1 + |U|_2) / |v|_2 (computed on the device);
  * v = 0 gives Jv = 0.  U: device float64.  v, Jv: device, float64 for
- * MUSIC_FP64 grids and float32 for MUSIC_MIXED grids.  U + eps v and the
- * difference of the two residuals are formed in FP64 in both modes.  Async.
+ * MUSIC_FP64 grids and float32 for MUSIC_MIXED grids.  On MUSIC_FP64 grids
+ * U + eps v and the difference of the two residuals are formed in FP64; on
+ * MUSIC_MIXED grids the form is the grid's Jv form (music_set_jv_form).
+ * Async.
  */
 int music_jv(music_grid *grid, const double *U, const void *v, void *Jv, double dt, double eps,
              void *stream);
@@ -274,6 +276,32 @@ int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_repor
    reads the current choice. */
 int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile, int precond_stages);
 int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile, int *precond_stages);
+
+/*
+ * Form of the Jacobian-free product of a MUSIC_MIXED grid (Sec. 2; used by
+ * music_jv and by the Arnoldi products of music_newton_step).
+ *   MUSIC_JV_FD64:   R(U + eps v) and R(U) evaluated in FP64 and subtracted.
+ *   MUSIC_JV_DIFF32: the same finite difference (same eps; every upwind and
+ *                    limiter branch taken at U and at U + eps v) computed in
+ *                    difference form: each intermediate's scaled difference
+ *                    (x(U + eps v) - x(U)) / eps is carried through exact
+ *                    sum, product, quotient and limiter identities in FP32,
+ *                    and only the neighbour differences at U that decide the
+ *                    limiter are formed in FP64.  No two nearly equal
+ *                    residuals are subtracted, so FP32 rounding stays
+ *                    relative to the product itself.  The default of mixed
+ *                    grids.
+ * The difference form covers 2-D Cartesian grids without radiative
+ * diffusion on the fused stencil; other grids, and products of FP64
+ * vectors (the GMRES restart residual), use the FP64 form whatever is set.
+ * MUSIC_E_INVAL for an unknown form or MUSIC_JV_DIFF32 on a MUSIC_FP64 grid.
+ * The environment variable MUSIC_JV=fd makes new mixed grids start with
+ * MUSIC_JV_FD64.  music_get_jv_form reads the setting.
+ */
+#define MUSIC_JV_FD64 0
+#define MUSIC_JV_DIFF32 1
+int music_set_jv_form(music_grid *grid, int form);
+int music_get_jv_form(const music_grid *grid, int *form);
 
 /*
  * Passive scalars (Sec. 2.2).  A grid created with nscalars > 0 carries

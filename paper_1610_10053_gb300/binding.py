@@ -22,6 +22,7 @@ MUSIC_OK = 0
 STATUS = {0: "OK", 1: "E_INVAL", 2: "E_OOM", 3: "E_CUDA", 4: "E_NEWTON_FAIL", 5: "E_GMRES_FAIL",
           6: "E_NONFINITE", 7: "E_TIMEOUT", 8: "E_BUSY", 9: "E_NOTFOUND"}
 FP64, MIXED = 0, 1
+JV_FD64, JV_DIFF32 = 0, 1  # forms of the Jacobian-free product (music_set_jv_form)
 
 
 class MusicError(RuntimeError):
@@ -123,6 +124,8 @@ SIGNATURES = {
     "music_get_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(ctypes.c_int)]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
+    "music_set_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -411,6 +414,16 @@ class Grid:
         st = (ctypes.c_int * 2)(*stencil) if stencil is not None else None
         pt = (ctypes.c_int * 2)(*precond) if precond is not None else None
         check(load().music_set_tiles(self.h, st, pt, int(stages)))
+
+    def set_jv_form(self, form: int):
+        """JV_FD64 or JV_DIFF32 (mixed grids): the form of the Jacobian-free
+        product (music_set_jv_form)."""
+        check(load().music_set_jv_form(self.h, int(form)))
+
+    def jv_form(self) -> int:
+        f = ctypes.c_int()
+        check(load().music_get_jv_form(self.h, ctypes.byref(f)))
+        return f.value
 
     def tiles(self):
         """((stencil TX, TY), (preconditioner TX, TY), preconditioner stages)"""

@@ -220,6 +220,9 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     // MUSIC_SOLVER=host sequences Newton and GMRES from the host
     const char *so = getenv("MUSIC_SOLVER");
     g->solver_variant = (so && strcmp(so, "host") == 0) ? SOLVER_HOST : SOLVER_GRAPH;
+    // mixed grids take the difference form of Jv; MUSIC_JV=fd keeps FP64
+    const char *jv = getenv("MUSIC_JV");
+    g->jv_form = (g->mixed && !(jv && strcmp(jv, "fd") == 0)) ? JV_DIFF : JV_FD;
     g->stile = STENCIL_TILE_DEFAULT;
     g->ptile = PRECOND_TILE_DEFAULT;
     g->psplit = default_split(d.precond_sweeps);
@@ -507,6 +510,30 @@ int music_jv(music_grid *grid, const double *U, const void *v, void *Jv, double 
     }
     TRY(dev_set_eps(grid, eps > 0.0 ? eps : 0.0, s));
     return stencil_apply(grid, SM_JV, U, grid->RU, v, kd, Jv, kd, nullptr, dt, 1.0, s);
+}
+
+int music_set_jv_form(music_grid *grid, int form)
+{
+    TRY(check_grid(grid));
+    if ((form != MUSIC_JV_FD64 && form != MUSIC_JV_DIFF32) || (form == MUSIC_JV_DIFF32 && !grid->mixed)) {
+        set_error("music_set_jv_form: form %d is not available on this grid", form);
+        return MUSIC_E_INVAL;
+    }
+    const int f = (form == MUSIC_JV_DIFF32) ? JV_DIFF : JV_FD;
+    if (f != grid->jv_form) graph_release(grid);  // recorded with the other kernel
+    grid->jv_form = f;
+    tune_lookup(grid);
+    return MUSIC_OK;
+}
+
+int music_get_jv_form(const music_grid *grid, int *form)
+{
+    if (!grid || !form) {
+        set_error("music_get_jv_form: NULL argument");
+        return MUSIC_E_INVAL;
+    }
+    *form = (grid->jv_form == JV_DIFF) ? MUSIC_JV_DIFF32 : MUSIC_JV_FD64;
+    return MUSIC_OK;
 }
 
 int music_precond_apply(music_grid *grid, const double *U, double dt, const void *r, void *z, void *stream)

@@ -27,6 +27,10 @@ struct ExtScratch {
 enum StencilVariant { STENCIL_AUTO = 0, STENCIL_FUSED = 1, STENCIL_MULTIPASS = 2 };
 enum SolverVariant { SOLVER_GRAPH = 0, SOLVER_HOST = 1 };
 enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
+// Form of the Jacobian-free product: FP64 difference of two residual
+// evaluations, or the difference form with FP32 differences (mixed-precision
+// grids on the fused 2-D stencil; tile_jvdiff.cuh)
+enum JvForm { JV_FD = 0, JV_DIFF = 1 };
 
 // grids that need the general (geometry / conduction) code paths
 inline bool general_grid(const GridParams &P) { return P.geom == MUSIC_GEOM_SPHERICAL || P.conduct; }
@@ -48,6 +52,7 @@ struct music_grid {
     int solver_variant;   // SOLVER_*: device-driven graph or host-sequenced Newton/GMRES
     int stile, ptile;     // tile shapes of the fused 2-D stencil / preconditioner (indices, tiles.h)
     int psplit;           // launches the fused preconditioner's sweeps are split over (1, 2 or 4)
+    int jv_form;          // JV_*: form of the Krylov products of a mixed-precision grid
     GridParams P;
     int mixed;
     int device;

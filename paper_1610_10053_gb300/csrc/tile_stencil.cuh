@@ -23,9 +23,10 @@ __device__ inline double vanleer(double a, double b)
     return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
 }
 
-template <typename VT>
-__device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[3], double &rho,
-                          double &E)
+// (rho, E) of cell ix through the ghost mapping: periodic images, mirror
+// walls, or the hydrostatic extrapolation of Sec. 3; W loads a state entry
+template <typename LD>
+__device__ void load_cell(const GridParams &P, const LD &W, const int ix[3], double &rho, double &E)
 {
     int j[3] = {ix[0], ix[1], ix[2]};
     int hd = -1, lower = 0;
@@ -65,11 +66,15 @@ __device__ void load_cell(const GridParams &P, const WLoad<VT> &W, const int ix[
     E = __dmul_rn(rg, Tg) / P.gm1;
 }
 
-template <typename VT>
-__device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const int ix[3], int d)
+// Ghost mapping of the d-face at ix (the face between cells ix - e_d and
+// ix): false when the face lies on a wall and its velocity is zero; else
+// the stored face c, its lower neighbour cl (both interior cells) and the
+// sign of the mirrored velocity.
+__device__ inline bool face_map(const GridParams &P, const int ix[3], int d, long long &c, long long &cl,
+                                double &sgn)
 {
     int j[3] = {ix[0], ix[1], ix[2]};
-    double sgn = 1.0;
+    sgn = 1.0;
     for (int w = 0; w < P.nd; w++) {
         const int n = P.n[w];
         const int a = (P.bc[w] == MUSIC_BC_WALL) ? min(max(j[w], -MUSIC_GHOST), n - 1 + MUSIC_GHOST) : j[w];
@@ -78,18 +83,29 @@ __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const i
         if (P.bc[w] == MUSIC_BC_PERIODIC) {
             j[w] = (a % n + n) % n;
         } else if (w == d) {
-            if (a == n) return 0.0;
+            if (a == n) return false;
             j[w] = (a < 0) ? -a : 2 * n - a;
             sgn = -sgn;
         } else {
             j[w] = (a < 0) ? (-1 - a) : (2 * n - 1 - a);
         }
     }
-    if (P.bc[d] == MUSIC_BC_WALL && j[d] == 0) return 0.0;
-    const long long c = cell_index(P, j);
+    if (P.bc[d] == MUSIC_BC_WALL && j[d] == 0) return false;
+    c = cell_index(P, j);
     int l[3] = {j[0], j[1], j[2]};
     l[d] = (j[d] == 0) ? P.n[d] - 1 : j[d] - 1;
-    const long long cl = cell_index(P, l);
+    cl = cell_index(P, l);
+    return true;
+}
+
+// staggered velocity of the d-face at ix: face momentum over the mean
+// density of the two cells it joins
+template <typename VT>
+__device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const int ix[3], int d)
+{
+    long long c, cl;
+    double sgn;
+    if (!face_map(P, ix, d, c, cl, sgn)) return 0.0;
     const double rbar = 0.5 * (W(cl) + W(c));
     return sgn * (W((long long)(2 + d) * P.N + c) / rbar);
 }

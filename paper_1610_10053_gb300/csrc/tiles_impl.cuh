@@ -1,6 +1,7 @@
 // Definitions behind tiles.h; included once per tile shape by tiles_*.cu,
 // which instantiate fused2d_apply_t / precond2d_apply_t for that shape.
 #pragma once
+#include "tile_jvdiff.cuh"
 #include "tile_precond.cuh"
 #include "tile_stencil.cuh"
 #include "tiles.h"
@@ -32,6 +33,29 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
     kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps,
                                          MODE == SM_JV ? nullptr : g->fr_capture);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+// Jv in difference form (tile_jvdiff.cuh): FP32 Krylov vectors in and out
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX *TY) k_jvdiff2d(GridParams P, const double *U, const float *v, float *out,
+                                                     double hdt, const double *eps)
+{
+    extern __shared__ double sm[];
+    jvdiff2d_tile<float, float, TX, TY>(P, U, v, out, call_hdt(P, hdt), *eps, blockIdx.x, blockIdx.y, sm);
+}
+
+template <int TX, int TY>
+int launch_jvdiff2d(music_grid *g, const double *U, const float *v, float *out, double hdt, cudaStream_t s)
+{
+    using TL = JvTile<TX, TY>;
+    static std::atomic<uint64_t> attr{0};
+    auto kern = k_jvdiff2d<TX, TY>;
+    TRY(allow_dynamic_smem(kern, TL::SMEM, attr));
+    const GridParams &P = g->P;
+    dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
+    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, v, out, hdt, &g->ds->eps);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -156,6 +180,8 @@ int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux,
         if (vin_double && out_double)
             return launch_fused2d<SM_JV, double, double, TX, TY>(g, U, aux, (const double *)v, (double *)out,
                                                                  nullptr, hdt, sign, s);
+        if (!vin_double && !out_double && g->jv_form == JV_DIFF)
+            return launch_jvdiff2d<TX, TY>(g, U, (const float *)v, (float *)out, hdt, s);
         if (!vin_double && !out_double)
             return launch_fused2d<SM_JV, float, float, TX, TY>(g, U, aux, (const float *)v, (float *)out, nullptr,
                                                                hdt, sign, s);

@@ -4,7 +4,7 @@
 // the same result bitwise (tiles.h), so the choice is by speed alone: each is
 // timed with CUDA events on the grid's own state, the median of a few
 // launches taken, and the fastest kept for the grid and for every later grid
-// of the same configuration (extent, boundaries, precision, sweeps) in this
+// of the same configuration (extent, boundaries, precision, Jv form, sweeps) in this
 // process.
 #include <algorithm>
 #include <cstring>
@@ -39,7 +39,8 @@ bool fused_precond(const music_grid *g)
 
 Key key_of(const music_grid *g)
 {
-    return Key(g->P.n[0], g->P.n[1], g->P.bc[0], g->P.bc[1], g->mixed, g->desc.precond_sweeps, g->desc.precond);
+    return Key(g->P.n[0], g->P.n[1], g->P.bc[0], g->P.bc[1], g->mixed + 2 * g->jv_form, g->desc.precond_sweeps,
+               g->desc.precond);
 }
 
 constexpr int WARM = 2, REPS = 5;
