@@ -165,6 +165,10 @@ void alloc_plan(music_grid *g, F &&f)
         }
     }
     if (P.geom == MUSIC_GEOM_SPHERICAL) f((void **)&g->gface, (size_t)(P.n[0] + 1) * sizeof(double));
+    // linearisation planes of the difference-form Jv (mixed grids on the
+    // fused 2-D stencil), written with every R and F evaluation
+    if (g->mixed && P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P))
+        f((void **)&g->lin, (size_t)LIN_PLANES * N * sizeof(float));
     // the multi-pass stencil (3-D, spherical, conducting, or 2-D on request)
     // keeps its planes on the ghosted grid; the fused 2-D kernels need none
     if (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS || general_grid(P)) {

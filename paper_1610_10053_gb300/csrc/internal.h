@@ -31,6 +31,16 @@ enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
 // evaluations, or the difference form with FP32 differences (mixed-precision
 // grids on the fused 2-D stencil; tile_jvdiff.cuh)
 enum JvForm { JV_FD = 0, JV_DIFF = 1 };
+// The linearisation planes written by the fused stencil's R and F modes for
+// the difference form of Jv (tile_jvdiff.cuh): at every cell, rounded to
+// FP32, the values at U of rho, e, the lower x-face velocity u and the lower
+// y-face velocity v, and the backward differences of each to the cell's x-
+// and y-neighbour, formed in FP64 first.  Plane k holds entry k per cell.
+enum LinPlane {
+    LIN_R = 0, LIN_E, LIN_U, LIN_V,
+    LIN_DRX, LIN_DRY, LIN_DEX, LIN_DEY, LIN_DUX, LIN_DUY, LIN_DVX, LIN_DVY,
+    LIN_PLANES
+};
 
 // grids that need the general (geometry / conduction) code paths
 inline bool general_grid(const GridParams &P) { return P.geom == MUSIC_GEOM_SPHERICAL || P.conduct; }
@@ -89,6 +99,7 @@ struct music_grid {
     double *sfr;           // face mass fluxes (nd planes of N, lower faces) of the frozen fluid
     const double *srho;    // density of the frozen fluid (device, N values)
     double *fr_capture;    // when set, the stencil's non-Jv modes write their face mass fluxes here
+    float *lin;            // linearisation planes (LIN_PLANES x N) of the difference-form Jv, or null
     // optional timing of the Jacobian-free stencil launches (music_profile_*)
     int prof_on;
     int prof_pending;            // event pairs recorded, not yet harvested

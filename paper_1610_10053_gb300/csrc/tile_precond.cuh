@@ -38,6 +38,7 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 // One TX x TY tile (bx, by) of the fused preconditioner, run by a CTA of
 // TX*TY threads with 6 (TX+2H)(TY+2H) PT of shared memory at `smraw`; returns
 // the calling thread's cell's |z|^2 (thread t owns cell (t % TX, t / TX)).
+// tau = dt/2 and tau2 = tau^2 are replaced by the device dt's when P has one.
 //
 // The K Jacobi sweeps may be split over several launches (stages) with a
 // shallower halo each: a FIRST stage builds the right-hand side from r and
@@ -64,7 +65,23 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     const int n0 = P.n[0], n1 = P.n[1];
     const bool px = P.bc[0] == MUSIC_BC_PERIODIC, py = P.bc[1] == MUSIC_BC_PERIODIC;
     const PT w = (PT)MUSIC_JACOBI_OMEGA;
-    const PT ix0 = (PT)P.idx[0], ix1 = (PT)P.idx[1];
+    // grid constants and tau (from the device dt when the grid has one) in
+    // the preconditioner's type, converted once per CTA
+    __shared__ PT s_c[7];
+    if (tid == 0) {
+        call_tau(P, tau, tau2);
+        s_c[0] = (PT)P.gm1;
+        s_c[1] = (PT)P.idx[0];
+        s_c[2] = (PT)P.idx[1];
+        s_c[3] = (PT)P.idx2[0];
+        s_c[4] = (PT)P.idx2[1];
+        s_c[5] = tau;
+        s_c[6] = tau2;
+    }
+    __syncthreads();
+    const PT gm1 = s_c[0], ix0 = s_c[1], ix1 = s_c[2], i20 = s_c[3], i21 = s_c[4];
+    tau = s_c[5];
+    tau2 = s_c[6];
     for (int q = tid; q < R; q += NT) {
         const int lx = q % RX, ly = q / RX;
         bool inx, iny;
@@ -85,14 +102,13 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
             PT divm = (axp * r[2 * N + cx] - axm * r[2 * N + c]) * ix0;
             divm += (ayp * r[3 * N + cy] - aym * r[3 * N + c]) * ix1;
-            b[q] = (PT)P.gm1 * r[N + c] / C.gp[c] - tau * divm;
+            b[q] = gm1 * r[N + c] / C.gp[c] - tau * divm;
         }
     }
     __syncthreads();
     const int tx = tid % TX, ty = tid / TX;
     const int gx = bx * TX + tx, gy = by * TY + ty;
     if (FIRST && !LAST && gx < n0 && gy < n1) bg[gx + (long long)n0 * gy] = b[(ty + H) * RX + tx + H];
-    const PT i20 = (PT)P.idx2[0], i21 = (PT)P.idx2[1];
     PT *src = dA, *dst = dB;
     // the first stage's sweep k is valid on [k, R - 1 - k) (its right-hand
     // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1)
@@ -193,7 +209,10 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         z[N + c] = ze;
         z[2 * N + c] = mx_own;
         z[3 * N + c] = my_own;
-        nrm = (double)zr * zr + (double)ze * ze + (double)mx_own * mx_own + (double)my_own * my_own;
+        if constexpr (sizeof(PT) == 4)  // the cell's square sum in FP32, one conversion
+            nrm = (double)(zr * zr + ze * ze + mx_own * mx_own + my_own * my_own);
+        else
+            nrm = (double)zr * zr + (double)ze * ze + (double)mx_own * mx_own + (double)my_own * my_own;
     }
     __syncthreads();  // the tile's shared memory may be reused by the caller
     return nrm;

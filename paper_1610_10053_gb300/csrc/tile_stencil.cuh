@@ -23,13 +23,14 @@ __device__ inline double vanleer(double a, double b)
     return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
 }
 
-// (rho, E) of cell ix through the ghost mapping: periodic images, mirror
-// walls, or the hydrostatic extrapolation of Sec. 3; W loads a state entry
-template <typename LD>
-__device__ void load_cell(const GridParams &P, const LD &W, const int ix[3], double &rho, double &E)
+// Ghost mapping of cell ix (in place into j, which starts as ix): periodic
+// images and mirror walls map to an interior cell; the return value is the
+// direction of a hydrostatic wall ghost (Sec. 3), -1 if none, with `lower`
+// telling which wall.
+__device__ inline int cell_map(const GridParams &P, int j[3], int &lower)
 {
-    int j[3] = {ix[0], ix[1], ix[2]};
-    int hd = -1, lower = 0;
+    int hd = -1;
+    lower = 0;
     for (int d = 0; d < P.nd; d++) {
         const int n = P.n[d];
         // tile halos of ragged edges may lie beyond the ghost layers; their
@@ -45,6 +46,17 @@ __device__ void load_cell(const GridParams &P, const LD &W, const int ix[3], dou
             lower = (a < 0);
         }
     }
+    return hd;
+}
+
+// (rho, E) of cell ix through the ghost mapping: periodic images, mirror
+// walls, or the hydrostatic extrapolation of Sec. 3; W loads a state entry
+template <typename LD>
+__device__ void load_cell(const GridParams &P, const LD &W, const int ix[3], double &rho, double &E)
+{
+    int j[3] = {ix[0], ix[1], ix[2]};
+    int lower;
+    const int hd = cell_map(P, j, lower);
     if (hd < 0) {
         const long long c = cell_index(P, j);
         rho = W(c);
@@ -138,12 +150,13 @@ struct Tile2D {
 // One tile (bx, by) of the fused stencil, run by a CTA of TX*TY threads with
 // Tile2D<TX, TY>::SMEM bytes of shared memory at `sm`.  epsv is the finite-
 // difference step (SM_JV).  Fr_out (null: none) receives the mass fluxes of
-// the tile cells' lower x- and y-faces (2 planes of N) for passive scalars.
+// the tile cells' lower x- and y-faces (2 planes of N) for passive scalars;
+// lin (null: none; R and F modes) the linearisation planes (LinPlane).
 // Callable from any kernel that owns such a CTA.
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __device__ void fused2d_tile(const GridParams &P, const double *U, const double *aux, const VIN *v, VOUT *out,
                              double *RU_out, double hdt, double sign, double epsv, int bx, int by, double *sm,
-                             double *Fr_out = nullptr)
+                             double *Fr_out = nullptr, float *lin = nullptr)
 {
     using TL = Tile2D<TX, TY>;
     constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
@@ -298,6 +311,21 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     if (MODE != SM_JV && Fr_out) {
         Fr_out[c] = Frx[q];
         Fr_out[P.N + c] = Fry[q];
+    }
+    if (MODE != SM_JV && lin) {
+        const long long N = P.N;
+        lin[LIN_R * N + c] = (float)rho[q];
+        lin[LIN_E * N + c] = (float)ee[q];
+        lin[LIN_U * N + c] = (float)uu[q];
+        lin[LIN_V * N + c] = (float)vv[q];
+        lin[LIN_DRX * N + c] = (float)(rho[q] - rho[q - 1]);
+        lin[LIN_DRY * N + c] = (float)(rho[q] - rho[q - RX]);
+        lin[LIN_DEX * N + c] = (float)(ee[q] - ee[q - 1]);
+        lin[LIN_DEY * N + c] = (float)(ee[q] - ee[q - RX]);
+        lin[LIN_DUX * N + c] = (float)(uu[q] - uu[q - 1]);
+        lin[LIN_DUY * N + c] = (float)(uu[q] - uu[q - RX]);
+        lin[LIN_DVX * N + c] = (float)(vv[q] - vv[q - 1]);
+        lin[LIN_DVY * N + c] = (float)(vv[q] - vv[q - RX]);
     }
     const double c_jv = (MODE == SM_JV && epsv != 0.0) ? hdt / epsv : 0.0;
 #pragma unroll

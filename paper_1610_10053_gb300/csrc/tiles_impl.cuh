@@ -13,12 +13,12 @@ using namespace tile;
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
                                                     const VIN *v, VOUT *out, double *RU_out, double hdt,
-                                                    double sign, const double *eps, double *Fr_out)
+                                                    double sign, const double *eps, double *Fr_out, float *lin)
 {
     extern __shared__ double sm[];
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
     fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
-                                          blockIdx.y, sm, Fr_out);
+                                          blockIdx.y, sm, Fr_out, lin);
 }
 
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
@@ -31,19 +31,22 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
     TRY(allow_dynamic_smem(kern, TL::SMEM, attr));
     const GridParams &P = g->P;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
+    // R and F evaluations refresh the difference-form Jv's linearisation planes
+    float *lin = (MODE != SM_JV && MODE != SM_CN && g->jv_form == JV_DIFF) ? g->lin : nullptr;
     kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps,
-                                         MODE == SM_JV ? nullptr : g->fr_capture);
+                                         MODE == SM_JV ? nullptr : g->fr_capture, lin);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
-// Jv in difference form (tile_jvdiff.cuh): FP32 Krylov vectors in and out
+// Jv in difference form (tile_jvdiff.cuh): FP32 Krylov vectors in and out.
+// At least 1024 resident threads per SM (64 registers a thread).
 template <int TX, int TY>
-__global__ void __launch_bounds__(TX *TY) k_jvdiff2d(GridParams P, const double *U, const float *v, float *out,
-                                                     double hdt, const double *eps)
+__global__ void __launch_bounds__(TX *TY, (TX * TY >= 1024) ? 1 : 1024 / (TX * TY)) k_jvdiff2d(GridParams P, JvConst K, const double *U, const float *lin,
+                                                     const float *v, float *out, double hdt, const double *eps)
 {
     extern __shared__ double sm[];
-    jvdiff2d_tile<float, float, TX, TY>(P, U, v, out, call_hdt(P, hdt), *eps, blockIdx.x, blockIdx.y, sm);
+    jvdiff2d_tile<float, float, TX, TY>(P, K, U, lin, v, out, hdt, eps, blockIdx.x, blockIdx.y, sm);
 }
 
 template <int TX, int TY>
@@ -55,7 +58,8 @@ int launch_jvdiff2d(music_grid *g, const double *U, const float *v, float *out, 
     TRY(allow_dynamic_smem(kern, TL::SMEM, attr));
     const GridParams &P = g->P;
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
-    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, v, out, hdt, &g->ds->eps);
+    const JvConst K{(float)P.idx[0], (float)P.idx[1], (float)P.gm1, (float)P.g[0], (float)P.g[1]};
+    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, K, U, g->lin, v, out, hdt, &g->ds->eps);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -78,7 +82,6 @@ __global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT>
                                                              PT tau2, int K, double *partial, DevScalars *ds,
                                                              PT *bg, const PT *dpin, PT *dpout)
 {
-    call_tau(P, tau, tau2);
     extern __shared__ unsigned char smraw[];
     __shared__ double buf[TX * TY];
     const double nrm = precond2d_tile<PT, KM, TX, TY, FIRST, LAST>(P, C, r, z, tau, tau2, K, blockIdx.x,
