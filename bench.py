@@ -215,11 +215,13 @@ def run_music(args):
         # host-sequenced; the kernels are the same)
         g.profile(True)
         time_steps(g, args.steps, stream, flush)
-        jv_launches, jv_ms = g.profile_read()
+        prof = {k: g.profile_read(c) for k, c in (("jv", B.PROF_JV), ("precond", B.PROF_PRECOND),
+                                                   ("residual", B.PROF_RESIDUAL))}
         g.profile(False)
+        jv_form = ("diff" if g.jv_form() == B.JV_DIFF32 else "fd") if prec == B.MIXED else "fd"
         total_ms = max_over_ranks(float(np.sum(times)), ws, "cuda")
         result[name] = dict(total_ms=total_ms, times=times, stats=stats, launches=launches,
-                            clocks=clk.summary(), grid=g, jv_launches=jv_launches, jv_ms=jv_ms,
+                            clocks=clk.summary(), grid=g, prof=prof, jv_form=jv_form,
                             tiles={"stencil": list(tune["stencil_tile"]), "precond": list(tune["precond_tile"]),
                                    "precond_stages": tune["precond_stages"]} if tune["tunable"] else None)
     mixed = result["mixed"]
@@ -228,7 +230,8 @@ def run_music(args):
     if "fp64" in result:
         fp64_value = job_rate(ws, N, args.steps, result["fp64"]["total_ms"])
 
-    roof = roofline_jv(mixed, prob)
+    mixed["kernels"] = kernel_classes(mixed, prob)
+    roof = roofline(mixed, prob, mixed["jv_form"])
     final_diag = mixed["grid"].diagnostics()
     if prob.q is not None:
         final_diag["scalar_mixing_width"] = mixed["grid"].scalar_mixing_width()
@@ -280,6 +283,7 @@ def run_music(args):
         else None,
         "fp64_ms_per_step": float(np.mean(result["fp64"]["times"])) if "fp64" in result else None,
         "roofline": roof,
+        "kernels": mixed["kernels"],
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(mixed["launches"]),
@@ -294,53 +298,93 @@ def run_music(args):
     print(json.dumps(line))
 
 
-# Algorithmic FP64 operations of one cell of the Jacobian-free stencil in 2-D
-# (each +, -, *, / counts 1, an FMA 2): forming U + eps v 8, e and p 2, two
-# face velocities 6, eight van Leer slopes 48, mass and energy fluxes 12,
-# momentum fluxes 20, residual assembly 43, Jv = v - c (R - R_U) 12.
-JV_FLOPS_PER_CELL_2D = 151
-# Algorithmic bytes of one cell in mixed precision: U (4 x 8), R(U) (4 x 8),
-# v (4 x 4) read, Jv (4 x 4) written.
-JV_BYTES_PER_CELL_2D = 96
-# DRAM bytes per cell of one Jv-mode launch (dram__bytes_read.sum +
-# dram__bytes_write.sum over the cells of the launch) from an ncu capture of
-# the same kernel source on KH 2048^2 (state larger than L2, 32x16 tile),
-# scaled to the bench's launch by its cell count
-JV_TRAFFIC_B_PER_CELL_2D = 93.3
-# FP64 peak derived from the part's unit counts and clock: 152 SMs x 2 FP64
-# FMA per clock x 2 flops x 2.07 GHz (nominal GB300 FP64 1.25 TFLOP/s).
+# Roofline models of the step's three kernel classes on the fused 2-D grids
+# (per cell; every +, -, *, / counts 1 and an FMA 2; bytes are the
+# algorithmic reads and writes of one launch).
+#
+# Jacobian-free product, FP64 form: forming U + eps v 8, e and p 2, two face
+# velocities 6, eight van Leer slopes 48, mass and energy fluxes 12, momentum
+# fluxes 20, residual assembly 43, Jv = v - c (R - R_U) 12.
+JV_FD_FLOPS_PER_CELL_2D = 151
+JV_FD_BYTES_PER_CELL_2D = 96      # U (4 x 8), R(U) (4 x 8), v (4 x 4) read, Jv (4 x 4) written
+# Jacobian-free product, difference form (FP32): the differences of e, u, v
+# by the quotient rule 16, eight limited slopes with their differences 144,
+# upwind mass and energy fluxes 32, four momentum fluxes 44, residual
+# differences and Jv = v - dt/2 dR 45.
+JV_DIFF_FLOPS_PER_CELL_2D = 281
+JV_DIFF_BYTES_PER_CELL_2D = 80    # v (16), the 12 linearisation planes (48) read, Jv (16) written
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of one launch on
+# KH 2048^2 (state above L2 size, 32 x 16 tile), scaled to the bench's cells
+JV_DIFF_TRAFFIC_B_PER_CELL_2D = 76.6
+JV_FD_TRAFFIC_B_PER_CELL_2D = 93.3
+# Preconditioner application (FP32), K Jacobi sweeps: right-hand side 12,
+# each sweep 15, back substitution 33.
+def precond_flops_per_cell(K):
+    return 12 + 15 * K + 33
+PRECOND_BYTES_PER_CELL_2D = 52    # r (16), coefficients a_x, a_y, gamma p, gamma E, D (20) read, z (16) written
+PRECOND_TRAFFIC_B_PER_CELL_2D = 84.5  # ncu, KH 2048^2, 32 x 16 tile in two stages (both launches)
+# Residual-type evaluation (FP64): R(U) as in the product without U + eps v,
+# and the assembly sign ((U - C^n) - dt/2 R) 12.
+RES_FLOPS_PER_CELL_2D = 143
+RES_BYTES_PER_CELL_2D = 176       # U, C^n read, F and R(U) written (4 x 8 each), linearisation planes (48)
+# Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
+# FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def roofline_jv(mixed, prob):
-    """The dominant kernel is the fused stencil in its Jv mode; it is bound by
-    FP64 arithmetic (ncu: FP64 pipe ~80 % busy, DRAM ~2 %).  Its average
-    launch time comes from CUDA events around every launch (music_profile_*),
-    on the stream it is launched on, in a pass of the timed number of steps
-    right after the timed region."""
-    n, ms = mixed["jv_launches"], mixed["jv_ms"]
-    if not n:
+def kernel_classes(mixed, prob):
+    """Live per-launch times of the three profiled classes (CUDA events
+    around every launch, on its stream, in a pass of the timed number of
+    steps right after the timed region) and their share of the step."""
+    out = {}
+    step_ms = mixed["total_ms"] / max(1, len(mixed["times"]))
+    for name, (n, ms) in mixed["prof"].items():
+        if n:
+            out[name] = {"launches": n, "ms_per_launch": ms / n, "ms_per_step": ms / len(mixed["times"]),
+                         "share_of_step": ms / len(mixed["times"]) / step_ms}
+    return out
+
+
+def roofline(mixed, prob, jv_form):
+    """The roofline of the class that takes the most device time per step."""
+    ks = mixed["kernels"]
+    if not ks:
         return None
-    per = ms / n
+    name = max(ks, key=lambda k: ks[k]["ms_per_step"])
+    per = ks[name]["ms_per_launch"]
     N = prob.ncells
-    # the per-cell figures are those of the fused 2-D kernel; 3-D, spherical
-    # and conducting grids run the multi-pass stencil
     fused = prob.nd == 2 and prob.geometry == 0 and not prob.conduct
-    flops = JV_FLOPS_PER_CELL_2D * N if fused else None
-    achieved = flops / (per / 1e3) / 1e12 if flops else None
     hbm, src = peaks()
-    return {"kernel": "k_fused2d (Jacobian-free product mode)" if fused else
-            "multi-pass stencil k_load..k_assemble (Jacobian-free product mode)", "bound": "alu",
-            "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-            "traffic": JV_TRAFFIC_B_PER_CELL_2D * N if fused else None,
+    if name == "jv" and jv_form == "diff" and fused:
+        flops, peak, unit, bpc, tpc = (JV_DIFF_FLOPS_PER_CELL_2D, FP32_PEAK_TFLOPS, "FP32",
+                                       JV_DIFF_BYTES_PER_CELL_2D, JV_DIFF_TRAFFIC_B_PER_CELL_2D)
+        kern = "k_jvdiff2d (Jacobian-free product, difference form)"
+    elif name == "jv":
+        flops, peak, unit, bpc, tpc = (JV_FD_FLOPS_PER_CELL_2D, FP64_PEAK_TFLOPS, "FP64",
+                                       JV_FD_BYTES_PER_CELL_2D, JV_FD_TRAFFIC_B_PER_CELL_2D)
+        kern = "k_fused2d (Jacobian-free product mode)" if fused else "multi-pass stencil (Jacobian-free product mode)"
+    elif name == "precond":
+        flops, peak, unit, bpc, tpc = (precond_flops_per_cell(prob.sweeps), FP32_PEAK_TFLOPS, "FP32",
+                                       PRECOND_BYTES_PER_CELL_2D, PRECOND_TRAFFIC_B_PER_CELL_2D)
+        kern = "k_precond_fused2d (preconditioner application, all stages)"
+    else:
+        flops, peak, unit, bpc, tpc = RES_FLOPS_PER_CELL_2D, FP64_PEAK_TFLOPS, "FP64", RES_BYTES_PER_CELL_2D, None
+        kern = "k_fused2d (R / C^n / F modes)"
+    if not fused:
+        return {"kernel": kern, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "launches": ks[name]["launches"], "ms_per_launch": per,
+                "note": "per-cell model given for the fused 2-D kernels only"}
+    achieved = flops * N / (per / 1e3) / 1e12
+    return {"kernel": kern, "class": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": tpc * N if tpc else None,
             "traffic_note": "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells",
-            "launches": n, "ms_per_launch": per, "flops_per_cell": JV_FLOPS_PER_CELL_2D if fused else None,
+            "launches": ks[name]["launches"], "ms_per_launch": per, "flops_per_cell": flops,
             "timing": "CUDA events around each launch, same-length pass after the timed region",
-            "peak_note": "FP64 derived from unit counts and clock (152 SM x 2 DFMA/clk x 2.07 GHz)",
-            "hbm_view": {"achieved_gbs": JV_BYTES_PER_CELL_2D * N / (per / 1e3) / 1e9 if fused else None,
-                         "peak_gbs": hbm, "peak_source": src,
-                         "bytes_per_cell": JV_BYTES_PER_CELL_2D if fused else None}}
+            "peak_note": "%s peak derived from unit counts and clock (152 SM x %s x 2.07 GHz)"
+                         % (unit, "2 DFMA/clk" if unit == "FP64" else "128 FFMA/clk"),
+            "hbm_view": {"achieved_gbs": bpc * N / (per / 1e3) / 1e9, "peak_gbs": hbm, "peak_source": src,
+                         "bytes_per_cell": bpc, "frac": bpc * N / (per / 1e3) / 1e9 / hbm if hbm else None}}
 
 
 def end_to_end(grid, prob, stream, steps):

@@ -397,15 +397,27 @@ int music_cfl_rate_noalloc(const music_grid_desc *desc, const double *U, double 
 int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out, void *stream);
 
 /*
- * Timing of the Jacobian-free stencil: while enabled, every launch of the
- * stencil in its Jv mode (the dominant kernel of a step) is bracketed by CUDA
- * events on the stream it is launched on; music_profile_read returns the
- * number of such launches and their summed device time since the last
- * enable (it waits for recorded launches to finish).  Enabling resets the
- * counters.  Off by default; costs two event records per launch.
+ * Timing of the step's main kernels: while enabled, every launch of one of
+ * them is bracketed by CUDA events on the stream it is launched on, by
+ * class:
+ *   MUSIC_PROF_JV        the Jacobian-free product (Sec. 2), in either form;
+ *   MUSIC_PROF_PRECOND   one application z = M^-1 r of the preconditioner
+ *                        (all its launches);
+ *   MUSIC_PROF_RESIDUAL  the stencil's other modes: R(U), the step constant
+ *                        and the Crank-Nicolson residual F(U).
+ * music_profile_read_class returns the number of such launches of a class
+ * and their summed device time since the last enable (it waits for
+ * recorded launches to finish); music_profile_read reads MUSIC_PROF_JV.
+ * Enabling resets the counters.  Off by default; costs two event records
+ * per launch, and a profiled grid steps with the host-sequenced driver.
  */
+#define MUSIC_PROF_JV 0
+#define MUSIC_PROF_PRECOND 1
+#define MUSIC_PROF_RESIDUAL 2
+#define MUSIC_PROF_CLASSES 3
 int music_profile_enable(music_grid *grid, int on);
 int music_profile_read(music_grid *grid, uint64_t *launches, double *ms);
+int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, double *ms);
 
 #ifdef __cplusplus
 }

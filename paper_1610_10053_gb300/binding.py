@@ -23,6 +23,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_OOM", 3: "E_CUDA", 4: "E_NEWTON_FAIL", 5:
           6: "E_NONFINITE", 7: "E_TIMEOUT", 8: "E_BUSY", 9: "E_NOTFOUND"}
 FP64, MIXED = 0, 1
 JV_FD64, JV_DIFF32 = 0, 1  # forms of the Jacobian-free product (music_set_jv_form)
+PROF_JV, PROF_PRECOND, PROF_RESIDUAL = 0, 1, 2  # profiled kernel classes (music_profile_read_class)
 
 
 class MusicError(RuntimeError):
@@ -125,6 +126,8 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_int)]),
     "music_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), _dbl_p]),
     "music_set_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "music_profile_read_class": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                                _dbl_p]),
     "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
 
@@ -439,10 +442,12 @@ class Grid:
         """Time every Jv-mode stencil launch with CUDA events (see music.h)."""
         check(load().music_profile_enable(self.h, 1 if on else 0))
 
-    def profile_read(self):
+    def profile_read(self, cls: int = 0):
+        """(launches, summed ms) of a profiled kernel class: PROF_JV,
+        PROF_PRECOND or PROF_RESIDUAL (music_profile_read_class)."""
         n = ctypes.c_uint64()
         ms = ctypes.c_double()
-        check(load().music_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        check(load().music_profile_read_class(self.h, int(cls), ctypes.byref(n), ctypes.byref(ms)))
         return int(n.value), float(ms.value)
 
     def diagnostics(self, rho_L: Optional[float] = None, rho_H: Optional[float] = None) -> dict:

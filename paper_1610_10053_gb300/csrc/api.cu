@@ -602,17 +602,28 @@ int music_profile_enable(music_grid *grid, int on)
     TRY(check_grid(grid));
     if (grid->prof_pending) TRY(prof_harvest(grid, 1));
     grid->prof_on = on ? 1 : 0;
-    grid->prof_launches = 0;
-    grid->prof_ms = 0.0;
+    for (int c = 0; c < MUSIC_PROF_CLASSES; c++) {
+        grid->prof_launches[c] = 0;
+        grid->prof_ms[c] = 0.0;
+    }
     return MUSIC_OK;
 }
 
 int music_profile_read(music_grid *grid, uint64_t *launches, double *ms)
 {
+    return music_profile_read_class(grid, MUSIC_PROF_JV, launches, ms);
+}
+
+int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, double *ms)
+{
     TRY(check_grid(grid));
+    if (cls < 0 || cls >= MUSIC_PROF_CLASSES) {
+        set_error("music_profile_read_class: no class %d", cls);
+        return MUSIC_E_INVAL;
+    }
     if (grid->prof_pending) TRY(prof_harvest(grid, 1));
-    if (launches) *launches = grid->prof_launches;
-    if (ms) *ms = grid->prof_ms;
+    if (launches) *launches = grid->prof_launches[cls];
+    if (ms) *ms = grid->prof_ms[cls];
     return MUSIC_OK;
 }
 

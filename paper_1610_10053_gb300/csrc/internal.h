@@ -100,17 +100,19 @@ struct music_grid {
     const double *srho;    // density of the frozen fluid (device, N values)
     double *fr_capture;    // when set, the stencil's non-Jv modes write their face mass fluxes here
     float *lin;            // linearisation planes (LIN_PLANES x N) of the difference-form Jv, or null
-    // optional timing of the Jacobian-free stencil launches (music_profile_*)
+    // optional timing of the main kernels by class (music_profile_*)
     int prof_on;
     int prof_pending;            // event pairs recorded, not yet harvested
     cudaEvent_t prof_ev[2 * 256];
-    unsigned long long prof_launches;
-    double prof_ms;
+    int prof_cls[256];           // class (MUSIC_PROF_*) of each recorded pair
+    unsigned long long prof_launches[MUSIC_PROF_CLASSES];
+    double prof_ms[MUSIC_PROF_CLASSES];
     int prof_events_made;
 };
 
 // record the start / end of a profiled launch; harvest completed pairs
-int prof_begin(music_grid *g, cudaStream_t s);
+int prof_begin(music_grid *g, cudaStream_t s);  // the pair that follows is of class cls
+int prof_begin_cls(music_grid *g, int cls, cudaStream_t s);
 int prof_end(music_grid *g, cudaStream_t s);
 int prof_harvest(music_grid *g, int wait);
 

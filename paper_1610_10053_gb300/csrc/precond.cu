@@ -473,7 +473,21 @@ int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
     return g->mixed ? setup_t<float>(g, U, dt, s) : setup_t<double>(g, U, dt, s);
 }
 
+namespace {
+int precond_apply_body(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);
+}
+
 int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
+{
+    const bool prof = g->prof_on && g->desc.precond != MUSIC_PC_NONE && !g->in_scalar;
+    if (prof) TRY(prof_begin_cls(g, MUSIC_PROF_PRECOND, s));
+    TRY(precond_apply_body(g, dt, r, z, want_norm, s));
+    if (prof) TRY(prof_end(g, s));
+    return MUSIC_OK;
+}
+
+namespace {
+int precond_apply_body(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
     const size_t n = g->n;
     if (g->desc.precond == MUSIC_PC_NONE || g->in_scalar) {  // the scalars' solve is unpreconditioned
@@ -497,6 +511,7 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
     }
     return MUSIC_OK;
 }
+}  // namespace
 
 int precond2d_dispatch(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {

@@ -244,13 +244,16 @@ int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_do
 }
 
 // ---- timing of the Jacobian-free stencil (CUDA events on the launch stream)
-int prof_begin(music_grid *g, cudaStream_t s)
+int prof_begin(music_grid *g, cudaStream_t s) { return prof_begin_cls(g, MUSIC_PROF_JV, s); }
+
+int prof_begin_cls(music_grid *g, int cls, cudaStream_t s)
 {
     if (!g->prof_events_made) {
         for (int i = 0; i < 2 * 256; i++) CUDA_TRY(cudaEventCreate(&g->prof_ev[i]));
         g->prof_events_made = 1;
     }
     if (g->prof_pending == 256) TRY(prof_harvest(g, 1));
+    g->prof_cls[g->prof_pending] = cls;
     CUDA_TRY(cudaEventRecord(g->prof_ev[2 * g->prof_pending], s));
     return MUSIC_OK;
 }
@@ -270,8 +273,8 @@ int prof_harvest(music_grid *g, int wait)
         if (wait) CUDA_TRY(cudaEventSynchronize(g->prof_ev[2 * i + 1]));
         float ms = 0.0f;
         CUDA_TRY(cudaEventElapsedTime(&ms, g->prof_ev[2 * i], g->prof_ev[2 * i + 1]));
-        g->prof_ms += ms;
-        g->prof_launches++;
+        g->prof_ms[g->prof_cls[i]] += ms;
+        g->prof_launches[g->prof_cls[i]]++;
     }
     g->prof_pending = 0;
     return MUSIC_OK;

@@ -296,14 +296,13 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
     if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P)) {
-        const bool prof = g->prof_on && mode == SM_JV;
-        if (prof) TRY(prof_begin(g, s));
+        if (g->prof_on) TRY(prof_begin_cls(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s));
         TRY(fused2d_dispatch(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
-        if (prof) TRY(prof_end(g, s));
+        if (g->prof_on) TRY(prof_end(g, s));
         return MUSIC_OK;
     }
-    const bool prof = g->prof_on && mode == SM_JV;
-    if (prof) TRY(prof_begin(g, s));
+    const bool prof = g->prof_on;
+    if (prof) TRY(prof_begin_cls(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s));
     const int nbn = blocks_for(P.N);
     const double *eps = &g->ds->eps;
     if (mode == SM_JV) {

@@ -362,3 +362,25 @@ def test_profile_counts_jv_launches():
         g.profile(False)
     # one Jv per Arnoldi step plus one per GMRES restart
     assert n >= st[0]["gmres_its"] and ms > 0.0
+
+
+def test_profile_counts_every_class():
+    """Per class: one preconditioner application per Arnoldi step and per
+    cycle's correction; one F evaluation per Newton iteration plus the step
+    constant C^n of each attempt."""
+    p = CASES["kh_64"]().with_options(nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        g.profile(True)
+        st = g.run()[0]
+        jv = g.profile_read(B().PROF_JV)
+        pc = g.profile_read(B().PROF_PRECOND)
+        res = g.profile_read(B().PROF_RESIDUAL)
+        with pytest.raises(B().MusicError):
+            g.profile_read(3)
+        g.profile(False)
+    assert jv[0] >= st["gmres_its"] and jv[1] > 0.0
+    assert pc[0] >= st["gmres_its"] and pc[1] > 0.0
+    assert res[0] >= st["newton_its"] + 1 and res[1] > 0.0
+    if st["dt_halvings"] == 0:
+        assert res[0] == st["newton_its"] + 1
