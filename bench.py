@@ -222,7 +222,8 @@ def run_music(args):
         total_ms = max_over_ranks(float(np.sum(times)), ws, "cuda")
         result[name] = dict(total_ms=total_ms, times=times, stats=stats, launches=launches,
                             clocks=clk.summary(), grid=g, prof=prof, jv_form=jv_form,
-                            tiles={"stencil": list(tune["stencil_tile"]), "precond": list(tune["precond_tile"]),
+                            tiles={"stencil": list(tune["stencil_tile"]), "residual": list(tune["residual_tile"]),
+                                   "precond": list(tune["precond_tile"]),
                                    "precond_stages": tune["precond_stages"]} if tune["tunable"] else None)
     mixed = result["mixed"]
     value = job_rate(ws, N, args.steps, mixed["total_ms"])

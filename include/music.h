@@ -254,6 +254,9 @@ typedef struct {
     double stencil_us[8];     /* ... and their median times in microseconds (stencil:
                                  one Jacobian-free product; preconditioner: all its launches) */
     double precond_us[16];
+    int residual_tile[2];     /* chosen (TX, TY) of the stencil's R, C^n and F modes, timed as
+                                 one F evaluation on the same candidates as the stencil */
+    double residual_us[8];
 } music_tune_report;
 
 #define MUSIC_TUNE_FORCE 1u   /* time the candidates even when the configuration is cached */
@@ -270,7 +273,8 @@ typedef struct {
 int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_report *report, void *stream);
 
 /* Set the fused kernels' tile shapes to given candidates ((TX, TY) pairs;
-   NULL keeps that kernel's shape) and the preconditioner's stage count (1, 2
+   NULL keeps that kernel's shape; stencil_tile sets the stencil's Jv mode
+   and its R / C^n / F modes alike) and the preconditioner's stage count (1, 2
    or 4; <= 0 keeps it).  MUSIC_E_INVAL for a shape that is not a candidate
    or a split that leaves more than 8 sweeps per stage.  music_get_tiles
    reads the current choice. */

@@ -69,14 +69,16 @@ class TuneReport(ctypes.Structure):
                 ("precond_tile", ctypes.c_int * 2), ("precond_stages", ctypes.c_int), ("n_stencil", ctypes.c_int),
                 ("n_precond", ctypes.c_int), ("stencil_cand", (ctypes.c_int * 2) * 8),
                 ("precond_cand", (ctypes.c_int * 3) * 16), ("stencil_us", ctypes.c_double * 8),
-                ("precond_us", ctypes.c_double * 16)]
+                ("precond_us", ctypes.c_double * 16), ("residual_tile", ctypes.c_int * 2),
+                ("residual_us", ctypes.c_double * 8)]
 
     def as_dict(self):
-        """stencil_us keys: (TX, TY); precond_us keys: (TX, TY, stages)."""
+        """stencil_us and residual_us keys: (TX, TY); precond_us keys: (TX, TY, stages)."""
         return {"tunable": self.tunable, "from_cache": self.from_cache,
                 "stencil_tile": tuple(self.stencil_tile), "precond_tile": tuple(self.precond_tile),
-                "precond_stages": self.precond_stages,
+                "precond_stages": self.precond_stages, "residual_tile": tuple(self.residual_tile),
                 "stencil_us": {tuple(self.stencil_cand[i]): self.stencil_us[i] for i in range(self.n_stencil)},
+                "residual_us": {tuple(self.stencil_cand[i]): self.residual_us[i] for i in range(self.n_stencil)},
                 "precond_us": {tuple(self.precond_cand[i]): self.precond_us[i] for i in range(self.n_precond)}}
 
 

@@ -228,6 +228,7 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     const char *jv = getenv("MUSIC_JV");
     g->jv_form = (g->mixed && !(jv && strcmp(jv, "fd") == 0)) ? JV_DIFF : JV_FD;
     g->stile = STENCIL_TILE_DEFAULT;
+    g->rtile = STENCIL_TILE_DEFAULT;
     g->ptile = PRECOND_TILE_DEFAULT;
     g->psplit = default_split(d.precond_sweeps);
     tune_lookup(g);  // shapes an earlier tuning picked for this configuration

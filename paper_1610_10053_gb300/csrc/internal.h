@@ -61,6 +61,7 @@ struct music_grid {
     int pc_variant;       // PC_*: fused 2-D preconditioner kernel or one kernel per sweep
     int solver_variant;   // SOLVER_*: device-driven graph or host-sequenced Newton/GMRES
     int stile, ptile;     // tile shapes of the fused 2-D stencil / preconditioner (indices, tiles.h)
+    int rtile;            // tile shape of the stencil's R, C^n and F modes (stile: its Jv mode)
     int psplit;           // launches the fused preconditioner's sweeps are split over (1, 2 or 4)
     int jv_form;          // JV_*: form of the Krylov products of a mixed-precision grid
     GridParams P;

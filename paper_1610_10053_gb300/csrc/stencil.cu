@@ -353,7 +353,8 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
 int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux, const void *v, int vin_double,
                      void *out, int out_double, double *RU_out, double hdt, double sign, cudaStream_t s)
 {
-    switch (g->stile) {
+    const int tile = (mode == SM_JV) ? g->stile : g->rtile;
+    switch (tile) {
     case 0:
         return fused2d_apply_t<16, 8>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
     case 1:
@@ -365,6 +366,6 @@ int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux
     case 4:
         return fused2d_apply_t<32, 32>(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
     }
-    set_error("stencil: bad tile index %d", g->stile);
+    set_error("stencil: bad tile index %d", tile);
     return MUSIC_E_INVAL;
 }

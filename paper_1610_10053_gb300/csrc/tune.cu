@@ -1,5 +1,6 @@
-// Autotuner of the fused 2-D kernels' tile shapes and of the halo depth of
-// the fused preconditioner (its sweeps in 1, 2 or 4 launches).  The paper's
+// Autotuner of the fused 2-D kernels' tile shapes (the stencil's Jv mode and
+// its R / C^n / F modes separately, the preconditioner) and of the halo depth
+// of the fused preconditioner (its sweeps in 1, 2 or 4 launches).  The paper's
 // code ran on CPUs; this has no counterpart there.  Every candidate computes
 // the same result bitwise (tiles.h), so the choice is by speed alone: each is
 // timed with CUDA events on the grid's own state, the median of a few
@@ -22,9 +23,9 @@ using Key = std::tuple<int, int, int, int, int, int, int>;
 
 std::mutex g_tune_mu;
 struct Choice {
-    int stile, ptile, psplit;
+    int stile, rtile, ptile, psplit;
 };
-std::map<Key, Choice> g_tune_cache;  // -> stencil tile, preconditioner tile and stages
+std::map<Key, Choice> g_tune_cache;  // -> stencil tiles (Jv, residual), preconditioner tile and stages
 
 bool fused_grid(const music_grid *g)
 {
@@ -138,6 +139,24 @@ int tune(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
     }
     rep->n_stencil = N_STENCIL_TILES;
     g->stile = best_s;
+    // the R / C^n / F modes (FP64) on their own: F at U with R(U) standing
+    // in for C^n, into scratch (R(U) and the linearisation planes are
+    // rewritten with the same values)
+    best = 1e300;
+    int best_r = g->rtile;
+    for (int t = 0; t < N_STENCIL_TILES; t++) {
+        g->rtile = t;
+        double us = 0.0;
+        TRY(time_median(s, E.ev, [&] {
+            return stencil_apply(g, SM_F, g->U, g->RU, nullptr, 1, g->t64, 1, g->RU, dt, -1.0, s);
+        }, &us));
+        rep->residual_us[t] = us;
+        if (us < best) {
+            best = us;
+            best_r = t;
+        }
+    }
+    g->rtile = best_r;
     return MUSIC_OK;
 }
 
@@ -157,6 +176,7 @@ void tune_lookup(music_grid *g)
     auto it = g_tune_cache.find(key_of(g));
     if (it == g_tune_cache.end()) return;
     g->stile = it->second.stile;
+    g->rtile = it->second.rtile;
     g->ptile = it->second.ptile;
     g->psplit = it->second.psplit;
 }
@@ -170,13 +190,14 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
     memset(rep, 0, sizeof(*rep));
     if (!fused_grid(g)) return MUSIC_OK;  // nothing to tune
     rep->tunable = 1;
-    const int s0 = g->stile, p0 = g->ptile, q0 = g->psplit;
+    const int s0 = g->stile, r0 = g->rtile, p0 = g->ptile, q0 = g->psplit;
     bool cached = false;
     if (!(flags & MUSIC_TUNE_FORCE)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key_of(g));
         if (it != g_tune_cache.end()) {
             g->stile = it->second.stile;
+            g->rtile = it->second.rtile;
             g->ptile = it->second.ptile;
             g->psplit = it->second.psplit;
             cached = true;
@@ -186,12 +207,13 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
         const int rc = tune(g, dt, rep, (cudaStream_t)stream);
         if (rc != MUSIC_OK) {
             g->stile = s0;
+            g->rtile = r0;
             g->ptile = p0;
             g->psplit = q0;
             return rc;
         }
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key_of(g)] = Choice{g->stile, g->ptile, g->psplit};
+        g_tune_cache[key_of(g)] = Choice{g->stile, g->rtile, g->ptile, g->psplit};
     }
     rep->from_cache = cached ? 1 : 0;
     rep->stencil_tile[0] = STENCIL_TILES[g->stile].x;
@@ -199,7 +221,10 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
     rep->precond_tile[0] = PRECOND_TILES[g->ptile].x;
     rep->precond_tile[1] = PRECOND_TILES[g->ptile].y;
     rep->precond_stages = g->psplit;
-    if (g->stile != s0 || g->ptile != p0 || g->psplit != q0) graph_release(g);  // recorded with the old ones
+    rep->residual_tile[0] = STENCIL_TILES[g->rtile].x;
+    rep->residual_tile[1] = STENCIL_TILES[g->rtile].y;
+    if (g->stile != s0 || g->rtile != r0 || g->ptile != p0 || g->psplit != q0)
+        graph_release(g);  // recorded with the old ones
     return MUSIC_OK;
 }
 
@@ -219,7 +244,8 @@ extern "C" int music_set_tiles(music_grid *g, const int *stencil_tile, const int
         set_error("music_set_tiles: not a candidate tile shape or stage count");
         return MUSIC_E_INVAL;
     }
-    if (st != g->stile || pt != g->ptile || q != g->psplit) graph_release(g);
+    if (st != g->stile || (stencil_tile && st != g->rtile) || pt != g->ptile || q != g->psplit) graph_release(g);
+    if (stencil_tile) g->rtile = st;
     g->stile = st;
     g->ptile = pt;
     g->psplit = q;

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 STENCIL = [(16, 8), (16, 16), (32, 8), (32, 16), (32, 32)]
-PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16)]
+PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16), (64, 16)]
 STAGES = [1, 2, 4]
 
 
@@ -105,6 +105,8 @@ def test_autotune_picks_a_candidate_and_caches_it():
         assert all(t > 0.0 for t in rep["stencil_us"].values())
         assert all(t > 0.0 for t in rep["precond_us"].values())
         assert rep["stencil_tile"] == min(rep["stencil_us"], key=rep["stencil_us"].get)
+        assert set(rep["residual_us"]) == set(STENCIL) and all(t > 0.0 for t in rep["residual_us"].values())
+        assert rep["residual_tile"] == min(rep["residual_us"], key=rep["residual_us"].get)
         best = min(rep["precond_us"], key=rep["precond_us"].get)
         assert rep["precond_tile"] + (rep["precond_stages"],) == best
         assert g.tiles() == (rep["stencil_tile"], rep["precond_tile"], rep["precond_stages"])
