@@ -123,6 +123,7 @@ void set_error(const char *fmt, ...);
     do {                                                                                \
         cudaError_t e_ = (call);                                                        \
         if (e_ != cudaSuccess) {                                                        \
+            (void)cudaGetLastError(); /* a failed call must not resurface at a later check */ \
             set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
             return MUSIC_E_CUDA;                                                        \
         }                                                                               \

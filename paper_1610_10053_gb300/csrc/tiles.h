@@ -28,6 +28,21 @@ inline bool split_ok(int sweeps, int stages)
 }
 // the split a grid starts with: one launch when the sweeps allow it
 inline int default_split(int sweeps) { return sweeps <= 16 ? 1 : 4; }
+// Shared memory of the widest stage of a fused preconditioner application
+// (6 planes of the tile and its halo of KM + 1 cells, KM the stage's sweep
+// bound, plus the |z|^2 buffer of TX*TY doubles) against the 227 KB a CTA
+// may have: an FP64 single-stage application on 64 x 16 tiles does not fit.
+constexpr size_t PC_SMEM_LIMIT = 227 * 1024;
+inline bool pc_fits(TileShape t, int sweeps, int stages, size_t elem)
+{
+    int km;
+    if (stages <= 1 || sweeps < 2)
+        km = sweeps <= 4 ? 4 : sweeps <= 8 ? 8 : sweeps <= 12 ? 12 : 16;
+    else
+        km = (sweeps + stages - 1) / stages <= 4 ? 4 : 8;
+    const size_t h = (size_t)km + 1;
+    return 6 * (t.x + 2 * h) * (t.y + 2 * h) * elem + (size_t)t.x * t.y * sizeof(double) + 256 <= PC_SMEM_LIMIT;
+}
 
 // fused 2-D stencil of one tile shape (same contract as stencil_apply's
 // fused branch; hdt = dt / 2)

@@ -201,6 +201,10 @@ int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux,
 template <int TX, int TY>
 int precond2d_apply_t(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
+    if (!pc_fits(TileShape{TX, TY}, g->desc.precond_sweeps, g->psplit, g->mixed ? 4 : 8)) {
+        set_error("preconditioner: %dx%d tiles in %d stage(s) exceed the shared memory of a CTA", TX, TY, g->psplit);
+        return MUSIC_E_INVAL;
+    }
     if (g->mixed)
         return apply_fused2d<float, TX, TY>(g, dt, (const float *)r, (float *)z, want_norm, g->psplit, s);
     return apply_fused2d<double, TX, TY>(g, dt, (const double *)r, (double *)z, want_norm, g->psplit, s);

@@ -96,6 +96,7 @@ int tune(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
         for (int p = 0; p < N_PRECOND_TILES; p++) {
             for (int q = 0; q < N_PRECOND_SPLITS; q++) {
                 if (!split_ok(g->desc.precond_sweeps, PRECOND_SPLITS[q])) continue;
+                if (!pc_fits(PRECOND_TILES[p], g->desc.precond_sweeps, PRECOND_SPLITS[q], g->mixed ? 4 : 8)) continue;
                 g->ptile = p;
                 g->psplit = PRECOND_SPLITS[q];
                 double us = 0.0;
@@ -240,8 +241,9 @@ extern "C" int music_set_tiles(music_grid *g, const int *stencil_tile, const int
     if (precond_stages > 0) q = precond_stages;
     bool q_ok = false;
     for (int i = 0; i < N_PRECOND_SPLITS; i++) q_ok |= (PRECOND_SPLITS[i] == q);
-    if (st < 0 || pt < 0 || !q_ok || !split_ok(g->desc.precond_sweeps, q)) {
-        set_error("music_set_tiles: not a candidate tile shape or stage count");
+    if (st < 0 || pt < 0 || !q_ok || !split_ok(g->desc.precond_sweeps, q) ||
+        !pc_fits(PRECOND_TILES[pt], g->desc.precond_sweeps, q, g->mixed ? 4 : 8)) {
+        set_error("music_set_tiles: not a candidate tile shape or stage count (or too large for shared memory)");
         return MUSIC_E_INVAL;
     }
     if (st != g->stile || (stencil_tile && st != g->rtile) || pt != g->ptile || q != g->psplit) graph_release(g);

@@ -26,6 +26,17 @@ PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16), (64, 16)]
 STAGES = [1, 2, 4]
 
 
+def fits(pt, q, prec, sweeps=16):
+    """The fused preconditioner's stage fits a CTA's 227 KB of shared memory:
+    6 planes of the tile plus a halo of (sweeps per stage bound) + 1, and the
+    |z|^2 buffer (FP64 on 64 x 16 tiles needs two stages)."""
+    km = (4 if sweeps <= 4 else 8 if sweeps <= 8 else 12 if sweeps <= 12 else 16) if q == 1 else \
+        (4 if -(-sweeps // q) <= 4 else 8)
+    h = km + 1
+    es = 4 if prec == "MIXED" else 8
+    return 6 * (pt[0] + 2 * h) * (pt[1] + 2 * h) * es + pt[0] * pt[1] * 8 + 256 <= 227 * 1024
+
+
 def B():
     from paper_1610_10053_gb300 import binding
     return binding
@@ -63,6 +74,10 @@ def test_operators_identical_for_every_tile(name, prec):
     ref = None
     for pt, q in itertools.product(PRECOND, STAGES):
         with B().Grid(p, precision=getattr(B(), prec)) as g:
+            if not fits(pt, q, prec):
+                with pytest.raises(B().MusicError):
+                    g.set_tiles(precond=pt, stages=q)
+                continue
             g.set_tiles(precond=pt, stages=q)
             assert g.tiles()[1:] == (pt, q)
             z = g.precond(U, dt, v)
@@ -79,7 +94,7 @@ def test_steps_identical_for_every_tile_pair(name, prec):
     also checks that the fused reduction does not depend on the tile."""
     p = problems()[name]
     ref = None
-    for st, pt, q in [(s, t, 1) for s, t in itertools.product(STENCIL, PRECOND)] + [
+    for st, pt, q in [(s, t, 1 if fits(t, 1, prec) else 2) for s, t in itertools.product(STENCIL, PRECOND)] + [
             ((16, 8), (16, 8), 2), ((32, 16), (32, 8), 4), ((16, 16), (32, 16), 2)]:
         with B().Grid(p, precision=getattr(B(), prec)) as g:
             g.set_tiles(stencil=st, precond=pt, stages=q)
@@ -101,7 +116,8 @@ def test_autotune_picks_a_candidate_and_caches_it():
         rep = g.autotune(force=True)
         assert rep["tunable"] == 1 and rep["from_cache"] == 0
         assert set(rep["stencil_us"]) == set(STENCIL)
-        assert set(rep["precond_us"]) == {pt + (q,) for pt, q in itertools.product(PRECOND, STAGES)}
+        assert set(rep["precond_us"]) == {pt + (q,) for pt, q in itertools.product(PRECOND, STAGES)
+                                          if fits(pt, q, "MIXED")}
         assert all(t > 0.0 for t in rep["stencil_us"].values())
         assert all(t > 0.0 for t in rep["precond_us"].values())
         assert rep["stencil_tile"] == min(rep["stencil_us"], key=rep["stencil_us"].get)
@@ -153,3 +169,18 @@ def test_stage_split_must_fit_the_staged_halo():
         with pytest.raises(B().MusicError):
             g.set_tiles(stages=2)  # 10 sweeps per stage
         g.set_tiles(stages=4)
+
+
+def test_fp64_autotune_skips_what_does_not_fit_and_leaves_no_error():
+    """An FP64 grid is never tuned onto a preconditioner stage larger than a
+    CTA's shared memory, and a rejected setting leaves no CUDA error behind
+    for the next call on the thread."""
+    p = I.rayleigh_taylor(nx=24, ny=72, nsteps=1)
+    with B().Grid(p, precision=B().FP64) as g:
+        g.set_state(p.U)
+        rep = g.autotune(force=True)
+        assert (64, 16, 1) not in rep["precond_us"] and (64, 16, 2) in rep["precond_us"]
+        with pytest.raises(B().MusicError):
+            g.set_tiles(precond=(64, 16), stages=1)
+        st = g.step()
+        assert st["newton_its"] >= 1
