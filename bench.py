@@ -328,6 +328,7 @@ PRECOND_TRAFFIC_B_PER_CELL_2D = 84.5  # ncu, KH 2048^2, 32 x 16 tile in two stag
 # and the assembly sign ((U - C^n) - dt/2 R) 12.
 RES_FLOPS_PER_CELL_2D = 143
 RES_BYTES_PER_CELL_2D = 176       # U, C^n read, F and R(U) written (4 x 8 each), linearisation planes (48)
+RES_TRAFFIC_B_PER_CELL_2D = 164.2 # ncu, F mode on KH 2048^2, 32 x 16 tile
 # Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
 # FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -370,7 +371,8 @@ def roofline(mixed, prob, jv_form):
                                        PRECOND_BYTES_PER_CELL_2D, PRECOND_TRAFFIC_B_PER_CELL_2D)
         kern = "k_precond_fused2d (preconditioner application, all stages)"
     else:
-        flops, peak, unit, bpc, tpc = RES_FLOPS_PER_CELL_2D, FP64_PEAK_TFLOPS, "FP64", RES_BYTES_PER_CELL_2D, None
+        flops, peak, unit, bpc, tpc = (RES_FLOPS_PER_CELL_2D, FP64_PEAK_TFLOPS, "FP64", RES_BYTES_PER_CELL_2D,
+                                       RES_TRAFFIC_B_PER_CELL_2D)
         kern = "k_fused2d (R / C^n / F modes)"
     if not fused:
         return {"kernel": kern, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
