@@ -20,6 +20,10 @@ struct PC {
     PT *D;      // diagonal of the Helmholtz operator
 };
 
+// a * b + c with one rounding, in the preconditioner's type
+__device__ __forceinline__ float pfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double pfma(double a, double b, double c) { return fma(a, b, c); }
+
 // index into an interior row or column: periodic wrap, or clamp on walls
 // (coefficients of faces outside a walled domain are zero, which decouples
 // the clamped cells)
@@ -58,13 +62,15 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
                                  PT *dpout = nullptr)
 {
     constexpr int NT = TX * TY, H = KM + 1, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
-    PT *ax = (PT *)smraw, *ay = ax + R, *iD = ay + R, *b = iD + R, *dA = b + R, *dB = dA + R;
+    // planes: face coefficients 1/rbar (x, y), the folded sweep coefficients
+    // cw = w tau^2 / D and bw = w b / D, and the two dp buffers
+    PT *ax = (PT *)smraw, *ay = ax + R, *cwp = ay + R, *bwp = cwp + R, *dA = bwp + R, *dB = dA + R;
     const int i0 = bx * TX - H, j0 = by * TY - H;
     const int tid = threadIdx.x;
     const long long N = P.N;
     const int n0 = P.n[0], n1 = P.n[1];
     const bool px = P.bc[0] == MUSIC_BC_PERIODIC, py = P.bc[1] == MUSIC_BC_PERIODIC;
-    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    const PT w = (PT)MUSIC_JACOBI_OMEGA, omw = (PT)1 - w;
     // grid constants and tau (from the device dt when the grid has one) in
     // the preconditioner's type, converted once per CTA
     __shared__ PT s_c[7];
@@ -82,6 +88,7 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     const PT gm1 = s_c[0], ix0 = s_c[1], ix1 = s_c[2], i20 = s_c[3], i21 = s_c[4];
     tau = s_c[5];
     tau2 = s_c[6];
+    const PT wt2 = w * tau2;
     for (int q = tid; q < R; q += NT) {
         const int lx = q % RX, ly = q / RX;
         bool inx, iny;
@@ -89,9 +96,11 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         const long long c = x + (long long)n0 * y;
         ax[q] = inx ? C.a[0][c] : (PT)0;
         ay[q] = iny ? C.a[1][c] : (PT)0;
-        iD[q] = (PT)1 / C.D[c];
+        const PT iD = (PT)1 / C.D[c];
+        cwp[q] = wt2 * iD;
+        PT bq = (PT)0;
         if (!FIRST) {
-            b[q] = bg[c];
+            bq = bg[c];
             dA[q] = dpin[c];
         } else if (lx < RX - 1 && ly < RY - 1) {
             // right-hand side needs r_m on the upper faces: the next cells'
@@ -102,51 +111,62 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
             PT divm = (axp * r[2 * N + cx] - axm * r[2 * N + c]) * ix0;
             divm += (ayp * r[3 * N + cy] - aym * r[3 * N + c]) * ix1;
-            b[q] = gm1 * r[N + c] / C.gp[c] - tau * divm;
+            bq = gm1 * r[N + c] / C.gp[c] - tau * divm;
+            // a first stage that is not the last hands its tile's right-hand side on
+            if (!LAST && lx >= H && lx < H + TX && ly >= H && ly < H + TY && i0 + lx < n0 && j0 + ly < n1)
+                bg[(i0 + lx) + (long long)n0 * (j0 + ly)] = bq;
         }
+        bwp[q] = w * (bq * iD);
     }
     __syncthreads();
     const int tx = tid % TX, ty = tid / TX;
     const int gx = bx * TX + tx, gy = by * TY + ty;
-    if (FIRST && !LAST && gx < n0 && gy < n1) bg[gx + (long long)n0 * gy] = b[(ty + H) * RX + tx + H];
     PT *src = dA, *dst = dB;
+    // one Jacobi update of cell q from dp in `src`: the same operations, in
+    // the same order, in both variants below
+    auto sweep = [&](PT cxp, PT cxm, PT cyp, PT cym, PT cw, PT bw, PT cur, const PT *sp, int q) {
+        PT off = cxp * sp[q + 1];
+        off = pfma(cxm, sp[q - 1], off);
+        off = pfma(cyp, sp[q + RX], off);
+        off = pfma(cym, sp[q - RX], off);
+        return pfma(omw, cur, pfma(cw, off, bw));
+    };
     // the first stage's sweep k is valid on [k, R - 1 - k) (its right-hand
-    // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1)
+    // side needs the upper neighbour); a later stage's on [k + 1, R - k - 1):
+    // cell (lx, ly) is updated by the sweeps k <= kmax(lx, ly)
+    auto kmax_of = [&](int lx, int ly) {
+        const int e = FIRST ? 0 : 1;
+        return min(min(lx - e, RX - 2 - lx), min(ly - e, RY - 2 - ly));
+    };
     constexpr int CPT = (R + NT - 1) / NT;  // staged cells per thread
     if constexpr (CPT <= MAXCPT) {
         // each thread keeps its cells' coefficients and current dp in
         // registers across the sweeps, so a sweep reads only the four
-        // neighbours from shared memory (same arithmetic as below)
-        PT cax[CPT], cxp[CPT], cay[CPT], cyp[CPT], cb[CPT], ci[CPT], cur[CPT];
+        // neighbours from shared memory
+        PT cxp[CPT], cxm[CPT], cyp[CPT], cym[CPT], cw[CPT], bw[CPT], cur[CPT];
+        int km[CPT];
 #pragma unroll
         for (int s = 0; s < CPT; s++) {
             const int q = tid + s * NT;
             const bool in = q < R;
             const int lx = q % RX, ly = q / RX;
             const bool nx = in && lx < RX - 1, ny = in && ly < RY - 1;
-            cax[s] = in ? ax[q] : (PT)0;
-            cxp[s] = nx ? ax[q + 1] : (PT)0;
-            cay[s] = in ? ay[q] : (PT)0;
-            cyp[s] = ny ? ay[q + RX] : (PT)0;
-            cb[s] = in ? b[q] : (PT)0;
-            ci[s] = in ? iD[q] : (PT)0;
+            cxp[s] = (nx ? ax[q + 1] : (PT)0) * i20;
+            cxm[s] = (in ? ax[q] : (PT)0) * i20;
+            cyp[s] = (ny ? ay[q + RX] : (PT)0) * i21;
+            cym[s] = (in ? ay[q] : (PT)0) * i21;
+            cw[s] = in ? cwp[q] : (PT)0;
+            bw[s] = in ? bwp[q] : (PT)0;
             cur[s] = (!FIRST && in) ? src[q] : (PT)0;
+            km[s] = in ? kmax_of(lx, ly) : -1;
         }
         for (int k = 0; k < K; k++) {
-            const int lo = FIRST ? k : k + 1, hx = RX - 1 - k, hy = RY - 1 - k;
 #pragma unroll
             for (int s = 0; s < CPT; s++) {
                 const int q = tid + s * NT;
-                const int lx = q % RX, ly = q / RX;
-                if (q < R && lx >= lo && lx < hx && ly >= lo && ly < hy) {
-                    PT v;
-                    if (FIRST && k == 0) {
-                        v = w * (cb[s] * ci[s]);
-                    } else {
-                        PT off = (cxp[s] * src[q + 1] + cax[s] * src[q - 1]) * i20;
-                        off += (cyp[s] * src[q + RX] + cay[s] * src[q - RX]) * i21;
-                        v = ((PT)1 - w) * cur[s] + w * ((cb[s] + tau2 * off) * ci[s]);
-                    }
+                if (k <= km[s]) {
+                    const PT v = (FIRST && k == 0) ? bw[s] : sweep(cxp[s], cxm[s], cyp[s], cym[s], cw[s], bw[s],
+                                                                   cur[s], src, q);
                     cur[s] = v;
                     dst[q] = v;
                 }
@@ -162,13 +182,11 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             const int wdt = hx - lo, cnt = wdt * (hy - lo);
             for (int t = tid; t < cnt; t += NT) {
                 const int q = (lo + t / wdt) * RX + lo + t % wdt;
-                if (FIRST && k == 0) {
-                    dst[q] = w * (b[q] * iD[q]);
-                } else {
-                    PT off = (ax[q + 1] * src[q + 1] + ax[q] * src[q - 1]) * i20;
-                    off += (ay[q + RX] * src[q + RX] + ay[q] * src[q - RX]) * i21;
-                    dst[q] = ((PT)1 - w) * src[q] + w * ((b[q] + tau2 * off) * iD[q]);
-                }
+                if (FIRST && k == 0)
+                    dst[q] = bwp[q];
+                else
+                    dst[q] = sweep(ax[q + 1] * i20, ax[q] * i20, ay[q + RX] * i21, ay[q] * i21, cwp[q], bwp[q],
+                                   src[q], src, q);
             }
             __syncthreads();
             PT *tt = src;
