@@ -20,6 +20,15 @@ struct PC {
     PT *D;      // diagonal of the Helmholtz operator
 };
 
+// shared-memory planes of one stage of precond2d_tile: 5 when its sweeps
+// run from registers (staged cells per thread <= MAXCPT), else 6
+template <typename PT, int KM, int TX, int TY, int MAXCPT = (sizeof(PT) == 4 ? 8 : 0)>
+constexpr int pc_planes()
+{
+    constexpr int R = (TX + 2 * (KM + 1)) * (TY + 2 * (KM + 1));
+    return (R + TX * TY - 1) / (TX * TY) <= MAXCPT ? 5 : 6;
+}
+
 // a * b + c with one rounding, in the preconditioner's type
 __device__ __forceinline__ float pfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double pfma(double a, double b, double c) { return fma(a, b, c); }
@@ -40,7 +49,7 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 }
 
 // One TX x TY tile (bx, by) of the fused preconditioner, run by a CTA of
-// TX*TY threads with 6 (TX+2H)(TY+2H) PT of shared memory at `smraw`; returns
+// TX*TY threads with pc_planes() (TX+2H)(TY+2H) PT of shared memory at `smraw`; returns
 // the calling thread's cell's |z|^2 (thread t owns cell (t % TX, t / TX)).
 // tau = dt/2 and tau2 = tau^2 are replaced by the device dt's when P has one.
 //
@@ -62,9 +71,15 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
                                  PT *dpout = nullptr)
 {
     constexpr int NT = TX * TY, H = KM + 1, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
+    // staged cells per thread; with at most MAXCPT the sweeps run from registers
+    constexpr int CPT = (R + NT - 1) / NT;
+    constexpr bool REG = CPT <= MAXCPT;
     // planes: face coefficients 1/rbar (x, y), the folded sweep coefficients
-    // cw = w tau^2 / D and bw = w b / D, and the two dp buffers
-    PT *ax = (PT *)smraw, *ay = ax + R, *cwp = ay + R, *bwp = cwp + R, *dA = bwp + R, *dB = dA + R;
+    // cw = w tau^2 / D and bw = w b / D, and the two dp buffers; when the
+    // sweeps run from registers the coefficient planes are dead once loaded
+    // and the second dp buffer takes the x-face plane (pc_planes)
+    PT *ax = (PT *)smraw, *ay = ax + R, *cwp = ay + R, *bwp = cwp + R, *dA = bwp + R;
+    PT *dB = REG ? ax : dA + R;
     const int i0 = bx * TX - H, j0 = by * TY - H;
     const int tid = threadIdx.x;
     const long long N = P.N;
@@ -138,8 +153,7 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         const int e = FIRST ? 0 : 1;
         return min(min(lx - e, RX - 2 - lx), min(ly - e, RY - 2 - ly));
     };
-    constexpr int CPT = (R + NT - 1) / NT;  // staged cells per thread
-    if constexpr (CPT <= MAXCPT) {
+    if constexpr (REG) {
         // each thread keeps its cells' coefficients and current dp in
         // registers across the sweeps, so a sweep reads only the four
         // neighbours from shared memory
@@ -160,6 +174,7 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             cur[s] = (!FIRST && in) ? src[q] : (PT)0;
             km[s] = in ? kmax_of(lx, ly) : -1;
         }
+        __syncthreads();  // the first sweep writes over the x-face plane
         for (int k = 0; k < K; k++) {
 #pragma unroll
             for (int s = 0; s < CPT; s++) {
@@ -219,8 +234,22 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         const PT mxm = wlx ? (PT)0 : mx_own, mym = wly ? (PT)0 : my_own;
         PT divm = (mxp - mxm) * ix0;
         divm += (myp - mym) * ix1;
-        PT divu = (ax[q + 1] * mxp - ax[q] * mxm) * ix0;
-        divu += (ay[q + RX] * myp - ay[q] * mym) * ix1;
+        // face coefficients of the cell: from the staged planes, or (their
+        // planes reused by the sweeps) the same values from global memory
+        PT axm, axp, aym, ayp;
+        if constexpr (REG) {
+            axm = (px || gx > 0) ? C.a[0][c] : (PT)0;
+            axp = (px || gx + 1 < n0) ? C.a[0][cxp] : (PT)0;
+            aym = (py || gy > 0) ? C.a[1][c] : (PT)0;
+            ayp = (py || gy + 1 < n1) ? C.a[1][cyp] : (PT)0;
+        } else {
+            axm = ax[q];
+            axp = ax[q + 1];
+            aym = ay[q];
+            ayp = ay[q + RX];
+        }
+        PT divu = (axp * mxp - axm * mxm) * ix0;
+        divu += (ayp * myp - aym * mym) * ix1;
         const PT zr = r[c] - tau * divm;
         const PT ze = r[N + c] - tau * C.hp[c] * divu;
         z[c] = zr;

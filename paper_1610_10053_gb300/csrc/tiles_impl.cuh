@@ -100,7 +100,7 @@ int launch_pc_stage(music_grid *g, double dt, const PT *r, PT *z, int K, int wan
                     cudaStream_t s)
 {
     constexpr int H = KM + 1;
-    constexpr size_t smem = (size_t)6 * (TX + 2 * H) * (TY + 2 * H) * sizeof(PT);
+    constexpr size_t smem = (size_t)pc_planes<PT, KM, TX, TY>() * (TX + 2 * H) * (TY + 2 * H) * sizeof(PT);
     auto kern = k_precond_fused2d<PT, KM, TX, TY, FIRST, LAST>;
     static std::atomic<uint64_t> attr{0};
     TRY(allow_dynamic_smem(kern, smem, attr));
