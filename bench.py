@@ -216,7 +216,7 @@ def run_music(args):
         g.profile(True)
         time_steps(g, args.steps, stream, flush)
         prof = {k: g.profile_read(c) for k, c in (("jv", B.PROF_JV), ("precond", B.PROF_PRECOND),
-                                                   ("residual", B.PROF_RESIDUAL))}
+                                                   ("residual", B.PROF_RESIDUAL), ("vector", B.PROF_VECTOR))}
         g.profile(False)
         jv_form = ("diff" if g.jv_form() == B.JV_DIFF32 else "fd") if prec == B.MIXED else "fd"
         total_ms = max_over_ranks(float(np.sum(times)), ws, "cuda")
@@ -345,12 +345,17 @@ def kernel_classes(mixed, prob):
         if n:
             out[name] = {"launches": n, "ms_per_launch": ms / n, "ms_per_step": ms / len(mixed["times"]),
                          "share_of_step": ms / len(mixed["times"]) / step_ms}
+    # what no class covers: the recorded graph's control kernels and the gaps
+    # between dependent launches
+    rest = step_ms - sum(v["ms_per_step"] for v in out.values())
+    out["unattributed"] = {"ms_per_step": rest, "share_of_step": rest / step_ms}
     return out
 
 
 def roofline(mixed, prob, jv_form):
     """The roofline of the class that takes the most device time per step."""
-    ks = mixed["kernels"]
+    # many small kernels in "vector", none in "unattributed": no one roofline for either
+    ks = {k: v for k, v in mixed["kernels"].items() if k not in ("vector", "unattributed")}
     if not ks:
         return None
     name = max(ks, key=lambda k: ks[k]["ms_per_step"])

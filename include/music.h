@@ -408,7 +408,10 @@ int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out,
  *   MUSIC_PROF_PRECOND   one application z = M^-1 r of the preconditioner
  *                        (all its launches);
  *   MUSIC_PROF_RESIDUAL  the stencil's other modes: R(U), the step constant
- *                        and the Crank-Nicolson residual F(U).
+ *                        and the Crank-Nicolson residual F(U);
+ *   MUSIC_PROF_VECTOR    the vector, reduction and set-up kernels of GMRES
+ *                        and Newton (CGS passes, norms, the Newton update,
+ *                        the preconditioner's coefficients).
  * music_profile_read_class returns the number of such launches of a class
  * and their summed device time since the last enable (it waits for
  * recorded launches to finish); music_profile_read reads MUSIC_PROF_JV.
@@ -418,7 +421,8 @@ int music_diagnostics(music_grid *grid, double rho_L, double rho_H, double *out,
 #define MUSIC_PROF_JV 0
 #define MUSIC_PROF_PRECOND 1
 #define MUSIC_PROF_RESIDUAL 2
-#define MUSIC_PROF_CLASSES 3
+#define MUSIC_PROF_VECTOR 3
+#define MUSIC_PROF_CLASSES 4
 int music_profile_enable(music_grid *grid, int on);
 int music_profile_read(music_grid *grid, uint64_t *launches, double *ms);
 int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, double *ms);

@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_OOM", 3: "E_CUDA", 4: "E_NEWTON_FAIL", 5:
           6: "E_NONFINITE", 7: "E_TIMEOUT", 8: "E_BUSY", 9: "E_NOTFOUND"}
 FP64, MIXED = 0, 1
 JV_FD64, JV_DIFF32 = 0, 1  # forms of the Jacobian-free product (music_set_jv_form)
-PROF_JV, PROF_PRECOND, PROF_RESIDUAL = 0, 1, 2  # profiled kernel classes (music_profile_read_class)
+PROF_JV, PROF_PRECOND, PROF_RESIDUAL, PROF_VECTOR = 0, 1, 2, 3  # profiled kernel classes (music_profile_read_class)
 
 
 class MusicError(RuntimeError):
@@ -446,7 +446,7 @@ class Grid:
 
     def profile_read(self, cls: int = 0):
         """(launches, summed ms) of a profiled kernel class: PROF_JV,
-        PROF_PRECOND or PROF_RESIDUAL (music_profile_read_class)."""
+        PROF_PRECOND, PROF_RESIDUAL or PROF_VECTOR (music_profile_read_class)."""
         n = ctypes.c_uint64()
         ms = ctypes.c_double()
         check(load().music_profile_read_class(self.h, int(cls), ctypes.byref(n), ctypes.byref(ms)))

@@ -116,6 +116,21 @@ int prof_begin(music_grid *g, cudaStream_t s);  // the pair that follows is of c
 int prof_begin_cls(music_grid *g, int cls, cudaStream_t s);
 int prof_end(music_grid *g, cudaStream_t s);
 int prof_harvest(music_grid *g, int wait);
+// times the enclosing host function's launches as class cls while the grid
+// is profiled (CUDA events on s around them)
+struct ProfScope {
+    music_grid *g;
+    cudaStream_t s;
+    bool on;
+    ProfScope(music_grid *g_, int cls, cudaStream_t s_)
+        : g(g_), s(s_), on(g_->prof_on && prof_begin_cls(g_, cls, s_) == MUSIC_OK)
+    {
+    }
+    ~ProfScope()
+    {
+        if (on) prof_end(g, s);
+    }
+};
 
 // error reporting (thread local)
 void set_error(const char *fmt, ...);

@@ -491,6 +491,7 @@ int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaSt
 
 int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     unsigned int *cnt = &g->ds->counters[CNT_SUMSQ];
     if (is_double)
         k_sumsq<double><<<g->nb, BS, 0, s>>>((const double *)x, (long long)n, g->partials, dst, cnt);
@@ -509,6 +510,7 @@ int final_sum(music_grid *g, int count, double *dst, cudaStream_t s)
 
 int dev_set_eps(music_grid *g, double fixed, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     k_set_eps<<<1, 1, 0, s>>>(g->ds, fixed);
     CHECK_LAUNCH();
     return MUSIC_OK;
@@ -518,6 +520,7 @@ int dev_set_eps(music_grid *g, double fixed, cudaStream_t s)
 // read on the device and j is its upper bound.
 int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     if (j < 8) return launch_dots<8>(g, j, jdev, s);
     if (j < 16) return launch_dots<16>(g, j, jdev, s);
     if (j < 32) return launch_dots<32>(g, j, jdev, s);
@@ -527,6 +530,7 @@ int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 template <bool NORM>
 int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const double *h = NORM ? g->ds->h2 : g->ds->h;
     if (j < 8) return launch_update<8, NORM>(g, j, jdev, h, s);
     if (j < 16) return launch_update<16, NORM>(g, j, jdev, h, s);
@@ -546,6 +550,7 @@ int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s)
 
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
@@ -560,6 +565,7 @@ int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
 // V_0 = r / beta  (the division keeps the oracle's rounding)
 int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
@@ -572,6 +578,7 @@ int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
 
 int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     Coef c;
     for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (y && i < k) ? y[i] : 0.0;
     const long long n = (long long)g->n;
@@ -586,6 +593,7 @@ int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const
 
 int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
     if (g->mixed)
@@ -598,6 +606,7 @@ int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s)
 
 int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     k_sub<<<grid_blocks(n, 152 * 16), BS, 0, s>>>(a, b, out, n);
     CHECK_LAUNCH();
@@ -606,6 +615,7 @@ int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaSt
 
 int vec_neg(music_grid *g, const double *a, double *out, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     k_neg<<<grid_blocks(n, 152 * 16), BS, 0, s>>>(a, out, n);
     CHECK_LAUNCH();
@@ -629,6 +639,7 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
 
 int newton_update(music_grid *g, const int *skip, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials, &g->ds->maxdrho,
                                           &g->ds->counters[CNT_NEWTON], skip);
     CHECK_LAUNCH();

@@ -468,6 +468,7 @@ int gen_apply(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
 
 int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s)
 {
+    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     if (g->desc.precond == MUSIC_PC_NONE) return MUSIC_OK;
     if (general_grid(g->P)) return g->mixed ? gen_setup<float>(g, U, dt, s) : gen_setup<double>(g, U, dt, s);
     return g->mixed ? setup_t<float>(g, U, dt, s) : setup_t<double>(g, U, dt, s);

@@ -376,11 +376,13 @@ def test_profile_counts_every_class():
         jv = g.profile_read(B().PROF_JV)
         pc = g.profile_read(B().PROF_PRECOND)
         res = g.profile_read(B().PROF_RESIDUAL)
+        vec = g.profile_read(B().PROF_VECTOR)
         with pytest.raises(B().MusicError):
-            g.profile_read(3)
+            g.profile_read(4)
         g.profile(False)
     assert jv[0] >= st["gmres_its"] and jv[1] > 0.0
     assert pc[0] >= st["gmres_its"] and pc[1] > 0.0
     assert res[0] >= st["newton_its"] + 1 and res[1] > 0.0
+    assert vec[0] >= 3 * st["gmres_its"] and vec[1] > 0.0
     if st["dt_halvings"] == 0:
         assert res[0] == st["newton_its"] + 1
