@@ -218,9 +218,13 @@ __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double 
                                                   const SolveCtl *c, cudaGraphConditionalHandle h_arnoldi)
 {
     const double *r = c->cycle == 0 ? b : t64;
-    const double beta = c->beta;
+    // r / beta as r times 1 / beta (formed once per CTA), as the host driver does
+    __shared__ KT s_rinv;
+    if (threadIdx.x == 0) s_rinv = (KT)(1.0 / c->beta);
+    __syncthreads();
+    const KT rinv = s_rinv;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        const KT v = (KT)(r[e] / beta);
+        const KT v = (KT)r[e] * rinv;
         V[e] = v;
         q[e] = v;
     }

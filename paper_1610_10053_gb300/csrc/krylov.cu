@@ -128,18 +128,7 @@ __device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, i
                 if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
         }
     }
-    if (NORM) {
-        const double r = block_sum<BS>(acc[0], sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = r;
-    } else {
-#pragma unroll
-        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
-            if (i <= j) {
-                const double r = block_sum<BS>(acc[i], sh);
-                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
-            }
-        }
-    }
+    block_partials_mixed<NORM ? 1 : NVM>(acc, NORM ? 1 : j + 1, partial, nb);
     if (last_block_done(counter)) {
         if (NORM)
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
@@ -175,11 +164,12 @@ __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long lo
         dst[e] = (KT)((double)w[e] * inv);
 }
 
+// V_0 = r / beta as r times 1 / beta (formed once, rounded to the Krylov type)
 template <typename KT>
-__global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long long n, double inv)
+__global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long long n, KT rinv)
 {
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
-        dst[e] = (KT)(r[e] / inv);
+        dst[e] = (KT)r[e] * rinv;
 }
 
 template <typename KT>
@@ -223,7 +213,10 @@ __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
         o[e] = (D)a[e];
 }
 
-// U += x over all unknowns; partial max of |x_rho| / rho_new over cells.
+// U += x over all unknowns; partial max of |x_rho| / rho_new over cells.  On
+// mixed grids (F32) the ratio is formed in FP32: it only meets the Newton
+// tolerance, and an FP64 division per cell costs more than the update itself.
+template <bool F32>
 __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
                                                       double *partial, double *dst, unsigned int *counter,
                                                       const int *skip)
@@ -231,11 +224,20 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
     if (skip && *skip) return;  // a hard error ended the linear solve: U stays as it is
     __shared__ double sh[BS / 32];
     double m = 0.0;
+    float m32 = 0.0f;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         const double u = U[e] + x[e];
         U[e] = u;
-        if (e < N) m = nanmax(m, fabs(x[e]) / u);
+        if (e < N) {
+            if (F32) {
+                const float t = fabsf((float)x[e]) / (float)u;
+                m32 = (t > m32 || t != t) ? t : m32;  // NaN-propagating, as nanmax
+            } else {
+                m = nanmax(m, fabs(x[e]) / u);
+            }
+        }
     }
+    if (F32) m = (double)m32;
     const double r = block_max<BS>(m, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
     if (last_block_done(counter)) finish_max<BS>(partial, gridDim.x, dst, sh);
@@ -244,6 +246,33 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
 
 // ---- mixed precision: FP32 basis, FP32 arithmetic inside a 4-element chunk
 // (float4 loads), FP64 accumulation across chunks and in the reductions.
+
+// Block partials of cnt <= NVM per-thread sums: each warp adds its lanes'
+// values in FP32 (a fixed tree of five levels), then one thread per sum adds
+// the warps' results in FP64 in warp order and writes partial[i * nb + block].
+// FP64 work and barriers stay per block, not per thread and sum: FP64 runs at
+// 1/64 of the FP32 rate on this part, and a thread of these kernels holds only
+// a few chunks on the grids the step is timed on.
+template <int NVM>
+__device__ __forceinline__ void block_partials_mixed(const double *acc, int cnt, double *partial, int nb)
+{
+    __shared__ double ws[NVM][BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NVM; i++) {
+        if (i < cnt) {
+            float v = (float)acc[i];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) ws[i][wid] = (double)v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += BS) {
+        double t = 0.0;
+        for (int w = 0; w < BS / 32; w++) t += ws[i][w];
+        partial[(long long)i * nb + blockIdx.x] = t;
+    }
+}
 __device__ inline float dot4(const float4 a, const float4 b)
 {
     float s = a.x * b.x;
@@ -256,7 +285,6 @@ template <int NVM>
 __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, long long n, int j, double *partial,
                                                 int nb, double *dst, unsigned int *counter)
 {
-    __shared__ double sh[BS / 32];
     double acc[NVM];
 #pragma unroll
     for (int i = 0; i < NVM; i++) acc[i] = 0.0;
@@ -278,27 +306,22 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
         if (++k == RUN) {
 #pragma unroll
             for (int i = 0; i < NVM; i++) {
-                acc[i] += (double)run[i];
+                if (i <= j) acc[i] += (double)run[i];
                 run[i] = 0.0f;
             }
             k = 0;
         }
     }
 #pragma unroll
-    for (int i = 0; i < NVM; i++) acc[i] += (double)run[i];
+    for (int i = 0; i < NVM; i++)
+        if (i <= j) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
         const float we = w[e];
 #pragma unroll
         for (int i = 0; i < NVM; i++)
             if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
     }
-#pragma unroll
-    for (int i = 0; i < NVM; i++) {
-        if (i <= j) {
-            const double r = block_sum<BS>(acc[i], sh);
-            if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
-        }
-    }
+    block_partials_mixed<NVM>(acc, j + 1, partial, nb);
     if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
@@ -366,14 +389,15 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
         if (++k == RUN) {
 #pragma unroll
             for (int i = 0; i < (NORM ? 1 : NVM); i++) {
-                acc[i] += (double)run[i];
+                if (NORM || i <= j) acc[i] += (double)run[i];
                 run[i] = 0.0f;
             }
             k = 0;
         }
     }
 #pragma unroll
-    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] += (double)run[i];
+    for (int i = 0; i < (NORM ? 1 : NVM); i++)
+        if (NORM || i <= j) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
         float we = w[e];
 #pragma unroll
@@ -388,18 +412,7 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
                 if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
         }
     }
-    if (NORM) {
-        const double r = block_sum<BS>(acc[0], sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = r;
-    } else {
-#pragma unroll
-        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
-            if (i <= j) {
-                const double r = block_sum<BS>(acc[i], sh);
-                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
-            }
-        }
-    }
+    block_partials_mixed<NORM ? 1 : NVM>(acc, NORM ? 1 : j + 1, partial, nb);
     if (last_block_done(counter)) {
         if (NORM)
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
@@ -568,10 +581,11 @@ int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
+    const double rinv = 1.0 / beta;
     if (g->mixed)
-        k_first<float><<<nb, BS, 0, s>>>(r, (float *)g->V, n, beta);
+        k_first<float><<<nb, BS, 0, s>>>(r, (float *)g->V, n, (float)rinv);
     else
-        k_first<double><<<nb, BS, 0, s>>>(r, (double *)g->V, n, beta);
+        k_first<double><<<nb, BS, 0, s>>>(r, (double *)g->V, n, rinv);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -640,8 +654,12 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
 int newton_update(music_grid *g, const int *skip, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    k_newton_update<<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials, &g->ds->maxdrho,
-                                          &g->ds->counters[CNT_NEWTON], skip);
+    if (g->mixed)
+        k_newton_update<true><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
+                                                    &g->ds->maxdrho, &g->ds->counters[CNT_NEWTON], skip);
+    else
+        k_newton_update<false><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
+                                                     &g->ds->maxdrho, &g->ds->counters[CNT_NEWTON], skip);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

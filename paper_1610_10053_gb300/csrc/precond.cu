@@ -24,21 +24,39 @@ using namespace tile;
 
 constexpr int BS = 256;
 
+// Coefficients frozen at U.  An FP32 preconditioner (PT = float) forms them
+// from the state rounded to FP32, with FP32 arithmetic: they are stored in
+// FP32 either way, and FP64 divisions and conversions per cell run at 1/64 of
+// the FP32 rate on this part.  g1 = gamma (gamma - 1) and g2 = gamma in PT.
 template <typename PT>
-__global__ void __launch_bounds__(BS) k_coeffs(GridParams P, const double *U, PC<PT> C)
+__global__ void __launch_bounds__(BS) k_coeffs(GridParams P, const double *U, PC<PT> C, PT g1, PT g2)
 {
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
-        const double E = U[P.N + c];
-        C.gp[c] = (PT)(P.gamma * (P.gm1 * E));
-        C.hp[c] = (PT)(P.gamma * E);
-        for (int d = 0; d < P.nd; d++) {
-            if (lower_wall(P, ix, d)) {
-                C.a[d][c] = (PT)0;
-            } else {
-                const long long l = cell_nb(P, ix, d, -1);
-                C.a[d][c] = (PT)(1.0 / (0.5 * (U[l] + U[c])));
+        if constexpr (sizeof(PT) == 4) {
+            const float E = (float)U[P.N + c], rc = (float)U[c];
+            C.gp[c] = g1 * E;
+            C.hp[c] = g2 * E;
+            for (int d = 0; d < P.nd; d++) {
+                if (lower_wall(P, ix, d)) {
+                    C.a[d][c] = 0.0f;
+                } else {
+                    const long long l = cell_nb(P, ix, d, -1);
+                    C.a[d][c] = 2.0f / ((float)U[l] + rc);
+                }
+            }
+        } else {
+            const double E = U[P.N + c];
+            C.gp[c] = (PT)(P.gamma * (P.gm1 * E));
+            C.hp[c] = (PT)(P.gamma * E);
+            for (int d = 0; d < P.nd; d++) {
+                if (lower_wall(P, ix, d)) {
+                    C.a[d][c] = (PT)0;
+                } else {
+                    const long long l = cell_nb(P, ix, d, -1);
+                    C.a[d][c] = (PT)(1.0 / (0.5 * (U[l] + U[c])));
+                }
             }
         }
     }
@@ -53,13 +71,22 @@ __device__ inline PT a_up(const GridParams &P, const PC<PT> &C, const int ix[3],
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
 {
-    PT tau_unused = 0;
-    call_tau(P, tau_unused, tau2);
+    // tau^2 (from the device dt when the grid has one) and 1 / dx^2 in PT,
+    // converted once per CTA
+    __shared__ PT s_c[4];
+    if (threadIdx.x == 0) {
+        PT tau_unused = 0;
+        call_tau(P, tau_unused, tau2);
+        s_c[0] = tau2;
+        for (int d = 0; d < 3; d++) s_c[1 + d] = (PT)P.idx2[d];
+    }
+    __syncthreads();
+    tau2 = s_c[0];
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
         PT diag = 0;
-        for (int d = 0; d < P.nd; d++) diag += (a_up(P, C, ix, d) + C.a[d][c]) * (PT)P.idx2[d];
+        for (int d = 0; d < P.nd; d++) diag += (a_up(P, C, ix, d) + C.a[d][c]) * s_c[1 + d];
         C.D[c] = (PT)1 / C.gp[c] + tau2 * diag;
     }
 }
@@ -179,7 +206,7 @@ int setup_t(music_grid *g, const double *U, double dt, cudaStream_t s)
     const GridParams &P = g->P;
     PC<PT> C = pc_of<PT>(g);
     const double tau = 0.5 * dt;
-    k_coeffs<PT><<<nblocks(P.N), BS, 0, s>>>(P, U, C);
+    k_coeffs<PT><<<nblocks(P.N), BS, 0, s>>>(P, U, C, (PT)(P.gamma * P.gm1), (PT)P.gamma);
     CHECK_LAUNCH();
     k_diag<PT><<<nblocks(P.N), BS, 0, s>>>(P, C, (PT)(tau * tau));
     CHECK_LAUNCH();
