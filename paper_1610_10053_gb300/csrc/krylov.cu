@@ -128,7 +128,18 @@ __device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, i
                 if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
         }
     }
-    block_partials_mixed<NORM ? 1 : NVM>(acc, NORM ? 1 : j + 1, partial, nb);
+    if (NORM) {
+        const double r = block_sum<BS>(acc[0], sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = r;
+    } else {
+#pragma unroll
+        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+            if (i <= j) {
+                const double r = block_sum<BS>(acc[i], sh);
+                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+            }
+        }
+    }
     if (last_block_done(counter)) {
         if (NORM)
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
