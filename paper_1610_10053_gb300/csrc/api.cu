@@ -239,7 +239,7 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     if (g->ns > 0) g->solver_variant = SOLVER_HOST;
     // reduction blocks: enough to fill the GPU, fixed per grid
     long long nb = ((long long)g->n + 255) / 256;
-    g->nb = (int)(nb > 8 * 152 ? 8 * 152 : (nb < 1 ? 1 : nb));
+    g->nb = (int)(nb > 2 * 152 ? 2 * 152 : (nb < 1 ? 1 : nb));
 }
 
 void free_grid(music_grid *g)
