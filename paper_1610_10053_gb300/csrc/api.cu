@@ -603,6 +603,7 @@ int music_profile_enable(music_grid *grid, int on)
     TRY(check_grid(grid));
     if (grid->prof_pending) TRY(prof_harvest(grid, 1));
     grid->prof_on = on ? 1 : 0;
+    grid->prof_depth = 0;
     for (int c = 0; c < MUSIC_PROF_CLASSES; c++) {
         grid->prof_launches[c] = 0;
         grid->prof_ms[c] = 0.0;

@@ -106,28 +106,34 @@ struct music_grid {
     int prof_pending;            // event pairs recorded, not yet harvested
     cudaEvent_t prof_ev[2 * 256];
     int prof_cls[256];           // class (MUSIC_PROF_*) of each recorded pair
+    int prof_depth;              // open ProfScope nesting
     unsigned long long prof_launches[MUSIC_PROF_CLASSES];
     double prof_ms[MUSIC_PROF_CLASSES];
     int prof_events_made;
 };
 
 // record the start / end of a profiled launch; harvest completed pairs
-int prof_begin(music_grid *g, cudaStream_t s);  // the pair that follows is of class cls
-int prof_begin_cls(music_grid *g, int cls, cudaStream_t s);
+int prof_begin_cls(music_grid *g, int cls, cudaStream_t s);  // the pair that follows is of class cls
 int prof_end(music_grid *g, cudaStream_t s);
 int prof_harvest(music_grid *g, int wait);
-// times the enclosing host function's launches as class cls while the grid
-// is profiled (CUDA events on s around them)
+// Times the enclosing host function's launches as class cls while the grid
+// is profiled (CUDA events on s around them).  Scopes do not nest: inside an
+// open scope (say a norm inside a preconditioner application) the launches
+// count to the outer class.
 struct ProfScope {
     music_grid *g;
     cudaStream_t s;
     bool on;
-    ProfScope(music_grid *g_, int cls, cudaStream_t s_)
-        : g(g_), s(s_), on(g_->prof_on && prof_begin_cls(g_, cls, s_) == MUSIC_OK)
+    ProfScope(music_grid *g_, int cls, cudaStream_t s_) : g(g_), s(s_), on(false)
     {
+        if (!g->prof_on) return;
+        on = g->prof_depth == 0 && prof_begin_cls(g, cls, s) == MUSIC_OK;
+        g->prof_depth++;
     }
     ~ProfScope()
     {
+        if (!g->prof_on) return;
+        g->prof_depth--;
         if (on) prof_end(g, s);
     }
 };

@@ -507,11 +507,9 @@ int precond_apply_body(music_grid *g, double dt, const void *r, void *z, int wan
 
 int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
-    const bool prof = g->prof_on && g->desc.precond != MUSIC_PC_NONE && !g->in_scalar;
-    if (prof) TRY(prof_begin_cls(g, MUSIC_PROF_PRECOND, s));
-    TRY(precond_apply_body(g, dt, r, z, want_norm, s));
-    if (prof) TRY(prof_end(g, s));
-    return MUSIC_OK;
+    if (g->desc.precond == MUSIC_PC_NONE || g->in_scalar) return precond_apply_body(g, dt, r, z, want_norm, s);
+    ProfScope prof_(g, MUSIC_PROF_PRECOND, s);
+    return precond_apply_body(g, dt, r, z, want_norm, s);
 }
 
 namespace {

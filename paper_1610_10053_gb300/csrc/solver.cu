@@ -244,8 +244,6 @@ int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_do
 }
 
 // ---- timing of the Jacobian-free stencil (CUDA events on the launch stream)
-int prof_begin(music_grid *g, cudaStream_t s) { return prof_begin_cls(g, MUSIC_PROF_JV, s); }
-
 int prof_begin_cls(music_grid *g, int cls, cudaStream_t s)
 {
     if (!g->prof_events_made) {

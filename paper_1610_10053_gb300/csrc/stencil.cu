@@ -296,13 +296,10 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     const GridParams &P = g->P;
     const double hdt = 0.5 * dt;
     if (P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P)) {
-        if (g->prof_on) TRY(prof_begin_cls(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s));
-        TRY(fused2d_dispatch(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s));
-        if (g->prof_on) TRY(prof_end(g, s));
-        return MUSIC_OK;
+        ProfScope prof_(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s);
+        return fused2d_dispatch(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
     }
-    const bool prof = g->prof_on;
-    if (prof) TRY(prof_begin_cls(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s));
+    ProfScope prof_(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s);
     const int nbn = blocks_for(P.N);
     const double *eps = &g->ds->eps;
     if (mode == SM_JV) {
@@ -346,7 +343,6 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
         return MUSIC_E_INVAL;
     }
     CHECK_LAUNCH();
-    if (prof) TRY(prof_end(g, s));
     return MUSIC_OK;
 }
 
