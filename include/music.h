@@ -295,9 +295,10 @@ int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile
  *                    residuals are subtracted, so FP32 rounding stays
  *                    relative to the product itself.  The default of mixed
  *                    grids.
- * The difference form covers 2-D Cartesian grids without radiative
- * diffusion on the fused stencil; other grids, and products of FP64
- * vectors (the GMRES restart residual), use the FP64 form whatever is set.
+ * The difference form covers Cartesian grids without radiative diffusion
+ * (2-D on the fused stencil, 3-D and 2-D on the multi-pass stencil);
+ * spherical and conducting grids, and products of FP64 vectors (the GMRES
+ * restart residual), use the FP64 form whatever is set.
  * MUSIC_E_INVAL for an unknown form or MUSIC_JV_DIFF32 on a MUSIC_FP64 grid.
  * The environment variable MUSIC_JV=fd makes new mixed grids start with
  * MUSIC_JV_FD64.  music_get_jv_form reads the setting.

@@ -169,6 +169,9 @@ void alloc_plan(music_grid *g, F &&f)
     // fused 2-D stencil), written with every R and F evaluation
     if (g->mixed && P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P))
         f((void **)&g->lin, (size_t)LIN_PLANES * N * sizeof(float));
+    // and on the ghosted grid for the multi-pass stencil's (3-D, or 2-D on request)
+    if (g->mixed && (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS) && !general_grid(P))
+        f((void **)&g->linx, (size_t)(2 + 4 * P.nd + P.nd * P.nd) * M * sizeof(float));
     // the multi-pass stencil (3-D, spherical, conducting, or 2-D on request)
     // keeps its planes on the ghosted grid; the fused 2-D kernels need none
     if (P.nd == 3 || g->stencil_variant == STENCIL_MULTIPASS || general_grid(P)) {

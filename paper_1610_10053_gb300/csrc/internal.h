@@ -101,6 +101,7 @@ struct music_grid {
     const double *srho;    // density of the frozen fluid (device, N values)
     double *fr_capture;    // when set, the stencil's non-Jv modes write their face mass fluxes here
     float *lin;            // linearisation planes (LIN_PLANES x N) of the difference-form Jv, or null
+    float *linx;           // the same on the ghosted grid for the multi-pass stencil ((2+4nd+nd^2) x M), or null
     // optional timing of the main kernels by class (music_profile_*)
     int prof_on;
     int prof_pending;            // event pairs recorded, not yet harvested
@@ -116,6 +117,11 @@ struct music_grid {
 int prof_begin_cls(music_grid *g, int cls, cudaStream_t s);  // the pair that follows is of class cls
 int prof_end(music_grid *g, cudaStream_t s);
 int prof_harvest(music_grid *g, int wait);
+// difference-form Jv on the multi-pass stencil (jvdiff_multipass.cu): the
+// linearisation arrays from the FP64 planes of the R / F evaluation just run
+// at U, and the product of an FP32 direction
+int lin_ext_write(music_grid *g, const double *U, cudaStream_t s);
+int jvdiff_multipass(music_grid *g, const double *U, const float *v, float *out, double hdt, cudaStream_t s);
 // Times the enclosing host function's launches as class cls while the grid
 // is profiled (CUDA events on s around them).  Scopes do not nest: inside an
 // open scope (say a norm inside a preconditioner application) the launches

@@ -300,6 +300,9 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
         return fused2d_dispatch(g, mode, U, aux, v, vin_double, out, out_double, RU_out, hdt, sign, s);
     }
     ProfScope prof_(g, mode == SM_JV ? MUSIC_PROF_JV : MUSIC_PROF_RESIDUAL, s);
+    const bool diff = g->linx && g->jv_form == JV_DIFF;
+    if (mode == SM_JV && diff && !vin_double && !out_double)
+        return jvdiff_multipass(g, U, (const float *)v, (float *)out, hdt, s);
     const int nbn = blocks_for(P.N);
     const double *eps = &g->ds->eps;
     if (mode == SM_JV) {
@@ -310,6 +313,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     } else {
         TRY(run_passes<double>(g, U, nullptr, s));
         if (g->fr_capture) TRY(capture_ext_fluxes(g, s));  // face mass fluxes for passive scalars
+        if (diff && (mode == SM_R || mode == SM_F)) TRY(lin_ext_write(g, U, s));
     }
     switch (mode) {
     case SM_R:

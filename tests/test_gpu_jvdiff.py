@@ -151,3 +151,57 @@ def test_steps_in_either_form_reach_the_same_solution(case):
     Ur, _ = O.run(p)
     for U in res:
         assert np.abs(U - Ur).max() <= 1e-9 * np.abs(Ur).max()
+
+
+# ---- the multi-pass path: 3-D grids, and 2-D grids on the multi-pass stencil
+CASES3 = {
+    "periodic3d_ragged": PARITY["periodic3d_ragged"],
+    "tgv_16": PARITY["tgv_16"],
+    "walls_hse3d": lambda: I.random_smooth(3, (10, 9, 8), seed=25, amp=0.3,
+                                           bc=(I.BC_PERIODIC, I.BC_WALL, I.BC_PERIODIC),
+                                           wall_scalar=(0, I.WALL_HSE, 0), g=(0.0, -0.4, 0.0)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES3))
+@pytest.mark.parametrize("which_eps", ["fixed", "default"])
+def test_multipass_difference_form_3d_against_oracle(case, which_eps):
+    p = CASES3[case]()
+    rng = np.random.default_rng(35)
+    v = rng.standard_normal(p.U.size).astype(np.float32).astype(np.float64)
+    dt = O.cfl_dt(p, p.U, 5.0)
+    eps = O.fd_eps(p.U, v) if which_eps == "default" else 1e-7 * np.linalg.norm(p.U) / np.linalg.norm(v)
+    Jv = gpu_jv(p, v.astype(np.float32), dt, eps if which_eps == "fixed" else 0.0, B().JV_DIFF32)
+    ref = O.jv(p, p.U, v, dt, eps)
+    compare(p, dR_planes(p, v, Jv, dt), dR_planes(p, v, ref, dt))
+
+
+@pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "rt_32x96"])
+def test_multipass_difference_form_2d_matches_fused(case, monkeypatch):
+    """2-D grids on the multi-pass stencil (MUSIC_STENCIL=multipass) against
+    the oracle, and against the fused kernel's difference form."""
+    p = CASES[case]()
+    rng = np.random.default_rng(36)
+    v = rng.standard_normal(p.U.size).astype(np.float32)
+    dt = O.cfl_dt(p, p.U, 5.0)
+    fused = gpu_jv(p, v, dt, 0.0, B().JV_DIFF32)
+    monkeypatch.setenv("MUSIC_STENCIL", "multipass")
+    multi = gpu_jv(p, v, dt, 0.0, B().JV_DIFF32)
+    v64 = v.astype(np.float64)
+    ref = O.jv(p, p.U, v64, dt)
+    compare(p, dR_planes(p, v64, multi, dt), dR_planes(p, v64, ref, dt))
+    compare(p, dR_planes(p, v64, multi, dt), dR_planes(p, v64, fused, dt))
+
+
+def test_3d_steps_in_either_form_reach_the_same_solution():
+    p = CASES3["tgv_16"]().with_options(newton_tol=1e-11, nsteps=2)
+    res = []
+    for form in (B().JV_DIFF32, B().JV_FD64):
+        with B().Grid(p, precision=B().MIXED) as g:
+            g.set_jv_form(form)
+            g.set_state(p.U)
+            g.run()
+            res.append(g.get_state())
+    Ur, _ = O.run(p)
+    for U in res:
+        assert np.abs(U - Ur).max() <= 1e-9 * np.abs(Ur).max()
