@@ -128,8 +128,18 @@ __host__ __device__ inline long long ext_index(const GridParams &P, int i, int j
            P.es[2] * (k + (P.nd == 3 ? MUSIC_GHOST : 0));
 }
 
+// (64-bit integer division is emulated in software on the GPU: grids whose
+// index fits 32 bits, all in practice, decompose it in 32-bit arithmetic)
 __device__ inline void ext_coords(const GridParams &P, long long x, int ix[3])
 {
+    if (P.M <= 0x7fffffffLL) {
+        const unsigned u = (unsigned)x, n0 = (unsigned)P.ne[0], n1 = (unsigned)P.ne[1];
+        const unsigned q = u / n0;
+        ix[0] = (int)(u - q * n0) - MUSIC_GHOST;
+        ix[1] = (int)(q % n1) - MUSIC_GHOST;
+        ix[2] = (int)(q / n1) - (P.nd == 3 ? MUSIC_GHOST : 0);
+        return;
+    }
     ix[0] = (int)(x % P.ne[0]) - MUSIC_GHOST;
     ix[1] = (int)((x / P.ne[0]) % P.ne[1]) - MUSIC_GHOST;
     ix[2] = (int)(x / P.es[2]) - (P.nd == 3 ? MUSIC_GHOST : 0);
@@ -144,6 +154,14 @@ __device__ inline bool ext_has(const GridParams &P, const int ix[3], int d, int 
 
 __device__ inline void cell_coords(const GridParams &P, long long c, int ix[3])
 {
+    if (P.N <= 0x7fffffffLL) {
+        const unsigned u = (unsigned)c, n0 = (unsigned)P.n[0], n1 = (unsigned)P.n[1];
+        const unsigned q = u / n0;
+        ix[0] = (int)(u - q * n0);
+        ix[1] = (int)(q % n1);
+        ix[2] = (int)(q / n1);
+        return;
+    }
     ix[0] = (int)(c % P.n[0]);
     ix[1] = (int)((c / P.n[0]) % P.n[1]);
     ix[2] = (int)(c / P.cs[2]);
@@ -160,9 +178,10 @@ __device__ inline long long cell_nb(const GridParams &P, const int ix[3], int d,
 {
     int j[3] = {ix[0], ix[1], ix[2]};
     int a = j[d] + off;
-    if (P.bc[d] == MUSIC_BC_PERIODIC)
-        a = (a % P.n[d] + P.n[d]) % P.n[d];
-    else if (a < 0)
+    if (P.bc[d] == MUSIC_BC_PERIODIC) {
+        while (a < 0) a += P.n[d];  // |off| is a cell or two: at most a shift or two
+        while (a >= P.n[d]) a -= P.n[d];
+    } else if (a < 0)
         a = 0;
     else if (a >= P.n[d])
         a = P.n[d] - 1;

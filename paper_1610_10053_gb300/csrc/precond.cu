@@ -62,6 +62,40 @@ __global__ void __launch_bounds__(BS) k_coeffs(GridParams P, const double *U, PC
     }
 }
 
+// grid constants in the preconditioner's type, formed once per launch on the host
+template <typename PT>
+struct PcK {
+    PT idx[3], idx2[3], gm1;
+};
+
+template <typename PT>
+PcK<PT> pck_of(const GridParams &P)
+{
+    PcK<PT> K;
+    for (int d = 0; d < 3; d++) {
+        K.idx[d] = (PT)P.idx[d];
+        K.idx2[d] = (PT)P.idx2[d];
+    }
+    K.gm1 = (PT)P.gm1;
+    return K;
+}
+
+// tau and tau^2 of the launch (from the device dt when the grid has one),
+// converted once per CTA
+template <typename PT>
+__device__ __forceinline__ void block_tau(const GridParams &P, PT &tau, PT &tau2)
+{
+    __shared__ PT s_t[2];
+    if (threadIdx.x == 0) {
+        call_tau(P, tau, tau2);
+        s_t[0] = tau;
+        s_t[1] = tau2;
+    }
+    __syncthreads();
+    tau = s_t[0];
+    tau2 = s_t[1];
+}
+
 template <typename PT>
 __device__ inline PT a_up(const GridParams &P, const PC<PT> &C, const int ix[3], int d)
 {
@@ -92,10 +126,10 @@ __global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
 }
 
 template <typename PT, typename RT>
-__global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, const RT *r, PT *b, PT tau)
+__global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, PT *b, PT tau)
 {
     PT tau2_unused = 0;
-    call_tau(P, tau, tau2_unused);
+    block_tau(P, tau, tau2_unused);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -104,19 +138,19 @@ __global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, const RT *r,
             const PT ap = a_up(P, C, ix, d), am = C.a[d][c];
             const PT rp = (PT)r[(2 + d) * P.N + cell_nb(P, ix, d, +1)];
             const PT rm = (PT)r[(2 + d) * P.N + c];
-            divm += (ap * rp - am * rm) * (PT)P.idx[d];
+            divm += (ap * rp - am * rm) * K.idx[d];
         }
-        b[c] = (PT)P.gm1 * (PT)r[P.N + c] / C.gp[c] - tau * divm;
+        b[c] = K.gm1 * (PT)r[P.N + c] / C.gp[c] - tau * divm;
     }
 }
 
 // dq = (1 - w) dp + w (b + tau^2 sum a dp_nb / dx^2) / D; first sweep from 0
 template <typename PT, bool FIRST>
-__global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, const PT *b, const PT *dp, PT *dq,
-                                               PT tau2)
+__global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, PcK<PT> K, const PT *b, const PT *dp,
+                                               PT *dq, PT tau2)
 {
     PT tau_unused = 0;
-    call_tau(P, tau_unused, tau2);
+    block_tau(P, tau_unused, tau2);
     const PT w = (PT)MUSIC_JACOBI_OMEGA;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
@@ -128,7 +162,7 @@ __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, const PT 
         PT off = 0;
         for (int d = 0; d < P.nd; d++) {
             const PT ap = a_up(P, C, ix, d), am = C.a[d][c];
-            off += (ap * dp[cell_nb(P, ix, d, +1)] + am * dp[cell_nb(P, ix, d, -1)]) * (PT)P.idx2[d];
+            off += (ap * dp[cell_nb(P, ix, d, +1)] + am * dp[cell_nb(P, ix, d, -1)]) * K.idx2[d];
         }
         dq[c] = ((PT)1 - w) * dp[c] + w * ((b[c] + tau2 * off) / C.D[c]);
     }
@@ -136,19 +170,19 @@ __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, const PT 
 
 template <typename PT, typename RT>
 __device__ inline PT dm_face(const GridParams &P, const RT *r, const PT *dp, const int ix[3], long long c,
-                             int d, PT tau)
+                             int d, PT tau, PT idx)
 {
     // momentum correction on the lower d-face of cell ix (c)
     if (lower_wall(P, ix, d)) return (PT)r[(2 + d) * P.N + c];
-    return (PT)r[(2 + d) * P.N + c] - tau * (dp[c] - dp[cell_nb(P, ix, d, -1)]) * (PT)P.idx[d];
+    return (PT)r[(2 + d) * P.N + c] - tau * (dp[c] - dp[cell_nb(P, ix, d, -1)]) * idx;
 }
 
 template <typename PT, typename RT>
-__global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, const RT *r, const PT *dp, RT *z, PT tau,
-                                             double *partial)
+__global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, const PT *dp, RT *z,
+                                             PT tau, double *partial)
 {
     PT tau2_unused = 0;
-    call_tau(P, tau, tau2_unused);
+    block_tau(P, tau, tau2_unused);
     __shared__ double sh[BS / 32];
     double nrm = 0.0;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
@@ -156,7 +190,7 @@ __global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, const RT *r
         cell_coords(P, c, ix);
         PT divm = 0, divu = 0;
         for (int d = 0; d < P.nd; d++) {
-            const PT mm_own = dm_face(P, r, dp, ix, c, d, tau);
+            const PT mm_own = dm_face(P, r, dp, ix, c, d, tau, K.idx[d]);
             z[(2 + d) * P.N + c] = (RT)mm_own;
             const double zz = (double)(RT)mm_own;
             nrm += zz * zz;
@@ -164,11 +198,11 @@ __global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, const RT *r
             if (!upper_wall(P, ix, d)) {
                 int jx[3] = {ix[0], ix[1], ix[2]};
                 jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
-                mp = dm_face(P, r, dp, jx, cell_index(P, jx), d, tau);
+                mp = dm_face(P, r, dp, jx, cell_index(P, jx), d, tau, K.idx[d]);
             }
             const PT mm = lower_wall(P, ix, d) ? (PT)0 : mm_own;
-            divm += (mp - mm) * (PT)P.idx[d];
-            divu += (a_up(P, C, ix, d) * mp - C.a[d][c] * mm) * (PT)P.idx[d];
+            divm += (mp - mm) * K.idx[d];
+            divu += (a_up(P, C, ix, d) * mp - C.a[d][c] * mm) * K.idx[d];
         }
         const PT zr = (PT)r[c] - tau * divm;
         const PT ze = (PT)r[P.N + c] - tau * C.hp[c] * divu;
@@ -222,21 +256,22 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     const PT taup = (PT)tau, tau2 = (PT)(tau * tau);
     const int nb = nblocks(P.N);
     PT *b = (PT *)g->pb, *dp = (PT *)g->pdp, *dq = (PT *)g->pdq;
-    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, r, b, taup);
+    const PcK<PT> K = pck_of<PT>(P);
+    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, K, r, b, taup);
     CHECK_LAUNCH();
     const int K = g->desc.precond_sweeps;
     for (int k = 0; k < K; k++) {
         if (k == 0)
-            k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau2);
+            k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, K, b, dp, dq, tau2);
         else
-            k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau2);
+            k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, K, b, dp, dq, tau2);
         CHECK_LAUNCH();
         PT *t = dp;
         dp = dq;
         dq = t;
     }
     if (K == 0) CUDA_TRY(cudaMemsetAsync(dp, 0, P.N * sizeof(PT), s));
-    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, r, dp, z, taup, nullptr);
+    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, K, r, dp, z, taup, nullptr);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
