@@ -256,22 +256,22 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     const PT taup = (PT)tau, tau2 = (PT)(tau * tau);
     const int nb = nblocks(P.N);
     PT *b = (PT *)g->pb, *dp = (PT *)g->pdp, *dq = (PT *)g->pdq;
-    const PcK<PT> K = pck_of<PT>(P);
-    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, K, r, b, taup);
+    const PcK<PT> pk = pck_of<PT>(P);
+    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, b, taup);
     CHECK_LAUNCH();
     const int K = g->desc.precond_sweeps;
     for (int k = 0; k < K; k++) {
         if (k == 0)
-            k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, K, b, dp, dq, tau2);
+            k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
         else
-            k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, K, b, dp, dq, tau2);
+            k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
         CHECK_LAUNCH();
         PT *t = dp;
         dp = dq;
         dq = t;
     }
     if (K == 0) CUDA_TRY(cudaMemsetAsync(dp, 0, P.N * sizeof(PT), s));
-    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, K, r, dp, z, taup, nullptr);
+    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, dp, z, taup, nullptr);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
