@@ -168,6 +168,43 @@ __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, PcK<PT> K
     }
 }
 
+// The same sweep as k_jacobi on a 3-D launch grid: x along the threads of a
+// row of XT, y and z by block, so no index is decomposed; the neighbours are
+// the ones cell_nb gives (periodic wrap, walls clamped onto the cell, whose
+// wall coefficient is zero), in the same expression, so both kernels give the
+// same bits.
+constexpr int XT = 128;
+
+template <typename PT, bool FIRST>
+__global__ void __launch_bounds__(XT) k_jacobi_rows(GridParams P, PC<PT> C, PcK<PT> K, const PT *b, const PT *dp,
+                                                    PT *dq, PT tau2)
+{
+    PT tau_unused = 0;
+    block_tau(P, tau_unused, tau2);
+    const int i = blockIdx.x * XT + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= P.n[0]) return;
+    const int ix[3] = {i, j, k};
+    const long long c = i + (long long)P.n[0] * (j + (long long)P.n[1] * k);
+    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    if (FIRST) {
+        dq[c] = w * (b[c] / C.D[c]);
+        return;
+    }
+    PT off = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= P.nd) break;
+        const int n = P.n[d], a = ix[d];
+        const long long st = P.cs[d];
+        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
+        const long long cu = (a + 1 < n) ? c + st : (per ? c - (long long)(n - 1) * st : c);
+        const long long cd = (a > 0) ? c - st : (per ? c + (long long)(n - 1) * st : c);
+        const PT ap = (!per && a == n - 1) ? (PT)0 : C.a[d][cu], am = C.a[d][c];
+        off += (ap * dp[cu] + am * dp[cd]) * K.idx2[d];
+    }
+    dq[c] = ((PT)1 - w) * dp[c] + w * ((b[c] + tau2 * off) / C.D[c]);
+}
+
 template <typename PT, typename RT>
 __device__ inline PT dm_face(const GridParams &P, const RT *r, const PT *dp, const int ix[3], long long c,
                              int d, PT tau, PT idx)
@@ -260,8 +297,15 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, b, taup);
     CHECK_LAUNCH();
     const int K = g->desc.precond_sweeps;
+    // rows launch unless an extent exceeds the grid's y / z limit (65535)
+    const bool by_rows = P.n[1] <= 65535 && (P.nd < 3 || P.n[2] <= 65535);
+    const dim3 rows((P.n[0] + XT - 1) / XT, P.n[1], P.nd == 3 ? P.n[2] : 1);
     for (int k = 0; k < K; k++) {
-        if (k == 0)
+        if (by_rows && k == 0)
+            k_jacobi_rows<PT, true><<<rows, XT, 0, s>>>(P, C, pk, b, dp, dq, tau2);
+        else if (by_rows)
+            k_jacobi_rows<PT, false><<<rows, XT, 0, s>>>(P, C, pk, b, dp, dq, tau2);
+        else if (k == 0)
             k_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
         else
             k_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
