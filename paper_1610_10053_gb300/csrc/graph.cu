@@ -189,8 +189,8 @@ __global__ void k_ctl_cycle_end(SolveCtl *c, cudaGraphConditionalHandle h_cycle,
 }
 
 // after the update U += x: statistics and the density-correction test
-__global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_newton, int newton_max,
-                             double tol, int cap)
+__global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_newton,
+                             cudaGraphConditionalHandle h_next, int newton_max, double tol, int cap)
 {
     unsigned go = 0u;
     if (!c->stop && !over_cap(c, cap)) {
@@ -208,6 +208,7 @@ __global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditi
             go = 1u;
     }
     cudaGraphSetConditional(h_newton, go);
+    cudaGraphSetConditional(h_next, go);  // the next iteration's residual, when there is one
 }
 
 // --------------------------------------------------------------- vector kernels
@@ -340,26 +341,27 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     SolveCtl *ctl = g->ctl;
     DevScalars *ds = g->ds;
     cudaStream_t s0 = C.st[0], s1 = C.st[1], s2 = C.st[2], s3 = C.st[3], s4 = C.st[4];
-    cudaGraph_t bN, bC, bR, bG, bA;
-    cudaGraphConditionalHandle hN, hC, hR, hG, hA;
+    cudaGraph_t bN, bC, bR, bG, bA, bF;
+    cudaGraphConditionalHandle hN, hC, hR, hG, hA, hF;
     long long t0;
 
     CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
     C.open[0] = true;
-    // ---- attempt: U^n, the step constant C^n, then the Newton loop
+    // ---- attempt: U^n; the step constant C^n with the first residual b = -F(U^n)
+    // and R(U^n) from one evaluation; then the Newton loop, each iteration
+    // closed by the residual of the next (an IF node, skipped after the last)
     t0 = capture_launches();
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s0));
-    TRY(stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt, 1.0, s0));
+    TRY(stencil_apply(g, SM_CNF, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s0));
     TRY(new_handle(s0, &hN));
     k_ctl_attempt<<<1, 1, 0, s0>>>(ctl, hN, d.newton_max_its);
     CHECK_LAUNCH();
     g->glaunch[0] = since(t0);
     TRY(add_conditional(s0, hN, cudaGraphCondTypeWhile, &bN));
     {
-        // ---- Newton iteration: b = -F(U), R(U), |U|, coefficients, |b|
+        // ---- Newton iteration (b = -F(U), R(U) ready): |U|, coefficients, |b|
         TRY(C.begin_body(1, bN));
         t0 = capture_launches();
-        TRY(stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s1));
         TRY(dev_norm2(g, g->U, 1, (size_t)n, &ds->unorm2, s1));
         TRY(precond_setup(g, g->U, dt, s1));
         CUDA_TRY(cudaMemsetAsync(g->x, 0, n * sizeof(double), s1));
@@ -441,9 +443,19 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
         }
         const long long u0 = capture_launches();
         TRY(newton_update(g, &ctl->stop, s1));
-        k_ctl_newton<<<1, 1, 0, s1>>>(ctl, ds, hN, d.newton_max_its, d.newton_tol, cap);
+        TRY(new_handle(s1, &hF));
+        k_ctl_newton<<<1, 1, 0, s1>>>(ctl, ds, hN, hF, d.newton_max_its, d.newton_tol, cap);
         CHECK_LAUNCH();
         g->glaunch[1] = nN + since(u0);
+        TRY(add_conditional(s1, hF, cudaGraphCondTypeIf, &bF));
+        {
+            // b = -F(U), R(U) of the updated iterate, for the next iteration
+            TRY(C.begin_body(2, bF));
+            const long long f0 = capture_launches();
+            TRY(stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s2));
+            g->glaunch[6] = since(f0);
+            TRY(C.end_body(2));
+        }
         TRY(C.end_body(1));
     }
     C.open[0] = false;
@@ -499,9 +511,12 @@ int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStr
     CUDA_TRY(cudaGraphLaunch(g->gexec, s));
     CUDA_TRY(cudaMemcpyAsync(h, g->ctl, offsetof(SolveCtl, cs), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    // kernels the replay ran, from the bodies each loop executed
+    // kernels the replay ran, from the bodies each loop executed (the closing
+    // residual runs after every Newton iteration but the last)
+    const long long nextres = h->newton_it > 0 ? h->newton_it - 1 : 0;
     count_launches(g->glaunch[0] + g->glaunch[1] * h->newton_it + g->glaunch[2] * h->cycles +
-                   g->glaunch[3] * h->restarts + g->glaunch[4] * h->solves + g->glaunch[5] * h->gmres_its);
+                   g->glaunch[3] * h->restarts + g->glaunch[4] * h->solves + g->glaunch[5] * h->gmres_its +
+                   g->glaunch[6] * nextres);
     st->newton_its = h->newton_its;
     st->gmres_its = h->gmres_its;
     st->gmres_unconverged = h->unconverged;

@@ -13,7 +13,9 @@ enum StencilMode {
     SM_R = 0,    // out = R(U)
     SM_CN = 1,   // out = U + dt/2 R(U)                  (step constant C^n)
     SM_F = 2,    // out = sign ((U - C^n) - dt/2 R(U)), also R(U) -> RU
-    SM_JV = 3    // W = U + eps v; out = v - dt/2 (R(W) - RU) / eps
+    SM_JV = 3,   // W = U + eps v; out = v - dt/2 (R(W) - RU) / eps
+    SM_CNF = 4   // at U = U^n: C^n = U + dt/2 R(U) into aux (written), out and RU_out as SM_F
+                 // (one evaluation of R(U^n) for the step constant and the first residual)
 };
 
 // Multi-pass stencil scratch on the extended grid (M doubles each).
@@ -90,7 +92,8 @@ struct music_grid {
     SolveCtl *ctl;         // device control of a graph-driven Newton attempt
     SolveCtl *hctl;        // pinned host mirror of its leading scalars
     cudaGraphExec_t gexec; // the recorded Newton attempt (null until first use)
-    long long glaunch[6];  // kernels per recorded section: top, Newton, cycle, restart, correction, Arnoldi
+    long long glaunch[7];  // kernels per recorded section: top, Newton, cycle, restart, correction, Arnoldi,
+                           // the residual that closes a Newton iteration
     double *diag_rows;     // per-row diagnostic partials
     // passive scalars (Sec. 2.2)
     int ns;                // scalars (planes of N partial densities in sc.U)

@@ -179,8 +179,15 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     const size_t n = g->n;
     const size_t nq = g->sc.n;
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt,
-                                                  1.0, s); }));
+    // Without scalars one evaluation of R(U^n) gives the step constant C^n and
+    // the first iteration's residual (U = U^n there); with them the scalars'
+    // flux captures keep the two evaluations apart.
+    const bool cnf = (g->ns == 0);
+    if (cnf)
+        TRY(stencil_apply(g, SM_CNF, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s));
+    else
+        TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt,
+                                                      1.0, s); }));
     if (g->ns > 0) {
         // scalar step constant C_s = q^n + dt/2 S(q^n) with the fluid at U^n
         CUDA_TRY(cudaMemcpyAsync(g->sq_n, g->sc.U, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -194,8 +201,9 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     int ok = 0;
     for (int k = 0; k < g->desc.newton_max_its; k++) {
         // b = -F(U), RU = R(U) (and the face mass fluxes of U for the scalars)
-        TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt,
-                                                      -1.0, s); }));
+        if (!(cnf && k == 0))
+            TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt,
+                                                          -1.0, s); }));
         double maxdq = 0.0;
         if (g->ns > 0) TRY(scalar_iteration(g, dt, st, &maxdq, s));
         TRY(dev_norm2(g, g->U, 1, n, &g->ds->unorm2, s));

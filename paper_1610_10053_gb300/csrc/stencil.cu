@@ -250,6 +250,12 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
             } else if (MODE == SM_F) {
                 out[i] = (VOUT)(sign * ((U[i] - aux[i]) - hdt * R[q]));
                 if (RU_out) RU_out[i] = R[q];
+            } else if (MODE == SM_CNF) {
+                // the step constant as SM_CN writes it (into aux), then the residual as SM_F forms it
+                const double cn = U[i] + hdt * R[q];
+                const_cast<double *>(aux)[i] = cn;
+                out[i] = (VOUT)(sign * ((U[i] - cn) - hdt * R[q]));
+                if (RU_out) RU_out[i] = R[q];
             } else {
                 out[i] = zero ? (VOUT)0 : (VOUT)((double)v[i] - c_jv * (R[q] - aux[i]));
             }
@@ -313,7 +319,7 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     } else {
         TRY(run_passes<double>(g, U, nullptr, s));
         if (g->fr_capture) TRY(capture_ext_fluxes(g, s));  // face mass fluxes for passive scalars
-        if (diff && (mode == SM_R || mode == SM_F)) TRY(lin_ext_write(g, U, s));
+        if (diff && (mode == SM_R || mode == SM_F || mode == SM_CNF)) TRY(lin_ext_write(g, U, s));
     }
     switch (mode) {
     case SM_R:
@@ -327,6 +333,10 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
     case SM_F:
         k_assemble<SM_F, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, nullptr, (double *)out,
                                                              RU_out, hdt, sign, eps);
+        break;
+    case SM_CNF:
+        k_assemble<SM_CNF, double, double><<<nbn, BS, 0, s>>>(P, g->ext, U, aux, nullptr, (double *)out,
+                                                               RU_out, hdt, sign, eps);
         break;
     case SM_JV:
         if (vin_double && out_double)

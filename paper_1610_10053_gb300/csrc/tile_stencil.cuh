@@ -156,7 +156,7 @@ struct Tile2D {
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __device__ void fused2d_tile(const GridParams &P, const double *U, const double *aux, const VIN *v, VOUT *out,
                              double *RU_out, double hdt, double sign, double epsv, int bx, int by, double *sm,
-                             double *Fr_out = nullptr, float *lin = nullptr)
+                             double *Fr_out = nullptr, float *lin = nullptr, double *Cn_out = nullptr)
 {
     using TL = Tile2D<TX, TY>;
     constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
@@ -337,6 +337,12 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
             out[i] = (VOUT)(U[i] + hdt * Rv[k]);
         } else if (MODE == SM_F) {
             out[i] = (VOUT)(sign * ((U[i] - aux[i]) - hdt * Rv[k]));
+            if (RU_out) RU_out[i] = Rv[k];
+        } else if (MODE == SM_CNF) {
+            // the step constant as SM_CN writes it, then the residual as SM_F forms it from that value
+            const double cn = U[i] + hdt * Rv[k];
+            Cn_out[i] = cn;
+            out[i] = (VOUT)(sign * ((U[i] - cn) - hdt * Rv[k]));
             if (RU_out) RU_out[i] = Rv[k];
         } else {
             out[i] = (epsv == 0.0) ? (VOUT)0 : (VOUT)((double)v[i] - c_jv * (Rv[k] - aux[i]));

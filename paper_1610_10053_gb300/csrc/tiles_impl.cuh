@@ -13,12 +13,13 @@ using namespace tile;
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
 __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *U, const double *aux,
                                                     const VIN *v, VOUT *out, double *RU_out, double hdt,
-                                                    double sign, const double *eps, double *Fr_out, float *lin)
+                                                    double sign, const double *eps, double *Fr_out, float *lin,
+                                                    double *Cn_out)
 {
     extern __shared__ double sm[];
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
     fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
-                                          blockIdx.y, sm, Fr_out, lin);
+                                          blockIdx.y, sm, Fr_out, lin, Cn_out);
 }
 
 template <int MODE, typename VIN, typename VOUT, int TX, int TY>
@@ -33,8 +34,10 @@ int launch_fused2d(music_grid *g, const double *U, const double *aux, const VIN 
     dim3 grid((P.n[0] + TX - 1) / TX, (P.n[1] + TY - 1) / TY);
     // R and F evaluations refresh the difference-form Jv's linearisation planes
     float *lin = (MODE != SM_JV && MODE != SM_CN && g->jv_form == JV_DIFF) ? g->lin : nullptr;
-    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, aux, v, out, RU_out, hdt, sign, &g->ds->eps,
-                                         MODE == SM_JV ? nullptr : g->fr_capture, lin);
+    // SM_CNF writes the step constant into aux
+    double *cn = (MODE == SM_CNF) ? const_cast<double *>(aux) : nullptr;
+    kern<<<grid, TX * TY, TL::SMEM, s>>>(P, U, MODE == SM_CNF ? nullptr : aux, v, out, RU_out, hdt, sign,
+                                         &g->ds->eps, MODE == SM_JV ? nullptr : g->fr_capture, lin, cn);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -179,6 +182,9 @@ int fused2d_apply_t(music_grid *g, int mode, const double *U, const double *aux,
     case SM_F:
         return launch_fused2d<SM_F, double, double, TX, TY>(g, U, aux, nullptr, (double *)out, RU_out, hdt, sign,
                                                             s);
+    case SM_CNF:
+        return launch_fused2d<SM_CNF, double, double, TX, TY>(g, U, aux, nullptr, (double *)out, RU_out, hdt,
+                                                              sign, s);
     case SM_JV:
         if (vin_double && out_double)
             return launch_fused2d<SM_JV, double, double, TX, TY>(g, U, aux, (const double *)v, (double *)out,

@@ -366,8 +366,8 @@ def test_profile_counts_jv_launches():
 
 def test_profile_counts_every_class():
     """Per class: one preconditioner application per Arnoldi step and per
-    cycle's correction; one F evaluation per Newton iteration plus the step
-    constant C^n of each attempt."""
+    cycle's correction; one residual-type evaluation per Newton iteration (the
+    first one also gives the step constant C^n of its attempt)."""
     p = CASES["kh_64"]().with_options(nsteps=1)
     with B().Grid(p, precision=B().MIXED) as g:
         g.set_state(p.U)
@@ -382,7 +382,7 @@ def test_profile_counts_every_class():
         g.profile(False)
     assert jv[0] >= st["gmres_its"] and jv[1] > 0.0
     assert pc[0] >= st["gmres_its"] and pc[1] > 0.0
-    assert res[0] >= st["newton_its"] + 1 and res[1] > 0.0
+    assert res[0] >= st["newton_its"] and res[1] > 0.0
     assert vec[0] >= 3 * st["gmres_its"] and vec[1] > 0.0
     if st["dt_halvings"] == 0:
-        assert res[0] == st["newton_its"] + 1
+        assert res[0] == st["newton_its"]
