@@ -353,16 +353,17 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     t0 = capture_launches();
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s0));
     TRY(stencil_apply(g, SM_CNF, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s0));
+    // |U^n|^2 for the products' eps (each Newton update forms the next one)
+    TRY(dev_norm2(g, g->U, 1, (size_t)n, &ds->unorm2, s0));
     TRY(new_handle(s0, &hN));
     k_ctl_attempt<<<1, 1, 0, s0>>>(ctl, hN, d.newton_max_its);
     CHECK_LAUNCH();
     g->glaunch[0] = since(t0);
     TRY(add_conditional(s0, hN, cudaGraphCondTypeWhile, &bN));
     {
-        // ---- Newton iteration (b = -F(U), R(U) ready): |U|, coefficients, |b|
+        // ---- Newton iteration (b = -F(U), R(U), |U| ready): coefficients, |b|
         TRY(C.begin_body(1, bN));
         t0 = capture_launches();
-        TRY(dev_norm2(g, g->U, 1, (size_t)n, &ds->unorm2, s1));
         TRY(precond_setup(g, g->U, dt, s1));
         CUDA_TRY(cudaMemsetAsync(g->x, 0, n * sizeof(double), s1));
         TRY(dev_norm2(g, g->b, 1, (size_t)n, &ds->rnorm2, s1));

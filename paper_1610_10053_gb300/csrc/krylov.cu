@@ -229,16 +229,17 @@ __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
 // tolerance, and an FP64 division per cell costs more than the update itself.
 template <bool F32>
 __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
-                                                      double *partial, double *dst, unsigned int *counter,
-                                                      const int *skip)
+                                                      double *partial, double *dst, double *unorm2,
+                                                      unsigned int *counter, const int *skip)
 {
     if (skip && *skip) return;  // a hard error ended the linear solve: U stays as it is
     __shared__ double sh[BS / 32];
-    double m = 0.0;
+    double m = 0.0, q = 0.0;
     float m32 = 0.0f;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         const double u = U[e] + x[e];
         U[e] = u;
+        q = fma(u, u, q);  // |U|^2 of the new iterate, for the next product's eps
         if (e < N) {
             if (F32) {
                 const float t = fabsf((float)x[e]) / (float)u;
@@ -251,7 +252,13 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
     if (F32) m = (double)m32;
     const double r = block_max<BS>(m, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
-    if (last_block_done(counter)) finish_max<BS>(partial, gridDim.x, dst, sh);
+    const double t = block_sum<BS>(q, sh);
+    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = t;
+    if (last_block_done(counter)) {
+        finish_max<BS>(partial, gridDim.x, dst, sh);
+        __syncthreads();
+        finish_sums<BS>(partial + gridDim.x, gridDim.x, 0, 1, unorm2, sh);
+    }
 }
 
 
@@ -667,10 +674,12 @@ int newton_update(music_grid *g, const int *skip, cudaStream_t s)
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     if (g->mixed)
         k_newton_update<true><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
-                                                    &g->ds->maxdrho, &g->ds->counters[CNT_NEWTON], skip);
+                                                    &g->ds->maxdrho, &g->ds->unorm2, &g->ds->counters[CNT_NEWTON],
+                                                    skip);
     else
         k_newton_update<false><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
-                                                     &g->ds->maxdrho, &g->ds->counters[CNT_NEWTON], skip);
+                                                     &g->ds->maxdrho, &g->ds->unorm2, &g->ds->counters[CNT_NEWTON],
+                                                     skip);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

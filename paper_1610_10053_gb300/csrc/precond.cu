@@ -24,44 +24,6 @@ using namespace tile;
 
 constexpr int BS = 256;
 
-// Coefficients frozen at U.  An FP32 preconditioner (PT = float) forms them
-// from the state rounded to FP32, with FP32 arithmetic: they are stored in
-// FP32 either way, and FP64 divisions and conversions per cell run at 1/64 of
-// the FP32 rate on this part.  g1 = gamma (gamma - 1) and g2 = gamma in PT.
-template <typename PT>
-__global__ void __launch_bounds__(BS) k_coeffs(GridParams P, const double *U, PC<PT> C, PT g1, PT g2)
-{
-    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
-        int ix[3];
-        cell_coords(P, c, ix);
-        if constexpr (sizeof(PT) == 4) {
-            const float E = (float)U[P.N + c], rc = (float)U[c];
-            C.gp[c] = g1 * E;
-            C.hp[c] = g2 * E;
-            for (int d = 0; d < P.nd; d++) {
-                if (lower_wall(P, ix, d)) {
-                    C.a[d][c] = 0.0f;
-                } else {
-                    const long long l = cell_nb(P, ix, d, -1);
-                    C.a[d][c] = 2.0f / ((float)U[l] + rc);
-                }
-            }
-        } else {
-            const double E = U[P.N + c];
-            C.gp[c] = (PT)(P.gamma * (P.gm1 * E));
-            C.hp[c] = (PT)(P.gamma * E);
-            for (int d = 0; d < P.nd; d++) {
-                if (lower_wall(P, ix, d)) {
-                    C.a[d][c] = (PT)0;
-                } else {
-                    const long long l = cell_nb(P, ix, d, -1);
-                    C.a[d][c] = (PT)(1.0 / (0.5 * (U[l] + U[c])));
-                }
-            }
-        }
-    }
-}
-
 // grid constants in the preconditioner's type, formed once per launch on the host
 template <typename PT>
 struct PcK {
@@ -102,26 +64,51 @@ __device__ inline PT a_up(const GridParams &P, const PC<PT> &C, const int ix[3],
     return upper_wall(P, ix, d) ? (PT)0 : C.a[d][cell_nb(P, ix, d, +1)];
 }
 
+// Coefficients frozen at U and the Helmholtz diagonal, in one pass: 1/rbar on
+// the lower d-faces (zero on walls), gamma p, gamma E, and
+// D = 1/(gamma p) + tau^2 sum_d (a_d + a_d+) / dx_d^2, where the upper face's
+// a_d+ is formed exactly as its own cell forms it as a lower face.  An FP32
+// preconditioner (PT = float) forms them from the state rounded to FP32, with
+// FP32 arithmetic: they are stored in FP32 either way, and FP64 divisions and
+// conversions per cell run at 1/64 of the FP32 rate on this part.
+// g1 = gamma (gamma - 1) and g2 = gamma in PT.
 template <typename PT>
-__global__ void __launch_bounds__(BS) k_diag(GridParams P, PC<PT> C, PT tau2)
+__device__ __forceinline__ PT face_coef(const GridParams &P, const double *U, long long lo, long long hi)
 {
-    // tau^2 (from the device dt when the grid has one) and 1 / dx^2 in PT,
-    // converted once per CTA
-    __shared__ PT s_c[4];
-    if (threadIdx.x == 0) {
-        PT tau_unused = 0;
-        call_tau(P, tau_unused, tau2);
-        s_c[0] = tau2;
-        for (int d = 0; d < 3; d++) s_c[1 + d] = (PT)P.idx2[d];
-    }
-    __syncthreads();
-    tau2 = s_c[0];
+    if constexpr (sizeof(PT) == 4)
+        return 2.0f / ((float)U[lo] + (float)U[hi]);
+    else
+        return (PT)(1.0 / (0.5 * (U[lo] + U[hi])));
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_setup(GridParams P, const double *U, PC<PT> C, PcK<PT> K, PT g1, PT g2,
+                                              PT tau2)
+{
+    PT tau_unused = 0;
+    block_tau(P, tau_unused, tau2);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
+        PT gp;
+        if constexpr (sizeof(PT) == 4) {
+            const float E = (float)U[P.N + c];
+            gp = g1 * E;
+            C.hp[c] = g2 * E;
+        } else {
+            const double E = U[P.N + c];
+            gp = (PT)(P.gamma * (P.gm1 * E));
+            C.hp[c] = (PT)(P.gamma * E);
+        }
+        C.gp[c] = gp;
         PT diag = 0;
-        for (int d = 0; d < P.nd; d++) diag += (a_up(P, C, ix, d) + C.a[d][c]) * s_c[1 + d];
-        C.D[c] = (PT)1 / C.gp[c] + tau2 * diag;
+        for (int d = 0; d < P.nd; d++) {
+            const PT am = lower_wall(P, ix, d) ? (PT)0 : face_coef<PT>(P, U, cell_nb(P, ix, d, -1), c);
+            const PT ap = upper_wall(P, ix, d) ? (PT)0 : face_coef<PT>(P, U, c, cell_nb(P, ix, d, +1));
+            C.a[d][c] = am;
+            diag += (ap + am) * K.idx2[d];
+        }
+        C.D[c] = (PT)1 / gp + tau2 * diag;
     }
 }
 
@@ -277,9 +264,8 @@ int setup_t(music_grid *g, const double *U, double dt, cudaStream_t s)
     const GridParams &P = g->P;
     PC<PT> C = pc_of<PT>(g);
     const double tau = 0.5 * dt;
-    k_coeffs<PT><<<nblocks(P.N), BS, 0, s>>>(P, U, C, (PT)(P.gamma * P.gm1), (PT)P.gamma);
-    CHECK_LAUNCH();
-    k_diag<PT><<<nblocks(P.N), BS, 0, s>>>(P, C, (PT)(tau * tau));
+    k_setup<PT><<<nblocks(P.N), BS, 0, s>>>(P, U, C, pck_of<PT>(P), (PT)(P.gamma * P.gm1), (PT)P.gamma,
+                                             (PT)(tau * tau));
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

@@ -188,6 +188,8 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     else
         TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_CN, g->Un, nullptr, nullptr, 1, g->Cn, 1, nullptr, dt,
                                                       1.0, s); }));
+    // |U|^2 for the products' eps: here for U^n, then by every Newton update
+    TRY(dev_norm2(g, g->U, 1, n, &g->ds->unorm2, s));
     if (g->ns > 0) {
         // scalar step constant C_s = q^n + dt/2 S(q^n) with the fluid at U^n
         CUDA_TRY(cudaMemcpyAsync(g->sq_n, g->sc.U, nq * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -206,7 +208,6 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
                                                           -1.0, s); }));
         double maxdq = 0.0;
         if (g->ns > 0) TRY(scalar_iteration(g, dt, st, &maxdq, s));
-        TRY(dev_norm2(g, g->U, 1, n, &g->ds->unorm2, s));
         TRY(precond_setup(g, g->U, dt, s));
         GmresOut go;
         int rc = gmres(g, dt, &go, s);
