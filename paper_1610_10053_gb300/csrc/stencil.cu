@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(BS) k_fluxes(GridParams P, ExtScratch X)
             const long long s = P.es[d];
             const double u = X.uf[d][x];
             double rs, es;
-            if (nonneg(u)) {
+            if (u >= 0.0) {
                 rs = X.rho[x - s] + 0.5 * X.srho[d][x - s];
                 es = X.e[x - s] + 0.5 * X.se[d][x - s];
             } else {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
             const long long s = P.es[d];
             if (ext_has(P, ix, d, -2) && ext_has(P, ix, d, +2)) {
                 const double fm = 0.5 * (X.Frho[d][x] + X.Frho[d][x + s]);
-                const double us = nonneg(fm) ? X.uf[d][x] + 0.5 * X.su[d][d][x]
+                const double us = (fm >= 0.0) ? X.uf[d][x] + 0.5 * X.su[d][d][x]
                                               : X.uf[d][x + s] - 0.5 * X.su[d][d][x + s];
                 X.Phi[d][x] = fm * us;
             }
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
                 if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, q, -2) || !ext_has(P, ix, q, +1)) continue;
                 const long long t = P.es[q];
                 const double fm = 0.5 * (X.Frho[q][x - s] + X.Frho[q][x]);
-                const double us = nonneg(fm) ? X.uf[d][x - t] + 0.5 * X.su[d][q][x - t]
+                const double us = (fm >= 0.0) ? X.uf[d][x - t] + 0.5 * X.su[d][q][x - t]
                                               : X.uf[d][x] - 0.5 * X.su[d][q][x];
                 X.Psi[d][q][x] = fm * us;
             }

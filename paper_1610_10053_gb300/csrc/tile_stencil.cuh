@@ -18,29 +18,9 @@ struct WLoad {
     }
 };
 
-// Branch tests of the FP64 stencil taken on the sign and magnitude bits with
-// integer operations (FP64 multiplies and compares run at 1/64 of the FP32
-// rate on this part).  For finite values they decide as the floating-point
-// forms do, except a * b so small that it underflows to zero, which they
-// count as positive (the limited slope is then of that size instead of 0).
-// pos_prod(a, b): a * b > 0, both nonzero with the same sign
-__device__ __forceinline__ bool pos_prod(double a, double b)
-{
-    const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
-    const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
-    return ((ua ^ ub) >> 63) == 0ull && (ua << 1) != 0ull && (ub << 1) != 0ull;
-}
-
-// nonneg(u): u >= 0, the sign bit clear or u = -0
-__device__ __forceinline__ bool nonneg(double u)
-{
-    const long long iu = __double_as_longlong(u);
-    return iu >= 0 || (iu << 1) == 0;
-}
-
 __device__ inline double vanleer(double a, double b)
 {
-    return pos_prod(a, b) ? (2.0 * a) * b / (a + b) : 0.0;
+    return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
 }
 
 // Ghost mapping of cell ix (in place into j, which starts as ix): periodic
@@ -249,7 +229,7 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     // ---- phase 3: upwind mass and energy fluxes
     TILE_RECT(X0 - 1, X1 + 1, Y0 - 1, Y1) {
         const double u = uu[q];
-        const bool up = nonneg(u);
+        const bool up = (u >= 0.0);
         const double rs = up ? rho[q - 1] + 0.5 * srx[q - 1] : rho[q] - 0.5 * srx[q];
         const double fr = u * rs;
         Frx[q] = fr;
@@ -260,7 +240,7 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     }
     TILE_RECT(X0 - 1, X1, Y0 - 1, Y1 + 1) {
         const double u = vv[q];
-        const bool up = nonneg(u);
+        const bool up = (u >= 0.0);
         const double rs = up ? rho[q - RX] + 0.5 * sry[q - RX] : rho[q] - 0.5 * sry[q];
         const double fr = u * rs;
         Fry[q] = fr;
@@ -274,22 +254,22 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     // ---- phase 4: momentum fluxes
     TILE_RECT(X0 - 1, X1, Y0, Y1) {
         const double fm = 0.5 * (Frx[q] + Frx[q + 1]);
-        const double us = nonneg(fm) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
+        const double us = (fm >= 0.0) ? uu[q] + 0.5 * sux[q] : uu[q + 1] - 0.5 * sux[q + 1];
         Phx[q] = fm * us;
     }
     TILE_RECT(X0, X1, Y0 - 1, Y1) {
         const double fm = 0.5 * (Fry[q] + Fry[q + RX]);
-        const double us = nonneg(fm) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
+        const double us = (fm >= 0.0) ? vv[q] + 0.5 * svy[q] : vv[q + RX] - 0.5 * svy[q + RX];
         Phy[q] = fm * us;
     }
     TILE_RECT(X0, X1, Y0, Y1 + 1) {
         const double fm = 0.5 * (Fry[q - 1] + Fry[q]);
-        const double us = nonneg(fm) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
+        const double us = (fm >= 0.0) ? uu[q - RX] + 0.5 * suy[q - RX] : uu[q] - 0.5 * suy[q];
         Psxy[q] = fm * us;
     }
     TILE_RECT(X0, X1 + 1, Y0, Y1) {
         const double fm = 0.5 * (Frx[q - RX] + Frx[q]);
-        const double us = nonneg(fm) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
+        const double us = (fm >= 0.0) ? vv[q - 1] + 0.5 * svx[q - 1] : vv[q] - 0.5 * svx[q];
         Psyx[q] = fm * us;
     }
     __syncthreads();
