@@ -528,7 +528,10 @@ int music_set_jv_form(music_grid *grid, int form)
         return MUSIC_E_INVAL;
     }
     const int f = (form == MUSIC_JV_DIFF32) ? JV_DIFF : JV_FD;
-    if (f != grid->jv_form) graph_release(grid);  // recorded with the other kernel
+    if (f != grid->jv_form) {
+        graph_release(grid);     // recorded with the other kernel
+        grid->binst_ready = 0;   // the batched solver's descriptor names the form too
+    }
     grid->jv_form = f;
     tune_lookup(grid);
     return MUSIC_OK;

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "tile_jvdiff.cuh"
 #include "tile_precond.cuh"
 #include "tile_stencil.cuh"
 
@@ -32,6 +33,7 @@ struct BInst {
     DevScalars *ds;
     int restart, max_restarts, newton_max, sweeps, max_halvings, precond;
     double rtol, newton_tol;
+    float *lin;   // linearisation planes: FP32 products in difference form (tile_jvdiff.cuh), or null
 };
 static_assert(sizeof(BInst<double>) <= 1024, "descriptor must fit the grid's 1 KiB slot");
 
@@ -79,11 +81,25 @@ __device__ double cta_dot(const KT *a, const KT *b, long long n, double *red)
 
 template <int MODE, typename VIN, typename VOUT>
 __device__ void stencil_all(const GridParams &P, const double *U, const double *aux, const VIN *v, VOUT *out,
-                            double *RU_out, double hdt, double sign, double epsv, double *sm)
+                            double *RU_out, double hdt, double sign, double epsv, double *sm, float *lin = nullptr)
 {
     const int ntx = (P.n[0] + STX - 1) / STX, nty = (P.n[1] + STY - 1) / STY;
     for (int t = 0; t < ntx * nty; t++) {
-        fused2d_tile<MODE, VIN, VOUT, STX, STY>(P, U, aux, v, out, RU_out, hdt, sign, epsv, t % ntx, t / ntx, sm);
+        fused2d_tile<MODE, VIN, VOUT, STX, STY>(P, U, aux, v, out, RU_out, hdt, sign, epsv, t % ntx, t / ntx, sm,
+                                                nullptr, lin);
+        __syncthreads();
+    }
+}
+
+// Jv of an FP32 direction in difference form over all tiles of the grid, from
+// the linearisation planes of the last F evaluation; eps in shared memory
+__device__ void jvdiff_all(const GridParams &P, const double *U, const float *lin, const float *v, float *out,
+                           double hdt, const double *eps_sh, double *sm)
+{
+    const JvConst K{(float)P.idx[0], (float)P.idx[1], (float)P.gm1, (float)P.g[0], (float)P.g[1]};
+    const int ntx = (P.n[0] + STX - 1) / STX, nty = (P.n[1] + STY - 1) / STY;
+    for (int t = 0; t < ntx * nty; t++) {
+        jvdiff2d_tile<float, float, STX, STY>(P, K, U, lin, v, out, hdt, eps_sh, t % ntx, t / ntx, sm);
         __syncthreads();
     }
 }
@@ -227,7 +243,18 @@ __device__ GmresRes gmres_cta(const BInst<KT> &I, double dt, double unorm2, doub
             const KT *Vj = I.V + (long long)j * n;
             const double zz = cta_sum(precond_all<KT, KM>(I, dt, Vj, I.z, sm), red);
             const double eps = fd_eps(unorm2, zz);
-            stencil_all<SM_JV, KT, KT>(P, I.U, I.RU, I.z, I.w, nullptr, hdt, 1.0, eps, (double *)sm);
+            if constexpr (sizeof(KT) == 4) {
+                if (I.lin) {
+                    __shared__ double sh_eps;
+                    if (threadIdx.x == 0) sh_eps = eps;
+                    __syncthreads();
+                    jvdiff_all(P, I.U, I.lin, I.z, I.w, hdt, &sh_eps, (double *)sm);
+                } else {
+                    stencil_all<SM_JV, KT, KT>(P, I.U, I.RU, I.z, I.w, nullptr, hdt, 1.0, eps, (double *)sm);
+                }
+            } else {
+                stencil_all<SM_JV, KT, KT>(P, I.U, I.RU, I.z, I.w, nullptr, hdt, 1.0, eps, (double *)sm);
+            }
             // classical Gram-Schmidt, twice: all dots against the same w,
             // then one update
             for (int pass = 0; pass < 2; pass++) {
@@ -337,7 +364,7 @@ __global__ void __launch_bounds__(NT, 1) k_batched_step(const __grid_constant__ 
             int ok = 0;
             for (int k = 0; k < I.newton_max; k++) {
                 stencil_all<SM_F, double, double>(P, I.U, I.Cn, nullptr, I.b, I.RU, 0.5 * dt, -1.0, 0.0,
-                                                  (double *)sm);
+                                                  (double *)sm, I.lin);
                 double uu = 0.0;
                 for (long long e = threadIdx.x; e < n; e += NT) uu += I.U[e] * I.U[e];
                 const double unorm2 = cta_sum(uu, red);
@@ -422,6 +449,7 @@ BInst<KT> make_inst(music_grid *g)
     I.precond = g->desc.precond;
     I.rtol = g->desc.gmres_rtol;
     I.newton_tol = g->desc.newton_tol;
+    I.lin = (g->mixed && g->jv_form == JV_DIFF) ? g->lin : nullptr;
     return I;
 }
 
@@ -429,7 +457,8 @@ template <typename KT, int KM>
 int launch_batched(music_grid **grids, int count, const double *cfl, const double *dt_max, cudaStream_t s)
 {
     // stencil tile (17 planes of 37 x 21 doubles) or preconditioner tile
-    const size_t st = Tile2D<STX, STY>::SMEM;
+    const size_t st = Tile2D<STX, STY>::SMEM > JvTile<STX, STY>::SMEM ? Tile2D<STX, STY>::SMEM
+                                                                        : JvTile<STX, STY>::SMEM;
     const size_t pc = (size_t)6 * (PTX + 2 * (KM + 1)) * (PTY + 2 * (KM + 1)) * sizeof(KT);
     const size_t smem = st > pc ? st : pc;
     static std::atomic<uint64_t> attr{0};
