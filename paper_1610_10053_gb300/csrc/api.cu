@@ -162,6 +162,7 @@ void alloc_plan(music_grid *g, F &&f)
         if (general_grid(P)) {
             f(&g->prh, N * ks);
             for (int k = 0; k < P.nd; k++) f(&g->pkf[k], N * ks);
+            f(&g->pgw, (size_t)2 * P.nd * N * ks);
         }
     }
     if (P.geom == MUSIC_GEOM_SPHERICAL) f((void **)&g->gface, (size_t)(P.n[0] + 1) * sizeof(double));

@@ -81,6 +81,7 @@ struct music_grid {
     // preconditioner (float for mixed, double otherwise)
     void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
     void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
+    void *pgw;             // general form: the sweeps' neighbour weights (2 nd planes)
     double *gface;         // spherical: radial gravity on the r-faces
     double *hg;            // Hessenberg and Givens storage of the batched solver
     void *binst;           // device copy of this grid's batched-solver descriptor

@@ -339,6 +339,7 @@ struct PCG {
     PT *a[3], *kf[3];  // 1/rbar and mean chi on the lower d-face (0 on walls)
     PT *gp, *hp, *rh, *D;
     PT *chi;           // cell chi (scratch during setup)
+    PT *wu[3], *wl[3]; // a sweep's weights of the upper / lower d-neighbour (metric, pressure and conduction)
 };
 
 template <typename PT>
@@ -400,16 +401,23 @@ __global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double
         int ix[3];
         cell_coords(P, c, ix);
         double diag = 0.0, dth = 0.0;
+        const double gp = C.gp[c];
+        const double th = tau * P.gm1 / gp;
         for (int d = 0; d < P.nd; d++) {
             const Geo G = geo(P, ix, d);
             long long u;
             double ap, kp;
             up_coeffs(P, C, ix, d, u, ap, kp);
-            diag += G.Wp * ap / G.h + G.Wm * (double)C.a[d][c] / G.h;
-            dth += G.Wp * kp / G.h + G.Wm * (double)C.kf[d][c] / G.h;
+            const long long l = cell_nb(P, ix, d, -1);
+            const double am = C.a[d][c], km = C.kf[d][c];
+            diag += G.Wp * ap / G.h + G.Wm * am / G.h;
+            dth += G.Wp * kp / G.h + G.Wm * km / G.h;
+            // the sweep's off-diagonal weights, formed once per Newton iteration
+            // (the metric costs FP64 trigonometry per cell)
+            C.wu[d][c] = (PT)(tau2 * (G.Wp * ap / G.h) + th * (G.Wp * kp / G.h / (double)C.rh[u]));
+            C.wl[d][c] = (PT)(tau2 * (G.Wm * am / G.h) + th * (G.Wm * km / G.h / (double)C.rh[l]));
         }
-        const double gp = C.gp[c];
-        C.D[c] = (PT)(1.0 / gp + tau2 * diag + (tau * P.gm1 / gp) * dth / (double)C.rh[c]);
+        C.D[c] = (PT)(1.0 / gp + tau2 * diag + th * dth / (double)C.rh[c]);
     }
 }
 
@@ -433,11 +441,10 @@ __global__ void __launch_bounds__(BS) k_gen_rhs(GridParams P, PCG<PT> C, const P
 }
 
 template <typename PT, bool FIRST>
-__global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq,
-                                                   double tau)
+__global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq)
 {
-    tau = call_hdt(P, tau);
-    const double w = MUSIC_JACOBI_OMEGA, tau2 = tau * tau;
+    const double w = MUSIC_JACOBI_OMEGA;
+    const PT wp = (PT)MUSIC_JACOBI_OMEGA;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
             dq[c] = (PT)(w * ((double)b[c] / (double)C.D[c]));
@@ -445,20 +452,13 @@ __global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, cons
         }
         int ix[3];
         cell_coords(P, c, ix);
-        const double th = tau * P.gm1 / (double)C.gp[c];
-        double off = 0.0;
+        // weights from the set-up; the sweep in the preconditioner's type
+        PT off = 0;
         for (int d = 0; d < P.nd; d++) {
-            const Geo G = geo(P, ix, d);
-            long long u;
-            double ap, kp;
-            up_coeffs(P, C, ix, d, u, ap, kp);
-            const long long l = cell_nb(P, ix, d, -1);
-            const double am = C.a[d][c], km = C.kf[d][c];
-            off += tau2 * (G.Wp * ap / G.h * (double)dp[u] + G.Wm * am / G.h * (double)dp[l]);
-            off += th * (G.Wp * kp / G.h * (double)dp[u] / (double)C.rh[u] +
-                         G.Wm * km / G.h * (double)dp[l] / (double)C.rh[l]);
+            const long long u = cell_nb(P, ix, d, +1), l = cell_nb(P, ix, d, -1);
+            off += C.wu[d][c] * dp[u] + C.wl[d][c] * dp[l];
         }
-        dq[c] = (PT)((1.0 - w) * (double)dp[c] + w * (((double)b[c] + off) / (double)C.D[c]));
+        dq[c] = ((PT)1 - wp) * dp[c] + wp * ((b[c] + off) / C.D[c]);
     }
 }
 
@@ -511,6 +511,10 @@ PCG<PT> pcg_of(music_grid *g)
     C.rh = (PT *)g->prh;
     C.D = (PT *)g->pD;
     C.chi = (PT *)g->pb;  // the rhs buffer is free during setup
+    for (int d = 0; d < 3; d++) {
+        C.wu[d] = d < g->P.nd ? (PT *)g->pgw + (size_t)(2 * d) * g->P.N : nullptr;
+        C.wl[d] = d < g->P.nd ? (PT *)g->pgw + (size_t)(2 * d + 1) * g->P.N : nullptr;
+    }
     return C;
 }
 
@@ -542,9 +546,9 @@ int gen_apply(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     const int K = g->desc.precond_sweeps;
     for (int k = 0; k < K; k++) {
         if (k == 0)
-            k_gen_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau);
+            k_gen_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq);
         else
-            k_gen_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, b, dp, dq, tau);
+            k_gen_jacobi<PT, false><<<nb, BS, 0, s>>>(P, C, b, dp, dq);
         CHECK_LAUNCH();
         PT *t = dp;
         dp = dq;
