@@ -140,6 +140,7 @@ GridParams make_params(const music_grid_desc &d)
     P.lum = d.lum;
     for (int k = 0; k < 3; k++) P.flux_wall[k] = (k < d.ndim && d.bc[k] == MUSIC_BC_WALL) ? d.flux_wall[k] : 0;
     P.gface = nullptr;
+    P.sgeo = nullptr;
     P.dt_dev = nullptr;
     return P;
 }
@@ -165,7 +166,10 @@ void alloc_plan(music_grid *g, F &&f)
             f(&g->pgw, (size_t)2 * P.nd * N * ks);
         }
     }
-    if (P.geom == MUSIC_GEOM_SPHERICAL) f((void **)&g->gface, (size_t)(P.n[0] + 1) * sizeof(double));
+    if (P.geom == MUSIC_GEOM_SPHERICAL) {
+        f((void **)&g->gface, (size_t)(P.n[0] + 1) * sizeof(double));
+        f((void **)&g->sgeo, (size_t)SG_COUNT * N * sizeof(double));
+    }
     // linearisation planes of the difference-form Jv (mixed grids on the
     // fused 2-D stencil), written with every R and F evaluation
     if (g->mixed && P.nd == 2 && g->stencil_variant != STENCIL_MULTIPASS && !general_grid(P))
@@ -363,6 +367,13 @@ int grid_create(const music_grid_desc *desc, cudaStream_t home, music_grid **out
             fail = 1;
         }
         g->P.gface = g->gface;
+    }
+    if (!fail && g->sgeo) {
+        g->P.sgeo = g->sgeo;
+        if (sph_geo_build(g, home) != MUSIC_OK || cudaStreamSynchronize(home) != cudaSuccess) {
+            cudaGetLastError();
+            fail = 1;
+        }
     }
     g->desc.g_radial = nullptr;  // copied; the caller's array is not retained
     if (!fail && cudaMallocHost(&g->hs, sizeof(DevScalars)) != cudaSuccess) {

@@ -29,6 +29,7 @@ struct GridParams {
     double chi0, lum;
     int flux_wall[3];
     const double *gface;   // spherical: radial gravity on the n[0]+1 r-faces (device), or null
+    const double *sgeo;    // spherical: the cells' metric (SG_COUNT planes of N, device), or null
     const double *dt_dev;  // launches recorded into a solver graph read dt here (device), else null
 };
 
@@ -66,6 +67,18 @@ __device__ inline double sph_area(const GridParams &P, int d, int i, int j)
     const double ra = sph_r(P, i), rb = sph_r(P, i + 1);
     return 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j));
 }
+// The metric of the (r, theta) cells, tabulated once per grid (the same
+// expressions as above, evaluated at grid creation instead of in every
+// stencil and preconditioner launch): volume, the four face areas, and the
+// control volumes of the r- and theta-momenta with their face and edge areas.
+enum SphGeo {
+    SG_V = 0, SG_ARM, SG_ARP, SG_ATM, SG_ATP,
+    SG_VR, SG_ACP, SG_ACM, SG_EM, SG_EP, SG_RF,
+    SG_VT, SG_BP, SG_BM, SG_FA, SG_FB, SG_RC,
+    SG_COUNT
+};
+__device__ inline double sgeo(const GridParams &P, int k, long long c) { return P.sgeo[(long long)k * P.N + c]; }
+
 // distance between the centres of the two cells sharing a d-face of column i
 __device__ inline double sph_h(const GridParams &P, int d, int i)
 {

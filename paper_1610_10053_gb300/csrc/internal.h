@@ -83,6 +83,7 @@ struct music_grid {
     void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
     void *pgw;             // general form: the sweeps' neighbour weights (2 nd planes)
     double *gface;         // spherical: radial gravity on the r-faces
+    double *sgeo;          // spherical: the cells' metric (SG_COUNT planes of N)
     double *hg;            // Hessenberg and Givens storage of the batched solver
     void *binst;           // device copy of this grid's batched-solver descriptor
     int binst_ready;
@@ -125,6 +126,8 @@ int prof_harvest(music_grid *g, int wait);
 // linearisation arrays from the FP64 planes of the R / F evaluation just run
 // at U, and the product of an FP32 direction
 int lin_ext_write(music_grid *g, const double *U, cudaStream_t s);
+// the spherical metric table of the grid (at creation)
+int sph_geo_build(music_grid *g, cudaStream_t s);
 int jvdiff_multipass(music_grid *g, const double *U, const float *v, float *out, double hdt, cudaStream_t s);
 // Times the enclosing host function's launches as class cls while the grid
 // is profiled (CUDA events on s around them).  Scopes do not nest: inside an

@@ -323,9 +323,10 @@ __device__ inline Geo geo(const GridParams &P, const int ix[3], int d)
 {
     Geo o;
     if (P.geom == MUSIC_GEOM_SPHERICAL) {
-        const double V = sph_vol(P, ix[0], ix[1]);
-        o.Wm = sph_area(P, d, ix[0], ix[1]) / V;
-        o.Wp = sph_area(P, d, ix[0] + (d == 0), ix[1] + (d == 1)) / V;
+        const long long c = cell_index(P, ix);
+        const double V = sgeo(P, SG_V, c);
+        o.Wm = sgeo(P, d == 0 ? SG_ARM : SG_ATM, c) / V;
+        o.Wp = sgeo(P, d == 0 ? SG_ARP : SG_ATP, c) / V;
         o.h = sph_h(P, d, ix[0]);
     } else {
         o.Wm = o.Wp = P.idx[d];

@@ -145,13 +145,15 @@ __global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
 // divergence is (1/V) sum(A F) over the control volume, the momenta carry
 // the geometric terms +rho u_t^2 / r (radial) and -rho u_r u_t / r (polar),
 // pressure gradients divide by dr or r_c dtheta, gravity from the r-face table.
-__device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int ix[3], long long x, double *R)
+// The metric comes from the grid's table (SphGeo).
+__device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int ix[3], long long x, long long c,
+                             double *R)
 {
     const int i = ix[0], j = ix[1];
     const long long s0 = P.es[0], s1 = P.es[1];
-    const double V = sph_vol(P, i, j);
-    const double Arm = sph_area(P, 0, i, j), Arp = sph_area(P, 0, i + 1, j);
-    const double Atm = sph_area(P, 1, i, j), Atp = sph_area(P, 1, i, j + 1);
+    const double V = sgeo(P, SG_V, c);
+    const double Arm = sgeo(P, SG_ARM, c), Arp = sgeo(P, SG_ARP, c);
+    const double Atm = sgeo(P, SG_ATM, c), Atp = sgeo(P, SG_ATP, c);
     const double fr = (Arp * X.Frho[0][x + s0] - Arm * X.Frho[0][x]) + (Atp * X.Frho[1][x + s1] - Atm * X.Frho[1][x]);
     const double fe = (Arp * X.FE[0][x + s0] - Arm * X.FE[0][x]) + (Atp * X.FE[1][x + s1] - Atm * X.FE[1][x]);
     const double du = (Arp * X.uf[0][x + s0] - Arm * X.uf[0][x]) + (Atp * X.uf[1][x + s1] - Atm * X.uf[1][x]);
@@ -161,15 +163,11 @@ __device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int
         const double cd = (Arp * X.Gc[0][x + s0] - Arm * X.Gc[0][x]) + (Atp * X.Gc[1][x + s1] - Atm * X.Gc[1][x]);
         R[1] = R[1] + cd / V;
     }
-    const double ctj = cos(sph_th(P, j)), ctj1 = cos(sph_th(P, j + 1));
     if (P.bc[0] == MUSIC_BC_WALL && i == 0) {
         R[2] = 0.0;
     } else {
-        const double rm = sph_r(P, i - 0.5), rp = sph_r(P, i + 0.5), rf = sph_r(P, i);
-        const double Vr = (rp * rp * rp - rm * rm * rm) / 3.0 * (ctj - ctj1);
-        const double Acp = rp * rp * (ctj - ctj1), Acm = rm * rm * (ctj - ctj1);
-        const double Em = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j));
-        const double Ep = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j + 1));
+        const double Vr = sgeo(P, SG_VR, c), Acp = sgeo(P, SG_ACP, c), Acm = sgeo(P, SG_ACM, c);
+        const double Em = sgeo(P, SG_EM, c), Ep = sgeo(P, SG_EP, c), rf = sgeo(P, SG_RF, c);
         const double acc = (Acp * X.Phi[0][x] - Acm * X.Phi[0][x - s0]) + (Ep * X.Psi[0][1][x + s1] - Em * X.Psi[0][1][x]);
         const double rbar = 0.5 * (X.rho[x - s0] + X.rho[x]);
         const double ut = 0.25 * ((X.uf[1][x - s0] + X.uf[1][x]) + (X.uf[1][x - s0 + s1] + X.uf[1][x + s1]));
@@ -178,16 +176,44 @@ __device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int
     if (P.bc[1] == MUSIC_BC_WALL && j == 0) {
         R[3] = 0.0;
     } else {
-        const double ra = sph_r(P, i), rb = sph_r(P, i + 1), rc = sph_r(P, i + 0.5);
-        const double cm = cos(sph_th(P, j - 0.5)), cp = cos(sph_th(P, j + 0.5));
-        const double Vt = (rb * rb * rb - ra * ra * ra) / 3.0 * (cm - cp);
-        const double Bp = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j + 0.5));
-        const double Bm = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j - 0.5));
-        const double Fa = ra * ra * (cm - cp), Fb = rb * rb * (cm - cp);
+        const double Vt = sgeo(P, SG_VT, c), Bp = sgeo(P, SG_BP, c), Bm = sgeo(P, SG_BM, c);
+        const double Fa = sgeo(P, SG_FA, c), Fb = sgeo(P, SG_FB, c), rc = sgeo(P, SG_RC, c);
         const double acc = (Fb * X.Psi[1][0][x + s0] - Fa * X.Psi[1][0][x]) + (Bp * X.Phi[1][x] - Bm * X.Phi[1][x - s1]);
         const double rbar = 0.5 * (X.rho[x - s1] + X.rho[x]);
         const double ur = 0.25 * ((X.uf[0][x - s1] + X.uf[0][x]) + (X.uf[0][x - s1 + s0] + X.uf[0][x + s0]));
         R[3] = ((-acc / Vt - (X.p[x] - X.p[x - s1]) / (rc * P.dx[1])) - rbar * ur * X.uf[1][x] / rc) + rbar * P.g[1];
+    }
+}
+
+// the table of the metric, from the expressions of common.cuh
+__global__ void __launch_bounds__(BS) k_sph_geo(GridParams P, double *T)
+{
+    for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
+        int ix[3];
+        cell_coords(P, c, ix);
+        const int i = ix[0], j = ix[1];
+        const long long N = P.N;
+        T[SG_V * N + c] = sph_vol(P, i, j);
+        T[SG_ARM * N + c] = sph_area(P, 0, i, j);
+        T[SG_ARP * N + c] = sph_area(P, 0, i + 1, j);
+        T[SG_ATM * N + c] = sph_area(P, 1, i, j);
+        T[SG_ATP * N + c] = sph_area(P, 1, i, j + 1);
+        const double ctj = cos(sph_th(P, j)), ctj1 = cos(sph_th(P, j + 1));
+        const double rm = sph_r(P, i - 0.5), rp = sph_r(P, i + 0.5), rf = sph_r(P, i);
+        T[SG_VR * N + c] = (rp * rp * rp - rm * rm * rm) / 3.0 * (ctj - ctj1);
+        T[SG_ACP * N + c] = rp * rp * (ctj - ctj1);
+        T[SG_ACM * N + c] = rm * rm * (ctj - ctj1);
+        T[SG_EM * N + c] = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j));
+        T[SG_EP * N + c] = 0.5 * (rp * rp - rm * rm) * sin(sph_th(P, j + 1));
+        T[SG_RF * N + c] = rf;
+        const double ra = sph_r(P, i), rb = sph_r(P, i + 1), rc = sph_r(P, i + 0.5);
+        const double cm = cos(sph_th(P, j - 0.5)), cp = cos(sph_th(P, j + 0.5));
+        T[SG_VT * N + c] = (rb * rb * rb - ra * ra * ra) / 3.0 * (cm - cp);
+        T[SG_BP * N + c] = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j + 0.5));
+        T[SG_BM * N + c] = 0.5 * (rb * rb - ra * ra) * sin(sph_th(P, j - 0.5));
+        T[SG_FA * N + c] = ra * ra * (cm - cp);
+        T[SG_FB * N + c] = rb * rb * (cm - cp);
+        T[SG_RC * N + c] = rc;
     }
 }
 
@@ -224,7 +250,7 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
             for (int d = 0; d < P.nd; d++) cond += (X.Gc[d][x + P.es[d]] - X.Gc[d][x]) * P.idx[d];
             R[1] = R[1] + cond;
         }
-        if (P.geom == MUSIC_GEOM_SPHERICAL) sph_assemble(P, X, ix, x, R);
+        if (P.geom == MUSIC_GEOM_SPHERICAL) sph_assemble(P, X, ix, x, c, R);
         for (int d = 0; d < P.nd && P.geom != MUSIC_GEOM_SPHERICAL; d++) {
             if (P.bc[d] == MUSIC_BC_WALL && ix[d] == 0) {
                 R[2 + d] = 0.0;
@@ -356,6 +382,13 @@ int stencil_apply(music_grid *g, int mode, const double *U, const double *aux, c
         set_error("stencil_apply: bad mode %d", mode);
         return MUSIC_E_INVAL;
     }
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int sph_geo_build(music_grid *g, cudaStream_t s)
+{
+    k_sph_geo<<<blocks_for(g->P.N), BS, 0, s>>>(g->P, g->sgeo);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
