@@ -441,26 +441,109 @@ __global__ void __launch_bounds__(BS) k_gen_rhs(GridParams P, PCG<PT> C, const P
     }
 }
 
+// One weighted-Jacobi update of the general form: the first sweep from zero,
+// later ones with the set-up's neighbour weights (wu, wl along d = 0, 1, 2,
+// their neighbours' dp in du, dl), in the preconditioner's type.  Shared by
+// the one-kernel-per-sweep and the tile-resident variant, so both round alike.
+template <typename PT>
+__device__ __forceinline__ PT gen_first(PT b, PT D)
+{
+    return (PT)(MUSIC_JACOBI_OMEGA * ((double)b / (double)D));
+}
+
+template <typename PT>
+__device__ __forceinline__ PT gen_update(int nd, const PT *wu, const PT *wl, const PT *du, const PT *dl, PT dp, PT b,
+                                         PT D)
+{
+    const PT wp = (PT)MUSIC_JACOBI_OMEGA;
+    PT off = 0;
+    for (int d = 0; d < nd; d++) {
+        off = pfma(wu[d], du[d], off);
+        off = pfma(wl[d], dl[d], off);
+    }
+    return pfma((PT)1 - wp, dp, wp * ((b + off) / D));
+}
+
 template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq)
 {
-    const double w = MUSIC_JACOBI_OMEGA;
-    const PT wp = (PT)MUSIC_JACOBI_OMEGA;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
-            dq[c] = (PT)(w * ((double)b[c] / (double)C.D[c]));
+            dq[c] = gen_first(b[c], C.D[c]);
             continue;
         }
         int ix[3];
         cell_coords(P, c, ix);
-        // weights from the set-up; the sweep in the preconditioner's type
-        PT off = 0;
+        PT wu[3], wl[3], du[3], dl[3];
         for (int d = 0; d < P.nd; d++) {
-            const long long u = cell_nb(P, ix, d, +1), l = cell_nb(P, ix, d, -1);
-            off += C.wu[d][c] * dp[u] + C.wl[d][c] * dp[l];
+            wu[d] = C.wu[d][c];
+            wl[d] = C.wl[d][c];
+            du[d] = dp[cell_nb(P, ix, d, +1)];
+            dl[d] = dp[cell_nb(P, ix, d, -1)];
         }
-        dq[c] = ((PT)1 - wp) * dp[c] + wp * ((b[c] + off) / C.D[c]);
+        dq[c] = gen_update(P.nd, wu, wl, du, dl, dp[c], b[c], C.D[c]);
     }
+}
+
+// All K sweeps of a 2-D application in one kernel (K <= GEN_KM): a CTA of
+// GTX x GTY threads stages its tile and a halo of GEN_KM + 1 cells (walls
+// clamp onto the edge cell, whose wall-face weight is zero; periodic
+// directions wrap), sweeps in shared memory on the region that shrinks by a
+// cell per sweep, and writes its tile's dp.
+constexpr int GTX = 32, GTY = 16, GEN_KM = 16, GEN_H = GEN_KM + 1;
+constexpr int GRX = GTX + 2 * GEN_H, GRY = GTY + 2 * GEN_H, GR = GRX * GRY;
+
+template <typename PT>
+__global__ void __launch_bounds__(GTX *GTY) k_gen_sweeps_tile(GridParams P, PCG<PT> C, const PT *b, PT *dpout,
+                                                              int K)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    PT *wu0 = (PT *)smraw, *wl0 = wu0 + GR, *wu1 = wl0 + GR, *wl1 = wu1 + GR, *bb = wl1 + GR, *DD = bb + GR;
+    PT *dA = DD + GR, *dB = dA + GR;
+    constexpr int NT = GTX * GTY;
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.x * GTX - GEN_H, j0 = blockIdx.y * GTY - GEN_H;
+    const int n0 = P.n[0], n1 = P.n[1];
+    const bool px = P.bc[0] == MUSIC_BC_PERIODIC, py = P.bc[1] == MUSIC_BC_PERIODIC;
+    for (int q = tid; q < GR; q += NT) {
+        const int lx = q % GRX, ly = q / GRX;
+        bool inx, iny;
+        const int x = pc_wrap(i0 + lx, n0, px, inx), y = pc_wrap(j0 + ly, n1, py, iny);
+        const long long c = x + (long long)n0 * y;
+        wu0[q] = C.wu[0][c];
+        wl0[q] = C.wl[0][c];
+        wu1[q] = C.wu[1][c];
+        wl1[q] = C.wl[1][c];
+        bb[q] = b[c];
+        DD[q] = C.D[c];
+    }
+    __syncthreads();
+    PT *src = dA, *dst = dB;
+    for (int k = 0; k < K; k++) {
+        // sweep k is valid on [k, R - k) of the staged region
+        const int lo = k, hx = GRX - k, hy = GRY - k;
+        const int wdt = hx - lo, cnt = wdt * (hy - lo);
+        for (int t = tid; t < cnt; t += NT) {
+            const int lx = lo + t % wdt, ly = lo + t / wdt, q = ly * GRX + lx;
+            if (k == 0) {
+                dst[q] = gen_first(bb[q], DD[q]);
+            } else {
+                // the staged region's edge points have no outer neighbour; they
+                // fall outside the next sweep's region and are never read
+                const PT wu[2] = {wu0[q], wu1[q]}, wl[2] = {wl0[q], wl1[q]};
+                const PT du[2] = {lx + 1 < GRX ? src[q + 1] : (PT)0, ly + 1 < GRY ? src[q + GRX] : (PT)0};
+                const PT dl[2] = {lx > 0 ? src[q - 1] : (PT)0, ly > 0 ? src[q - GRX] : (PT)0};
+                dst[q] = gen_update(2, wu, wl, du, dl, src[q], bb[q], DD[q]);
+            }
+        }
+        __syncthreads();
+        PT *tt = src;
+        src = dst;
+        dst = tt;
+    }
+    const int tx = tid % GTX, ty = tid / GTX;
+    const int gx = blockIdx.x * GTX + tx, gy = blockIdx.y * GTY + ty;
+    if (gx < n0 && gy < n1) dpout[gx + (long long)n0 * gy] = src[(ty + GEN_H) * GRX + tx + GEN_H];
 }
 
 template <typename PT>
@@ -545,6 +628,18 @@ int gen_apply(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     k_gen_rhs<PT><<<nb, BS, 0, s>>>(P, C, r, b, tau);
     CHECK_LAUNCH();
     const int K = g->desc.precond_sweeps;
+    if (P.nd == 2 && K >= 1 && K <= GEN_KM) {
+        // the sweeps in one tile-resident launch
+        constexpr size_t smem = (size_t)8 * GR * sizeof(PT);
+        static std::atomic<uint64_t> attr{0};
+        TRY(allow_dynamic_smem(k_gen_sweeps_tile<PT>, smem, attr));
+        const dim3 grid((P.n[0] + GTX - 1) / GTX, (P.n[1] + GTY - 1) / GTY);
+        k_gen_sweeps_tile<PT><<<grid, GTX * GTY, smem, s>>>(P, C, b, dp, K);
+        CHECK_LAUNCH();
+        k_gen_back<PT><<<nb, BS, 0, s>>>(P, C, r, dp, z, tau);
+        CHECK_LAUNCH();
+        return MUSIC_OK;
+    }
     for (int k = 0; k < K; k++) {
         if (k == 0)
             k_gen_jacobi<PT, true><<<nb, BS, 0, s>>>(P, C, b, dp, dq);
