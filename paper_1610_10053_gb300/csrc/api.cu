@@ -158,6 +158,7 @@ void alloc_plan(music_grid *g, F &&f)
     f(&g->V, (size_t)(d.gmres_restart + 1) * n * ks);
     for (void **p : {&g->w, &g->z, &g->u, &g->q}) f(p, n * ks);
     if (d.precond != MUSIC_PC_NONE) {
+        f(&g->Z, (size_t)d.gmres_restart * n * ks);
         for (int k = 0; k < P.nd; k++) f(&g->pa[k], N * ks);
         for (void **p : {&g->pgp, &g->php, &g->pD, &g->pb, &g->pdp, &g->pdq}) f(p, N * ks);
         if (general_grid(P)) {

@@ -430,9 +430,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                 const long long c1 = capture_launches();
                 k_ctl_solve<<<1, 1, 0, s3>>>(ctl);
                 CHECK_LAUNCH();
-                TRY(krylov_combine(g, 0, nullptr, &ctl->k, ctl->y, s3));
-                TRY(precond_apply(g, dt, g->u, g->z, 0, s3));
-                TRY(vec_axpy_k(g, g->z, g->x, s3));
+                TRY(krylov_correct(g, 0, nullptr, &ctl->k, ctl->y, s3));
                 g->glaunch[4] = nG + since(c1);
                 TRY(C.end_body(3));
             }

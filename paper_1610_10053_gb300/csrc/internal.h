@@ -78,6 +78,7 @@ struct music_grid {
     // Krylov vectors (float for mixed, double otherwise)
     void *V, *w, *z, *u;
     void *q;              // copy of the current Arnoldi vector (solver graph)
+    void *Z;              // preconditioned basis Z_j = M^-1 V_j (m vectors, Krylov type), or null
     // preconditioner (float for mixed, double otherwise)
     void *pa[3], *pgp, *php, *pD, *pb, *pdp, *pdq;
     void *prh, *pkf[3];    // general form: cell rho, face chi (spherical / conducting grids)
@@ -151,6 +152,13 @@ struct ProfScope {
     }
 };
 
+// Where the Arnoldi step stores its preconditioned vector M^-1 V_j: Z, or
+// null when the current solve is unpreconditioned (its Z is V itself).
+inline void *krylov_zstore(const music_grid *g)
+{
+    return (g->desc.precond == MUSIC_PC_NONE || g->in_scalar) ? nullptr : g->Z;
+}
+
 // error reporting (thread local)
 void set_error(const char *fmt, ...);
 #define CUDA_TRY(call)                                                                  \
@@ -207,14 +215,14 @@ int final_sum(music_grid *g, int count, double *dst, cudaStream_t s);
 // eps = sqrt(2^-52) (1 + sqrt(unorm2)) / sqrt(vnorm2), or the fixed value if > 0
 int dev_set_eps(music_grid *g, double fixed, cudaStream_t s);
 // the three CGS passes; jdev (device, or null) overrides j, which then bounds it
-int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s);        // h = V[0..j]^T w
+int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s);        // h = V[0..j]^T w; Z_j = z
 int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h; h2 = V^T w
 int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h2; wnorm2
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s);            // V_{j+1} = w * inv
 int krylov_first(music_grid *g, const double *r, double inv, cudaStream_t s);  // V_0 = r * inv
-// u = sum_{i<k} y_i V_i; kdev / ydev (device, or null) override k / y
-int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s);
-int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s);      // x += z (z Krylov type)
+// x += sum_{i<k} y_i Z_i (Z = M^-1 V stored by krylov_dots, or V when the
+// solve is unpreconditioned); kdev / ydev (device, or null) override k / y
+int krylov_correct(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s);
 int vec_sub(music_grid *g, const double *a, const double *b, double *out, cudaStream_t s); // out = a - b
 int vec_neg(music_grid *g, const double *a, double *out, cudaStream_t s);
 int newton_update(music_grid *g, const int *skip, cudaStream_t s);             // U += x, maxdrho (unless *skip)

@@ -57,13 +57,15 @@ __global__ void k_set_eps(DevScalars *ds, double fixed)
 // h_i = <V_i, w>, i <= j; accumulators in registers (NVM >= j + 1).
 template <int NVM, typename KT>
 __device__ __forceinline__ void k_dots_body(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                            double *dst, unsigned int *counter)
+                                            double *dst, unsigned int *counter, const KT *zs, KT *Zb)
 {
     __shared__ double sh[BS / 32];
     double acc[NVM];
 #pragma unroll
     for (int i = 0; i < NVM; i++) acc[i] = 0.0;
+    KT *Zj = Zb ? Zb + (long long)j * n : nullptr;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+        if (Zj) Zj[e] = zs[e];
         const double we = (double)w[e];
 #pragma unroll
         for (int i = 0; i < NVM; i++)
@@ -79,24 +81,25 @@ __device__ __forceinline__ void k_dots_body(const KT *V, const KT *w, long long 
     if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
+// With Zb, the preconditioned vector zs = M^-1 V_j is also stored as Z_j.
 template <int NVM, typename KT>
 __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                  double *dst, unsigned int *counter, const int *jdev)
+                                  double *dst, unsigned int *counter, const int *jdev, const KT *zs, KT *Zb)
 {
     if (!jdev) {
-        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
         return;
     }
     // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
     j = *jdev;
     if (j < 8)
-        k_dots_body<8, KT>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_body<8, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else if (NVM > 8 && j < 16)
-        k_dots_body<(NVM > 8 ? 16 : 8), KT>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_body<(NVM > 8 ? 16 : 8), KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else if (NVM > 16 && j < 32)
-        k_dots_body<(NVM > 16 ? 32 : 8), KT>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_body<(NVM > 16 ? 32 : 8), KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else
-        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
 }
 
 // w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
@@ -183,8 +186,10 @@ __global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long lon
         dst[e] = (KT)r[e] * rinv;
 }
 
+// x += sum_{i<k} y_i Z_i: the cycle's correction M^-1 V y from the stored
+// preconditioned basis Z_i = M^-1 V_i (V itself when unpreconditioned)
 template <typename KT>
-__global__ void __launch_bounds__(BS) k_combine(const KT *V, KT *u, long long n, int k, Coef y, const int *kdev,
+__global__ void __launch_bounds__(BS) k_correct(const KT *Z, double *x, long long n, int k, Coef y, const int *kdev,
                                                 const double *ydev)
 {
     __shared__ double ys[MUSIC_MAXV];
@@ -193,16 +198,9 @@ __global__ void __launch_bounds__(BS) k_combine(const KT *V, KT *u, long long n,
     __syncthreads();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         double s = 0.0;
-        for (int i = 0; i < k; i++) s += ys[i] * (double)V[(long long)i * n + e];
-        u[e] = (KT)s;
+        for (int i = 0; i < k; i++) s += ys[i] * (double)Z[(long long)i * n + e];
+        x[e] += (double)(KT)s;
     }
-}
-
-template <typename KT>
-__global__ void __launch_bounds__(BS) k_axpy(const KT *z, double *x, long long n)
-{
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
-        x[e] += (double)z[e];
 }
 
 __global__ void __launch_bounds__(BS) k_sub(const double *a, const double *b, double *o, long long n)
@@ -301,8 +299,10 @@ __device__ inline float dot4(const float4 a, const float4 b)
 
 template <int NVM>
 __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, long long n, int j, double *partial,
-                                                int nb, double *dst, unsigned int *counter)
+                                                int nb, double *dst, unsigned int *counter, const float *zs,
+                                                float *Zb)
 {
+    float *Zj = Zb ? Zb + (long long)j * n : nullptr;
     double acc[NVM];
 #pragma unroll
     for (int i = 0; i < NVM; i++) acc[i] = 0.0;
@@ -317,6 +317,7 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
     for (int i = 0; i < NVM; i++) run[i] = 0.0f;
     int k = 0;
     for (long long e = t0; e < n4; e += stride) {
+        if (Zj) reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
         const float4 we = reinterpret_cast<const float4 *>(w)[e];
 #pragma unroll
         for (int i = 0; i < NVM; i++)
@@ -334,6 +335,7 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
     for (int i = 0; i < NVM; i++)
         if (i <= j) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
+        if (Zj) Zj[e] = zs[e];
         const float we = w[e];
 #pragma unroll
         for (int i = 0; i < NVM; i++)
@@ -345,22 +347,23 @@ __device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, 
 
 template <int NVM>
 __global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev,
+                                  const float *zs, float *Zb)
 {
     if (!jdev) {
-        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
         return;
     }
     // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
     j = *jdev;
     if (j < 8)
-        k_dots_f32_body<8>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_f32_body<8>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else if (NVM > 8 && j < 16)
-        k_dots_f32_body<(NVM > 8 ? 16 : 8)>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_f32_body<(NVM > 8 ? 16 : 8)>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else if (NVM > 16 && j < 32)
-        k_dots_f32_body<(NVM > 16 ? 32 : 8)>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_f32_body<(NVM > 16 ? 32 : 8)>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
     else
-        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter);
+        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
 }
 
 template <int NVM, bool NORM>
@@ -459,7 +462,7 @@ __global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, lon
         k_update_f32_body<NVM, NORM>(V, w, n, j, h, partial, nb, dst, counter);
 }
 
-__global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, long long n, int k, Coef y,
+__global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, long long n, int k, Coef y,
                                                     const int *kdev, const double *ydev)
 {
     __shared__ float ys[MUSIC_MAXV];
@@ -468,8 +471,8 @@ __global__ void __launch_bounds__(BS) k_combine_f32(const float *V, float *u, lo
     __syncthreads();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         float s = 0.0f;
-        for (int i = 0; i < k; i++) s = fmaf(ys[i], V[(long long)i * n + e], s);
-        u[e] = s;
+        for (int i = 0; i < k; i++) s = fmaf(ys[i], Z[(long long)i * n + e], s);
+        x[e] += (double)s;
     }
 }
 
@@ -492,12 +495,13 @@ int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     unsigned int *cnt = &g->ds->counters[CNT_DOTS];
+    void *Zb = krylov_zstore(g);
     if (g->mixed)
         k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
-                                             g->ds->h, cnt, jdev);
+                                             g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
     else
         k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
-                                                 g->nb, g->ds->h, cnt, jdev);
+                                                 g->nb, g->ds->h, cnt, jdev, (const double *)g->z, (double *)Zb);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -608,30 +612,18 @@ int krylov_first(music_grid *g, const double *r, double beta, cudaStream_t s)
     return MUSIC_OK;
 }
 
-int krylov_combine(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s)
+int krylov_correct(music_grid *g, int k, const double *y, const int *kdev, const double *ydev, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     Coef c;
     for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (y && i < k) ? y[i] : 0.0;
     const long long n = (long long)g->n;
     const int nb = grid_blocks(n, 152 * 16);
+    const void *Z = krylov_zstore(g) ? krylov_zstore(g) : g->V;
     if (g->mixed)
-        k_combine_f32<<<nb, BS, 0, s>>>((const float *)g->V, (float *)g->u, n, k, c, kdev, ydev);
+        k_correct_f32<<<nb, BS, 0, s>>>((const float *)Z, g->x, n, k, c, kdev, ydev);
     else
-        k_combine<double><<<nb, BS, 0, s>>>((const double *)g->V, (double *)g->u, n, k, c, kdev, ydev);
-    CHECK_LAUNCH();
-    return MUSIC_OK;
-}
-
-int vec_axpy_k(music_grid *g, const void *zk, double *x, cudaStream_t s)
-{
-    ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    const long long n = (long long)g->n;
-    const int nb = grid_blocks(n, 152 * 16);
-    if (g->mixed)
-        k_axpy<float><<<nb, BS, 0, s>>>((const float *)zk, x, n);
-    else
-        k_axpy<double><<<nb, BS, 0, s>>>((const double *)zk, x, n);
+        k_correct<double><<<nb, BS, 0, s>>>((const double *)Z, g->x, n, k, c, kdev, ydev);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

@@ -124,9 +124,9 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
             for (int l = i + 1; l < k; l++) t -= H[i][l] * y[l];
             y[i] = t / H[i][i];
         }
-        TRY(krylov_combine(g, k, y, nullptr, nullptr, s));
-        TRY(precond_apply(g, dt, g->u, g->z, 0, s));
-        TRY(vec_axpy_k(g, g->z, g->x, s));
+        // x += M^-1 V y as sum_i y_i Z_i: M^-1 (a fixed number of sweeps from
+        // zero) is linear, and Z_i = M^-1 V_i is stored by each Arnoldi step
+        TRY(krylov_correct(g, k, y, nullptr, nullptr, s));
         if (resid <= target) {
             o->converged = 1;
             break;
