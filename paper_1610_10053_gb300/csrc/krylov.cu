@@ -25,7 +25,17 @@ __global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *p
 {
     __shared__ double sh[BS / 32];
     double s = 0.0;
-    for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < n; i += (long long)gridDim.x * BS) {
+    // four elements' loads in flight per step, summed in element order
+    const long long stride = (long long)gridDim.x * BS;
+    long long i = blockIdx.x * (long long)BS + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        double v[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) v[r] = (double)x[i + r * stride];
+#pragma unroll
+        for (int r = 0; r < 4; r++) s += v[r] * v[r];
+    }
+    for (; i < n; i += stride) {
         const double v = (double)x[i];
         s += v * v;
     }
@@ -54,93 +64,101 @@ __global__ void k_set_eps(DevScalars *ds, double fixed)
     ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
 }
 
-// h_i = <V_i, w>, i <= j; accumulators in registers (NVM >= j + 1).
-template <int NVM, typename KT>
-__device__ __forceinline__ void k_dots_body(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                            double *dst, unsigned int *counter, const KT *zs, KT *Zb)
+// The CGS passes hold NG accumulators per thread: a pass over more basis
+// vectors runs in groups of NG, each group one more sweep over w and its
+// NG basis vectors, so the register count (and the occupancy) does not grow
+// with the Arnoldi index.  Every group visits the thread's elements in the
+// same order, so each product is summed exactly as one sweep would sum it.
+constexpr int NG = 8;
+
+// acc[i] = <V_{i0+i}, w> over the thread's elements in FP64, i < cnt <= NG
+template <typename KT>
+__device__ __forceinline__ void dots_pass(const KT *V, const KT *w, long long n, int i0, int cnt, double acc[NG])
 {
-    __shared__ double sh[BS / 32];
-    double acc[NVM];
 #pragma unroll
-    for (int i = 0; i < NVM; i++) acc[i] = 0.0;
-    KT *Zj = Zb ? Zb + (long long)j * n : nullptr;
+    for (int i = 0; i < NG; i++) acc[i] = 0.0;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        if (Zj) Zj[e] = zs[e];
         const double we = (double)w[e];
 #pragma unroll
-        for (int i = 0; i < NVM; i++)
-            if (i <= j) acc[i] += (double)V[(long long)i * n + e] * we;
+        for (int i = 0; i < NG; i++)
+            if (i < cnt) acc[i] += (double)V[(long long)(i0 + i) * n + e] * we;
     }
+}
+
+// block partials of acc[0, cnt) into partial[(i0 + i) * nb + block]
+__device__ __forceinline__ void write_partials(const double acc[NG], int i0, int cnt, double *partial, int nb,
+                                               double *sh)
+{
 #pragma unroll
-    for (int i = 0; i < NVM; i++) {
-        if (i <= j) {
+    for (int i = 0; i < NG; i++) {
+        if (i < cnt) {
             const double r = block_sum<BS>(acc[i], sh);
-            if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
+            if (threadIdx.x == 0) partial[(long long)(i0 + i) * nb + blockIdx.x] = r;
         }
+    }
+}
+
+// h_i = <V_i, w>, i <= j (j read from jdev when given).  With Zb, the
+// preconditioned vector zs = M^-1 V_j is also stored as Z_j.
+template <typename KT>
+__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
+                                  double *dst, unsigned int *counter, const int *jdev, const KT *zs, KT *Zb)
+{
+    __shared__ double sh[BS / 32];
+    if (jdev) j = *jdev;
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    if (Zb) {
+        KT *Zj = Zb + (long long)j * n;
+        for (long long e = t0; e < n; e += stride) Zj[e] = zs[e];
+    }
+    for (int i0 = 0; i0 <= j; i0 += NG) {
+        const int cnt = min(NG, j + 1 - i0);
+        double acc[NG];
+        dots_pass<KT>(V, w, n, i0, cnt, acc);
+        write_partials(acc, i0, cnt, partial, nb, sh);
     }
     if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
-// With Zb, the preconditioned vector zs = M^-1 V_j is also stored as Z_j.
-template <int NVM, typename KT>
-__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                  double *dst, unsigned int *counter, const int *jdev, const KT *zs, KT *Zb)
-{
-    if (!jdev) {
-        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-        return;
-    }
-    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
-    j = *jdev;
-    if (j < 8)
-        k_dots_body<8, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else if (NVM > 8 && j < 16)
-        k_dots_body<(NVM > 8 ? 16 : 8), KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else if (NVM > 16 && j < 32)
-        k_dots_body<(NVM > 16 ? 32 : 8), KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else
-        k_dots_body<NVM, KT>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-}
-
 // w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
-// NORM, |w|^2 only.
-template <int NVM, bool NORM, typename KT>
-__device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, int j, const double *h,
-                                              double *partial, int nb, double *dst, unsigned int *counter)
+// NORM, |w|^2 only.  Up to NG products ride on the update sweep; beyond
+// that the updated w is swept again in groups.
+template <bool NORM, typename KT>
+__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
 {
     __shared__ double sh[BS / 32];
     __shared__ double hs[MUSIC_MAXV];
+    if (jdev) j = *jdev;
     for (int i = threadIdx.x; i <= j; i += BS) hs[i] = h[i];
     __syncthreads();
-    double acc[NORM ? 1 : NVM];
+    const bool fused = NORM || j < NG;
+    double acc[NG];
 #pragma unroll
-    for (int i = 0; i < (NORM ? 1 : NVM); i++) acc[i] = 0.0;
+    for (int i = 0; i < NG; i++) acc[i] = 0.0;
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
         double we = (double)w[e];
-#pragma unroll
-        for (int i = 0; i < NVM; i++)
-            if (i <= j) we -= hs[i] * (double)V[(long long)i * n + e];
+        for (int i = 0; i <= j; i++) we -= hs[i] * (double)V[(long long)i * n + e];
         const KT ws = (KT)we;
         w[e] = ws;
         const double wr = (double)ws;
         if (NORM) {
             acc[0] += wr * wr;
-        } else {
+        } else if (fused) {
 #pragma unroll
-            for (int i = 0; i < NVM; i++)
+            for (int i = 0; i < NG; i++)
                 if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
         }
     }
     if (NORM) {
-        const double r = block_sum<BS>(acc[0], sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = r;
+        write_partials(acc, 0, 1, partial, nb, sh);
+    } else if (fused) {
+        write_partials(acc, 0, j + 1, partial, nb, sh);
     } else {
-#pragma unroll
-        for (int i = 0; i < (NORM ? 1 : NVM); i++) {
-            if (i <= j) {
-                const double r = block_sum<BS>(acc[i], sh);
-                if (threadIdx.x == 0) partial[(long long)i * nb + blockIdx.x] = r;
-            }
+        for (int i0 = 0; i0 <= j; i0 += NG) {
+            const int cnt = min(NG, j + 1 - i0);
+            dots_pass<KT>(V, w, n, i0, cnt, acc);
+            write_partials(acc, i0, cnt, partial, nb, sh);
         }
     }
     if (last_block_done(counter)) {
@@ -149,26 +167,6 @@ __device__ __forceinline__ void k_update_body(const KT *V, KT *w, long long n, i
         else
             finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
     }
-}
-
-template <int NVM, bool NORM, typename KT>
-__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
-{
-    if (!jdev) {
-        k_update_body<NVM, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
-        return;
-    }
-    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
-    j = *jdev;
-    if (j < 8)
-        k_update_body<8, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
-    else if (NVM > 8 && j < 16)
-        k_update_body<(NVM > 8 ? 16 : 8), NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
-    else if (NVM > 16 && j < 32)
-        k_update_body<(NVM > 16 ? 32 : 8), NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
-    else
-        k_update_body<NVM, NORM, KT>(V, w, n, j, h, partial, nb, dst, counter);
 }
 
 template <typename KT>
@@ -234,19 +232,33 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
     __shared__ double sh[BS / 32];
     double m = 0.0, q = 0.0;
     float m32 = 0.0f;
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        const double u = U[e] + x[e];
+    auto one = [&](long long e, double Ue, double xe) {
+        const double u = Ue + xe;
         U[e] = u;
         q = fma(u, u, q);  // |U|^2 of the new iterate, for the next product's eps
         if (e < N) {
             if (F32) {
-                const float t = fabsf((float)x[e]) / (float)u;
+                const float t = fabsf((float)xe) / (float)u;
                 m32 = (t > m32 || t != t) ? t : m32;  // NaN-propagating, as nanmax
             } else {
-                m = nanmax(m, fabs(x[e]) / u);
+                m = nanmax(m, fabs(xe) / u);
             }
         }
+    };
+    // four elements' loads in flight per step, processed in element order
+    const long long stride = (long long)gridDim.x * BS;
+    long long e = blockIdx.x * (long long)BS + threadIdx.x;
+    for (; e + 3 * stride < n; e += 4 * stride) {
+        double Ue[4], xe[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            Ue[r] = U[e + r * stride];
+            xe[r] = x[e + r * stride];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) one(e + r * stride, Ue[r], xe[r]);
     }
+    for (; e < n; e += stride) one(e, U[e], x[e]);
     if (F32) m = (double)m32;
     const double r = block_max<BS>(m, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -297,87 +309,90 @@ __device__ inline float dot4(const float4 a, const float4 b)
     return fmaf(a.w, b.w, s);
 }
 
-template <int NVM>
-__device__ __forceinline__ void k_dots_f32_body(const float *V, const float *w, long long n, int j, double *partial,
-                                                int nb, double *dst, unsigned int *counter, const float *zs,
-                                                float *Zb)
+// acc[i] = <V_{i0+i}, w> over the thread's elements, i < cnt <= NG: FP32
+// runs of RUN float4 chunks, then FP64 (FP64 adds and conversions run at
+// 1/74 of the FP32 rate on this part)
+__device__ __forceinline__ void dots_pass_f32(const float *V, const float *w, long long n, int i0, int cnt,
+                                              double acc[NG])
 {
-    float *Zj = Zb ? Zb + (long long)j * n : nullptr;
-    double acc[NVM];
+    float run[NG];
 #pragma unroll
-    for (int i = 0; i < NVM; i++) acc[i] = 0.0;
+    for (int i = 0; i < NG; i++) {
+        acc[i] = 0.0;
+        run[i] = 0.0f;
+    }
     // float4 path only when every basis vector starts 16-byte aligned
     const long long n4 = (n & 3) ? 0 : (n >> 2);
     const long long stride = (long long)gridDim.x * BS;
     const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    // FP32 runs of RUN float4 chunks (16 elements), then FP64: FP64 adds and
-    // conversions run at 1/74 of the FP32 rate on this part
-    float run[NVM];
-#pragma unroll
-    for (int i = 0; i < NVM; i++) run[i] = 0.0f;
     int k = 0;
     for (long long e = t0; e < n4; e += stride) {
-        if (Zj) reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
         const float4 we = reinterpret_cast<const float4 *>(w)[e];
 #pragma unroll
-        for (int i = 0; i < NVM; i++)
-            if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+        for (int i = 0; i < NG; i++)
+            if (i < cnt) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)(i0 + i) * n)[e], we);
         if (++k == RUN) {
 #pragma unroll
-            for (int i = 0; i < NVM; i++) {
-                if (i <= j) acc[i] += (double)run[i];
+            for (int i = 0; i < NG; i++) {
+                if (i < cnt) acc[i] += (double)run[i];
                 run[i] = 0.0f;
             }
             k = 0;
         }
     }
 #pragma unroll
-    for (int i = 0; i < NVM; i++)
-        if (i <= j) acc[i] += (double)run[i];
+    for (int i = 0; i < NG; i++)
+        if (i < cnt) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
-        if (Zj) Zj[e] = zs[e];
         const float we = w[e];
 #pragma unroll
-        for (int i = 0; i < NVM; i++)
-            if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
+        for (int i = 0; i < NG; i++)
+            if (i < cnt) acc[i] += (double)(V[(long long)(i0 + i) * n + e] * we);
     }
-    block_partials_mixed<NVM>(acc, j + 1, partial, nb);
+}
+
+// h_i = <V_i, w>, i <= j (j read from jdev when given); with Zb, also Z_j = zs
+__global__ void __launch_bounds__(BS, 4) k_dots_f32(const float *V, const float *w, long long n, int j,
+                                                 double *partial, int nb, double *dst, unsigned int *counter,
+                                                 const int *jdev, const float *zs, float *Zb)
+{
+    if (jdev) j = *jdev;
+    if (Zb) {
+        float *Zj = Zb + (long long)j * n;
+        const long long n4 = (n & 3) ? 0 : (n >> 2);
+        const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+        for (long long e = t0; e < n4; e += stride)
+            reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
+        for (long long e = 4 * n4 + t0; e < n; e += stride) Zj[e] = zs[e];
+    }
+    for (int i0 = 0; i0 <= j; i0 += NG) {
+        const int cnt = min(NG, j + 1 - i0);
+        double acc[NG];
+        dots_pass_f32(V, w, n, i0, cnt, acc);
+        block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
+        __syncthreads();  // the block's warp sums are reused by the next group
+    }
     if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
-template <int NVM>
-__global__ void __launch_bounds__(BS) k_dots_f32(const float *V, const float *w, long long n, int j,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev,
-                                  const float *zs, float *Zb)
-{
-    if (!jdev) {
-        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-        return;
-    }
-    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
-    j = *jdev;
-    if (j < 8)
-        k_dots_f32_body<8>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else if (NVM > 8 && j < 16)
-        k_dots_f32_body<(NVM > 8 ? 16 : 8)>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else if (NVM > 16 && j < 32)
-        k_dots_f32_body<(NVM > 16 ? 32 : 8)>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-    else
-        k_dots_f32_body<NVM>(V, w, n, j, partial, nb, dst, counter, zs, Zb);
-}
-
-template <int NVM, bool NORM>
-__device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long long n, int j, const double *h,
-                                                  double *partial, int nb, double *dst, unsigned int *counter)
+// w <- w - sum_i h_i V_i (FP32), then h2_i = <V_i, w> or, with NORM, |w|^2.
+// Up to NG products ride on the update sweep; beyond that the updated w is
+// swept again in groups.
+template <bool NORM>
+__global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
+                                                   double *partial, int nb, double *dst, unsigned int *counter,
+                                                   const int *jdev)
 {
     __shared__ double sh[BS / 32];
     __shared__ float hs[MUSIC_MAXV];
+    if (jdev) j = *jdev;
     for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (float)h[i];
     __syncthreads();
-    double acc[NORM ? 1 : NVM];
-    float run[NORM ? 1 : NVM];
+    const bool fused = NORM || j < NG;
+    double acc[NG];
+    float run[NG];
 #pragma unroll
-    for (int i = 0; i < (NORM ? 1 : NVM); i++) {
+    for (int i = 0; i < NG; i++) {
         acc[i] = 0.0;
         run[i] = 0.0f;
     }
@@ -388,78 +403,64 @@ __device__ __forceinline__ void k_update_f32_body(const float *V, float *w, long
     const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
     for (long long e = t0; e < n4; e += stride) {
         float4 we = reinterpret_cast<const float4 *>(w)[e];
-#pragma unroll
-        for (int i = 0; i < NVM; i++) {
-            if (i <= j) {
-                const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
-                const float c = -hs[i];
-                we.x = fmaf(c, v.x, we.x);
-                we.y = fmaf(c, v.y, we.y);
-                we.z = fmaf(c, v.z, we.z);
-                we.w = fmaf(c, v.w, we.w);
-            }
+        for (int i = 0; i <= j; i++) {
+            const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
+            const float c = -hs[i];
+            we.x = fmaf(c, v.x, we.x);
+            we.y = fmaf(c, v.y, we.y);
+            we.z = fmaf(c, v.z, we.z);
+            we.w = fmaf(c, v.w, we.w);
         }
         reinterpret_cast<float4 *>(w)[e] = we;
         if (NORM) {
             run[0] += dot4(we, we);
-        } else {
+        } else if (fused) {
 #pragma unroll
-            for (int i = 0; i < NVM; i++)
+            for (int i = 0; i < NG; i++)
                 if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
         }
-        if (++k == RUN) {
+        if (fused && ++k == RUN) {
 #pragma unroll
-            for (int i = 0; i < (NORM ? 1 : NVM); i++) {
-                if (NORM || i <= j) acc[i] += (double)run[i];
+            for (int i = 0; i < NG; i++) {
+                if (NORM ? i == 0 : i <= j) acc[i] += (double)run[i];
                 run[i] = 0.0f;
             }
             k = 0;
         }
     }
 #pragma unroll
-    for (int i = 0; i < (NORM ? 1 : NVM); i++)
-        if (NORM || i <= j) acc[i] += (double)run[i];
+    for (int i = 0; i < NG; i++)
+        if (fused && (NORM ? i == 0 : i <= j)) acc[i] += (double)run[i];
     for (long long e = 4 * n4 + t0; e < n; e += stride) {
         float we = w[e];
-#pragma unroll
-        for (int i = 0; i < NVM; i++)
-            if (i <= j) we = fmaf(-hs[i], V[(long long)i * n + e], we);
+        for (int i = 0; i <= j; i++) we = fmaf(-hs[i], V[(long long)i * n + e], we);
         w[e] = we;
         if (NORM) {
             acc[0] += (double)(we * we);
-        } else {
+        } else if (fused) {
 #pragma unroll
-            for (int i = 0; i < NVM; i++)
+            for (int i = 0; i < NG; i++)
                 if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
         }
     }
-    block_partials_mixed<NORM ? 1 : NVM>(acc, NORM ? 1 : j + 1, partial, nb);
+    if (NORM) {
+        block_partials_mixed<1>(acc, 1, partial, nb);
+    } else if (fused) {
+        block_partials_mixed<NG>(acc, j + 1, partial, nb);
+    } else {
+        for (int i0 = 0; i0 <= j; i0 += NG) {
+            const int cnt = min(NG, j + 1 - i0);
+            dots_pass_f32(V, w, n, i0, cnt, acc);
+            block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
+            __syncthreads();
+        }
+    }
     if (last_block_done(counter)) {
         if (NORM)
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
         else
             finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
     }
-}
-
-template <int NVM, bool NORM>
-__global__ void __launch_bounds__(BS) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
-{
-    if (!jdev) {
-        k_update_f32_body<NVM, NORM>(V, w, n, j, h, partial, nb, dst, counter);
-        return;
-    }
-    // j read on the device; NVM bounds j + 1 and the narrowest width that covers it runs
-    j = *jdev;
-    if (j < 8)
-        k_update_f32_body<8, NORM>(V, w, n, j, h, partial, nb, dst, counter);
-    else if (NVM > 8 && j < 16)
-        k_update_f32_body<(NVM > 8 ? 16 : 8), NORM>(V, w, n, j, h, partial, nb, dst, counter);
-    else if (NVM > 16 && j < 32)
-        k_update_f32_body<(NVM > 16 ? 32 : 8), NORM>(V, w, n, j, h, partial, nb, dst, counter);
-    else
-        k_update_f32_body<NVM, NORM>(V, w, n, j, h, partial, nb, dst, counter);
 }
 
 __global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, long long n, int k, Coef y,
@@ -490,34 +491,33 @@ int grid_blocks(long long n, int cap)
     return (int)b;
 }
 
-template <int NVM>
 int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     unsigned int *cnt = &g->ds->counters[CNT_DOTS];
     void *Zb = krylov_zstore(g);
     if (g->mixed)
-        k_dots_f32<NVM><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
-                                             g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
+        k_dots_f32<<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
+                                        g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
     else
-        k_dots<NVM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials,
-                                                 g->nb, g->ds->h, cnt, jdev, (const double *)g->z, (double *)Zb);
+        k_dots<double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials, g->nb,
+                                            g->ds->h, cnt, jdev, (const double *)g->z, (double *)Zb);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
 
-template <int NVM, bool NORM>
+template <bool NORM>
 int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
     unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
     if (g->mixed)
-        k_update_f32<NVM, NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials,
-                                                      g->nb, dst, cnt, jdev);
+        k_update_f32<NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials, g->nb,
+                                                dst, cnt, jdev);
     else
-        k_update<NVM, NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h,
-                                                         g->partials, g->nb, dst, cnt, jdev);
+        k_update<NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h, g->partials,
+                                                    g->nb, dst, cnt, jdev);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -551,26 +551,18 @@ int dev_set_eps(music_grid *g, double fixed, cudaStream_t s)
     return MUSIC_OK;
 }
 
-// NVM (basis vectors a thread accumulates) covers j; with jdev the index is
-// read on the device and j is its upper bound.
+// With jdev the Arnoldi index is read on the device (j then bounds it).
 int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    if (j < 8) return launch_dots<8>(g, j, jdev, s);
-    if (j < 16) return launch_dots<16>(g, j, jdev, s);
-    if (j < 32) return launch_dots<32>(g, j, jdev, s);
-    return launch_dots<64>(g, j, jdev, s);
+    return launch_dots(g, j, jdev, s);
 }
 
 template <bool NORM>
 int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    const double *h = NORM ? g->ds->h2 : g->ds->h;
-    if (j < 8) return launch_update<8, NORM>(g, j, jdev, h, s);
-    if (j < 16) return launch_update<16, NORM>(g, j, jdev, h, s);
-    if (j < 32) return launch_update<32, NORM>(g, j, jdev, h, s);
-    return launch_update<64, NORM>(g, j, jdev, h, s);
+    return launch_update<NORM>(g, j, jdev, NORM ? g->ds->h2 : g->ds->h, s);
 }
 
 int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
