@@ -17,22 +17,16 @@
 #include <cstddef>
 
 #include "internal.h"
+#include "ctl.cuh"
 
 namespace {
 
 constexpr int BS = 256;
 
 // ------------------------------------------------------------ control kernels
-// All run with one thread: they are the only callers of cudaGraphSetConditional
-// for their handles, as the API requires.
-
-__device__ inline bool over_cap(SolveCtl *c, int cap)
-{
-    if (++c->guard <= cap) return false;
-    c->status = MUSIC_E_TIMEOUT;
-    c->stop = 1;
-    return true;
-}
+// All run with one thread, and each handle has one setter: these kernels, or
+// (the Arnoldi loop's) thread 0 of the norm pass's last block, which runs
+// ctl_givens.
 
 __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, int newton_max)
 {
@@ -108,58 +102,6 @@ __global__ void k_ctl_cycle_start(SolveCtl *c, const DevScalars *ds, cudaGraphCo
         }
     }
     cudaGraphSetConditional(h_go, go);
-}
-
-// Arnoldi step j: column j of H from the two CGS passes and |w|, the earlier
-// rotations, a new rotation, the residual estimate |g_{j+1}|, the next index.
-__global__ void k_ctl_givens(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_arnoldi, int m,
-                             int cap)
-{
-    const int j = c->j;
-    const double hn = sqrt(ds->wnorm2);
-    c->scale = 0;
-    if (!isfinite(hn)) {
-        c->status = MUSIC_E_NONFINITE;
-        c->stop = 1;
-    }
-    if (c->stop || over_cap(c, cap)) {
-        cudaGraphSetConditional(h_arnoldi, 0u);
-        return;
-    }
-    double *H = c->H;
-    constexpr int L = MUSIC_MAXV;
-    for (int i = 0; i <= j; i++) H[i * L + j] = __dadd_rn(ds->h[i], ds->h2[i]);
-    H[(j + 1) * L + j] = hn;
-    for (int i = 0; i < j; i++) {
-        const double t0 = H[i * L + j], t1 = H[(i + 1) * L + j];
-        H[i * L + j] = __dadd_rn(__dmul_rn(c->cs[i], t0), __dmul_rn(c->sn[i], t1));
-        H[(i + 1) * L + j] = __dadd_rn(__dmul_rn(-c->sn[i], t0), __dmul_rn(c->cs[i], t1));
-    }
-    const double a0 = H[j * L + j], a1 = H[(j + 1) * L + j];
-    if (a1 == 0.0) {
-        c->cs[j] = 1.0;
-        c->sn[j] = 0.0;
-    } else {
-        const double t = __dsqrt_rn(__dadd_rn(__dmul_rn(a0, a0), __dmul_rn(a1, a1)));
-        c->cs[j] = __ddiv_rn(a0, t);
-        c->sn[j] = __ddiv_rn(a1, t);
-    }
-    H[j * L + j] = __dadd_rn(__dmul_rn(c->cs[j], a0), __dmul_rn(c->sn[j], a1));
-    H[(j + 1) * L + j] = 0.0;
-    c->gv[j + 1] = __dmul_rn(-c->sn[j], c->gv[j]);
-    c->gv[j] = __dmul_rn(c->cs[j], c->gv[j]);
-    c->its++;
-    c->k = j + 1;
-    const double resid = fabs(c->gv[j + 1]);
-    c->resid = resid;
-    const bool done = (hn == 0.0 || resid <= c->target);
-    if (!done) {
-        c->scale = 1;
-        c->scale_idx = j + 1;
-        c->inv = __ddiv_rn(1.0, hn);
-    }
-    c->j = j + 1;
-    cudaGraphSetConditional(h_arnoldi, (!done && j + 1 < m) ? 1u : 0u);
 }
 
 // y from the k x k upper triangle: H y = g
@@ -296,10 +238,11 @@ int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphCondi
 
 // Streams capturing nested bodies; every capture still open when recording
 // fails is ended (innermost first) so the streams stay usable.
+// Streams 5 and 6 only join captures (side branches forked by events).
 struct Capture {
-    cudaStream_t st[5] = {};
+    cudaStream_t st[7] = {};
     bool open[5] = {};
-    long long mark[6] = {};
+    cudaEvent_t ev[4] = {};
     ~Capture()
     {
         for (int i = 4; i >= 0; i--) {
@@ -308,8 +251,11 @@ struct Capture {
                 cudaStreamEndCapture(st[i], &gr);
                 if (gr && i == 0) cudaGraphDestroy(gr);
             }
-            if (st[i]) cudaStreamDestroy(st[i]);
         }
+        for (int i = 6; i >= 0; i--)
+            if (st[i]) cudaStreamDestroy(st[i]);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
         cudaGetLastError();
     }
     int begin_body(int i, cudaGraph_t body)
@@ -329,6 +275,24 @@ struct Capture {
 // kernels launched by this thread since `from`
 long long since(long long from) { return capture_launches() - from; }
 
+// The preconditioner's coefficients at U on side stream a, forked from s
+// with event ef: they depend on U alone, so they overlap the residual
+// evaluation that s runs next (FP64-bound, while the set-up is a memory
+// pass).  join() merges the branch back into s.
+int fork_setup(music_grid *g, cudaStream_t s, cudaStream_t a, cudaEvent_t ef, double dt)
+{
+    CUDA_TRY(cudaEventRecord(ef, s));
+    CUDA_TRY(cudaStreamWaitEvent(a, ef, 0));
+    return precond_setup(g, g->U, dt, a);
+}
+
+int join(cudaStream_t s, cudaStream_t a, cudaEvent_t ej)
+{
+    CUDA_TRY(cudaEventRecord(ej, a));
+    CUDA_TRY(cudaStreamWaitEvent(s, ej, 0));
+    return MUSIC_OK;
+}
+
 int record(music_grid *g, Capture &C, cudaGraph_t *out)
 {
     const music_grid_desc &d = g->desc;
@@ -341,6 +305,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     SolveCtl *ctl = g->ctl;
     DevScalars *ds = g->ds;
     cudaStream_t s0 = C.st[0], s1 = C.st[1], s2 = C.st[2], s3 = C.st[3], s4 = C.st[4];
+    cudaStream_t sa0 = C.st[5], sa2 = C.st[6];
     cudaGraph_t bN, bC, bR, bG, bA, bF;
     cudaGraphConditionalHandle hN, hC, hR, hG, hA, hF;
     long long t0;
@@ -352,19 +317,21 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     // closed by the residual of the next (an IF node, skipped after the last)
     t0 = capture_launches();
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s0));
+    TRY(fork_setup(g, s0, sa0, C.ev[0], dt));
     TRY(stencil_apply(g, SM_CNF, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s0));
     // |U^n|^2 for the products' eps (each Newton update forms the next one)
     TRY(dev_norm2(g, g->U, 1, (size_t)n, &ds->unorm2, s0));
+    TRY(join(s0, sa0, C.ev[1]));
     TRY(new_handle(s0, &hN));
     k_ctl_attempt<<<1, 1, 0, s0>>>(ctl, hN, d.newton_max_its);
     CHECK_LAUNCH();
     g->glaunch[0] = since(t0);
     TRY(add_conditional(s0, hN, cudaGraphCondTypeWhile, &bN));
     {
-        // ---- Newton iteration (b = -F(U), R(U), |U| ready): coefficients, |b|
+        // ---- Newton iteration (b = -F(U), R(U), |U| and the preconditioner's
+        // coefficients at U ready): |b|
         TRY(C.begin_body(1, bN));
         t0 = capture_launches();
-        TRY(precond_setup(g, g->U, dt, s1));
         CUDA_TRY(cudaMemsetAsync(g->x, 0, n * sizeof(double), s1));
         TRY(dev_norm2(g, g->b, 1, (size_t)n, &ds->rnorm2, s1));
         TRY(new_handle(s1, &hC));
@@ -414,9 +381,9 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                     TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s4));
                     TRY(krylov_dots(g, m - 1, &ctl->j, s4));
                     TRY(krylov_update_dots(g, m - 1, &ctl->j, s4));
-                    TRY(krylov_update_norm(g, m - 1, &ctl->j, s4));
-                    k_ctl_givens<<<1, 1, 0, s4>>>(ctl, ds, hA, m, cap);
-                    CHECK_LAUNCH();
+                    // the last block of the norm pass runs the Givens rotations
+                    const GivensCtl gc{ctl, ds, hA, m, cap};
+                    TRY(krylov_update_norm(g, m - 1, &ctl->j, s4, &gc));
                     if (g->mixed)
                         k_scale_dev<float><<<nb, BS, 0, s4>>>((const float *)g->w, (float *)g->V, (float *)g->q, n,
                                                               ctl);
@@ -448,10 +415,13 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
         g->glaunch[1] = nN + since(u0);
         TRY(add_conditional(s1, hF, cudaGraphCondTypeIf, &bF));
         {
-            // b = -F(U), R(U) of the updated iterate, for the next iteration
+            // b = -F(U), R(U) and the coefficients of the updated iterate, for
+            // the next iteration
             TRY(C.begin_body(2, bF));
             const long long f0 = capture_launches();
+            TRY(fork_setup(g, s2, sa2, C.ev[2], dt));
             TRY(stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s2));
+            TRY(join(s2, sa2, C.ev[3]));
             g->glaunch[6] = since(f0);
             TRY(C.end_body(2));
         }
@@ -466,7 +436,8 @@ int record_attempt(music_grid *g)
 {
     if (!g->hctl) CUDA_TRY(cudaMallocHost((void **)&g->hctl, offsetof(SolveCtl, cs)));
     Capture C;
-    for (int i = 0; i < 5; i++) CUDA_TRY(cudaStreamCreateWithFlags(&C.st[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 7; i++) CUDA_TRY(cudaStreamCreateWithFlags(&C.st[i], cudaStreamNonBlocking));
+    for (int i = 0; i < 4; i++) CUDA_TRY(cudaEventCreateWithFlags(&C.ev[i], cudaEventDisableTiming));
     const long long before = capture_launches();
     const GridParams saved = g->P;
     g->P.dt_dev = &g->ctl->dt;

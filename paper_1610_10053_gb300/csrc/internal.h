@@ -217,7 +217,15 @@ int dev_set_eps(music_grid *g, double fixed, cudaStream_t s);
 // the three CGS passes; jdev (device, or null) overrides j, which then bounds it
 int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s);        // h = V[0..j]^T w; Z_j = z
 int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h; h2 = V^T w
-int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s); // w -= V h2; wnorm2
+// the solver graph's Arnoldi control, run by the last block of the norm pass
+struct GivensCtl {
+    SolveCtl *c;
+    const DevScalars *ds;
+    cudaGraphConditionalHandle h;  // the Arnoldi loop's condition
+    int m, cap;                    // restart length, loop-body cap
+};
+// w -= V h2; wnorm2; with gc, then the Givens rotations of the Arnoldi step
+int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc = nullptr);
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s);            // V_{j+1} = w * inv
 int krylov_first(music_grid *g, const double *r, double inv, cudaStream_t s);  // V_0 = r * inv
 // x += sum_{i<k} y_i Z_i (Z = M^-1 V stored by krylov_dots, or V when the

@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "ctl.cuh"
 
 namespace {
 
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long
 // that the updated w is swept again in groups.
 template <bool NORM, typename KT>
 __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev)
+                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev,
+                                  GivensCtl gc)
 {
     __shared__ double sh[BS / 32];
     __shared__ double hs[MUSIC_MAXV];
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, 
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
         else
             finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+        // |w| is in *dst (written by thread 0): the Arnoldi step's control
+        if (NORM && gc.c && threadIdx.x == 0) ctl_givens(gc.c, gc.ds, gc.h, gc.m, gc.cap);
     }
 }
 
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(BS, 4) k_dots_f32(const float *V, const float 
 template <bool NORM>
 __global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
                                                    double *partial, int nb, double *dst, unsigned int *counter,
-                                                   const int *jdev)
+                                                   const int *jdev, GivensCtl gc)
 {
     __shared__ double sh[BS / 32];
     __shared__ float hs[MUSIC_MAXV];
@@ -460,6 +464,8 @@ __global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, 
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
         else
             finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+        // |w| is in *dst (written by thread 0): the Arnoldi step's control
+        if (NORM && gc.c && threadIdx.x == 0) ctl_givens(gc.c, gc.ds, gc.h, gc.m, gc.cap);
     }
 }
 
@@ -507,17 +513,18 @@ int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 }
 
 template <bool NORM>
-int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s)
+int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s, const GivensCtl *gcp)
 {
+    const GivensCtl gc = gcp ? *gcp : GivensCtl{};
     const long long n = (long long)g->n;
     double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
     unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
     if (g->mixed)
         k_update_f32<NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials, g->nb,
-                                                dst, cnt, jdev);
+                                                dst, cnt, jdev, gc);
     else
         k_update<NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h, g->partials,
-                                                    g->nb, dst, cnt, jdev);
+                                                    g->nb, dst, cnt, jdev, gc);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -559,20 +566,20 @@ int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 }
 
 template <bool NORM>
-int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s)
+int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    return launch_update<NORM>(g, j, jdev, NORM ? g->ds->h2 : g->ds->h, s);
+    return launch_update<NORM>(g, j, jdev, NORM ? g->ds->h2 : g->ds->h, s, gc);
 }
 
 int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
-    return update_any<false>(g, j, jdev, s);
+    return update_any<false>(g, j, jdev, s, nullptr);
 }
 
-int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s)
+int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc)
 {
-    return update_any<true>(g, j, jdev, s);
+    return update_any<true>(g, j, jdev, s, gc);
 }
 
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
