@@ -365,9 +365,11 @@ def test_profile_counts_jv_launches():
 
 
 def test_profile_counts_every_class():
-    """Per class: one preconditioner application per Arnoldi step and per
-    cycle's correction; one residual-type evaluation per Newton iteration (the
-    first one also gives the step constant C^n of its attempt)."""
+    """Per class: one preconditioner application and one product per Arnoldi
+    step (the cycle's correction combines the stored M^-1 V_i); one
+    residual-type evaluation per Newton iteration (the first one also gives
+    the step constant C^n of its attempt); the three CGS passes of every
+    Arnoldi step."""
     p = CASES["kh_64"]().with_options(nsteps=1)
     with B().Grid(p, precision=B().MIXED) as g:
         g.set_state(p.U)
