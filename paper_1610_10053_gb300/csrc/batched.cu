@@ -343,6 +343,7 @@ struct BArgs {
 template <typename KT, int KM>
 __global__ void __launch_bounds__(NT, 1) k_batched_step(const __grid_constant__ BArgs args)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red[NT / 32];
     const BInst<KT> &I = *(const BInst<KT> *)args.p[blockIdx.x];

@@ -24,6 +24,7 @@ __device__ inline double face_u(const GridParams &P, const double *U, const int 
 __global__ void __launch_bounds__(BS) k_rows(GridParams P, const double *U, double rho_L, double rho_H,
                                              double kmode, double *rows)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     const int j = blockIdx.x;
     const double dV = P.dx[0] * P.dx[1] * (P.nd == 3 ? P.dx[2] : 1.0);
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(BS) k_rows(GridParams P, const double *U, doub
 __global__ void __launch_bounds__(BS) k_combine_rows(GridParams P, const double *rows, DevScalars *ds,
                                                       int want_diag)
 {
+    pdl_entry();
     // one block; thread t takes rows t, t + BS, ... and the block tree
     // combines them: a fixed order for a given grid
     __shared__ double sh[BS / 32];
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(BS) k_combine_rows(GridParams P, const double 
 // diffusion); the first has k_rows' expression, so both give the same rate.
 __global__ void __launch_bounds__(BS) k_rate_rows(GridParams P, const double *U, double *rows)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     const int j = blockIdx.x;
     double s[3] = {0, 0, 0};
@@ -153,6 +156,7 @@ __global__ void __launch_bounds__(BS) k_rate_rows(GridParams P, const double *U,
 
 __global__ void __launch_bounds__(BS) k_combine_rates(GridParams P, const double *rows, DevScalars *ds)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     double a[3] = {0, 0, 0};
     for (int j = threadIdx.x; j < P.n[1]; j += BS)
@@ -203,6 +207,7 @@ __device__ inline double yface_v(const GridParams &P, const double *U, int i, in
 __global__ void __launch_bounds__(BS) k_vy_error(GridParams Pf, const double *Uf, GridParams Pc, const double *Uc,
                                                  int r, double *partial, double *dst, unsigned int *counter)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     double a = 0.0, b = 0.0;
     for (long long f = blockIdx.x * (long long)BS + threadIdx.x; f < Pc.N; f += (long long)gridDim.x * BS) {
@@ -313,7 +318,8 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 NoallocScratch *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 std::mutex g_noalloc_mu;
 
-__global__ void k_copy_rate(const NoallocScratch *S, double *rate) { *rate = S->ds.rate; }
+__global__ void k_copy_rate(const NoallocScratch *S, double *rate) {
+    pdl_entry(); *rate = S->ds.rate; }
 
 }  // namespace
 

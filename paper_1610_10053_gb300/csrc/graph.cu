@@ -15,6 +15,9 @@
 // backs those bounds up and ends the attempt with MUSIC_E_TIMEOUT.
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "ctl.cuh"
@@ -30,6 +33,7 @@ constexpr int BS = 256;
 
 __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, int newton_max)
 {
+    pdl_entry();
     c->newton_it = 0;
     c->newton_its = 0;
     c->gmres_its = 0;
@@ -50,6 +54,7 @@ __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, 
 // GMRES set-up after |b|^2 -> ds->rnorm2 (b = -F(U), x = 0)
 __global__ void k_ctl_gmres(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_cycle, double rtol)
 {
+    pdl_entry();
     const double bnorm = sqrt(ds->rnorm2);
     c->bnorm = bnorm;
     c->its = 0;
@@ -74,6 +79,7 @@ __global__ void k_ctl_gmres(SolveCtl *c, const DevScalars *ds, cudaGraphConditio
 // a cycle after the first starts from the true residual b - J x
 __global__ void k_ctl_cycle_pre(SolveCtl *c, cudaGraphConditionalHandle h_restart)
 {
+    pdl_entry();
     c->cycles++;
     const unsigned r = c->cycle > 0 ? 1u : 0u;
     c->restarts += (int)r;
@@ -83,6 +89,7 @@ __global__ void k_ctl_cycle_pre(SolveCtl *c, cudaGraphConditionalHandle h_restar
 // beta = |b| (first cycle) or |b - J x| (ds->rnorm2); build the cycle or stop
 __global__ void k_ctl_cycle_start(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_go, int m)
 {
+    pdl_entry();
     const double beta = c->cycle == 0 ? c->bnorm : sqrt(ds->rnorm2);
     c->beta = beta;
     c->j = 0;
@@ -107,6 +114,7 @@ __global__ void k_ctl_cycle_start(SolveCtl *c, const DevScalars *ds, cudaGraphCo
 // y from the k x k upper triangle: H y = g
 __global__ void k_ctl_solve(SolveCtl *c)
 {
+    pdl_entry();
     constexpr int L = MUSIC_MAXV;
     const int k = c->k;
     for (int i = k - 1; i >= 0; i--) {
@@ -118,6 +126,7 @@ __global__ void k_ctl_solve(SolveCtl *c)
 
 __global__ void k_ctl_cycle_end(SolveCtl *c, cudaGraphConditionalHandle h_cycle, int max_restarts, int cap)
 {
+    pdl_entry();
     unsigned go = 0u;
     if (!c->stop && !over_cap(c, cap)) {
         if (c->resid <= c->target) {
@@ -134,6 +143,7 @@ __global__ void k_ctl_cycle_end(SolveCtl *c, cudaGraphConditionalHandle h_cycle,
 __global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_newton,
                              cudaGraphConditionalHandle h_next, int newton_max, double tol, int cap)
 {
+    pdl_entry();
     unsigned go = 0u;
     if (!c->stop && !over_cap(c, cap)) {
         c->gmres_its += c->its;
@@ -160,6 +170,7 @@ template <typename KT>
 __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double *t64, KT *V, KT *q, long long n,
                                                   const SolveCtl *c, cudaGraphConditionalHandle h_arnoldi)
 {
+    pdl_entry();
     const double *r = c->cycle == 0 ? b : t64;
     // r / beta as r times 1 / beta (formed once per CTA), as the host driver does
     __shared__ KT s_rinv;
@@ -178,6 +189,7 @@ __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double 
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_scale_dev(const KT *w, KT *V, KT *q, long long n, const SolveCtl *c)
 {
+    pdl_entry();
     if (!c->scale) return;
     KT *dst = V + (long long)c->scale_idx * n;
     const KT inv = (KT)c->inv;
@@ -236,6 +248,38 @@ int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphCondi
     return MUSIC_OK;
 }
 
+// record_attempt's status when the driver refuses the programmatic edges
+constexpr int PDL_REFUSED = 1000;
+
+// Every kernel-to-kernel edge of graph gr made programmatic: the downstream
+// kernel may launch as the upstream's blocks exit, ahead of the upstream's
+// completion, and waits for that completion (pdl_entry) before it reads
+// anything, so its launch overlaps the upstream's tail.
+int programmatic_edges(cudaGraph_t gr)
+{
+    size_t ne = 0;
+    CUDA_TRY(cudaGraphGetEdges(gr, nullptr, nullptr, nullptr, &ne));
+    if (ne == 0) return MUSIC_OK;
+    std::vector<cudaGraphNode_t> from(ne), to(ne);
+    std::vector<cudaGraphEdgeData> ed(ne);
+    CUDA_TRY(cudaGraphGetEdges(gr, from.data(), to.data(), ed.data(), &ne));
+    for (size_t i = 0; i < ne; i++) {
+        cudaGraphNodeType a, b;
+        CUDA_TRY(cudaGraphNodeGetType(from[i], &a));
+        CUDA_TRY(cudaGraphNodeGetType(to[i], &b));
+        if (a != cudaGraphNodeTypeKernel || b != cudaGraphNodeTypeKernel || ed[i].type != cudaGraphDependencyTypeDefault ||
+            ed[i].from_port != cudaGraphKernelNodePortDefault)
+            continue;
+        cudaGraphEdgeData pe;
+        memset(&pe, 0, sizeof(pe));
+        pe.from_port = cudaGraphKernelNodePortProgrammatic;
+        pe.type = cudaGraphDependencyTypeProgrammatic;
+        CUDA_TRY(cudaGraphRemoveDependencies(gr, &from[i], &to[i], &ed[i], 1));
+        CUDA_TRY(cudaGraphAddDependencies(gr, &from[i], &to[i], &pe, 1));
+    }
+    return MUSIC_OK;
+}
+
 // Streams capturing nested bodies; every capture still open when recording
 // fails is ended (innermost first) so the streams stay usable.
 // Streams 5 and 6 only join captures (side branches forked by events).
@@ -243,6 +287,7 @@ struct Capture {
     cudaStream_t st[7] = {};
     bool open[5] = {};
     cudaEvent_t ev[4] = {};
+    std::vector<cudaGraph_t> bodies;  // the conditional nodes' body graphs
     ~Capture()
     {
         for (int i = 4; i >= 0; i--) {
@@ -327,6 +372,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     CHECK_LAUNCH();
     g->glaunch[0] = since(t0);
     TRY(add_conditional(s0, hN, cudaGraphCondTypeWhile, &bN));
+    C.bodies.push_back(bN);
     {
         // ---- Newton iteration (b = -F(U), R(U), |U| and the preconditioner's
         // coefficients at U ready): |b|
@@ -339,6 +385,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
         CHECK_LAUNCH();
         long long nN = since(t0);
         TRY(add_conditional(s1, hC, cudaGraphCondTypeWhile, &bC));
+        C.bodies.push_back(bC);
         {
             // ---- GMRES cycle
             TRY(C.begin_body(2, bC));
@@ -347,6 +394,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
             k_ctl_cycle_pre<<<1, 1, 0, s2>>>(ctl, hR);
             CHECK_LAUNCH();
             TRY(add_conditional(s2, hR, cudaGraphCondTypeIf, &bR));
+            C.bodies.push_back(bR);
             {
                 // restart: t64 = b - J x, |t64|^2
                 TRY(C.begin_body(3, bR));
@@ -361,6 +409,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
             k_ctl_cycle_start<<<1, 1, 0, s2>>>(ctl, ds, hG, m);
             CHECK_LAUNCH();
             TRY(add_conditional(s2, hG, cudaGraphCondTypeIf, &bG));
+            C.bodies.push_back(bG);
             {
                 // Arnoldi process and the cycle's correction x += M^-1 V y
                 TRY(C.begin_body(3, bG));
@@ -374,6 +423,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                 CHECK_LAUNCH();
                 long long nG = since(c0);
                 TRY(add_conditional(s3, hA, cudaGraphCondTypeWhile, &bA));
+                C.bodies.push_back(bA);
                 {
                     TRY(C.begin_body(4, bA));
                     const long long a0 = capture_launches();
@@ -414,6 +464,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
         CHECK_LAUNCH();
         g->glaunch[1] = nN + since(u0);
         TRY(add_conditional(s1, hF, cudaGraphCondTypeIf, &bF));
+        C.bodies.push_back(bF);
         {
             // b = -F(U), R(U) and the coefficients of the updated iterate, for
             // the next iteration
@@ -432,7 +483,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     return MUSIC_OK;
 }
 
-int record_attempt(music_grid *g)
+int record_attempt(music_grid *g, bool pdl_ok)
 {
     if (!g->hctl) CUDA_TRY(cudaMallocHost((void **)&g->hctl, offsetof(SolveCtl, cs)));
     Capture C;
@@ -450,11 +501,23 @@ int record_attempt(music_grid *g)
         if (graph) cudaGraphDestroy(graph);
         return rc;
     }
+    // programmatic launches between consecutive kernels (MUSIC_PDL=0: plain
+    // edges); a graph the driver will not instantiate with them is recorded
+    // again without
+    const char *pv = getenv("MUSIC_PDL");
+    const bool pdl = pdl_ok && !(pv && strcmp(pv, "0") == 0);
+    int prc = MUSIC_OK;
+    if (pdl) {
+        prc = programmatic_edges(graph);
+        for (cudaGraph_t b : C.bodies)
+            if (prc == MUSIC_OK) prc = programmatic_edges(b);
+    }
     cudaGraphExec_t exec = nullptr;
-    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    const cudaError_t e = prc == MUSIC_OK ? cudaGraphInstantiate(&exec, graph, 0) : cudaErrorNotSupported;
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (pdl) return PDL_REFUSED;
         set_error("solver graph: instantiation failed: %s", cudaGetErrorString(e));
         return MUSIC_E_CUDA;
     }
@@ -474,7 +537,13 @@ void graph_release(music_grid *g)
 
 int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s)
 {
-    if (!g->gexec) TRY(record_attempt(g));
+    if (!g->gexec) {
+        const int rc = record_attempt(g, true);
+        if (rc == PDL_REFUSED)
+            TRY(record_attempt(g, false));
+        else
+            TRY(rc);
+    }
     SolveCtl *h = g->hctl;
     h->dt = dt;
     CUDA_TRY(cudaMemcpyAsync(&g->ctl->dt, &h->dt, sizeof(double), cudaMemcpyHostToDevice, s));

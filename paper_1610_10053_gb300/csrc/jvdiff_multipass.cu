@@ -123,6 +123,7 @@ struct DConst {
 // ---- lin: the values at U from the FP64 planes of the evaluation just run
 __global__ void __launch_bounds__(BS) k_lin_ext(GridParams P, const double *U, ExtScratch X, LinX L)
 {
+    pdl_entry();
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -173,6 +174,7 @@ template <typename VT>
 __global__ void __launch_bounds__(BS) k_dload(GridParams P, const double *U, const VT *v, const double *eps_dev,
                                               LinX L, DiffX D)
 {
+    pdl_entry();
     const Kc K = launch_consts(P, eps_dev, 0.0);
     if (K.eps64 == 0.0) return;
     const long long N = P.N;
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(BS) k_dload(GridParams P, const double *U, con
 // ---- B: limited slopes of rho, e and every u_q along every d, and their differences
 __global__ void __launch_bounds__(BS) k_dslopes(GridParams P, const double *eps_dev, LinX L, DiffX D)
 {
+    pdl_entry();
     const Kc K = launch_consts(P, eps_dev, 0.0);
     if (K.eps64 == 0.0) return;
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(BS) k_dslopes(GridParams P, const double *eps_
 // ---- C: upwind mass and energy fluxes on d-faces; the face velocity decides
 __global__ void __launch_bounds__(BS) k_dfluxes(GridParams P, const double *eps_dev, LinX L, DiffX D)
 {
+    pdl_entry();
     const Kc K = launch_consts(P, eps_dev, 0.0);
     if (K.eps64 == 0.0) return;
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
@@ -260,6 +264,7 @@ __global__ void __launch_bounds__(BS) k_dfluxes(GridParams P, const double *eps_
 // edges (Psi, the flux of u_d across q)
 __global__ void __launch_bounds__(BS) k_dmomentum(GridParams P, const double *eps_dev, LinX L, DiffX D)
 {
+    pdl_entry();
     const Kc K = launch_consts(P, eps_dev, 0.0);
     if (K.eps64 == 0.0) return;
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
@@ -288,6 +293,7 @@ template <typename VT>
 __global__ void __launch_bounds__(BS) k_dassemble(GridParams P, DConst C, const double *eps_dev, double hdt,
                                                   LinX L, DiffX D, const VT *v, VT *out)
 {
+    pdl_entry();
     const Kc K = launch_consts(P, eps_dev, hdt);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (K.eps64 == 0.0) {

@@ -24,6 +24,7 @@ template <typename T>
 __global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *partial, double *dst,
                                               unsigned int *counter)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     double s = 0.0;
     // four elements' loads in flight per step, summed in element order
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *p
 // dst[k] = sum_b partial[k * nb + b], one block per k, fixed order.
 __global__ void __launch_bounds__(BS) k_final_sum(const double *partial, int nb, double *dst)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     const double *p = partial + (long long)blockIdx.x * nb;
     double s = 0.0;
@@ -58,6 +60,7 @@ __global__ void __launch_bounds__(BS) k_final_sum(const double *partial, int nb,
 
 __global__ void k_set_eps(DevScalars *ds, double fixed)
 {
+    pdl_entry();
     if (fixed > 0.0) {
         ds->eps = fixed;
         return;
@@ -105,6 +108,7 @@ template <typename KT>
 __global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
                                   double *dst, unsigned int *counter, const int *jdev, const KT *zs, KT *Zb)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     if (jdev) j = *jdev;
     const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
@@ -129,6 +133,7 @@ __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, 
                                   double *partial, int nb, double *dst, unsigned int *counter, const int *jdev,
                                   GivensCtl gc)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     __shared__ double hs[MUSIC_MAXV];
     if (jdev) j = *jdev;
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, 
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long long n, double inv)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         dst[e] = (KT)((double)w[e] * inv);
 }
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long lo
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long long n, KT rinv)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         dst[e] = (KT)r[e] * rinv;
 }
@@ -194,6 +201,7 @@ template <typename KT>
 __global__ void __launch_bounds__(BS) k_correct(const KT *Z, double *x, long long n, int k, Coef y, const int *kdev,
                                                 const double *ydev)
 {
+    pdl_entry();
     __shared__ double ys[MUSIC_MAXV];
     if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += BS) ys[i] = ydev ? ydev[i] : y.c[i];
@@ -207,12 +215,14 @@ __global__ void __launch_bounds__(BS) k_correct(const KT *Z, double *x, long lon
 
 __global__ void __launch_bounds__(BS) k_sub(const double *a, const double *b, double *o, long long n)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         o[e] = a[e] - b[e];
 }
 
 __global__ void __launch_bounds__(BS) k_neg(const double *a, double *o, long long n)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         o[e] = -a[e];
 }
@@ -220,6 +230,7 @@ __global__ void __launch_bounds__(BS) k_neg(const double *a, double *o, long lon
 template <typename S, typename D>
 __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         o[e] = (D)a[e];
 }
@@ -232,6 +243,7 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
                                                       double *partial, double *dst, double *unorm2,
                                                       unsigned int *counter, const int *skip)
 {
+    pdl_entry();
     if (skip && *skip) return;  // a hard error ended the linear solve: U stays as it is
     __shared__ double sh[BS / 32];
     double m = 0.0, q = 0.0;
@@ -360,6 +372,7 @@ __global__ void __launch_bounds__(BS, 4) k_dots_f32(const float *V, const float 
                                                  double *partial, int nb, double *dst, unsigned int *counter,
                                                  const int *jdev, const float *zs, float *Zb)
 {
+    pdl_entry();
     if (jdev) j = *jdev;
     if (Zb) {
         float *Zj = Zb + (long long)j * n;
@@ -387,6 +400,7 @@ __global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, 
                                                    double *partial, int nb, double *dst, unsigned int *counter,
                                                    const int *jdev, GivensCtl gc)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     __shared__ float hs[MUSIC_MAXV];
     if (jdev) j = *jdev;
@@ -472,6 +486,7 @@ __global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, 
 __global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, long long n, int k, Coef y,
                                                     const int *kdev, const double *ydev)
 {
+    pdl_entry();
     __shared__ float ys[MUSIC_MAXV];
     if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)(ydev ? ydev[i] : y.c[i]);
@@ -485,6 +500,7 @@ __global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, l
 
 __global__ void __launch_bounds__(BS) k_scale_f32(const float *w, float *dst, long long n, float inv)
 {
+    pdl_entry();
     for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
         dst[e] = w[e] * inv;
 }

@@ -85,6 +85,7 @@ template <typename PT>
 __global__ void __launch_bounds__(BS) k_setup(GridParams P, const double *U, PC<PT> C, PcK<PT> K, PT g1, PT g2,
                                               PT tau2)
 {
+    pdl_entry();
     PT tau_unused = 0;
     block_tau(P, tau_unused, tau2);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(BS) k_setup(GridParams P, const double *U, PC<
 template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, PT *b, PT tau)
 {
+    pdl_entry();
     PT tau2_unused = 0;
     block_tau(P, tau, tau2_unused);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
@@ -136,6 +138,7 @@ template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, PcK<PT> K, const PT *b, const PT *dp,
                                                PT *dq, PT tau2)
 {
+    pdl_entry();
     PT tau_unused = 0;
     block_tau(P, tau_unused, tau2);
     const PT w = (PT)MUSIC_JACOBI_OMEGA;
@@ -166,6 +169,7 @@ template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(XT) k_jacobi_rows(GridParams P, PC<PT> C, PcK<PT> K, const PT *b, const PT *dp,
                                                     PT *dq, PT tau2)
 {
+    pdl_entry();
     PT tau_unused = 0;
     block_tau(P, tau_unused, tau2);
     const int i = blockIdx.x * XT + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
@@ -205,6 +209,7 @@ template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, const PT *dp, RT *z,
                                              PT tau, double *partial)
 {
+    pdl_entry();
     PT tau2_unused = 0;
     block_tau(P, tau, tau2_unused);
     __shared__ double sh[BS / 32];
@@ -346,6 +351,7 @@ struct PCG {
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_cell(GridParams P, const double *U, PCG<PT> C)
 {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -374,6 +380,7 @@ __global__ void __launch_bounds__(BS) k_gen_cell(GridParams P, const double *U, 
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_face(GridParams P, PCG<PT> C, double tau)
 {
+    pdl_entry();
     tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
@@ -396,6 +403,7 @@ __device__ inline void up_coeffs(const GridParams &P, const PCG<PT> &C, const in
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double tau)
 {
+    pdl_entry();
     tau = call_hdt(P, tau);
     const double tau2 = tau * tau;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
@@ -425,6 +433,7 @@ __global__ void __launch_bounds__(BS) k_gen_diag(GridParams P, PCG<PT> C, double
 template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_rhs(GridParams P, PCG<PT> C, const PT *r, PT *b, double tau)
 {
+    pdl_entry();
     tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
@@ -467,6 +476,7 @@ __device__ __forceinline__ PT gen_update(int nd, const PT *wu, const PT *wl, con
 template <typename PT, bool FIRST>
 __global__ void __launch_bounds__(BS) k_gen_jacobi(GridParams P, PCG<PT> C, const PT *b, const PT *dp, PT *dq)
 {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         if (FIRST) {
             dq[c] = gen_first(b[c], C.D[c]);
@@ -497,6 +507,7 @@ template <typename PT>
 __global__ void __launch_bounds__(GTX *GTY) k_gen_sweeps_tile(GridParams P, PCG<PT> C, const PT *b, PT *dpout,
                                                               int K)
 {
+    pdl_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
     PT *wu0 = (PT *)smraw, *wl0 = wu0 + GR, *wu1 = wl0 + GR, *wl1 = wu1 + GR, *bb = wl1 + GR, *DD = bb + GR;
     PT *dA = DD + GR, *dB = dA + GR;
@@ -550,6 +561,7 @@ template <typename PT>
 __global__ void __launch_bounds__(BS) k_gen_back(GridParams P, PCG<PT> C, const PT *r, const PT *dp, PT *z,
                                                  double tau)
 {
+    pdl_entry();
     tau = call_hdt(P, tau);
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];

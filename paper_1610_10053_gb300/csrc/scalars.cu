@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(BS) k_scalar_op(GridParams P, int ns, const do
                                                   const VIN *v, VOUT *out, double *RS_out, const double *rho,
                                                   const double *Fr, double hdt, double sign, const double *eps)
 {
+    pdl_entry();
     const double e = (MODE == SM_JV) ? *eps : 0.0;
     const QLoad<VIN> W{q, (MODE == SM_JV) ? v : nullptr, e};
     const double c_jv = (MODE == SM_JV && e != 0.0) ? hdt / e : 0.0;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(BS) k_scalar_op(GridParams P, int ns, const do
 __global__ void __launch_bounds__(BS) k_scalar_update(double *q, const double *x, const double *rho, long long N,
                                                       int ns, double *partial, double *dst, unsigned int *counter)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     double m = 0.0;
     const long long n = (long long)ns * N;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(BS) k_scalar_update(double *q, const double *x
 // c_i <- c_i / sum_j c_j per cell (cells whose sum is not positive are left)
 __global__ void __launch_bounds__(BS) k_renormalise(double *q, const double *rho, long long N, int ns)
 {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < N; c += (long long)gridDim.x * BS) {
         const double r = rho[c];
         double s = 0.0;
@@ -145,6 +148,7 @@ __global__ void __launch_bounds__(BS) k_renormalise(double *q, const double *rho
 __global__ void __launch_bounds__(BS) k_copy_fluxes(GridParams P, const double *F0, const double *F1,
                                                     const double *F2, double *out)
 {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(BS) k_copy_fluxes(GridParams P, const double *
 // one block per row normal to direction 1: 2 min(<c_1>, <c_2>) dy
 __global__ void __launch_bounds__(BS) k_mix_rows(GridParams P, const double *q, const double *rho, double *rows)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     const int j = blockIdx.x;
     const long long cnt = (long long)P.n[0] * P.n[2];
@@ -178,6 +183,7 @@ __global__ void __launch_bounds__(BS) k_mix_rows(GridParams P, const double *q, 
 
 __global__ void __launch_bounds__(BS) k_sum_rows(const double *rows, int n, double *dst)
 {
+    pdl_entry();
     __shared__ double sh[BS / 32];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += BS) s += rows[i];

@@ -25,6 +25,7 @@ template <typename VT>
 __global__ void __launch_bounds__(BS) k_load(GridParams P, const double *U, const VT *v, const double *eps,
                                              ExtScratch X)
 {
+    pdl_entry();
     const WLoad<VT> W{U, v, v ? *eps : 0.0};
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(BS) k_load(GridParams P, const double *U, cons
 // r-walls) or none
 __global__ void __launch_bounds__(BS) k_cond(GridParams P, ExtScratch X)
 {
+    pdl_entry();
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -77,6 +79,7 @@ __global__ void __launch_bounds__(BS) k_cond(GridParams P, ExtScratch X)
 
 __global__ void __launch_bounds__(BS) k_slopes(GridParams P, ExtScratch X)
 {
+    pdl_entry();
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(BS) k_slopes(GridParams P, ExtScratch X)
 
 __global__ void __launch_bounds__(BS) k_fluxes(GridParams P, ExtScratch X)
 {
+    pdl_entry();
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -117,6 +121,7 @@ __global__ void __launch_bounds__(BS) k_fluxes(GridParams P, ExtScratch X)
 
 __global__ void __launch_bounds__(BS) k_momentum(GridParams P, ExtScratch X)
 {
+    pdl_entry();
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
@@ -188,6 +193,7 @@ __device__ void sph_assemble(const GridParams &P, const ExtScratch &X, const int
 // the table of the metric, from the expressions of common.cuh
 __global__ void __launch_bounds__(BS) k_sph_geo(GridParams P, double *T)
 {
+    pdl_entry();
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
@@ -223,6 +229,7 @@ __global__ void __launch_bounds__(BS) k_assemble(GridParams P, ExtScratch X, con
                                                  double *RU_out, double hdt, double sign,
                                                  const double *eps)
 {
+    pdl_entry();
     hdt = call_hdt(P, hdt);
     double c_jv = 0.0;
     bool zero = false;

@@ -16,6 +16,7 @@ __global__ void __launch_bounds__(TX *TY) k_fused2d(GridParams P, const double *
                                                     double sign, const double *eps, double *Fr_out, float *lin,
                                                     double *Cn_out)
 {
+    pdl_entry();
     extern __shared__ double sm[];
     const double epsv = (MODE == SM_JV) ? *eps : 0.0;
     fused2d_tile<MODE, VIN, VOUT, TX, TY>(P, U, aux, v, out, RU_out, call_hdt(P, hdt), sign, epsv, blockIdx.x,
@@ -48,6 +49,7 @@ template <int TX, int TY>
 __global__ void __launch_bounds__(TX *TY, (TX * TY >= 1024) ? 1 : 1024 / (TX * TY)) k_jvdiff2d(GridParams P, JvConst K, const double *U, const float *lin,
                                                      const float *v, float *out, double hdt, const double *eps)
 {
+    pdl_entry();
     extern __shared__ double sm[];
     jvdiff2d_tile<float, float, TX, TY>(P, K, U, lin, v, out, hdt, eps, blockIdx.x, blockIdx.y, sm);
 }
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT>
                                                              PT tau2, int K, double *partial, DevScalars *ds,
                                                              PT *bg, const PT *dpin, PT *dpout)
 {
+    pdl_entry();
     extern __shared__ unsigned char smraw[];
     __shared__ double buf[TX * TY];
     const double nrm = precond2d_tile<PT, KM, TX, TY, FIRST, LAST>(P, C, r, z, tau, tau2, K, blockIdx.x,
