@@ -177,7 +177,20 @@ __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double 
     if (threadIdx.x == 0) s_rinv = (KT)(1.0 / c->beta);
     __syncthreads();
     const KT rinv = s_rinv;
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    long long e0 = t0;
+    if constexpr (sizeof(KT) == 4) {
+        // four elements a step when the vectors start 16-byte aligned
+        const long long n4 = (n & 3) ? 0 : (n >> 2);
+        for (long long e = t0; e < n4; e += stride) {
+            const double2 a = reinterpret_cast<const double2 *>(r)[2 * e], b = reinterpret_cast<const double2 *>(r)[2 * e + 1];
+            const float4 v = make_float4((float)a.x * rinv, (float)a.y * rinv, (float)b.x * rinv, (float)b.y * rinv);
+            reinterpret_cast<float4 *>(V)[e] = v;
+            reinterpret_cast<float4 *>(q)[e] = v;
+        }
+        e0 = 4 * n4 + t0;
+    }
+    for (long long e = e0; e < n; e += stride) {
         const KT v = (KT)r[e] * rinv;
         V[e] = v;
         q[e] = v;
@@ -193,7 +206,20 @@ __global__ void __launch_bounds__(BS) k_scale_dev(const KT *w, KT *V, KT *q, lon
     if (!c->scale) return;
     KT *dst = V + (long long)c->scale_idx * n;
     const KT inv = (KT)c->inv;
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    long long e0 = t0;
+    if constexpr (sizeof(KT) == 4) {
+        // four elements a step when the vectors start 16-byte aligned
+        const long long n4 = (n & 3) ? 0 : (n >> 2);
+        for (long long e = t0; e < n4; e += stride) {
+            const float4 a = reinterpret_cast<const float4 *>(w)[e];
+            const float4 v = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+            reinterpret_cast<float4 *>(dst)[e] = v;
+            reinterpret_cast<float4 *>(q)[e] = v;
+        }
+        e0 = 4 * n4 + t0;
+    }
+    for (long long e = e0; e < n; e += stride) {
         const KT v = w[e] * inv;
         dst[e] = v;
         q[e] = v;

@@ -191,8 +191,19 @@ template <typename KT>
 __global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long long n, KT rinv)
 {
     pdl_entry();
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
-        dst[e] = (KT)r[e] * rinv;
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    long long e0 = t0;
+    if constexpr (sizeof(KT) == 4) {
+        // four elements a step when the vectors start 16-byte aligned
+        const long long n4 = (n & 3) ? 0 : (n >> 2);
+        for (long long e = t0; e < n4; e += stride) {
+            const double2 a = reinterpret_cast<const double2 *>(r)[2 * e], b = reinterpret_cast<const double2 *>(r)[2 * e + 1];
+            reinterpret_cast<float4 *>(dst)[e] =
+                make_float4((float)a.x * rinv, (float)a.y * rinv, (float)b.x * rinv, (float)b.y * rinv);
+        }
+        e0 = 4 * n4 + t0;
+    }
+    for (long long e = e0; e < n; e += stride) dst[e] = (KT)r[e] * rinv;
 }
 
 // x += sum_{i<k} y_i Z_i: the cycle's correction M^-1 V y from the stored
@@ -491,7 +502,29 @@ __global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, l
     if (kdev) k = *kdev;
     for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)(ydev ? ydev[i] : y.c[i]);
     __syncthreads();
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
+    // four elements a step (float4 loads of the basis) when every vector
+    // starts 16-byte aligned; each element summed as the scalar loop sums it
+    const long long n4 = (n & 3) ? 0 : (n >> 2);
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    for (long long e = t0; e < n4; e += stride) {
+        float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int i = 0; i < k; i++) {
+            const float4 z = reinterpret_cast<const float4 *>(Z + (long long)i * n)[e];
+            s.x = fmaf(ys[i], z.x, s.x);
+            s.y = fmaf(ys[i], z.y, s.y);
+            s.z = fmaf(ys[i], z.z, s.z);
+            s.w = fmaf(ys[i], z.w, s.w);
+        }
+        double2 *x2 = reinterpret_cast<double2 *>(x) + 2 * e;
+        double2 a = x2[0], b = x2[1];
+        a.x += (double)s.x;
+        a.y += (double)s.y;
+        b.x += (double)s.z;
+        b.y += (double)s.w;
+        x2[0] = a;
+        x2[1] = b;
+    }
+    for (long long e = 4 * n4 + t0; e < n; e += stride) {
         float s = 0.0f;
         for (int i = 0; i < k; i++) s = fmaf(ys[i], Z[(long long)i * n + e], s);
         x[e] += (double)s;
@@ -501,8 +534,14 @@ __global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, l
 __global__ void __launch_bounds__(BS) k_scale_f32(const float *w, float *dst, long long n, float inv)
 {
     pdl_entry();
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
-        dst[e] = w[e] * inv;
+    // four elements a step when the vectors start 16-byte aligned
+    const long long n4 = (n & 3) ? 0 : (n >> 2);
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
+    for (long long e = t0; e < n4; e += stride) {
+        const float4 a = reinterpret_cast<const float4 *>(w)[e];
+        reinterpret_cast<float4 *>(dst)[e] = make_float4(a.x * inv, a.y * inv, a.z * inv, a.w * inv);
+    }
+    for (long long e = 4 * n4 + t0; e < n; e += stride) dst[e] = w[e] * inv;
 }
 
 int grid_blocks(long long n, int cap)

@@ -124,3 +124,21 @@ def test_graph_replays_count_their_kernels(monkeypatch):
     # host: the CFL rate kernels are counted in both; the graph adds its
     # control kernels (a few per Newton iteration and per Arnoldi step)
     assert nh < ng < nh + 3 * (sg["newton_its"] + sg["gmres_its"]) + 16
+
+
+@pytest.mark.parametrize("case", ["kh_mixed", "rt_fp64", "tgv_mixed_3d", "wedge_mixed"])
+def test_programmatic_launches_change_no_bit(case, monkeypatch):
+    """The recorded graph with programmatic kernel-to-kernel edges (the
+    default) and with plain edges (MUSIC_PDL=0) runs the same kernels on the
+    same data in the same order: every kernel waits for its predecessor's
+    completion before it reads anything."""
+    make, prec = CASES[case]
+    p = make()
+    monkeypatch.delenv("MUSIC_PDL", raising=False)
+    Ua, sa = run(p, prec, "graph", monkeypatch)
+    monkeypatch.setenv("MUSIC_PDL", "0")
+    Ub, sb = run(p, prec, "graph", monkeypatch)
+    assert np.array_equal(Ua, Ub), case
+    for a, b in zip(sa, sb):
+        for k in STAT_KEYS:
+            assert a[k] == b[k], (case, k, a[k], b[k])
