@@ -329,6 +329,10 @@ PRECOND_TRAFFIC_B_PER_CELL_2D = 84.5  # ncu, KH 2048^2, 32 x 16 tile in two stag
 RES_FLOPS_PER_CELL_2D = 143
 RES_BYTES_PER_CELL_2D = 176       # U, C^n read, F and R(U) written (4 x 8 each), linearisation planes (48)
 RES_TRAFFIC_B_PER_CELL_2D = 164.2 # ncu, F mode on KH 2048^2, 32 x 16 tile
+# ncu dram bytes of one launch of each kernel on the bench's own KH 512^2
+# workload with its tuned tiles (MUSIC_TILES=32x16,16x16,64x16,1), cold L2:
+# the launch's reads; its writes stay in the 126 MB L2 (profiles/*_kh512.md)
+TRAFFIC_KH512 = {"residual": 17.14e6, "jv": 16.89e6, "precond": 9.47e6}
 # Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
 # FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -384,9 +388,14 @@ def roofline(mixed, prob, jv_form):
                 "traffic": None, "launches": ks[name]["launches"], "ms_per_launch": per,
                 "note": "per-cell model given for the fused 2-D kernels only"}
     achieved = flops * N / (per / 1e3) / 1e12
+    if N == 512 * 512 and (name != "jv" or jv_form == "diff"):
+        traffic = TRAFFIC_KH512[name]
+        tnote = "ncu dram read+write of one launch of this workload (tuned tiles, cold L2)"
+    else:
+        traffic = tpc * N if tpc else None
+        tnote = "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells"
     return {"kernel": kern, "class": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": tpc * N if tpc else None,
-            "traffic_note": "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells",
+            "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
             "launches": ks[name]["launches"], "ms_per_launch": per, "flops_per_cell": flops,
             "timing": "CUDA events around each launch, same-length pass after the timed region",
             "peak_note": "%s peak derived from unit counts and clock (152 SM x %s x 2.07 GHz)"

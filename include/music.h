@@ -250,10 +250,10 @@ typedef struct {
     int precond_stages;       /* chosen number of launches of its sweeps */
     int n_stencil, n_precond; /* candidates timed (0 when not timed) */
     int stencil_cand[8][2];   /* candidate (TX, TY) ... */
-    int precond_cand[16][3];  /* candidate (TX, TY, stages) ... */
+    int precond_cand[24][3];  /* candidate (TX, TY, stages) ... */
     double stencil_us[8];     /* ... and their median times in microseconds (stencil:
                                  one Jacobian-free product; preconditioner: all its launches) */
-    double precond_us[16];
+    double precond_us[24];
     int residual_tile[2];     /* chosen (TX, TY) of the stencil's R, C^n and F modes, timed as
                                  one F evaluation on the same candidates as the stencil */
     double residual_us[8];
@@ -268,6 +268,10 @@ typedef struct {
  * preconditioner and sweeps): grids created later with the same
  * configuration start with these shapes.  Overwrites the grid's solver
  * scratch buffers (the state is unchanged).  Synchronises `stream`.
+ * The environment variable MUSIC_TILES=<Jv>,<residual>,<preconditioner>,
+ * <stages> (e.g. 32x16,16x16,64x16,1) pins the choice without timing when
+ * it names valid candidates for the grid (a profiler slows every launch, so
+ * timings taken under one are meaningless); the report's timings are then 0.
  * Errors: MUSIC_E_INVAL, MUSIC_E_CUDA.
  */
 int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_report *report, void *stream);

@@ -68,8 +68,8 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("tunable", ctypes.c_int), ("from_cache", ctypes.c_int), ("stencil_tile", ctypes.c_int * 2),
                 ("precond_tile", ctypes.c_int * 2), ("precond_stages", ctypes.c_int), ("n_stencil", ctypes.c_int),
                 ("n_precond", ctypes.c_int), ("stencil_cand", (ctypes.c_int * 2) * 8),
-                ("precond_cand", (ctypes.c_int * 3) * 16), ("stencil_us", ctypes.c_double * 8),
-                ("precond_us", ctypes.c_double * 16), ("residual_tile", ctypes.c_int * 2),
+                ("precond_cand", (ctypes.c_int * 3) * 24), ("stencil_us", ctypes.c_double * 8),
+                ("precond_us", ctypes.c_double * 24), ("residual_tile", ctypes.c_int * 2),
                 ("residual_us", ctypes.c_double * 8)]
 
     def as_dict(self):

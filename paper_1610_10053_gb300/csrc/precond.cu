@@ -729,6 +729,8 @@ int precond2d_dispatch(music_grid *g, double dt, const void *r, void *z, int wan
         return precond2d_apply_t<32, 16>(g, dt, r, z, want_norm, s);
     case 4:
         return precond2d_apply_t<64, 16>(g, dt, r, z, want_norm, s);
+    case 5:
+        return precond2d_apply_t<32, 32>(g, dt, r, z, want_norm, s);
     }
     set_error("preconditioner: bad tile index %d", g->ptile);
     return MUSIC_E_INVAL;

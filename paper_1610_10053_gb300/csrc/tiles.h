@@ -12,9 +12,9 @@ struct TileShape {
     int x, y;
 };
 
-constexpr int N_STENCIL_TILES = 5, N_PRECOND_TILES = 5;
+constexpr int N_STENCIL_TILES = 5, N_PRECOND_TILES = 6;
 constexpr TileShape STENCIL_TILES[N_STENCIL_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}, {32, 32}};
-constexpr TileShape PRECOND_TILES[N_PRECOND_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}, {64, 16}};
+constexpr TileShape PRECOND_TILES[N_PRECOND_TILES] = {{16, 8}, {16, 16}, {32, 8}, {32, 16}, {64, 16}, {32, 32}};
 constexpr int STENCIL_TILE_DEFAULT = 3, PRECOND_TILE_DEFAULT = 3;  // 32 x 16 both
 // the preconditioner's K sweeps run in 1, 2 or 4 launches (halo depth K + 1,
 // K/2 + 1 or K/4 + 1): one launch takes up to 16 sweeps, a split up to 8 per

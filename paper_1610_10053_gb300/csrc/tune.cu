@@ -8,6 +8,8 @@
 // of the same configuration (extent, boundaries, precision, Jv form, sweeps) in this
 // process.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -168,6 +170,30 @@ int tile_index(const TileShape *tab, int n, const int *xy)
     return -1;
 }
 
+// MUSIC_TILES=<Jv>,<residual>,<preconditioner>,<stages>, e.g.
+// 32x16,16x16,64x16,1, pins the choice instead of timing the candidates (a
+// profiler slows every launch, so a tuner run under it picks at random):
+// true when the variable names valid candidates for this grid
+bool pinned_tiles(music_grid *g)
+{
+    const char *e = getenv("MUSIC_TILES");
+    if (!e) return false;
+    int a[2], b[2], c[2], q;
+    if (sscanf(e, "%dx%d,%dx%d,%dx%d,%d", &a[0], &a[1], &b[0], &b[1], &c[0], &c[1], &q) != 7) return false;
+    const int st = tile_index(STENCIL_TILES, N_STENCIL_TILES, a), rt = tile_index(STENCIL_TILES, N_STENCIL_TILES, b);
+    const int pt = tile_index(PRECOND_TILES, N_PRECOND_TILES, c);
+    bool q_ok = false;
+    for (int i = 0; i < N_PRECOND_SPLITS; i++) q_ok |= (PRECOND_SPLITS[i] == q);
+    if (st < 0 || rt < 0 || pt < 0 || !q_ok || !split_ok(g->desc.precond_sweeps, q) ||
+        !pc_fits(PRECOND_TILES[pt], g->desc.precond_sweeps, q, g->mixed ? 4 : 8))
+        return false;
+    g->stile = st;
+    g->rtile = rt;
+    g->ptile = pt;
+    g->psplit = q;
+    return true;
+}
+
 }  // namespace
 
 void tune_lookup(music_grid *g)
@@ -205,7 +231,7 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
         }
     }
     if (!cached) {
-        const int rc = tune(g, dt, rep, (cudaStream_t)stream);
+        const int rc = pinned_tiles(g) ? MUSIC_OK : tune(g, dt, rep, (cudaStream_t)stream);
         if (rc != MUSIC_OK) {
             g->stile = s0;
             g->rtile = r0;

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 STENCIL = [(16, 8), (16, 16), (32, 8), (32, 16), (32, 32)]
-PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16), (64, 16)]
+PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16), (64, 16), (32, 32)]
 STAGES = [1, 2, 4]
 
 
@@ -139,6 +139,25 @@ def test_autotune_picks_a_candidate_and_caches_it():
         assert g3.tiles() == ((32, 16), (32, 16), 1)
 
 
+def test_autotune_pinned_by_the_environment(monkeypatch):
+    """MUSIC_TILES pins the tuner's choice (no timing); an invalid value is
+    ignored and the candidates are timed."""
+    p = I.kelvin_helmholtz(n=64, ny=48, seed=13, nsteps=1)
+    monkeypatch.setenv("MUSIC_TILES", "16x8,32x16,32x8,1")
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        rep = g.autotune(force=True)
+        assert rep["stencil_tile"] == (16, 8) and rep["residual_tile"] == (32, 16)
+        assert rep["precond_tile"] == (32, 8) and rep["precond_stages"] == 1
+        assert all(t == 0.0 for t in rep["stencil_us"].values())
+        g.step()
+    monkeypatch.setenv("MUSIC_TILES", "24x8,32x16,32x8,1")  # not a candidate
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        rep = g.autotune(force=True)
+        assert all(t > 0.0 for t in rep["stencil_us"].values())
+
+
 def test_autotune_has_nothing_to_do_on_general_grids():
     p = I.taylor_green(n=12, nsteps=1)
     with B().Grid(p, precision=B().MIXED) as g:
@@ -153,7 +172,7 @@ def test_set_tiles_rejects_other_shapes():
             g.set_tiles(stencil=(24, 8))
         assert e.value.code == 1
         with pytest.raises(B().MusicError):
-            g.set_tiles(precond=(32, 32))
+            g.set_tiles(precond=(64, 32))
         with pytest.raises(B().MusicError):
             g.set_tiles(stages=3)
 
