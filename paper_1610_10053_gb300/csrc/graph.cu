@@ -166,12 +166,26 @@ __global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditi
 // --------------------------------------------------------------- vector kernels
 // V_0 = r / beta, r = b on the first cycle and b - J x after a restart; the
 // same values go to q, the fixed-address copy the preconditioner reads.
+// With fold (the preconditioner takes the scaling, precond_folds_scale) it
+// writes r to w unscaled instead, and 1 / beta and index 0 as the scaling
+// the preconditioner applies and stores.
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double *t64, KT *V, KT *q, long long n,
-                                                  const SolveCtl *c, cudaGraphConditionalHandle h_arnoldi)
+                                                  SolveCtl *c, cudaGraphConditionalHandle h_arnoldi, KT *w,
+                                                  int fold)
 {
     pdl_entry();
     const double *r = c->cycle == 0 ? b : t64;
+    if (fold) {
+        for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
+            w[e] = (KT)r[e];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->inv = 1.0 / c->beta;
+            c->scale_idx = 0;
+            cudaGraphSetConditional(h_arnoldi, 1u);
+        }
+        return;
+    }
     // r / beta as r times 1 / beta (formed once per CTA), as the host driver does
     __shared__ KT s_rinv;
     if (threadIdx.x == 0) s_rinv = (KT)(1.0 / c->beta);
@@ -441,11 +455,15 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                 TRY(C.begin_body(3, bG));
                 const long long c0 = capture_launches();
                 TRY(new_handle(s3, &hA));
+                // on grids whose preconditioner takes the scaling of the next
+                // basis vector, it reads w and writes V_j (no scaling pass)
+                const int fold = precond_folds_scale(g) ? 1 : 0;
                 if (g->mixed)
-                    k_first_dev<float><<<nb, BS, 0, s3>>>(g->b, g->t64, (float *)g->V, (float *)g->q, n, ctl, hA);
+                    k_first_dev<float><<<nb, BS, 0, s3>>>(g->b, g->t64, (float *)g->V, (float *)g->q, n, ctl, hA,
+                                                          (float *)g->w, fold);
                 else
                     k_first_dev<double><<<nb, BS, 0, s3>>>(g->b, g->t64, (double *)g->V, (double *)g->q, n, ctl,
-                                                           hA);
+                                                           hA, (double *)g->w, fold);
                 CHECK_LAUNCH();
                 long long nG = since(c0);
                 TRY(add_conditional(s3, hA, cudaGraphCondTypeWhile, &bA));
@@ -453,20 +471,29 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                 {
                     TRY(C.begin_body(4, bA));
                     const long long a0 = capture_launches();
-                    TRY(precond_apply(g, dt, g->q, g->z, 1, s4));
+                    if (fold) {
+                        g->pc_scale = ctl;
+                        const int rc = precond_apply(g, dt, g->w, g->z, 1, s4);
+                        g->pc_scale = nullptr;
+                        TRY(rc);
+                    } else {
+                        TRY(precond_apply(g, dt, g->q, g->z, 1, s4));
+                    }
                     TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s4));
                     TRY(krylov_dots(g, m - 1, &ctl->j, s4));
                     TRY(krylov_update_dots(g, m - 1, &ctl->j, s4));
                     // the last block of the norm pass runs the Givens rotations
                     const GivensCtl gc{ctl, ds, hA, m, cap};
                     TRY(krylov_update_norm(g, m - 1, &ctl->j, s4, &gc));
-                    if (g->mixed)
-                        k_scale_dev<float><<<nb, BS, 0, s4>>>((const float *)g->w, (float *)g->V, (float *)g->q, n,
-                                                              ctl);
-                    else
-                        k_scale_dev<double><<<nb, BS, 0, s4>>>((const double *)g->w, (double *)g->V,
-                                                               (double *)g->q, n, ctl);
-                    CHECK_LAUNCH();
+                    if (!fold) {
+                        if (g->mixed)
+                            k_scale_dev<float><<<nb, BS, 0, s4>>>((const float *)g->w, (float *)g->V, (float *)g->q,
+                                                                  n, ctl);
+                        else
+                            k_scale_dev<double><<<nb, BS, 0, s4>>>((const double *)g->w, (double *)g->V,
+                                                                   (double *)g->q, n, ctl);
+                        CHECK_LAUNCH();
+                    }
                     g->glaunch[5] = since(a0);
                     TRY(C.end_body(4));
                 }

@@ -114,6 +114,11 @@ struct music_grid {
     cudaEvent_t prof_ev[2 * 256];
     int prof_cls[256];           // class (MUSIC_PROF_*) of each recorded pair
     int prof_depth;              // open ProfScope nesting
+    // set while the solver graph records an Arnoldi step on a grid whose
+    // fused 2-D preconditioner takes the scaling of the next basis vector:
+    // its input is then w * pc_scale->inv and its first stage writes
+    // V[pc_scale->scale_idx] (precond_folds_scale)
+    const SolveCtl *pc_scale;
     unsigned long long prof_launches[MUSIC_PROF_CLASSES];
     double prof_ms[MUSIC_PROF_CLASSES];
     int prof_events_made;
@@ -238,6 +243,9 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
 
 // ----- precond.cu -----
 int precond_setup(music_grid *g, const double *U, double dt, cudaStream_t s);  // frozen coefficients
+// the grid's preconditioner application is the fused 2-D kernel, which can
+// take an input scale and write the scaled input (music_grid::pc_scale)
+bool precond_folds_scale(const music_grid *g);
 // z = M^-1 r; with want_norm also |z|^2 -> ds->vnorm2 and the Jv step
 // eps(|U|, |z|) -> ds->eps
 int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s);

@@ -716,6 +716,12 @@ int precond_apply_body(music_grid *g, double dt, const void *r, void *z, int wan
 }
 }  // namespace
 
+bool precond_folds_scale(const music_grid *g)
+{
+    return g->desc.precond != MUSIC_PC_NONE && !g->in_scalar && !general_grid(g->P) && g->P.nd == 2 &&
+           g->desc.precond_sweeps <= PC_STAGED_MAXK && g->pc_variant != PC_MULTIKERNEL;
+}
+
 int precond2d_dispatch(music_grid *g, double dt, const void *r, void *z, int want_norm, cudaStream_t s)
 {
     switch (g->ptile) {

@@ -32,6 +32,9 @@ constexpr int pc_planes()
 // a * b + c with one rounding, in the preconditioner's type
 __device__ __forceinline__ float pfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double pfma(double a, double b, double c) { return fma(a, b, c); }
+// a * b rounded on its own (never contracted into a later operation)
+__device__ __forceinline__ float pmul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double pmul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // index into an interior row or column: periodic wrap, or clamp on walls
 // (coefficients of faces outside a walled domain are zero, which decouples
@@ -64,12 +67,18 @@ __device__ inline int pc_wrap(int a, int n, bool periodic, bool &inside)
 // shared memory only).  Measured on KH grids, registers pay for FP32 (512^2:
 // 61 -> 55 us per application) and cost for FP64 (226 -> 244 us), hence the
 // default.
+//
+// The input is rs * r (each entry rounded on its own, so the result equals
+// that of r scaled in memory beforehand); a FIRST stage with vout also
+// writes that scaled input of its tile to vout (the solver graph's next
+// Arnoldi vector, formed here instead of by a separate pass).
 template <typename PT, int KM, int TX = PTX, int TY = PTY, bool FIRST = true, bool LAST = true,
           int MAXCPT = (sizeof(PT) == 4 ? 8 : 0)>
 __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT *r, PT *z, PT tau, PT tau2, int K,
                                  int bx, int by, unsigned char *smraw, PT *bg = nullptr, const PT *dpin = nullptr,
-                                 PT *dpout = nullptr)
+                                 PT *dpout = nullptr, PT rs = (PT)1, PT *vout = nullptr)
 {
+    auto rin = [&](long long i) { return pmul_rn(r[i], rs); };
     constexpr int NT = TX * TY, H = KM + 1, RX = TX + 2 * H, RY = TY + 2 * H, R = RX * RY;
     // staged cells per thread; with at most MAXCPT the sweeps run from registers
     constexpr int CPT = (R + NT - 1) / NT;
@@ -124,9 +133,9 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             const long long cx = xp + (long long)n0 * y, cy = x + (long long)n0 * yp;
             const PT axp = inxp ? C.a[0][cx] : (PT)0, ayp = inyp ? C.a[1][cy] : (PT)0;
             const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
-            PT divm = (axp * r[2 * N + cx] - axm * r[2 * N + c]) * ix0;
-            divm += (ayp * r[3 * N + cy] - aym * r[3 * N + c]) * ix1;
-            bq = gm1 * r[N + c] / C.gp[c] - tau * divm;
+            PT divm = (axp * rin(2 * N + cx) - axm * rin(2 * N + c)) * ix0;
+            divm += (ayp * rin(3 * N + cy) - aym * rin(3 * N + c)) * ix1;
+            bq = gm1 * rin(N + c) / C.gp[c] - tau * divm;
             // a first stage that is not the last hands its tile's right-hand side on
             if (!LAST && lx >= H && lx < H + TX && ly >= H && ly < H + TY && i0 + lx < n0 && j0 + ly < n1)
                 bg[(i0 + lx) + (long long)n0 * (j0 + ly)] = bq;
@@ -136,6 +145,11 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     __syncthreads();
     const int tx = tid % TX, ty = tid / TX;
     const int gx = bx * TX + tx, gy = by * TY + ty;
+    if (FIRST && vout && gx < n0 && gy < n1) {
+        const long long c = gx + (long long)n0 * gy;
+#pragma unroll
+        for (int k = 0; k < 4; k++) vout[k * N + c] = rin(k * N + c);
+    }
     PT *src = dA, *dst = dB;
     // one Jacobi update of cell q from dp in `src`: the same operations, in
     // the same order, in both variants below
@@ -227,10 +241,10 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         const PT dp = (K > 0) ? src[q] : (PT)0;
         const PT dpxm = (K > 0) ? src[q - 1] : (PT)0, dpxp = (K > 0) ? src[q + 1] : (PT)0;
         const PT dpym = (K > 0) ? src[q - RX] : (PT)0, dpyp = (K > 0) ? src[q + RX] : (PT)0;
-        const PT mx_own = wlx ? r[2 * N + c] : r[2 * N + c] - tau * (dp - dpxm) * ix0;
-        const PT my_own = wly ? r[3 * N + c] : r[3 * N + c] - tau * (dp - dpym) * ix1;
-        const PT mxp = wux ? (PT)0 : r[2 * N + cxp] - tau * (dpxp - dp) * ix0;
-        const PT myp = wuy ? (PT)0 : r[3 * N + cyp] - tau * (dpyp - dp) * ix1;
+        const PT mx_own = wlx ? rin(2 * N + c) : rin(2 * N + c) - tau * (dp - dpxm) * ix0;
+        const PT my_own = wly ? rin(3 * N + c) : rin(3 * N + c) - tau * (dp - dpym) * ix1;
+        const PT mxp = wux ? (PT)0 : rin(2 * N + cxp) - tau * (dpxp - dp) * ix0;
+        const PT myp = wuy ? (PT)0 : rin(3 * N + cyp) - tau * (dpyp - dp) * ix1;
         const PT mxm = wlx ? (PT)0 : mx_own, mym = wly ? (PT)0 : my_own;
         PT divm = (mxp - mxm) * ix0;
         divm += (myp - mym) * ix1;
@@ -250,8 +264,8 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
         }
         PT divu = (axp * mxp - axm * mxm) * ix0;
         divu += (ayp * myp - aym * mym) * ix1;
-        const PT zr = r[c] - tau * divm;
-        const PT ze = r[N + c] - tau * C.hp[c] * divu;
+        const PT zr = rin(c) - tau * divm;
+        const PT ze = rin(N + c) - tau * C.hp[c] * divu;
         z[c] = zr;
         z[N + c] = ze;
         z[2 * N + c] = mx_own;

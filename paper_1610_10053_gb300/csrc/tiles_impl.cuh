@@ -82,16 +82,25 @@ int launch_jvdiff2d(music_grid *g, const double *U, const float *v, float *out, 
 // redundant halo work.  |z|^2 is reduced on the tile-independent
 // decomposition, and the last block finishes it and the finite-difference
 // step of the Jv that follows.
+// With sc (the solver graph's control), the input is r * sc->inv and the
+// first stage writes it to basis vector sc->scale_idx of Vb (nV entries each).
 template <typename PT, int KM, int TX, int TY, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z, PT tau,
                                                              PT tau2, int K, double *partial, DevScalars *ds,
-                                                             PT *bg, const PT *dpin, PT *dpout)
+                                                             PT *bg, const PT *dpin, PT *dpout, const SolveCtl *sc,
+                                                             PT *Vb, long long nV)
 {
     pdl_entry();
     extern __shared__ unsigned char smraw[];
     __shared__ double buf[TX * TY];
+    PT rs = (PT)1;
+    PT *vout = nullptr;
+    if (sc) {
+        rs = (PT)sc->inv;
+        if (FIRST) vout = Vb + (long long)sc->scale_idx * nV;
+    }
     const double nrm = precond2d_tile<PT, KM, TX, TY, FIRST, LAST>(P, C, r, z, tau, tau2, K, blockIdx.x,
-                                                                   blockIdx.y, smraw, bg, dpin, dpout);
+                                                                   blockIdx.y, smraw, bg, dpin, dpout, rs, vout);
     if (LAST && partial) {
         norm_partials<TX, TY>(P, nrm, blockIdx.x, blockIdx.y, partial, buf);
         if (last_block_done(&ds->counters[CNT_PRECOND])) {
@@ -119,7 +128,7 @@ int launch_pc_stage(music_grid *g, double dt, const PT *r, PT *z, int K, int wan
     C.hp = (PT *)g->php;
     C.D = (PT *)g->pD;
     kern<<<grid, TX * TY, smem, s>>>(P, C, r, z, (PT)tau, (PT)(tau * tau), K, want_norm ? g->partials : nullptr,
-                                     g->ds, (PT *)g->pb, dpin, dpout);
+                                     g->ds, (PT *)g->pb, dpin, dpout, g->pc_scale, (PT *)g->V, (long long)g->n);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
