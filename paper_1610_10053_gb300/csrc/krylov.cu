@@ -1,11 +1,13 @@
 // Vector kernels of the GMRES / Newton loop (Saad & Schultz 1986, cited in
 // Sec. 2): classical Gram-Schmidt with one re-orthogonalisation, each pass a
-// single sweep over w and the basis with FP64 accumulation; norms; the
-// Newton update with its density-correction test.
+// sweep over w and up to eight basis vectors (more in further sweeps) with
+// FP64 accumulation; norms; the cycle's correction from the stored
+// preconditioned basis; the Newton update with its density-correction test.
 //
 // Reductions are two-stage and deterministic: every block writes one partial
-// per quantity, then one block per quantity sums the partials in block order.
-// The block count per grid is fixed, so results do not depend on timing.
+// per quantity, then the last block to finish sums the partials in block
+// order.  The block count per grid is fixed, so results do not depend on
+// timing.
 #include <cmath>
 
 #include "internal.h"
