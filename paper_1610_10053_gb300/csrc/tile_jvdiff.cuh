@@ -182,15 +182,26 @@ __device__ void jvdiff2d_tile(const GridParams &P, const JvConst &K, const doubl
         // ---- phase 1 (plane tiles): values at U, the direction's entries
         // periodic images by repeated shifts: the staged region overhangs
         // the grid by less than one tile on either side
+        // (the wrapped column and row offset of every staged point, formed
+        // once per CTA)
         const int n0 = P.n[0], n1 = P.n[1];
-        auto cidx = [&](int lx, int ly) {
-            int gx = i0 + lx, gy = j0 + ly;
-            while (gx < 0) gx += n0;
-            while (gx >= n0) gx -= n0;
-            while (gy < 0) gy += n1;
-            while (gy >= n1) gy -= n1;
-            return gx + (long long)n0 * gy;
-        };
+        __shared__ int s_col[RX];
+        __shared__ long long s_row[RY];
+        for (int t = tid; t < RX + RY; t += NT) {
+            if (t < RX) {
+                int gx = i0 + t;
+                while (gx < 0) gx += n0;
+                while (gx >= n0) gx -= n0;
+                s_col[t] = gx;
+            } else {
+                int gy = j0 + (t - RX);
+                while (gy < 0) gy += n1;
+                while (gy >= n1) gy -= n1;
+                s_row[t - RX] = (long long)n0 * gy;
+            }
+        }
+        __syncthreads();
+        auto cidx = [&](int lx, int ly) { return s_row[ly] + s_col[lx]; };
         auto cell_at = [&](int lx, int ly, int q) {
             const long long c = cidx(lx, ly);
             const float r = lin[LIN_R * N + c], d1 = (float)v[c];
