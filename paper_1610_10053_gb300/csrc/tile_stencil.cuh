@@ -172,24 +172,52 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     const WLoad<VIN> W{U, (MODE == SM_JV) ? v : nullptr, epsv};
 
     // ---- phase 1: cell scalars on the cross-shaped region, face velocities
+    // (a tile whose staged region lies inside the grid indexes its cells
+    // directly: no ghost, wall face or periodic image to map, so the same
+    // operations on the same values as the ghost-mapping path)
+    const bool inner = i0 >= 0 && i0 + RX <= P.n[0] && j0 >= 0 && j0 + RY <= P.n[1];
+    const long long cs1 = P.cs[1];
+    auto cix = [&](int lx, int ly) { return (long long)(i0 + lx) + cs1 * (j0 + ly); };
     auto rho_at = [&](int lx, int ly, int q) {
+        if (inner) {
+            rho[q] = W(cix(lx, ly));
+            return;
+        }
         const int ix[3] = {i0 + lx, j0 + ly, 0};
         double r, E;
         load_cell(P, W, ix, r, E);
         rho[q] = r;
     };
     auto e_at = [&](int lx, int ly, int q) {
-        const int ix[3] = {i0 + lx, j0 + ly, 0};
         double r, E;
-        load_cell(P, W, ix, r, E);
+        if (inner) {
+            const long long c = cix(lx, ly);
+            r = W(c);
+            E = W(P.N + c);
+        } else {
+            const int ix[3] = {i0 + lx, j0 + ly, 0};
+            load_cell(P, W, ix, r, E);
+        }
         ee[q] = E / r;
         pp[q] = P.gm1 * E;
     };
     auto u_at = [&](int lx, int ly, int q) {
+        if (inner) {
+            const long long c = cix(lx, ly);
+            const double rbar = 0.5 * (W(c - 1) + W(c));
+            uu[q] = W(2 * P.N + c) / rbar;
+            return;
+        }
         const int ix[3] = {i0 + lx, j0 + ly, 0};
         uu[q] = face_velocity(P, W, ix, 0);
     };
     auto v_at = [&](int lx, int ly, int q) {
+        if (inner) {
+            const long long c = cix(lx, ly);
+            const double rbar = 0.5 * (W(c - cs1) + W(c));
+            vv[q] = W(3 * P.N + c) / rbar;
+            return;
+        }
         const int ix[3] = {i0 + lx, j0 + ly, 0};
         vv[q] = face_velocity(P, W, ix, 1);
     };
