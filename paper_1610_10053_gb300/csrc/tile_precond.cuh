@@ -113,10 +113,17 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
     tau = s_c[5];
     tau2 = s_c[6];
     const PT wt2 = w * tau2;
+    // a tile whose staged region and its upper neighbours lie strictly inside
+    // the grid needs no wrap and meets no wall face: direct indices
+    const bool inner = i0 >= 1 && i0 + RX + 1 <= n0 && j0 >= 1 && j0 + RY + 1 <= n1;
     for (int q = tid; q < R; q += NT) {
         const int lx = q % RX, ly = q / RX;
-        bool inx, iny;
-        const int x = pc_wrap(i0 + lx, n0, px, inx), y = pc_wrap(j0 + ly, n1, py, iny);
+        bool inx = true, iny = true;
+        int x = i0 + lx, y = j0 + ly;
+        if (!inner) {
+            x = pc_wrap(i0 + lx, n0, px, inx);
+            y = pc_wrap(j0 + ly, n1, py, iny);
+        }
         const long long c = x + (long long)n0 * y;
         ax[q] = inx ? C.a[0][c] : (PT)0;
         ay[q] = iny ? C.a[1][c] : (PT)0;
@@ -128,8 +135,12 @@ __device__ double precond2d_tile(const GridParams &P, const PC<PT> &C, const PT 
             dA[q] = dpin[c];
         } else if (lx < RX - 1 && ly < RY - 1) {
             // right-hand side needs r_m on the upper faces: the next cells'
-            bool inxp, inyp;
-            const int xp = pc_wrap(i0 + lx + 1, n0, px, inxp), yp = pc_wrap(j0 + ly + 1, n1, py, inyp);
+            bool inxp = true, inyp = true;
+            int xp = x + 1, yp = y + 1;
+            if (!inner) {
+                xp = pc_wrap(i0 + lx + 1, n0, px, inxp);
+                yp = pc_wrap(j0 + ly + 1, n1, py, inyp);
+            }
             const long long cx = xp + (long long)n0 * y, cy = x + (long long)n0 * yp;
             const PT axp = inxp ? C.a[0][cx] : (PT)0, ayp = inyp ? C.a[1][cy] : (PT)0;
             const PT axm = inx ? C.a[0][c] : (PT)0, aym = iny ? C.a[1][c] : (PT)0;
