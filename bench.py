@@ -330,9 +330,9 @@ RES_FLOPS_PER_CELL_2D = 143
 RES_BYTES_PER_CELL_2D = 176       # U, C^n read, F and R(U) written (4 x 8 each), linearisation planes (48)
 RES_TRAFFIC_B_PER_CELL_2D = 164.2 # ncu, F mode on KH 2048^2, 32 x 16 tile
 # ncu dram bytes of one launch of each kernel on the bench's own KH 512^2
-# workload with its tuned tiles (MUSIC_TILES=32x16,16x16,64x16,1), cold L2:
+# workload with its tuned tiles (MUSIC_TILES=32x16,16x16,32x32,1), cold L2:
 # the launch's reads; its writes stay in the 126 MB L2 (profiles/*_kh512.md)
-TRAFFIC_KH512 = {"residual": 17.14e6, "jv": 16.89e6, "precond": 9.47e6}
+TRAFFIC_KH512 = {"residual": 17.04e6, "jv": 16.88e6, "precond": 9.47e6}
 # Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
 # FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
