@@ -457,7 +457,7 @@ BInst<KT> make_inst(music_grid *g)
 template <typename KT, int KM>
 int launch_batched(music_grid **grids, int count, const double *cfl, const double *dt_max, cudaStream_t s)
 {
-    // stencil tile (17 planes of 37 x 21 doubles) or preconditioner tile
+    // stencil tile (16 planes of 37 x 21 doubles) or preconditioner tile
     const size_t st = Tile2D<STX, STY>::SMEM > JvTile<STX, STY>::SMEM ? Tile2D<STX, STY>::SMEM
                                                                         : JvTile<STX, STY>::SMEM;
     const size_t pc = (size_t)6 * (PTX + 2 * (KM + 1)) * (PTY + 2 * (KM + 1)) * sizeof(KT);

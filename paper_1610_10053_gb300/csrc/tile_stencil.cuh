@@ -136,7 +136,7 @@ __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const i
 //   5 the residuals of the tile's cells, written per mode (coalesced in x).
 template <int TX, int TY>
 struct Tile2D {
-    static constexpr int RX = TX + 5, RY = TY + 5, R = RX * RY, NARR = 17;
+    static constexpr int RX = TX + 5, RY = TY + 5, R = RX * RY, NARR = 16;
     static constexpr int X0 = 3, X1 = 3 + TX, Y0 = 3, Y1 = 3 + TY;
     static constexpr size_t SMEM = (size_t)NARR * R * sizeof(double);
 };
@@ -161,10 +161,12 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     using TL = Tile2D<TX, TY>;
     constexpr int RX = TL::RX, RY = TL::RY, R = TL::R, NT = TX * TY;
     constexpr int X0 = TL::X0, X1 = TL::X1, Y0 = TL::Y0, Y1 = TL::Y1;
-    double *rho = sm, *ee = sm + R, *pp = sm + 2 * R, *uu = sm + 3 * R, *vv = sm + 4 * R;
-    double *srx = sm + 5 * R, *sry = sm + 6 * R, *sex = sm + 7 * R, *sey = sm + 8 * R;
-    double *sux = sm + 9 * R, *suy = sm + 10 * R, *svx = sm + 11 * R, *svy = sm + 12 * R;
-    double *Frx = sm + 13 * R, *Fry = sm + 14 * R, *FEx = sm + 15 * R, *FEy = sm + 16 * R;
+    // (no pressure plane: phase 5 forms p = (gamma - 1) E of its three cells
+    // from U again, which keeps a 16 x 16 tile at four CTAs per SM)
+    double *rho = sm, *ee = sm + R, *uu = sm + 2 * R, *vv = sm + 3 * R;
+    double *srx = sm + 4 * R, *sry = sm + 5 * R, *sex = sm + 6 * R, *sey = sm + 7 * R;
+    double *sux = sm + 8 * R, *suy = sm + 9 * R, *svx = sm + 10 * R, *svy = sm + 11 * R;
+    double *Frx = sm + 12 * R, *Fry = sm + 13 * R, *FEx = sm + 14 * R, *FEy = sm + 15 * R;
     // scalar slopes are dead after phase 3: their planes hold the momentum fluxes
     double *Phx = srx, *Phy = sry, *Psxy = sex, *Psyx = sey;
     const int i0 = bx * TX - 3, j0 = by * TY - 3;
@@ -199,7 +201,6 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
             load_cell(P, W, ix, r, E);
         }
         ee[q] = E / r;
-        pp[q] = P.gm1 * E;
     };
     auto u_at = [&](int lx, int ly, int q) {
         if (inner) {
@@ -308,6 +309,21 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
     if (gx >= P.n[0] || gy >= P.n[1]) return;
     const int q = (ty + Y0) * RX + (tx + X0);
     const double ix0 = P.idx[0], ix1 = P.idx[1];
+    // p = (gamma - 1) E of the cell offset by (dx, dy), E as phase 1 loads
+    // it; the product rounded on its own, as a stored value would be (a
+    // product contracted into the difference below would break the exact
+    // mirror symmetry of the operator)
+    auto p_at = [&](int dx, int dy) {
+        double r, E;
+        if (inner) {
+            E = W(P.N + cix(tx + X0 + dx, ty + Y0 + dy));
+        } else {
+            const int ix[3] = {gx + dx, gy + dy, 0};
+            load_cell(P, W, ix, r, E);
+        }
+        return __dmul_rn(P.gm1, E);
+    };
+    const double pc = p_at(0, 0);
     double Rv[4];
     {
         double accr = (Frx[q + 1] - Frx[q]) * ix0;
@@ -317,7 +333,7 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
         double divu = (uu[q + 1] - uu[q]) * ix0;
         divu += (vv[q + RX] - vv[q]) * ix1;
         Rv[0] = -accr;
-        Rv[1] = -acce - pp[q] * divu;
+        Rv[1] = -acce - pc * divu;
     }
     if (P.bc[0] == MUSIC_BC_WALL && gx == 0) {
         Rv[2] = 0.0;
@@ -325,7 +341,7 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
         double acc = (Phx[q] - Phx[q - 1]) * ix0;
         acc += (Psxy[q + RX] - Psxy[q]) * ix1;
         const double rbar = 0.5 * (rho[q - 1] + rho[q]);
-        Rv[2] = (-acc - (pp[q] - pp[q - 1]) * ix0) + rbar * P.g[0];
+        Rv[2] = (-acc - (pc - p_at(-1, 0)) * ix0) + rbar * P.g[0];
     }
     if (P.bc[1] == MUSIC_BC_WALL && gy == 0) {
         Rv[3] = 0.0;
@@ -333,7 +349,7 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
         double acc = (Psyx[q + 1] - Psyx[q]) * ix0;
         acc += (Phy[q] - Phy[q - RX]) * ix1;
         const double rbar = 0.5 * (rho[q - RX] + rho[q]);
-        Rv[3] = (-acc - (pp[q] - pp[q - RX]) * ix1) + rbar * P.g[1];
+        Rv[3] = (-acc - (pc - p_at(0, -1)) * ix1) + rbar * P.g[1];
     }
     const long long c = gx + (long long)P.n[0] * gy;
     if (MODE != SM_JV && Fr_out) {
