@@ -332,7 +332,9 @@ RES_TRAFFIC_B_PER_CELL_2D = 164.2 # ncu, F mode on KH 2048^2, 32 x 16 tile
 # ncu dram bytes of one launch of each kernel on the bench's own KH 512^2
 # workload with its tuned tiles (MUSIC_TILES=32x16,16x16,32x32,1), cold L2:
 # the launch's reads; its writes stay in the 126 MB L2 (profiles/*_kh512.md)
-TRAFFIC_KH512 = {"residual": 17.04e6, "jv": 16.88e6, "precond": 9.47e6}
+# (the residual kernel has changed since its capture: no figure until the
+# next one)
+TRAFFIC_KH512 = {"residual": None, "jv": 16.88e6, "precond": 9.47e6}
 # Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
 # FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -390,7 +392,8 @@ def roofline(mixed, prob, jv_form):
     achieved = flops * N / (per / 1e3) / 1e12
     if N == 512 * 512 and (name != "jv" or jv_form == "diff"):
         traffic = TRAFFIC_KH512[name]
-        tnote = "ncu dram read+write of one launch of this workload (tuned tiles, cold L2)"
+        tnote = ("ncu dram read+write of one launch of this workload (tuned tiles, cold L2)" if traffic is not None
+                 else "kernel changed since its last ncu capture (17.04 MB a launch before the change)")
     else:
         traffic = tpc * N if tpc else None
         tnote = "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells"
