@@ -60,3 +60,17 @@ def test_fp64_form_product_uses_the_fp64_peak(bench):
     r = bench.roofline(classes(0.1, pc_ms=0.1, jv_ms=2.0), p, "diff")
     assert r["peak"] == pytest.approx(bench.FP32_PEAK_TFLOPS)
     assert r["traffic"] == bench.TRAFFIC_KH512["jv"]
+
+
+def test_job_rate_and_clock_summary(bench):
+    # replicas: every rank's cell-steps over the slowest rank's time
+    assert bench.job_rate(4, 1000, 10, 2000.0) == pytest.approx(4 * 1000 * 10 / 2.0)
+    cs = bench.ClockSampler(0)
+    cs.lines = ["2070, 2070, 900.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "garbage",
+                "2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
