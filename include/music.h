@@ -104,6 +104,12 @@ typedef struct {
     int nscalars;             /* scalars carried as partial densities c_i rho, 0..8 [0] */
     int scalar_enforce;       /* 1: the Newton test also requires max |delta(c_i rho)| / rho
                                  <= newton_tol; 0: the density test alone (Sec. 2.2) [0] */
+    /* time-step limits music_newton_step applies (Sec. 2, choice of the time
+       step; the rates are those of music_select_dt; each <= 0 is not applied,
+       and a grid with none takes the caller's dt_max as its step) */
+    double cfl_hydro;         /* CFL_hydro: dt <= cfl_hydro / max (|u_d| + c_s) / h_d (Eq. 4) */
+    double cfl_adv;           /* CFL_adv:   dt <= cfl_adv / max |u_d| / h_d */
+    double cfl_rad;           /* CFL_rad:   dt <= cfl_rad / max D / h_d^2 (radiative diffusion) */
 } music_grid_desc;
 
 typedef struct {
@@ -205,15 +211,23 @@ int music_precond_apply(music_grid *grid, const double *U, double dt, const void
                         void *stream);
 
 /*
- * Advance the grid's own state by one implicit step of size dt > 0 (pick dt
- * with music_cfl_dt, Eq. 4): Newton on the Crank-Nicolson system (Sec. 2)
- * with right-preconditioned restarted GMRES; a failed Newton solve is
- * retried at dt/2 up to max_dt_halvings times.  `st` may be NULL.
- * Synchronises `stream` (GMRES reads its scalars back every Arnoldi step).
- * Errors: MUSIC_E_INVAL (dt <= 0), MUSIC_E_NEWTON_FAIL (state restored to
- * U^n), MUSIC_E_NONFINITE, MUSIC_E_CUDA.
+ * Advance the grid's own state by one implicit step: Newton on the
+ * Crank-Nicolson system (Sec. 2) with right-preconditioned restarted GMRES.
+ * The step size is chosen from the state at the start of the step: the most
+ * restrictive of the grid's time-step limits (desc.cfl_hydro, cfl_adv,
+ * cfl_rad, reduced on the device as in music_select_dt) and of dt_max when
+ * dt_max > 0; a grid created without limits takes dt_max (> 0 then) as the
+ * step.  A failed Newton solve is retried at dt/2 up to max_dt_halvings
+ * times.  `st` (may be NULL) receives the step actually taken and the
+ * iteration counts.  Synchronises `stream` (it reads the step size and the
+ * outcome back; with the default driver the Newton and GMRES loops run on
+ * the device in a recorded CUDA graph with no other host round trip).
+ * Errors: MUSIC_E_INVAL (no limit and dt_max <= 0, or no limit applies),
+ * MUSIC_E_NEWTON_FAIL (state restored to U^n), MUSIC_E_TIMEOUT (the bound on
+ * loop bodies of an attempt was reached; state restored to U^n),
+ * MUSIC_E_NONFINITE, MUSIC_E_CUDA.
  */
-int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *stream);
+int music_newton_step(music_grid *grid, double dt_max, music_step_stats *st, void *stream);
 
 /*
  * Advance `count` grids (1..512) by one implicit step each in ONE kernel
@@ -379,16 +393,24 @@ int music_cfl_dt(music_grid *grid, double cfl, double *dt, void *stream);
  * the device is nearly full.  The paper has no counterpart: it is a service
  * variant of the reduction behind music_cfl_dt that needs no music_grid.
  *
- * Writes rate = max_cells,d ((|u_d| + c_s) / dx_d) of the state U (Eq. 4;
- * dt = cfl / rate) into *rate.  U: device, float64, nv*N in the layout above;
+ * Writes into *rate the same rate music_cfl_dt divides by: the maximum over
+ * cells and directions of (|u_d| + c_s) / h_d, u_d the mean of the cell's two
+ * face velocities and h_d the cell spacing along d (dx_d on Cartesian grids;
+ * dr radially and r_c dtheta tangentially on spherical grids); a caller
+ * takes dt = cfl / rate.  U: device, float64, nv*N in the layout above;
  * rate: device pointer to one double.  Async on `stream`; it allocates
  * nothing: its scratch is a fixed device array inside the library, sized for
  * grids of at most 16384 rows (n[1]), held by every GPU that loads the
  * library until the process exits.  The first call on each device looks up
  * that array's address; make it before any stream capture.  Calls whose work
  * overlaps on the GPU (other streams, other threads) share the array and
- * race; serialise them.  Errors: MUSIC_E_INVAL (bad descriptor or pointers,
- * n[1] > 16384), MUSIC_E_CUDA.
+ * race; serialise them.
+ * The result stays on the device, so the call cannot inspect it: a state with
+ * a NaN anywhere gives *rate = NaN and a state with no sound speed and no
+ * motion gives 0, both with MUSIC_OK (music_cfl_dt reports both as
+ * MUSIC_E_NONFINITE).  Test *rate before dividing by it.
+ * Errors: MUSIC_E_INVAL (bad descriptor or pointers, n[1] > 16384),
+ * MUSIC_E_CUDA.
  */
 int music_cfl_rate_noalloc(const music_grid_desc *desc, const double *U, double *rate, void *stream);
 

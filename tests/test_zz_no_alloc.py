@@ -20,7 +20,10 @@ torch = pytest.importorskip("torch")
 
 @pytest.mark.parametrize("make", [lambda: I.kelvin_helmholtz(n=128, seed=3),
                                   lambda: I.rayleigh_taylor(),
-                                  lambda: I.taylor_green(n=16)])
+                                  lambda: I.taylor_green(n=16),
+                                  # spherical: tangential spacing r_c dtheta
+                                  lambda: I.spherical_wedge(nr=64, nth=32, nsteps=1)],
+                         ids=["kh128", "rt64x192", "tgv16", "wedge64x32"])
 def test_noalloc_rate_matches_grid_cfl_twice(make):
     from paper_1610_10053_gb300 import binding as B
     p = make()
@@ -47,3 +50,28 @@ def test_noalloc_rejects_too_many_rows():
     rc = B.load().music_cfl_rate_noalloc(ctypes.byref(d), ctypes.c_void_p(U.data_ptr()),
                                          ctypes.c_void_p(rate.data_ptr()), None)
     assert rc == 1 and "16384" in B.last_error()
+
+
+def test_noalloc_rate_of_a_nan_state_is_nan():
+    """The rate never leaves the device, so the call cannot flag a bad state:
+    one NaN cell must come back as a NaN rate (with MUSIC_OK) for the
+    caller to test, while the grid-based call reports MUSIC_E_NONFINITE."""
+    from paper_1610_10053_gb300 import binding as B
+    p = I.kelvin_helmholtz(n=64, seed=3)
+    U = p.U.copy()
+    U[p.ncells + 777] = np.nan  # one cell's energy
+    rate = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.cfl_rate_noalloc(p, torch.from_numpy(U).cuda(), rate)
+    torch.cuda.synchronize()
+    assert np.isnan(rate.item())
+    with B.Grid(p) as g:
+        g.set_state(U)
+        with pytest.raises(B.MusicError) as e:
+            g.cfl_dt(5.0)
+        assert e.value.code == 6
+    # a finite state right after still gives the grid's rate (nothing sticks)
+    B.cfl_rate_noalloc(p, torch.from_numpy(p.U.copy()).cuda(), rate)
+    with B.Grid(p) as g:
+        g.set_state(p.U)
+        dt_ref = g.cfl_dt(5.0)
+    assert abs(5.0 / rate.item() - dt_ref) <= 1e-14 * dt_ref
