@@ -48,7 +48,9 @@ typedef struct {
                                  planes of partial densities when desc.nscalars > 0 (copied at
                                  submission) */
     int n_steps;              /* implicit steps to take (>= 0) */
-    double cfl;               /* each step: dt = cfl-limited (Eq. 4), > 0 */
+    double cfl;               /* each step: dt = cfl-limited (Eq. 4), > 0; with cfl_adv and
+                                 cfl_rad it replaces desc's time-step limits, and every step is
+                                 music_newton_step(grid, dt_max) */
     double dt_max;            /* optional cap on dt (<= 0: none) */
     double rho_L, rho_H;      /* densities of the mixing-height diagnostic */
     double cfl_adv, cfl_rad;  /* optional advective / radiative CFL limits (<= 0: none); the step

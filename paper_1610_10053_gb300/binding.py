@@ -43,6 +43,7 @@ class GridDesc(ctypes.Structure):
         ("geometry", ctypes.c_int), ("g_radial", ctypes.POINTER(ctypes.c_double)), ("conduct", ctypes.c_int),
         ("chi0", ctypes.c_double), ("flux_wall", ctypes.c_int * 3), ("lum", ctypes.c_double),
         ("nscalars", ctypes.c_int), ("scalar_enforce", ctypes.c_int),
+        ("cfl_hydro", ctypes.c_double), ("cfl_adv", ctypes.c_double), ("cfl_rad", ctypes.c_double),
     ]
 
 
@@ -218,6 +219,10 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
     d.lum = float(getattr(prob, "lum", 0.0))
     d.nscalars = int(getattr(prob, "nscalars", 0))
     d.scalar_enforce = int(getattr(prob, "scalar_enforce", 0))
+    # the problem's time-step limits: music_newton_step applies them
+    d.cfl_hydro = float(getattr(prob, "cfl", 0.0))
+    d.cfl_adv = float(getattr(prob, "cfl_adv", 0.0))
+    d.cfl_rad = float(getattr(prob, "cfl_rad", 0.0))
     for k, v in over.items():
         setattr(d, k, v)
     return d
@@ -379,9 +384,12 @@ class Grid:
         check(load().music_cfl_dt(self.h, float(cfl), ctypes.byref(out), _stream()))
         return out.value
 
-    def newton_step(self, dt: float) -> dict:
+    def newton_step(self, dt_max: float = 0.0) -> dict:
+        """One implicit step (music_newton_step): the most restrictive of the
+        grid's time-step limits and dt_max (> 0), or dt_max itself on a grid
+        created without limits (cfl_hydro = cfl_adv = cfl_rad = 0)."""
         st = StepStats()
-        check(load().music_newton_step(self.h, float(dt), ctypes.byref(st), _stream()))
+        check(load().music_newton_step(self.h, float(dt_max), ctypes.byref(st), _stream()))
         return st.as_dict()
 
     def select_dt(self, cfl_hydro: float = 0.0, cfl_adv: float = 0.0, cfl_rad: float = 0.0,
@@ -392,16 +400,10 @@ class Grid:
         check(load().music_select_dt(self.h, ctypes.byref(lim), ctypes.byref(dt), ctypes.byref(w), _stream()))
         return dt.value, w.value
 
-    def step(self, cfl: Optional[float] = None, dt_max: Optional[float] = None) -> dict:
-        cfl = self.prob.cfl if cfl is None else cfl
-        dt_max = self.prob.dt_max if dt_max is None else dt_max
-        if self.prob.cfl_adv > 0 or self.prob.cfl_rad > 0:
-            dt, _ = self.select_dt(cfl, self.prob.cfl_adv, self.prob.cfl_rad, dt_max or 0.0)
-        else:
-            dt = self.cfl_dt(cfl)
-            if dt_max and dt_max > 0 and dt > dt_max:
-                dt = dt_max
-        return self.newton_step(dt)
+    def step(self, dt_max: Optional[float] = None) -> dict:
+        """One implicit step with the grid's time-step limits (the problem's
+        cfl, cfl_adv and cfl_rad), capped by dt_max (default: the problem's)."""
+        return self.newton_step(self.prob.dt_max if dt_max is None else dt_max)
 
     def autotune(self, dt: Optional[float] = None, force: bool = False) -> dict:
         """Pick the fused kernels' tile shapes by timing (music_autotune); dt
@@ -436,9 +438,9 @@ class Grid:
         check(load().music_get_tiles(self.h, st, pt, ctypes.byref(q)))
         return tuple(st), tuple(pt), q.value
 
-    def run(self, nsteps: Optional[int] = None, cfl: Optional[float] = None, dt_max: Optional[float] = None):
+    def run(self, nsteps: Optional[int] = None, dt_max: Optional[float] = None):
         nsteps = self.prob.nsteps if nsteps is None else nsteps
-        return [self.step(cfl, dt_max) for _ in range(nsteps)]
+        return [self.step(dt_max) for _ in range(nsteps)]
 
     def profile(self, on: bool = True):
         """Time every Jv-mode stencil launch with CUDA events (see music.h)."""

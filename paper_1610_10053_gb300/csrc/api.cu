@@ -67,6 +67,10 @@ int validate(const music_grid_desc &d)
         set_error("gamma must be > 1");
         return MUSIC_E_INVAL;
     }
+    if (!std::isfinite(d.cfl_hydro) || !std::isfinite(d.cfl_adv) || !std::isfinite(d.cfl_rad)) {
+        set_error("time-step limits must be finite");
+        return MUSIC_E_INVAL;
+    }
     if (d.precision != MUSIC_FP64 && d.precision != MUSIC_MIXED) {
         set_error("precision %d unknown", d.precision);
         return MUSIC_E_INVAL;
@@ -236,6 +240,11 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     // mixed grids take the difference form of Jv; MUSIC_JV=fd keeps FP64
     const char *jv = getenv("MUSIC_JV");
     g->jv_form = (g->mixed && !(jv && strcmp(jv, "fd") == 0)) ? JV_DIFF : JV_FD;
+    // MUSIC_LOOP_CAP=<n> lowers the bound on loop bodies per Newton attempt
+    // (for tests of the bound's expiry; the default is never reached)
+    const char *lc = getenv("MUSIC_LOOP_CAP");
+    g->loop_cap = lc ? atoi(lc) : 0;
+    if (g->loop_cap < 0) g->loop_cap = 0;
     g->stile = STENCIL_TILE_DEFAULT;
     g->rtile = STENCIL_TILE_DEFAULT;
     g->ptile = PRECOND_TILE_DEFAULT;
@@ -289,6 +298,13 @@ void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 long long capture_launches() { return t_launches; }
 
 void fill_grid_params(const music_grid_desc &d, GridParams *P) { *P = make_params(d); }
+
+int loop_cap_of(const music_grid *g)
+{
+    const music_grid_desc &d = g->desc;
+    if (g->loop_cap > 0) return g->loop_cap;
+    return d.newton_max_its * (d.gmres_max_restarts + 1) * (d.gmres_restart + 3) + 64;
+}
 
 int grid_validate(music_grid_desc *d)
 {
@@ -572,11 +588,21 @@ int music_precond_apply(music_grid *grid, const double *U, double dt, const void
     return precond_apply(grid, dt, r, z, 0, s);
 }
 
-int music_newton_step(music_grid *grid, double dt, music_step_stats *st, void *stream)
+int music_newton_step(music_grid *grid, double dt_max, music_step_stats *st, void *stream)
 {
     TRY(check_grid(grid));
-    if (!(dt > 0.0) || !std::isfinite(dt)) {
-        set_error("music_newton_step: dt must be finite and > 0");
+    const music_grid_desc &d = grid->desc;
+    if (std::isnan(dt_max) || std::isinf(dt_max)) {
+        set_error("music_newton_step: dt_max must be finite");
+        return MUSIC_E_INVAL;
+    }
+    double dt = dt_max;
+    if (d.cfl_hydro > 0.0 || d.cfl_adv > 0.0 || d.cfl_rad > 0.0) {
+        // the most restrictive limit, from the state at the start of the step
+        const music_dt_limits lim = {d.cfl_hydro, d.cfl_adv, d.cfl_rad, dt_max};
+        TRY(music_select_dt(grid, &lim, &dt, nullptr, stream));
+    } else if (!(dt_max > 0.0)) {
+        set_error("music_newton_step: the grid has no time-step limit, so dt_max must be > 0");
         return MUSIC_E_INVAL;
     }
     return newton_solve(grid, dt, st, (cudaStream_t)stream);

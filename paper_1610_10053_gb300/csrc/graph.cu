@@ -385,7 +385,7 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
     const int kd = !g->mixed;
     const long long n = (long long)g->n;
     const int nb = (int)((n + BS - 1) / BS < 152 * 16 ? (n + BS - 1) / BS : 152 * 16);
-    const int cap = d.newton_max_its * (d.gmres_max_restarts + 1) * (m + 3) + 64;
+    const int cap = loop_cap_of(g);
     const double dt = 1.0;  // every recorded kernel reads dt from g->ctl->dt instead
     SolveCtl *ctl = g->ctl;
     DevScalars *ds = g->ds;

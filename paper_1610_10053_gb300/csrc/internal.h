@@ -66,6 +66,8 @@ struct music_grid {
     int rtile;            // tile shape of the stencil's R, C^n and F modes (stile: its Jv mode)
     int psplit;           // launches the fused preconditioner's sweeps are split over (1, 2 or 4)
     int jv_form;          // JV_*: form of the Krylov products of a mixed-precision grid
+    int loop_cap;         // bound on the loop bodies of one Newton attempt (0: the default
+                          // newton_max (restarts + 1) (m + 3) + 64, loop_cap_of)
     GridParams P;
     int mixed;
     int device;
@@ -260,6 +262,8 @@ void grid_destroy(music_grid *g);
 int grid_footprint(const music_grid_desc *desc, size_t *bytes);
 // geometry and physics of a descriptor whose defaults are filled in
 void fill_grid_params(const music_grid_desc &d, GridParams *P);
+// the loop-body bound of one Newton attempt (both drivers)
+int loop_cap_of(const music_grid *g);
 // fill in defaults and validate, allocating nothing
 int grid_validate(music_grid_desc *d);
 int grid_set_state(music_grid *g, const double *U, int is_device, cudaStream_t s);

@@ -146,18 +146,8 @@ int run_job(Job *j, cudaStream_t s)
     double t = 0.0;
     for (int k = 0; rc == MUSIC_OK && k < j->n_steps; k++) {
         const auto t0 = clk::now();
-        double dt = 0.0;
-        if (j->cfl_adv > 0.0 || j->cfl_rad > 0.0) {
-            const music_dt_limits lim = {j->cfl, j->cfl_adv, j->cfl_rad, j->dt_max};
-            rc = music_select_dt(g, &lim, &dt, nullptr, s);
-            if (rc != MUSIC_OK) break;
-        } else {
-            rc = music_cfl_dt(g, j->cfl, &dt, s);
-            if (rc != MUSIC_OK) break;
-            if (j->dt_max > 0.0 && dt > j->dt_max) dt = j->dt_max;
-        }
         music_step_stats st;
-        rc = newton_solve(g, dt, &st, s);
+        rc = music_newton_step(g, j->dt_max, &st, s);
         if (rc != MUSIC_OK) break;
         j->step_ms.push_back(ms_between(t0, clk::now()));
         t += st.dt;
@@ -404,6 +394,10 @@ int music_submit_solve(music_server *S, const music_solve_req *req, uint64_t *ti
     j->dt_max = req->dt_max;
     j->cfl_adv = req->cfl_adv;
     j->cfl_rad = req->cfl_rad;
+    // the request's limits are the grid's: music_newton_step applies them
+    j->desc.cfl_hydro = req->cfl;
+    j->desc.cfl_adv = req->cfl_adv;
+    j->desc.cfl_rad = req->cfl_rad;
     j->rho_L = req->rho_L;
     j->rho_H = (req->rho_H == req->rho_L) ? req->rho_L + 1.0 : req->rho_H;
     j->footprint = fp;

@@ -18,6 +18,21 @@ struct GmresOut {
     double bnorm;
 };
 
+// The bound on loop bodies of one Newton attempt, counted where the recorded
+// graph's control kernels count them: every Arnoldi step, every GMRES cycle
+// and every Newton iteration.
+struct LoopGuard {
+    long long bodies;
+    int cap;
+    bool over() { return ++bodies > cap; }
+};
+
+int loop_timeout()
+{
+    set_error("solver: loop-body bound reached");
+    return MUSIC_E_TIMEOUT;
+}
+
 int sync_scalars(music_grid *g, cudaStream_t s)
 {
     CUDA_TRY(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
@@ -27,7 +42,7 @@ int sync_scalars(music_grid *g, cudaStream_t s)
 }
 
 // Solve J x = b (b = g->b, FP64) into g->x (FP64).
-int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
+int gmres(music_grid *g, double dt, GmresOut *o, LoopGuard &guard, cudaStream_t s)
 {
     const int m = g->desc.gmres_restart;
     const double rtol = g->desc.gmres_rtol;
@@ -72,6 +87,7 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
         }
         resid = beta;
         if (beta <= target) {
+            if (guard.over()) return loop_timeout();
             o->converged = 1;
             break;
         }
@@ -93,6 +109,7 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
                 set_error("GMRES: non-finite Arnoldi vector");
                 return MUSIC_E_NONFINITE;
             }
+            if (guard.over()) return loop_timeout();
             for (int i = 0; i <= j; i++) H[i][j] = hs->h[i] + hs->h2[i];
             H[j + 1][j] = hn;
             for (int i = 0; i < j; i++) {
@@ -127,6 +144,7 @@ int gmres(music_grid *g, double dt, GmresOut *o, cudaStream_t s)
         // x += M^-1 V y as sum_i y_i Z_i: M^-1 (a fixed number of sweeps from
         // zero) is linear, and Z_i = M^-1 V_i is stored by each Arnoldi step
         TRY(krylov_correct(g, k, y, nullptr, nullptr, s));
+        if (guard.over()) return loop_timeout();
         if (resid <= target) {
             o->converged = 1;
             break;
@@ -157,14 +175,15 @@ struct ScalarSpace {
 // frozen at its current iterate, whose face mass fluxes are in g->sfr:
 // b = -((q - C_s) - dt/2 S(q)), unpreconditioned GMRES, q += x.  *maxdq
 // receives max |delta q| / rho.
-int scalar_iteration(music_grid *g, double dt, music_step_stats *st, double *maxdq, cudaStream_t s)
+int scalar_iteration(music_grid *g, double dt, music_step_stats *st, double *maxdq, LoopGuard &guard,
+                     cudaStream_t s)
 {
     g->srho = g->U;  // the fluid iterate's density plane
     ScalarSpace sp(g);
     TRY(stencil_apply(g, SM_F, g->U, g->sq_c, nullptr, 1, g->b, 1, g->RU, dt, -1.0, s));
     TRY(dev_norm2(g, g->U, 1, g->n, &g->ds->unorm2, s));
     GmresOut go;
-    TRY(gmres(g, dt, &go, s));
+    TRY(gmres(g, dt, &go, guard, s));
     st->scalar_gmres_its += go.its;
     TRY(scalar_update(g, s));
     TRY(sync_scalars(g, s));
@@ -201,16 +220,17 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     st->gmres_unconverged = 0;
     st->scalar_gmres_its = 0;
     int ok = 0;
+    LoopGuard guard{0, loop_cap_of(g)};
     for (int k = 0; k < g->desc.newton_max_its; k++) {
         // b = -F(U), RU = R(U) (and the face mass fluxes of U for the scalars)
         if (!(cnf && k == 0))
             TRY(with_fluxes(g, [&] { return stencil_apply(g, SM_F, g->U, g->Cn, nullptr, 1, g->b, 1, g->RU, dt,
                                                           -1.0, s); }));
         double maxdq = 0.0;
-        if (g->ns > 0) TRY(scalar_iteration(g, dt, st, &maxdq, s));
+        if (g->ns > 0) TRY(scalar_iteration(g, dt, st, &maxdq, guard, s));
         TRY(precond_setup(g, g->U, dt, s));
         GmresOut go;
-        int rc = gmres(g, dt, &go, s);
+        int rc = gmres(g, dt, &go, guard, s);
         if (rc != MUSIC_OK) return rc;
         st->gmres_its += go.its;
         st->gmres_unconverged += !go.converged;
@@ -220,6 +240,7 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
         TRY(sync_scalars(g, s));
         st->max_drho = g->hs->maxdrho;
         st->newton_its = k + 1;
+        if (guard.over()) return loop_timeout();
         if (g->hs->maxdrho <= g->desc.newton_tol && (!g->desc.scalar_enforce || maxdq <= g->desc.newton_tol)) {
             ok = 1;
             break;
@@ -300,6 +321,15 @@ int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_
             rc = graph_newton_attempt(g, dt, &st, s);
         else
             rc = newton_attempt(g, dt, &st, s);
+        if (rc == MUSIC_E_TIMEOUT) {
+            // an attempt stopped by the loop-body bound leaves a partial
+            // iterate: restore U^n (and the scalars) as a failed attempt does
+            CUDA_TRY(cudaMemcpyAsync(g->U, g->Un, g->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            if (g->ns > 0)
+                CUDA_TRY(cudaMemcpyAsync(g->sc.U, g->sq_n, g->sc.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            break;
+        }
         if (rc != MUSIC_E_NEWTON_FAIL) break;
         if (h >= g->desc.max_dt_halvings) break;
         dt *= 0.5;

@@ -70,3 +70,27 @@ def test_server_applies_the_caps():
         t = s.submit(p, B().MIXED)
         assert s.wait(t, timeout_ms=300000)["status"] == 0
         assert np.array_equal(s.result_state(t), U)
+
+
+def test_newton_step_takes_the_most_restrictive_limit():
+    """music_newton_step chooses the step on the device from the grid's limits
+    (here CFL_hydro 10 and CFL_adv 0.05), capped by dt_max; a grid without
+    limits takes dt_max as given and refuses dt_max <= 0."""
+    p = I.kelvin_helmholtz(n=32, seed=12, nsteps=1).with_options(cfl=10.0, cfl_adv=0.05)
+    ref, w = O.select_dt(p, p.U, 10.0, 0.05, 0.0, 0.0)
+    assert w == 1
+    with B().Grid(p, precision=B().FP64) as g:
+        g.set_state(p.U)
+        st = g.newton_step(0.0)
+    assert st["dt_halvings"] == 0 and st["dt"] == pytest.approx(ref, rel=1e-14)
+    with B().Grid(p, precision=B().FP64) as g:
+        g.set_state(p.U)
+        st = g.newton_step(0.25 * ref)
+    assert st["dt"] == 0.25 * ref
+    with B().Grid(p, precision=B().FP64, cfl_hydro=0.0, cfl_adv=0.0) as g:
+        g.set_state(p.U)
+        with pytest.raises(B().MusicError) as e:
+            g.newton_step(0.0)
+        assert e.value.code == 1
+        st = g.newton_step(0.5 * ref)
+    assert st["dt"] == 0.5 * ref

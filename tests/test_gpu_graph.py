@@ -95,7 +95,9 @@ def test_nonfinite_state_reports_the_same_error(monkeypatch):
             monkeypatch.setenv("MUSIC_SOLVER", "host")
         else:
             monkeypatch.delenv("MUSIC_SOLVER", raising=False)
-        with B().Grid(bad, precision=B().FP64) as g:
+        # no time-step limits: the step is the given dt, so the solver itself
+        # meets the NaN (the limits' reduction would report it first)
+        with B().Grid(bad, precision=B().FP64, cfl_hydro=0.0) as g:
             g.set_state(bad.U)
             with pytest.raises(B().MusicError) as e:
                 g.newton_step(1e-3)
@@ -142,3 +144,29 @@ def test_programmatic_launches_change_no_bit(case, monkeypatch):
     for a, b in zip(sa, sb):
         for k in STAT_KEYS:
             assert a[k] == b[k], (case, k, a[k], b[k])
+
+
+@pytest.mark.parametrize("solver", ["graph", "host"])
+def test_loop_body_bound_expires_with_timeout(solver, monkeypatch):
+    """The bound on loop bodies of a Newton attempt (every Arnoldi step, GMRES
+    cycle and Newton iteration counts one) lowered to 5: the attempt stops
+    with MUSIC_E_TIMEOUT, through either driver, and the state is restored
+    to U^n.  The bound is a counter in the control code, so its expiry is an
+    ordinary status; the grid and the context stay usable."""
+    p = I.kelvin_helmholtz(n=32, seed=9, nsteps=1)
+    monkeypatch.setenv("MUSIC_LOOP_CAP", "5")
+    if solver == "host":
+        monkeypatch.setenv("MUSIC_SOLVER", "host")
+    else:
+        monkeypatch.delenv("MUSIC_SOLVER", raising=False)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        with pytest.raises(B().MusicError) as e:
+            g.step()
+        assert e.value.code == 7  # MUSIC_E_TIMEOUT
+        assert np.array_equal(g.get_state(), p.U)
+    monkeypatch.delenv("MUSIC_LOOP_CAP")
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        st = g.step()
+        assert st["newton_its"] >= 1 and st["gmres_its"] > 5
