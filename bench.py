@@ -15,6 +15,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl music|referen
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -185,7 +186,7 @@ def run_music(args):
     # CPU baseline first (rank 0, N = 1 only), so it never overlaps GPU timing
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(prob)
+        cpu = cpu_baseline(prob, args.workload)
 
     result = {}
     for name, prec in (("mixed", B.MIXED), ("fp64", B.FP64)):
@@ -592,48 +593,87 @@ def run_convergence(n_max, t_end, n_min=64):
     return out
 
 
-def cpu_baseline(prob, steps=1):
-    """The FP64 CPU oracle as it stands, single-threaded, on one implicit step
-    of the same workload."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(prob, label, steps=1):
+    """The FP64 CPU oracle as it stands, on one implicit step of the same
+    workload: on all host cores (its OpenMP build: loops over cells split
+    over threads, reductions in fixed order, bitwise the serial results) and
+    on one core."""
     from oracle import oracle as O
     O.build()
+    model, ncpu = cpu_model(), os.cpu_count() or 1
     t0 = time.perf_counter()
-    U, st = O.run(prob, nsteps=steps)
-    el = time.perf_counter() - t0
-    return {"value": prob.ncells * steps / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d implicit step(s) of KH 512x512 (FP64, single thread), %.1f s" % (steps, el)}
+    O.run(prob, nsteps=steps)
+    el1 = time.perf_counter() - t0
+    single = {"value": prob.ncells * steps / el1, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+              "sample": "%d implicit step(s) of %s (FP64, one thread), %.1f s" % (steps, label, el1)}
+    if not O.openmp_available():
+        single.update(cpu_model=model, single_thread=dict(single), note="no OpenMP runtime: one core only")
+        return single
+    with O.threaded(0) as nt:
+        t0 = time.perf_counter()
+        O.run(prob, nsteps=steps)
+        eln = time.perf_counter() - t0
+    return {"value": prob.ncells * steps / eln, "unit": "cell-steps/s", "cores": nt, "kind": "oracle",
+            "sample": "%d implicit step(s) of %s (FP64, %d threads, OpenMP over cells), %.1f s"
+                      % (steps, label, nt, eln),
+            "cpu_model": model, "host_cpus": ncpu, "single_thread": single}
+
 
 
 def run_reference(args):
-    """The oracle (plain FP64 CPU solver) on the host cores, bounded sample per
-    step: one implicit step of the same Kelvin-Helmholtz setup at 256x256."""
+    """The oracle (plain FP64 CPU solver) on the host cores, on the GPU arm's
+    own workload: each step is one implicit step of the Kelvin-Helmholtz setup
+    on the 512x512 grid, on all host cores (the oracle's OpenMP build)."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
     from oracle import oracle as O
     from paper_1610_10053_gb300 import inputs as I
     O.build()
-    prob = I.kelvin_helmholtz(n=256, seed=2)
+    prob = workload("kh512", 0)
     U = prob.U.copy()
-    for _ in range(args.warmup):
-        U, _ = O.run(prob, U=U, nsteps=1)
-    times = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        U, _ = O.run(prob, U=U, nsteps=1)
-        times.append(time.perf_counter() - t0)
+    omp = O.openmp_available()
+    ctx = O.threaded(0) if omp else contextlib.nullcontext(1)
+    with ctx as nt:
+        for _ in range(args.warmup):
+            U, _ = O.run(prob, U=U, nsteps=1)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            U, _ = O.run(prob, U=U, nsteps=1)
+            times.append(time.perf_counter() - t0)
     total = float(np.sum(times))
     value = prob.ncells * args.steps / total
-    sample = ("each step: one implicit step of the same Kelvin-Helmholtz setup on a 256x256 grid "
-              "(a quarter of the cells; FP64, single thread); cell-steps/s is a rate")
+    sample = ("each step: one implicit step of the same Kelvin-Helmholtz 512x512 workload (FP64 oracle, "
+              "%d thread(s), OpenMP over cells); cell-steps/s is a rate" % nt)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS["kh512"][0], "cells": 512 * 512, "precision": "fp64 (oracle)",
+        "config": {"workload": WORKLOADS["kh512"][0], "cells": prob.ncells, "precision": "fp64 (oracle)",
                    "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": nt, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

@@ -44,6 +44,36 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops over independent cells, points or vector entries carry OR_PAR.  The
+ * oracle as tested is serial; built with -fopenmp (the multi-core CPU
+ * baseline only) these loops are split over threads.  No sum, norm, maximum
+ * or dot product is ever split, so both builds produce the same bits. */
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PAR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PAR
+#endif
+
+/* threads the OR_PAR loops use (1 in the serial build) */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 #define OR_BC_PERIODIC 0
 #define OR_BC_WALL 1
 #define OR_WALL_MIRROR 0
@@ -221,9 +251,9 @@ void or_spatial_operator_dir(const or_grid *g, const double *U, const double *V,
     const double h = 1e-30;
     double complex *Uc = (double complex *)malloc(n * sizeof(double complex));
     double complex *Rc = (double complex *)malloc(n * sizeof(double complex));
-    for (long i = 0; i < n; i++) Uc[i] = U[i] + I * (h * V[i]);
+        for (long i = 0; i < n; i++) Uc[i] = U[i] + I * (h * V[i]);
     spatial_operator_c(g, Uc, Rc);
-    for (long i = 0; i < n; i++) dR[i] = cimag(Rc[i]) / h;
+        for (long i = 0; i < n; i++) dR[i] = cimag(Rc[i]) / h;
     free(Uc);
     free(Rc);
 }
@@ -248,6 +278,7 @@ void or_step_constant(const or_grid *g, const double *Un, double dt, double *Cn)
     double *R = (double *)malloc(n * sizeof(double));
     spatial_operator_r(g, Un, R);
     const double hdt = 0.5 * dt;
+    OR_PAR
     for (long i = 0; i < n; i++) Cn[i] = Un[i] + hdt * R[i];
     free(R);
 }
@@ -258,6 +289,7 @@ void or_cn_residual_cached(const or_grid *g, const double *U, const double *Cn, 
     const long n = (long)or_nvars(g) * or_ncells(g);
     spatial_operator_r(g, U, RU);
     const double hdt = 0.5 * dt;
+    OR_PAR
     for (long i = 0; i < n; i++) F[i] = (U[i] - Cn[i]) - hdt * RU[i];
 }
 
@@ -288,14 +320,17 @@ void or_jv(const or_grid *g, const double *U, const double *RU, const double *v,
     const long n = (long)or_nvars(g) * or_ncells(g);
     if (eps <= 0.0) eps = or_fd_eps(n, or_norm(n, U), v);
     if (eps == 0.0) {
+        OR_PAR
         for (long i = 0; i < n; i++) Jv[i] = 0.0;
         return;
     }
     double *W = (double *)malloc(n * sizeof(double));
     double *RW = (double *)malloc(n * sizeof(double));
+    OR_PAR
     for (long i = 0; i < n; i++) W[i] = U[i] + eps * v[i];
     spatial_operator_r(g, W, RW);
     const double c = 0.5 * dt / eps;
+    OR_PAR
     for (long i = 0; i < n; i++) Jv[i] = v[i] - c * (RW[i] - RU[i]);
     free(W);
     free(RW);
@@ -373,6 +408,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
     double *dp = (double *)calloc(N, sizeof(double));
     double *dq = (double *)malloc(N * sizeof(double));
     double *chi = (double *)calloc(N, sizeof(double));
+    OR_PAR
     for (long c = 0; c < N; c++) {
         gp[c] = gam * (gm1 * U[N + c]);
         hp[c] = gam * U[N + c];
@@ -391,6 +427,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
     double *hm = (double *)malloc(N * 3 * sizeof(double)), *hpl = (double *)malloc(N * 3 * sizeof(double));
     double *am = (double *)malloc(N * 3 * sizeof(double)), *ap = (double *)malloc(N * 3 * sizeof(double));
     double *km = (double *)malloc(N * 3 * sizeof(double)), *kp = (double *)malloc(N * 3 * sizeof(double));
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -415,6 +452,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
         }
     }
     double *D = (double *)malloc(N * sizeof(double));
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -431,6 +469,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
     }
     const double omega = OR_JACOBI_OMEGA;
     for (int sw = 0; sw < g->sweeps; sw++) {
+        OR_PAR
         for (long c = 0; c < N; c++) {
             int ix[3];
             or_cell_coords(g, c, ix);
@@ -448,6 +487,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
     }
     /* back substitution */
     for (int d = 0; d < nd; d++) {
+        OR_PAR
         for (long c = 0; c < N; c++) {
             int ix[3];
             or_cell_coords(g, c, ix);
@@ -457,6 +497,7 @@ static void or_precond_general(const or_grid *g, const double *U, double dt, con
                 z[(2 + d) * N + c] = r[(2 + d) * N + c] - tau * (dp[c] - dp[or_nb(g, ix, d, -1)]) / hm[c * 3 + d];
         }
     }
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -504,6 +545,7 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
     for (int d = 0; d < nd; d++) a[d] = (double *)malloc(N * sizeof(double));
 
     /* frozen coefficients: a_d = 1/rbar on the lower d-face (0 on walls) */
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -522,6 +564,7 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
        cell, or 0 on the implicit upper wall */
 #define A_UP(d, c, ix) ((g->bc[d] == OR_BC_WALL && (ix)[d] == g->n[d] - 1) ? 0.0 : a[d][or_nb(g, ix, d, +1)])
 
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -541,6 +584,7 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
     const double omega = OR_JACOBI_OMEGA;
     double *dq = (double *)malloc(N * sizeof(double));
     for (int s = 0; s < g->sweeps; s++) {
+        OR_PAR
         for (long c = 0; c < N; c++) {
             int ix[3];
             or_cell_coords(g, c, ix);
@@ -558,6 +602,7 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
 
     /* back substitution: dm on faces, then drho and dE in flux form */
     for (int d = 0; d < nd; d++) {
+        OR_PAR
         for (long c = 0; c < N; c++) {
             int ix[3];
             or_cell_coords(g, c, ix);
@@ -568,6 +613,7 @@ void or_precond(const or_grid *g, const double *U, double dt, const double *r, d
                     r[(2 + d) * N + c] - tau * (dp[c] - dp[or_nb(g, ix, d, -1)]) / g->dx[d];
         }
     }
+    OR_PAR
     for (long c = 0; c < N; c++) {
         int ix[3];
         or_cell_coords(g, c, ix);
@@ -607,6 +653,7 @@ typedef struct {
 int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x, int m,
              int max_restarts, double rtol, or_gmres_stats *st)
 {
+    OR_PAR
     for (long i = 0; i < n; i++) x[i] = 0.0;
     if (m < 1 || m > 63) return 2;
     st->its = 0;
@@ -636,6 +683,7 @@ int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x,
             memcpy(V, b, n * sizeof(double));
         } else {
             A(ctx, x, w);
+            OR_PAR
             for (long i = 0; i < n; i++) V[i] = b[i] - w[i];
         }
         double beta = or_norm(n, V);
@@ -644,6 +692,7 @@ int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x,
             st->converged = 1;
             break;
         }
+        OR_PAR
         for (long i = 0; i < n; i++) V[i] = V[i] / beta;
         for (int i = 0; i <= m; i++) gv[i] = 0.0;
         gv[0] = beta;
@@ -659,6 +708,7 @@ int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x,
                 for (int i = 0; i <= j; i++) hp_[i] = or_dot(n, V + (size_t)i * n, w);
                 for (int i = 0; i <= j; i++) {
                     const double *Vi = V + (size_t)i * n;
+                    OR_PAR
                     for (long q = 0; q < n; q++) w[q] -= hp_[i] * Vi[q];
                     h[i] += hp_[i];
                 }
@@ -691,6 +741,7 @@ int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x,
             st->resid = fabs(gv[j + 1]);
             if (hn == 0.0 || fabs(gv[j + 1]) <= target) break;
             double *Vn = V + (size_t)(j + 1) * n;
+            OR_PAR
             for (long q = 0; q < n; q++) Vn[q] = w[q] / hn;
         }
         /* y = H^-1 g (upper triangular k x k) */
@@ -700,12 +751,15 @@ int or_gmres(long n, or_op A, or_op Minv, void *ctx, const double *b, double *x,
             y[i] = s / H[i * m + i];
         }
         /* x += M^-1 (V y) */
+        OR_PAR
         for (long q = 0; q < n; q++) w[q] = 0.0;
         for (int i = 0; i < k; i++) {
             const double *Vi = V + (size_t)i * n;
+            OR_PAR
             for (long q = 0; q < n; q++) w[q] += y[i] * Vi[q];
         }
         Minv(ctx, w, z);
+        OR_PAR
         for (long q = 0; q < n; q++) x[q] += z[q];
         if (st->resid <= target) {
             st->converged = 1;
@@ -763,6 +817,7 @@ static void or_ctx_jv(void *ctx, const double *v, double *out)
     const long n = (long)or_nvars(c->g) * or_ncells(c->g);
     double eps = or_fd_eps(n, c->unorm, v);
     if (eps == 0.0) {
+        OR_PAR
         for (long i = 0; i < n; i++) out[i] = 0.0;
         return;
     }
@@ -797,6 +852,7 @@ int or_newton_step(const or_grid *g, double *U, double dt, or_step_stats *st)
         or_cn_residual_cached(g, U, Cn, dt, F, RU);
         st->fnorm = or_norm(n, F);
         if (k == 0) st->fnorm0 = st->fnorm;
+        OR_PAR
         for (long i = 0; i < n; i++) F[i] = -F[i];
         or_newton_ctx ctx = {g, U, RU, or_norm(n, U), dt};
         or_gmres_stats gs;
@@ -805,6 +861,7 @@ int or_newton_step(const or_grid *g, double *U, double dt, or_step_stats *st)
         st->gmres_its += gs.its;
         st->gmres_failures += rc;
         double mx = 0.0;
+        OR_PAR
         for (long i = 0; i < n; i++) U[i] += x[i];
         for (long c = 0; c < N; c++) {
             double q = fabs(x[c]) / U[c];
@@ -1007,9 +1064,9 @@ void or_scalar_operator_dir(const or_grid *g, const double *U, const double *q, 
     double complex *qc = (double complex *)malloc(nq * sizeof(double complex));
     double complex *Sc = (double complex *)malloc(nq * sizeof(double complex));
     const double h = 1e-30;
-    for (long i = 0; i < nq; i++) qc[i] = q[i] + I * h * v[i];
+        for (long i = 0; i < nq; i++) qc[i] = q[i] + I * h * v[i];
     scalar_operator_c(g, U, Fr, qc, ns, Sc);
-    for (long i = 0; i < nq; i++) dS[i] = cimag(Sc[i]) / h;
+        for (long i = 0; i < nq; i++) dS[i] = cimag(Sc[i]) / h;
     free(qc);
     free(Sc);
     or_free_fluxes(g, Fr);
@@ -1033,14 +1090,17 @@ static void or_scal_jv(void *ctx, const double *v, double *out)
     const long nq = (long)c->ns * or_ncells(c->g);
     const double eps = or_fd_eps(nq, c->qnorm, v);
     if (eps == 0.0) {
+        OR_PAR
         for (long i = 0; i < nq; i++) out[i] = 0.0;
         return;
     }
     double *W = (double *)malloc(nq * sizeof(double));
     double *SW = (double *)malloc(nq * sizeof(double));
+    OR_PAR
     for (long i = 0; i < nq; i++) W[i] = c->q[i] + eps * v[i];
     scalar_operator_r(c->g, c->rho, c->Fr, W, c->ns, SW);
     const double a = 0.5 * c->dt / eps;
+    OR_PAR
     for (long i = 0; i < nq; i++) out[i] = v[i] - a * (SW[i] - c->Sq[i]);
     free(W);
     free(SW);
@@ -1057,6 +1117,7 @@ static void or_scal_identity(void *ctx, const double *in, double *out)
 static void or_scalar_renormalise(const or_grid *g, const double *rho, double *q, int ns)
 {
     const long N = or_ncells(g);
+    OR_PAR
     for (long k = 0; k < N; k++) {
         double s = 0.0;
         for (int i = 0; i < ns; i++) s += q[(long)i * N + k] / rho[k];
@@ -1089,6 +1150,7 @@ int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, 
     {
         double **Fr = or_mass_fluxes(g, Un);
         scalar_operator_r(g, Un, Fr, qn, ns, Sq);
+        OR_PAR
         for (long i = 0; i < nq; i++) Cs[i] = qn[i] + 0.5 * dt * Sq[i];
         or_free_fluxes(g, Fr);
     }
@@ -1102,6 +1164,7 @@ int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, 
         /* scalars, with the fluid frozen at U^k */
         double **Fr = or_mass_fluxes(g, U);
         scalar_operator_r(g, U, Fr, q, ns, Sq);
+        OR_PAR
         for (long i = 0; i < nq; i++) bs[i] = -((q[i] - Cs[i]) - 0.5 * dt * Sq[i]);
         or_scal_ctx sc = {g, U, Fr, q, Sq, or_norm(nq, q), dt, ns};
         or_gmres_stats sgs;
@@ -1119,6 +1182,7 @@ int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, 
         or_cn_residual_cached(g, U, Cn, dt, F, RU);
         st->fnorm = or_norm(n, F);
         if (k == 0) st->fnorm0 = st->fnorm;
+        OR_PAR
         for (long i = 0; i < n; i++) F[i] = -F[i];
         or_newton_ctx ctx = {g, U, RU, or_norm(n, U), dt};
         or_gmres_stats gs;
@@ -1127,6 +1191,7 @@ int or_newton_step_s(const or_grid *g, double *U, double *q, int ns, double dt, 
         st->gmres_its += gs.its;
         st->gmres_failures += rc;
         double mx = 0.0;
+        OR_PAR
         for (long i = 0; i < n; i++) U[i] += x[i];
         for (long c = 0; c < N; c++) {
             double t = fabs(x[c]) / U[c];

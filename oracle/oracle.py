@@ -8,6 +8,7 @@ from ``paper_1610_10053_gb300.inputs`` only.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -17,6 +18,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liboracle.so")
+# the same source built with -fopenmp: its independent per-cell loops run on
+# all host cores (the multi-core CPU baseline); every reduction stays serial
+LIB_OMP = os.path.join(BUILD, "liboracle_omp.so")
 SRC = [os.path.join(HERE, "music_oracle.c"), os.path.join(HERE, "residual_body.h")]
 
 _dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -46,28 +50,65 @@ class OrStepStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math)."""
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        if os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in SRC):
-            return LIB
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=gnu11",
-           "-o", tmp, SRC[0], "-lm"]
+def _compile(out, extra):
+    if os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(s) for s in SRC):
+        return
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=gnu11"] + extra + [
+        "-o", tmp, SRC[0], "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, no fast-math),
+    and its OpenMP build where the compiler supports -fopenmp."""
+    os.makedirs(BUILD, exist_ok=True)
+    if force:
+        for f in (LIB, LIB_OMP):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(LIB, [])
+    try:
+        _compile(LIB_OMP, ["-fopenmp"])
+    except (subprocess.CalledProcessError, OSError):
+        pass  # no OpenMP runtime: only the serial baseline is available
     return LIB
 
 
-_lib = None
+_libs = {}
+_active = "serial"
+
+
+def openmp_available() -> bool:
+    build()
+    return os.path.exists(LIB_OMP)
+
+
+@contextlib.contextmanager
+def threaded(threads: int = 0):
+    """Run the oracle calls inside the block with the OpenMP build on
+    `threads` host threads (0: all).  Results are bitwise those of the serial
+    build."""
+    global _active
+    if not openmp_available():
+        raise RuntimeError("the oracle's OpenMP build is not available")
+    prev = _active
+    _active = "omp"
+    try:
+        lib().or_set_threads(int(threads) if threads > 0 else (os.cpu_count() or 1))
+        yield lib().or_threads()
+    finally:
+        _active = prev
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
+    key = _active
+    if key not in _libs:
+        _libs[key] = ctypes.CDLL(LIB_OMP if key == "omp" else build())
+        L = _libs[key]
+        L.or_threads.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [ctypes.c_int]
         G = ctypes.POINTER(OrGrid)
         L.or_spatial_operator.argtypes = [G, _dbl_p, _dbl_p]
         L.or_spatial_operator_dir.argtypes = [G, _dbl_p, _dbl_p, _dbl_p]
@@ -102,7 +143,7 @@ def lib():
         L.or_select_dt.argtypes = [G, _dbl_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                    ctypes.POINTER(ctypes.c_int)]
         L.or_select_dt.restype = ctypes.c_double
-    return _lib
+    return _libs[key]
 
 
 def _p(a: np.ndarray):

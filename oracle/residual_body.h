@@ -80,12 +80,14 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     const double gm1 = g->gamma - 1.0;
 
     /* --- a1: interior values, then ghost layers direction by direction --- */
+    OR_PAR
     for (long c = 0; c < N; c++) {
         long x = or_ext_of_cell(&X, g, c);
         rho[x] = U[c];
         Erho[x] = U[N + c];
     }
     for (int d = 0; d < nd; d++) {
+        OR_PAR
         for (long x = 0; x < M; x++) {
             int ix[3];
             or_ext_coords(&X, x, ix);
@@ -131,6 +133,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             }
         }
     }
+    OR_PAR
     for (long x = 0; x < M; x++) {
         e[x] = Erho[x] / rho[x];
         p[x] = gm1 * Erho[x];
@@ -139,6 +142,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
         /* temperature and conductivity per cell; gradient flux chi dT/dn on
            every d-face (arithmetic mean of the two cells' chi); wall faces
            carry the prescribed flux or none */
+        OR_PAR
         for (long x = 0; x < M; x++) {
             Tt[x] = gm1 * e[x];
             T t3 = Tt[x] * Tt[x] * Tt[x];
@@ -146,6 +150,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
         }
         for (int d = 0; d < nd; d++) {
             const long s = X.stride[d];
+            OR_PAR
             for (long x = 0; x < M; x++) {
                 int ix[3];
                 or_ext_coords(&X, x, ix);
@@ -170,6 +175,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
 
     /* --- face velocities: interior faces from m / (mean of the two cells) --- */
     for (int d = 0; d < nd; d++) {
+        OR_PAR
         for (long c = 0; c < N; c++) {
             long x = or_ext_of_cell(&X, g, c);
             int ix[3];
@@ -185,6 +191,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     }
     /* ghost face velocities, direction by direction */
     for (int w = 0; w < nd; w++) {
+        OR_PAR
         for (long x = 0; x < M; x++) {
             int ix[3];
             or_ext_coords(&X, x, ix);
@@ -221,6 +228,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     /* --- limited slopes --- */
     for (int d = 0; d < nd; d++) {
         const long s = X.stride[d];
+        OR_PAR
         for (long x = 0; x < M; x++) {
             int ix[3];
             or_ext_coords(&X, x, ix);
@@ -235,6 +243,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     /* --- mass and internal-energy fluxes on d-faces (upwind reconstruction) --- */
     for (int d = 0; d < nd; d++) {
         const long s = X.stride[d];
+        OR_PAR
         for (long x = 0; x < M; x++) {
             int ix[3];
             or_ext_coords(&X, x, ix);
@@ -257,6 +266,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     for (int d = 0; d < nd; d++) {
         const long s = X.stride[d];
         /* flux of m_d along d at cell centres */
+        OR_PAR
         for (long x = 0; x < M; x++) {
             int ix[3];
             or_ext_coords(&X, x, ix);
@@ -271,6 +281,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
         for (int q = 0; q < nd; q++) {
             if (q == d) continue;
             const long t = X.stride[q];
+            OR_PAR
             for (long x = 0; x < M; x++) {
                 int ix[3];
                 or_ext_coords(&X, x, ix);
@@ -286,7 +297,8 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     }
 
     /* --- residual assembly on the interior --- */
-    for (long c = 0; c < N && !sph; c++) {
+    OR_PAR
+    for (long c = 0; c < (sph ? 0 : N); c++) {
         long x = or_ext_of_cell(&X, g, c);
         int ix[3];
         or_ext_coords(&X, x, ix);
@@ -325,7 +337,8 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
         }
     }
     /* spherical (r, theta): area-weighted divergences over each control volume */
-    for (long c = 0; c < N && sph; c++) {
+    OR_PAR
+    for (long c = 0; c < (sph ? N : 0); c++) {
         long x = or_ext_of_cell(&X, g, c);
         int ix[3];
         or_ext_coords(&X, x, ix);
@@ -411,8 +424,10 @@ static void FN(scalar_operator)(const or_grid *g, const double *rho, double *con
     T *Fs[3] = {NULL, NULL, NULL};
     for (int d = 0; d < nd; d++) Fs[d] = (T *)calloc(M, sizeof(T));
     for (int i = 0; i < ns; i++) {
+        OR_PAR
         for (long k = 0; k < N; k++) c[or_ext_of_cell(&X, g, k)] = q[(long)i * N + k] / rho[k];
         for (int d = 0; d < nd; d++) {
+            OR_PAR
             for (long x = 0; x < M; x++) {
                 int ix[3];
                 or_ext_coords(&X, x, ix);
@@ -432,6 +447,7 @@ static void FN(scalar_operator)(const or_grid *g, const double *rho, double *con
         }
         for (int d = 0; d < nd; d++) {
             const long s = X.stride[d];
+            OR_PAR
             for (long x = 0; x < M; x++) {
                 int ix[3];
                 or_ext_coords(&X, x, ix);
@@ -439,6 +455,7 @@ static void FN(scalar_operator)(const or_grid *g, const double *rho, double *con
                 if (!or_ext_has(&X, ix, d, -1) || !or_ext_has(&X, ix, d, +1)) continue;
                 sc[x] = FN(vanleer)(c[x] - c[x - s], c[x + s] - c[x]);
             }
+            OR_PAR
             for (long x = 0; x < M; x++) {
                 int ix[3];
                 or_ext_coords(&X, x, ix);
@@ -449,6 +466,7 @@ static void FN(scalar_operator)(const or_grid *g, const double *rho, double *con
                 Fs[d][x] = f * cs;
             }
         }
+        OR_PAR
         for (long k = 0; k < N; k++) {
             const long x = or_ext_of_cell(&X, g, k);
             T acc = 0.0;
