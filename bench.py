@@ -188,6 +188,9 @@ def run_music(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(prob, args.workload)
 
+    # the FP64 / FP32 ceilings of this GPU, measured in this run (the residual
+    # stencil is FP64-bound; the roofline is reported against these)
+    alu_peaks = B.measure_peaks()
     result = {}
     for name, prec in (("mixed", B.MIXED), ("fp64", B.FP64)):
         if name == "fp64" and args.skip_fp64:
@@ -233,7 +236,7 @@ def run_music(args):
         fp64_value = job_rate(ws, N, args.steps, result["fp64"]["total_ms"])
 
     mixed["kernels"] = kernel_classes(mixed, prob)
-    roof = roofline(mixed, prob, mixed["jv_form"])
+    roof = roofline(mixed, prob, mixed["jv_form"], alu_peaks)
     final_diag = mixed["grid"].diagnostics()
     if prob.q is not None:
         final_diag["scalar_mixing_width"] = mixed["grid"].scalar_mixing_width()
@@ -359,8 +362,10 @@ def kernel_classes(mixed, prob):
     return out
 
 
-def roofline(mixed, prob, jv_form):
-    """The roofline of the class that takes the most device time per step."""
+def roofline(mixed, prob, jv_form, alu=None):
+    """The roofline of the class that takes the most device time per step,
+    against the FP64 or FP32 FMA throughput measured in this run
+    (music_measure_peaks; the unit-count figure when none was measured)."""
     # many small kernels in "vector", none in "unattributed": no one roofline for either
     ks = {k: v for k, v in mixed["kernels"].items() if k not in ("vector", "unattributed")}
     if not ks:
@@ -390,6 +395,9 @@ def roofline(mixed, prob, jv_form):
         return {"kernel": kern, "bound": "alu", "achieved": None, "peak": peak, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "launches": ks[name]["launches"], "ms_per_launch": per,
                 "note": "per-cell model given for the fused 2-D kernels only"}
+    derived = peak
+    if alu:
+        peak = alu["fp64_fma_tflops"] if unit == "FP64" else alu["fp32_fma_tflops"]
     achieved = flops * N / (per / 1e3) / 1e12
     if N == 512 * 512 and (name != "jv" or jv_form == "diff"):
         traffic = TRAFFIC_KH512[name]
@@ -402,8 +410,12 @@ def roofline(mixed, prob, jv_form):
             "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
             "launches": ks[name]["launches"], "ms_per_launch": per, "flops_per_cell": flops,
             "timing": "CUDA events around each launch, same-length pass after the timed region",
-            "peak_note": "%s peak derived from unit counts and clock (152 SM x %s x 2.07 GHz)"
-                         % (unit, "2 DFMA/clk" if unit == "FP64" else "128 FFMA/clk"),
+            "peak_note": ("%s FMA throughput measured in this run by music_measure_peaks (unit-count figure "
+                          "152 SM x %s x 2.07 GHz = %.3f)" % (unit, "2 DFMA/clk" if unit == "FP64" else "128 FFMA/clk",
+                                                             derived)) if alu else
+                         ("%s peak derived from unit counts and clock (152 SM x %s x 2.07 GHz)"
+                          % (unit, "2 DFMA/clk" if unit == "FP64" else "128 FFMA/clk")),
+            "measured_alu_peaks": alu,
             "hbm_view": {"achieved_gbs": bpc * N / (per / 1e3) / 1e9, "peak_gbs": hbm, "peak_source": src,
                          "bytes_per_cell": bpc, "frac": bpc * N / (per / 1e3) / 1e9 / hbm if hbm else None}}
 

@@ -454,6 +454,25 @@ int music_profile_enable(music_grid *grid, int on);
 int music_profile_read(music_grid *grid, uint64_t *launches, double *ms);
 int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, double *ms);
 
+/*
+ * Measured arithmetic ceilings of the current device: FP64 and FP32 fused
+ * multiply-add throughput (2 flops each) and FP64 division throughput, each
+ * the best of five launches of 8 resident blocks per SM, every thread running
+ * 8 independent dependency chains.  The paper has no counterpart (it reports
+ * no hardware figures); the library uses none of these numbers itself.  They
+ * are the denominators that the FP64-bound stencil and the FP32 kernels are
+ * compared with.  Allocates a scratch buffer of 2 KB per SM, takes about
+ * 50 ms, synchronises `stream`.  Errors: MUSIC_E_INVAL (NULL), MUSIC_E_CUDA.
+ */
+typedef struct {
+    double fp64_fma_tflops;   /* FP64 FMA, 10^12 flop/s */
+    double fp32_fma_tflops;   /* FP32 FMA, 10^12 flop/s */
+    double fp64_div_gops;     /* FP64 IEEE divisions, 10^9 per second */
+    int sms;                  /* streaming multiprocessors of the device */
+    int pad;
+} music_peaks;
+int music_measure_peaks(music_peaks *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

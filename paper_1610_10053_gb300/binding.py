@@ -85,6 +85,11 @@ class TuneReport(ctypes.Structure):
 
 MUSIC_TUNE_FORCE = 1
 
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("fp64_div_gops", ctypes.c_double), ("sms", ctypes.c_int), ("pad", ctypes.c_int)]
+
 SIGNATURES = {
     "music_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
     "music_version": (ctypes.c_char_p, []),
@@ -132,6 +137,7 @@ SIGNATURES = {
     "music_profile_read_class": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
                                                 _dbl_p]),
     "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "music_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
 }
 
 _lib = None
@@ -248,6 +254,15 @@ def batch_step(grids, cfl=None, dt_max=None):
     if code == 1:
         check(code)
     return code, [st[i].as_dict() for i in range(n)]
+
+
+def measure_peaks() -> dict:
+    """Measured FP64 / FP32 FMA and FP64 division throughput of the current
+    device (music_measure_peaks)."""
+    pk = Peaks()
+    check(load().music_measure_peaks(ctypes.byref(pk), _stream()))
+    return {"fp64_fma_tflops": pk.fp64_fma_tflops, "fp32_fma_tflops": pk.fp32_fma_tflops,
+            "fp64_div_gops": pk.fp64_div_gops, "sms": pk.sms}
 
 
 def velocity_error(fine, coarse) -> float:

@@ -480,10 +480,10 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
                         TRY(precond_apply(g, dt, g->q, g->z, 1, s4));
                     }
                     TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s4));
-                    TRY(krylov_dots(g, m - 1, &ctl->j, s4));
-                    TRY(krylov_update_dots(g, m - 1, &ctl->j, s4));
                     // the last block of the norm pass runs the Givens rotations
                     const GivensCtl gc{ctl, ds, hA, m, cap};
+                    TRY(krylov_dots(g, m - 1, &ctl->j, s4));
+                    TRY(krylov_update_dots(g, m - 1, &ctl->j, s4));
                     TRY(krylov_update_norm(g, m - 1, &ctl->j, s4, &gc));
                     if (!fold) {
                         if (g->mixed)
@@ -591,11 +591,9 @@ void graph_release(music_grid *g)
 int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s)
 {
     if (!g->gexec) {
-        const int rc = record_attempt(g, true);
-        if (rc == PDL_REFUSED)
-            TRY(record_attempt(g, false));
-        else
-            TRY(rc);
+        int rc = record_attempt(g, true);
+        if (rc == PDL_REFUSED) rc = record_attempt(g, false);
+        TRY(rc);
     }
     SolveCtl *h = g->hctl;
     h->dt = dt;

@@ -104,82 +104,6 @@ __device__ __forceinline__ void write_partials(const double acc[NG], int i0, int
     }
 }
 
-// h_i = <V_i, w>, i <= j (j read from jdev when given).  With Zb, the
-// preconditioned vector zs = M^-1 V_j is also stored as Z_j.
-template <typename KT>
-__global__ void __launch_bounds__(BS) k_dots(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                  double *dst, unsigned int *counter, const int *jdev, const KT *zs, KT *Zb)
-{
-    pdl_entry();
-    __shared__ double sh[BS / 32];
-    if (jdev) j = *jdev;
-    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    if (Zb) {
-        KT *Zj = Zb + (long long)j * n;
-        for (long long e = t0; e < n; e += stride) Zj[e] = zs[e];
-    }
-    for (int i0 = 0; i0 <= j; i0 += NG) {
-        const int cnt = min(NG, j + 1 - i0);
-        double acc[NG];
-        dots_pass<KT>(V, w, n, i0, cnt, acc);
-        write_partials(acc, i0, cnt, partial, nb, sh);
-    }
-    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
-}
-
-// w <- w - sum_i h_i V_i; then h2_i = <V_i, w> (second CGS pass) or, with
-// NORM, |w|^2 only.  Up to NG products ride on the update sweep; beyond
-// that the updated w is swept again in groups.
-template <bool NORM, typename KT>
-__global__ void __launch_bounds__(BS) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                  double *partial, int nb, double *dst, unsigned int *counter, const int *jdev,
-                                  GivensCtl gc)
-{
-    pdl_entry();
-    __shared__ double sh[BS / 32];
-    __shared__ double hs[MUSIC_MAXV];
-    if (jdev) j = *jdev;
-    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = h[i];
-    __syncthreads();
-    const bool fused = NORM || j < NG;
-    double acc[NG];
-#pragma unroll
-    for (int i = 0; i < NG; i++) acc[i] = 0.0;
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        double we = (double)w[e];
-        for (int i = 0; i <= j; i++) we -= hs[i] * (double)V[(long long)i * n + e];
-        const KT ws = (KT)we;
-        w[e] = ws;
-        const double wr = (double)ws;
-        if (NORM) {
-            acc[0] += wr * wr;
-        } else if (fused) {
-#pragma unroll
-            for (int i = 0; i < NG; i++)
-                if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
-        }
-    }
-    if (NORM) {
-        write_partials(acc, 0, 1, partial, nb, sh);
-    } else if (fused) {
-        write_partials(acc, 0, j + 1, partial, nb, sh);
-    } else {
-        for (int i0 = 0; i0 <= j; i0 += NG) {
-            const int cnt = min(NG, j + 1 - i0);
-            dots_pass<KT>(V, w, n, i0, cnt, acc);
-            write_partials(acc, i0, cnt, partial, nb, sh);
-        }
-    }
-    if (last_block_done(counter)) {
-        if (NORM)
-            finish_sums<BS>(partial, nb, nb, 1, dst, sh);
-        else
-            finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
-        // |w| is in *dst (written by thread 0): the Arnoldi step's control
-        if (NORM && gc.c && threadIdx.x == 0) ctl_givens(gc.c, gc.ds, gc.h, gc.m, gc.cap);
-    }
-}
-
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long long n, double inv)
 {
@@ -380,112 +304,177 @@ __device__ __forceinline__ void dots_pass_f32(const float *V, const float *w, lo
     }
 }
 
-// h_i = <V_i, w>, i <= j (j read from jdev when given); with Zb, also Z_j = zs
-__global__ void __launch_bounds__(BS, 4) k_dots_f32(const float *V, const float *w, long long n, int j,
-                                                 double *partial, int nb, double *dst, unsigned int *counter,
-                                                 const int *jdev, const float *zs, float *Zb)
+// ---- the passes of one Arnoldi step's CGS2 (classical Gram-Schmidt with one
+// re-orthogonalisation), as block partials, one kernel each.
+
+// Pass 1: Z_j = zs (with Zb) and the block partials of h_i = <V_i, w>, i <= j,
+// at partial[i * nb + block].
+template <typename KT>
+__device__ __forceinline__ void cgs_dots_pass(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
+                                              const KT *zs, KT *Zb, double *sh)
 {
-    pdl_entry();
-    if (jdev) j = *jdev;
+    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
     if (Zb) {
-        float *Zj = Zb + (long long)j * n;
-        const long long n4 = (n & 3) ? 0 : (n >> 2);
-        const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
-        for (long long e = t0; e < n4; e += stride)
-            reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
-        for (long long e = 4 * n4 + t0; e < n; e += stride) Zj[e] = zs[e];
+        KT *Zj = Zb + (long long)j * n;
+        long long e0 = t0;
+        if constexpr (sizeof(KT) == 4) {
+            const long long n4 = (n & 3) ? 0 : (n >> 2);
+            for (long long e = t0; e < n4; e += stride)
+                reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
+            e0 = 4 * n4 + t0;
+        }
+        for (long long e = e0; e < n; e += stride) Zj[e] = zs[e];
     }
     for (int i0 = 0; i0 <= j; i0 += NG) {
         const int cnt = min(NG, j + 1 - i0);
         double acc[NG];
-        dots_pass_f32(V, w, n, i0, cnt, acc);
-        block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
-        __syncthreads();  // the block's warp sums are reused by the next group
+        if constexpr (sizeof(KT) == 4) {
+            dots_pass_f32(V, w, n, i0, cnt, acc);
+            block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
+            __syncthreads();  // the block's warp sums are reused by the next group
+        } else {
+            dots_pass<KT>(V, w, n, i0, cnt, acc);
+            write_partials(acc, i0, cnt, partial, nb, sh);
+        }
     }
-    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
 }
 
-// w <- w - sum_i h_i V_i (FP32), then h2_i = <V_i, w> or, with NORM, |w|^2.
+// Passes 2 and 3: w <- w - sum_i h_i V_i (FP32 coefficients on an FP32
+// basis), then the block partials of h2_i = <V_i, w> or, with NORM, of |w|^2.
 // Up to NG products ride on the update sweep; beyond that the updated w is
-// swept again in groups.
-template <bool NORM>
-__global__ void __launch_bounds__(BS, 4) k_update_f32(const float *V, float *w, long long n, int j, const double *h,
-                                                   double *partial, int nb, double *dst, unsigned int *counter,
-                                                   const int *jdev, GivensCtl gc)
+// swept again in groups.  h: the j + 1 coefficients (device or shared memory).
+template <bool NORM, typename KT>
+__device__ __forceinline__ void cgs_update_pass(const KT *V, KT *w, long long n, int j, const double *h,
+                                                double *partial, int nb, double *sh)
 {
-    pdl_entry();
-    __shared__ double sh[BS / 32];
-    __shared__ float hs[MUSIC_MAXV];
-    if (jdev) j = *jdev;
-    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (float)h[i];
+    using CT = KT;  // coefficient type
+    __shared__ CT hs[MUSIC_MAXV];
+    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (CT)h[i];
     __syncthreads();
     const bool fused = NORM || j < NG;
     double acc[NG];
-    float run[NG];
-#pragma unroll
-    for (int i = 0; i < NG; i++) {
-        acc[i] = 0.0;
-        run[i] = 0.0f;
-    }
-    int k = 0;
-    // float4 path only when every basis vector starts 16-byte aligned
-    const long long n4 = (n & 3) ? 0 : (n >> 2);
     const long long stride = (long long)gridDim.x * BS;
     const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    for (long long e = t0; e < n4; e += stride) {
-        float4 we = reinterpret_cast<const float4 *>(w)[e];
-        for (int i = 0; i <= j; i++) {
-            const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
-            const float c = -hs[i];
-            we.x = fmaf(c, v.x, we.x);
-            we.y = fmaf(c, v.y, we.y);
-            we.z = fmaf(c, v.z, we.z);
-            we.w = fmaf(c, v.w, we.w);
-        }
-        reinterpret_cast<float4 *>(w)[e] = we;
-        if (NORM) {
-            run[0] += dot4(we, we);
-        } else if (fused) {
+    if constexpr (sizeof(KT) == 4) {
+        float run[NG];
 #pragma unroll
-            for (int i = 0; i < NG; i++)
-                if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+        for (int i = 0; i < NG; i++) {
+            acc[i] = 0.0;
+            run[i] = 0.0f;
         }
-        if (fused && ++k == RUN) {
-#pragma unroll
-            for (int i = 0; i < NG; i++) {
-                if (NORM ? i == 0 : i <= j) acc[i] += (double)run[i];
-                run[i] = 0.0f;
+        int k = 0;
+        // float4 path only when every basis vector starts 16-byte aligned
+        const long long n4 = (n & 3) ? 0 : (n >> 2);
+        for (long long e = t0; e < n4; e += stride) {
+            float4 we = reinterpret_cast<const float4 *>(w)[e];
+            for (int i = 0; i <= j; i++) {
+                const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
+                const float c = -hs[i];
+                we.x = fmaf(c, v.x, we.x);
+                we.y = fmaf(c, v.y, we.y);
+                we.z = fmaf(c, v.z, we.z);
+                we.w = fmaf(c, v.w, we.w);
             }
-            k = 0;
-        }
-    }
+            reinterpret_cast<float4 *>(w)[e] = we;
+            if (NORM) {
+                run[0] += dot4(we, we);
+            } else if (fused) {
 #pragma unroll
-    for (int i = 0; i < NG; i++)
-        if (fused && (NORM ? i == 0 : i <= j)) acc[i] += (double)run[i];
-    for (long long e = 4 * n4 + t0; e < n; e += stride) {
-        float we = w[e];
-        for (int i = 0; i <= j; i++) we = fmaf(-hs[i], V[(long long)i * n + e], we);
-        w[e] = we;
+                for (int i = 0; i < NG; i++)
+                    if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
+            }
+            if (fused && ++k == RUN) {
+#pragma unroll
+                for (int i = 0; i < NG; i++) {
+                    if (NORM ? i == 0 : i <= j) acc[i] += (double)run[i];
+                    run[i] = 0.0f;
+                }
+                k = 0;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NG; i++)
+            if (fused && (NORM ? i == 0 : i <= j)) acc[i] += (double)run[i];
+        for (long long e = 4 * n4 + t0; e < n; e += stride) {
+            float we = w[e];
+            for (int i = 0; i <= j; i++) we = fmaf(-hs[i], V[(long long)i * n + e], we);
+            w[e] = we;
+            if (NORM) {
+                acc[0] += (double)(we * we);
+            } else if (fused) {
+#pragma unroll
+                for (int i = 0; i < NG; i++)
+                    if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
+            }
+        }
         if (NORM) {
-            acc[0] += (double)(we * we);
+            block_partials_mixed<1>(acc, 1, partial, nb);
         } else if (fused) {
-#pragma unroll
-            for (int i = 0; i < NG; i++)
-                if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
+            block_partials_mixed<NG>(acc, j + 1, partial, nb);
+        } else {
+            for (int i0 = 0; i0 <= j; i0 += NG) {
+                const int cnt = min(NG, j + 1 - i0);
+                dots_pass_f32(V, w, n, i0, cnt, acc);
+                block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
+                __syncthreads();
+            }
         }
-    }
-    if (NORM) {
-        block_partials_mixed<1>(acc, 1, partial, nb);
-    } else if (fused) {
-        block_partials_mixed<NG>(acc, j + 1, partial, nb);
     } else {
-        for (int i0 = 0; i0 <= j; i0 += NG) {
-            const int cnt = min(NG, j + 1 - i0);
-            dots_pass_f32(V, w, n, i0, cnt, acc);
-            block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
-            __syncthreads();
+#pragma unroll
+        for (int i = 0; i < NG; i++) acc[i] = 0.0;
+        for (long long e = t0; e < n; e += stride) {
+            double we = (double)w[e];
+            for (int i = 0; i <= j; i++) we -= hs[i] * (double)V[(long long)i * n + e];
+            const KT ws = (KT)we;
+            w[e] = ws;
+            const double wr = (double)ws;
+            if (NORM) {
+                acc[0] += wr * wr;
+            } else if (fused) {
+#pragma unroll
+                for (int i = 0; i < NG; i++)
+                    if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
+            }
+        }
+        if (NORM) {
+            write_partials(acc, 0, 1, partial, nb, sh);
+        } else if (fused) {
+            write_partials(acc, 0, j + 1, partial, nb, sh);
+        } else {
+            for (int i0 = 0; i0 <= j; i0 += NG) {
+                const int cnt = min(NG, j + 1 - i0);
+                dots_pass<KT>(V, w, n, i0, cnt, acc);
+                write_partials(acc, i0, cnt, partial, nb, sh);
+            }
         }
     }
+}
+
+// h_i = <V_i, w>, i <= j (j read from jdev when given); with Zb, also Z_j = zs
+template <typename KT>
+__global__ void __launch_bounds__(BS, sizeof(KT) == 4 ? 4 : 1) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
+                                                int nb, double *dst, unsigned int *counter, const int *jdev,
+                                                const KT *zs, KT *Zb)
+{
+    pdl_entry();
+    __shared__ double sh[BS / 32];
+    if (jdev) j = *jdev;
+    cgs_dots_pass<KT>(V, w, n, j, partial, nb, zs, Zb, sh);
+    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+}
+
+// w <- w - sum_i h_i V_i, then h2_i = <V_i, w> (second CGS pass) or, with
+// NORM, |w|^2 only; with gc.c the last block then runs the Arnoldi step's
+// Givens control
+template <bool NORM, typename KT>
+__global__ void __launch_bounds__(BS, sizeof(KT) == 4 ? 4 : 1) k_update(const KT *V, KT *w, long long n, int j, const double *h,
+                                                  double *partial, int nb, double *dst, unsigned int *counter,
+                                                  const int *jdev, GivensCtl gc)
+{
+    pdl_entry();
+    __shared__ double sh[BS / 32];
+    if (jdev) j = *jdev;
+    cgs_update_pass<NORM, KT>(V, w, n, j, h, partial, nb, sh);
     if (last_block_done(counter)) {
         if (NORM)
             finish_sums<BS>(partial, nb, nb, 1, dst, sh);
@@ -560,8 +549,8 @@ int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
     unsigned int *cnt = &g->ds->counters[CNT_DOTS];
     void *Zb = krylov_zstore(g);
     if (g->mixed)
-        k_dots_f32<<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
-                                        g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
+        k_dots<float><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
+                                           g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
     else
         k_dots<double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials, g->nb,
                                             g->ds->h, cnt, jdev, (const double *)g->z, (double *)Zb);
@@ -577,8 +566,8 @@ int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaSt
     double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
     unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
     if (g->mixed)
-        k_update_f32<NORM><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials, g->nb,
-                                                dst, cnt, jdev, gc);
+        k_update<NORM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials, g->nb,
+                                                   dst, cnt, jdev, gc);
     else
         k_update<NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h, g->partials,
                                                     g->nb, dst, cnt, jdev, gc);

@@ -198,6 +198,7 @@ int newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t 
     const size_t n = g->n;
     const size_t nq = g->sc.n;
     CUDA_TRY(cudaMemcpyAsync(g->Un, g->U, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+
     // Without scalars one evaluation of R(U^n) gives the step constant C^n and
     // the first iteration's residual (U = U^n there); with them the scalars'
     // flux captures keep the two evaluations apart.

@@ -53,7 +53,8 @@ def test_struct_layouts_match_binding(tmp_path):
     from paper_1610_10053_gb300 import binding as b
     structs = {"music_grid_desc": b.GridDesc, "music_step_stats": b.StepStats,
                "music_server_opts": b.ServerOpts, "music_solve_req": b.SolveReq,
-               "music_solve_result": b.SolveResult, "music_tune_report": b.TuneReport, "music_dt_limits": b.DtLimits}
+               "music_solve_result": b.SolveResult, "music_tune_report": b.TuneReport, "music_dt_limits": b.DtLimits,
+               "music_peaks": b.Peaks}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "music_server.h"', "int main(void) {"]
     for cname, cls in structs.items():
         lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))

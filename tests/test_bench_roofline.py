@@ -74,3 +74,18 @@ def test_job_rate_and_clock_summary(bench):
     assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["sw_power_cap"]
     assert bench.ClockSampler(0).summary()["reasons"] == ["unsampled"]
+
+
+def test_measured_alu_peak_is_the_denominator(bench):
+    """With the FMA throughput measured in the run (music_measure_peaks), the
+    FP64 residual's fraction is taken against the measured FP64 figure; the
+    unit-count figure is kept in the note only."""
+    p = I.kelvin_helmholtz(n=512)
+    alu = {"fp64_fma_tflops": 1.058, "fp32_fma_tflops": 76.3, "fp64_div_gops": 61.4, "sms": 152}
+    r = bench.roofline(classes(1.02), p, "diff", alu)
+    assert r["peak"] == pytest.approx(1.058)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.058)
+    assert "measured" in r["peak_note"] and r["measured_alu_peaks"] == alu
+    # the FP32 product's class uses the FP32 figure
+    r = bench.roofline(classes(0.1, jv_ms=2.0), p, "diff", alu)
+    assert r["class"] == "jv" and r["peak"] == pytest.approx(76.3)

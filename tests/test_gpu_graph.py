@@ -170,3 +170,4 @@ def test_loop_body_bound_expires_with_timeout(solver, monkeypatch):
         g.set_state(p.U)
         st = g.step()
         assert st["newton_its"] >= 1 and st["gmres_its"] > 5
+
