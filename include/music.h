@@ -271,9 +271,18 @@ typedef struct {
     int residual_tile[2];     /* chosen (TX, TY) of the stencil's R, C^n and F modes, timed as
                                  one F evaluation on the same candidates as the stencil */
     double residual_us[8];
+    int batch_tile[2];        /* chosen (TX, TY) of the persistent batched kernel
+                                 (music_batch_step), timed with MUSIC_TUNE_BATCH as one batched
+                                 step of this grid alone, for grids of at most 65536 cells that
+                                 it accepts */
+    int n_batch, pad;         /* its candidates timed (0 when not timed) */
+    int batch_cand[4][2];     /* candidate (TX, TY) ... */
+    double batch_us[4];       /* ... and their median times in microseconds */
 } music_tune_report;
 
 #define MUSIC_TUNE_FORCE 1u   /* time the candidates even when the configuration is cached */
+#define MUSIC_TUNE_BATCH 2u   /* also time the persistent batched kernel's tile shapes (grids of
+                                 at most 65536 cells that music_batch_step accepts) */
 
 /*
  * Time every candidate tile shape of the grid's fused 2-D kernels on its
@@ -298,6 +307,14 @@ int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_repor
    reads the current choice. */
 int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile, int precond_stages);
 int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile, int *precond_stages);
+
+/* Tile shape (TX, TY) of the persistent batched kernel for this grid: one of
+   32 x 16, 16 x 32, 64 x 8 (a CTA of 512 threads each, so every shape gives
+   bitwise the same step).  music_batch_step runs a batch with the shape of
+   its first grid; music_autotune picks it by timing for small grids.
+   MUSIC_E_INVAL for a shape that is not a candidate. */
+int music_set_batch_tile(music_grid *grid, const int *tile);
+int music_get_batch_tile(const music_grid *grid, int *tile);
 
 /*
  * Form of the Jacobian-free product of a MUSIC_MIXED grid (Sec. 2; used by

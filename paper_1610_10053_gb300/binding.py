@@ -71,7 +71,8 @@ class TuneReport(ctypes.Structure):
                 ("n_precond", ctypes.c_int), ("stencil_cand", (ctypes.c_int * 2) * 8),
                 ("precond_cand", (ctypes.c_int * 3) * 24), ("stencil_us", ctypes.c_double * 8),
                 ("precond_us", ctypes.c_double * 24), ("residual_tile", ctypes.c_int * 2),
-                ("residual_us", ctypes.c_double * 8)]
+                ("residual_us", ctypes.c_double * 8), ("batch_tile", ctypes.c_int * 2), ("n_batch", ctypes.c_int),
+                ("pad", ctypes.c_int), ("batch_cand", (ctypes.c_int * 2) * 4), ("batch_us", ctypes.c_double * 4)]
 
     def as_dict(self):
         """stencil_us and residual_us keys: (TX, TY); precond_us keys: (TX, TY, stages)."""
@@ -80,10 +81,13 @@ class TuneReport(ctypes.Structure):
                 "precond_stages": self.precond_stages, "residual_tile": tuple(self.residual_tile),
                 "stencil_us": {tuple(self.stencil_cand[i]): self.stencil_us[i] for i in range(self.n_stencil)},
                 "residual_us": {tuple(self.stencil_cand[i]): self.residual_us[i] for i in range(self.n_stencil)},
-                "precond_us": {tuple(self.precond_cand[i]): self.precond_us[i] for i in range(self.n_precond)}}
+                "precond_us": {tuple(self.precond_cand[i]): self.precond_us[i] for i in range(self.n_precond)},
+                "batch_tile": tuple(self.batch_tile),
+                "batch_us": {tuple(self.batch_cand[i]): self.batch_us[i] for i in range(self.n_batch)}}
 
 
 MUSIC_TUNE_FORCE = 1
+MUSIC_TUNE_BATCH = 2
 
 
 class Peaks(ctypes.Structure):
@@ -138,6 +142,8 @@ SIGNATURES = {
                                                 _dbl_p]),
     "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
+    "music_set_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "music_get_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -420,22 +426,32 @@ class Grid:
         cfl, cfl_adv and cfl_rad), capped by dt_max (default: the problem's)."""
         return self.newton_step(self.prob.dt_max if dt_max is None else dt_max)
 
-    def autotune(self, dt: Optional[float] = None, force: bool = False) -> dict:
-        """Pick the fused kernels' tile shapes by timing (music_autotune); dt
-        defaults to the CFL step of the problem."""
+    def autotune(self, dt: Optional[float] = None, force: bool = False, batch: bool = False) -> dict:
+        """Pick the fused kernels' tile shapes by timing (music_autotune), with
+        `batch` also the batched kernel's; dt defaults to the CFL step of the
+        problem."""
         if dt is None:
             dt = self.cfl_dt(self.prob.cfl)
             if self.prob.dt_max and 0 < self.prob.dt_max < dt:
                 dt = self.prob.dt_max
         rep = TuneReport()
-        check(load().music_autotune(self.h, float(dt), MUSIC_TUNE_FORCE if force else 0, ctypes.byref(rep),
-                                    _stream()))
+        flags = (MUSIC_TUNE_FORCE if force else 0) | (MUSIC_TUNE_BATCH if batch else 0)
+        check(load().music_autotune(self.h, float(dt), flags, ctypes.byref(rep), _stream()))
         return rep.as_dict()
 
     def set_tiles(self, stencil=None, precond=None, stages: int = 0):
         st = (ctypes.c_int * 2)(*stencil) if stencil is not None else None
         pt = (ctypes.c_int * 2)(*precond) if precond is not None else None
         check(load().music_set_tiles(self.h, st, pt, int(stages)))
+
+    def set_batch_tile(self, tile):
+        """Tile shape of the persistent batched kernel (music_set_batch_tile)."""
+        check(load().music_set_batch_tile(self.h, (ctypes.c_int * 2)(*tile)))
+
+    def batch_tile(self):
+        t = (ctypes.c_int * 2)()
+        check(load().music_get_batch_tile(self.h, t))
+        return tuple(t)
 
     def set_jv_form(self, form: int):
         """JV_FD64 or JV_DIFF32 (mixed grids): the form of the Jacobian-free

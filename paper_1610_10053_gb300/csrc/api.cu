@@ -249,6 +249,7 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     g->rtile = STENCIL_TILE_DEFAULT;
     g->ptile = PRECOND_TILE_DEFAULT;
     g->psplit = default_split(d.precond_sweeps);
+    g->btile = BATCH_TILE_DEFAULT;
     tune_lookup(g);  // shapes an earlier tuning picked for this configuration
     g->n = (size_t)g->P.nv * g->P.N;
     g->ns = d.nscalars;

@@ -1,0 +1,7 @@
+// The persistent batched kernel with 32x16 tiles (one translation unit per
+// shape, so the library builds in parallel).
+#include "batched_impl.cuh"
+
+namespace batch {
+MUSIC_BATCHED_INSTANTIATE(32, 16)
+}

@@ -65,6 +65,7 @@ struct music_grid {
     int stile, ptile;     // tile shapes of the fused 2-D stencil / preconditioner (indices, tiles.h)
     int rtile;            // tile shape of the stencil's R, C^n and F modes (stile: its Jv mode)
     int psplit;           // launches the fused preconditioner's sweeps are split over (1, 2 or 4)
+    int btile;            // tile shape of the batched kernel (index, tiles.h)
     int jv_form;          // JV_*: form of the Krylov products of a mixed-precision grid
     int loop_cap;         // bound on the loop bodies of one Newton attempt (0: the default
                           // newton_max (restarts + 1) (m + 3) + 64, loop_cap_of)

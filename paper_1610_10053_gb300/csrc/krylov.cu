@@ -29,15 +29,25 @@ __global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *p
     pdl_entry();
     __shared__ double sh[BS / 32];
     double s = 0.0;
-    // four elements' loads in flight per step, summed in element order
+    // four elements' loads in flight per step, summed in element order; an
+    // FP32 vector's squares are summed in FP32 over each step's four, then
+    // added in FP64 (as the dot products do: FP64 adds run at 1/73 of the FP32
+    // rate on this part)
     const long long stride = (long long)gridDim.x * BS;
     long long i = blockIdx.x * (long long)BS + threadIdx.x;
     for (; i + 3 * stride < n; i += 4 * stride) {
-        double v[4];
+        T v[4];
 #pragma unroll
-        for (int r = 0; r < 4; r++) v[r] = (double)x[i + r * stride];
+        for (int r = 0; r < 4; r++) v[r] = x[i + r * stride];
+        if constexpr (sizeof(T) == 4) {
+            float q = v[0] * v[0];
 #pragma unroll
-        for (int r = 0; r < 4; r++) s += v[r] * v[r];
+            for (int r = 1; r < 4; r++) q = fmaf(v[r], v[r], q);
+            s += (double)q;
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; r++) s += v[r] * v[r];
+        }
     }
     for (; i < n; i += stride) {
         const double v = (double)x[i];

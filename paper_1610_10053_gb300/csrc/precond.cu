@@ -158,6 +158,29 @@ __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, PcK<PT> K
     }
 }
 
+// One weighted-Jacobi update of cell c (coordinates ix) from dp, with the
+// neighbour rule of cell_nb (periodic wrap; at a wall the neighbour beyond it
+// is the cell itself, whose wall coefficient is zero); nb(cell) returns dp at
+// an interior cell index.
+template <typename PT, typename NB>
+__device__ __forceinline__ PT jacobi_cell(const GridParams &P, const PC<PT> &C, const PcK<PT> &K, const PT *b,
+                                          const int ix[3], long long c, PT tau2, PT w, NB &&nb)
+{
+    PT off = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= P.nd) break;
+        const int n = P.n[d], a = ix[d];
+        const long long st = P.cs[d];
+        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
+        const long long cu = (a + 1 < n) ? c + st : (per ? c - (long long)(n - 1) * st : c);
+        const long long cd = (a > 0) ? c - st : (per ? c + (long long)(n - 1) * st : c);
+        const PT ap = (!per && a == n - 1) ? (PT)0 : C.a[d][cu], am = C.a[d][c];
+        off += (ap * nb(cu, d, +1) + am * nb(cd, d, -1)) * K.idx2[d];
+    }
+    return ((PT)1 - w) * nb(c, 0, 0) + w * ((b[c] + tau2 * off) / C.D[c]);
+}
+
 // The same sweep as k_jacobi on a 3-D launch grid: x along the threads of a
 // row of XT, y and z by block, so no index is decomposed; the neighbours are
 // the ones cell_nb gives (periodic wrap, walls clamped onto the cell, whose
@@ -181,19 +204,7 @@ __global__ void __launch_bounds__(XT) k_jacobi_rows(GridParams P, PC<PT> C, PcK<
         dq[c] = w * (b[c] / C.D[c]);
         return;
     }
-    PT off = 0;
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        if (d >= P.nd) break;
-        const int n = P.n[d], a = ix[d];
-        const long long st = P.cs[d];
-        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
-        const long long cu = (a + 1 < n) ? c + st : (per ? c - (long long)(n - 1) * st : c);
-        const long long cd = (a > 0) ? c - st : (per ? c + (long long)(n - 1) * st : c);
-        const PT ap = (!per && a == n - 1) ? (PT)0 : C.a[d][cu], am = C.a[d][c];
-        off += (ap * dp[cu] + am * dp[cd]) * K.idx2[d];
-    }
-    dq[c] = ((PT)1 - w) * dp[c] + w * ((b[c] + tau2 * off) / C.D[c]);
+    dq[c] = jacobi_cell(P, C, K, b, ix, c, tau2, w, [&](long long q, int, int) { return dp[q]; });
 }
 
 template <typename PT, typename RT>

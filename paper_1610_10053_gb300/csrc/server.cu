@@ -214,6 +214,10 @@ void lane_main(music_server *S)
             music_grid *g = nullptr;
             int rc = grid_create(&j->desc, s, &g);
             if (rc == MUSIC_OK) rc = grid_set_state(g, j->U0.data(), 0, s);
+            // (the lane's grids run the batched kernel only: they take the
+            // batched tile shape cached for their configuration by an earlier
+            // music_autotune with MUSIC_TUNE_BATCH, if any; timing the shapes
+            // here would cost a batched step per candidate inside the service)
             if (rc != MUSIC_OK) {
                 if (g) grid_destroy(g);
                 std::lock_guard<std::mutex> lk(S->mu);

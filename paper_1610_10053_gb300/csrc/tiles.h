@@ -44,6 +44,22 @@ inline bool pc_fits(TileShape t, int sweeps, int stages, size_t elem)
     return 6 * (t.x + 2 * h) * (t.y + 2 * h) * elem + (size_t)t.x * t.y * sizeof(double) + 256 <= PC_SMEM_LIMIT;
 }
 
+// Tile shapes of the persistent batched kernel (music_batch_step).  Its CTA
+// is one tile of 512 threads whatever the shape, so every CTA-wide sum runs
+// in the same order and all shapes give bitwise identical results.
+constexpr int N_BATCH_TILES = 3;
+constexpr TileShape BATCH_TILES[N_BATCH_TILES] = {{32, 16}, {16, 32}, {64, 8}};
+constexpr int BATCH_TILE_DEFAULT = 0;
+// grids small enough for the autotuner to time a batched step of (a batched
+// step runs a whole grid on one SM)
+constexpr long long BATCH_TUNE_MAX_CELLS = 65536;
+// a grid the batched kernel accepts: 2-D Cartesian, no radiative diffusion,
+// at most 16 preconditioner sweeps, no passive scalars (batched.cu)
+bool batchable(const music_grid *g);
+// one batched step of `count` grids with batched tile `tile` (no read-back;
+// grids must be batchable and share a precision; batched.cu)
+int batch_launch(music_grid **grids, int count, const double *cfl, const double *dt_max, int tile, cudaStream_t s);
+
 // fused 2-D stencil of one tile shape (same contract as stencil_apply's
 // fused branch; hdt = dt / 2)
 template <int TX, int TY>

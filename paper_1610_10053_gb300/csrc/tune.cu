@@ -1,6 +1,7 @@
 // Autotuner of the fused 2-D kernels' tile shapes (the stencil's Jv mode and
-// its R / C^n / F modes separately, the preconditioner) and of the halo depth
-// of the fused preconditioner (its sweeps in 1, 2 or 4 launches).  The paper's
+// its R / C^n / F modes separately, the preconditioner), of the halo depth
+// of the fused preconditioner (its sweeps in 1, 2 or 4 launches) and of the
+// persistent batched kernel's tile shape (small grids).  The paper's
 // code ran on CPUs; this has no counterpart there.  Every candidate computes
 // the same result bitwise (tiles.h), so the choice is by speed alone: each is
 // timed with CUDA events on the grid's own state, the median of a few
@@ -25,7 +26,7 @@ using Key = std::tuple<int, int, int, int, int, int, int>;
 
 std::mutex g_tune_mu;
 struct Choice {
-    int stile, rtile, ptile, psplit;
+    int stile, rtile, ptile, psplit, btile, btimed;  // btimed: the batched shapes were timed
 };
 std::map<Key, Choice> g_tune_cache;  // -> stencil tiles (Jv, residual), preconditioner tile and stages
 
@@ -163,6 +164,63 @@ int tune(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
     return MUSIC_OK;
 }
 
+// The batched kernel's tile: one batched step of this grid alone per
+// candidate (a batched step runs the whole grid on one SM, so the grid's
+// latency on one SM is what the shape changes), from the same state each
+// time; the step size is dt (cfl left unbounded, dt_max = dt).
+int tune_batch(music_grid *g, double dt, music_tune_report *rep, cudaStream_t s)
+{
+    Events E;
+    TRY(E.make());
+    double best = 1e300;
+    if (batchable(g) && g->P.N <= BATCH_TUNE_MAX_CELLS) {
+        const size_t bytes = g->n * sizeof(double);
+        double *U0 = nullptr;
+        CUDA_TRY(cudaMallocAsync((void **)&U0, bytes, s));
+        int rc = MUSIC_OK;
+        if (cudaMemcpyAsync(U0, g->U, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("music_autotune: state copy failed");
+            rc = MUSIC_E_CUDA;
+        }
+        const double cfl = 1e300, dtm = dt;
+        music_grid *one[1] = {g};
+        best = 1e300;
+        int best_b = g->btile;
+        for (int t = 0; t < N_BATCH_TILES && rc == MUSIC_OK; t++) {
+            double us = 0.0;
+            rc = time_median(s, E.ev, [&]() -> int {
+                CUDA_TRY(cudaMemcpyAsync(g->U, U0, bytes, cudaMemcpyDeviceToDevice, s));
+                return batch_launch(one, 1, &cfl, &dtm, t, s);
+            }, &us);
+            rep->batch_cand[t][0] = BATCH_TILES[t].x;
+            rep->batch_cand[t][1] = BATCH_TILES[t].y;
+            rep->batch_us[t] = us;
+            if (us < best) {
+                best = us;
+                best_b = t;
+            }
+        }
+        if (rc == MUSIC_OK) {
+            rep->n_batch = N_BATCH_TILES;
+            g->btile = best_b;
+        }
+        if (cudaMemcpyAsync(g->U, U0, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess && rc == MUSIC_OK) {
+            cudaGetLastError();
+            set_error("music_autotune: state restore failed");
+            rc = MUSIC_E_CUDA;
+        }
+        cudaFreeAsync(U0, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess && rc == MUSIC_OK) {
+            cudaGetLastError();
+            set_error("music_autotune: batched timing failed");
+            rc = MUSIC_E_CUDA;
+        }
+        TRY(rc);
+    }
+    return MUSIC_OK;
+}
+
 int tile_index(const TileShape *tab, int n, const int *xy)
 {
     for (int i = 0; i < n; i++)
@@ -206,7 +264,10 @@ void tune_lookup(music_grid *g)
     g->rtile = it->second.rtile;
     g->ptile = it->second.ptile;
     g->psplit = it->second.psplit;
+    g->btile = it->second.btile;
 }
+
+bool batch_tunable(const music_grid *g) { return batchable(g) && g->P.N <= BATCH_TUNE_MAX_CELLS; }
 
 extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tune_report *rep, void *stream)
 {
@@ -217,8 +278,8 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
     memset(rep, 0, sizeof(*rep));
     if (!fused_grid(g)) return MUSIC_OK;  // nothing to tune
     rep->tunable = 1;
-    const int s0 = g->stile, r0 = g->rtile, p0 = g->ptile, q0 = g->psplit;
-    bool cached = false;
+    const int s0 = g->stile, r0 = g->rtile, p0 = g->ptile, q0 = g->psplit, b0 = g->btile;
+    bool cached = false, btimed = false;
     if (!(flags & MUSIC_TUNE_FORCE)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key_of(g));
@@ -227,20 +288,29 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
             g->rtile = it->second.rtile;
             g->ptile = it->second.ptile;
             g->psplit = it->second.psplit;
+            g->btile = it->second.btile;
+            btimed = it->second.btimed;
             cached = true;
         }
     }
-    if (!cached) {
-        const int rc = pinned_tiles(g) ? MUSIC_OK : tune(g, dt, rep, (cudaStream_t)stream);
-        if (rc != MUSIC_OK) {
-            g->stile = s0;
-            g->rtile = r0;
-            g->ptile = p0;
-            g->psplit = q0;
-            return rc;
-        }
+    const bool want_batch = (flags & MUSIC_TUNE_BATCH) && batch_tunable(g) && !btimed;
+    int rc = MUSIC_OK;
+    if (!cached) rc = pinned_tiles(g) ? MUSIC_OK : tune(g, dt, rep, (cudaStream_t)stream);
+    if (rc == MUSIC_OK && want_batch) {
+        rc = tune_batch(g, dt, rep, (cudaStream_t)stream);
+        btimed = (rc == MUSIC_OK);
+    }
+    if (rc != MUSIC_OK) {
+        g->stile = s0;
+        g->rtile = r0;
+        g->ptile = p0;
+        g->psplit = q0;
+        g->btile = b0;
+        return rc;
+    }
+    if (!cached || want_batch) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key_of(g)] = Choice{g->stile, g->rtile, g->ptile, g->psplit};
+        g_tune_cache[key_of(g)] = Choice{g->stile, g->rtile, g->ptile, g->psplit, g->btile, btimed ? 1 : 0};
     }
     rep->from_cache = cached ? 1 : 0;
     rep->stencil_tile[0] = STENCIL_TILES[g->stile].x;
@@ -250,6 +320,8 @@ extern "C" int music_autotune(music_grid *g, double dt, unsigned flags, music_tu
     rep->precond_stages = g->psplit;
     rep->residual_tile[0] = STENCIL_TILES[g->rtile].x;
     rep->residual_tile[1] = STENCIL_TILES[g->rtile].y;
+    rep->batch_tile[0] = BATCH_TILES[g->btile].x;
+    rep->batch_tile[1] = BATCH_TILES[g->btile].y;
     if (g->stile != s0 || g->rtile != r0 || g->ptile != p0 || g->psplit != q0)
         graph_release(g);  // recorded with the old ones
     return MUSIC_OK;

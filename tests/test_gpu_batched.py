@@ -82,3 +82,52 @@ def test_batch_rejects_unsupported_grids():
     with B().Grid(pc) as gc:
         with pytest.raises(B().MusicError):
             B().batch_step([gc], cfl=[1.0])
+
+
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_batched_tile_shapes_give_the_same_bits(prec):
+    """Every tile shape of the persistent batched kernel (a CTA of 512 threads
+    whatever the shape) gives bitwise the same step."""
+    probs = problems()
+    out = {}
+    for tile in ((32, 16), (16, 32), (64, 8)):
+        grids = [B().Grid(p, precision=getattr(B(), prec)) for p in probs]
+        for g, p in zip(grids, probs):
+            g.set_state(p.U)
+            g.set_batch_tile(tile)
+            assert g.batch_tile() == tile
+        for _ in range(2):
+            code, st = B().batch_step(grids)
+            assert code == 0, B().last_error()
+        out[tile] = [g.get_state() for g in grids]
+        for g in grids:
+            g.close()
+    ref = out[(32, 16)]
+    for tile, states in out.items():
+        for a, b in zip(states, ref):
+            assert np.array_equal(a, b), tile
+
+
+def test_autotune_picks_a_batched_tile_for_small_grids():
+    """music_autotune with MUSIC_TUNE_BATCH times the batched kernel's shapes
+    on a small grid (one batched step of it alone each, the state restored);
+    without the flag, or on a grid too large for one SM, it leaves them."""
+    p = I.kelvin_helmholtz(n=64, seed=31, nsteps=1)
+    with B().Grid(p, precision=B().MIXED) as g:
+        g.set_state(p.U)
+        rep = g.autotune(force=True)
+        assert rep["batch_us"] == {}
+        rep = g.autotune(force=True, batch=True)
+        assert set(rep["batch_us"]) == {(32, 16), (16, 32), (64, 8)}
+        assert all(t > 0 for t in rep["batch_us"].values())
+        assert rep["batch_tile"] == min(rep["batch_us"], key=rep["batch_us"].get)
+        assert g.batch_tile() == rep["batch_tile"]
+        assert np.array_equal(g.get_state(), p.U)  # tuning leaves the state alone
+    big = I.kelvin_helmholtz(n=512, seed=31, nsteps=1)
+    with B().Grid(big, precision=B().MIXED) as g:
+        g.set_state(big.U)
+        rep = g.autotune(force=True, batch=True)
+        assert rep["batch_us"] == {} and rep["batch_tile"] == (32, 16)
+    with B().Grid(p, precision=B().MIXED) as g:
+        with pytest.raises(B().MusicError):
+            g.set_batch_tile((8, 8))

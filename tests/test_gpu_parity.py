@@ -388,3 +388,4 @@ def test_profile_counts_every_class():
     assert vec[0] >= 3 * st["gmres_its"] and vec[1] > 0.0
     if st["dt_halvings"] == 0:
         assert res[0] == st["newton_its"]
+
