@@ -8,13 +8,15 @@
 //         velocities at U, the face densities, and the FP64-formed backward
 //         differences of rho, e and every u_q along every d
 //   A     the direction's entries: d rho, d E, d e and every d u_q
-//   B     limited slopes and their differences
 //   C     upwind mass and energy fluxes at U and their differences
 //   D     momentum flux differences at cell centres and on edges
 //   E     dR of the interior cells and Jv = v - dt/2 dR.
-// Stages A-E keep their FP32 planes in the FP64 planes of the multi-pass
-// scratch, which are free once the evaluation that opens the Newton
-// iteration has written the linearisation arrays.
+// The limited slopes (and their differences) that C and D need are formed
+// where they are used, by the same function on the same inputs as a slope
+// stage would (twice the slope arithmetic, in FP32, instead of thirty planes
+// written and read back).  Stages A-E keep their FP32 planes in the FP64
+// planes of the multi-pass scratch, which are free once the evaluation that
+// opens the Newton iteration has written the linearisation arrays.
 #include "internal.h"
 #include "tile_jvdiff.cuh"
 
@@ -59,7 +61,6 @@ LinX linx_of(const music_grid *g)
 // FP32 scratch of stages A-E, carved from the FP64 multi-pass planes
 struct DiffX {
     float *dr, *dE, *de, *du[3];
-    float *Sr[3], *dSr[3], *Se[3], *dSe[3], *Su[3][3], *dSu[3][3];
     float *Fr[3], *dFr[3], *dFE[3];
     float *dPhi[3], *dPsi[3][3];
 };
@@ -92,21 +93,14 @@ int diffx_of(music_grid *g, DiffX *D)
     R.de = take();
     for (int d = 0; d < nd; d++) R.du[d] = take();
     for (int d = 0; d < nd; d++) {
-        R.Sr[d] = take();
-        R.dSr[d] = take();
-        R.Se[d] = take();
-        R.dSe[d] = take();
         R.Fr[d] = take();
         R.dFr[d] = take();
         R.dFE[d] = take();
         R.dPhi[d] = take();
     }
     for (int q = 0; q < nd; q++)
-        for (int d = 0; d < nd; d++) {
-            R.Su[q][d] = take();
-            R.dSu[q][d] = take();
+        for (int d = 0; d < nd; d++)
             if (q != d) R.dPsi[q][d] = take();
-        }
     if (k > 2 * np) {
         set_error("difference-form Jv: %d FP32 planes exceed the multi-pass scratch", k);
         return MUSIC_E_INVAL;
@@ -211,27 +205,14 @@ __global__ void __launch_bounds__(BS) k_dload(GridParams P, const double *U, con
     }
 }
 
-// ---- B: limited slopes of rho, e and every u_q along every d, and their differences
-__global__ void __launch_bounds__(BS) k_dslopes(GridParams P, const double *eps_dev, LinX L, DiffX D)
+// The limited slope of a quantity along d at point y, and its difference:
+// backward differences at U (FP64-formed, Dq) at y and y + s, the
+// direction's entries dq at y - s, y, y + s.  Valid where y has both
+// neighbours along d.
+__device__ __forceinline__ void slope_at(const float *Dq, const float *dq, long long y, long long s, const Kc &K,
+                                         float &S, float &dS)
 {
-    pdl_entry();
-    const Kc K = launch_consts(P, eps_dev, 0.0);
-    if (K.eps64 == 0.0) return;
-    for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
-        int ix[3];
-        ext_coords(P, x, ix);
-        for (int d = 0; d < P.nd; d++) {
-            if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, d, +1)) continue;
-            const long long s = P.es[d];
-            vanleer_d(L.Dr[d][x], L.Dr[d][x + s], D.dr[x] - D.dr[x - s], D.dr[x + s] - D.dr[x], K.eps, K.ieps,
-                      D.Sr[d][x], D.dSr[d][x]);
-            vanleer_d(L.De[d][x], L.De[d][x + s], D.de[x] - D.de[x - s], D.de[x + s] - D.de[x], K.eps, K.ieps,
-                      D.Se[d][x], D.dSe[d][x]);
-            for (int q = 0; q < P.nd; q++)
-                vanleer_d(L.Du[q][d][x], L.Du[q][d][x + s], D.du[q][x] - D.du[q][x - s], D.du[q][x + s] - D.du[q][x],
-                          K.eps, K.ieps, D.Su[q][d][x], D.dSu[q][d][x]);
-        }
-    }
+    vanleer_d(Dq[y], Dq[y + s], dq[y] - dq[y - s], dq[y + s] - dq[y], K.eps, K.ieps, S, dS);
 }
 
 // ---- C: upwind mass and energy fluxes on d-faces; the face velocity decides
@@ -247,11 +228,17 @@ __global__ void __launch_bounds__(BS) k_dfluxes(GridParams P, const double *eps_
             if (!ext_has(P, ix, d, -2) || !ext_has(P, ix, d, +1)) continue;
             const long long s = P.es[d];
             const float u = L.u[d][x], du = D.du[d][x], u2 = fmaf(K.eps, du, u);
+            // slopes of rho and e of the two cells the face joins
+            float Srm, dSrm, Sr0, dSr0, Sem, dSem, Se0, dSe0;
+            slope_at(L.Dr[d], D.dr, x - s, s, K, Srm, dSrm);
+            slope_at(L.Dr[d], D.dr, x, s, K, Sr0, dSr0);
+            slope_at(L.De[d], D.de, x - s, s, K, Sem, dSem);
+            slope_at(L.De[d], D.de, x, s, K, Se0, dSe0);
             float rs, drs, es, des;
-            upwind_d(u, u2, L.r[x - s] + 0.5f * D.Sr[d][x - s], D.dr[x - s] + 0.5f * D.dSr[d][x - s],
-                     L.r[x] - 0.5f * D.Sr[d][x], D.dr[x] - 0.5f * D.dSr[d][x], K.ieps, rs, drs);
-            upwind_d(u, u2, L.e[x - s] + 0.5f * D.Se[d][x - s], D.de[x - s] + 0.5f * D.dSe[d][x - s],
-                     L.e[x] - 0.5f * D.Se[d][x], D.de[x] - 0.5f * D.dSe[d][x], K.ieps, es, des);
+            upwind_d(u, u2, L.r[x - s] + 0.5f * Srm, D.dr[x - s] + 0.5f * dSrm, L.r[x] - 0.5f * Sr0,
+                     D.dr[x] - 0.5f * dSr0, K.ieps, rs, drs);
+            upwind_d(u, u2, L.e[x - s] + 0.5f * Sem, D.de[x - s] + 0.5f * dSem, L.e[x] - 0.5f * Se0,
+                     D.de[x] - 0.5f * dSe0, K.ieps, es, des);
             const float fr = u * rs, dfr = du * fmaf(K.eps, drs, rs) + u * drs;
             D.Fr[d][x] = fr;
             D.dFr[d][x] = dfr;
@@ -272,17 +259,24 @@ __global__ void __launch_bounds__(BS) k_dmomentum(GridParams P, const double *ep
         ext_coords(P, x, ix);
         for (int d = 0; d < P.nd; d++) {
             const long long s = P.es[d];
-            if (ext_has(P, ix, d, -2) && ext_has(P, ix, d, +2))
-                D.dPhi[d][x] = momflux_d(D.Fr[d][x], D.Fr[d][x + s], D.dFr[d][x], D.dFr[d][x + s], L.u[d][x],
-                                         D.Su[d][d][x], D.du[d][x], D.dSu[d][d][x], L.u[d][x + s], D.Su[d][d][x + s],
-                                         D.du[d][x + s], D.dSu[d][d][x + s], K.eps, K.ieps);
+            if (ext_has(P, ix, d, -2) && ext_has(P, ix, d, +2)) {
+                // slopes of u_d along d at the centre's two faces
+                float S0, dS0, S1, dS1;
+                slope_at(L.Du[d][d], D.du[d], x, s, K, S0, dS0);
+                slope_at(L.Du[d][d], D.du[d], x + s, s, K, S1, dS1);
+                D.dPhi[d][x] = momflux_d(D.Fr[d][x], D.Fr[d][x + s], D.dFr[d][x], D.dFr[d][x + s], L.u[d][x], S0,
+                                         D.du[d][x], dS0, L.u[d][x + s], S1, D.du[d][x + s], dS1, K.eps, K.ieps);
+            }
             for (int q = 0; q < P.nd; q++) {
                 if (q == d) continue;
                 if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, q, -2) || !ext_has(P, ix, q, +1)) continue;
                 const long long t = P.es[q];
+                // slopes of u_d along q at the edge's two faces
+                float Sm, dSm, S0, dS0;
+                slope_at(L.Du[d][q], D.du[d], x - t, t, K, Sm, dSm);
+                slope_at(L.Du[d][q], D.du[d], x, t, K, S0, dS0);
                 D.dPsi[d][q][x] = momflux_d(D.Fr[q][x - s], D.Fr[q][x], D.dFr[q][x - s], D.dFr[q][x], L.u[d][x - t],
-                                            D.Su[d][q][x - t], D.du[d][x - t], D.dSu[d][q][x - t], L.u[d][x],
-                                            D.Su[d][q][x], D.du[d][x], D.dSu[d][q][x], K.eps, K.ieps);
+                                            Sm, D.du[d][x - t], dSm, L.u[d][x], S0, D.du[d][x], dS0, K.eps, K.ieps);
             }
         }
     }
@@ -366,8 +360,6 @@ int jvdiff_multipass(music_grid *g, const double *U, const float *v, float *out,
     const double *eps = &g->ds->eps;
     const int nbm = blocks_for(P.M);
     k_dload<float><<<nbm, BS, 0, s>>>(P, U, v, eps, L, D);
-    CHECK_LAUNCH();
-    k_dslopes<<<nbm, BS, 0, s>>>(P, eps, L, D);
     CHECK_LAUNCH();
     k_dfluxes<<<nbm, BS, 0, s>>>(P, eps, L, D);
     CHECK_LAUNCH();
