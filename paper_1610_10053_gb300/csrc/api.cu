@@ -203,7 +203,7 @@ void alloc_plan(music_grid *g, F &&f)
     }
     // reduction partials: the Krylov kernels' and the preconditioner's
     // tile-independent |z|^2 blocks (2-D)
-    size_t np = (size_t)MUSIC_MAXV * g->nb;
+    size_t np = (size_t)MUSIC_MAXV * (g->nb > VEC_BLOCKS_MAX ? g->nb : VEC_BLOCKS_MAX);
     if (P.nd == 2 && (size_t)tile::norm_partial_count(P) > np) np = (size_t)tile::norm_partial_count(P);
     f((void **)&g->partials, np * sizeof(double));
     f((void **)&g->hg, (size_t)(MUSIC_MAXV * MUSIC_MAXV + 4 * MUSIC_MAXV) * sizeof(double));

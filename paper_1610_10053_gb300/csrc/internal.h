@@ -167,6 +167,11 @@ inline void *krylov_zstore(const music_grid *g)
     return (g->desc.precond == MUSIC_PC_NONE || g->in_scalar) ? nullptr : g->Z;
 }
 
+// SMs of the part, and the most blocks a vector sweep of krylov.cu takes
+// (its partials per reduced quantity): two per SM, all resident at once
+constexpr int NUM_SMS = 152;
+constexpr int VEC_BLOCKS_MAX = 2 * NUM_SMS;
+
 // error reporting (thread local)
 void set_error(const char *fmt, ...);
 #define CUDA_TRY(call)                                                                  \

@@ -4,10 +4,19 @@
 // FP64 accumulation; norms; the cycle's correction from the stored
 // preconditioned basis; the Newton update with its density-correction test.
 //
+// Every sweep takes its vectors in 16-byte chunks (4 floats or 2 doubles;
+// element by element when a vector's length is not a multiple of 16 bytes).
+// A thread owns a fixed set of chunks and issues the loads of K of them, in
+// every vector the pass reads, before it uses any: at the few chunks a
+// thread owns here, a pass is bound by the latency of its loads, and one
+// round trip per K chunks instead of one per chunk and vector is what makes
+// it fast.  The passes are specialised on the number of basis vectors they
+// read together (1 to 8), so those loads are independent instructions.
+//
 // Reductions are two-stage and deterministic: every block writes one partial
 // per quantity, then the last block to finish sums the partials in block
-// order.  The block count per grid is fixed, so results do not depend on
-// timing.
+// order.  The block count and the chunks of every thread depend on the
+// vector length alone, so results do not depend on timing.
 #include <cmath>
 
 #include "internal.h"
@@ -16,42 +25,133 @@
 namespace {
 
 constexpr int BS = 256;
-constexpr int RUN = 4;  // float4 chunks summed in FP32 before an FP64 add (16 elements)
+constexpr int NG = 8;  // basis vectors a sweep reads together
 
 struct Coef {
     double c[MUSIC_MAXV];
 };
 
-template <typename T>
-__global__ void __launch_bounds__(BS) k_sumsq(const T *x, long long n, double *partial, double *dst,
+// ---------------------------------------------------------------- chunks
+template <typename T, int W>
+struct Ch {
+    T v[W];
+};
+
+template <typename T, int W>
+__device__ __forceinline__ Ch<T, W> ldch(const T *p, long long c)
+{
+    static_assert(W == 1 || W * sizeof(T) == 16, "a chunk is one element or 16 bytes");
+    Ch<T, W> r;
+    if constexpr (W == 1) {
+        r.v[0] = p[c];
+    } else if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4 *>(p)[c];
+        r.v[0] = a.x;
+        r.v[1] = a.y;
+        r.v[2] = a.z;
+        r.v[3] = a.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2 *>(p)[c];
+        r.v[0] = a.x;
+        r.v[1] = a.y;
+    }
+    return r;
+}
+
+template <typename T, int W>
+__device__ __forceinline__ void stch(T *p, long long c, const Ch<T, W> &r)
+{
+    if constexpr (W == 1) {
+        p[c] = r.v[0];
+    } else if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4 *>(p)[c] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[c] = make_double2(r.v[0], r.v[1]);
+    }
+}
+
+template <typename T, int W>
+__device__ __forceinline__ Ch<T, W> zero_ch()
+{
+    Ch<T, W> r;
+#pragma unroll
+    for (int e = 0; e < W; e++) r.v[e] = (T)0;
+    return r;
+}
+
+// chunk c of a load that may lie beyond the last chunk (then zero)
+template <typename T, int W>
+__device__ __forceinline__ Ch<T, W> ldch_or0(const T *p, long long c, bool in)
+{
+    return in ? ldch<T, W>(p, c) : zero_ch<T, W>();
+}
+
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
+// The chunks of a sweep: step s of thread t (of T in the grid) takes chunks
+// s K T + k T + t, k < K, consecutive threads reading consecutive chunks.
+struct Sweep {
+    long long T, t;
+    __device__ Sweep() : T((long long)gridDim.x * BS), t(blockIdx.x * (long long)BS + threadIdx.x) {}
+};
+
+// Block partials of cnt <= NG per-thread sums: each warp adds its lanes'
+// values (in FP32 for an FP32 basis, a fixed tree of five levels), then one
+// thread per sum adds the warps' results in FP64 in warp order and writes
+// partial[i * nb + block].  Ends with a barrier, so it may be called again.
+template <typename KT>
+__device__ __forceinline__ void block_partials(const double *acc, int cnt, double *partial, int nb)
+{
+    __shared__ double ws[NG][BS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NG; i++) {
+        if (i < cnt) {
+            if constexpr (sizeof(KT) == 4) {
+                float v = (float)acc[i];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) ws[i][wid] = (double)v;
+            } else {
+                double v = acc[i];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                if (lane == 0) ws[i][wid] = v;
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += BS) {
+        double t = 0.0;
+        for (int w = 0; w < BS / 32; w++) t += ws[i][w];
+        partial[(long long)i * nb + blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// |x|^2: squares summed in T over each step's K chunks, then in FP64
+template <typename T, int W>
+__global__ void __launch_bounds__(BS, 2) k_sumsq(const T *x, long long n, double *partial, double *dst,
                                               unsigned int *counter)
 {
     pdl_entry();
+    constexpr int K = 4;
     __shared__ double sh[BS / 32];
+    const Sweep S;
+    const long long nc = n / W;
     double s = 0.0;
-    // four elements' loads in flight per step, summed in element order; an
-    // FP32 vector's squares are summed in FP32 over each step's four, then
-    // added in FP64 (as the dot products do: FP64 adds run at 1/73 of the FP32
-    // rate on this part)
-    const long long stride = (long long)gridDim.x * BS;
-    long long i = blockIdx.x * (long long)BS + threadIdx.x;
-    for (; i + 3 * stride < n; i += 4 * stride) {
-        T v[4];
+    for (long long base = 0; base < nc; base += K * S.T) {
+        Ch<T, W> xc[K];
 #pragma unroll
-        for (int r = 0; r < 4; r++) v[r] = x[i + r * stride];
-        if constexpr (sizeof(T) == 4) {
-            float q = v[0] * v[0];
-#pragma unroll
-            for (int r = 1; r < 4; r++) q = fmaf(v[r], v[r], q);
-            s += (double)q;
-        } else {
-#pragma unroll
-            for (int r = 0; r < 4; r++) s += v[r] * v[r];
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            xc[k] = ldch_or0<T, W>(x, c, c < nc);
         }
-    }
-    for (; i < n; i += stride) {
-        const double v = (double)x[i];
-        s += v * v;
+        T r = (T)0;
+#pragma unroll
+        for (int k = 0; k < K; k++)
+#pragma unroll
+            for (int e = 0; e < W; e++) r = fmat(xc[k].v[e], xc[k].v[e], r);
+        s += (double)r;
     }
     const double r = block_sum<BS>(s, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -80,40 +180,266 @@ __global__ void k_set_eps(DevScalars *ds, double fixed)
     ds->eps = fd_eps(ds->unorm2, ds->vnorm2);
 }
 
-// The CGS passes hold NG accumulators per thread: a pass over more basis
-// vectors runs in groups of NG, each group one more sweep over w and its
-// NG basis vectors, so the register count (and the occupancy) does not grow
-// with the Arnoldi index.  Every group visits the thread's elements in the
-// same order, so each product is summed exactly as one sweep would sum it.
-constexpr int NG = 8;
+// ---------------------------------------------------------------- CGS passes
+// The passes of one Arnoldi step's CGS2 (classical Gram-Schmidt with one
+// re-orthogonalisation), as block partials, one kernel each.  Products are
+// summed in KT over each step's chunks, then in FP64.
 
-// acc[i] = <V_{i0+i}, w> over the thread's elements in FP64, i < cnt <= NG
-template <typename KT>
-__device__ __forceinline__ void dots_pass(const KT *V, const KT *w, long long n, int i0, int cnt, double acc[NG])
+// acc[i] = <V_{i0+i}, w> over the thread's chunks, i < J; with Zj, also
+// Zj = zs over the same chunks (pass 1 stores the preconditioned vector)
+template <typename KT, int W, int J, int K>
+__device__ __forceinline__ void dots_group(const KT *V, const KT *w, long long n, int i0, double *acc,
+                                           const KT *zs, KT *Zj)
 {
+    const Sweep S;
+    const long long nc = n / W;
 #pragma unroll
-    for (int i = 0; i < NG; i++) acc[i] = 0.0;
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        const double we = (double)w[e];
+    for (int i = 0; i < J; i++) acc[i] = 0.0;
+    for (long long base = 0; base < nc; base += K * S.T) {
+        Ch<KT, W> wc[K], vc[J][K];
 #pragma unroll
-        for (int i = 0; i < NG; i++)
-            if (i < cnt) acc[i] += (double)V[(long long)(i0 + i) * n + e] * we;
-    }
-}
-
-// block partials of acc[0, cnt) into partial[(i0 + i) * nb + block]
-__device__ __forceinline__ void write_partials(const double acc[NG], int i0, int cnt, double *partial, int nb,
-                                               double *sh)
-{
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            const bool in = c < nc;
+            wc[k] = ldch_or0<KT, W>(w, c, in);
 #pragma unroll
-    for (int i = 0; i < NG; i++) {
-        if (i < cnt) {
-            const double r = block_sum<BS>(acc[i], sh);
-            if (threadIdx.x == 0) partial[(long long)(i0 + i) * nb + blockIdx.x] = r;
+            for (int i = 0; i < J; i++) vc[i][k] = ldch_or0<KT, W>(V + (long long)(i0 + i) * n, c, in);
+            if (Zj && in) stch<KT, W>(Zj, c, ldch<KT, W>(zs, c));
+        }
+#pragma unroll
+        for (int i = 0; i < J; i++) {
+            KT r = (KT)0;
+#pragma unroll
+            for (int k = 0; k < K; k++)
+#pragma unroll
+                for (int e = 0; e < W; e++) r = fmat(vc[i][k].v[e], wc[k].v[e], r);
+            acc[i] += (double)r;
         }
     }
 }
 
+// chunks a step of a pass reading J basis vectors: fewer when more vectors
+// come with each chunk (registers)
+template <int J>
+constexpr int steps_k() { return J <= 3 ? 4 : 2; }
+
+// dots_group for cnt = 1..NG vectors (cnt known on the device only)
+template <typename KT, int W>
+__device__ __forceinline__ void dots_any(int cnt, const KT *V, const KT *w, long long n, int i0, double *acc,
+                                         const KT *zs, KT *Zj)
+{
+    switch (cnt) {
+    case 1: dots_group<KT, W, 1, steps_k<1>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 2: dots_group<KT, W, 2, steps_k<2>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 3: dots_group<KT, W, 3, steps_k<3>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 4: dots_group<KT, W, 4, steps_k<4>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 5: dots_group<KT, W, 5, steps_k<5>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 6: dots_group<KT, W, 6, steps_k<6>()>(V, w, n, i0, acc, zs, Zj); break;
+    case 7: dots_group<KT, W, 7, steps_k<7>()>(V, w, n, i0, acc, zs, Zj); break;
+    default: dots_group<KT, W, 8, steps_k<8>()>(V, w, n, i0, acc, zs, Zj); break;
+    }
+}
+
+// Pass 1: h_i = <V_i, w>, i <= j, in groups of NG vectors (each group one
+// sweep over w), block partials at partial[i * nb + block]; the first group
+// also stores Z_j = zs when Zb is given.
+template <typename KT, int W>
+__device__ __forceinline__ void cgs_dots_pass(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
+                                              const KT *zs, KT *Zb)
+{
+    for (int i0 = 0; i0 <= j; i0 += NG) {
+        const int cnt = min(NG, j + 1 - i0);
+        double acc[NG];
+        dots_any<KT, W>(cnt, V, w, n, i0, acc, zs, (Zb && i0 == 0) ? Zb + (long long)j * n : nullptr);
+        block_partials<KT>(acc, cnt, partial + (long long)i0 * nb, nb);
+    }
+}
+
+// w <- w - sum_{i<J} h_i V_i (J <= NG), in the order of i, then the products
+// <V_i, w> (acc[0, J)) or, with NORM, |w|^2 (acc[0]) from the values in
+// registers
+template <typename KT, int W, int J, int K, bool NORM>
+__device__ __forceinline__ void update_group(const KT *V, KT *w, long long n, const KT *hs, double *acc)
+{
+    const Sweep S;
+    const long long nc = n / W;
+#pragma unroll
+    for (int i = 0; i < J; i++) acc[i] = 0.0;
+    for (long long base = 0; base < nc; base += K * S.T) {
+        Ch<KT, W> wc[K], vc[J][K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            const bool in = c < nc;
+            wc[k] = ldch_or0<KT, W>(w, c, in);
+#pragma unroll
+            for (int i = 0; i < J; i++) vc[i][k] = ldch_or0<KT, W>(V + (long long)i * n, c, in);
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+#pragma unroll
+            for (int i = 0; i < J; i++) {
+                const KT cf = -hs[i];
+#pragma unroll
+                for (int e = 0; e < W; e++) wc[k].v[e] = fmat(cf, vc[i][k].v[e], wc[k].v[e]);
+            }
+            const long long c = base + k * S.T + S.t;
+            if (c < nc) stch<KT, W>(w, c, wc[k]);
+        }
+        if (NORM) {
+            KT r = (KT)0;
+#pragma unroll
+            for (int k = 0; k < K; k++)
+#pragma unroll
+                for (int e = 0; e < W; e++) r = fmat(wc[k].v[e], wc[k].v[e], r);
+            acc[0] += (double)r;
+        } else {
+#pragma unroll
+            for (int i = 0; i < J; i++) {
+                KT r = (KT)0;
+#pragma unroll
+                for (int k = 0; k < K; k++)
+#pragma unroll
+                    for (int e = 0; e < W; e++) r = fmat(vc[i][k].v[e], wc[k].v[e], r);
+                acc[i] += (double)r;
+            }
+        }
+    }
+}
+
+// The same update for jp1 > NG vectors: per step, the basis in groups of NG
+// (each group's loads issued together), the coefficients still applied in
+// the order of i; with NORM also |w|^2 (acc[0])
+template <typename KT, int W, int K, bool NORM>
+__device__ __forceinline__ void update_long(const KT *V, KT *w, long long n, int jp1, const KT *hs, double *acc)
+{
+    const Sweep S;
+    const long long nc = n / W;
+    acc[0] = 0.0;
+    for (long long base = 0; base < nc; base += K * S.T) {
+        Ch<KT, W> wc[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            wc[k] = ldch_or0<KT, W>(w, c, c < nc);
+        }
+        for (int g0 = 0; g0 < jp1; g0 += NG) {
+            const int cnt = min(NG, jp1 - g0);
+            Ch<KT, W> vc[NG][K];
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const long long c = base + k * S.T + S.t;
+#pragma unroll
+                for (int i = 0; i < NG; i++)
+                    vc[i][k] = ldch_or0<KT, W>(V + (long long)(g0 + i) * n, c, c < nc && i < cnt);
+            }
+#pragma unroll
+            for (int k = 0; k < K; k++)
+#pragma unroll
+                for (int i = 0; i < NG; i++) {
+                    if (i < cnt) {
+                        const KT cf = -hs[g0 + i];
+#pragma unroll
+                        for (int e = 0; e < W; e++) wc[k].v[e] = fmat(cf, vc[i][k].v[e], wc[k].v[e]);
+                    }
+                }
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            if (c < nc) stch<KT, W>(w, c, wc[k]);
+        }
+        if (NORM) {
+            KT r = (KT)0;
+#pragma unroll
+            for (int k = 0; k < K; k++)
+#pragma unroll
+                for (int e = 0; e < W; e++) r = fmat(wc[k].v[e], wc[k].v[e], r);
+            acc[0] += (double)r;
+        }
+    }
+}
+
+template <typename KT, int W, bool NORM>
+__device__ __forceinline__ void update_any(int jp1, const KT *V, KT *w, long long n, const KT *hs, double *acc)
+{
+    switch (jp1) {
+    case 1: update_group<KT, W, 1, steps_k<1>(), NORM>(V, w, n, hs, acc); break;
+    case 2: update_group<KT, W, 2, steps_k<2>(), NORM>(V, w, n, hs, acc); break;
+    case 3: update_group<KT, W, 3, steps_k<3>(), NORM>(V, w, n, hs, acc); break;
+    case 4: update_group<KT, W, 4, steps_k<4>(), NORM>(V, w, n, hs, acc); break;
+    case 5: update_group<KT, W, 5, steps_k<5>(), NORM>(V, w, n, hs, acc); break;
+    case 6: update_group<KT, W, 6, steps_k<6>(), NORM>(V, w, n, hs, acc); break;
+    case 7: update_group<KT, W, 7, steps_k<7>(), NORM>(V, w, n, hs, acc); break;
+    case 8: update_group<KT, W, 8, steps_k<8>(), NORM>(V, w, n, hs, acc); break;
+    default: update_long<KT, W, 2, NORM>(V, w, n, jp1, hs, acc); break;
+    }
+}
+
+// Passes 2 and 3: w <- w - sum_i h_i V_i (coefficients rounded to the
+// Krylov type), then the block partials of h2_i = <V_i, w> or, with NORM, of
+// |w|^2.  Up to NG products ride on the update sweep; beyond that the
+// updated w is swept again in groups.  h: the j + 1 coefficients.
+template <bool NORM, typename KT, int W>
+__device__ __forceinline__ void cgs_update_pass(const KT *V, KT *w, long long n, int j, const double *h,
+                                                double *partial, int nb)
+{
+    __shared__ KT hs[MUSIC_MAXV];
+    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (KT)h[i];
+    __syncthreads();
+    const int jp1 = j + 1;
+    double acc[NG];
+    update_any<KT, W, NORM>(jp1, V, w, n, hs, acc);
+    if (NORM) {
+        block_partials<KT>(acc, 1, partial, nb);
+    } else if (jp1 <= NG) {
+        block_partials<KT>(acc, jp1, partial, nb);
+    } else {
+        for (int i0 = 0; i0 < jp1; i0 += NG) {
+            const int cnt = min(NG, jp1 - i0);
+            dots_any<KT, W>(cnt, V, w, n, i0, acc, nullptr, nullptr);
+            block_partials<KT>(acc, cnt, partial + (long long)i0 * nb, nb);
+        }
+    }
+}
+
+// h_i = <V_i, w>, i <= j (j read from jdev when given); with Zb, also Z_j = zs
+template <typename KT, int W>
+__global__ void __launch_bounds__(BS, 2) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
+                                                double *dst, unsigned int *counter, const int *jdev, const KT *zs,
+                                                KT *Zb)
+{
+    pdl_entry();
+    if (jdev) j = *jdev;
+    const int nb = gridDim.x;
+    cgs_dots_pass<KT, W>(V, w, n, j, partial, nb, zs, Zb);
+    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+}
+
+// w <- w - sum_i h_i V_i, then h2_i = <V_i, w> (second CGS pass) or, with
+// NORM, |w|^2 only; with gc.c the last block then runs the Arnoldi step's
+// Givens control
+template <bool NORM, typename KT, int W>
+__global__ void __launch_bounds__(BS, 2) k_update(const KT *V, KT *w, long long n, int j, const double *h,
+                                                  double *partial, double *dst, unsigned int *counter,
+                                                  const int *jdev, GivensCtl gc)
+{
+    pdl_entry();
+    __shared__ double sh[BS / 32];
+    if (jdev) j = *jdev;
+    const int nb = gridDim.x;
+    cgs_update_pass<NORM, KT, W>(V, w, n, j, h, partial, nb);
+    if (last_block_done(counter)) {
+        if (NORM)
+            finish_sums<BS>(partial, nb, nb, 1, dst, sh);
+        else
+            finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
+        // |w| is in *dst (written by thread 0): the Arnoldi step's control
+        if (NORM && gc.c && threadIdx.x == 0) ctl_givens(gc.c, gc.ds, gc.h, gc.m, gc.cap);
+    }
+}
+
+// ---------------------------------------------------------------- the rest
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_scale_into(const KT *w, KT *dst, long long n, double inv)
 {
@@ -142,21 +468,87 @@ __global__ void __launch_bounds__(BS) k_first(const double *r, KT *dst, long lon
     for (long long e = e0; e < n; e += stride) dst[e] = (KT)r[e] * rinv;
 }
 
+// the W FP64 values of x at the elements of chunk c (W of them, 16-byte
+// aligned pairs when W > 1)
+template <int W>
+__device__ __forceinline__ void ldx(const double *x, long long c, double *out)
+{
+    if constexpr (W == 1) {
+        out[0] = x[c];
+    } else {
+#pragma unroll
+        for (int h = 0; h < W / 2; h++) {
+            const double2 a = reinterpret_cast<const double2 *>(x)[c * (W / 2) + h];
+            out[2 * h] = a.x;
+            out[2 * h + 1] = a.y;
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void stx(double *x, long long c, const double *in)
+{
+    if constexpr (W == 1) {
+        x[c] = in[0];
+    } else {
+#pragma unroll
+        for (int h = 0; h < W / 2; h++) reinterpret_cast<double2 *>(x)[c * (W / 2) + h] = make_double2(in[2 * h], in[2 * h + 1]);
+    }
+}
+
 // x += sum_{i<k} y_i Z_i: the cycle's correction M^-1 V y from the stored
-// preconditioned basis Z_i = M^-1 V_i (V itself when unpreconditioned)
-template <typename KT>
-__global__ void __launch_bounds__(BS) k_correct(const KT *Z, double *x, long long n, int k, Coef y, const int *kdev,
-                                                const double *ydev)
+// preconditioned basis Z_i = M^-1 V_i (V itself when unpreconditioned).
+// Each element's sum runs over i in order in the Krylov type (coefficients
+// rounded to it), then is added to x in FP64; the basis is read in groups of
+// NG vectors whose loads are issued together.
+template <typename KT, int W>
+__global__ void __launch_bounds__(BS) k_correct(const KT *Z, double *x, long long n, int k, Coef y,
+                                                const int *kdev, const double *ydev)
 {
     pdl_entry();
-    __shared__ double ys[MUSIC_MAXV];
+    constexpr int K = 2;
+    __shared__ KT ys[MUSIC_MAXV];
     if (kdev) k = *kdev;
-    for (int i = threadIdx.x; i < k; i += BS) ys[i] = ydev ? ydev[i] : y.c[i];
+    for (int i = threadIdx.x; i < k; i += BS) ys[i] = (KT)(ydev ? ydev[i] : y.c[i]);
     __syncthreads();
-    for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS) {
-        double s = 0.0;
-        for (int i = 0; i < k; i++) s += ys[i] * (double)Z[(long long)i * n + e];
-        x[e] += (double)(KT)s;
+    const Sweep S;
+    const long long nc = n / W;
+    for (long long base = 0; base < nc; base += K * S.T) {
+        KT s[K][W];
+#pragma unroll
+        for (int kk = 0; kk < K; kk++)
+#pragma unroll
+            for (int e = 0; e < W; e++) s[kk][e] = (KT)0;
+        for (int g0 = 0; g0 < k; g0 += NG) {
+            const int cnt = min(NG, k - g0);
+            Ch<KT, W> zc[NG][K];
+#pragma unroll
+            for (int kk = 0; kk < K; kk++) {
+                const long long c = base + kk * S.T + S.t;
+#pragma unroll
+                for (int i = 0; i < NG; i++)
+                    zc[i][kk] = ldch_or0<KT, W>(Z + (long long)(g0 + i) * n, c, c < nc && i < cnt);
+            }
+#pragma unroll
+            for (int kk = 0; kk < K; kk++)
+#pragma unroll
+                for (int i = 0; i < NG; i++)
+                    if (i < cnt) {
+#pragma unroll
+                        for (int e = 0; e < W; e++) s[kk][e] = fmat(ys[g0 + i], zc[i][kk].v[e], s[kk][e]);
+                    }
+        }
+#pragma unroll
+        for (int kk = 0; kk < K; kk++) {
+            const long long c = base + kk * S.T + S.t;
+            if (c < nc) {
+                double xv[W];
+                ldx<W>(x, c, xv);
+#pragma unroll
+                for (int e = 0; e < W; e++) xv[e] += (double)s[kk][e];
+                stx<W>(x, c, xv);
+            }
+        }
     }
 }
 
@@ -185,43 +577,49 @@ __global__ void __launch_bounds__(BS) k_cast(const S *a, D *o, long long n)
 // U += x over all unknowns; partial max of |x_rho| / rho_new over cells.  On
 // mixed grids (F32) the ratio is formed in FP32: it only meets the Newton
 // tolerance, and an FP64 division per cell costs more than the update itself.
-template <bool F32>
-__global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x, long long n, long long N,
+template <bool F32, int W>
+__global__ void __launch_bounds__(BS, 2) k_newton_update(double *U, const double *x, long long n, long long N,
                                                       double *partial, double *dst, double *unorm2,
                                                       unsigned int *counter, const int *skip)
 {
     pdl_entry();
     if (skip && *skip) return;  // a hard error ended the linear solve: U stays as it is
+    constexpr int K = 4;
     __shared__ double sh[BS / 32];
+    const Sweep S;
+    const long long nc = n / W;
     double m = 0.0, q = 0.0;
     float m32 = 0.0f;
-    auto one = [&](long long e, double Ue, double xe) {
-        const double u = Ue + xe;
-        U[e] = u;
-        q = fma(u, u, q);  // |U|^2 of the new iterate, for the next product's eps
-        if (e < N) {
-            if (F32) {
-                const float t = fabsf((float)xe) / (float)u;
-                m32 = (t > m32 || t != t) ? t : m32;  // NaN-propagating, as nanmax
-            } else {
-                m = nanmax(m, fabs(xe) / u);
+    for (long long base = 0; base < nc; base += K * S.T) {
+        Ch<double, W> uc[K], xc[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            const bool in = c < nc;
+            uc[k] = ldch_or0<double, W>(U, c, in);
+            xc[k] = ldch_or0<double, W>(x, c, in);
+        }
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const long long c = base + k * S.T + S.t;
+            if (c >= nc) continue;
+#pragma unroll
+            for (int e = 0; e < W; e++) {
+                const double xe = xc[k].v[e], u = uc[k].v[e] + xe;
+                uc[k].v[e] = u;
+                q = fma(u, u, q);  // |U|^2 of the new iterate, for the next product's eps
+                if (c * W + e < N) {
+                    if (F32) {
+                        const float t = fabsf((float)xe) / (float)u;
+                        m32 = (t > m32 || t != t) ? t : m32;  // NaN-propagating, as nanmax
+                    } else {
+                        m = nanmax(m, fabs(xe) / u);
+                    }
+                }
             }
+            stch<double, W>(U, c, uc[k]);
         }
-    };
-    // four elements' loads in flight per step, processed in element order
-    const long long stride = (long long)gridDim.x * BS;
-    long long e = blockIdx.x * (long long)BS + threadIdx.x;
-    for (; e + 3 * stride < n; e += 4 * stride) {
-        double Ue[4], xe[4];
-#pragma unroll
-        for (int r = 0; r < 4; r++) {
-            Ue[r] = U[e + r * stride];
-            xe[r] = x[e + r * stride];
-        }
-#pragma unroll
-        for (int r = 0; r < 4; r++) one(e + r * stride, Ue[r], xe[r]);
     }
-    for (; e < n; e += stride) one(e, U[e], x[e]);
     if (F32) m = (double)m32;
     const double r = block_max<BS>(m, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -231,304 +629,6 @@ __global__ void __launch_bounds__(BS) k_newton_update(double *U, const double *x
         finish_max<BS>(partial, gridDim.x, dst, sh);
         __syncthreads();
         finish_sums<BS>(partial + gridDim.x, gridDim.x, 0, 1, unorm2, sh);
-    }
-}
-
-
-// ---- mixed precision: FP32 basis, FP32 arithmetic inside a 4-element chunk
-// (float4 loads), FP64 accumulation across chunks and in the reductions.
-
-// Block partials of cnt <= NVM per-thread sums: each warp adds its lanes'
-// values in FP32 (a fixed tree of five levels), then one thread per sum adds
-// the warps' results in FP64 in warp order and writes partial[i * nb + block].
-// FP64 work and barriers stay per block, not per thread and sum: FP64 runs at
-// 1/64 of the FP32 rate on this part, and a thread of these kernels holds only
-// a few chunks on the grids the step is timed on.
-template <int NVM>
-__device__ __forceinline__ void block_partials_mixed(const double *acc, int cnt, double *partial, int nb)
-{
-    __shared__ double ws[NVM][BS / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < NVM; i++) {
-        if (i < cnt) {
-            float v = (float)acc[i];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) ws[i][wid] = (double)v;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += BS) {
-        double t = 0.0;
-        for (int w = 0; w < BS / 32; w++) t += ws[i][w];
-        partial[(long long)i * nb + blockIdx.x] = t;
-    }
-}
-__device__ inline float dot4(const float4 a, const float4 b)
-{
-    float s = a.x * b.x;
-    s = fmaf(a.y, b.y, s);
-    s = fmaf(a.z, b.z, s);
-    return fmaf(a.w, b.w, s);
-}
-
-// acc[i] = <V_{i0+i}, w> over the thread's elements, i < cnt <= NG: FP32
-// runs of RUN float4 chunks, then FP64 (FP64 adds and conversions run at
-// 1/74 of the FP32 rate on this part)
-__device__ __forceinline__ void dots_pass_f32(const float *V, const float *w, long long n, int i0, int cnt,
-                                              double acc[NG])
-{
-    float run[NG];
-#pragma unroll
-    for (int i = 0; i < NG; i++) {
-        acc[i] = 0.0;
-        run[i] = 0.0f;
-    }
-    // float4 path only when every basis vector starts 16-byte aligned
-    const long long n4 = (n & 3) ? 0 : (n >> 2);
-    const long long stride = (long long)gridDim.x * BS;
-    const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    int k = 0;
-    for (long long e = t0; e < n4; e += stride) {
-        const float4 we = reinterpret_cast<const float4 *>(w)[e];
-#pragma unroll
-        for (int i = 0; i < NG; i++)
-            if (i < cnt) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)(i0 + i) * n)[e], we);
-        if (++k == RUN) {
-#pragma unroll
-            for (int i = 0; i < NG; i++) {
-                if (i < cnt) acc[i] += (double)run[i];
-                run[i] = 0.0f;
-            }
-            k = 0;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < NG; i++)
-        if (i < cnt) acc[i] += (double)run[i];
-    for (long long e = 4 * n4 + t0; e < n; e += stride) {
-        const float we = w[e];
-#pragma unroll
-        for (int i = 0; i < NG; i++)
-            if (i < cnt) acc[i] += (double)(V[(long long)(i0 + i) * n + e] * we);
-    }
-}
-
-// ---- the passes of one Arnoldi step's CGS2 (classical Gram-Schmidt with one
-// re-orthogonalisation), as block partials, one kernel each.
-
-// Pass 1: Z_j = zs (with Zb) and the block partials of h_i = <V_i, w>, i <= j,
-// at partial[i * nb + block].
-template <typename KT>
-__device__ __forceinline__ void cgs_dots_pass(const KT *V, const KT *w, long long n, int j, double *partial, int nb,
-                                              const KT *zs, KT *Zb, double *sh)
-{
-    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    if (Zb) {
-        KT *Zj = Zb + (long long)j * n;
-        long long e0 = t0;
-        if constexpr (sizeof(KT) == 4) {
-            const long long n4 = (n & 3) ? 0 : (n >> 2);
-            for (long long e = t0; e < n4; e += stride)
-                reinterpret_cast<float4 *>(Zj)[e] = reinterpret_cast<const float4 *>(zs)[e];
-            e0 = 4 * n4 + t0;
-        }
-        for (long long e = e0; e < n; e += stride) Zj[e] = zs[e];
-    }
-    for (int i0 = 0; i0 <= j; i0 += NG) {
-        const int cnt = min(NG, j + 1 - i0);
-        double acc[NG];
-        if constexpr (sizeof(KT) == 4) {
-            dots_pass_f32(V, w, n, i0, cnt, acc);
-            block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
-            __syncthreads();  // the block's warp sums are reused by the next group
-        } else {
-            dots_pass<KT>(V, w, n, i0, cnt, acc);
-            write_partials(acc, i0, cnt, partial, nb, sh);
-        }
-    }
-}
-
-// Passes 2 and 3: w <- w - sum_i h_i V_i (FP32 coefficients on an FP32
-// basis), then the block partials of h2_i = <V_i, w> or, with NORM, of |w|^2.
-// Up to NG products ride on the update sweep; beyond that the updated w is
-// swept again in groups.  h: the j + 1 coefficients (device or shared memory).
-template <bool NORM, typename KT>
-__device__ __forceinline__ void cgs_update_pass(const KT *V, KT *w, long long n, int j, const double *h,
-                                                double *partial, int nb, double *sh)
-{
-    using CT = KT;  // coefficient type
-    __shared__ CT hs[MUSIC_MAXV];
-    for (int i = threadIdx.x; i <= j; i += BS) hs[i] = (CT)h[i];
-    __syncthreads();
-    const bool fused = NORM || j < NG;
-    double acc[NG];
-    const long long stride = (long long)gridDim.x * BS;
-    const long long t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    if constexpr (sizeof(KT) == 4) {
-        float run[NG];
-#pragma unroll
-        for (int i = 0; i < NG; i++) {
-            acc[i] = 0.0;
-            run[i] = 0.0f;
-        }
-        int k = 0;
-        // float4 path only when every basis vector starts 16-byte aligned
-        const long long n4 = (n & 3) ? 0 : (n >> 2);
-        for (long long e = t0; e < n4; e += stride) {
-            float4 we = reinterpret_cast<const float4 *>(w)[e];
-            for (int i = 0; i <= j; i++) {
-                const float4 v = reinterpret_cast<const float4 *>(V + (long long)i * n)[e];
-                const float c = -hs[i];
-                we.x = fmaf(c, v.x, we.x);
-                we.y = fmaf(c, v.y, we.y);
-                we.z = fmaf(c, v.z, we.z);
-                we.w = fmaf(c, v.w, we.w);
-            }
-            reinterpret_cast<float4 *>(w)[e] = we;
-            if (NORM) {
-                run[0] += dot4(we, we);
-            } else if (fused) {
-#pragma unroll
-                for (int i = 0; i < NG; i++)
-                    if (i <= j) run[i] += dot4(reinterpret_cast<const float4 *>(V + (long long)i * n)[e], we);
-            }
-            if (fused && ++k == RUN) {
-#pragma unroll
-                for (int i = 0; i < NG; i++) {
-                    if (NORM ? i == 0 : i <= j) acc[i] += (double)run[i];
-                    run[i] = 0.0f;
-                }
-                k = 0;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < NG; i++)
-            if (fused && (NORM ? i == 0 : i <= j)) acc[i] += (double)run[i];
-        for (long long e = 4 * n4 + t0; e < n; e += stride) {
-            float we = w[e];
-            for (int i = 0; i <= j; i++) we = fmaf(-hs[i], V[(long long)i * n + e], we);
-            w[e] = we;
-            if (NORM) {
-                acc[0] += (double)(we * we);
-            } else if (fused) {
-#pragma unroll
-                for (int i = 0; i < NG; i++)
-                    if (i <= j) acc[i] += (double)(V[(long long)i * n + e] * we);
-            }
-        }
-        if (NORM) {
-            block_partials_mixed<1>(acc, 1, partial, nb);
-        } else if (fused) {
-            block_partials_mixed<NG>(acc, j + 1, partial, nb);
-        } else {
-            for (int i0 = 0; i0 <= j; i0 += NG) {
-                const int cnt = min(NG, j + 1 - i0);
-                dots_pass_f32(V, w, n, i0, cnt, acc);
-                block_partials_mixed<NG>(acc, cnt, partial + (long long)i0 * nb, nb);
-                __syncthreads();
-            }
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < NG; i++) acc[i] = 0.0;
-        for (long long e = t0; e < n; e += stride) {
-            double we = (double)w[e];
-            for (int i = 0; i <= j; i++) we -= hs[i] * (double)V[(long long)i * n + e];
-            const KT ws = (KT)we;
-            w[e] = ws;
-            const double wr = (double)ws;
-            if (NORM) {
-                acc[0] += wr * wr;
-            } else if (fused) {
-#pragma unroll
-                for (int i = 0; i < NG; i++)
-                    if (i <= j) acc[i] += (double)V[(long long)i * n + e] * wr;
-            }
-        }
-        if (NORM) {
-            write_partials(acc, 0, 1, partial, nb, sh);
-        } else if (fused) {
-            write_partials(acc, 0, j + 1, partial, nb, sh);
-        } else {
-            for (int i0 = 0; i0 <= j; i0 += NG) {
-                const int cnt = min(NG, j + 1 - i0);
-                dots_pass<KT>(V, w, n, i0, cnt, acc);
-                write_partials(acc, i0, cnt, partial, nb, sh);
-            }
-        }
-    }
-}
-
-// h_i = <V_i, w>, i <= j (j read from jdev when given); with Zb, also Z_j = zs
-template <typename KT>
-__global__ void __launch_bounds__(BS, sizeof(KT) == 4 ? 4 : 1) k_dots(const KT *V, const KT *w, long long n, int j, double *partial,
-                                                int nb, double *dst, unsigned int *counter, const int *jdev,
-                                                const KT *zs, KT *Zb)
-{
-    pdl_entry();
-    __shared__ double sh[BS / 32];
-    if (jdev) j = *jdev;
-    cgs_dots_pass<KT>(V, w, n, j, partial, nb, zs, Zb, sh);
-    if (last_block_done(counter)) finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
-}
-
-// w <- w - sum_i h_i V_i, then h2_i = <V_i, w> (second CGS pass) or, with
-// NORM, |w|^2 only; with gc.c the last block then runs the Arnoldi step's
-// Givens control
-template <bool NORM, typename KT>
-__global__ void __launch_bounds__(BS, sizeof(KT) == 4 ? 4 : 1) k_update(const KT *V, KT *w, long long n, int j, const double *h,
-                                                  double *partial, int nb, double *dst, unsigned int *counter,
-                                                  const int *jdev, GivensCtl gc)
-{
-    pdl_entry();
-    __shared__ double sh[BS / 32];
-    if (jdev) j = *jdev;
-    cgs_update_pass<NORM, KT>(V, w, n, j, h, partial, nb, sh);
-    if (last_block_done(counter)) {
-        if (NORM)
-            finish_sums<BS>(partial, nb, nb, 1, dst, sh);
-        else
-            finish_sums_warps<BS>(partial, nb, nb, j + 1, dst);
-        // |w| is in *dst (written by thread 0): the Arnoldi step's control
-        if (NORM && gc.c && threadIdx.x == 0) ctl_givens(gc.c, gc.ds, gc.h, gc.m, gc.cap);
-    }
-}
-
-__global__ void __launch_bounds__(BS) k_correct_f32(const float *Z, double *x, long long n, int k, Coef y,
-                                                    const int *kdev, const double *ydev)
-{
-    pdl_entry();
-    __shared__ float ys[MUSIC_MAXV];
-    if (kdev) k = *kdev;
-    for (int i = threadIdx.x; i < k; i += BS) ys[i] = (float)(ydev ? ydev[i] : y.c[i]);
-    __syncthreads();
-    // four elements a step (float4 loads of the basis) when every vector
-    // starts 16-byte aligned; each element summed as the scalar loop sums it
-    const long long n4 = (n & 3) ? 0 : (n >> 2);
-    const long long stride = (long long)gridDim.x * BS, t0 = blockIdx.x * (long long)BS + threadIdx.x;
-    for (long long e = t0; e < n4; e += stride) {
-        float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int i = 0; i < k; i++) {
-            const float4 z = reinterpret_cast<const float4 *>(Z + (long long)i * n)[e];
-            s.x = fmaf(ys[i], z.x, s.x);
-            s.y = fmaf(ys[i], z.y, s.y);
-            s.z = fmaf(ys[i], z.z, s.z);
-            s.w = fmaf(ys[i], z.w, s.w);
-        }
-        double2 *x2 = reinterpret_cast<double2 *>(x) + 2 * e;
-        double2 a = x2[0], b = x2[1];
-        a.x += (double)s.x;
-        a.y += (double)s.y;
-        b.x += (double)s.z;
-        b.y += (double)s.w;
-        x2[0] = a;
-        x2[1] = b;
-    }
-    for (long long e = 4 * n4 + t0; e < n; e += stride) {
-        float s = 0.0f;
-        for (int i = 0; i < k; i++) s = fmaf(ys[i], Z[(long long)i * n + e], s);
-        x[e] += (double)s;
     }
 }
 
@@ -553,17 +653,61 @@ int grid_blocks(long long n, int cap)
     return (int)b;
 }
 
-int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
+// Is a vector of n elements of T swept in 16-byte chunks?
+template <typename T>
+bool chunked(long long n)
+{
+    return (n * (long long)sizeof(T)) % 16 == 0;
+}
+
+// Blocks of a sweep over nc chunks taking K a step: enough for one step to
+// cover the vector, rounded up to a whole number of blocks per SM beyond
+// one per SM, at most VEC_BLOCKS_MAX (more steps then).  Depends on nc alone.
+int sweep_blocks(long long nc, int K)
+{
+    long long b = (nc + (long long)BS * K - 1) / ((long long)BS * K);
+    if (b > NUM_SMS) b = (b + NUM_SMS - 1) / NUM_SMS * NUM_SMS;
+    if (b > VEC_BLOCKS_MAX) b = VEC_BLOCKS_MAX;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <typename KT>
+int launch_dots_t(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
     const long long n = (long long)g->n;
     unsigned int *cnt = &g->ds->counters[CNT_DOTS];
-    void *Zb = krylov_zstore(g);
-    if (g->mixed)
-        k_dots<float><<<g->nb, BS, 0, s>>>((const float *)g->V, (const float *)g->w, n, j, g->partials, g->nb,
-                                           g->ds->h, cnt, jdev, (const float *)g->z, (float *)Zb);
-    else
-        k_dots<double><<<g->nb, BS, 0, s>>>((const double *)g->V, (const double *)g->w, n, j, g->partials, g->nb,
-                                            g->ds->h, cnt, jdev, (const double *)g->z, (double *)Zb);
+    const KT *V = (const KT *)g->V, *w = (const KT *)g->w, *z = (const KT *)g->z;
+    KT *Zb = (KT *)krylov_zstore(g);
+    if (chunked<KT>(n)) {
+        constexpr int W = 16 / sizeof(KT);
+        k_dots<KT, W><<<sweep_blocks(n / W, 4), BS, 0, s>>>(V, w, n, j, g->partials, g->ds->h, cnt, jdev, z, Zb);
+    } else {
+        k_dots<KT, 1><<<sweep_blocks(n, 4), BS, 0, s>>>(V, w, n, j, g->partials, g->ds->h, cnt, jdev, z, Zb);
+    }
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+int launch_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
+{
+    return g->mixed ? launch_dots_t<float>(g, j, jdev, s) : launch_dots_t<double>(g, j, jdev, s);
+}
+
+template <bool NORM, typename KT>
+int launch_update_t(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s, const GivensCtl &gc)
+{
+    const long long n = (long long)g->n;
+    double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
+    unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
+    const KT *V = (const KT *)g->V;
+    KT *w = (KT *)g->w;
+    if (chunked<KT>(n)) {
+        constexpr int W = 16 / sizeof(KT);
+        k_update<NORM, KT, W><<<sweep_blocks(n / W, 4), BS, 0, s>>>(V, w, n, j, h, g->partials, dst, cnt, jdev, gc);
+    } else {
+        k_update<NORM, KT, 1><<<sweep_blocks(n, 4), BS, 0, s>>>(V, w, n, j, h, g->partials, dst, cnt, jdev, gc);
+    }
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -572,15 +716,20 @@ template <bool NORM>
 int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaStream_t s, const GivensCtl *gcp)
 {
     const GivensCtl gc = gcp ? *gcp : GivensCtl{};
-    const long long n = (long long)g->n;
-    double *dst = NORM ? &g->ds->wnorm2 : g->ds->h2;
-    unsigned int *cnt = &g->ds->counters[NORM ? CNT_NORMW : CNT_UPDATE];
-    if (g->mixed)
-        k_update<NORM, float><<<g->nb, BS, 0, s>>>((const float *)g->V, (float *)g->w, n, j, h, g->partials, g->nb,
-                                                   dst, cnt, jdev, gc);
-    else
-        k_update<NORM, double><<<g->nb, BS, 0, s>>>((const double *)g->V, (double *)g->w, n, j, h, g->partials,
-                                                    g->nb, dst, cnt, jdev, gc);
+    return g->mixed ? launch_update_t<NORM, float>(g, j, jdev, h, s, gc)
+                    : launch_update_t<NORM, double>(g, j, jdev, h, s, gc);
+}
+
+template <typename T>
+int launch_sumsq(music_grid *g, const T *x, long long n, double *dst, cudaStream_t s)
+{
+    unsigned int *cnt = &g->ds->counters[CNT_SUMSQ];
+    if (chunked<T>(n)) {
+        constexpr int W = 16 / sizeof(T);
+        k_sumsq<T, W><<<sweep_blocks(n / W, 4), BS, 0, s>>>(x, n, g->partials, dst, cnt);
+    } else {
+        k_sumsq<T, 1><<<sweep_blocks(n, 4), BS, 0, s>>>(x, n, g->partials, dst, cnt);
+    }
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -590,13 +739,8 @@ int launch_update(music_grid *g, int j, const int *jdev, const double *h, cudaSt
 int dev_norm2(music_grid *g, const void *x, int is_double, size_t n, double *dst, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    unsigned int *cnt = &g->ds->counters[CNT_SUMSQ];
-    if (is_double)
-        k_sumsq<double><<<g->nb, BS, 0, s>>>((const double *)x, (long long)n, g->partials, dst, cnt);
-    else
-        k_sumsq<float><<<g->nb, BS, 0, s>>>((const float *)x, (long long)n, g->partials, dst, cnt);
-    CHECK_LAUNCH();
-    return MUSIC_OK;
+    return is_double ? launch_sumsq<double>(g, (const double *)x, (long long)n, dst, s)
+                     : launch_sumsq<float>(g, (const float *)x, (long long)n, dst, s);
 }
 
 int final_sum(music_grid *g, int count, double *dst, cudaStream_t s)
@@ -622,7 +766,7 @@ int krylov_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 }
 
 template <bool NORM>
-int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc)
+int update_pass(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
     return launch_update<NORM>(g, j, jdev, NORM ? g->ds->h2 : g->ds->h, s, gc);
@@ -630,12 +774,12 @@ int update_any(music_grid *g, int j, const int *jdev, cudaStream_t s, const Give
 
 int krylov_update_dots(music_grid *g, int j, const int *jdev, cudaStream_t s)
 {
-    return update_any<false>(g, j, jdev, s, nullptr);
+    return update_pass<false>(g, j, jdev, s, nullptr);
 }
 
 int krylov_update_norm(music_grid *g, int j, const int *jdev, cudaStream_t s, const GivensCtl *gc)
 {
-    return update_any<true>(g, j, jdev, s, gc);
+    return update_pass<true>(g, j, jdev, s, gc);
 }
 
 int krylov_scale(music_grid *g, int j, double inv, cudaStream_t s)
@@ -673,12 +817,22 @@ int krylov_correct(music_grid *g, int k, const double *y, const int *kdev, const
     Coef c;
     for (int i = 0; i < MUSIC_MAXV; i++) c.c[i] = (y && i < k) ? y[i] : 0.0;
     const long long n = (long long)g->n;
-    const int nb = grid_blocks(n, 152 * 16);
     const void *Z = krylov_zstore(g) ? krylov_zstore(g) : g->V;
-    if (g->mixed)
-        k_correct_f32<<<nb, BS, 0, s>>>((const float *)Z, g->x, n, k, c, kdev, ydev);
-    else
-        k_correct<double><<<nb, BS, 0, s>>>((const double *)Z, g->x, n, k, c, kdev, ydev);
+    if (g->mixed) {
+        if (chunked<float>(n))
+            k_correct<float, 4><<<grid_blocks((n / 4 + 1) / 2, 152 * 16), BS, 0, s>>>((const float *)Z, g->x, n, k, c,
+                                                                                    kdev, ydev);
+        else
+            k_correct<float, 1><<<grid_blocks((n + 1) / 2, 152 * 16), BS, 0, s>>>((const float *)Z, g->x, n, k, c, kdev,
+                                                                                ydev);
+    } else {
+        if (chunked<double>(n))
+            k_correct<double, 2><<<grid_blocks((n / 2 + 1) / 2, 152 * 16), BS, 0, s>>>((const double *)Z, g->x, n, k,
+                                                                                     c, kdev, ydev);
+        else
+            k_correct<double, 1><<<grid_blocks((n + 1) / 2, 152 * 16), BS, 0, s>>>((const double *)Z, g->x, n, k, c,
+                                                                                 kdev, ydev);
+    }
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
@@ -716,17 +870,24 @@ int vec_cast_copy(const void *src, int src_double, void *dst, int dst_double, si
     return MUSIC_OK;
 }
 
+template <bool F32>
+int newton_update_t(music_grid *g, const int *skip, cudaStream_t s)
+{
+    const long long n = (long long)g->n;
+    double *const dst = &g->ds->maxdrho, *const un = &g->ds->unorm2;
+    unsigned int *cnt = &g->ds->counters[CNT_NEWTON];
+    if (chunked<double>(n))
+        k_newton_update<F32, 2><<<sweep_blocks(n / 2, 4), BS, 0, s>>>(g->U, g->x, n, g->P.N, g->partials, dst, un,
+                                                                      cnt, skip);
+    else
+        k_newton_update<F32, 1><<<sweep_blocks(n, 4), BS, 0, s>>>(g->U, g->x, n, g->P.N, g->partials, dst, un, cnt,
+                                                                  skip);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
 int newton_update(music_grid *g, const int *skip, cudaStream_t s)
 {
     ProfScope prof_(g, MUSIC_PROF_VECTOR, s);
-    if (g->mixed)
-        k_newton_update<true><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
-                                                    &g->ds->maxdrho, &g->ds->unorm2, &g->ds->counters[CNT_NEWTON],
-                                                    skip);
-    else
-        k_newton_update<false><<<g->nb, BS, 0, s>>>(g->U, g->x, (long long)g->n, g->P.N, g->partials,
-                                                     &g->ds->maxdrho, &g->ds->unorm2, &g->ds->counters[CNT_NEWTON],
-                                                     skip);
-    CHECK_LAUNCH();
-    return MUSIC_OK;
+    return g->mixed ? newton_update_t<true>(g, skip, s) : newton_update_t<false>(g, skip, s);
 }
