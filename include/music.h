@@ -238,8 +238,9 @@ int music_newton_step(music_grid *grid, double dt_max, music_step_stats *st, voi
  * failure) runs in one CTA on the device with no host synchronisation, using
  * the grid's own buffers.  Meant for many small grids, which cannot fill the
  * GPU one at a time.  Every grid must be 2-D Cartesian without radiative
- * diffusion, use at most 16 preconditioner sweeps, and all must share one
- * precision.  stats[i] (may be NULL) receives grid i's outcome.  Synchronises
+ * diffusion, use at most 24 preconditioner sweeps in mixed precision (16 in
+ * FP64, whose planes of a deeper halo exceed shared memory), and all must
+ * share one precision.  stats[i] (may be NULL) receives grid i's outcome.  Synchronises
  * `stream`.  Returns MUSIC_OK, or the first failing grid's status (its state
  * is restored to the start of the step); MUSIC_E_INVAL for a bad batch.
  */
@@ -249,7 +250,7 @@ int music_batch_step(music_grid **grids, int count, const double *cfl, const dou
 /*
  * Tile shapes of the fused 2-D kernels (the residual / Jacobian-free product
  * stencil of Sec. 2 and the physics-based preconditioner) and the halo depth
- * of the preconditioner (its K sweeps in 1, 2 or 4 launches, halo K/stages +
+ * of the preconditioner (its K sweeps in 1, 2, 3 or 4 launches, halo K/stages +
  * 1), picked by timing.  The paper has no counterpart: its code ran on CPUs.
  * Every candidate gives bitwise identical results, so tuning changes speed
  * only.

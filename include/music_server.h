@@ -31,8 +31,8 @@ typedef struct {
     int max_active;           /* per-stream workers = concurrently resident solves off the batch
                                  lane [16], <= 256 */
     int batch_max_cells;      /* > 0: solves of at most this many cells (2-D Cartesian, no radiative
-                                 diffusion, <= 16 preconditioner sweeps) join the batch lane;
-                                 <= 0: no batch lane [0] */
+                                 diffusion, <= 24 preconditioner sweeps in mixed precision, <= 16
+                                 in FP64) join the batch lane; <= 0: no batch lane [0] */
     int batch_size;           /* solves per batched launch [152], <= 512 */
     int autotune;             /* 1: a worker tunes the tile shapes of each new grid configuration
                                  (music_autotune) before its first step; later solves of that

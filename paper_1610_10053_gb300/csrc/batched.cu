@@ -11,11 +11,9 @@ int launch_batched(music_grid **grids, int count, const double *cfl, const doubl
 }
 
 #define MUSIC_BATCHED_DECLARE(TX, TY)                                                                                    \
-    extern template int batch::launch_batched<float, 8, TX, TY>(music_grid **, int, const double *, const double *,    \
-                                                                cudaStream_t);                                        \
     extern template int batch::launch_batched<float, 16, TX, TY>(music_grid **, int, const double *, const double *,   \
                                                                  cudaStream_t);                                       \
-    extern template int batch::launch_batched<double, 8, TX, TY>(music_grid **, int, const double *, const double *,   \
+    extern template int batch::launch_batched<float, 24, TX, TY>(music_grid **, int, const double *, const double *,   \
                                                                  cudaStream_t);                                       \
     extern template int batch::launch_batched<double, 16, TX, TY>(music_grid **, int, const double *, const double *,  \
                                                                   cudaStream_t);
@@ -29,18 +27,20 @@ template <int TX, int TY>
 int launch_shape(music_grid **grids, int count, const double *cfl, const double *dt_max, bool mixed, int km,
                  cudaStream_t s)
 {
-    if (km <= 8)
-        return mixed ? batch::launch_batched<float, 8, TX, TY>(grids, count, cfl, dt_max, s)
-                     : batch::launch_batched<double, 8, TX, TY>(grids, count, cfl, dt_max, s);
-    return mixed ? batch::launch_batched<float, 16, TX, TY>(grids, count, cfl, dt_max, s)
-                 : batch::launch_batched<double, 16, TX, TY>(grids, count, cfl, dt_max, s);
+    if (km <= 16)
+        return mixed ? batch::launch_batched<float, 16, TX, TY>(grids, count, cfl, dt_max, s)
+                     : batch::launch_batched<double, 16, TX, TY>(grids, count, cfl, dt_max, s);
+    // deeper halos in FP32 only (FP64 planes of that halo exceed shared memory; batchable)
+    return batch::launch_batched<float, 24, TX, TY>(grids, count, cfl, dt_max, s);
 }
 
 }  // namespace
 
 bool batchable(const music_grid *g)
 {
-    return g && g->P.nd == 2 && !general_grid(g->P) && g->desc.precond_sweeps <= tile::PC_FUSED_MAXK && g->ns == 0;
+    if (!g) return false;
+    const int kmax = g->mixed ? tile::PC_BATCH_MAXK_F32 : tile::PC_FUSED_MAXK;
+    return g->P.nd == 2 && !general_grid(g->P) && g->desc.precond_sweeps <= kmax && g->ns == 0;
 }
 
 int batch_launch(music_grid **grids, int count, const double *cfl, const double *dt_max, int tile, cudaStream_t s)

@@ -1,0 +1,7 @@
+// The persistent batched kernel with 16 x 32 tiles, FP32 Krylov type (one translation unit
+// per shape and precision, so the library builds in parallel).
+#include "batched_impl.cuh"
+
+namespace batch {
+MUSIC_BATCHED_INSTANTIATE_F32(16, 32)
+}

@@ -1,0 +1,7 @@
+// The persistent batched kernel with 64 x 8 tiles, FP64 (one translation unit
+// per shape and precision, so the library builds in parallel).
+#include "batched_impl.cuh"
+
+namespace batch {
+MUSIC_BATCHED_INSTANTIATE_F64(64, 8)
+}

@@ -501,11 +501,13 @@ int launch_batched(music_grid **grids, int count, const double *cfl, const doubl
     return MUSIC_OK;
 }
 
-// the four instantiations (precision x halo depth) of one tile shape
-#define MUSIC_BATCHED_INSTANTIATE(TX, TY)                                                                         \
-    template int launch_batched<float, 8, TX, TY>(music_grid **, int, const double *, const double *, cudaStream_t);  \
+// the instantiations of one tile shape: FP32 with the halos of 16 and 24
+// sweeps, FP64 with that of 16 (one translation unit each, so the library
+// builds in parallel)
+#define MUSIC_BATCHED_INSTANTIATE_F32(TX, TY)                                                                     \
     template int launch_batched<float, 16, TX, TY>(music_grid **, int, const double *, const double *, cudaStream_t); \
-    template int launch_batched<double, 8, TX, TY>(music_grid **, int, const double *, const double *, cudaStream_t); \
+    template int launch_batched<float, 24, TX, TY>(music_grid **, int, const double *, const double *, cudaStream_t);
+#define MUSIC_BATCHED_INSTANTIATE_F64(TX, TY)                                                                     \
     template int launch_batched<double, 16, TX, TY>(music_grid **, int, const double *, const double *, cudaStream_t);
 
 }  // namespace batch

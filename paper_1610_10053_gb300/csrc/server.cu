@@ -91,7 +91,7 @@ bool lane_eligible(const music_server *S, const Job *j)
     const long long cells = (long long)d.n[0] * d.n[1] * (d.ndim == 3 ? d.n[2] : 1);
     return S->lane && d.ndim == 2 && d.geometry == MUSIC_GEOM_CARTESIAN && !d.conduct && d.nscalars == 0 &&
            !(j->cfl_adv > 0.0) && !(j->cfl_rad > 0.0) &&
-           d.precond_sweeps <= 16 && cells <= S->lane_cells;
+           d.precond_sweeps <= (d.precision == MUSIC_MIXED ? 24 : 16) && cells <= S->lane_cells;
 }
 
 // Take the first pending job that fits (the lane takes only its own kind,

@@ -10,6 +10,7 @@ constexpr int PTX = 32, PTY = 16;  // tile of the persistent batched kernel
 constexpr int PC_FUSED_MAXK = 16;  // sweeps of a one-launch application
 constexpr int PC_STAGE_MAXK = 8;   // sweeps of one stage of a split application
 constexpr int PC_STAGED_MAXK = 32; // sweeps of a split application (4 stages)
+constexpr int PC_BATCH_MAXK_F32 = 24;  // sweeps of the batched kernel's FP32 tiles (FP64: PC_FUSED_MAXK)
 constexpr int NRX = 16, NRY = 8;  // blocks of cells of the tile-independent |z|^2 reduction
 
 template <typename PT>

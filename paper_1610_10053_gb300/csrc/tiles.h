@@ -19,15 +19,15 @@ constexpr int STENCIL_TILE_DEFAULT = 3, PRECOND_TILE_DEFAULT = 3;  // 32 x 16 bo
 // the preconditioner's K sweeps run in 1, 2 or 4 launches (halo depth K + 1,
 // K/2 + 1 or K/4 + 1): one launch takes up to 16 sweeps, a split up to 8 per
 // stage (so 17..32 sweeps need 4 stages)
-constexpr int N_PRECOND_SPLITS = 3;
-constexpr int PRECOND_SPLITS[N_PRECOND_SPLITS] = {1, 2, 4};
+constexpr int N_PRECOND_SPLITS = 4;
+constexpr int PRECOND_SPLITS[N_PRECOND_SPLITS] = {1, 2, 3, 4};
 inline bool split_ok(int sweeps, int stages)
 {
     if (stages == 1) return sweeps <= 16;
     return sweeps >= stages && (sweeps + stages - 1) / stages <= 8;
 }
-// the split a grid starts with: one launch when the sweeps allow it
-inline int default_split(int sweeps) { return sweeps <= 16 ? 1 : 4; }
+// the split a grid starts with: the fewest launches the sweeps allow
+inline int default_split(int sweeps) { return sweeps <= 16 ? 1 : sweeps <= 24 ? 3 : 4; }
 // Shared memory of the widest stage of a fused preconditioner application
 // (6 planes of the tile and its halo of KM + 1 cells, KM the stage's sweep
 // bound, plus the |z|^2 buffer of TX*TY doubles) against the 227 KB a CTA

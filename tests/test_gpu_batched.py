@@ -12,9 +12,12 @@ torch = pytest.importorskip("torch")
 from test_gpu_parity import B, diag_close  # noqa: E402
 
 
-def problems():
-    return [I.rayleigh_taylor(nx=32, ny=96, nsteps=3), I.kelvin_helmholtz(n=64, seed=3, nsteps=3),
-            I.kelvin_helmholtz(n=40, ny=72, seed=4, nsteps=3), I.rayleigh_taylor(nx=20, ny=60, nsteps=3)]
+def problems(fp64=False):
+    """Small RT and KH setups; in FP64 the KH ones at 16 sweeps (the batched
+    kernel's FP64 limit; mixed takes their default 24)."""
+    kh = (lambda p: p.with_options(sweeps=16)) if fp64 else (lambda p: p)
+    return [I.rayleigh_taylor(nx=32, ny=96, nsteps=3), kh(I.kelvin_helmholtz(n=64, seed=3, nsteps=3)),
+            kh(I.kelvin_helmholtz(n=40, ny=72, seed=4, nsteps=3)), I.rayleigh_taylor(nx=20, ny=60, nsteps=3)]
 
 
 def run_batched(probs, prec, nsteps):
@@ -33,7 +36,7 @@ def run_batched(probs, prec, nsteps):
 
 
 def test_batched_fp64_matches_oracle():
-    probs = problems()
+    probs = problems(fp64=True)
     out, stats = run_batched(probs, B().FP64, 3)
     for k, p in enumerate(probs):
         Uref, sref = O.run(p)
@@ -82,13 +85,24 @@ def test_batch_rejects_unsupported_grids():
     with B().Grid(pc) as gc:
         with pytest.raises(B().MusicError):
             B().batch_step([gc], cfl=[1.0])
+    # more sweeps than the kernel's halo takes: 16 in FP64, 24 in mixed precision
+    kh = I.kelvin_helmholtz(n=32, seed=1)
+    with B().Grid(kh.with_options(sweeps=24), precision=B().FP64) as g64, \
+            B().Grid(kh.with_options(sweeps=32), precision=B().MIXED) as g32:
+        for g in (g64, g32):
+            with pytest.raises(B().MusicError):
+                B().batch_step([g])
+    with B().Grid(kh.with_options(sweeps=24), precision=B().MIXED) as g24:
+        g24.set_state(kh.U)
+        code, _ = B().batch_step([g24])
+        assert code == 0, B().last_error()
 
 
 @pytest.mark.parametrize("prec", ["FP64", "MIXED"])
 def test_batched_tile_shapes_give_the_same_bits(prec):
     """Every tile shape of the persistent batched kernel (a CTA of 512 threads
     whatever the shape) gives bitwise the same step."""
-    probs = problems()
+    probs = problems(fp64=(prec == "FP64"))
     out = {}
     for tile in ((32, 16), (16, 32), (64, 8)):
         grids = [B().Grid(p, precision=getattr(B(), prec)) for p in probs]

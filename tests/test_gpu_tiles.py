@@ -23,7 +23,13 @@ torch = pytest.importorskip("torch")
 
 STENCIL = [(16, 8), (16, 16), (32, 8), (32, 16), (32, 32)]
 PRECOND = [(16, 8), (16, 16), (32, 8), (32, 16), (64, 16), (32, 32)]
-STAGES = [1, 2, 4]
+STAGES = [1, 2, 3, 4]
+
+
+def split_ok(sweeps, q):
+    """One launch takes at most 16 sweeps; a split at most 8 a stage, and at
+    least one."""
+    return sweeps <= 16 if q == 1 else (sweeps >= q and -(-sweeps // q) <= 8)
 
 
 def fits(pt, q, prec, sweeps=16):
@@ -35,6 +41,15 @@ def fits(pt, q, prec, sweeps=16):
     h = km + 1
     es = 4 if prec == "MIXED" else 8
     return 6 * (pt[0] + 2 * h) * (pt[1] + 2 * h) * es + pt[0] * pt[1] * 8 + 256 <= 227 * 1024
+
+
+def valid(pt, q, prec, sweeps):
+    """A preconditioner tile and split the library accepts for the grid."""
+    return split_ok(sweeps, q) and fits(pt, q, prec, sweeps)
+
+
+def default_split(sweeps):
+    return 1 if sweeps <= 16 else 3 if sweeps <= 24 else 4
 
 
 def B():
@@ -74,7 +89,7 @@ def test_operators_identical_for_every_tile(name, prec):
     ref = None
     for pt, q in itertools.product(PRECOND, STAGES):
         with B().Grid(p, precision=getattr(B(), prec)) as g:
-            if not fits(pt, q, prec):
+            if not valid(pt, q, prec, p.sweeps):
                 with pytest.raises(B().MusicError):
                     g.set_tiles(precond=pt, stages=q)
                 continue
@@ -94,8 +109,11 @@ def test_steps_identical_for_every_tile_pair(name, prec):
     also checks that the fused reduction does not depend on the tile."""
     p = problems()[name]
     ref = None
-    for st, pt, q in [(s, t, 1 if fits(t, 1, prec) else 2) for s, t in itertools.product(STENCIL, PRECOND)] + [
-            ((16, 8), (16, 8), 2), ((32, 16), (32, 8), 4), ((16, 16), (32, 16), 2)]:
+    first = {t: min(q for q in STAGES if valid(t, q, prec, p.sweeps)) for t in PRECOND}
+    extra = [c for c in (((16, 8), (16, 8), 2), ((32, 16), (32, 8), 4), ((16, 16), (32, 16), 2),
+                         ((32, 8), (16, 16), 3), ((32, 32), (32, 16), 4)) if valid(c[1], c[2], prec, p.sweeps)]
+    assert len({q for _, _, q in extra} | set(first.values())) >= 2  # at least two splits compared
+    for st, pt, q in [(s, t, first[t]) for s, t in itertools.product(STENCIL, PRECOND)] + extra:
         with B().Grid(p, precision=getattr(B(), prec)) as g:
             g.set_tiles(stencil=st, precond=pt, stages=q)
             g.set_state(p.U)
@@ -117,7 +135,7 @@ def test_autotune_picks_a_candidate_and_caches_it():
         assert rep["tunable"] == 1 and rep["from_cache"] == 0
         assert set(rep["stencil_us"]) == set(STENCIL)
         assert set(rep["precond_us"]) == {pt + (q,) for pt, q in itertools.product(PRECOND, STAGES)
-                                          if fits(pt, q, "MIXED")}
+                                          if valid(pt, q, "MIXED", p.sweeps)}
         assert all(t > 0.0 for t in rep["stencil_us"].values())
         assert all(t > 0.0 for t in rep["precond_us"].values())
         assert rep["stencil_tile"] == min(rep["stencil_us"], key=rep["stencil_us"].get)
@@ -136,13 +154,13 @@ def test_autotune_picks_a_candidate_and_caches_it():
         assert rep2["from_cache"] == 1 and rep2["stencil_tile"] == rep["stencil_tile"]
     # another precision is another configuration
     with B().Grid(p, precision=B().FP64) as g3:
-        assert g3.tiles() == ((32, 16), (32, 16), 1)
+        assert g3.tiles() == ((32, 16), (32, 16), default_split(p.sweeps))
 
 
 def test_autotune_pinned_by_the_environment(monkeypatch):
     """MUSIC_TILES pins the tuner's choice (no timing); an invalid value is
     ignored and the candidates are timed."""
-    p = I.kelvin_helmholtz(n=64, ny=48, seed=13, nsteps=1)
+    p = I.kelvin_helmholtz(n=64, ny=48, seed=13, nsteps=1).with_options(sweeps=16)  # one launch allowed
     monkeypatch.setenv("MUSIC_TILES", "16x8,32x16,32x8,1")
     with B().Grid(p, precision=B().MIXED) as g:
         g.set_state(p.U)
@@ -174,7 +192,7 @@ def test_set_tiles_rejects_other_shapes():
         with pytest.raises(B().MusicError):
             g.set_tiles(precond=(64, 32))
         with pytest.raises(B().MusicError):
-            g.set_tiles(stages=3)
+            g.set_tiles(stages=5)
 
 
 def test_stage_split_must_fit_the_staged_halo():
