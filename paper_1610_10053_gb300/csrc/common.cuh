@@ -131,6 +131,8 @@ struct SolveCtl {
     int stop;         // 1: leave every loop (hard error)
     int ok;           // 1: Newton converged
     int guard;        // loop bodies run, against a hard cap
+    int go;           // 1: the current cycle builds an Arnoldi basis (its kernels run)
+    int nocycle;      // 1: the GMRES solve needs no cycle at all (|b| zero or not finite)
     double cs[MUSIC_MAXV], sn[MUSIC_MAXV], gv[MUSIC_MAXV + 1], y[MUSIC_MAXV];
     double H[MUSIC_MAXV * MUSIC_MAXV]; // H[i * MUSIC_MAXV + j]
 };

@@ -1,11 +1,14 @@
 // One Newton attempt of the implicit step (Sec. 2: Newton-Raphson on the
 // Crank-Nicolson system, restarted right-preconditioned GMRES with
 // Jacobian-free products) recorded once per grid as a CUDA graph and replayed
-// for every attempt.  The Newton, restart and Arnoldi loops are conditional
-// WHILE nodes and the restart residual and the correction are IF nodes; tiny
-// single-thread control kernels run the Givens rotations and the stopping
-// tests and set the loop conditions, so an attempt needs no host round trip
-// until it ends.  The vector kernels are the same as those of the
+// for every attempt.  The Newton loop, the Arnoldi loop of each GMRES cycle
+// and the loop over restarted cycles are conditional WHILE nodes, the next
+// iteration's residual an IF node; tiny single-thread control kernels run the
+// Givens rotations and the stopping tests and set the loop conditions, so an
+// attempt needs no host round trip until it ends.  The first cycle of a solve
+// sits in the Newton body itself (a solve rarely restarts, and every
+// conditional node a body enters costs several microseconds); a cycle that
+// builds no basis leaves its kernels to return at once on a device flag.  The vector kernels are the same as those of the
 // host-sequenced attempt in solver.cu, and so is every floating-point
 // operation (the control kernels use explicitly rounded, uncontracted
 // arithmetic to match the host), so both drivers give identical results.
@@ -51,8 +54,10 @@ __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, 
     cudaGraphSetConditional(h_newton, newton_max > 0 ? 1u : 0u);
 }
 
-// GMRES set-up after |b|^2 -> ds->rnorm2 (b = -F(U), x = 0)
-__global__ void k_ctl_gmres(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_cycle, double rtol)
+// GMRES set-up after |b|^2 -> ds->rnorm2 (b = -F(U), x = 0), and the start
+// of its first cycle (beta = |b|): the condition of that cycle's Arnoldi loop
+__global__ void k_ctl_gmres(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_arnoldi, double rtol,
+                            int m)
 {
     pdl_entry();
     const double bnorm = sqrt(ds->rnorm2);
@@ -60,55 +65,65 @@ __global__ void k_ctl_gmres(SolveCtl *c, const DevScalars *ds, cudaGraphConditio
     c->its = 0;
     c->converged = 0;
     c->cycle = 0;
+    c->j = 0;
     c->k = 0;
     c->scale = 0;
     c->resid = bnorm;
     c->target = __dmul_rn(rtol, bnorm);
-    unsigned go = 1u;
+    c->go = 0;
+    c->nocycle = 0;
     if (!isfinite(bnorm)) {
         c->status = MUSIC_E_NONFINITE;
         c->stop = 1;
-        go = 0u;
+        c->nocycle = 1;
     } else if (bnorm == 0.0) {
         c->converged = 1;
-        go = 0u;
+        c->nocycle = 1;
+    } else {
+        c->cycles++;
+        c->beta = bnorm;
+        if (!(bnorm <= c->target)) {
+            c->go = 1;
+            for (int i = 0; i <= m; i++) c->gv[i] = 0.0;
+            c->gv[0] = bnorm;
+            c->solves++;
+        }
     }
-    cudaGraphSetConditional(h_cycle, go);
+    cudaGraphSetConditional(h_arnoldi, c->go ? 1u : 0u);
 }
 
 // a cycle after the first starts from the true residual b - J x
-__global__ void k_ctl_cycle_pre(SolveCtl *c, cudaGraphConditionalHandle h_restart)
+__global__ void k_ctl_cycle_pre(SolveCtl *c)
 {
     pdl_entry();
     c->cycles++;
-    const unsigned r = c->cycle > 0 ? 1u : 0u;
-    c->restarts += (int)r;
-    cudaGraphSetConditional(h_restart, r);
+    c->restarts++;
 }
 
-// beta = |b| (first cycle) or |b - J x| (ds->rnorm2); build the cycle or stop
-__global__ void k_ctl_cycle_start(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_go, int m)
+// beta = |b - J x| (ds->rnorm2) of a restarted cycle; build its basis (the
+// condition of its Arnoldi loop) or stop
+__global__ void k_ctl_cycle_start(SolveCtl *c, const DevScalars *ds, cudaGraphConditionalHandle h_arnoldi, int m)
 {
     pdl_entry();
-    const double beta = c->cycle == 0 ? c->bnorm : sqrt(ds->rnorm2);
+    const double beta = sqrt(ds->rnorm2);
     c->beta = beta;
     c->j = 0;
     c->k = 0;
     c->scale = 0;
-    unsigned go = 0u;
+    c->go = 0;
     if (!isfinite(beta)) {
         c->status = MUSIC_E_NONFINITE;
         c->stop = 1;
     } else {
         c->resid = beta;
         if (!(beta <= c->target)) {
-            go = 1u;
+            c->go = 1;
             for (int i = 0; i <= m; i++) c->gv[i] = 0.0;
             c->gv[0] = beta;
             c->solves++;
         }
     }
-    cudaGraphSetConditional(h_go, go);
+    cudaGraphSetConditional(h_arnoldi, c->go ? 1u : 0u);
 }
 
 // y from the k x k upper triangle: H y = g
@@ -128,7 +143,7 @@ __global__ void k_ctl_cycle_end(SolveCtl *c, cudaGraphConditionalHandle h_cycle,
 {
     pdl_entry();
     unsigned go = 0u;
-    if (!c->stop && !over_cap(c, cap)) {
+    if (!c->nocycle && !c->stop && !over_cap(c, cap)) {
         if (c->resid <= c->target) {
             c->converged = 1;
         } else {
@@ -171,10 +186,10 @@ __global__ void k_ctl_newton(SolveCtl *c, const DevScalars *ds, cudaGraphConditi
 // the preconditioner applies and stores.
 template <typename KT>
 __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double *t64, KT *V, KT *q, long long n,
-                                                  SolveCtl *c, cudaGraphConditionalHandle h_arnoldi, KT *w,
-                                                  int fold)
+                                                  SolveCtl *c, KT *w, int fold)
 {
     pdl_entry();
+    if (!c->go) return;  // the cycle builds no basis
     const double *r = c->cycle == 0 ? b : t64;
     if (fold) {
         for (long long e = blockIdx.x * (long long)BS + threadIdx.x; e < n; e += (long long)gridDim.x * BS)
@@ -182,7 +197,6 @@ __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double 
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->inv = 1.0 / c->beta;
             c->scale_idx = 0;
-            cudaGraphSetConditional(h_arnoldi, 1u);
         }
         return;
     }
@@ -209,7 +223,6 @@ __global__ void __launch_bounds__(BS) k_first_dev(const double *b, const double 
         V[e] = v;
         q[e] = v;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_arnoldi, 1u);
 }
 
 // V_{j+1} = w / h_{j+1,j} (and q) when the Arnoldi step asked for it
@@ -378,22 +391,82 @@ int join(cudaStream_t s, cudaStream_t a, cudaEvent_t ej)
     return MUSIC_OK;
 }
 
+// One GMRES cycle on stream s (capturing body level `lvl`): the first basis
+// vector, the Arnoldi loop (WHILE on hA, set by the cycle's start), the
+// small solve and the correction x += M^-1 V y.  The Arnoldi body's kernels
+// per step go to g->glaunch[5].
+int record_cycle(music_grid *g, Capture &C, cudaStream_t s, int lvl, cudaGraphConditionalHandle hA, SolveCtl *ctl,
+                 int nb, int fold, int cap, int m)
+{
+    const long long n = (long long)g->n;
+    const int kd = !g->mixed;
+    const double dt = 1.0;  // every recorded kernel reads dt from g->ctl->dt instead
+    DevScalars *ds = g->ds;
+    cudaStream_t sa = C.st[lvl + 1];
+    if (g->mixed)
+        k_first_dev<float><<<nb, BS, 0, s>>>(g->b, g->t64, (float *)g->V, (float *)g->q, n, ctl, (float *)g->w, fold);
+    else
+        k_first_dev<double><<<nb, BS, 0, s>>>(g->b, g->t64, (double *)g->V, (double *)g->q, n, ctl, (double *)g->w,
+                                              fold);
+    CHECK_LAUNCH();
+    cudaGraph_t bA;
+    TRY(add_conditional(s, hA, cudaGraphCondTypeWhile, &bA));
+    C.bodies.push_back(bA);
+    {
+        TRY(C.begin_body(lvl + 1, bA));
+        const long long a0 = capture_launches();
+        // on grids whose preconditioner takes the scaling of the next basis
+        // vector, it reads w and writes V_j (no scaling pass)
+        if (fold) {
+            g->pc_scale = ctl;
+            const int rc = precond_apply(g, dt, g->w, g->z, 1, sa);
+            g->pc_scale = nullptr;
+            TRY(rc);
+        } else {
+            TRY(precond_apply(g, dt, g->q, g->z, 1, sa));
+        }
+        TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, sa));
+        // the last block of the norm pass runs the Givens rotations
+        const GivensCtl gc{ctl, ds, hA, m, cap};
+        TRY(krylov_dots(g, m - 1, &ctl->j, sa));
+        TRY(krylov_update_dots(g, m - 1, &ctl->j, sa));
+        TRY(krylov_update_norm(g, m - 1, &ctl->j, sa, &gc));
+        if (!fold) {
+            if (g->mixed)
+                k_scale_dev<float><<<nb, BS, 0, sa>>>((const float *)g->w, (float *)g->V, (float *)g->q, n, ctl);
+            else
+                k_scale_dev<double><<<nb, BS, 0, sa>>>((const double *)g->w, (double *)g->V, (double *)g->q, n,
+                                                       ctl);
+            CHECK_LAUNCH();
+        }
+        g->glaunch[5] = since(a0);
+        TRY(C.end_body(lvl + 1));
+    }
+    k_ctl_solve<<<1, 1, 0, s>>>(ctl);
+    CHECK_LAUNCH();
+    TRY(krylov_correct(g, 0, nullptr, &ctl->k, ctl->y, s));
+    return MUSIC_OK;
+}
+
 int record(music_grid *g, Capture &C, cudaGraph_t *out)
 {
     const music_grid_desc &d = g->desc;
     const int m = d.gmres_restart;
-    const int kd = !g->mixed;
     const long long n = (long long)g->n;
     const int nb = (int)((n + BS - 1) / BS < 152 * 16 ? (n + BS - 1) / BS : 152 * 16);
     const int cap = loop_cap_of(g);
     const double dt = 1.0;  // every recorded kernel reads dt from g->ctl->dt instead
+    // on grids whose preconditioner takes the scaling of the next basis
+    // vector, it reads w and writes V_j (no scaling pass)
+    const int fold = precond_folds_scale(g) ? 1 : 0;
     SolveCtl *ctl = g->ctl;
     DevScalars *ds = g->ds;
-    cudaStream_t s0 = C.st[0], s1 = C.st[1], s2 = C.st[2], s3 = C.st[3], s4 = C.st[4];
+    cudaStream_t s0 = C.st[0], s1 = C.st[1], s2 = C.st[2];
     cudaStream_t sa0 = C.st[5], sa2 = C.st[6];
-    cudaGraph_t bN, bC, bR, bG, bA, bF;
-    cudaGraphConditionalHandle hN, hC, hR, hG, hA, hF;
+    cudaGraph_t bN, bC, bF;
+    cudaGraphConditionalHandle hN, hC, hA, hA2, hF;
     long long t0;
+    g->glaunch[3] = g->glaunch[4] = 0;
 
     CUDA_TRY(cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed));
     C.open[0] = true;
@@ -420,94 +493,34 @@ int record(music_grid *g, Capture &C, cudaGraph_t *out)
         t0 = capture_launches();
         CUDA_TRY(cudaMemsetAsync(g->x, 0, n * sizeof(double), s1));
         TRY(dev_norm2(g, g->b, 1, (size_t)n, &ds->rnorm2, s1));
-        TRY(new_handle(s1, &hC));
-        k_ctl_gmres<<<1, 1, 0, s1>>>(ctl, ds, hC, d.gmres_rtol);
+        // the first cycle (beta = |b|): its Arnoldi loop's condition comes
+        // from the set-up, its kernels return at once when it builds no basis
+        TRY(new_handle(s1, &hA));
+        k_ctl_gmres<<<1, 1, 0, s1>>>(ctl, ds, hA, d.gmres_rtol, m);
         CHECK_LAUNCH();
-        long long nN = since(t0);
+        TRY(record_cycle(g, C, s1, 2, hA, ctl, nb, fold, cap, m));
+        TRY(new_handle(s1, &hC));
+        k_ctl_cycle_end<<<1, 1, 0, s1>>>(ctl, hC, d.gmres_max_restarts, cap);
+        CHECK_LAUNCH();
+        long long nN = since(t0) - g->glaunch[5];  // the Arnoldi body is counted per step
         TRY(add_conditional(s1, hC, cudaGraphCondTypeWhile, &bC));
         C.bodies.push_back(bC);
         {
-            // ---- GMRES cycle
+            // ---- a restarted cycle: t64 = b - J x, |t64|^2, then as the first
             TRY(C.begin_body(2, bC));
-            t0 = capture_launches();
-            TRY(new_handle(s2, &hR));
-            k_ctl_cycle_pre<<<1, 1, 0, s2>>>(ctl, hR);
+            const long long r0 = capture_launches();
+            k_ctl_cycle_pre<<<1, 1, 0, s2>>>(ctl);
             CHECK_LAUNCH();
-            TRY(add_conditional(s2, hR, cudaGraphCondTypeIf, &bR));
-            C.bodies.push_back(bR);
-            {
-                // restart: t64 = b - J x, |t64|^2
-                TRY(C.begin_body(3, bR));
-                const long long r0 = capture_launches();
-                TRY(jv_apply(g, g->x, 1, g->t64, 1, dt, 1, s3));
-                TRY(vec_sub(g, g->b, g->t64, g->t64, s3));
-                TRY(dev_norm2(g, g->t64, 1, (size_t)n, &ds->rnorm2, s3));
-                g->glaunch[3] = since(r0);
-                TRY(C.end_body(3));
-            }
-            TRY(new_handle(s2, &hG));
-            k_ctl_cycle_start<<<1, 1, 0, s2>>>(ctl, ds, hG, m);
+            TRY(jv_apply(g, g->x, 1, g->t64, 1, dt, 1, s2));
+            TRY(vec_sub(g, g->b, g->t64, g->t64, s2));
+            TRY(dev_norm2(g, g->t64, 1, (size_t)n, &ds->rnorm2, s2));
+            TRY(new_handle(s2, &hA2));
+            k_ctl_cycle_start<<<1, 1, 0, s2>>>(ctl, ds, hA2, m);
             CHECK_LAUNCH();
-            TRY(add_conditional(s2, hG, cudaGraphCondTypeIf, &bG));
-            C.bodies.push_back(bG);
-            {
-                // Arnoldi process and the cycle's correction x += M^-1 V y
-                TRY(C.begin_body(3, bG));
-                const long long c0 = capture_launches();
-                TRY(new_handle(s3, &hA));
-                // on grids whose preconditioner takes the scaling of the next
-                // basis vector, it reads w and writes V_j (no scaling pass)
-                const int fold = precond_folds_scale(g) ? 1 : 0;
-                if (g->mixed)
-                    k_first_dev<float><<<nb, BS, 0, s3>>>(g->b, g->t64, (float *)g->V, (float *)g->q, n, ctl, hA,
-                                                          (float *)g->w, fold);
-                else
-                    k_first_dev<double><<<nb, BS, 0, s3>>>(g->b, g->t64, (double *)g->V, (double *)g->q, n, ctl,
-                                                           hA, (double *)g->w, fold);
-                CHECK_LAUNCH();
-                long long nG = since(c0);
-                TRY(add_conditional(s3, hA, cudaGraphCondTypeWhile, &bA));
-                C.bodies.push_back(bA);
-                {
-                    TRY(C.begin_body(4, bA));
-                    const long long a0 = capture_launches();
-                    if (fold) {
-                        g->pc_scale = ctl;
-                        const int rc = precond_apply(g, dt, g->w, g->z, 1, s4);
-                        g->pc_scale = nullptr;
-                        TRY(rc);
-                    } else {
-                        TRY(precond_apply(g, dt, g->q, g->z, 1, s4));
-                    }
-                    TRY(jv_apply(g, g->z, kd, g->w, kd, dt, 0, s4));
-                    // the last block of the norm pass runs the Givens rotations
-                    const GivensCtl gc{ctl, ds, hA, m, cap};
-                    TRY(krylov_dots(g, m - 1, &ctl->j, s4));
-                    TRY(krylov_update_dots(g, m - 1, &ctl->j, s4));
-                    TRY(krylov_update_norm(g, m - 1, &ctl->j, s4, &gc));
-                    if (!fold) {
-                        if (g->mixed)
-                            k_scale_dev<float><<<nb, BS, 0, s4>>>((const float *)g->w, (float *)g->V, (float *)g->q,
-                                                                  n, ctl);
-                        else
-                            k_scale_dev<double><<<nb, BS, 0, s4>>>((const double *)g->w, (double *)g->V,
-                                                                   (double *)g->q, n, ctl);
-                        CHECK_LAUNCH();
-                    }
-                    g->glaunch[5] = since(a0);
-                    TRY(C.end_body(4));
-                }
-                const long long c1 = capture_launches();
-                k_ctl_solve<<<1, 1, 0, s3>>>(ctl);
-                CHECK_LAUNCH();
-                TRY(krylov_correct(g, 0, nullptr, &ctl->k, ctl->y, s3));
-                g->glaunch[4] = nG + since(c1);
-                TRY(C.end_body(3));
-            }
-            const long long e0 = capture_launches();
+            TRY(record_cycle(g, C, s2, 3, hA2, ctl, nb, fold, cap, m));
             k_ctl_cycle_end<<<1, 1, 0, s2>>>(ctl, hC, d.gmres_max_restarts, cap);
             CHECK_LAUNCH();
-            g->glaunch[2] = 2 + since(e0);  // cycle_pre, cycle_start, cycle_end
+            g->glaunch[2] = since(r0) - g->glaunch[5];
             TRY(C.end_body(2));
         }
         const long long u0 = capture_launches();
@@ -604,9 +617,8 @@ int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStr
     // kernels the replay ran, from the bodies each loop executed (the closing
     // residual runs after every Newton iteration but the last)
     const long long nextres = h->newton_it > 0 ? h->newton_it - 1 : 0;
-    count_launches(g->glaunch[0] + g->glaunch[1] * h->newton_it + g->glaunch[2] * h->cycles +
-                   g->glaunch[3] * h->restarts + g->glaunch[4] * h->solves + g->glaunch[5] * h->gmres_its +
-                   g->glaunch[6] * nextres);
+    count_launches(g->glaunch[0] + g->glaunch[1] * h->newton_it + g->glaunch[2] * h->restarts +
+                   g->glaunch[5] * h->gmres_its + g->glaunch[6] * nextres);
     st->newton_its = h->newton_its;
     st->gmres_its = h->gmres_its;
     st->gmres_unconverged = h->unconverged;

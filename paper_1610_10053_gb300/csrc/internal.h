@@ -98,8 +98,9 @@ struct music_grid {
     SolveCtl *ctl;         // device control of a graph-driven Newton attempt
     SolveCtl *hctl;        // pinned host mirror of its leading scalars
     cudaGraphExec_t gexec; // the recorded Newton attempt (null until first use)
-    long long glaunch[7];  // kernels per recorded section: top, Newton, cycle, restart, correction, Arnoldi,
-                           // the residual that closes a Newton iteration
+    long long glaunch[7];  // kernels per recorded section: top, Newton iteration (with its first GMRES
+                           // cycle), restarted cycle, (unused), (unused), Arnoldi step, the residual
+                           // that closes a Newton iteration
     double *diag_rows;     // per-row diagnostic partials
     // passive scalars (Sec. 2.2)
     int ns;                // scalars (planes of N partial densities in sc.U)
