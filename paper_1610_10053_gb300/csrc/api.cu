@@ -231,9 +231,12 @@ void init_grid_struct(music_grid *g, const music_grid_desc &d)
     // MUSIC_STENCIL=multipass selects the multi-pass stencil on 2-D grids
     const char *sv = getenv("MUSIC_STENCIL");
     g->stencil_variant = (sv && strcmp(sv, "multipass") == 0) ? STENCIL_MULTIPASS : STENCIL_AUTO;
-    // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep
+    // MUSIC_PRECOND=multikernel selects one kernel per Jacobi sweep;
+    // MUSIC_PRECOND=rows keeps those sweeps one cell a thread (no 16-byte chunks)
     const char *pv = getenv("MUSIC_PRECOND");
-    g->pc_variant = (pv && strcmp(pv, "multikernel") == 0) ? PC_MULTIKERNEL : PC_AUTO;
+    g->pc_variant = !pv ? PC_AUTO
+                        : strcmp(pv, "multikernel") == 0 ? PC_MULTIKERNEL
+                                                         : strcmp(pv, "rows") == 0 ? PC_ROWS : PC_AUTO;
     // MUSIC_SOLVER=host sequences Newton and GMRES from the host
     const char *so = getenv("MUSIC_SOLVER");
     g->solver_variant = (so && strcmp(so, "host") == 0) ? SOLVER_HOST : SOLVER_GRAPH;

@@ -28,7 +28,7 @@ struct ExtScratch {
 
 enum StencilVariant { STENCIL_AUTO = 0, STENCIL_FUSED = 1, STENCIL_MULTIPASS = 2 };
 enum SolverVariant { SOLVER_GRAPH = 0, SOLVER_HOST = 1 };
-enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1 };
+enum PrecondVariant { PC_AUTO = 0, PC_MULTIKERNEL = 1, PC_ROWS = 2 };
 // Form of the Jacobian-free product: FP64 difference of two residual
 // evaluations, or the difference form with FP32 differences (mixed-precision
 // grids on the fused 2-D stencil; tile_jvdiff.cuh)

@@ -158,6 +158,23 @@ __global__ void __launch_bounds__(BS) k_jacobi(GridParams P, PC<PT> C, PcK<PT> K
     }
 }
 
+// The weighted-Jacobi update of one cell from its dp, its neighbours' along
+// each direction (upper dpu, lower dpd), its upper and lower face
+// coefficients, its right-hand side and diagonal: one expression, shared by
+// the per-cell and the vectorised sweeps so that both give the same bits.
+template <typename PT>
+__device__ __forceinline__ PT jacobi_value(int nd, PT dpc, const PT *dpu, const PT *dpd, const PT *ap,
+                                           const PT *am, PT bc, PT Dc, const PcK<PT> &K, PT tau2, PT w)
+{
+    PT off = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= nd) break;
+        off += (ap[d] * dpu[d] + am[d] * dpd[d]) * K.idx2[d];
+    }
+    return ((PT)1 - w) * dpc + w * ((bc + tau2 * off) / Dc);
+}
+
 // One weighted-Jacobi update of cell c (coordinates ix) from dp, with the
 // neighbour rule of cell_nb (periodic wrap; at a wall the neighbour beyond it
 // is the cell itself, whose wall coefficient is zero); nb(cell) returns dp at
@@ -166,19 +183,22 @@ template <typename PT, typename NB>
 __device__ __forceinline__ PT jacobi_cell(const GridParams &P, const PC<PT> &C, const PcK<PT> &K, const PT *b,
                                           const int ix[3], long long c, PT tau2, PT w, NB &&nb)
 {
-    PT off = 0;
+    PT dpu[3], dpd[3], ap[3], am[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
+        dpu[d] = dpd[d] = ap[d] = am[d] = (PT)0;
         if (d >= P.nd) break;
         const int n = P.n[d], a = ix[d];
         const long long st = P.cs[d];
         const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
         const long long cu = (a + 1 < n) ? c + st : (per ? c - (long long)(n - 1) * st : c);
         const long long cd = (a > 0) ? c - st : (per ? c + (long long)(n - 1) * st : c);
-        const PT ap = (!per && a == n - 1) ? (PT)0 : C.a[d][cu], am = C.a[d][c];
-        off += (ap * nb(cu, d, +1) + am * nb(cd, d, -1)) * K.idx2[d];
+        ap[d] = (!per && a == n - 1) ? (PT)0 : C.a[d][cu];
+        am[d] = C.a[d][c];
+        dpu[d] = nb(cu, d, +1);
+        dpd[d] = nb(cd, d, -1);
     }
-    return ((PT)1 - w) * nb(c, 0, 0) + w * ((b[c] + tau2 * off) / C.D[c]);
+    return jacobi_value<PT>(P.nd, nb(c, 0, 0), dpu, dpd, ap, am, b[c], C.D[c], K, tau2, w);
 }
 
 // The same sweep as k_jacobi on a 3-D launch grid: x along the threads of a
@@ -205,6 +225,109 @@ __global__ void __launch_bounds__(XT) k_jacobi_rows(GridParams P, PC<PT> C, PcK<
         return;
     }
     dq[c] = jacobi_cell(P, C, K, b, ix, c, tau2, w, [&](long long q, int, int) { return dp[q]; });
+}
+
+// The same sweep with each thread on one 16-byte chunk of W cells adjacent in
+// x (4 floats or 2 doubles; rows of a multiple of W cells): dp, the
+// coefficients, b and D of the chunk and dp and the coefficients of its y and
+// z neighbours in 16-byte loads, the two x neighbours beyond the chunk's ends
+// in single loads, all issued before any update.  Every cell's update is
+// jacobi_value on the neighbours cell_nb gives, so the bits are those of
+// k_jacobi_rows; a sweep over TGV 128^3 is one chunk a thread instead of one
+// cell, a quarter of the loads and blocks.
+template <typename PT>
+__device__ __forceinline__ void ldw(const PT *p, long long c, PT *v)
+{
+    if constexpr (sizeof(PT) == 4) {
+        const float4 a = *reinterpret_cast<const float4 *>(p + c);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2 *>(p + c);
+        v[0] = a.x;
+        v[1] = a.y;
+    }
+}
+
+template <typename PT>
+__device__ __forceinline__ void stw(PT *p, long long c, const PT *v)
+{
+    if constexpr (sizeof(PT) == 4)
+        *reinterpret_cast<float4 *>(p + c) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        *reinterpret_cast<double2 *>(p + c) = make_double2(v[0], v[1]);
+}
+
+template <typename PT, bool FIRST>
+__global__ void __launch_bounds__(BS) k_jacobi_vec(GridParams P, PC<PT> C, PcK<PT> K, const PT *b, const PT *dp,
+                                                   PT *dq, PT tau2)
+{
+    pdl_entry();
+    constexpr int W = 16 / sizeof(PT);
+    PT tau_unused = 0;
+    block_tau(P, tau_unused, tau2);
+    const PT w = (PT)MUSIC_JACOBI_OMEGA;
+    const long long e = blockIdx.x * (long long)BS + threadIdx.x;
+    if (e >= P.N / W) return;
+    const long long c0 = e * W;
+    PT bv[W], Dv[W], out[W];
+    ldw(b, c0, bv);
+    ldw(C.D, c0, Dv);
+    if (FIRST) {
+#pragma unroll
+        for (int q = 0; q < W; q++) out[q] = w * (bv[q] / Dv[q]);
+        stw(dq, c0, out);
+        return;
+    }
+    int ix[3];
+    cell_coords(P, c0, ix);
+    // y and z: the chunk's cells share their neighbours' offsets
+    PT dpc[W], dpu[3][W], dpd[3][W], apv[3][W], amv[3][W];
+    ldw(dp, c0, dpc);
+    bool upw[3] = {false, false, false};
+#pragma unroll
+    for (int d = 1; d < 3; d++) {
+        if (d >= P.nd) break;
+        const int n = P.n[d], a = ix[d];
+        const long long st = P.cs[d];
+        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
+        const long long cu = (a + 1 < n) ? c0 + st : (per ? c0 - (long long)(n - 1) * st : c0);
+        const long long cd = (a > 0) ? c0 - st : (per ? c0 + (long long)(n - 1) * st : c0);
+        upw[d] = !per && a == n - 1;
+        ldw(C.a[d], cu, apv[d]);
+        ldw(C.a[d], c0, amv[d]);
+        ldw(dp, cu, dpu[d]);
+        ldw(dp, cd, dpd[d]);
+    }
+    // x: neighbours inside the chunk, and the two beyond its ends
+    const int n0 = P.n[0], i0 = ix[0];
+    const bool perx = P.bc[0] == MUSIC_BC_PERIODIC;
+    const long long cu_end = (i0 + W < n0) ? c0 + W : (perx ? c0 + W - n0 : c0 + W - 1);
+    const long long cd_end = (i0 > 0) ? c0 - 1 : (perx ? c0 + n0 - 1 : c0);
+    const PT dp_after = dp[cu_end], dp_before = dp[cd_end], a_after = C.a[0][cu_end];
+    PT a0[W];
+    ldw(C.a[0], c0, a0);
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        PT u[3], dn[3], ap[3], am[3];
+        u[0] = (q + 1 < W) ? dpc[q + 1] : dp_after;
+        dn[0] = (q > 0) ? dpc[q - 1] : dp_before;
+        ap[0] = (!perx && i0 + q == n0 - 1) ? (PT)0 : ((q + 1 < W) ? a0[q + 1] : a_after);
+        am[0] = a0[q];
+#pragma unroll
+        for (int d = 1; d < 3; d++) {
+            u[d] = dn[d] = ap[d] = am[d] = (PT)0;
+            if (d >= P.nd) break;
+            u[d] = dpu[d][q];
+            dn[d] = dpd[d][q];
+            ap[d] = upw[d] ? (PT)0 : apv[d][q];
+            am[d] = amv[d][q];
+        }
+        out[q] = jacobi_value<PT>(P.nd, dpc[q], u, dn, ap, am, bv[q], Dv[q], K, tau2, w);
+    }
+    stw(dq, c0, out);
 }
 
 template <typename PT, typename RT>
@@ -299,11 +422,19 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, b, taup);
     CHECK_LAUNCH();
     const int K = g->desc.precond_sweeps;
-    // rows launch unless an extent exceeds the grid's y / z limit (65535)
+    // 16-byte chunks when rows hold a whole number of them; else the rows
+    // launch unless an extent exceeds the grid's y / z limit (65535)
+    constexpr int W = 16 / sizeof(PT);
+    const bool by_chunks = P.n[0] % W == 0 && g->pc_variant != PC_ROWS;
+    const int nbc = (int)((P.N / W + BS - 1) / BS);
     const bool by_rows = P.n[1] <= 65535 && (P.nd < 3 || P.n[2] <= 65535);
     const dim3 rows((P.n[0] + XT - 1) / XT, P.n[1], P.nd == 3 ? P.n[2] : 1);
     for (int k = 0; k < K; k++) {
-        if (by_rows && k == 0)
+        if (by_chunks && k == 0)
+            k_jacobi_vec<PT, true><<<nbc, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
+        else if (by_chunks)
+            k_jacobi_vec<PT, false><<<nbc, BS, 0, s>>>(P, C, pk, b, dp, dq, tau2);
+        else if (by_rows && k == 0)
             k_jacobi_rows<PT, true><<<rows, XT, 0, s>>>(P, C, pk, b, dp, dq, tau2);
         else if (by_rows)
             k_jacobi_rows<PT, false><<<rows, XT, 0, s>>>(P, C, pk, b, dp, dq, tau2);

@@ -338,6 +338,38 @@ def test_precond_variants(case, variant, monkeypatch):
     planewise_close(p, z, O.precond(p, p.U, dt, r), 1e-12, extra=r)
 
 
+@pytest.mark.parametrize("case", ["tgv_16", "periodic3d_ragged", "walls_3d"])
+@pytest.mark.parametrize("prec", ["FP64", "MIXED"])
+def test_precond_chunked_sweeps_give_the_rows_bits(case, prec, monkeypatch):
+    """The per-sweep kernels on 16-byte chunks of cells (rows holding a whole
+    number of chunks) and one cell a thread (MUSIC_PRECOND=rows) give the
+    same bits: one update expression, the same neighbours."""
+    if case == "walls_3d":
+        p = I.random_smooth(3, (12, 10, 8), seed=25, amp=0.3, bc=(I.BC_WALL, I.BC_PERIODIC, I.BC_WALL))
+    else:
+        p = CASES[case]()
+    rng = np.random.default_rng(13)
+    r = rng.standard_normal(p.U.size)
+    N = p.ncells
+    for d in range(p.nd):  # no momentum residual on wall faces
+        if p.bc[d] == I.BC_WALL:
+            m = r[(2 + d) * N:(3 + d) * N].reshape(p.n[2], p.n[1], p.n[0])
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            m[tuple(sl)] = 0.0
+    dt = O.cfl_dt(p, p.U, 8.0)
+    out = []
+    for variant in (None, "rows"):
+        if variant:
+            monkeypatch.setenv("MUSIC_PRECOND", variant)
+        kt = torch.float32 if prec == "MIXED" else torch.float64
+        with B().Grid(p, precision=getattr(B(), prec)) as g:
+            out.append(host(g.precond(dev(p.U), dt, dev(r, kt))))
+    assert np.array_equal(out[0], out[1])
+    if prec == "FP64":
+        planewise_close(p, out[0], O.precond(p, p.U, dt, r), 1e-12, extra=r)
+
+
 def test_precond_sweep_counts():
     """1 and 16 sweeps (the one-launch kernel's halo limit), 17 and 32 (four
     staged launches) and 33 (one kernel per sweep)."""
