@@ -113,6 +113,24 @@ __global__ void __launch_bounds__(BS) k_setup(GridParams P, const double *U, PC<
     }
 }
 
+// Right-hand side of the pressure system of one cell from its r_E, gamma p,
+// and per direction the upper and lower face coefficients and momentum
+// residuals (shared by the per-cell and the chunked kernels: the same bits)
+// (every product and fused step is spelled out, so the compiler's choice of
+// contractions cannot differ between the kernels that inline it)
+template <typename PT>
+__device__ __forceinline__ PT rhs_value(int nd, PT rE, PT gp, const PT *ap, const PT *rp, const PT *am,
+                                        const PT *rm, const PcK<PT> &K, PT tau)
+{
+    PT divm = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= nd) break;
+        divm = pfma(pfma(ap[d], rp[d], -pmul_rn(am[d], rm[d])), K.idx[d], divm);
+    }
+    return pfma(-tau, divm, pmul_rn(K.gm1, rE) / gp);
+}
+
 template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, PT *b, PT tau)
 {
@@ -122,14 +140,17 @@ __global__ void __launch_bounds__(BS) k_rhs(GridParams P, PC<PT> C, PcK<PT> K, c
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
-        PT divm = 0;
-        for (int d = 0; d < P.nd; d++) {
-            const PT ap = a_up(P, C, ix, d), am = C.a[d][c];
-            const PT rp = (PT)r[(2 + d) * P.N + cell_nb(P, ix, d, +1)];
-            const PT rm = (PT)r[(2 + d) * P.N + c];
-            divm += (ap * rp - am * rm) * K.idx[d];
+        PT ap[3], rp[3], am[3], rm[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            ap[d] = rp[d] = am[d] = rm[d] = (PT)0;
+            if (d >= P.nd) break;
+            ap[d] = a_up(P, C, ix, d);
+            am[d] = C.a[d][c];
+            rp[d] = (PT)r[(2 + d) * P.N + cell_nb(P, ix, d, +1)];
+            rm[d] = (PT)r[(2 + d) * P.N + c];
         }
-        b[c] = K.gm1 * (PT)r[P.N + c] / C.gp[c] - tau * divm;
+        b[c] = rhs_value<PT>(P.nd, (PT)r[P.N + c], C.gp[c], ap, rp, am, rm, K, tau);
     }
 }
 
@@ -330,53 +351,231 @@ __global__ void __launch_bounds__(BS) k_jacobi_vec(GridParams P, PC<PT> C, PcK<P
     stw(dq, c0, out);
 }
 
+// The momentum correction on the lower d-face of a cell: its residual, less
+// tau (dp - dp of the lower neighbour) / dx; the residual alone on a wall face
+template <typename PT>
+__device__ __forceinline__ PT dm_value(bool lwall, PT rm, PT dpc, PT dpl, PT tau, PT idx)
+{
+    return lwall ? rm : pfma(-pmul_rn(tau, dpc - dpl), idx, rm);
+}
+
 template <typename PT, typename RT>
 __device__ inline PT dm_face(const GridParams &P, const RT *r, const PT *dp, const int ix[3], long long c,
                              int d, PT tau, PT idx)
 {
     // momentum correction on the lower d-face of cell ix (c)
-    if (lower_wall(P, ix, d)) return (PT)r[(2 + d) * P.N + c];
-    return (PT)r[(2 + d) * P.N + c] - tau * (dp[c] - dp[cell_nb(P, ix, d, -1)]) * idx;
+    return dm_value<PT>(lower_wall(P, ix, d), (PT)r[(2 + d) * P.N + c], dp[c], dp[cell_nb(P, ix, d, -1)], tau, idx);
+}
+
+// Back substitution of one cell in flux form from its own lower-face
+// momentum corrections (mm_own), those of its upper faces (mp, 0 on walls),
+// whether each lower face is a wall, and the face coefficients (shared by the
+// per-cell and the chunked kernels: the same bits)
+template <typename PT>
+__device__ __forceinline__ void back_value(int nd, PT rr, PT rE, PT hp, const PT *mm_own, const PT *mp,
+                                           const bool *lwall, const PT *ap, const PT *am, const PcK<PT> &K, PT tau,
+                                           PT &zr, PT &ze)
+{
+    PT divm = 0, divu = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        if (d >= nd) break;
+        const PT mm = lwall[d] ? (PT)0 : mm_own[d];
+        divm = pfma(mp[d] - mm, K.idx[d], divm);
+        divu = pfma(pfma(ap[d], mp[d], -pmul_rn(am[d], mm)), K.idx[d], divu);
+    }
+    zr = pfma(-tau, divm, rr);
+    ze = pfma(-pmul_rn(tau, hp), divu, rE);
 }
 
 template <typename PT, typename RT>
 __global__ void __launch_bounds__(BS) k_back(GridParams P, PC<PT> C, PcK<PT> K, const RT *r, const PT *dp, RT *z,
-                                             PT tau, double *partial)
+                                             PT tau)
 {
     pdl_entry();
     PT tau2_unused = 0;
     block_tau(P, tau, tau2_unused);
-    __shared__ double sh[BS / 32];
-    double nrm = 0.0;
     for (long long c = blockIdx.x * (long long)BS + threadIdx.x; c < P.N; c += (long long)gridDim.x * BS) {
         int ix[3];
         cell_coords(P, c, ix);
-        PT divm = 0, divu = 0;
-        for (int d = 0; d < P.nd; d++) {
-            const PT mm_own = dm_face(P, r, dp, ix, c, d, tau, K.idx[d]);
-            z[(2 + d) * P.N + c] = (RT)mm_own;
-            const double zz = (double)(RT)mm_own;
-            nrm += zz * zz;
-            PT mp = 0;
+        PT mm_own[3], mp[3], ap[3], am[3];
+        bool lwall[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            mm_own[d] = mp[d] = ap[d] = am[d] = (PT)0;
+            lwall[d] = false;
+            if (d >= P.nd) break;
+            mm_own[d] = dm_face(P, r, dp, ix, c, d, tau, K.idx[d]);
+            z[(2 + d) * P.N + c] = (RT)mm_own[d];
             if (!upper_wall(P, ix, d)) {
                 int jx[3] = {ix[0], ix[1], ix[2]};
                 jx[d] = (ix[d] + 1 == P.n[d]) ? 0 : ix[d] + 1;
-                mp = dm_face(P, r, dp, jx, cell_index(P, jx), d, tau, K.idx[d]);
+                mp[d] = dm_face(P, r, dp, jx, cell_index(P, jx), d, tau, K.idx[d]);
             }
-            const PT mm = lower_wall(P, ix, d) ? (PT)0 : mm_own;
-            divm += (mp - mm) * K.idx[d];
-            divu += (a_up(P, C, ix, d) * mp - C.a[d][c] * mm) * K.idx[d];
+            lwall[d] = lower_wall(P, ix, d);
+            ap[d] = a_up(P, C, ix, d);
+            am[d] = C.a[d][c];
         }
-        const PT zr = (PT)r[c] - tau * divm;
-        const PT ze = (PT)r[P.N + c] - tau * C.hp[c] * divu;
+        PT zr, ze;
+        back_value<PT>(P.nd, (PT)r[c], (PT)r[P.N + c], C.hp[c], mm_own, mp, lwall, ap, am, K, tau, zr, ze);
         z[c] = (RT)zr;
         z[P.N + c] = (RT)ze;
-        nrm += (double)(RT)zr * (double)(RT)zr + (double)(RT)ze * (double)(RT)ze;
     }
-    if (partial) {
-        const double t = block_sum<BS>(nrm, sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// The right-hand side and the back substitution on 16-byte chunks of W cells
+// adjacent in x (rows of a multiple of W cells), as k_jacobi_vec: the
+// chunk's own values and those of its y and z neighbours in 16-byte loads,
+// the x neighbours beyond its two ends in single loads; every cell's value is
+// rhs_value / dm_value / back_value on what the per-cell kernels read, so the
+// bits are theirs.
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_rhs_vec(GridParams P, PC<PT> C, PcK<PT> K, const PT *r, PT *b, PT tau)
+{
+    pdl_entry();
+    constexpr int W = 16 / sizeof(PT);
+    PT tau2_unused = 0;
+    block_tau(P, tau, tau2_unused);
+    const long long e = blockIdx.x * (long long)BS + threadIdx.x;
+    if (e >= P.N / W) return;
+    const long long c0 = e * W, N = P.N;
+    int ix[3];
+    cell_coords(P, c0, ix);
+    PT rE[W], gp[W], am[3][W], ap[3][W], rm[3][W], rp[3][W];
+    ldw(r + N, c0, rE);
+    ldw(C.gp, c0, gp);
+#pragma unroll
+    for (int d = 1; d < 3; d++) {
+        if (d >= P.nd) break;
+        const int n = P.n[d], a = ix[d];
+        const long long st = P.cs[d];
+        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
+        const long long cu = (a + 1 < n) ? c0 + st : (per ? c0 - (long long)(n - 1) * st : c0);
+        ldw(C.a[d], c0, am[d]);
+        ldw(C.a[d], cu, ap[d]);
+        if (!per && a == n - 1)
+#pragma unroll
+            for (int q = 0; q < W; q++) ap[d][q] = (PT)0;
+        ldw(r + (2 + d) * N, c0, rm[d]);
+        ldw(r + (2 + d) * N, cu, rp[d]);
     }
+    const int n0 = P.n[0], i0 = ix[0];
+    const bool perx = P.bc[0] == MUSIC_BC_PERIODIC;
+    const long long cu_end = (i0 + W < n0) ? c0 + W : (perx ? c0 + W - n0 : c0 + W - 1);
+    ldw(C.a[0], c0, am[0]);
+    ldw(r + 2 * N, c0, rm[0]);
+    const PT a_after = C.a[0][cu_end], r_after = r[2 * N + cu_end];
+    PT out[W];
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        PT apq[3], rpq[3], amq[3], rmq[3];
+        apq[0] = (!perx && i0 + q == n0 - 1) ? (PT)0 : ((q + 1 < W) ? am[0][q + 1] : a_after);
+        rpq[0] = (q + 1 < W) ? rm[0][q + 1] : r_after;
+        amq[0] = am[0][q];
+        rmq[0] = rm[0][q];
+#pragma unroll
+        for (int d = 1; d < 3; d++) {
+            apq[d] = rpq[d] = amq[d] = rmq[d] = (PT)0;
+            if (d >= P.nd) break;
+            apq[d] = ap[d][q];
+            rpq[d] = rp[d][q];
+            amq[d] = am[d][q];
+            rmq[d] = rm[d][q];
+        }
+        out[q] = rhs_value<PT>(P.nd, rE[q], gp[q], apq, rpq, amq, rmq, K, tau);
+    }
+    stw(b, c0, out);
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(BS) k_back_vec(GridParams P, PC<PT> C, PcK<PT> K, const PT *r, const PT *dp,
+                                                 PT *z, PT tau)
+{
+    pdl_entry();
+    constexpr int W = 16 / sizeof(PT);
+    PT tau2_unused = 0;
+    block_tau(P, tau, tau2_unused);
+    const long long e = blockIdx.x * (long long)BS + threadIdx.x;
+    if (e >= P.N / W) return;
+    const long long c0 = e * W, N = P.N;
+    int ix[3];
+    cell_coords(P, c0, ix);
+    PT rr[W], rE[W], hp[W], dpc[W];
+    ldw(r, c0, rr);
+    ldw(r + N, c0, rE);
+    ldw(C.hp, c0, hp);
+    ldw(dp, c0, dpc);
+    // per direction and cell: own lower-face correction, upper-face one,
+    // lower wall, face coefficients
+    PT mmo[3][W], mpv[3][W], apv[3][W], amv[3][W];
+    bool lw[3][W];
+#pragma unroll
+    for (int d = 1; d < 3; d++) {
+        if (d >= P.nd) break;
+        const int n = P.n[d], a = ix[d];
+        const long long st = P.cs[d];
+        const bool per = P.bc[d] == MUSIC_BC_PERIODIC;
+        const long long cu = (a + 1 < n) ? c0 + st : (per ? c0 - (long long)(n - 1) * st : c0);
+        const long long cd = (a > 0) ? c0 - st : (per ? c0 + (long long)(n - 1) * st : c0);
+        const bool upw = !per && a == n - 1, low = !per && a == 0;
+        PT rmc[W], rmu[W], dpd[W], dpu[W];
+        ldw(r + (2 + d) * N, c0, rmc);
+        ldw(r + (2 + d) * N, cu, rmu);
+        ldw(dp, cd, dpd);
+        ldw(dp, cu, dpu);
+        ldw(C.a[d], c0, amv[d]);
+        ldw(C.a[d], cu, apv[d]);
+        const PT idx = K.idx[d];
+#pragma unroll
+        for (int q = 0; q < W; q++) {
+            lw[d][q] = low;
+            mmo[d][q] = dm_value<PT>(low, rmc[q], dpc[q], dpd[q], tau, idx);
+            mpv[d][q] = upw ? (PT)0 : dm_value<PT>(false, rmu[q], dpu[q], dpc[q], tau, idx);
+            if (upw) apv[d][q] = (PT)0;
+        }
+        stw(z + (2 + d) * N, c0, mmo[d]);
+    }
+    const int n0 = P.n[0], i0 = ix[0];
+    const bool perx = P.bc[0] == MUSIC_BC_PERIODIC;
+    const long long cu_end = (i0 + W < n0) ? c0 + W : (perx ? c0 + W - n0 : c0 + W - 1);
+    const long long cd_end = (i0 > 0) ? c0 - 1 : (perx ? c0 + n0 - 1 : c0);
+    PT rm0[W];
+    ldw(r + 2 * N, c0, rm0);
+    ldw(C.a[0], c0, amv[0]);
+    const PT dp_after = dp[cu_end], dp_before = dp[cd_end], r_after = r[2 * N + cu_end], a_after = C.a[0][cu_end];
+    const PT idx0 = K.idx[0];
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        const bool low = !perx && i0 + q == 0, upw = !perx && i0 + q == n0 - 1;
+        const PT dpl = (q > 0) ? dpc[q - 1] : dp_before;
+        const PT dpu = (q + 1 < W) ? dpc[q + 1] : dp_after;
+        const PT rmu = (q + 1 < W) ? rm0[q + 1] : r_after;
+        lw[0][q] = low;
+        mmo[0][q] = dm_value<PT>(low, rm0[q], dpc[q], dpl, tau, idx0);
+        mpv[0][q] = upw ? (PT)0 : dm_value<PT>(false, rmu, dpu, dpc[q], tau, idx0);
+        apv[0][q] = upw ? (PT)0 : ((q + 1 < W) ? amv[0][q + 1] : a_after);
+    }
+    stw(z + 2 * N, c0, mmo[0]);
+    PT zr[W], ze[W];
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        PT mo[3], mq[3], aq[3], bq[3];
+        bool lq[3];
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            mo[d] = mq[d] = aq[d] = bq[d] = (PT)0;
+            lq[d] = false;
+            if (d >= P.nd) break;
+            mo[d] = mmo[d][q];
+            mq[d] = mpv[d][q];
+            aq[d] = apv[d][q];
+            bq[d] = amv[d][q];
+            lq[d] = lw[d][q];
+        }
+        back_value<PT>(P.nd, rr[q], rE[q], hp[q], mo, mq, lq, aq, bq, K, tau, zr[q], ze[q]);
+    }
+    stw(z, c0, zr);
+    stw(z + N, c0, ze);
 }
 
 int nblocks(long long n)
@@ -419,14 +618,18 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
     const int nb = nblocks(P.N);
     PT *b = (PT *)g->pb, *dp = (PT *)g->pdp, *dq = (PT *)g->pdq;
     const PcK<PT> pk = pck_of<PT>(P);
-    k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, b, taup);
-    CHECK_LAUNCH();
-    const int K = g->desc.precond_sweeps;
-    // 16-byte chunks when rows hold a whole number of them; else the rows
-    // launch unless an extent exceeds the grid's y / z limit (65535)
+    // 16-byte chunks when rows hold a whole number of them; else one cell a
+    // thread, the sweeps' rows launch unless an extent exceeds the grid's y /
+    // z limit (65535)
     constexpr int W = 16 / sizeof(PT);
     const bool by_chunks = P.n[0] % W == 0 && g->pc_variant != PC_ROWS;
     const int nbc = (int)((P.N / W + BS - 1) / BS);
+    if (by_chunks)
+        k_rhs_vec<PT><<<nbc, BS, 0, s>>>(P, C, pk, r, b, taup);
+    else
+        k_rhs<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, b, taup);
+    CHECK_LAUNCH();
+    const int K = g->desc.precond_sweeps;
     const bool by_rows = P.n[1] <= 65535 && (P.nd < 3 || P.n[2] <= 65535);
     const dim3 rows((P.n[0] + XT - 1) / XT, P.n[1], P.nd == 3 ? P.n[2] : 1);
     for (int k = 0; k < K; k++) {
@@ -448,7 +651,10 @@ int apply_t(music_grid *g, double dt, const PT *r, PT *z, cudaStream_t s)
         dq = t;
     }
     if (K == 0) CUDA_TRY(cudaMemsetAsync(dp, 0, P.N * sizeof(PT), s));
-    k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, dp, z, taup, nullptr);
+    if (by_chunks)
+        k_back_vec<PT><<<nbc, BS, 0, s>>>(P, C, pk, r, dp, z, taup);
+    else
+        k_back<PT, PT><<<nb, BS, 0, s>>>(P, C, pk, r, dp, z, taup);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }
