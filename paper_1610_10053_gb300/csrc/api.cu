@@ -602,8 +602,11 @@ int music_newton_step(music_grid *grid, double dt_max, music_step_stats *st, voi
     }
     double dt = dt_max;
     if (d.cfl_hydro > 0.0 || d.cfl_adv > 0.0 || d.cfl_rad > 0.0) {
-        // the most restrictive limit, from the state at the start of the step
+        // the most restrictive limit, from the state at the start of the step:
+        // chosen on the device when the recorded graph steps the grid (the same
+        // choice, without a host round trip), else here
         const music_dt_limits lim = {d.cfl_hydro, d.cfl_adv, d.cfl_rad, dt_max};
+        if (graph_driven(grid)) return newton_solve(grid, 0.0, st, (cudaStream_t)stream, &lim);
         TRY(music_select_dt(grid, &lim, &dt, nullptr, stream));
     } else if (!(dt_max > 0.0)) {
         set_error("music_newton_step: the grid has no time-step limit, so dt_max must be > 0");

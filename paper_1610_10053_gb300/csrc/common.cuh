@@ -117,6 +117,8 @@ enum { CNT_DOTS = 0, CNT_UPDATE, CNT_NORMW, CNT_SUMSQ, CNT_NEWTON, CNT_PRECOND }
 // then the Hessenberg matrix with its Givens rotations.
 struct SolveCtl {
     double dt;                         // step size of the attempt
+    int dt_status;    // MUSIC_OK, or why the device-side choice of dt found none (k_ctl_dt)
+    int dt_which;     // the limit that chose dt (0-2: CFL_hydro, advective, radiative; 3: dt_max)
     double bnorm, target, beta, resid; // |b|, eta |b|, cycle start residual, current residual
     double inv;                        // 1 / h_{j+1,j} of the pending basis scaling
     double fnorm0, fnorm, maxdrho;

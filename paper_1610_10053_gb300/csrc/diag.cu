@@ -252,6 +252,16 @@ extern "C" int music_velocity_error(music_grid *fine, music_grid *coarse, double
     return MUSIC_OK;
 }
 
+int step_rates(music_grid *g, cudaStream_t s)
+{
+    const GridParams &P = g->P;
+    k_rate_rows<<<P.n[1], BS, 0, s>>>(P, g->U, g->diag_rows);
+    CHECK_LAUNCH();
+    k_combine_rates<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
 extern "C" int music_select_dt(music_grid *g, const music_dt_limits *lim, double *dt, int *which, void *stream)
 {
     if (!g || !lim || !dt) {
@@ -259,11 +269,7 @@ extern "C" int music_select_dt(music_grid *g, const music_dt_limits *lim, double
         return MUSIC_E_INVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const GridParams &P = g->P;
-    k_rate_rows<<<P.n[1], BS, 0, s>>>(P, g->U, g->diag_rows);
-    CHECK_LAUNCH();
-    k_combine_rates<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds);
-    CHECK_LAUNCH();
+    TRY(step_rates(g, s));
     CUDA_TRY(cudaMemcpyAsync(g->hs, g->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     const double rates[3] = {g->hs->rate, g->hs->rate_adv, g->hs->rate_rad};

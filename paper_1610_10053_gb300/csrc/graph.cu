@@ -34,6 +34,40 @@ constexpr int BS = 256;
 // (the Arnoldi loop's) thread 0 of the norm pass's last block, which runs
 // ctl_givens.
 
+// dt of the attempt from the rates at U^n (ds->rate, rate_adv, rate_rad) and
+// the limits: the most restrictive cfl_k / rate_k over the limits set (> 0)
+// with a positive rate, capped by dt_max > 0 — music_select_dt's choice, in
+// the same correctly rounded FP64 operations.  A non-finite rate, or no
+// limit that applies, leaves dt_status set and the attempt does nothing.
+__global__ void k_ctl_dt(SolveCtl *c, const DevScalars *ds, double cfl_h, double cfl_a, double cfl_r, double dt_max)
+{
+    pdl_entry();
+    const double rates[3] = {ds->rate, ds->rate_adv, ds->rate_rad};
+    const double cfl[3] = {cfl_h, cfl_a, cfl_r};
+    double best = __longlong_as_double(0x7ff0000000000000LL);  // +infinity
+    int w = -1, status = MUSIC_OK;
+    for (int k = 0; k < 3; k++) {
+        if (!isfinite(rates[k])) {
+            status = MUSIC_E_NONFINITE;
+            break;
+        }
+        if (!(cfl[k] > 0.0) || !(rates[k] > 0.0)) continue;
+        const double t = __ddiv_rn(cfl[k], rates[k]);
+        if (t < best) {
+            best = t;
+            w = k;
+        }
+    }
+    if (status == MUSIC_OK && dt_max > 0.0 && dt_max < best) {
+        best = dt_max;
+        w = 3;
+    }
+    if (status == MUSIC_OK && w < 0) status = MUSIC_E_INVAL;
+    c->dt = best;
+    c->dt_which = w;
+    c->dt_status = status;
+}
+
 __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, int newton_max)
 {
     pdl_entry();
@@ -51,7 +85,8 @@ __global__ void k_ctl_attempt(SolveCtl *c, cudaGraphConditionalHandle h_newton, 
     c->stop = 0;
     c->ok = 0;
     c->guard = 0;
-    cudaGraphSetConditional(h_newton, newton_max > 0 ? 1u : 0u);
+    // no dt (the device-side choice found none): no Newton iteration
+    cudaGraphSetConditional(h_newton, (newton_max > 0 && c->dt_status == MUSIC_OK) ? 1u : 0u);
 }
 
 // GMRES set-up after |b|^2 -> ds->rnorm2 (b = -F(U), x = 0), and the start
@@ -601,7 +636,7 @@ void graph_release(music_grid *g)
     g->hctl = nullptr;
 }
 
-int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s)
+int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s, const music_dt_limits *lim)
 {
     if (!g->gexec) {
         int rc = record_attempt(g, true);
@@ -609,11 +644,30 @@ int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStr
         TRY(rc);
     }
     SolveCtl *h = g->hctl;
-    h->dt = dt;
-    CUDA_TRY(cudaMemcpyAsync(&g->ctl->dt, &h->dt, sizeof(double), cudaMemcpyHostToDevice, s));
+    if (lim) {
+        // dt chosen on the device from the rates at U^n: no host round trip
+        // between the step's start and its graph
+        TRY(step_rates(g, s));
+        k_ctl_dt<<<1, 1, 0, s>>>(g->ctl, g->ds, lim->cfl_hydro, lim->cfl_adv, lim->cfl_rad, lim->dt_max);
+        CHECK_LAUNCH();
+    } else {
+        h->dt = dt;
+        h->dt_status = MUSIC_OK;
+        h->dt_which = -1;
+        CUDA_TRY(cudaMemcpyAsync(&g->ctl->dt, &h->dt, offsetof(SolveCtl, bnorm), cudaMemcpyHostToDevice, s));
+    }
     CUDA_TRY(cudaGraphLaunch(g->gexec, s));
     CUDA_TRY(cudaMemcpyAsync(h, g->ctl, offsetof(SolveCtl, cs), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    st->dt = h->dt;
+    if (h->dt_status == MUSIC_E_NONFINITE) {
+        set_error("music_select_dt: non-finite rate");
+        return MUSIC_E_NONFINITE;
+    }
+    if (h->dt_status != MUSIC_OK) {
+        set_error("music_select_dt: no limit applies (all <= 0, or the state is at rest)");
+        return MUSIC_E_INVAL;
+    }
     // kernels the replay ran, from the bodies each loop executed (the closing
     // residual runs after every Newton iteration but the last)
     const long long nextres = h->newton_it > 0 ? h->newton_it - 1 : 0;

@@ -261,6 +261,8 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
 
 // ----- diag.cu -----
 int cfl_rate(music_grid *g, const double *U, cudaStream_t s);                  // -> ds->rate
+// the three rates of the time-step limits at the grid's state -> ds->rate, rate_adv, rate_rad
+int step_rates(music_grid *g, cudaStream_t s);
 int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s);
 
 // ----- api.cu: grid lifetime on a given home stream (used by the server) -----
@@ -295,7 +297,12 @@ int capture_ext_fluxes(music_grid *g, cudaStream_t s);
 void swap_space(music_grid *g);
 
 // ----- solver.cu -----
-int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);
+// lim (recorded-graph grids only): the first attempt's dt is chosen on the
+// device from the limits, as music_select_dt would choose it; dt is then unused
+int newton_solve(music_grid *g, double dt, music_step_stats *st, cudaStream_t s,
+                 const music_dt_limits *lim = nullptr);
+// whether newton_solve steps the grid with the recorded graph
+bool graph_driven(const music_grid *g);
 // J v for the current Newton iterate (eps from |U| and, with need_vnorm, |v|)
 int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_double, double dt,
              int need_vnorm, cudaStream_t s);
@@ -304,7 +311,8 @@ int jv_apply(music_grid *g, const void *v, int vin_double, void *out, int out_do
 // One Newton attempt (Sec. 2) as a recorded CUDA graph whose Newton, restart
 // and Arnoldi loops are conditional nodes driven by device-side control.
 // Same arguments and results as the host-sequenced attempt.
-int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s);
+int graph_newton_attempt(music_grid *g, double dt, music_step_stats *st, cudaStream_t s,
+                         const music_dt_limits *lim = nullptr);
 void graph_release(music_grid *g);
 
 // ----- tune.cu -----

@@ -309,7 +309,12 @@ int prof_harvest(music_grid *g, int wait)
     return MUSIC_OK;
 }
 
-int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_t s)
+bool graph_driven(const music_grid *g)
+{
+    return g->solver_variant == SOLVER_GRAPH && !g->prof_on && g->ns == 0;
+}
+
+int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_t s, const music_dt_limits *lim)
 {
     auto t0 = std::chrono::steady_clock::now();
     music_step_stats st;
@@ -318,10 +323,13 @@ int newton_solve(music_grid *g, double dt, music_step_stats *st_out, cudaStream_
     int h = 0;
     for (;;) {
         st.dt = dt;
-        if (g->solver_variant == SOLVER_GRAPH && !g->prof_on && g->ns == 0)
-            rc = graph_newton_attempt(g, dt, &st, s);
-        else
+        if (graph_driven(g)) {
+            // the first attempt may choose its dt on the device (st.dt receives it)
+            rc = graph_newton_attempt(g, dt, &st, s, h == 0 ? lim : nullptr);
+            dt = st.dt;
+        } else {
             rc = newton_attempt(g, dt, &st, s);
+        }
         if (rc == MUSIC_E_TIMEOUT) {
             // an attempt stopped by the loop-body bound leaves a partial
             // iterate: restore U^n (and the scalars) as a failed attempt does
