@@ -271,7 +271,8 @@ def run_music(args):
         serving = run_serving(args.serve_solves, lane_cells=args.serve_lane_cells)
         # a mix of small grids only, which cannot fill the GPU one solve at a time
         serving = {"mix": serving, "small_grids": run_serving(
-            args.serve_solves, lane_cells=args.serve_lane_cells, grids=((64, 64), (128, 128)), label="small")}
+            args.serve_solves, lane_cells=args.serve_lane_cells, grids=((64, 64), (128, 128)), label="small"),
+            "burst_64": run_burst(args.serve_solves, lane_cells=args.serve_lane_cells)}
 
     if rank != 0:
         return
@@ -544,6 +545,22 @@ def run_serving(nsolves=256, max_active=16, lane_cells=16384,
     for k in ("cell_steps_per_s", "step_ms_p50", "step_ms_p99", "request_ms_p50", "request_ms_p99",
               "queue_ms_p99", "over_sequential_fp64", "completed"):
         out[k] = out[best][k]
+    return out
+
+
+def run_burst(nsolves=256, max_active=16, lane_cells=16384):
+    """A burst of small solves: the mix's 64^2 setups only, all arriving at
+    once, through the server with the batch lane off (max_active solves on
+    the GPU at a time, each on the whole GPU) and on (every resident solve
+    one CTA of one batched launch per round)."""
+    probs, gaps = serving_mix(nsolves, grids=((64, 64),))
+    zero = np.zeros_like(np.asarray(gaps))
+    out = {"mix": "burst of 64x64 solves, all arriving at once", "solves": nsolves, "max_active": max_active,
+           "cell_steps": sum(p.ncells * p.nsteps for p in probs)}
+    for name, lc in (("lane_off", 0), ("lane_on", lane_cells)):
+        out[name] = serve(probs, zero, max_active, lc)
+    out["best"] = max(("lane_off", "lane_on"), key=lambda k: out[k]["cell_steps_per_s"])
+    out["lane_on_over_lane_off"] = out["lane_on"]["cell_steps_per_s"] / out["lane_off"]["cell_steps_per_s"]
     return out
 
 
