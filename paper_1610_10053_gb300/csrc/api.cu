@@ -210,7 +210,9 @@ void alloc_plan(music_grid *g, F &&f)
     f(&g->binst, 1024);  // batched-solver descriptor (sizeof checked in batched.cu)
     f((void **)&g->ds, sizeof(DevScalars));
     f((void **)&g->ctl, sizeof(SolveCtl));
-    f((void **)&g->diag_rows, (size_t)8 * P.n[1] * sizeof(double));
+    // per-row partials of the diagnostics (8 a row) and of the rates (3 a row and slab)
+    const size_t nrow = (size_t)P.n[1] * (8 > 3 * rate_slabs(P) ? 8 : 3 * rate_slabs(P));
+    f((void **)&g->diag_rows, nrow * sizeof(double));
     if (g->ns > 0) {
         const size_t nq = (size_t)g->ns * N;
         KSpace &S = g->sc;

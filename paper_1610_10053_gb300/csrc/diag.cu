@@ -105,18 +105,21 @@ __global__ void __launch_bounds__(BS) k_combine_rows(GridParams P, const double 
     }
 }
 
-// Per row j: the maxima over its cells and directions of (|u_d| + c_s) / h_d,
-// |u_d| / h_d and D / h_d^2 (D = chi / (rho c_v), 0 without radiative
-// diffusion); the first has k_rows' expression, so both give the same rate.
+// Per row j and slab sl of its z range (gridDim.y slabs): the maxima over
+// its cells and directions of (|u_d| + c_s) / h_d, |u_d| / h_d and D / h_d^2
+// (D = chi / (rho c_v), 0 without radiative diffusion); the first has k_rows'
+// expression, so both give the same rate.  A maximum does not depend on the
+// order it is taken in, so neither do the rates on the slab count.
 __global__ void __launch_bounds__(BS) k_rate_rows(GridParams P, const double *U, double *rows)
 {
     pdl_entry();
     __shared__ double sh[BS / 32];
-    const int j = blockIdx.x;
+    const int j = blockIdx.x, sl = blockIdx.y, ns = gridDim.y;
+    const int z0 = (int)((long long)sl * P.n[2] / ns), z1 = (int)((long long)(sl + 1) * P.n[2] / ns);
     double s[3] = {0, 0, 0};
-    const long long per_row = (long long)P.n[0] * P.n[2];
-    for (long long t = threadIdx.x; t < per_row; t += BS) {
-        int ix[3] = {(int)(t % P.n[0]), j, (int)(t / P.n[0])};
+    const long long per_slab = (long long)P.n[0] * (z1 - z0);
+    for (long long t = threadIdx.x; t < per_slab; t += BS) {
+        int ix[3] = {(int)(t % P.n[0]), j, z0 + (int)(t / P.n[0])};
         const long long c = cell_index(P, ix);
         const double rho = U[c];
         const double cs = sqrt(P.gamma * (P.gm1 * U[P.N + c]) / rho);
@@ -148,19 +151,21 @@ __global__ void __launch_bounds__(BS) k_rate_rows(GridParams P, const double *U,
             }
         }
     }
+    const long long per_q = (long long)P.n[1] * ns;
     for (int q = 0; q < 3; q++) {
         const double r = block_max<BS>(s[q], sh);
-        if (threadIdx.x == 0) rows[(long long)q * P.n[1] + j] = r;
+        if (threadIdx.x == 0) rows[q * per_q + (long long)j * ns + sl] = r;
     }
 }
 
-__global__ void __launch_bounds__(BS) k_combine_rates(GridParams P, const double *rows, DevScalars *ds)
+// the three rates from the partial maxima of k_rate_rows (count per rate)
+__global__ void __launch_bounds__(BS) k_combine_rates(GridParams P, const double *rows, DevScalars *ds, int count)
 {
     pdl_entry();
     __shared__ double sh[BS / 32];
     double a[3] = {0, 0, 0};
-    for (int j = threadIdx.x; j < P.n[1]; j += BS)
-        for (int q = 0; q < 3; q++) a[q] = nanmax(a[q], rows[(long long)q * P.n[1] + j]);
+    for (int j = threadIdx.x; j < count; j += BS)
+        for (int q = 0; q < 3; q++) a[q] = nanmax(a[q], rows[(long long)q * count + j]);
     double r[3];
     for (int q = 0; q < 3; q++) r[q] = block_max<BS>(a[q], sh);
     if (threadIdx.x == 0) {
@@ -255,9 +260,10 @@ extern "C" int music_velocity_error(music_grid *fine, music_grid *coarse, double
 int step_rates(music_grid *g, cudaStream_t s)
 {
     const GridParams &P = g->P;
-    k_rate_rows<<<P.n[1], BS, 0, s>>>(P, g->U, g->diag_rows);
+    const int ns = rate_slabs(P);
+    k_rate_rows<<<dim3(P.n[1], ns), BS, 0, s>>>(P, g->U, g->diag_rows);
     CHECK_LAUNCH();
-    k_combine_rates<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds);
+    k_combine_rates<<<1, BS, 0, s>>>(P, g->diag_rows, g->ds, P.n[1] * ns);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

@@ -263,6 +263,8 @@ int precond_apply(music_grid *g, double dt, const void *r, void *z, int want_nor
 int cfl_rate(music_grid *g, const double *U, cudaStream_t s);                  // -> ds->rate
 // the three rates of the time-step limits at the grid's state -> ds->rate, rate_adv, rate_rad
 int step_rates(music_grid *g, cudaStream_t s);
+// z slabs a row of the rate reduction is split into (3-D grids: more blocks)
+inline int rate_slabs(const GridParams &P) { return P.nd == 3 ? (P.n[2] < 16 ? P.n[2] : 16) : 1; }
 int diagnostics(music_grid *g, const double *U, double rho_L, double rho_H, cudaStream_t s);
 
 // ----- api.cu: grid lifetime on a given home stream (used by the server) -----
