@@ -220,27 +220,40 @@ static double or_gface(const or_grid *g, int d, int i)
 #define T double
 #define RE(x) (x)
 #define SQRT(x) sqrt(x)
+#define TABS(x) fabs(x)
 #define FN(name) FN1(name, _r)
 #include "residual_body.h"
 #undef T
 #undef RE
 #undef SQRT
+#undef TABS
 #undef FN
 
 #define T double complex
 #define RE(x) creal(x)
 #define SQRT(x) csqrt(x)
+#define TABS(x) cabs(x)
 #define FN(name) FN1(name, _c)
 #include "residual_body.h"
 #undef T
 #undef RE
 #undef SQRT
+#undef TABS
 #undef FN
 
 /* Eqs. 1-3: R(U) (spatial operator, no time discretisation). */
 void or_spatial_operator(const or_grid *g, const double *U, double *R)
 {
     spatial_operator_r(g, U, R);
+}
+
+/* R(U), and per cell and variable the sum of the magnitudes of the terms R
+ * adds there (fluxes over the cell's faces, pressure work and gradient,
+ * gravity and, on spherical grids, the curvature terms, each with its
+ * geometric weight): the scale of R's rounding, for per-cell tolerances. */
+void or_spatial_operator_terms(const or_grid *g, const double *U, double *R, double *A)
+{
+    spatial_operator_f_r(g, U, R, NULL, A);
 }
 
 /* Exact directional derivative dR = (dR/dU) V by complex-step
@@ -1036,7 +1049,7 @@ static double **or_mass_fluxes(const or_grid *g, const double *U)
     double **Fr = (double **)calloc(3, sizeof(double *));
     for (int d = 0; d < g->nd; d++) Fr[d] = (double *)calloc(X.total, sizeof(double));
     double *R = (double *)malloc(n * sizeof(double));
-    spatial_operator_f_r(g, U, R, Fr);
+    spatial_operator_f_r(g, U, R, Fr, NULL);
     free(R);
     return Fr;
 }

@@ -111,6 +111,7 @@ def lib():
         L.or_set_threads.argtypes = [ctypes.c_int]
         G = ctypes.POINTER(OrGrid)
         L.or_spatial_operator.argtypes = [G, _dbl_p, _dbl_p]
+        L.or_spatial_operator_terms.argtypes = [G, _dbl_p, _dbl_p, _dbl_p]
         L.or_spatial_operator_dir.argtypes = [G, _dbl_p, _dbl_p, _dbl_p]
         L.or_cn_residual.argtypes = [G, _dbl_p, _dbl_p, ctypes.c_double, _dbl_p]
         L.or_step_constant.argtypes = [G, _dbl_p, ctypes.c_double, _dbl_p]
@@ -194,6 +195,17 @@ def spatial_operator(prob, U) -> np.ndarray:
     g = grid(prob)
     lib().or_spatial_operator(ctypes.byref(g), _p(U), _p(R))
     return R
+
+
+def spatial_operator_terms(prob, U):
+    """(R(U), A): A per cell and variable is the sum of the magnitudes of the
+    terms R adds there, the scale of R's rounding (per-cell tolerances)."""
+    U = _vec(U)
+    R = np.empty_like(U)
+    A = np.empty_like(U)
+    g = grid(prob)
+    lib().or_spatial_operator_terms(ctypes.byref(g), _p(U), _p(R), _p(A))
+    return R, A
 
 
 def spatial_operator_dir(prob, U, V) -> np.ndarray:

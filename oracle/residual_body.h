@@ -39,7 +39,7 @@ static T FN(vanleer)(T a, T b)
  * mass fluxes u rho* on the d-faces (one extended-grid array per direction,
  * the flux of the lower d-face of each point) for the passive scalars.
  */
-static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
+static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout, T *Aout)
 {
     const int nd = g->nd;
     const long N = or_ncells(g);
@@ -319,6 +319,19 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             }
             R[N + c] = R[N + c] + cond;
         }
+        if (Aout) {
+            /* the magnitude of every term the residual of this cell sums */
+            T ar = 0.0, ae = 0.0, au = 0.0;
+            for (int d = 0; d < nd; d++) {
+                const long s = X.stride[d];
+                ar += (TABS(Frho[d][x + s]) + TABS(Frho[d][x])) / g->dx[d];
+                ae += (TABS(FE[d][x + s]) + TABS(FE[d][x])) / g->dx[d];
+                au += (TABS(uf[d][x + s]) + TABS(uf[d][x])) / g->dx[d];
+                if (g->conduct) ae += (TABS(Gc[d][x + s]) + TABS(Gc[d][x])) / g->dx[d];
+            }
+            Aout[c] = ar;
+            Aout[N + c] = ae + TABS(p[x]) * au;
+        }
         for (int d = 0; d < nd; d++) {
             if (g->bc[d] == OR_BC_WALL && ix[d] == 0) {
                 R[(2 + d) * N + c] = 0.0;
@@ -334,7 +347,20 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             }
             T rbar = 0.5 * (rho[x - s] + rho[x]);
             R[(2 + d) * N + c] = (-acc - (p[x] - p[x - s]) / g->dx[d]) + rbar * g->g[d];
+            if (Aout) {
+                T am = 0.0;
+                for (int q = 0; q < nd; q++) {
+                    if (q == d)
+                        am += (TABS(Phi[d][x]) + TABS(Phi[d][x - s])) / g->dx[d];
+                    else
+                        am += (TABS(Psi[d][q][x + X.stride[q]]) + TABS(Psi[d][q][x])) / g->dx[q];
+                }
+                Aout[(2 + d) * N + c] = am + (TABS(p[x]) + TABS(p[x - s])) / g->dx[d] + TABS(rbar * g->g[d]);
+            }
         }
+        if (Aout)
+            for (int d = 0; d < nd; d++)
+                if (g->bc[d] == OR_BC_WALL && ix[d] == 0) Aout[(2 + d) * N + c] = 0.0;
     }
     /* spherical (r, theta): area-weighted divergences over each control volume */
     OR_PAR
@@ -356,6 +382,20 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             T cd = (Arp * Gc[0][x + s0] - Arm * Gc[0][x]) + (Atp * Gc[1][x + s1] - Atm * Gc[1][x]);
             R[N + c] = R[N + c] + cd / V;
         }
+        if (Aout) {
+            Aout[c] = (Arp * TABS(Frho[0][x + s0]) + Arm * TABS(Frho[0][x]) + Atp * TABS(Frho[1][x + s1]) +
+                       Atm * TABS(Frho[1][x])) / V;
+            T ae = (Arp * TABS(FE[0][x + s0]) + Arm * TABS(FE[0][x]) + Atp * TABS(FE[1][x + s1]) +
+                    Atm * TABS(FE[1][x])) / V;
+            ae += TABS(p[x]) * ((Arp * TABS(uf[0][x + s0]) + Arm * TABS(uf[0][x]) + Atp * TABS(uf[1][x + s1]) +
+                                 Atm * TABS(uf[1][x])) / V);
+            if (g->conduct)
+                ae += (Arp * TABS(Gc[0][x + s0]) + Arm * TABS(Gc[0][x]) + Atp * TABS(Gc[1][x + s1]) +
+                       Atm * TABS(Gc[1][x])) / V;
+            Aout[N + c] = ae;
+            Aout[2 * N + c] = 0.0;
+            Aout[3 * N + c] = 0.0;
+        }
         const double ctj = cos(or_th(g, j)), ctj1 = cos(or_th(g, j + 1));
         /* radial momentum on r-face i: control volume r_{i-1/2}..r_{i+1/2} */
         if (g->bc[0] == OR_BC_WALL && i == 0) {
@@ -371,6 +411,11 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             T ut = 0.25 * ((uf[1][x - s0] + uf[1][x]) + (uf[1][x - s0 + s1] + uf[1][x + s1]));
             R[2 * N + c] = ((-acc / Vr - (p[x] - p[x - s0]) / g->dx[0]) + rbar * ut * ut / rf) +
                            rbar * or_gface(g, 0, i);
+            if (Aout)
+                Aout[2 * N + c] = (Acp * TABS(Phi[0][x]) + Acm * TABS(Phi[0][x - s0]) + Ep * TABS(Psi[0][1][x + s1]) +
+                                   Em * TABS(Psi[0][1][x])) / Vr +
+                                  (TABS(p[x]) + TABS(p[x - s0])) / g->dx[0] + TABS(rbar * ut * ut / rf) +
+                                  TABS(rbar * or_gface(g, 0, i));
         }
         /* polar momentum on theta-face j: control volume theta_{j-1/2}..theta_{j+1/2} */
         if (g->bc[1] == OR_BC_WALL && j == 0) {
@@ -387,6 +432,11 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
             T ur = 0.25 * ((uf[0][x - s1] + uf[0][x]) + (uf[0][x - s1 + s0] + uf[0][x + s0]));
             R[3 * N + c] = ((-acc / Vt - (p[x] - p[x - s1]) / (rc * g->dx[1])) - rbar * ur * uf[1][x] / rc) +
                            rbar * g->g[1];
+            if (Aout)
+                Aout[3 * N + c] = (Fb * TABS(Psi[1][0][x + s0]) + Fa * TABS(Psi[1][0][x]) + Bp * TABS(Phi[1][x]) +
+                                   Bm * TABS(Phi[1][x - s1])) / Vt +
+                                  (TABS(p[x]) + TABS(p[x - s1])) / (rc * g->dx[1]) + TABS(rbar * ur * uf[1][x] / rc) +
+                                  TABS(rbar * g->g[1]);
         }
     }
 
@@ -400,7 +450,7 @@ static void FN(spatial_operator_f)(const or_grid *g, const T *U, T *R, T **Fout)
     }
 }
 
-static void FN(spatial_operator)(const or_grid *g, const T *U, T *R) { FN(spatial_operator_f)(g, U, R, NULL); }
+static void FN(spatial_operator)(const or_grid *g, const T *U, T *R) { FN(spatial_operator_f)(g, U, R, NULL, NULL); }
 
 /*
  * Passive scalars (Sec. 2.2): S_i(q) = -div(c_i rho u) for the partial

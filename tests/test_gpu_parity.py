@@ -84,13 +84,33 @@ def planewise_close(prob, got, ref, rtol, extra=None, U=None):
     return worst
 
 
+def cellwise_close(got, ref, A, rtol):
+    """|got - ref| <= rtol A per cell and variable, A the sum of the
+    magnitudes of the terms the residual adds there (the oracle's
+    spatial_operator_terms): the rounding of a sum of such terms is a few ulp
+    of A, whatever their cancellation.  Where A is 0 (a wall face) both must
+    be exactly 0."""
+    err = np.abs(got - ref)
+    worst = float((err / np.where(A > 0, A, 1.0)).max())
+    assert (err <= rtol * A).all(), worst
+    return worst
+
+
+def residual_terms(p, U, Un, dt):
+    """Term magnitudes of F(U) = U - C^n - dt/2 R(U), C^n = U^n + dt/2 R(U^n)."""
+    A = O.spatial_operator_terms(p, U)[1]
+    An = O.spatial_operator_terms(p, Un)[1]
+    return np.abs(U) + np.abs(Un) + 0.5 * dt * (A + An)
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_spatial_operator(case):
     p = CASES[case]()
     with B().Grid(p) as g:
         R = host(g.spatial_operator(dev(p.U)))
-    ref = O.spatial_operator(p, p.U)
+    ref, A = O.spatial_operator_terms(p, p.U)
     planewise_close(p, R, ref, 1e-12)
+    cellwise_close(R, ref, A, 1e-12)
     # wall faces carry exactly zero
     N = p.ncells
     for d in range(p.nd):
@@ -118,6 +138,7 @@ def test_cn_residual(case):
         F = host(g.residual(dev(U), dev(p.U), dt))
     ref = O.cn_residual(p, U, p.U, dt)
     planewise_close(p, F, ref, 1e-12, extra=U, U=U)
+    cellwise_close(F, ref, residual_terms(p, U, p.U, dt), 1e-12)
 
 
 @pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "periodic3d_ragged"])
@@ -289,21 +310,24 @@ def test_full_size_kh_residual():
         F = host(g.residual(dev(U), dev(p.U), dt))
     ref = O.cn_residual(p, U, p.U, dt)
     planewise_close(p, F, ref, 1e-12, extra=U, U=U)
+    cellwise_close(F, ref, residual_terms(p, U, p.U, dt), 1e-12)
 
 
 def test_tgv256_residual_by_periodic_tiling():
     """256^3: a state periodic with period 32 cells must give the oracle's
     residual of one 32^3 period, tiled (R is local)."""
     base = I.random_smooth(3, (32, 32, 32), seed=25, amp=0.3, length=(1.0, 1.0, 1.0))
-    Rb = O.spatial_operator(base, base.U)
+    Rb, Ab = O.spatial_operator_terms(base, base.U)
     nv, N = base.nvars, base.ncells
     tile = lambda a: np.tile(a.reshape(32, 32, 32), (8, 8, 8)).reshape(-1)
     U = np.concatenate([tile(base.U[v * N:(v + 1) * N]) for v in range(nv)])
     Rt = np.concatenate([tile(Rb[v * N:(v + 1) * N]) for v in range(nv)])
+    At = np.concatenate([tile(Ab[v * N:(v + 1) * N]) for v in range(nv)])
     big = base.with_options(n=(256, 256, 256), length=(8.0, 8.0, 8.0)).with_state(U)
     with B().Grid(big, precision=B().MIXED) as g:
         R = host(g.spatial_operator(dev(U)))
     planewise_close(big, R, Rt, 1e-12)
+    cellwise_close(R, Rt, At, 1e-12)
 
 
 @pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "walls_mirror_x", "rt_64x192"])
@@ -313,7 +337,9 @@ def test_spatial_operator_multipass_variant(case, monkeypatch):
     p = CASES[case]()
     with B().Grid(p) as g:
         R = host(g.spatial_operator(dev(p.U)))
-    planewise_close(p, R, O.spatial_operator(p, p.U), 1e-12)
+    ref, A = O.spatial_operator_terms(p, p.U)
+    planewise_close(p, R, ref, 1e-12)
+    cellwise_close(R, ref, A, 1e-12)
 
 
 @pytest.mark.parametrize("case", ["periodic2d_ragged", "walls_hse2d", "walls_mirror_x"])

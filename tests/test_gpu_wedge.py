@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-from test_gpu_parity import B, dev, host, planewise_close, diag_close  # noqa: E402
+from test_gpu_parity import B, dev, host, planewise_close, cellwise_close, diag_close  # noqa: E402
 
 
 def wedge(nr=20, nth=12, noise=1e-3):
@@ -42,7 +42,9 @@ def test_operator_and_residual(case, prec):
     pr = B().FP64 if prec == "fp64" else B().MIXED
     with B().Grid(p, precision=pr) as g:
         R = host(g.spatial_operator(dev(p.U)))
-    planewise_close(p, R, O.spatial_operator(p, p.U), 1e-12)
+    ref, A = O.spatial_operator_terms(p, p.U)
+    planewise_close(p, R, ref, 1e-12)
+    cellwise_close(R, ref, A, 1e-12)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))

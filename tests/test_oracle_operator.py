@@ -28,6 +28,56 @@ def test_uniform_flow_is_steady(nd, n):
     assert np.abs(R).max() <= 1e-13
 
 
+def test_term_magnitudes_of_uniform_flow():
+    """Per-cell sum of the magnitudes of R's terms (the scale the GPU parity
+    tests hold R's rounding to), on a uniform flow along x and y, where every
+    term is a known flux: mass rho u_d and energy u_d E through both faces of
+    each direction, p |u_d| of the velocity divergence, centre momentum flux
+    rho u_d^2, edge flux rho u_q u_d, and the pressure on both faces.  R
+    itself vanishes, so this also shows the sum is not |R|."""
+    nx, ny, rho, pr, ux, uy, gam = 8, 6, 1.3, 2.0, 0.3, -0.2, 1.4
+    p = I.uniform_flow(2, (nx, ny), rho=rho, p=pr, u=(ux, uy, 0.0), gamma=gam)
+    R, A = O.spatial_operator_terms(p, p.U)
+    assert np.array_equal(R, O.spatial_operator(p, p.U))
+    E = pr / (gam - 1.0)
+    ix, iy = nx, ny  # 1 / dx, 1 / dy on the unit box
+    want = [2 * rho * (abs(ux) * ix + abs(uy) * iy),
+            2 * (abs(ux) * E * ix + abs(uy) * E * iy) + pr * 2 * (abs(ux) * ix + abs(uy) * iy),
+            2 * rho * ux * ux * ix + 2 * abs(rho * uy * ux) * iy + 2 * pr * ix,
+            2 * rho * uy * uy * iy + 2 * abs(rho * ux * uy) * ix + 2 * pr * iy]
+    N = p.ncells
+    for v, w in enumerate(want):
+        np.testing.assert_allclose(A[v * N:(v + 1) * N], w, rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["periodic3d", "walls_gravity2d", "wedge", "conduct2d"])
+def test_term_magnitudes_bound_the_residual(case):
+    """|R| <= sum of |terms| per cell and variable (the triangle inequality,
+    up to rounding), with equality to zero where R is zero by construction
+    (lower wall faces); R as the plain operator gives it."""
+    if case == "periodic3d":
+        p = I.random_smooth(3, (7, 6, 5), seed=41, amp=0.4)
+    elif case == "walls_gravity2d":
+        p = I.random_smooth(2, (12, 10), seed=42, amp=0.3, bc=(I.BC_WALL, I.BC_WALL, I.BC_PERIODIC), g=(0.0, -0.5, 0.0))
+    elif case == "wedge":
+        p = I.spherical_wedge(nr=16, nth=12)
+    else:
+        p = I.random_smooth(2, (12, 10), seed=43, amp=0.3).with_options(conduct=1, chi0=0.01)
+    R, A = O.spatial_operator_terms(p, p.U)
+    assert np.array_equal(R, O.spatial_operator(p, p.U))
+    assert (A >= 0).all()
+    assert (np.abs(R) <= A * (1 + 1e-12)).all()
+    N = p.ncells
+    for d in range(p.nd):
+        if p.bc[d] == I.BC_WALL:
+            a = A[(2 + d) * N:(3 + d) * N].reshape(p.n[2], p.n[1], p.n[0])
+            sl = [slice(None)] * 3
+            sl[2 - d] = 0
+            assert (a[tuple(sl)] == 0).all()
+    # terms cancel: |R| is well below their magnitudes in most cells
+    assert np.median(np.abs(R) / np.where(A > 0, A, 1.0)) < 0.5
+
+
 def test_rt_hydrostatic_state_is_discrete_equilibrium():
     """Sec. 3 / Sec. 6: the unperturbed Rayleigh-Taylor state P = P0 - rho g y
     is balanced exactly by the staggered pressure gradient and the face
