@@ -164,7 +164,7 @@ __device__ __forceinline__ Kc launch_consts(const GridParams &P, const double *e
 
 // ---- A: the direction's entries (cells through the ghost mapping; faces as
 // d(m / rb) = (dm - u drb) / rb')
-template <typename VT>
+template <typename VT, int ND>
 __global__ void __launch_bounds__(BS) k_dload(GridParams P, const double *U, const VT *v, const double *eps_dev,
                                               LinX L, DiffX D)
 {
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(BS) k_dload(GridParams P, const double *U, con
         D.dr[x] = d1;
         D.dE[x] = d2;
         D.de[x] = __fdividef(d2 - e * d1, fmaf(K.eps, d1, r));
-        for (int d = 0; d < P.nd; d++) {
+        for (int d = 0; d < ND; d++) {
             long long c, cl;
             double sgn;
             float du = 0.0f;
@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(BS) k_dfluxes(GridParams P, const double *eps_
 
 // ---- D: momentum flux differences at cell centres (Phi, along d) and on
 // edges (Psi, the flux of u_d across q)
+template <int ND>
 __global__ void __launch_bounds__(BS) k_dmomentum(GridParams P, const double *eps_dev, LinX L, DiffX D)
 {
     pdl_entry();
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(BS) k_dmomentum(GridParams P, const double *ep
     for (long long x = blockIdx.x * (long long)BS + threadIdx.x; x < P.M; x += (long long)gridDim.x * BS) {
         int ix[3];
         ext_coords(P, x, ix);
-        for (int d = 0; d < P.nd; d++) {
+        for (int d = 0; d < ND; d++) {
             const long long s = P.es[d];
             if (ext_has(P, ix, d, -2) && ext_has(P, ix, d, +2)) {
                 // slopes of u_d along d at the centre's two faces
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(BS) k_dmomentum(GridParams P, const double *ep
                 D.dPhi[d][x] = momflux_d(D.Fr[d][x], D.Fr[d][x + s], D.dFr[d][x], D.dFr[d][x + s], L.u[d][x], S0,
                                          D.du[d][x], dS0, L.u[d][x + s], S1, D.du[d][x + s], dS1, K.eps, K.ieps);
             }
-            for (int q = 0; q < P.nd; q++) {
+            for (int q = 0; q < ND; q++) {
                 if (q == d) continue;
                 if (!ext_has(P, ix, d, -1) || !ext_has(P, ix, q, -2) || !ext_has(P, ix, q, +1)) continue;
                 const long long t = P.es[q];
@@ -359,11 +360,20 @@ int jvdiff_multipass(music_grid *g, const double *U, const float *v, float *out,
     const LinX L = linx_of(g);
     const double *eps = &g->ds->eps;
     const int nbm = blocks_for(P.M);
-    k_dload<float><<<nbm, BS, 0, s>>>(P, U, v, eps, L, D);
+    // the direction entries and the momentum fluxes instantiated for the grid's
+    // dimension count (their direction loops unroll: k_dmomentum 206 -> 161 us
+    // a launch cold on TGV 128^3; the flux pass ran slower that way)
+    if (P.nd == 3)
+        k_dload<float, 3><<<nbm, BS, 0, s>>>(P, U, v, eps, L, D);
+    else
+        k_dload<float, 2><<<nbm, BS, 0, s>>>(P, U, v, eps, L, D);
     CHECK_LAUNCH();
     k_dfluxes<<<nbm, BS, 0, s>>>(P, eps, L, D);
     CHECK_LAUNCH();
-    k_dmomentum<<<nbm, BS, 0, s>>>(P, eps, L, D);
+    if (P.nd == 3)
+        k_dmomentum<3><<<nbm, BS, 0, s>>>(P, eps, L, D);
+    else
+        k_dmomentum<2><<<nbm, BS, 0, s>>>(P, eps, L, D);
     CHECK_LAUNCH();
     DConst C{};
     for (int d = 0; d < 3; d++) {
