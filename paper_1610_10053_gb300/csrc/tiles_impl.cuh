@@ -69,6 +69,17 @@ int launch_jvdiff2d(music_grid *g, const double *U, const float *v, float *out, 
     return MUSIC_OK;
 }
 
+// Two 1024-thread CTAs of a single-precision stage whose shared memory is
+// under half an SM's fit one SM once a thread holds at most 32 registers:
+// the 16 x 16 launches of a 512^2 grid then run in one wave.
+template <typename PT, int KM, int TX, int TY>
+constexpr int pc_min_blocks()
+{
+    constexpr size_t smem = (size_t)pc_planes<PT, KM, TX, TY>() * (TX + 2 * (KM + 1)) * (TY + 2 * (KM + 1)) *
+                                sizeof(PT) + TX * TY * sizeof(double);
+    return sizeof(PT) == 4 && TX * TY == 1024 && smem <= 100 * 1024 ? 2 : 1;
+}
+
 // The application z = M^-1 r in one kernel, or in a few (stages) with a
 // shallower halo each: a CTA owns a TX x TY tile and stages the frozen
 // coefficients and r (or, after the first stage, the right-hand side and dp)
@@ -85,7 +96,7 @@ int launch_jvdiff2d(music_grid *g, const double *U, const float *v, float *out, 
 // With sc (the solver graph's control), the input is r * sc->inv and the
 // first stage writes it to basis vector sc->scale_idx of Vb (nV entries each).
 template <typename PT, int KM, int TX, int TY, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(TX *TY) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z, PT tau,
+__global__ void __launch_bounds__(TX *TY, pc_min_blocks<PT, KM, TX, TY>()) k_precond_fused2d(GridParams P, PC<PT> C, const PT *r, PT *z, PT tau,
                                                              PT tau2, int K, double *partial, DevScalars *ds,
                                                              PT *bg, const PT *dpin, PT *dpout, const SolveCtl *sc,
                                                              PT *Vb, long long nV)
