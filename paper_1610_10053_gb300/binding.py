@@ -142,6 +142,8 @@ SIGNATURES = {
                                                 _dbl_p]),
     "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
+    "music_quotients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                       ctypes.c_void_p]),
     "music_set_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_get_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
@@ -269,6 +271,17 @@ def measure_peaks() -> dict:
     check(load().music_measure_peaks(ctypes.byref(pk), _stream()))
     return {"fp64_fma_tflops": pk.fp64_fma_tflops, "fp32_fma_tflops": pk.fp32_fma_tflops,
             "fp64_div_gops": pk.fp64_div_gops, "sms": pk.sms}
+
+
+def quotients(n, d):
+    """n / d element by element as the FP64 stencils form the van Leer
+    slope's quotient (music_quotients); n and d contiguous float64 CUDA
+    tensors of one size."""
+    import torch
+    assert n.dtype == torch.float64 and d.dtype == torch.float64 and n.numel() == d.numel()
+    q = torch.empty_like(n)
+    check(load().music_quotients(_ptr(n), _ptr(d), _ptr(q), n.numel(), _stream()))
+    return q
 
 
 def velocity_error(fine, coarse) -> float:

@@ -433,3 +433,21 @@ int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux
     set_error("stencil: bad tile index %d", tile);
     return MUSIC_E_INVAL;
 }
+
+__global__ void __launch_bounds__(BS) k_quotients(const double *n, const double *d, double *q, long long count)
+{
+    for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < count; i += (long long)gridDim.x * BS)
+        q[i] = quot(n[i], d[i]);
+}
+
+extern "C" int music_quotients(const double *n, const double *d, double *q, long long count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!n || !d || !q))) {
+        set_error("music_quotients: NULL array or negative count");
+        return MUSIC_E_INVAL;
+    }
+    if (count == 0) return MUSIC_OK;
+    k_quotients<<<blocks_for(count), BS, 0, (cudaStream_t)stream>>>(n, d, q, count);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}

@@ -18,9 +18,33 @@ struct WLoad {
     }
 };
 
+// n / d within 2 ulp of the correctly rounded quotient: Newton's
+// method for the reciprocal of d, started from a single-precision estimate y0
+// (rcp.approx.ftz.f32 of d rounded to single, relative error below 2^-22)
+// and taken to third order in one step, y = y0 (1 + e + e^2) with
+// e = 1 - d y0, which leaves a relative error of e^3 (below 2^-66) before
+// the roundings of y and of n y.  Three FMAs and a product take the place
+// of a division's longer sequence on the FP64 pipe, which bounds the
+// stencil.  A d whose single-precision value is not a normal number far
+// from the range's ends (zero, subnormal, huge, infinite or NaN) divides.
+__device__ __forceinline__ double quot(double n, double d)
+{
+    const float df = __double2float_rn(d);
+    const float ad = fabsf(df);
+    if (!(ad > 0x1p-120f && ad < 0x1p120f)) return n / d;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(df));
+    const double y0 = (double)rf;
+    const double e = fma(-d, y0, 1.0);
+    const double y = fma(y0, fma(e, e, e), y0);
+    return n * y;
+}
+
+// van Leer's limited slope 2ab / (a + b) of the one-sided differences a and
+// b where they have the same sign, else 0 (Sec. 2)
 __device__ inline double vanleer(double a, double b)
 {
-    return (a * b > 0.0) ? (2.0 * a) * b / (a + b) : 0.0;
+    return (a * b > 0.0) ? quot((2.0 * a) * b, a + b) : 0.0;
 }
 
 // Ghost mapping of cell ix (in place into j, which starts as ix): periodic
