@@ -473,18 +473,18 @@ int music_profile_read(music_grid *grid, uint64_t *launches, double *ms);
 int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, double *ms);
 
 /*
- * q[i] = n[i] / d[i] computed the way the FP64 stencils form the quotient of
- * the van Leer slope 2ab/(a+b) (Sec. 2): the reciprocal of d by one third-order Newton
- * step from a single-precision estimate, then a product, within 2 ulp of
- * the correctly rounded quotient; a d whose single-precision value is zero,
- * subnormal, infinite, NaN or beyond 2^+-120 takes the IEEE division.  It
- * exists so that a test can hold that bound against the host's division.
- * n, d, q: device arrays of `count` doubles (the caller owns them; q may
- * alias neither input).  Asynchronous on `stream`.
- * Errors: MUSIC_E_INVAL (count < 0, or a NULL array with count > 0),
- * MUSIC_E_CUDA.
+ * s[i] = the van Leer slope of Sec. 2 of the one-sided differences a[i] and
+ * b[i] as the FP64 stencils compute it: 2ab / (a + b) where a b > 0, else
+ * 0, with the quotient from one third-order Newton step for the reciprocal
+ * of a + b from a single-precision estimate (within 2 ulp of the correctly
+ * rounded (2a b) / (a + b)); a + b beyond 2^+-120, subnormal, infinite or
+ * NaN takes the IEEE division.  It exists so that a test can hold that
+ * bound against the host's arithmetic.  a, b, s: device arrays of `count`
+ * doubles (the caller owns them; s may alias neither input).  Asynchronous
+ * on `stream`.  Errors: MUSIC_E_INVAL (count < 0, or a NULL array with
+ * count > 0), MUSIC_E_CUDA.
  */
-int music_quotients(const double *n, const double *d, double *q, long long count, void *stream);
+int music_vanleer_slopes(const double *a, const double *b, double *s, long long count, void *stream);
 
 /*
  * Measured arithmetic ceilings of the current device: FP64 and FP32 fused

@@ -142,8 +142,8 @@ SIGNATURES = {
                                                 _dbl_p]),
     "music_get_jv_form": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
-    "music_quotients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
-                                       ctypes.c_void_p]),
+    "music_vanleer_slopes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
+                                            ctypes.c_void_p]),
     "music_set_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_get_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
@@ -273,15 +273,15 @@ def measure_peaks() -> dict:
             "fp64_div_gops": pk.fp64_div_gops, "sms": pk.sms}
 
 
-def quotients(n, d):
-    """n / d element by element as the FP64 stencils form the van Leer
-    slope's quotient (music_quotients); n and d contiguous float64 CUDA
-    tensors of one size."""
+def vanleer_slopes(a, b):
+    """The van Leer slopes of the one-sided differences a and b as the FP64
+    stencils compute them (music_vanleer_slopes); a and b contiguous float64
+    CUDA tensors of one size."""
     import torch
-    assert n.dtype == torch.float64 and d.dtype == torch.float64 and n.numel() == d.numel()
-    q = torch.empty_like(n)
-    check(load().music_quotients(_ptr(n), _ptr(d), _ptr(q), n.numel(), _stream()))
-    return q
+    assert a.dtype == torch.float64 and b.dtype == torch.float64 and a.numel() == b.numel()
+    s = torch.empty_like(a)
+    check(load().music_vanleer_slopes(_ptr(a), _ptr(b), _ptr(s), a.numel(), _stream()))
+    return s
 
 
 def velocity_error(fine, coarse) -> float:

@@ -434,20 +434,20 @@ int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux
     return MUSIC_E_INVAL;
 }
 
-__global__ void __launch_bounds__(BS) k_quotients(const double *n, const double *d, double *q, long long count)
+__global__ void __launch_bounds__(BS) k_vanleer(const double *a, const double *b, double *s, long long count)
 {
     for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < count; i += (long long)gridDim.x * BS)
-        q[i] = quot(n[i], d[i]);
+        s[i] = vanleer(a[i], b[i]);
 }
 
-extern "C" int music_quotients(const double *n, const double *d, double *q, long long count, void *stream)
+extern "C" int music_vanleer_slopes(const double *a, const double *b, double *s, long long count, void *stream)
 {
-    if (count < 0 || (count > 0 && (!n || !d || !q))) {
-        set_error("music_quotients: NULL array or negative count");
+    if (count < 0 || (count > 0 && (!a || !b || !s))) {
+        set_error("music_vanleer_slopes: NULL array or negative count");
         return MUSIC_E_INVAL;
     }
     if (count == 0) return MUSIC_OK;
-    k_quotients<<<blocks_for(count), BS, 0, (cudaStream_t)stream>>>(n, d, q, count);
+    k_vanleer<<<blocks_for(count), BS, 0, (cudaStream_t)stream>>>(a, b, s, count);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

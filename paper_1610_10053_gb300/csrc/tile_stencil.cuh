@@ -18,33 +18,47 @@ struct WLoad {
     }
 };
 
-// n / d within 2 ulp of the correctly rounded quotient: Newton's
-// method for the reciprocal of d, started from a single-precision estimate y0
-// (rcp.approx.ftz.f32 of d rounded to single, relative error below 2^-22)
-// and taken to third order in one step, y = y0 (1 + e + e^2) with
-// e = 1 - d y0, which leaves a relative error of e^3 (below 2^-66) before
-// the roundings of y and of n y.  Three FMAs and a product take the place
-// of a division's longer sequence on the FP64 pipe, which bounds the
-// stencil.  A d whose single-precision value is not a normal number far
-// from the range's ends (zero, subnormal, huge, infinite or NaN) divides.
-__device__ __forceinline__ double quot(double n, double d)
+// 2n / d within 2 ulp of the correctly rounded quotient of 2n by d, with
+// four FP64-pipe operations: Newton's method for the reciprocal of d, started
+// from a single-precision estimate y0 and taken to third order in one step,
+// y = y0 (1 + e + e^2) with e = 1 - d y0, leaves a relative error of e^3
+// (below 2^-63) before the roundings of y and of 2n y.  The estimate is
+// rcp.approx.ftz.f32 of d truncated to single precision (relative error
+// below 2^-21 in all), and both conversions are done on the bit patterns:
+// for d between 2^-120 and 2^120 they only move the exponent and the leading
+// mantissa bits, and the factor 2 goes into the exponent of the estimate
+// (the iteration's steps scale exactly with it).  Any other d (zero,
+// subnormal, huge, infinite, NaN) takes the IEEE division.
+__device__ __forceinline__ double twice_quot(double n, double d)
 {
-    const float df = __double2float_rn(d);
-    const float ad = fabsf(df);
-    if (!(ad > 0x1p-120f && ad < 0x1p120f)) return n / d;
+    const int hi = __double2hiint(d);
+    const unsigned lo = (unsigned)__double2loint(d);
+    const int E = (hi >> 20) & 0x7ff;
+    if ((unsigned)(E - (1023 - 120)) > 240u) return (2.0 * n) / d;
+    const int fb = (hi & (int)0x80000000) | ((E - 896) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29);
     float rf;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(df));
-    const double y0 = (double)rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(fb)));
+    const int rb = __float_as_int(rf);
+    const int rhi = (rb & (int)0x80000000) | ((((rb >> 23) & 0xff) + 896) << 20) | ((rb & 0x7fffff) >> 3);
+    const int rlo = (rb & 7) << 29;
+    const double y0 = __hiloint2double(rhi, rlo);
+    const double y2 = __hiloint2double(rhi + (1 << 20), rlo);
     const double e = fma(-d, y0, 1.0);
-    const double y = fma(y0, fma(e, e, e), y0);
-    return n * y;
+    return n * fma(y2, fma(e, e, e), y2);
 }
 
 // van Leer's limited slope 2ab / (a + b) of the one-sided differences a and
-// b where they have the same sign, else 0 (Sec. 2)
+// b where a b > 0, else 0 (Sec. 2).  The sign test reads the bit patterns:
+// a and b nonzero, neither NaN, and of one sign.  (Where a b underflows to
+// zero the numerator is that zero, so the slope is zero as the product's
+// test would make it.)
 __device__ inline double vanleer(double a, double b)
 {
-    return (a * b > 0.0) ? quot((2.0 * a) * b, a + b) : 0.0;
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    const unsigned long long ma = (unsigned long long)ia << 1, mb = (unsigned long long)ib << 1;
+    const unsigned long long inf2 = 0xffe0000000000000ull;
+    if ((ia ^ ib) < 0 || ma - 1 >= inf2 || mb - 1 >= inf2) return 0.0;
+    return twice_quot(a * b, a + b);
 }
 
 // Ghost mapping of cell ix (in place into j, which starts as ix): periodic

@@ -105,6 +105,6 @@ def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
     assert L.music_create_grid(None, ctypes.byref(h)) == 1
     assert L.music_destroy_grid(None) == 0
     assert L.music_state_size(None) == 0
-    assert L.music_quotients(None, None, None, -1, None) == 1
-    assert L.music_quotients(None, None, None, 5, None) == 1
-    assert L.music_quotients(None, None, None, 0, None) == 0
+    assert L.music_vanleer_slopes(None, None, None, -1, None) == 1
+    assert L.music_vanleer_slopes(None, None, None, 5, None) == 1
+    assert L.music_vanleer_slopes(None, None, None, 0, None) == 0
