@@ -436,6 +436,7 @@ int fused2d_dispatch(music_grid *g, int mode, const double *U, const double *aux
 
 __global__ void __launch_bounds__(BS) k_vanleer(const double *a, const double *b, double *s, long long count)
 {
+    pdl_entry();
     for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < count; i += (long long)gridDim.x * BS)
         s[i] = vanleer(a[i], b[i]);
 }
