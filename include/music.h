@@ -487,6 +487,21 @@ int music_profile_read_class(music_grid *grid, int cls, uint64_t *launches, doub
 int music_vanleer_slopes(const double *a, const double *b, double *s, long long count, void *stream);
 
 /*
+ * q[i] = n[i] / d[i] as the FP64 stencils form the quotients they stage:
+ * the specific internal energy e = E / rho and the face velocities
+ * u_d = m_d / rbar of Sec. 2's staggered grid (rbar the mean density of the
+ * face's two cells).  The same third-order Newton step for the reciprocal
+ * of d from a single-precision estimate as music_vanleer_slopes, without
+ * the factor 2: within 2 ulp of the correctly rounded n / d; d beyond
+ * 2^+-120, zero, subnormal, infinite or NaN takes the IEEE division.  It
+ * exists so that a test can hold that bound against the host's arithmetic.
+ * n, d, q: device arrays of `count` doubles (the caller owns them; q may
+ * alias neither input).  Asynchronous on `stream`.  Errors: MUSIC_E_INVAL
+ * (count < 0, or a NULL array with count > 0), MUSIC_E_CUDA.
+ */
+int music_stencil_quotients(const double *n, const double *d, double *q, long long count, void *stream);
+
+/*
  * Measured arithmetic ceilings of the current device: FP64 and FP32 fused
  * multiply-add throughput (2 flops each) and FP64 division throughput, each
  * the best of five launches of 8 resident blocks per SM, every thread running

@@ -144,6 +144,8 @@ SIGNATURES = {
     "music_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), ctypes.c_void_p]),
     "music_vanleer_slopes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong,
                                             ctypes.c_void_p]),
+    "music_stencil_quotients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_longlong, ctypes.c_void_p]),
     "music_set_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     "music_get_batch_tile": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
 }
@@ -282,6 +284,17 @@ def vanleer_slopes(a, b):
     s = torch.empty_like(a)
     check(load().music_vanleer_slopes(_ptr(a), _ptr(b), _ptr(s), a.numel(), _stream()))
     return s
+
+
+def stencil_quotients(n, d):
+    """n / d as the FP64 stencils form E / rho and m / rbar
+    (music_stencil_quotients); n and d contiguous float64 CUDA tensors of one
+    size."""
+    import torch
+    assert n.dtype == torch.float64 and d.dtype == torch.float64 and n.numel() == d.numel()
+    q = torch.empty_like(n)
+    check(load().music_stencil_quotients(_ptr(n), _ptr(d), _ptr(q), n.numel(), _stream()))
+    return q
 
 
 def velocity_error(fine, coarse) -> float:

@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(BS) k_load(GridParams P, const double *U, cons
         const double e = E / rho;
         X.e[x] = e;
         X.p[x] = P.gm1 * E;
-        for (int d = 0; d < P.nd; d++) X.uf[d][x] = face_velocity(P, W, ix, d);
+        for (int d = 0; d < P.nd; d++) X.uf[d][x] = face_velocity<false>(P, W, ix, d);
         if (P.conduct) {
             // T = (gamma-1) e and the photon conductivity chi = chi0 T^6.5 / rho^2
             const double T = P.gm1 * e;
@@ -449,6 +449,25 @@ extern "C" int music_vanleer_slopes(const double *a, const double *b, double *s,
     }
     if (count == 0) return MUSIC_OK;
     k_vanleer<<<blocks_for(count), BS, 0, (cudaStream_t)stream>>>(a, b, s, count);
+    CHECK_LAUNCH();
+    return MUSIC_OK;
+}
+
+__global__ void __launch_bounds__(BS) k_quot(const double *n, const double *d, double *q, long long count)
+{
+    pdl_entry();
+    for (long long i = blockIdx.x * (long long)BS + threadIdx.x; i < count; i += (long long)gridDim.x * BS)
+        q[i] = quot(n[i], d[i]);
+}
+
+extern "C" int music_stencil_quotients(const double *n, const double *d, double *q, long long count, void *stream)
+{
+    if (count < 0 || (count > 0 && (!n || !d || !q))) {
+        set_error("music_stencil_quotients: NULL array or negative count");
+        return MUSIC_E_INVAL;
+    }
+    if (count == 0) return MUSIC_OK;
+    k_quot<<<blocks_for(count), BS, 0, (cudaStream_t)stream>>>(n, d, q, count);
     CHECK_LAUNCH();
     return MUSIC_OK;
 }

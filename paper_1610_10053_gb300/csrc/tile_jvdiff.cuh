@@ -308,7 +308,9 @@ __device__ void jvdiff2d_tile(const GridParams &P, const JvConst &K, const doubl
         JV_RECT(0, RX, Y0 - 1, Y1) cell_at(lx, ly, q);
         JV_RECT(X0 - 1, X1, 0, Y0 - 1) cell_at(lx, ly, q);
         JV_RECT(X0 - 1, X1, Y1, RY) cell_at(lx, ly, q);
-        // face velocity u = m / rb at U (as the stencil forms it) and its difference
+        // face velocity u = m / rb at U (as the stencil forms it, by the IEEE
+        // division where the fused stencil's quotient is within 2 ulp of it)
+        // and its difference
         auto face_at = [&](int lx, int ly, int q, int d, double *vel64, float *vel, float *dvel) {
             const int ix[3] = {i0 + lx, j0 + ly, 0};
             long long c, cl;

@@ -18,23 +18,25 @@ struct WLoad {
     }
 };
 
-// 2n / d within 2 ulp of the correctly rounded quotient of 2n by d, with
-// four FP64-pipe operations: Newton's method for the reciprocal of d, started
-// from a single-precision estimate y0 and taken to third order in one step,
-// y = y0 (1 + e + e^2) with e = 1 - d y0, leaves a relative error of e^3
-// (below 2^-63) before the roundings of y and of 2n y.  The estimate is
-// rcp.approx.ftz.f32 of d truncated to single precision (relative error
-// below 2^-21 in all), and both conversions are done on the bit patterns:
-// for d between 2^-120 and 2^120 they only move the exponent and the leading
-// mantissa bits, and the factor 2 goes into the exponent of the estimate
-// (the iteration's steps scale exactly with it).  Any other d (zero,
-// subnormal, huge, infinite, NaN) takes the IEEE division.
-__device__ __forceinline__ double twice_quot(double n, double d)
+// 2^K n / d (K = 0 or 1) within 2 ulp of the correctly rounded quotient,
+// with four FP64-pipe operations: Newton's method for the reciprocal of d,
+// started from a single-precision estimate y0 and taken to third order in
+// one step, y = y0 (1 + e + e^2) with e = 1 - d y0, leaves a relative error
+// of e^3 (below 2^-63) before the roundings of y and of 2^K n y.  The
+// estimate is rcp.approx.ftz.f32 of d truncated to single precision
+// (relative error below 2^-21 in all), and both conversions are done on the
+// bit patterns: for d between 2^-120 and 2^120 they only move the exponent
+// and the leading mantissa bits, and the factor 2^K goes into the exponent
+// of the estimate (the iteration's steps scale exactly with it).  Any other d
+// (zero, subnormal, huge, infinite, NaN) takes the IEEE division.  The
+// result is odd in n and in d: negating either only flips sign bits.
+template <int K>
+__device__ __forceinline__ double newton_quot(double n, double d)
 {
     const int hi = __double2hiint(d);
     const unsigned lo = (unsigned)__double2loint(d);
     const int E = (hi >> 20) & 0x7ff;
-    if ((unsigned)(E - (1023 - 120)) > 240u) return (2.0 * n) / d;
+    if ((unsigned)(E - (1023 - 120)) > 240u) return K ? (2.0 * n) / d : n / d;
     const int fb = (hi & (int)0x80000000) | ((E - 896) << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29);
     float rf;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(fb)));
@@ -42,10 +44,21 @@ __device__ __forceinline__ double twice_quot(double n, double d)
     const int rhi = (rb & (int)0x80000000) | ((((rb >> 23) & 0xff) + 896) << 20) | ((rb & 0x7fffff) >> 3);
     const int rlo = (rb & 7) << 29;
     const double y0 = __hiloint2double(rhi, rlo);
-    const double y2 = __hiloint2double(rhi + (1 << 20), rlo);
+    const double yk = K ? __hiloint2double(rhi + (1 << 20), rlo) : y0;
     const double e = fma(-d, y0, 1.0);
-    return n * fma(y2, fma(e, e, e), y2);
+    return n * fma(yk, fma(e, e, e), yk);
 }
+
+// 2n / d, for van Leer's slope
+__device__ __forceinline__ double twice_quot(double n, double d) { return newton_quot<1>(n, d); }
+
+// n / d, for the specific internal energy E / rho and the face velocities
+// m_d / rbar that the fused 2-D tiles stage.  (The multi-pass stencil keeps
+// the IEEE division: on conducting grids T = (gamma - 1) e enters the
+// radiative flux through differences of neighbouring cells, whose
+// cancellation in radiative equilibrium would turn a quotient 2 ulp off into
+// an operator error above 1e-12 of the oracle's.)
+__device__ __forceinline__ double quot(double n, double d) { return newton_quot<0>(n, d); }
 
 // van Leer's limited slope 2ab / (a + b) of the one-sided differences a and
 // b where a b > 0, else 0 (Sec. 2).  The sign test reads the bit patterns:
@@ -149,15 +162,18 @@ __device__ inline bool face_map(const GridParams &P, const int ix[3], int d, lon
 }
 
 // staggered velocity of the d-face at ix: face momentum over the mean
-// density of the two cells it joins
-template <typename VT>
+// density of the two cells it joins.  The fused 2-D tiles take the quotient
+// by quot (NEWTON); the multi-pass stencil, which also serves the spherical
+// and conducting grids, by the IEEE division.
+template <bool NEWTON, typename VT>
 __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const int ix[3], int d)
 {
     long long c, cl;
     double sgn;
     if (!face_map(P, ix, d, c, cl, sgn)) return 0.0;
     const double rbar = 0.5 * (W(cl) + W(c));
-    return sgn * (W((long long)(2 + d) * P.N + c) / rbar);
+    const double m = W((long long)(2 + d) * P.N + c);
+    return sgn * (NEWTON ? quot(m, rbar) : m / rbar);
 }
 
 // ---------------------------------------------------------------- fused 2-D
@@ -166,7 +182,8 @@ __device__ double face_velocity(const GridParams &P, const WLoad<VT> &W, const i
 // halo of 3 cells below / 2 above in shared memory (RX x RY points, x
 // fastest).  Each intermediate is computed once, and only on the exact
 // sub-rectangle that the tile's residuals reach (the stencil is a cross, not
-// a square), which keeps FP64 divisions near the minimum of 11 per cell:
+// a square), which keeps the FP64 quotients (E / rho, m / rbar, the slopes;
+// each a Newton step for the reciprocal) near the minimum of 11 per cell:
 //   1 ghost-mapped rho, e, p and face velocities u, v (global loads, L1/L2)
 //   2 van Leer slopes of rho, e, u, v along x and y
 //   3 upwind mass and energy fluxes on x- and y-faces
@@ -238,27 +255,27 @@ __device__ void fused2d_tile(const GridParams &P, const double *U, const double 
             const int ix[3] = {i0 + lx, j0 + ly, 0};
             load_cell(P, W, ix, r, E);
         }
-        ee[q] = E / r;
+        ee[q] = quot(E, r);
     };
     auto u_at = [&](int lx, int ly, int q) {
         if (inner) {
             const long long c = cix(lx, ly);
             const double rbar = 0.5 * (W(c - 1) + W(c));
-            uu[q] = W(2 * P.N + c) / rbar;
+            uu[q] = quot(W(2 * P.N + c), rbar);
             return;
         }
         const int ix[3] = {i0 + lx, j0 + ly, 0};
-        uu[q] = face_velocity(P, W, ix, 0);
+        uu[q] = face_velocity<true>(P, W, ix, 0);
     };
     auto v_at = [&](int lx, int ly, int q) {
         if (inner) {
             const long long c = cix(lx, ly);
             const double rbar = 0.5 * (W(c - cs1) + W(c));
-            vv[q] = W(3 * P.N + c) / rbar;
+            vv[q] = quot(W(3 * P.N + c), rbar);
             return;
         }
         const int ix[3] = {i0 + lx, j0 + ly, 0};
-        vv[q] = face_velocity(P, W, ix, 1);
+        vv[q] = face_velocity<true>(P, W, ix, 1);
     };
     TILE_RECT(0, RX, Y0 - 1, Y1) rho_at(lx, ly, q);
     TILE_RECT(X0 - 1, X1, 0, Y0 - 1) rho_at(lx, ly, q);

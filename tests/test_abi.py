@@ -108,3 +108,6 @@ def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
     assert L.music_vanleer_slopes(None, None, None, -1, None) == 1
     assert L.music_vanleer_slopes(None, None, None, 5, None) == 1
     assert L.music_vanleer_slopes(None, None, None, 0, None) == 0
+    assert L.music_stencil_quotients(None, None, None, -1, None) == 1
+    assert L.music_stencil_quotients(None, None, None, 5, None) == 1
+    assert L.music_stencil_quotients(None, None, None, 0, None) == 0
