@@ -337,24 +337,26 @@ JV_FD_BYTES_PER_CELL_2D = 96      # U (4 x 8), R(U) (4 x 8), v (4 x 4) read, Jv 
 JV_DIFF_FLOPS_PER_CELL_2D = 281
 JV_DIFF_BYTES_PER_CELL_2D = 80    # v (16), the 12 linearisation planes (48) read, Jv (16) written
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of one launch on
-# KH 2048^2 (state above L2 size, 32 x 16 tile), scaled to the bench's cells
-JV_DIFF_TRAFFIC_B_PER_CELL_2D = 76.6
-JV_FD_TRAFFIC_B_PER_CELL_2D = 93.3
+# KH 2048^2 (state above L2 size), scaled to the bench's cells; None where
+# the kernel changed after its last 2048^2 capture
+JV_DIFF_TRAFFIC_B_PER_CELL_2D = None
+JV_FD_TRAFFIC_B_PER_CELL_2D = None
 # Preconditioner application (FP32), K Jacobi sweeps: right-hand side 12,
 # each sweep 15, back substitution 33.
 def precond_flops_per_cell(K):
     return 12 + 15 * K + 33
 PRECOND_BYTES_PER_CELL_2D = 52    # r (16), coefficients a_x, a_y, gamma p, gamma E, D (20) read, z (16) written
-PRECOND_TRAFFIC_B_PER_CELL_2D = 84.5  # ncu, KH 2048^2, 32 x 16 tile in two stages (both launches)
+PRECOND_TRAFFIC_B_PER_CELL_2D = None  # (changed since its 2048^2 capture)
 # Residual-type evaluation (FP64): R(U) as in the product without U + eps v,
 # and the assembly sign ((U - C^n) - dt/2 R) 12.
 RES_FLOPS_PER_CELL_2D = 143
 RES_BYTES_PER_CELL_2D = 176       # U, C^n read, F and R(U) written (4 x 8 each), linearisation planes (48)
-RES_TRAFFIC_B_PER_CELL_2D = 164.2 # ncu, F mode on KH 2048^2, 32 x 16 tile
+RES_TRAFFIC_B_PER_CELL_2D = 166.4 # ncu, F mode on KH 2048^2, 16 x 16 tile
 # ncu dram bytes of one launch of each kernel on the bench's own KH 512^2
-# workload with its tuned tiles (MUSIC_TILES=32x16,16x16,32x32,1), cold L2:
-# the launch's reads; its writes stay in the 126 MB L2 (profiles/*_kh512.md)
-TRAFFIC_KH512 = {"residual": 17.457e6, "jv": 16.88e6, "precond": 9.47e6}
+# workload with its tuned tiles (MUSIC_TILES=32x16,16x16,32x32,3), cold L2:
+# the launch's reads; its writes stay in the 126 MB L2 (profiles/*_kh512.md).
+# None: the kernel changed since its last capture of DRAM bytes.
+TRAFFIC_KH512 = {"residual": 17.626e6, "jv": 16.88e6, "precond": None}
 # Peaks derived from the part's unit counts and clock (152 SMs, 2.07 GHz):
 # FP64 2 FMA per SM per clock; FP32 128 FMA per SM per clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -418,10 +420,11 @@ def roofline(mixed, prob, jv_form, alu=None):
     if N == 512 * 512 and (name != "jv" or jv_form == "diff"):
         traffic = TRAFFIC_KH512[name]
         tnote = ("ncu dram read+write of one launch of this workload (tuned tiles, cold L2)" if traffic is not None
-                 else "kernel changed since its last ncu capture (17.04 MB a launch before the change)")
+                 else "kernel changed since its last ncu capture of DRAM bytes")
     else:
         traffic = tpc * N if tpc else None
-        tnote = "ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells"
+        tnote = ("ncu dram read+write per cell on KH 2048^2, scaled to this launch's cells" if tpc
+                 else "kernel changed since its last ncu capture of DRAM bytes")
     return {"kernel": kern, "class": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "traffic_note": tnote,
             "launches": ks[name]["launches"], "ms_per_launch": per, "flops_per_cell": flops,
