@@ -568,11 +568,13 @@ def run_burst(nsolves=256, max_active=16, lane_cells=16384):
 
 
 def run_series(prob, nsteps, every):
-    """Mixing widths over a run (mixed precision, after the timed part): the
-    density-based width of Sec. 3 and, with scalars, the scalar-based one,
-    every `every` steps."""
+    """Diagnostics over a run (mixed precision, after the timed part): the
+    density-based mixing width of Sec. 3 and, with scalars, the scalar-based
+    one, and the maximum speed (the velocity residual of Sec. 6's hydrostatic
+    test), every `every` steps."""
     from paper_1610_10053_gb300 import binding as B
-    out = {"t": [], "h_density": [], "h_scalar": [], "newton_its": [], "gmres_its": []}
+    out = {"t": [], "h_density": [], "h_scalar": [], "max_speed": [], "max_mach": [], "newton_its": [],
+           "gmres_its": []}
     t = 0.0
     with B.Grid(prob, precision=B.MIXED) as g:
         g.set_state(prob.U)
@@ -585,7 +587,10 @@ def run_series(prob, nsteps, every):
             t += st["dt"]
             if (k + 1) % every == 0 or k + 1 == nsteps:
                 out["t"].append(t)
-                out["h_density"].append(g.diagnostics()["mixing_height"])
+                diag = g.diagnostics()
+                out["h_density"].append(diag["mixing_height"])
+                out["max_speed"].append(diag["max_speed"])
+                out["max_mach"].append(diag["max_mach"])
                 out["h_scalar"].append(g.scalar_mixing_width() if prob.q is not None else None)
                 out["newton_its"].append(st["newton_its"])
                 out["gmres_its"].append(st["gmres_its"])
