@@ -191,6 +191,26 @@ def check(code: int):
         raise MusicError(code, last_error())
 
 
+def _require(cond, msg: str):
+    """Argument checks that stay on under python -O: a wrong size would have
+    the library read or write past the caller's buffer."""
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_vecs(*args):
+    """Device vector arguments, each (tensor, entries, dtype, name): type,
+    dtype and size of all of them, then their placement, checked before the
+    library reads or writes that many entries through their pointers."""
+    import torch
+    for t, n, dtype, what in args:
+        _require(isinstance(t, torch.Tensor), "%s must be a torch tensor" % what)
+        _require(t.dtype == dtype, "%s must be %s, not %s" % (what, dtype, t.dtype))
+        _require(t.numel() == n, "%s has %d entries, the grid needs %d" % (what, t.numel(), n))
+    for t, _, _, what in args:
+        _require(t.is_cuda and t.is_contiguous(), "%s must be a contiguous CUDA tensor" % what)
+
+
 def _stream():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -198,7 +218,7 @@ def _stream():
 
 def _ptr(t) -> ctypes.c_void_p:
     import torch
-    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    _require(isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -247,6 +267,8 @@ def desc_from_problem(prob, precision: int = FP64, **over) -> GridDesc:
 def cfl_rate_noalloc(prob, U, rate, precision: int = FP64):
     """max (|u|+c)/dx of the device state U into the one-element device tensor
     `rate`, without any device allocation (music_cfl_rate_noalloc)."""
+    import torch
+    _check_vecs((U, prob.nvars * prob.ncells, torch.float64, "U"), (rate, 1, torch.float64, "rate"))
     d = desc_from_problem(prob, precision)
     check(load().music_cfl_rate_noalloc(ctypes.byref(d), _ptr(U), _ptr(rate), _stream()))
 
@@ -280,7 +302,8 @@ def vanleer_slopes(a, b):
     stencils compute them (music_vanleer_slopes); a and b contiguous float64
     CUDA tensors of one size."""
     import torch
-    assert a.dtype == torch.float64 and b.dtype == torch.float64 and a.numel() == b.numel()
+    _require(a.dtype == torch.float64 and b.dtype == torch.float64 and a.numel() == b.numel(),
+             "a and b must be float64 tensors of one size")
     s = torch.empty_like(a)
     check(load().music_vanleer_slopes(_ptr(a), _ptr(b), _ptr(s), a.numel(), _stream()))
     return s
@@ -291,7 +314,8 @@ def stencil_quotients(n, d):
     (music_stencil_quotients); n and d contiguous float64 CUDA tensors of one
     size."""
     import torch
-    assert n.dtype == torch.float64 and d.dtype == torch.float64 and n.numel() == d.numel()
+    _require(n.dtype == torch.float64 and d.dtype == torch.float64 and n.numel() == d.numel(),
+             "n and d must be float64 tensors of one size")
     q = torch.empty_like(n)
     check(load().music_stencil_quotients(_ptr(n), _ptr(d), _ptr(q), n.numel(), _stream()))
     return q
@@ -356,21 +380,24 @@ class Grid:
     def set_state(self, U):
         import torch
         if isinstance(U, torch.Tensor) and U.is_cuda:
+            _require(U.numel() == self.n, "state has %d entries, the grid %d" % (U.numel(), self.n))
             U = U.contiguous().to(torch.float64)
             check(load().music_set_state(self.h, _ptr(U), 1))
         elif isinstance(U, torch.Tensor):
-            assert U.dtype == torch.float64 and U.is_contiguous() and U.numel() == self.n
+            _require(U.dtype == torch.float64 and U.is_contiguous() and U.numel() == self.n,
+                     "host state must be a contiguous float64 tensor of %d entries" % self.n)
             check(load().music_set_state(self.h, ctypes.c_void_p(U.data_ptr()), 0))
         else:
             a = np.ascontiguousarray(U, dtype=np.float64)
-            assert a.size == self.n
+            _require(a.size == self.n, "state has %d entries, the grid %d" % (a.size, self.n))
             check(load().music_set_state(self.h, a.ctypes.data_as(ctypes.c_void_p), 0))
 
     def get_state_into(self, out):
         """Copy the state into a contiguous float64 host (e.g. pinned) tensor."""
         import torch
-        assert isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
-        assert out.is_contiguous() and out.numel() == self.n
+        _require(isinstance(out, torch.Tensor) and not out.is_cuda and out.dtype == torch.float64
+                 and out.is_contiguous() and out.numel() == self.n,
+                 "out must be a contiguous float64 host tensor of %d entries" % self.n)
         check(load().music_get_state(self.h, ctypes.c_void_p(out.data_ptr()), 0))
         return out
 
@@ -391,6 +418,8 @@ class Grid:
 
     def scalar_operator(self, U, q):
         import torch
+        _check_vecs((U, self.n, torch.float64, "U"),
+                    (q, self.desc.nscalars * self.prob.ncells, torch.float64, "q"))
         S = torch.empty_like(q)
         check(load().music_scalar_operator(self.h, _ptr(U), _ptr(q), _ptr(S), _stream()))
         return S
@@ -403,24 +432,28 @@ class Grid:
     # ---- single-call operators (device tensors in, device tensors out)
     def spatial_operator(self, U):
         import torch
+        _check_vecs((U, self.n, torch.float64, "U"))
         R = torch.empty_like(U)
         check(load().music_spatial_operator(self.h, _ptr(U), _ptr(R), _stream()))
         return R
 
     def residual(self, U, Un, dt: float):
         import torch
+        _check_vecs((U, self.n, torch.float64, "U"), (Un, self.n, torch.float64, "Un"))
         F = torch.empty_like(U)
         check(load().music_residual(self.h, _ptr(U), _ptr(Un), float(dt), _ptr(F), _stream()))
         return F
 
     def jv(self, U, v, dt: float, eps: float = 0.0):
         import torch
+        _check_vecs((U, self.n, torch.float64, "U"), (v, self.n, self.kdtype, "v"))
         out = torch.empty_like(v)
         check(load().music_jv(self.h, _ptr(U), _ptr(v), _ptr(out), float(dt), float(eps), _stream()))
         return out
 
     def precond(self, U, dt: float, r):
         import torch
+        _check_vecs((U, self.n, torch.float64, "U"), (r, self.n, self.kdtype, "r"))
         z = torch.empty_like(r)
         check(load().music_precond_apply(self.h, _ptr(U), float(dt), _ptr(r), _ptr(z), _stream()))
         return z

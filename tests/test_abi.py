@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -111,3 +112,38 @@ def test_invalid_descriptor_is_rejected_without_gpu_work(lib):
     assert L.music_stencil_quotients(None, None, None, -1, None) == 1
     assert L.music_stencil_quotients(None, None, None, 5, None) == 1
     assert L.music_stencil_quotients(None, None, None, 0, None) == 0
+
+
+def test_binding_rejects_mis_sized_vectors_before_any_library_call(lib):
+    """The binding checks the dtype, size and placement of every device
+    vector it hands to the library, which would otherwise read or write the
+    grid's full size through the caller's pointer.  A stand-in grid object
+    (no device state) is enough: the checks come before any call."""
+    torch = pytest.importorskip("torch")
+    from paper_1610_10053_gb300 import binding as B
+    from paper_1610_10053_gb300 import inputs as I
+    p = I.kelvin_helmholtz(n=8)
+    g = object.__new__(B.Grid)
+    g.prob, g.precision, g.h = p, B.MIXED, None
+    g.desc = B.desc_from_problem(p, B.MIXED)
+    g.n = p.U.size
+    U = torch.zeros(g.n, dtype=torch.float64)
+    v32 = torch.zeros(g.n, dtype=torch.float32)
+    cases = [
+        (lambda: g.spatial_operator(U[:-1]), "entries"),
+        (lambda: g.spatial_operator(U.float()), "float64"),
+        (lambda: g.spatial_operator(U), "CUDA"),
+        (lambda: g.residual(U, U[:5], 0.1), "entries"),
+        (lambda: g.jv(U, U, 0.1), "float32"),          # a mixed grid's Krylov vectors are FP32
+        (lambda: g.jv(U, v32[:-4], 0.1), "entries"),
+        (lambda: g.precond(U, 0.1, U), "float32"),
+        (lambda: g.set_state(np.zeros(g.n - 1)), "entries"),
+    ]
+    for call, word in cases:
+        with pytest.raises(ValueError, match=word):
+            call()
+    g.precision = B.FP64
+    with pytest.raises(ValueError, match="float64"):
+        g.jv(U, v32, 0.1)
+    with pytest.raises(ValueError, match="rate"):
+        B.cfl_rate_noalloc(p, U, torch.zeros(2, dtype=torch.float64))
