@@ -128,7 +128,8 @@ typedef struct {
 
 typedef struct music_grid music_grid;
 
-/* Message of the last failed call on this thread (always NUL-terminated).
+/* Service calls (the paper has no counterpart).
+   Message of the last failed call on this thread (always NUL-terminated).
    Returns the full message length. */
 size_t music_last_error(char *buf, size_t len);
 
@@ -140,7 +141,10 @@ const char *music_version(void);
 uint64_t music_kernel_launches(void);
 
 /*
- * Create a grid: validates `desc`, selects the current CUDA device, and
+ * Create a grid: the discretised problem of Sec. 2 (Eqs. 1-3 on the
+ * staggered grid, Crank-Nicolson in time) with the boundaries of Secs. 3-6
+ * and the solver settings of Sec. 2 that `desc` gives.  Validates `desc`,
+ * selects the current CUDA device, and
  * allocates and owns every device buffer the solver needs (state, step
  * constant, Krylov basis, preconditioner coefficients and scratch).  The
  * state starts at zero; set it with music_set_state.  Sizes: periodic
@@ -149,7 +153,8 @@ uint64_t music_kernel_launches(void);
  */
 int music_create_grid(const music_grid_desc *desc, music_grid **out);
 
-/* Free everything owned by the grid.  NULL is accepted.  Synchronises the
+/* Memory management of a grid (no counterpart in the paper).
+   Free everything owned by the grid.  NULL is accepted.  Synchronises the
    device first (the caller may still have work using the grid queued on
    other streams). */
 int music_destroy_grid(music_grid *grid);
@@ -164,7 +169,8 @@ size_t music_state_size(const music_grid *grid);
 /* Device bytes owned by the grid. */
 size_t music_grid_bytes(const music_grid *grid);
 
-/* Copy a state (layout above) into / out of the grid.  `is_device` says
+/* Copy a state (the conserved variables of Eqs. 1-3 in the staggered layout
+   of Sec. 2, described above) into / out of the grid.  `is_device` says
    whether `U` is a device pointer (else host).  Synchronous: waits for all
    work on the device first, then copies. */
 int music_set_state(music_grid *grid, const double *U, int is_device);
@@ -286,6 +292,8 @@ typedef struct {
                                  at most 65536 cells that music_batch_step accepts) */
 
 /*
+ * Autotuner (no counterpart in the paper: a choice of GPU tiling that
+ * changes no result, every shape giving the same bits).
  * Time every candidate tile shape of the grid's fused 2-D kernels on its
  * current state at step size dt (> 0), keep the fastest for this grid, and
  * remember them for the configuration (extent, boundaries, precision,
@@ -300,7 +308,8 @@ typedef struct {
  */
 int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_report *report, void *stream);
 
-/* Set the fused kernels' tile shapes to given candidates ((TX, TY) pairs;
+/* (No counterpart in the paper, as for music_autotune.)
+   Set the fused kernels' tile shapes to given candidates ((TX, TY) pairs;
    NULL keeps that kernel's shape; stencil_tile sets the stencil's Jv mode
    and its R / C^n / F modes alike) and the preconditioner's stage count (1, 2
    or 4; <= 0 keeps it).  MUSIC_E_INVAL for a shape that is not a candidate
@@ -309,7 +318,8 @@ int music_autotune(music_grid *grid, double dt, unsigned flags, music_tune_repor
 int music_set_tiles(music_grid *grid, const int *stencil_tile, const int *precond_tile, int precond_stages);
 int music_get_tiles(const music_grid *grid, int *stencil_tile, int *precond_tile, int *precond_stages);
 
-/* Tile shape (TX, TY) of the persistent batched kernel for this grid: one of
+/* (No counterpart in the paper, as for music_autotune.)
+   Tile shape (TX, TY) of the persistent batched kernel for this grid: one of
    32 x 16, 16 x 32, 64 x 8 (a CTA of 512 threads each, so every shape gives
    bitwise the same step).  music_batch_step runs a batch with the shape of
    its first grid; music_autotune picks it by timing for small grids.
@@ -360,8 +370,10 @@ int music_get_jv_form(const music_grid *grid, int *form);
 int music_set_scalars(music_grid *grid, const double *q, int is_device, void *stream);
 int music_get_scalars(music_grid *grid, double *q, int is_device, void *stream);
 
-/* S_i = -div(c_i rho u) of device partial densities q (nscalars planes)
-   with the fluid frozen at the device state U; S device, same layout. */
+/* The passive scalars' operator (Sec. 2.2): S_i = -div(c_i rho u) of device
+   partial densities q (nscalars planes) with the fluid frozen at the device
+   state U, c_i reconstructed upwind with the van Leer limiter; S device,
+   same layout.  Errors: MUSIC_E_INVAL (no scalars, NULL), MUSIC_E_CUDA. */
 int music_scalar_operator(music_grid *grid, const double *U, const double *q, double *S, void *stream);
 
 /* Mixing width of Sec. 3 from the grid's first two scalars and state:
