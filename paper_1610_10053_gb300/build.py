@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
